@@ -1,0 +1,487 @@
+"""Pins for the CPU oracle against facts fixed by the paper and by mathematics (no GPU).
+
+Each test names what it pins.  The oracle is test infrastructure; these tests are what make it
+trustworthy before any GPU result is compared with it.
+"""
+import itertools
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+from scipy.sparse import coo_matrix
+from scipy.sparse.csgraph import connected_components, minimum_spanning_tree
+
+from oracle import oracle as O
+from paper_2204_11757_gb300 import inputs as I
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ---- hand-worked example (tests/golden/hand_example.txt) ---------------------------------
+
+def _parse_golden():
+    rows = {}
+    ncs = {}
+    with open(os.path.join(GOLDEN, "hand_example.txt")) as fh:
+        for line in fh:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            if line.startswith("nc "):
+                head, rest = line.split(":", 1)
+                nc = int(head.split()[1])
+                parts = [p.split() for p in rest.split("|")]
+                ncs[nc] = parts
+            else:
+                key, rest = line.split(" ", 1)
+                rows[key] = rest
+    return rows, ncs
+
+
+def test_golden_hand_example():
+    """Scores, sort, merges and contraction of a 4-node example worked by hand."""
+    rows, ncs = _parse_golden()
+    trip = [t.split() for t in rows["edges"].split("|")]
+    eu = np.array([int(t[0]) for t in trip]); ev = np.array([int(t[1]) for t in trip])
+    w = np.array([int(t[2]) for t in trip], dtype=np.int32)
+    g = I.csr_from_edges(4, eu, ev, w)
+    assert list(O.degree(g)) == [int(x) for x in rows["degree"].split()]
+    f = O.score(g)
+    exact = [Fraction(s) for s in rows["score_num_den"].split()]
+    bits = [int(b, 16) for b in rows["score_f64_bits"].split()]
+    assert [int(x) for x in f.view(np.uint64)] == bits
+    for fi, ex in zip(f, exact):
+        assert abs(Fraction(float(fi)) - ex) <= Fraction(1, 2 ** 50)
+    order = O.sort_fitness(f)
+    assert list(order) == [int(x) for x in rows["order"].split()]
+    for nc, parts in ncs.items():
+        lv = O.coarsen_level(g, nc)
+        lift, emap, sm, rp, cc, wc = ([int(x) for x in p] for p in parts)
+        assert list(lv.lift) == lift, nc
+        assert list(lv.coarse.emap) == emap, nc
+        assert list(lv.coarse.self_mass) == sm, nc
+        assert list(lv.coarse.graph.rowptr) == rp, nc
+        assert list(lv.coarse.graph.col) == cc, nc
+        assert list(lv.coarse.graph.w) == wc, nc
+
+
+# ---- score closed forms -------------------------------------------------------------------
+
+@pytest.mark.parametrize("n", [4, 5, 9, 30])
+def test_cycle_score_is_two(n):
+    """k-regular with t common neighbours: f = 2(k - t)/k; a cycle (k=2, t=0) gives 2."""
+    f = O.score(I.cycle_graph(n))
+    assert np.all(f == 2.0)
+
+
+@pytest.mark.parametrize("n", [3, 4, 7, 12])
+def test_complete_graph_score(n):
+    """K_n (k = n-1, t = n-2): f = 2/(n-1) (the a and b coordinates are the only terms)."""
+    f = O.score(I.complete_graph(n))
+    np.testing.assert_allclose(f, 2.0 / (n - 1), rtol=1e-15)
+
+
+def test_regular_triangulation_interior_is_four_thirds():
+    """Interior edges of a regular triangulation: degree 6, 2 common neighbours -> 4/3."""
+    nx = 12
+    g = I.tri_mesh_2d(nx, nx, seed=0)
+    # rebuild with every diagonal in the same direction (coin 0 everywhere)
+    ii, jj = np.meshgrid(np.arange(nx), np.arange(nx))
+    vid = jj * nx + ii
+    eu = np.concatenate([vid[:, :-1].ravel(), vid[:-1, :].ravel(), vid[:-1, :-1].ravel()])
+    ev = np.concatenate([vid[:, 1:].ravel(), vid[1:, :].ravel(), vid[1:, 1:].ravel()])
+    g = I.csr_from_edges(nx * nx, eu, ev, np.ones(eu.shape[0], np.int32))
+    f = O.score(g)
+    deg = np.diff(g.rowptr)
+    interior = (deg[g.eu] == 6) & (deg[g.ev] == 6)
+    W = O.dense_weights(g) > 0
+    common = (W[g.eu] & W[g.ev]).sum(axis=1)
+    sel = interior & (common == 2)
+    assert sel.sum() > 50
+    np.testing.assert_allclose(f[sel], 4.0 / 3.0, rtol=1e-15)
+
+
+def _score_identity(g):
+    """||p - q||_1 = 2 - 2 sum_x min(p_x, q_x) for probability vectors p, q; the common
+    coordinates of rows a and b are N(a) n N(b) (a is not in N(a), no self-loops)."""
+    W = O.dense_weights(g)
+    d = W.sum(axis=1)
+    P = W / d[:, None]
+    out = np.empty(g.m)
+    for e in range(g.m):
+        a, b = g.eu[e], g.ev[e]
+        out[e] = 2.0 - 2.0 * np.minimum(P[a], P[b]).sum()
+    return out
+
+
+@pytest.mark.parametrize("seed,weight", [(0, "float"), (1, "int"), (2, "float"), (3, "unit")])
+def test_score_identity_random_weighted(seed, weight):
+    """Pins the weighted degree, the p_ax orientation and the a/b coordinates at once."""
+    dt = np.int32 if weight in ("int", "unit") else np.float64
+    g = I.random_graph(40, 0.2, seed, weight=weight, dtype=dt, connected=True)
+    np.testing.assert_allclose(O.score(g), _score_identity(g), rtol=0, atol=1e-13)
+
+
+def test_score_identity_float32():
+    g = I.random_graph(30, 0.3, 7, weight="float", dtype=np.float32, connected=True)
+    f = O.score(g)
+    assert f.dtype == np.float32
+    np.testing.assert_allclose(f, _score_identity(g), rtol=0, atol=2e-6)
+
+
+def test_score_exact_rational():
+    """The binary64 score is within a few ulps of the exact rational value (int weights)."""
+    g = I.random_graph(14, 0.4, 11, weight="int", dtype=np.int32, connected=True)
+    f = O.score(g)
+    W = O.dense_weights(g).astype(np.int64)
+    d = W.sum(axis=1)
+    for e in range(g.m):
+        a, b = int(g.eu[e]), int(g.ev[e])
+        ex = sum(abs(Fraction(int(W[a, x]), int(d[a])) - Fraction(int(W[b, x]), int(d[b])))
+                 for x in range(g.n))
+        assert abs(Fraction(float(f[e])) - ex) <= ex * Fraction(g.n, 2 ** 52)
+
+
+def test_degree_and_normalise_definitions():
+    g = I.random_graph(25, 0.3, 5, weight="int", dtype=np.int32, connected=True)
+    d = O.degree(g)
+    assert np.array_equal(d, O.dense_weights(g).sum(axis=1).astype(np.int64))
+    p = O.normalise(g, d)
+    rows = np.repeat(np.arange(g.n), np.diff(g.rowptr))
+    assert np.array_equal(p, g.w.astype(np.float64) / d[rows].astype(np.float64))
+
+
+def test_score_range():
+    """0 <= f <= 2 (a difference of two probability vectors)."""
+    g, _ = I.config_graph("s2_tri256_f64")
+    f = O.score(g)
+    assert np.all(f >= 0) and np.all(f <= 2.0 + 1e-12)
+
+
+# ---- sort ------------------------------------------------------------------------------
+
+def test_sort_fitness_is_the_definition():
+    g = I.random_graph(60, 0.15, 3, weight="unit", dtype=np.int32, connected=True)
+    f = O.score(g)
+    order = O.sort_fitness(f)
+    ref = sorted(range(g.m), key=lambda e: (f[e], e))
+    assert list(order) == ref
+    f32 = f.astype(np.float32)
+    assert list(O.sort_fitness(f32)) == sorted(range(g.m), key=lambda e: (f32[e], e))
+
+
+# ---- greedy merge: brute force (P2) --------------------------------------------------------
+
+def _threshold_partition(n, eu, ev, order, n_c):
+    """Components of the shortest prefix of the sorted list that leaves n_c components (all
+    edges if none does), by plain graph search on each prefix."""
+    m = len(order)
+    best = None
+    for T in range(0, m + 1):
+        sel = np.asarray(order[:T], dtype=np.int64)
+        A = coo_matrix((np.ones(T), (eu[sel], ev[sel])), shape=(n, n))
+        k, lab = connected_components(A, directed=False)
+        best = lab
+        if k <= n_c:
+            break
+    return _canonical(best)
+
+
+def _canonical(lab):
+    first = {}
+    out = np.empty(len(lab), dtype=np.int32)
+    for x, l in enumerate(lab):
+        if l not in first:
+            first[l] = len(first)
+        out[x] = first[l]
+    return out
+
+
+def _msf_partition(n, eu, ev, order, n_c):
+    """Components of the n - n_c lightest minimum-spanning-forest edges (rank as weight)."""
+    m = len(order)
+    rank = np.empty(m, dtype=np.int64)
+    rank[np.asarray(order)] = np.arange(m)
+    A = coo_matrix((rank + 1.0, (eu, ev)), shape=(n, n)).tocsr()
+    T = minimum_spanning_tree(A).tocoo()
+    r = np.sort((T.data - 1).astype(np.int64))
+    k = max(0, n - n_c)
+    keep = r[:k]
+    inv = np.asarray(order)[keep]
+    B = coo_matrix((np.ones(len(inv)), (eu[inv], ev[inv])), shape=(n, n))
+    _, lab = connected_components(B, directed=False)
+    return _canonical(lab)
+
+
+def test_greedy_bruteforce_small_graphs():
+    """Oracle loop == literal set-based loop == threshold components == lightest-MSF components,
+    for every target n_c, on random and exhaustive tiny graphs."""
+    cases = []
+    for seed in range(60):
+        n = 3 + seed % 7
+        wt = ["unit", "int", "float"][seed % 3]
+        dt = np.float64 if wt == "float" else np.int32
+        cases.append(I.random_graph(n, 0.5, seed, weight=wt, dtype=dt))
+    # every graph on 5 nodes with unit weights, sampled every 7th edge subset
+    iu, iv = np.triu_indices(5, 1)
+    for mask in range(1, 1 << len(iu), 7):
+        sel = np.array([(mask >> i) & 1 for i in range(len(iu))], dtype=bool)
+        cases.append(I.csr_from_edges(5, iu[sel], iv[sel], np.ones(sel.sum(), np.int32)))
+    checked = 0
+    for g in cases:
+        if g.m == 0:
+            continue
+        f = O.score(g)
+        order = O.sort_fitness(f)
+        edges = list(zip(g.eu.tolist(), g.ev.tolist()))
+        for n_c in range(1, g.n + 1):
+            rep, merged, s, rc = O.greedy_merge(g, order, n_c)
+            lift, nca = O.relabel(rep)
+            lit, nlit = O.greedy_literal(g.n, edges, f.tolist(), n_c)
+            assert nca == nlit and np.array_equal(lift, lit)
+            thr = _threshold_partition(g.n, g.eu, g.ev, order, n_c)
+            assert np.array_equal(lift, thr)
+            msf = _msf_partition(g.n, g.eu, g.ev, order, n_c)
+            assert np.array_equal(lift, msf)
+            ncc = connected_components(coo_matrix((np.ones(g.m), (g.eu, g.ev)),
+                                                  shape=(g.n, g.n)), directed=False)[0]
+            assert nca == max(n_c, ncc)
+            assert (rc == O.WARN_TARGET_NOT_REACHED) == (ncc > n_c)
+            assert merged.sum() == g.n - nca
+            checked += 1
+    assert checked > 300
+
+
+def test_relabel_is_first_occurrence_order():
+    g = I.random_graph(50, 0.1, 9, weight="float", dtype=np.float64, connected=True)
+    lv = O.coarsen_level(g, 17)
+    # ids appear in increasing order of first occurrence when scanning nodes 0..n-1
+    seen = -1
+    for x in range(g.n):
+        if lv.lift[x] > seen:
+            assert lv.lift[x] == seen + 1
+            seen = lv.lift[x]
+    assert seen + 1 == lv.n_c == 17
+
+
+# ---- contraction (P5) ----------------------------------------------------------------------
+
+def _check_contraction(g, lv):
+    co = lv.coarse
+    C = O.membership(lv.lift, lv.n_c)
+    A = C.T @ O.dense_weights(g) @ C          # Definition 1 summed over super-node pairs
+    off = A - np.diag(np.diag(A))
+    Gc = O.dense_weights(co.graph)
+    np.testing.assert_allclose(Gc, off, rtol=1e-12, atol=0)
+    np.testing.assert_allclose(2.0 * co.self_mass.astype(np.float64), np.diag(A), rtol=1e-12)
+    # weight conservation
+    tot = g.w_und.astype(np.float64).sum()
+    np.testing.assert_allclose(co.a_und.astype(np.float64).sum()
+                               + co.self_mass.astype(np.float64).sum(), tot, rtol=1e-12)
+    # emap: fine edge -> coarse edge with matching endpoints
+    U = lv.lift[g.eu]; V = lv.lift[g.ev]
+    inter = U != V
+    assert np.all((co.emap >= 0) == inter)
+    ce = co.emap[inter]
+    assert np.array_equal(co.graph.eu[ce], np.minimum(U, V)[inter])
+    assert np.array_equal(co.graph.ev[ce], np.maximum(U, V)[inter])
+    # every super-node induces a connected subgraph of G
+    for s in range(lv.n_c):
+        mem = np.nonzero(lv.lift == s)[0]
+        if len(mem) > 1:
+            sub = O.dense_weights(g)[np.ix_(mem, mem)] > 0
+            assert connected_components(sub, directed=False)[0] == 1
+    # symmetric coarse CSR with sorted rows
+    rows = np.repeat(np.arange(lv.n_c), np.diff(co.graph.rowptr))
+    for r in range(lv.n_c):
+        seg = co.graph.col[co.graph.rowptr[r]:co.graph.rowptr[r + 1]]
+        assert np.all(np.diff(seg) > 0)
+    assert not np.any(co.graph.col == rows)
+
+
+@pytest.mark.parametrize("seed,weight,nc", [(0, "int", 10), (1, "float", 5), (2, "unit", 25),
+                                            (3, "float", 1), (4, "int", 30)])
+def test_contraction_matches_dense_definition(seed, weight, nc):
+    dt = np.float64 if weight == "float" else np.int32
+    g = I.random_graph(30, 0.15, seed, weight=weight, dtype=dt, connected=(seed % 2 == 0))
+    lv = O.coarsen_level(g, nc)
+    _check_contraction(g, lv)
+
+
+def test_contraction_float32_order():
+    """F32 coarse weights are sums in ascending fine edge id (checked by replaying them)."""
+    g = I.random_graph(40, 0.2, 21, weight="float", dtype=np.float32, connected=True)
+    lv = O.coarsen_level(g, 6)
+    co = lv.coarse
+    for k in range(co.m_c):
+        es = np.nonzero(co.emap == k)[0]
+        s = np.float32(0)
+        for e in es:
+            s = np.float32(s + g.w_und[e])
+        assert s == co.a_und[k]
+
+
+def test_int_overflow_is_reported():
+    g = I.csr_from_edges(3, np.array([0, 1]), np.array([1, 2]),
+                         np.array([2 ** 31 - 1, 2 ** 31 - 1], dtype=np.int32))
+    lift = np.array([0, 1, 1], dtype=np.int32)
+    O.contract(g, lift, 2)  # one fine edge per coarse edge: fits
+    g2 = I.csr_from_edges(3, np.array([0, 0]), np.array([1, 2]),
+                          np.array([2 ** 31 - 1, 2 ** 31 - 1], dtype=np.int32))
+    with pytest.raises(OverflowError):
+        O.contract(g2, lift, 2)
+
+
+# ---- spectral pins: Theorem 1 (P1) and the lift invariant (P3) ----------------------------
+
+def _lift_eigs(W, lift, n_c):
+    return np.linalg.eigvalsh(O.laplacian_norm(O.lift_weights(W, lift, n_c)))
+
+
+def test_theorem1_single_merges():
+    """||Lambda - Lambda_hat||_inf <= f(a, b) for every single-edge merge (Theorem 1)."""
+    checked = 0
+    for seed in range(40):
+        n = 4 + seed % 5
+        wt = ["float", "int", "unit"][seed % 3]
+        dt = np.float64 if wt == "float" else np.int32
+        g = I.random_graph(n, 0.6, 100 + seed, weight=wt, dtype=dt, connected=True)
+        W = O.dense_weights(g)
+        lam = np.linalg.eigvalsh(O.laplacian_norm(W))
+        f = O.score(g)
+        for e in range(g.m):
+            a, b = int(g.eu[e]), int(g.ev[e])
+            rep = np.arange(n, dtype=np.int32)
+            rep[b] = a
+            lift, nc = O.relabel(rep)
+            lam_hat = _lift_eigs(W, lift, nc)
+            assert np.max(np.abs(lam - lam_hat)) <= f[e] + 1e-12
+            checked += 1
+    assert checked > 200
+
+
+def test_theorem2_multi_merges():
+    """s merges whose scores are all <= eps move eigenvalues by at most s(s+1)/2 eps."""
+    for seed in range(20):
+        g = I.random_graph(8, 0.5, 300 + seed, weight="float", dtype=np.float64, connected=True)
+        W = O.dense_weights(g)
+        lam = np.linalg.eigvalsh(O.laplacian_norm(W))
+        for n_c in range(2, 8):
+            lv = O.coarsen_level(g, n_c)
+            s = int(lv.merged.sum())
+            eps = float(lv.f[lv.merged].max())
+            lam_hat = _lift_eigs(W, lv.lift, lv.n_c)
+            assert np.max(np.abs(lam - lam_hat)) <= s * (s + 1) / 2 * eps + 1e-12
+
+
+def test_lift_invariant_small():
+    """eig(L(G_hat)) = eig(L_c) plus (n - n_c) eigenvalues equal to 1, where L_c is the
+    normalized Laplacian of C^T W C built from the oracle's coarse graph and self-mass."""
+    for seed in range(12):
+        g = I.random_graph(9, 0.4, 500 + seed, weight="float", dtype=np.float64,
+                           connected=True)
+        W = O.dense_weights(g)
+        for n_c in (2, 4, 7):
+            lv = O.coarsen_level(g, n_c)
+            Ac = O.dense_weights(lv.coarse.graph) + 2.0 * np.diag(lv.coarse.self_mass)
+            lc = np.linalg.eigvalsh(O.laplacian_norm(Ac))
+            lh = _lift_eigs(W, lv.lift, lv.n_c)
+            ref = np.sort(np.concatenate([lc, np.ones(g.n - lv.n_c)]))
+            np.testing.assert_allclose(lh, ref, atol=1e-10)
+
+
+def test_lift_matrix_form_matches_definition():
+    """C S^-1 (C^T W C) S^-1 C^T equals Definition 2's double sum (used for large checks)."""
+    g = I.random_graph(12, 0.4, 77, weight="float", dtype=np.float64, connected=True)
+    lv = O.coarsen_level(g, 5)
+    W = O.dense_weights(g)
+    C = O.membership(lv.lift, lv.n_c)
+    Sinv = np.diag(1.0 / C.sum(axis=0))
+    np.testing.assert_allclose(C @ Sinv @ (C.T @ W @ C) @ Sinv @ C.T,
+                               O.lift_weights(W, lv.lift, lv.n_c), rtol=1e-13)
+
+
+@pytest.mark.slow
+def test_c1_mesh_eigen_check():
+    """64x64 triangle mesh, one level to 2048: the lift invariant by dense FP64 eigensolves
+    (4096^2 and 2048^2), and the 10 smallest eigenvalues of G against the lift."""
+    g, cfg = I.config_graph("c1_tri64_unit")
+    lv = O.coarsen_level(g, 2048)
+    assert lv.n_c == 2048 and lv.status == O.OK
+    W = O.dense_weights(g)
+    C = O.membership(lv.lift, lv.n_c)
+    A = C.T @ W @ C
+    Ac = O.dense_weights(lv.coarse.graph) + 2.0 * np.diag(lv.coarse.self_mass.astype(float))
+    np.testing.assert_array_equal(A, Ac)
+    lc = np.linalg.eigvalsh(O.laplacian_norm(Ac))
+    sizes = C.sum(axis=0)
+    What = (C / sizes) @ A @ (C / sizes).T
+    lh = np.linalg.eigvalsh(O.laplacian_norm(What))
+    ref = np.sort(np.concatenate([lc, np.ones(g.n - lv.n_c)]))
+    np.testing.assert_allclose(lh, ref, atol=1e-10)
+    lam = np.linalg.eigvalsh(O.laplacian_norm(W))
+    # smallest eigenvalue is the trivial 0 for both; the lift's spectrum stays in [0, 2]
+    assert abs(lam[0]) < 1e-10 and abs(lh[0]) < 1e-10
+    assert lh[-1] <= 2.0 + 1e-10
+    assert np.all(np.abs(lam[:10] - lh[:10]) <= 2.0)
+
+
+# ---- backward (P6) --------------------------------------------------------------------------
+
+def test_contract_backward_adjoint_and_fd():
+    g = I.random_graph(30, 0.2, 41, weight="float", dtype=np.float64, connected=True)
+    lv = O.coarsen_level(g, 8)
+    co = lv.coarse
+    S = np.zeros((co.m_c, g.m))
+    for e in range(g.m):
+        if co.emap[e] >= 0:
+            S[co.emap[e], e] = 1.0
+    rng = np.random.default_rng(0)
+    gw = rng.standard_normal(co.m_c)
+    gr = O.contract_backward(co.emap, gw)
+    np.testing.assert_array_equal(gr, S.T @ gw)
+    # adjoint identity <S w, g> = <w, S^T g>
+    w = g.w_und
+    np.testing.assert_allclose(np.dot(co.a_und, gw), np.dot(w, gr), rtol=1e-12)
+    # central differences of L(w) = sum_k a_k(w) g_k with the assignment held fixed
+    h = 1e-3
+    for e in rng.choice(g.m, 10, replace=False):
+        wp = w.copy(); wp[e] += h
+        wm = w.copy(); wm[e] -= h
+        ap = O.contract(_with_weights(g, wp), lv.lift, lv.n_c).a_und
+        am = O.contract(_with_weights(g, wm), lv.lift, lv.n_c).a_und
+        fd = (np.dot(ap, gw) - np.dot(am, gw)) / (2 * h)
+        assert abs(fd - gr[e]) < 1e-9
+
+
+def _with_weights(g, w_und):
+    return I.csr_from_edges(g.n, g.eu, g.ev, w_und)
+
+
+# ---- multilevel and batch drivers -------------------------------------------------------------
+
+def test_multilevel_composition():
+    g, _ = I.config_graph("s2_tri256_f64")
+    levels, total = O.coarsen(g, 64, "halving")
+    assert [lv.n_c for lv in levels] == [g.n // 2 ** l for l in range(1, 7)]
+    # the composed map is onto [0, n_c) and the final coarse graph conserves weight
+    assert set(np.unique(total)) == set(range(levels[-1].n_c))
+    sm = 0.0
+    for lv in levels:
+        sm += lv.coarse.self_mass.sum()
+    np.testing.assert_allclose(levels[-1].coarse.a_und.sum() + sm, g.w_und.sum(), rtol=1e-11)
+    em = O.compose_emaps(levels)
+    fin = levels[-1].coarse.graph
+    U = total[g.eu]; V = total[g.ev]
+    assert np.all((em >= 0) == (U != V))
+    sel = em >= 0
+    assert np.array_equal(fin.eu[em[sel]], np.minimum(U, V)[sel])
+
+
+def test_batch_oracle_is_per_graph():
+    b, _ = I.config_graph("s5_batch40_f32")
+    res = O.coarsen_batch(b, 8, "halving")
+    for gi, (levels, total) in enumerate(res):
+        n = int(b.graph_ptr[gi + 1] - b.graph_ptr[gi])
+        assert levels[-1].n_c == n // 8
