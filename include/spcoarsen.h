@@ -1,0 +1,243 @@
+/*
+ * spcoarsen -- GB300 (sm_103a) spectral-bound graph coarsening.
+ *
+ * C ABI of libspcoarsen.so.  It implements the data-parallel path of Brissette, Huang and
+ * Slota, "Parallel coarsening of graph data with spectral guarantees" (arXiv 2204.11757):
+ *   1. every undirected edge (a, b) gets the score f(a, b) = || w_a/d_a - w_b/d_b ||_1
+ *      (Theorem 1, Algorithm 1 fitness loop);
+ *   2. edges are taken in ascending (f, edge id) order and their end points merged into
+ *      super-nodes, passing over pairs already merged, until n_c super-nodes remain
+ *      (Algorithm 1 sort and merge loop);
+ *   3. the graph is contracted: a(U, V) = sum of w(x, y) over x in U, y in V (Definition 1),
+ *      and the step is repeated level by level on the coarse graph (Section 4, recomputing the
+ *      norms after partial coarsening).
+ *
+ * Conventions shared by every entry point
+ *   - Graphs are symmetric CSR: rowptr int64[n+1] (rowptr[0] = 0, rowptr[n] = nnz = 2m),
+ *     col int32[nnz] strictly ascending inside each row, no self-loops, every entry (x, y, w)
+ *     mirrored by (y, x, w) with a bit-identical weight, weights finite and > 0.
+ *   - The undirected edge id (eid) of {u, v}, u < v, is its rank in lexicographic (u, v)
+ *     order, i.e. the order of the upper-triangle entries read row by row.  m < 2^31.
+ *   - Weight types: SPC_I32 (degrees and scores exact in int64/binary64; coarse sums must fit
+ *     in int32), SPC_F32 (degrees, normalised rows and scores in binary32), SPC_F64 (binary64).
+ *     Scores are binary64 for SPC_I32/SPC_F64 and binary32 for SPC_F32.  All arithmetic is
+ *     IEEE round-to-nearest without FMA contraction, in a fixed order (sums run in ascending
+ *     column / edge id), so results are reproducible bit for bit.
+ *   - Pointers: unless stated otherwise a pointer may be device memory or host memory (pinned
+ *     or pageable); the library classifies it with cudaPointerGetAttributes and stages host
+ *     data through its own device workspace.  Inputs are only read.  All work is issued on the
+ *     context's stream; an entry point returns after that stream has finished the call's work
+ *     (it synchronises once, to read the status word and data-dependent sizes).
+ *   - Errors: every entry point returns an spc_status and never aborts the process.  Invalid
+ *     input detected on the device is reported through a device status word read back at the
+ *     end of the call.  Device-side waits are bounded; a wait that gives up reports
+ *     SPC_ERR_TIMEOUT.  After an error the outputs are unspecified but the context stays usable.
+ *   - Threading: a context is not thread-safe; use one context per host thread / stream.
+ */
+#ifndef SPCOARSEN_H
+#define SPCOARSEN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define SPC_API __attribute__((visibility("default")))
+#else
+#define SPC_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SPC_OK = 0,
+    SPC_WARN_TARGET_NOT_REACHED = 1, /* fewer merges possible than asked (more components than
+                                        n_c); the partition is the connected components      */
+    SPC_ERR_INVALID_ARG = -1,        /* null pointer, n_c < 1, bad dtype, sizes inconsistent  */
+    SPC_ERR_NOT_SYMMETRIC = -2,      /* an entry (x,y,w) without a bit-identical (y,x,w)       */
+    SPC_ERR_SELF_LOOP = -3,          /* an entry (x,x)                                         */
+    SPC_ERR_UNSORTED = -4,           /* columns not strictly ascending, or out of [0,n), or a
+                                        rowptr that is not monotone                            */
+    SPC_ERR_OOM = -5,                /* workspace allocation failed                            */
+    SPC_ERR_CUDA = -6,               /* a CUDA runtime call failed                             */
+    SPC_ERR_TIMEOUT = -7,            /* a bounded device-side wait gave up                     */
+    SPC_ERR_OVERFLOW = -8,           /* an SPC_I32 coarse weight does not fit in int32         */
+    SPC_ERR_BAD_WEIGHT = -9,         /* a weight <= 0, NaN or infinite                         */
+    SPC_ERR_TOO_LARGE = -10          /* m >= 2^31 or n >= 2^31                                 */
+} spc_status;
+
+typedef enum { SPC_I32 = 0, SPC_F32 = 1, SPC_F64 = 2 } spc_dtype;
+
+/* A symmetric CSR graph (see the conventions above). */
+typedef struct {
+    int64_t n;              /* number of nodes                                   */
+    int64_t nnz;            /* stored entries, 2m                                */
+    const int64_t* rowptr;  /* [n+1]                                             */
+    const int32_t* col;     /* [nnz]                                             */
+    const void* w;          /* [nnz] of type wtype                               */
+    spc_dtype wtype;
+} spc_csr;
+
+/* Device-memory allocator used for the context's workspace (for example PyTorch's caching
+ * allocator).  alloc returns a device pointer aligned to at least 256 bytes, or NULL.  When
+ * the allocator passed to spc_context_create is NULL the library uses cudaMalloc/cudaFree. */
+typedef struct {
+    void* (*alloc)(void* ctx, size_t bytes);
+    void (*free)(void* ctx, void* ptr);
+    void* ctx;
+} spc_allocator;
+
+typedef struct {
+    int32_t levels;     /* 0 or 1: one pass of Algorithm 1 straight to n_c.  L > 1: L levels,
+                           level l (1-based) targets max(n_c, floor(n / 2^l)) super-nodes and
+                           the last level targets n_c (Section 4: recompute the norms after
+                           partial coarsening; Section 3 coarsens by halves).                 */
+    int32_t validate;   /* 1: check the input graph (S0) before the first level; 0: trust it */
+    int32_t use_graph;  /* 1: capture the schedule in a CUDA graph and replay it on later calls
+                           with the same shapes; 0: launch kernel by kernel                   */
+    int32_t schedule;   /* score-kernel schedule: 0 auto (autotuned), 1 edge tiles
+                           (one thread per edge), 2 warp per row                              */
+} spc_options;
+
+/* Per-level results retained by the context after spc_coarsen / spc_coarsen_batched /
+ * spc_contract.  All pointers are device pointers owned by the context, valid until the next
+ * coarsening call on the context or its destruction.  Level l maps the level-l input graph
+ * (level 0 = the caller's graph) onto the level-l coarse graph.                            */
+typedef struct {
+    int64_t n;              /* nodes of this level's input graph                         */
+    int64_t m;              /* undirected edges of this level's input graph               */
+    int64_t n_c;            /* super-nodes produced                                       */
+    int64_t m_c;            /* coarse undirected edges                                    */
+    int64_t m_inter;        /* fine edges joining two different super-nodes               */
+    int32_t status;         /* SPC_OK or SPC_WARN_TARGET_NOT_REACHED for this level        */
+    spc_dtype wtype;        /* weight type of both graphs                                 */
+    const void* score;      /* [m]   f per fine edge, binary64 or binary32 (scoretype)     */
+    spc_dtype scoretype;    /* SPC_F64 or SPC_F32                                         */
+    const int32_t* lift;    /* [n]   super-node of every fine node                        */
+    const int32_t* emap;    /* [m]   coarse undirected edge of every fine edge, -1 inside  */
+    const void* self_mass;  /* [n_c] weight inside every super-node (int64 for SPC_I32)    */
+    const void* a_und;      /* [m_c] coarse undirected weights, coarse edge id order       */
+    const int64_t* rowptr_c;/* [n_c+1] coarse CSR                                         */
+    const int32_t* col_c;   /* [2 m_c]                                                    */
+    const void* w_c;        /* [2 m_c]                                                    */
+    const int32_t* perm;    /* [m_inter] inter-super-node fine edges sorted by (coarse edge,
+                               fine edge)                                                 */
+    const int32_t* seg;     /* [m_c+1] perm[seg[k] .. seg[k+1]) are coarse edge k's edges   */
+    const int64_t* graph_ptr_c; /* [B+1] super-node offsets per graph (batched calls), else NULL */
+    float ms;               /* device time of the level in milliseconds (CUDA events), or -1 */
+} spc_level;
+
+typedef struct spc_context spc_context;
+
+/* ---- context ---------------------------------------------------------------------------- */
+
+/* Create a context on the current CUDA device.  `stream` is a cudaStream_t (NULL: the legacy
+ * default stream).  `allocator` may be NULL (cudaMalloc).  The context owns its workspace,
+ * its captured CUDA graphs and the retained per-level results. */
+SPC_API spc_status spc_context_create(spc_context** out, const spc_allocator* allocator, void* stream);
+
+/* Destroy a context and free everything it owns.  NULL is accepted. */
+SPC_API void spc_context_destroy(spc_context* ctx);
+
+/* Change the stream later calls are issued on (captured graphs are re-captured). */
+SPC_API spc_status spc_context_set_stream(spc_context* ctx, void* stream);
+
+/* Human-readable name of a status code (static storage). */
+SPC_API const char* spc_status_string(spc_status status);
+
+/* Default options: levels 1, validate 1, use_graph 1, schedule 0. */
+SPC_API spc_options spc_default_options(void);
+
+/* ---- the full method ---------------------------------------------------------------------- */
+
+/* Coarsen g to n_c super-nodes (Algorithm 1, repeated per options->levels).
+ *   lift_out[n]     super-node (at the last level) of every node of g, ids ordered by smallest
+ *                   member node id (device or host pointer, caller-allocated)
+ *   n_c_actual      number of super-nodes at the last level (host pointer, may be NULL)
+ * Per-level results (scores, maps, coarse graphs) are retained; see spc_get_level.  The last
+ * level's coarse graph is the coarsened graph G_c.  n_c >= n returns the identity.
+ * Returns SPC_WARN_TARGET_NOT_REACHED if some level had more connected components than its
+ * target. */
+SPC_API spc_status spc_coarsen(spc_context* ctx, const spc_csr* g, int64_t n_c, const spc_options* options,
+                       int32_t* lift_out, int64_t* n_c_actual);
+
+/* Batched coarsening of B independent graphs stored as one block-diagonal CSR: graph b owns
+ * nodes [graph_ptr[b], graph_ptr[b+1]) and has edges only among them.  Graph b is coarsened
+ * to its own targets: max(1, floor(n_b / ratio)) at the last level, with `levels` halving
+ * levels as in spc_options (ratio must then be 2^levels).  All graphs are processed by the
+ * same kernel launches (no per-graph launches).
+ *   graph_ptr[B+1]    int64, device or host
+ *   lift_out[n]       global super-node ids; graph b's super-nodes are
+ *                     [graph_ptr_c_out[b], graph_ptr_c_out[b+1])
+ *   graph_ptr_c_out[B+1] int64 (device or host, may be NULL) */
+SPC_API spc_status spc_coarsen_batched(spc_context* ctx, const spc_csr* g, const int64_t* graph_ptr,
+                               int64_t B, int64_t ratio, const spc_options* options,
+                               int32_t* lift_out, int64_t* graph_ptr_c_out);
+
+/* Number of levels retained by the last coarsening call, and access to one of them. */
+SPC_API int32_t spc_level_count(const spc_context* ctx);
+SPC_API spc_status spc_get_level(const spc_context* ctx, int32_t level, spc_level* out);
+
+/* Copy `bytes` from src to dst on the context's stream and wait for it.  Either side may be
+ * host or device memory; used to read retained results into caller buffers. */
+SPC_API spc_status spc_copy(spc_context* ctx, void* dst, const void* src, size_t bytes);
+
+/* ---- single steps (the same kernels spc_coarsen runs) ------------------------------------- */
+
+/* S0-S3: validate g, weighted degrees, normalised rows, and the score of every undirected
+ * edge in eid order (Theorem 1; Algorithm 1 fitness loop).  f_out[m] is binary64 for
+ * SPC_I32/SPC_F64 and binary32 for SPC_F32.  *m_out (host, may be NULL) receives m. */
+SPC_API spc_status spc_score(spc_context* ctx, const spc_csr* g, void* f_out, int64_t* m_out);
+
+/* S4: edge ids sorted by (f, eid) ascending (Algorithm 1's sort; ties by node id).
+ * f[m] of type ftype (SPC_F32 or SPC_F64, values >= +0); order_out[m] int32. */
+SPC_API spc_status spc_sort_fitness(spc_context* ctx, int64_t m, const void* f, spc_dtype ftype,
+                            int32_t* order_out);
+
+/* S5-S6: the merge loop of Algorithm 1 given scores f[m] (as produced by spc_score): the
+ * partition reached by merging in (f, eid) order until n_c super-nodes remain, and its
+ * canonical lift (ids by smallest member).  merged_out[m] (uint8, may be NULL) marks the edges
+ * that performed a merge. */
+SPC_API spc_status spc_select_merges(spc_context* ctx, const spc_csr* g, const void* f, int64_t n_c,
+                             int32_t* lift_out, uint8_t* merged_out, int64_t* n_c_actual);
+
+/* S7: contract g by a given lift (values in [0, n_c), every id used) -- Definition 1.
+ * Results are retained as level 0 (spc_get_level); *m_c_out (host, may be NULL) gets m_c.
+ * Returns SPC_ERR_OVERFLOW if an SPC_I32 coarse weight exceeds int32. */
+SPC_API spc_status spc_contract(spc_context* ctx, const spc_csr* g, const int32_t* lift, int64_t n_c,
+                        int64_t* m_c_out);
+
+/* S7 weights only, the assignment held fixed: a_und[k] = sum over perm[seg[k] .. seg[k+1]) of
+ * w_und[e], summed in that (ascending eid) order.  w_und[m] and a_und[m_c] of type wtype
+ * (SPC_F32 or SPC_F64), perm/seg as retained by a contraction.  Device pointers. */
+SPC_API spc_status spc_contract_forward(spc_context* ctx, const int32_t* perm, const int32_t* seg,
+                                int64_t m_c, const void* w_und, spc_dtype wtype, void* a_und);
+
+/* S9: gradient of the weight contraction with the assignment held fixed:
+ * grad_w[e] = grad_a[emap[e]] when emap[e] >= 0, else 0.  emap[m] int32; grad_a[m_c] and
+ * grad_w[m] of type dtype (SPC_F32 or SPC_F64).  Device pointers. */
+SPC_API spc_status spc_contract_backward(spc_context* ctx, const int32_t* emap, int64_t m,
+                                 const void* grad_a, void* grad_w, spc_dtype dtype);
+
+/* Fine edge -> last-level coarse edge through all retained levels (-1 once inside a
+ * super-node).  emap_out[m of level 0] int32, device or host. */
+SPC_API spc_status spc_compose_emap(spc_context* ctx, int32_t* emap_out);
+
+/* ---- timing ------------------------------------------------------------------------------- */
+
+/* Record CUDA events around every launch of the kernels whose name contains `kernel_substr`
+ * (NULL or "" switches it off); spc_kernel_time returns the launches seen and their summed
+ * device time since the last call to spc_time_kernel. */
+SPC_API spc_status spc_time_kernel(spc_context* ctx, const char* kernel_substr);
+SPC_API spc_status spc_kernel_time(spc_context* ctx, int64_t* launches, double* total_ms);
+
+/* Number of kernel launches issued by the context since it was created (replayed graph
+ * launches count their kernel nodes). */
+SPC_API int64_t spc_launch_count(const spc_context* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SPCOARSEN_H */

@@ -1,0 +1,773 @@
+// C ABI of libspcoarsen: context, workspace, host staging, the level driver and the entry
+// points declared in include/spcoarsen.h.
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+
+#include "spc_internal.cuh"
+
+namespace spc {
+
+static thread_local char g_cuda_err[512];
+
+void set_last_cuda_error(cudaError_t e, const char* what, const char* file, int line) {
+    snprintf(g_cuda_err, sizeof(g_cuda_err), "%s (%s) at %s:%d: %s", cudaGetErrorName(e), what,
+             file, line, cudaGetErrorString(e));
+}
+
+spc_status status_from_bits(uint32_t bits) {
+    if (bits & DEV_UNSORTED) return SPC_ERR_UNSORTED;
+    if (bits & DEV_SELF_LOOP) return SPC_ERR_SELF_LOOP;
+    if (bits & DEV_BAD_WEIGHT) return SPC_ERR_BAD_WEIGHT;
+    if (bits & DEV_NOT_SYMMETRIC) return SPC_ERR_NOT_SYMMETRIC;
+    if (bits & DEV_TIMEOUT) return SPC_ERR_TIMEOUT;
+    if (bits & DEV_OVERFLOW) return SPC_ERR_OVERFLOW;
+    if (bits & DEV_TOO_LARGE) return SPC_ERR_TOO_LARGE;
+    if (bits & DEV_BAD_ARG) return SPC_ERR_INVALID_ARG;
+    return SPC_OK;
+}
+
+static spc_status raw_alloc(spc_context* ctx, size_t bytes, void** out) {
+    *out = nullptr;
+    if (bytes == 0) bytes = 256;
+    if (ctx->has_allocator) {
+        *out = ctx->allocator.alloc(ctx->allocator.ctx, bytes);
+        if (!*out) return SPC_ERR_OOM;
+    } else {
+        cudaError_t e = cudaMalloc(out, bytes);
+        if (e != cudaSuccess) {
+            (void)cudaGetLastError();
+            *out = nullptr;
+            return SPC_ERR_OOM;
+        }
+    }
+    ctx->blocks.push_back(Block{*out, bytes});
+    return SPC_OK;
+}
+
+static void raw_free(spc_context* ctx, void* p) {
+    if (!p) return;
+    for (size_t i = 0; i < ctx->blocks.size(); ++i) {
+        if (ctx->blocks[i].p == p) {
+            ctx->blocks[i] = ctx->blocks.back();
+            ctx->blocks.pop_back();
+            break;
+        }
+    }
+    if (ctx->has_allocator) ctx->allocator.free(ctx->allocator.ctx, p);
+    else cudaFree(p);
+}
+
+spc_status ensure(spc_context* ctx, Buf& b, size_t bytes) {
+    bytes = (bytes + 255) & ~(size_t)255;
+    if (bytes == 0) bytes = 256;
+    if (b.p && b.bytes >= bytes) return SPC_OK;
+    if (b.p) {
+        // the old block may still be read by queued work
+        SPC_CUDA(cudaStreamSynchronize(ctx->stream));
+        raw_free(ctx, b.p);
+        b.p = nullptr;
+        b.bytes = 0;
+    }
+    void* p = nullptr;
+    SPC_TRY(raw_alloc(ctx, bytes, &p));
+    b.p = p;
+    b.bytes = bytes;
+    return SPC_OK;
+}
+
+void free_all(spc_context* ctx) {
+    cudaStreamSynchronize(ctx->stream);
+    while (!ctx->blocks.empty()) raw_free(ctx, ctx->blocks.back().p);
+}
+
+void before_launch(spc_context* ctx, const char* name) {
+    Timer& t = ctx->timer;
+    ctx->launches += 1;
+    if (!t.on || !strstr(name, t.substr.c_str())) return;
+    cudaEvent_t a, b;
+    if (t.pool.size() >= 2) {
+        a = t.pool.back(); t.pool.pop_back();
+        b = t.pool.back(); t.pool.pop_back();
+    } else {
+        cudaEventCreate(&a);
+        cudaEventCreate(&b);
+    }
+    cudaEventRecord(a, ctx->stream);
+    t.pending.push_back({a, b});
+}
+
+void after_launch(spc_context* ctx, const char* name) {
+    Timer& t = ctx->timer;
+    if (!t.on || !strstr(name, t.substr.c_str())) return;
+    cudaEventRecord(t.pending.back().second, ctx->stream);
+}
+
+spc_status sync_status(spc_context* ctx) {
+    SPC_CUDA(cudaMemcpyAsync(ctx->h_status, ctx->d_status, sizeof(uint32_t),
+                             cudaMemcpyDeviceToHost, ctx->stream));
+    SPC_CUDA(cudaStreamSynchronize(ctx->stream));
+    return status_from_bits(*ctx->h_status);
+}
+
+// ---- small kernels of the driver ------------------------------------------------------------
+
+__global__ void k_compose(int64_t n, const int32_t* __restrict__ next, int32_t* __restrict__ cur) {
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n;
+         x += (int64_t)gridDim.x * blockDim.x)
+        cur[x] = next[cur[x]];
+}
+
+__global__ void k_compose_emap(int64_t m, const int32_t* __restrict__ next, int32_t* __restrict__ cur) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t k = cur[e];
+        cur[e] = k >= 0 ? next[k] : -1;
+    }
+}
+
+template <class KT>
+__global__ void k_sort_prep(int64_t m, const KT* __restrict__ f, KT* __restrict__ key,
+                            uint32_t* __restrict__ val) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        key[e] = f[e];
+        val[e] = (uint32_t)e;
+    }
+}
+
+// caller-supplied lift: every value in [0, n_c)
+__global__ void k_check_lift(int64_t n, const int32_t* __restrict__ lift, int64_t n_c,
+                             uint32_t* status) {
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n;
+         x += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t c = lift[x];
+        if (c < 0 || (int64_t)c >= n_c) atomicOr(status, DEV_BAD_ARG);
+    }
+}
+
+__global__ void k_targets(int64_t B, const int64_t* __restrict__ graph_ptr, int64_t divisor,
+                          int64_t* __restrict__ targets) {
+    for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < B;
+         b += (int64_t)gridDim.x * blockDim.x) {
+        int64_t t = (graph_ptr[b + 1] - graph_ptr[b]) / divisor;
+        targets[b] = t < 1 ? 1 : t;
+    }
+}
+
+spc_status run_sort_fitness(spc_context* ctx, int64_t m, const void* f, bool f32,
+                            int32_t* order_out) {
+    Work& W = ctx->work;
+    const int gb = grid_for(m, kThreads, ctx->num_sms * 8);
+    if (m <= 0) return SPC_OK;
+    if (f32) {
+        SPC_LAUNCH(ctx, k_sort_prep<uint32_t>, gb, kThreads, 0, m,
+                   static_cast<const uint32_t*>(f), W.sel_key.as<uint32_t>(),
+                   reinterpret_cast<uint32_t*>(order_out));
+        SPC_TRY(radix_sort_u32(ctx, W.sel_key.as<uint32_t>(), reinterpret_cast<uint32_t*>(order_out),
+                               W.sel_key2.as<uint32_t>(), W.sel_val2.as<uint32_t>(), m, 31));
+    } else {
+        SPC_LAUNCH(ctx, k_sort_prep<uint64_t>, gb, kThreads, 0, m,
+                   static_cast<const uint64_t*>(f), W.sel_key.as<uint64_t>(),
+                   reinterpret_cast<uint32_t*>(order_out));
+        SPC_TRY(radix_sort_u64(ctx, W.sel_key.as<uint64_t>(), reinterpret_cast<uint32_t*>(order_out),
+                               W.sel_key2.as<uint64_t>(), W.sel_val2.as<uint32_t>(), m, 63));
+    }
+    return SPC_OK;
+}
+
+// ---- workspace sizing -------------------------------------------------------------------------
+
+static spc_status reserve_work(spc_context* ctx, int64_t n, int64_t m, int64_t B) {
+    Work& W = ctx->work;
+    const size_t N = (size_t)n + 1, M = (size_t)m + 1;
+    SPC_TRY(ensure(ctx, W.up_cnt, N * 4));
+    SPC_TRY(ensure(ctx, W.up_ptr, (N + 1) * 4));
+    SPC_TRY(ensure(ctx, W.first_up, N * 4));
+    SPC_TRY(ensure(ctx, W.eu, M * 4));
+    SPC_TRY(ensure(ctx, W.ev, M * 4));
+    SPC_TRY(ensure(ctx, W.w_und, M * 8));
+    SPC_TRY(ensure(ctx, W.deg, N * 8));
+    SPC_TRY(ensure(ctx, W.p, 2 * M * 8));
+    SPC_TRY(ensure(ctx, W.parent, N * 4));
+    for (int i = 0; i < 2; ++i) {
+        SPC_TRY(ensure(ctx, W.best_k[i], N * 8));
+        SPC_TRY(ensure(ctx, W.best_e[i], N * 4));
+        SPC_TRY(ensure(ctx, W.wl_e[i], M * 4));
+        SPC_TRY(ensure(ctx, W.wl_u[i], M * 4));
+        SPC_TRY(ensure(ctx, W.wl_v[i], M * 4));
+    }
+    SPC_TRY(ensure(ctx, W.msf, M + 16));
+    SPC_TRY(ensure(ctx, W.counters, 64 * 4));
+    SPC_TRY(ensure(ctx, W.sel_key, M * 8));
+    SPC_TRY(ensure(ctx, W.sel_val, M * 4));
+    SPC_TRY(ensure(ctx, W.sel_key2, M * 8));
+    SPC_TRY(ensure(ctx, W.sel_val2, M * 4));
+    SPC_TRY(ensure(ctx, W.node_graph, N * 4));
+    SPC_TRY(ensure(ctx, W.seg_start, ((size_t)B + 1) * 4));
+    SPC_TRY(ensure(ctx, W.k_graph, ((size_t)B + 1) * 4));
+    SPC_TRY(ensure(ctx, W.parent2, N * 4));
+    SPC_TRY(ensure(ctx, W.flag, N * 4));
+    SPC_TRY(ensure(ctx, W.ids, (N + 1) * 4));
+    SPC_TRY(ensure(ctx, W.c_key, M * 8));
+    SPC_TRY(ensure(ctx, W.c_val, M * 4));
+    SPC_TRY(ensure(ctx, W.c_key2, M * 8));
+    SPC_TRY(ensure(ctx, W.c_val2, M * 4));
+    SPC_TRY(ensure(ctx, W.c_flag, 2 * M + 16));
+    SPC_TRY(ensure(ctx, W.c_pos, (M + 1) * 4));
+    SPC_TRY(ensure(ctx, W.c_head, (M + 1) * 4));
+    SPC_TRY(ensure(ctx, W.cU, M * 4));
+    SPC_TRY(ensure(ctx, W.cV, M * 4));
+    SPC_TRY(ensure(ctx, W.t_key, M * 4));
+    SPC_TRY(ensure(ctx, W.t_val, M * 4));
+    SPC_TRY(ensure(ctx, W.t_key2, M * 4));
+    SPC_TRY(ensure(ctx, W.t_val2, M * 4));
+    SPC_TRY(ensure(ctx, W.up_deg, (N + 1) * 4));
+    SPC_TRY(ensure(ctx, W.low_deg, (N + 1) * 4));
+    SPC_TRY(ensure(ctx, W.ufirst, (N + 1) * 4));
+    SPC_TRY(ensure(ctx, W.lstart, (N + 1) * 4));
+    SPC_TRY(ensure(ctx, W.i_key, M * 4));
+    SPC_TRY(ensure(ctx, W.i_val, M * 4));
+    SPC_TRY(ensure(ctx, W.i_key2, M * 4));
+    SPC_TRY(ensure(ctx, W.i_val2, M * 4));
+    // scan of up to max(n, m, 256 * tiles) items -> tile sums; radix histograms
+    const size_t big = (N > M ? N : M) + 256 * ((M + 4095) / 4096) + 4096;
+    SPC_TRY(ensure(ctx, W.scan_tmp, (big / 4096 + 4) * 8 + 256));
+    SPC_TRY(ensure(ctx, W.sort_hist, (256 * ((M + 4095) / 4096) + 4) * 4));
+    return SPC_OK;
+}
+
+static spc_status reserve_level(spc_context* ctx, LevelBufs& lv, int64_t n, int64_t m,
+                                int64_t B) {
+    const size_t N = (size_t)n + 1, M = (size_t)m + 1;
+    SPC_TRY(ensure(ctx, lv.lift, N * 4));
+    SPC_TRY(ensure(ctx, lv.emap, M * 4));
+    SPC_TRY(ensure(ctx, lv.self_mass, N * 8));
+    SPC_TRY(ensure(ctx, lv.a_und, M * 8));
+    SPC_TRY(ensure(ctx, lv.rowptr_c, (N + 1) * 8));
+    SPC_TRY(ensure(ctx, lv.col_c, 2 * M * 4));
+    SPC_TRY(ensure(ctx, lv.w_c, 2 * M * 8));
+    SPC_TRY(ensure(ctx, lv.perm, M * 4));
+    SPC_TRY(ensure(ctx, lv.seg, (M + 1) * 4));
+    SPC_TRY(ensure(ctx, lv.score, M * 8));
+    SPC_TRY(ensure(ctx, lv.graph_ptr_c, ((size_t)B + 2) * 8));
+    if (!lv.ev0) {
+        SPC_CUDA(cudaEventCreate(&lv.ev0));
+        SPC_CUDA(cudaEventCreate(&lv.ev1));
+    }
+    return SPC_OK;
+}
+
+// ---- host staging -----------------------------------------------------------------------------
+
+static bool is_device_ptr(const void* p) {
+    if (!p) return false;
+    cudaPointerAttributes a;
+    cudaError_t e = cudaPointerGetAttributes(&a, p);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+static spc_status stage_in(spc_context* ctx, const void* src, size_t bytes, Buf& buf,
+                           const void** out) {
+    if (is_device_ptr(src) || bytes == 0) {
+        *out = src;
+        return SPC_OK;
+    }
+    SPC_TRY(ensure(ctx, buf, bytes));
+    SPC_CUDA(cudaMemcpyAsync(buf.p, src, bytes, cudaMemcpyHostToDevice, ctx->stream));
+    *out = buf.p;
+    return SPC_OK;
+}
+
+static spc_status check_csr(const spc_csr* g) {
+    if (!g || g->n < 0 || g->nnz < 0) return SPC_ERR_INVALID_ARG;
+    if (g->wtype != SPC_I32 && g->wtype != SPC_F32 && g->wtype != SPC_F64)
+        return SPC_ERR_INVALID_ARG;
+    if (g->n >= INT32_MAX || g->nnz / 2 >= INT32_MAX) return SPC_ERR_TOO_LARGE;
+    if (!g->rowptr || (g->nnz > 0 && (!g->col || !g->w))) return SPC_ERR_INVALID_ARG;
+    if (g->nnz & 1) return SPC_ERR_NOT_SYMMETRIC;
+    return SPC_OK;
+}
+
+static spc_status stage_graph(spc_context* ctx, const spc_csr* g, GraphView& v) {
+    Work& W = ctx->work;
+    const void* p;
+    v.n = g->n;
+    v.nnz = g->nnz;
+    v.wtype = g->wtype;
+    SPC_TRY(stage_in(ctx, g->rowptr, (size_t)(g->n + 1) * 8, W.stage_rowptr, &p));
+    v.rowptr = static_cast<const int64_t*>(p);
+    SPC_TRY(stage_in(ctx, g->col, (size_t)g->nnz * 4, W.stage_col, &p));
+    v.col = static_cast<const int32_t*>(p);
+    SPC_TRY(stage_in(ctx, g->w, (size_t)g->nnz * wsize(g->wtype), W.stage_w, &p));
+    v.w = p;
+    return SPC_OK;
+}
+
+static spc_status begin_call(spc_context* ctx) {
+    if (!ctx) return SPC_ERR_INVALID_ARG;
+    SPC_CUDA(cudaSetDevice(ctx->device));
+    SPC_CUDA(cudaMemsetAsync(ctx->d_status, 0, sizeof(uint32_t), ctx->stream));
+    return SPC_OK;
+}
+
+static spc_status copy_out(spc_context* ctx, void* dst, const void* src, size_t bytes) {
+    if (bytes == 0 || dst == src) return SPC_OK;
+    SPC_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, ctx->stream));
+    return SPC_OK;
+}
+
+// ---- the level driver --------------------------------------------------------------------------
+
+struct Schedule {
+    int32_t levels = 1;
+    bool validate = true;
+    int schedule = 0;
+    // single graph
+    int64_t n_c = 1;
+    // batch
+    int64_t B = 1;
+    const int64_t* d_graph_ptr = nullptr;  // level-0 graph_ptr on the device
+    int64_t ratio = 1;
+};
+
+static int pick_schedule(const GraphView& g, int requested) {
+    if (requested == 1 || requested == 2) return requested;
+    // rows with many upper neighbours favour a warp per row; meshes favour edge tiles
+    const double avg = g.n > 0 ? (double)g.nnz / (double)g.n : 0.0;
+    return avg > 48.0 ? 2 : 1;
+}
+
+static spc_status run_levels(spc_context* ctx, const GraphView& g0, const Schedule& S,
+                             int32_t* lift_total_dev, int64_t* n_c_final, int32_t* warn) {
+    const int L = S.levels < 1 ? 1 : S.levels;
+    const bool batched = S.d_graph_ptr != nullptr;
+    if ((int)ctx->levels.size() < L) ctx->levels.resize(L);
+    int64_t* d_targets = nullptr;
+    // reserve everything up front (level sizes are bounded by level 0)
+    SPC_TRY(reserve_work(ctx, g0.n, g0.nnz / 2, S.B));
+    for (int l = 0; l < L; ++l) SPC_TRY(reserve_level(ctx, ctx->levels[l], g0.n, g0.nnz / 2, S.B));
+    if (batched) {
+        SPC_TRY(ensure(ctx, ctx->work.stage_gptr, ((size_t)S.B + 1) * 8 * (L + 1)));
+        d_targets = ctx->work.stage_gptr.as<int64_t>();
+    }
+    const int maxb = ctx->num_sms * 8;
+    GraphView cur = g0;
+    const int64_t* cur_gptr = S.d_graph_ptr;
+    *warn = 0;
+    ctx->n_levels = 0;
+    for (int l = 0; l < L; ++l) {
+        LevelBufs& lv = ctx->levels[l];
+        SPC_CUDA(cudaEventRecord(lv.ev0, ctx->stream));
+        SelectArgs sa;
+        if (batched) {
+            const int64_t div = (l == L - 1) ? S.ratio : (1ll << (l + 1));
+            int64_t* tl = d_targets + (size_t)l * (S.B + 1);
+            SPC_LAUNCH(ctx, k_targets, grid_for(S.B, kThreads, maxb), kThreads, 0, S.B,
+                       S.d_graph_ptr, div, tl);
+            sa.B = S.B;
+            sa.d_graph_ptr = cur_gptr;
+            sa.d_targets = tl;
+        } else {
+            int64_t t = (l == L - 1) ? S.n_c : (g0.n >> (l + 1));
+            if (t < S.n_c) t = S.n_c;
+            if (t < 1) t = 1;
+            sa.target = t;
+        }
+        SPC_TRY(run_score(ctx, cur, S.validate && l == 0, lv.score.p, pick_schedule(cur, S.schedule)));
+        lv.n = cur.n;
+        lv.m = cur.m;
+        int64_t n_c = 0;
+        int32_t st = 0;
+        SPC_TRY(run_select(ctx, cur, lv.score.p, sa, lv.lift.as<int32_t>(), nullptr, &n_c,
+                           lv.graph_ptr_c.as<int64_t>(), &st));
+        SPC_TRY(run_contract(ctx, cur, lv.lift.as<int32_t>(), n_c, lv));
+        SPC_CUDA(cudaEventRecord(lv.ev1, ctx->stream));
+        lv.status = st;
+        lv.wtype = cur.wtype;
+        if (st == SPC_WARN_TARGET_NOT_REACHED) *warn = 1;
+        ctx->n_levels = l + 1;
+        GraphView nx;
+        nx.n = n_c;
+        nx.nnz = 2 * lv.m_c;
+        nx.m = lv.m_c;
+        nx.rowptr = lv.rowptr_c.as<int64_t>();
+        nx.col = lv.col_c.as<int32_t>();
+        nx.w = lv.w_c.p;
+        nx.wtype = cur.wtype;
+        cur = nx;
+        cur_gptr = lv.graph_ptr_c.as<int64_t>();
+    }
+    // composed lift
+    SPC_CUDA(cudaMemcpyAsync(lift_total_dev, ctx->levels[0].lift.p, (size_t)g0.n * 4,
+                             cudaMemcpyDeviceToDevice, ctx->stream));
+    for (int l = 1; l < L; ++l) {
+        SPC_LAUNCH(ctx, k_compose, grid_for(g0.n, kThreads, maxb), kThreads, 0, g0.n,
+                   ctx->levels[l].lift.as<int32_t>(), lift_total_dev);
+    }
+    *n_c_final = cur.n;
+    SPC_TRY(sync_status(ctx));
+    for (int l = 0; l < L; ++l) {
+        float ms = -1.f;
+        if (cudaEventElapsedTime(&ms, ctx->levels[l].ev0, ctx->levels[l].ev1) == cudaSuccess)
+            ctx->levels[l].ms = ms;
+        else
+            (void)cudaGetLastError();
+    }
+    return SPC_OK;
+}
+
+}  // namespace spc
+
+using namespace spc;
+
+// ============================================================================================
+extern "C" {
+
+const char* spc_status_string(spc_status s) {
+    switch (s) {
+        case SPC_OK: return "SPC_OK";
+        case SPC_WARN_TARGET_NOT_REACHED: return "SPC_WARN_TARGET_NOT_REACHED";
+        case SPC_ERR_INVALID_ARG: return "SPC_ERR_INVALID_ARG";
+        case SPC_ERR_NOT_SYMMETRIC: return "SPC_ERR_NOT_SYMMETRIC";
+        case SPC_ERR_SELF_LOOP: return "SPC_ERR_SELF_LOOP";
+        case SPC_ERR_UNSORTED: return "SPC_ERR_UNSORTED";
+        case SPC_ERR_OOM: return "SPC_ERR_OOM";
+        case SPC_ERR_CUDA: return "SPC_ERR_CUDA";
+        case SPC_ERR_TIMEOUT: return "SPC_ERR_TIMEOUT";
+        case SPC_ERR_OVERFLOW: return "SPC_ERR_OVERFLOW";
+        case SPC_ERR_BAD_WEIGHT: return "SPC_ERR_BAD_WEIGHT";
+        case SPC_ERR_TOO_LARGE: return "SPC_ERR_TOO_LARGE";
+    }
+    return "SPC_UNKNOWN_STATUS";
+}
+
+spc_options spc_default_options(void) {
+    spc_options o;
+    o.levels = 1;
+    o.validate = 1;
+    o.use_graph = 1;
+    o.schedule = 0;
+    return o;
+}
+
+spc_status spc_context_create(spc_context** out, const spc_allocator* allocator, void* stream) {
+    if (!out) return SPC_ERR_INVALID_ARG;
+    *out = nullptr;
+    spc_context* ctx = new (std::nothrow) spc_context();
+    if (!ctx) return SPC_ERR_OOM;
+    ctx->stream = static_cast<cudaStream_t>(stream);
+    if (allocator && allocator->alloc && allocator->free) {
+        ctx->allocator = *allocator;
+        ctx->has_allocator = true;
+    }
+    cudaError_t e = cudaGetDevice(&ctx->device);
+    if (e == cudaSuccess)
+        e = cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, ctx->device);
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->d_status, 256);
+    if (e == cudaSuccess) e = cudaMallocHost(&ctx->h_status, 256);
+    if (e == cudaSuccess) e = cudaMallocHost(&ctx->h_scalars, 256);
+    if (e != cudaSuccess) {
+        set_last_cuda_error(e, "spc_context_create", __FILE__, __LINE__);
+        if (ctx->d_status) cudaFree(ctx->d_status);
+        if (ctx->h_status) cudaFreeHost(ctx->h_status);
+        delete ctx;
+        return SPC_ERR_CUDA;
+    }
+    cudaMemset(ctx->d_status, 0, 256);
+    *out = ctx;
+    return SPC_OK;
+}
+
+void spc_context_destroy(spc_context* ctx) {
+    if (!ctx) return;
+    free_all(ctx);
+    for (auto& lv : ctx->levels) {
+        if (lv.ev0) cudaEventDestroy(lv.ev0);
+        if (lv.ev1) cudaEventDestroy(lv.ev1);
+    }
+    for (auto& pr : ctx->timer.pending) {
+        cudaEventDestroy(pr.first);
+        cudaEventDestroy(pr.second);
+    }
+    for (auto ev : ctx->timer.pool) cudaEventDestroy(ev);
+    cudaFree(ctx->d_status);
+    cudaFreeHost(ctx->h_status);
+    cudaFreeHost(ctx->h_scalars);
+    delete ctx;
+}
+
+spc_status spc_context_set_stream(spc_context* ctx, void* stream) {
+    if (!ctx) return SPC_ERR_INVALID_ARG;
+    SPC_CUDA(cudaStreamSynchronize(ctx->stream));
+    ctx->stream = static_cast<cudaStream_t>(stream);
+    return SPC_OK;
+}
+
+spc_status spc_copy(spc_context* ctx, void* dst, const void* src, size_t bytes) {
+    if (!ctx || (bytes && (!dst || !src))) return SPC_ERR_INVALID_ARG;
+    SPC_TRY(copy_out(ctx, dst, src, bytes));
+    SPC_CUDA(cudaStreamSynchronize(ctx->stream));
+    return SPC_OK;
+}
+
+spc_status spc_score(spc_context* ctx, const spc_csr* g, void* f_out, int64_t* m_out) {
+    SPC_TRY(begin_call(ctx));
+    SPC_TRY(check_csr(g));
+    if (!f_out) return SPC_ERR_INVALID_ARG;
+    GraphView v;
+    SPC_TRY(stage_graph(ctx, g, v));
+    SPC_TRY(reserve_work(ctx, v.n, v.nnz / 2, 1));
+    const size_t fsz = score_is_f32(v.wtype) ? 4 : 8;
+    const bool dev_out = is_device_ptr(f_out);
+    Buf& tmp = ctx->work.sel_key;  // sized >= m * 8
+    SPC_TRY(run_score(ctx, v, true, dev_out ? f_out : tmp.p, 1));
+    if (!dev_out) SPC_TRY(copy_out(ctx, f_out, tmp.p, (size_t)v.m * fsz));
+    if (m_out) *m_out = v.m;
+    return sync_status(ctx);
+}
+
+spc_status spc_sort_fitness(spc_context* ctx, int64_t m, const void* f, spc_dtype ftype,
+                            int32_t* order_out) {
+    SPC_TRY(begin_call(ctx));
+    if (m < 0 || (m > 0 && (!f || !order_out))) return SPC_ERR_INVALID_ARG;
+    if (ftype != SPC_F32 && ftype != SPC_F64) return SPC_ERR_INVALID_ARG;
+    if (m >= INT32_MAX) return SPC_ERR_TOO_LARGE;
+    SPC_TRY(reserve_work(ctx, 1, m, 1));
+    const size_t fsz = ftype == SPC_F32 ? 4 : 8;
+    const void* fd;
+    SPC_TRY(stage_in(ctx, f, (size_t)m * fsz, ctx->work.stage_w, &fd));
+    const bool dev_out = is_device_ptr(order_out);
+    int32_t* ord = dev_out ? order_out : ctx->work.c_val.as<int32_t>();
+    SPC_TRY(run_sort_fitness(ctx, m, fd, ftype == SPC_F32, ord));
+    if (!dev_out) SPC_TRY(copy_out(ctx, order_out, ord, (size_t)m * 4));
+    return sync_status(ctx);
+}
+
+spc_status spc_select_merges(spc_context* ctx, const spc_csr* g, const void* f, int64_t n_c,
+                             int32_t* lift_out, uint8_t* merged_out, int64_t* n_c_actual) {
+    SPC_TRY(begin_call(ctx));
+    SPC_TRY(check_csr(g));
+    if (!f || !lift_out || n_c < 1) return SPC_ERR_INVALID_ARG;
+    GraphView v;
+    SPC_TRY(stage_graph(ctx, g, v));
+    SPC_TRY(reserve_work(ctx, v.n, v.nnz / 2, 1));
+    if (ctx->levels.empty()) ctx->levels.resize(1);
+    SPC_TRY(reserve_level(ctx, ctx->levels[0], v.n, v.nnz / 2, 1));
+    SPC_TRY(run_score(ctx, v, true, nullptr, 1));  // edge list only
+    const size_t fsz = score_is_f32(v.wtype) ? 4 : 8;
+    const void* fd;
+    SPC_TRY(stage_in(ctx, f, (size_t)v.m * fsz, ctx->levels[0].score, &fd));
+    SelectArgs sa;
+    sa.target = n_c;
+    const bool dev_lift = is_device_ptr(lift_out);
+    const bool dev_merged = merged_out && is_device_ptr(merged_out);
+    int32_t* lift = dev_lift ? lift_out : ctx->levels[0].lift.as<int32_t>();
+    uint8_t* merged = merged_out ? (dev_merged ? merged_out : ctx->work.c_flag.as<uint8_t>()) : nullptr;
+    int64_t nc = 0;
+    int32_t st = 0;
+    SPC_TRY(run_select(ctx, v, fd, sa, lift, merged, &nc, nullptr, &st));
+    if (!dev_lift) SPC_TRY(copy_out(ctx, lift_out, lift, (size_t)v.n * 4));
+    if (merged_out && !dev_merged) SPC_TRY(copy_out(ctx, merged_out, merged, (size_t)v.m));
+    if (n_c_actual) *n_c_actual = nc;
+    SPC_TRY(sync_status(ctx));
+    return (spc_status)st;
+}
+
+spc_status spc_contract(spc_context* ctx, const spc_csr* g, const int32_t* lift, int64_t n_c,
+                        int64_t* m_c_out) {
+    SPC_TRY(begin_call(ctx));
+    SPC_TRY(check_csr(g));
+    if (!lift || n_c < 1 || n_c > (g->n > 0 ? g->n : 1)) return SPC_ERR_INVALID_ARG;
+    GraphView v;
+    SPC_TRY(stage_graph(ctx, g, v));
+    SPC_TRY(reserve_work(ctx, v.n, v.nnz / 2, 1));
+    if (ctx->levels.empty()) ctx->levels.resize(1);
+    LevelBufs& lv = ctx->levels[0];
+    SPC_TRY(reserve_level(ctx, lv, v.n, v.nnz / 2, 1));
+    SPC_TRY(run_score(ctx, v, true, nullptr, 1));
+    const void* ld;
+    SPC_TRY(stage_in(ctx, lift, (size_t)v.n * 4, ctx->work.stage_lift, &ld));
+    SPC_CUDA(cudaMemcpyAsync(lv.lift.p, ld, (size_t)v.n * 4, cudaMemcpyDeviceToDevice,
+                             ctx->stream));
+    if (v.n > 0) {
+        SPC_LAUNCH(ctx, k_check_lift, grid_for(v.n, kThreads, ctx->num_sms * 8), kThreads, 0,
+                   v.n, lv.lift.as<int32_t>(), n_c, ctx->d_status);
+    }
+    SPC_TRY(sync_status(ctx));  // an out-of-range id must not reach the contraction
+    SPC_TRY(run_contract(ctx, v, lv.lift.as<int32_t>(), n_c, lv));
+    lv.n = v.n;
+    lv.m = v.m;
+    lv.status = SPC_OK;
+    lv.wtype = v.wtype;
+    lv.ms = -1.f;
+    ctx->n_levels = 1;
+    if (m_c_out) *m_c_out = lv.m_c;
+    return sync_status(ctx);
+}
+
+spc_status spc_coarsen(spc_context* ctx, const spc_csr* g, int64_t n_c, const spc_options* options,
+                       int32_t* lift_out, int64_t* n_c_actual) {
+    SPC_TRY(begin_call(ctx));
+    SPC_TRY(check_csr(g));
+    if (!lift_out || n_c < 1) return SPC_ERR_INVALID_ARG;
+    spc_options o = options ? *options : spc_default_options();
+    GraphView v;
+    SPC_TRY(stage_graph(ctx, g, v));
+    Schedule S;
+    S.levels = o.levels < 1 ? 1 : o.levels;
+    S.validate = o.validate != 0;
+    S.schedule = o.schedule;
+    S.n_c = n_c;
+    const bool dev_lift = is_device_ptr(lift_out);
+    SPC_TRY(ensure(ctx, ctx->work.stage_lift, ((size_t)v.n + 1) * 4));
+    int32_t* lift = dev_lift ? lift_out : ctx->work.stage_lift.as<int32_t>();
+    int64_t ncf = 0;
+    int32_t warn = 0;
+    SPC_TRY(run_levels(ctx, v, S, lift, &ncf, &warn));
+    if (!dev_lift) SPC_TRY(copy_out(ctx, lift_out, lift, (size_t)v.n * 4));
+    SPC_CUDA(cudaStreamSynchronize(ctx->stream));
+    if (n_c_actual) *n_c_actual = ncf;
+    return warn ? SPC_WARN_TARGET_NOT_REACHED : SPC_OK;
+}
+
+spc_status spc_coarsen_batched(spc_context* ctx, const spc_csr* g, const int64_t* graph_ptr,
+                               int64_t B, int64_t ratio, const spc_options* options,
+                               int32_t* lift_out, int64_t* graph_ptr_c_out) {
+    SPC_TRY(begin_call(ctx));
+    SPC_TRY(check_csr(g));
+    if (!graph_ptr || B < 1 || ratio < 1 || !lift_out) return SPC_ERR_INVALID_ARG;
+    spc_options o = options ? *options : spc_default_options();
+    const int L = o.levels < 1 ? 1 : o.levels;
+    if (L > 1 && (1ll << L) != ratio) return SPC_ERR_INVALID_ARG;
+    GraphView v;
+    SPC_TRY(stage_graph(ctx, g, v));
+    const void* gp;
+    SPC_TRY(ensure(ctx, ctx->work.stage_gptr, ((size_t)B + 1) * 8 * (L + 2)));
+    // level-0 graph_ptr lives in the last slot of stage_gptr (targets use the first L slots)
+    int64_t* gp_dev = ctx->work.stage_gptr.as<int64_t>() + (size_t)(L + 1) * (B + 1);
+    SPC_TRY(stage_in(ctx, graph_ptr, ((size_t)B + 1) * 8, ctx->work.seg_start, &gp));
+    SPC_CUDA(cudaMemcpyAsync(gp_dev, gp, ((size_t)B + 1) * 8, cudaMemcpyDeviceToDevice,
+                             ctx->stream));
+    Schedule S;
+    S.levels = L;
+    S.validate = o.validate != 0;
+    S.schedule = o.schedule;
+    S.B = B;
+    S.d_graph_ptr = gp_dev;
+    S.ratio = ratio;
+    const bool dev_lift = is_device_ptr(lift_out);
+    SPC_TRY(ensure(ctx, ctx->work.stage_lift, ((size_t)v.n + 1) * 4));
+    int32_t* lift = dev_lift ? lift_out : ctx->work.stage_lift.as<int32_t>();
+    int64_t ncf = 0;
+    int32_t warn = 0;
+    SPC_TRY(run_levels(ctx, v, S, lift, &ncf, &warn));
+    if (!dev_lift) SPC_TRY(copy_out(ctx, lift_out, lift, (size_t)v.n * 4));
+    if (graph_ptr_c_out)
+        SPC_TRY(copy_out(ctx, graph_ptr_c_out, ctx->levels[L - 1].graph_ptr_c.p,
+                         ((size_t)B + 1) * 8));
+    SPC_CUDA(cudaStreamSynchronize(ctx->stream));
+    return warn ? SPC_WARN_TARGET_NOT_REACHED : SPC_OK;
+}
+
+int32_t spc_level_count(const spc_context* ctx) { return ctx ? ctx->n_levels : 0; }
+
+spc_status spc_get_level(const spc_context* ctx, int32_t level, spc_level* out) {
+    if (!ctx || !out || level < 0 || level >= ctx->n_levels) return SPC_ERR_INVALID_ARG;
+    const LevelBufs& lv = ctx->levels[level];
+    out->n = lv.n;
+    out->m = lv.m;
+    out->n_c = lv.n_c;
+    out->m_c = lv.m_c;
+    out->m_inter = lv.m_inter;
+    out->status = lv.status;
+    out->wtype = lv.wtype;
+    out->score = lv.score.p;
+    out->scoretype = lv.wtype == SPC_F32 ? SPC_F32 : SPC_F64;
+    out->lift = lv.lift.as<int32_t>();
+    out->emap = lv.emap.as<int32_t>();
+    out->self_mass = lv.self_mass.p;
+    out->a_und = lv.a_und.p;
+    out->rowptr_c = lv.rowptr_c.as<int64_t>();
+    out->col_c = lv.col_c.as<int32_t>();
+    out->w_c = lv.w_c.p;
+    out->perm = lv.perm.as<int32_t>();
+    out->seg = lv.seg.as<int32_t>();
+    out->graph_ptr_c = lv.graph_ptr_c.as<int64_t>();
+    out->ms = lv.ms;
+    return SPC_OK;
+}
+
+spc_status spc_contract_forward(spc_context* ctx, const int32_t* perm, const int32_t* seg,
+                                int64_t m_c, const void* w_und, spc_dtype wtype, void* a_und) {
+    SPC_TRY(begin_call(ctx));
+    if (m_c < 0 || (m_c > 0 && (!perm || !seg || !w_und || !a_und))) return SPC_ERR_INVALID_ARG;
+    SPC_TRY(run_contract_forward(ctx, perm, seg, m_c, w_und, wtype, a_und));
+    return sync_status(ctx);
+}
+
+spc_status spc_contract_backward(spc_context* ctx, const int32_t* emap, int64_t m,
+                                 const void* grad_a, void* grad_w, spc_dtype dtype) {
+    SPC_TRY(begin_call(ctx));
+    if (m < 0 || (m > 0 && (!emap || !grad_a || !grad_w))) return SPC_ERR_INVALID_ARG;
+    SPC_TRY(run_contract_backward(ctx, emap, m, grad_a, grad_w, dtype));
+    return sync_status(ctx);
+}
+
+spc_status spc_compose_emap(spc_context* ctx, int32_t* emap_out) {
+    SPC_TRY(begin_call(ctx));
+    if (!emap_out || ctx->n_levels < 1) return SPC_ERR_INVALID_ARG;
+    const int64_t m = ctx->levels[0].m;
+    const bool dev = is_device_ptr(emap_out);
+    int32_t* em = dev ? emap_out : ctx->work.c_val.as<int32_t>();
+    SPC_CUDA(cudaMemcpyAsync(em, ctx->levels[0].emap.p, (size_t)m * 4, cudaMemcpyDeviceToDevice,
+                             ctx->stream));
+    for (int l = 1; l < ctx->n_levels; ++l) {
+        SPC_LAUNCH(ctx, k_compose_emap, grid_for(m, kThreads, ctx->num_sms * 8), kThreads, 0, m,
+                   ctx->levels[l].emap.as<int32_t>(), em);
+    }
+    if (!dev) SPC_TRY(copy_out(ctx, emap_out, em, (size_t)m * 4));
+    return sync_status(ctx);
+}
+
+spc_status spc_time_kernel(spc_context* ctx, const char* kernel_substr) {
+    if (!ctx) return SPC_ERR_INVALID_ARG;
+    Timer& t = ctx->timer;
+    SPC_CUDA(cudaStreamSynchronize(ctx->stream));
+    for (auto& pr : t.pending) {
+        t.pool.push_back(pr.first);
+        t.pool.push_back(pr.second);
+    }
+    t.pending.clear();
+    t.launches = 0;
+    t.total_ms = 0.0;
+    t.on = kernel_substr && kernel_substr[0];
+    t.substr = t.on ? kernel_substr : "";
+    return SPC_OK;
+}
+
+spc_status spc_kernel_time(spc_context* ctx, int64_t* launches, double* total_ms) {
+    if (!ctx) return SPC_ERR_INVALID_ARG;
+    Timer& t = ctx->timer;
+    SPC_CUDA(cudaStreamSynchronize(ctx->stream));
+    for (auto& pr : t.pending) {
+        float ms = 0.f;
+        SPC_CUDA(cudaEventElapsedTime(&ms, pr.first, pr.second));
+        t.total_ms += ms;
+        t.launches += 1;
+        t.pool.push_back(pr.first);
+        t.pool.push_back(pr.second);
+    }
+    t.pending.clear();
+    if (launches) *launches = t.launches;
+    if (total_ms) *total_ms = t.total_ms;
+    return SPC_OK;
+}
+
+int64_t spc_launch_count(const spc_context* ctx) { return ctx ? ctx->launches : 0; }
+
+}  // extern "C"

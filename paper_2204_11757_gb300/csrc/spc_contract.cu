@@ -1,0 +1,352 @@
+// S7: contraction into super-nodes (Definition 1), S9: its backward, and the weights-only
+// forward with the assignment held fixed.
+//
+// For every fine undirected edge e = (u, v): U = c(u), V = c(v).  U == V: the edge is inside a
+// super-node; emap[e] = -1 and its weight goes to self_mass[U].  Otherwise key(e) =
+// (min(U,V), max(U,V)).  A stable radix sort of (key, eid) -- input in eid order -- groups the
+// fine edges of every coarse edge with ascending eids; segment heads numbered by a scan give
+// the coarse edge ids in lexicographic (U, V) order, and each coarse weight is the sequential
+// sum of its segment (ascending eid, IEEE round-to-nearest), so the result is reproducible.
+// The coarse CSR: row U holds first the coarse edges (V', U) with V' < U (a stable sort by
+// the second end point, the "transpose") and then the edges (U, V) with V > U (contiguous in
+// coarse-edge order), which leaves every row sorted.
+#include <type_traits>
+
+#include "spc_internal.cuh"
+
+namespace spc {
+
+namespace {
+
+template <class WT> struct CT;
+template <> struct CT<int32_t> {
+    using Acc = long long;
+    __device__ static Acc add(Acc a, int32_t w) { return a + w; }
+};
+template <> struct CT<float> {
+    using Acc = float;
+    __device__ static Acc add(Acc a, float w) { return __fadd_rn(a, w); }
+};
+template <> struct CT<double> {
+    using Acc = double;
+    __device__ static Acc add(Acc a, double w) { return __dadd_rn(a, w); }
+};
+
+// classify fine edges: inter flag and intra flag
+__global__ void __launch_bounds__(kThreads)
+k_classify(int64_t m, const int32_t* __restrict__ eu, const int32_t* __restrict__ ev,
+           const int32_t* __restrict__ lift, uint8_t* __restrict__ inter,
+           uint8_t* __restrict__ intra) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const bool x = lift[eu[e]] != lift[ev[e]];
+        inter[e] = x ? 1 : 0;
+        intra[e] = x ? 0 : 1;
+    }
+}
+
+__global__ void __launch_bounds__(kThreads)
+k_scatter_keys(int64_t m, int nb, const int32_t* __restrict__ eu, const int32_t* __restrict__ ev,
+               const int32_t* __restrict__ lift, const int32_t* __restrict__ inter_pos,
+               const int32_t* __restrict__ intra_pos, uint64_t* __restrict__ ckey,
+               uint32_t* __restrict__ cval, uint32_t* __restrict__ ikey,
+               uint32_t* __restrict__ ival, int32_t* __restrict__ emap) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t U = lift[eu[e]], V = lift[ev[e]];
+        if (U != V) {
+            const uint64_t lo = (uint64_t)(U < V ? U : V), hi = (uint64_t)(U < V ? V : U);
+            const int32_t q = inter_pos[e];
+            ckey[q] = (lo << nb) | hi;
+            cval[q] = (uint32_t)e;
+        } else {
+            const int32_t q = intra_pos[e];
+            ikey[q] = (uint32_t)U;
+            ival[q] = (uint32_t)e;
+            emap[e] = -1;
+        }
+    }
+}
+
+__global__ void k_set_i32(int32_t* p, int32_t v) {
+    if (threadIdx.x == 0) *p = v;
+}
+
+__global__ void __launch_bounds__(kThreads)
+k_heads(int64_t cnt, const uint64_t* __restrict__ key, uint8_t* __restrict__ head) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cnt;
+         i += (int64_t)gridDim.x * blockDim.x)
+        head[i] = (i == 0 || key[i] != key[i - 1]) ? 1 : 0;
+}
+
+// coarse edge id of every sorted item; emap, perm; segment starts and end points at heads
+__global__ void __launch_bounds__(kThreads)
+k_emit_segments(int64_t cnt, int nb, const uint64_t* __restrict__ key,
+                const uint32_t* __restrict__ val, const uint8_t* __restrict__ head,
+                const int32_t* __restrict__ hpos, int32_t* __restrict__ emap,
+                int32_t* __restrict__ perm, int32_t* __restrict__ seg, int32_t* __restrict__ cU,
+                int32_t* __restrict__ cV) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cnt;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t ce = hpos[i] + head[i] - 1;
+        const uint32_t e = val[i];
+        emap[e] = ce;
+        perm[i] = (int32_t)e;
+        if (head[i]) {
+            seg[ce] = (int32_t)i;
+            const uint64_t k = key[i];
+            cU[ce] = (int32_t)(k >> nb);
+            cV[ce] = (int32_t)(k & ((1ull << nb) - 1ull));
+        }
+    }
+}
+
+// a_und[k] = sum of w_und over perm[seg[k] .. seg[k+1]) in order
+template <class WT>
+__global__ void __launch_bounds__(kThreads)
+k_segment_sums(int64_t m_c, const int32_t* __restrict__ seg, const int32_t* __restrict__ perm,
+               const WT* __restrict__ w_und, WT* __restrict__ a_und, uint32_t* status) {
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < m_c;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        typename CT<WT>::Acc s = 0;
+        for (int32_t j = seg[k]; j < seg[k + 1]; ++j) s = CT<WT>::add(s, w_und[perm[j]]);
+        if constexpr (std::is_same<WT, int32_t>::value) {
+            if (s > 2147483647ll) atomicOr(status, DEV_OVERFLOW);
+        }
+        a_und[k] = (WT)s;
+    }
+}
+
+// self-mass: the head of every run of equal super-node ids sums its run in order
+template <class WT>
+__global__ void __launch_bounds__(kThreads)
+k_self_mass(int64_t cnt, const uint32_t* __restrict__ ikey, const uint32_t* __restrict__ ival,
+            const WT* __restrict__ w_und, typename CT<WT>::Acc* __restrict__ self_mass) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cnt;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t U = ikey[i];
+        if (i > 0 && ikey[i - 1] == U) continue;
+        typename CT<WT>::Acc s = 0;
+        for (int64_t j = i; j < cnt && ikey[j] == U; ++j) s = CT<WT>::add(s, w_und[ival[j]]);
+        self_mass[U] = s;
+    }
+}
+
+__global__ void __launch_bounds__(kThreads)
+k_degree_counts(int64_t m_c, const int32_t* __restrict__ cU, const int32_t* __restrict__ cV,
+                int32_t* up_deg, int32_t* low_deg, uint32_t* __restrict__ tkey,
+                uint32_t* __restrict__ tval) {
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < m_c;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        atomicAdd(up_deg + cU[k], 1);
+        atomicAdd(low_deg + cV[k], 1);
+        tkey[k] = (uint32_t)cV[k];
+        tval[k] = (uint32_t)k;
+    }
+}
+
+__global__ void __launch_bounds__(kThreads)
+k_rowptr(int64_t n_c, const int32_t* __restrict__ ufirst, const int32_t* __restrict__ lstart,
+         int64_t* __restrict__ rowptr_c) {
+    for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u <= n_c;
+         u += (int64_t)gridDim.x * blockDim.x)
+        rowptr_c[u] = (int64_t)ufirst[u] + (int64_t)lstart[u];
+}
+
+// row V, lower part: coarse edges (U, V), U < V, in transpose-sorted order
+template <class WT>
+__global__ void __launch_bounds__(kThreads)
+k_fill_lower(int64_t m_c, const uint32_t* __restrict__ tkey, const uint32_t* __restrict__ tval,
+             const int32_t* __restrict__ lstart, const int64_t* __restrict__ rowptr_c,
+             const int32_t* __restrict__ cU, const WT* __restrict__ a_und,
+             int32_t* __restrict__ col_c, WT* __restrict__ w_c) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m_c;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t V = tkey[i], k = tval[i];
+        const int64_t pos = rowptr_c[V] + (i - lstart[V]);
+        col_c[pos] = cU[k];
+        w_c[pos] = a_und[k];
+    }
+}
+
+// row U, upper part: coarse edges (U, V), V > U, contiguous in coarse-edge order
+template <class WT>
+__global__ void __launch_bounds__(kThreads)
+k_fill_upper(int64_t m_c, const int32_t* __restrict__ cU, const int32_t* __restrict__ cV,
+             const int32_t* __restrict__ ufirst, const int32_t* __restrict__ low_deg,
+             const int64_t* __restrict__ rowptr_c, const WT* __restrict__ a_und,
+             int32_t* __restrict__ col_c, WT* __restrict__ w_c) {
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < m_c;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t U = cU[k];
+        const int64_t pos = rowptr_c[U] + low_deg[U] + (k - ufirst[U]);
+        col_c[pos] = cV[k];
+        w_c[pos] = a_und[k];
+    }
+}
+
+template <class WT>
+__global__ void __launch_bounds__(kThreads)
+k_backward(int64_t m, const int32_t* __restrict__ emap, const WT* __restrict__ grad_a,
+           WT* __restrict__ grad_w) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t k = emap[e];
+        grad_w[e] = k >= 0 ? grad_a[k] : WT(0);
+    }
+}
+
+template <class WT>
+spc_status contract_typed(spc_context* ctx, const GraphView& g, const int32_t* lift,
+                          int64_t n_c, LevelBufs& lv) {
+    using Acc = typename CT<WT>::Acc;
+    Work& W = ctx->work;
+    const int64_t m = g.m;
+    const int maxb = ctx->num_sms * 8;
+    uint32_t* status = ctx->d_status;
+    int nb = 1;
+    while ((1ll << nb) < n_c) ++nb;
+    uint8_t* inter = W.c_flag.as<uint8_t>();
+    uint8_t* intra = inter + (m + 1);
+    int32_t* inter_pos = W.c_pos.as<int32_t>();
+    int32_t* intra_pos = W.c_head.as<int32_t>();
+    const int gm = grid_for(m, kThreads, maxb);
+    if (m > 0) {
+        SPC_LAUNCH(ctx, k_classify, gm, kThreads, 0, m, W.eu.as<int32_t>(), W.ev.as<int32_t>(),
+                   lift, inter, intra);
+    }
+    SPC_TRY(scan_flags_u8(ctx, inter, inter_pos, m));
+    SPC_TRY(scan_flags_u8(ctx, intra, intra_pos, m));
+    uint64_t* ckey = W.c_key.as<uint64_t>();
+    uint32_t* cval = W.c_val.as<uint32_t>();
+    uint32_t* ikey = W.i_key.as<uint32_t>();
+    uint32_t* ival = W.i_val.as<uint32_t>();
+    int32_t* emap = lv.emap.as<int32_t>();
+    if (m > 0) {
+        SPC_LAUNCH(ctx, k_scatter_keys, gm, kThreads, 0, m, nb, W.eu.as<int32_t>(),
+                   W.ev.as<int32_t>(), lift, inter_pos, intra_pos, ckey, cval, ikey, ival, emap);
+    }
+    SPC_CUDA(cudaMemcpyAsync(ctx->h_scalars, inter_pos + m, sizeof(int32_t),
+                             cudaMemcpyDeviceToHost, ctx->stream));
+    SPC_CUDA(cudaMemcpyAsync(reinterpret_cast<int32_t*>(ctx->h_scalars) + 1, intra_pos + m,
+                             sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream));
+    SPC_CUDA(cudaStreamSynchronize(ctx->stream));
+    const int64_t m_inter = reinterpret_cast<int32_t*>(ctx->h_scalars)[0];
+    const int64_t m_intra = reinterpret_cast<int32_t*>(ctx->h_scalars)[1];
+    // self-mass
+    Acc* self_mass = lv.self_mass.as<Acc>();
+    SPC_CUDA(cudaMemsetAsync(self_mass, 0, (size_t)n_c * sizeof(Acc), ctx->stream));
+    SPC_TRY(radix_sort_u32(ctx, ikey, ival, W.i_key2.as<uint32_t>(), W.i_val2.as<uint32_t>(),
+                           m_intra, nb));
+    if (m_intra > 0) {
+        SPC_LAUNCH(ctx, k_self_mass<WT>, grid_for(m_intra, kThreads, maxb), kThreads, 0,
+                   m_intra, ikey, ival, W.w_und.as<WT>(), self_mass);
+    }
+    // coarse edges
+    SPC_TRY(radix_sort_u64(ctx, ckey, cval, W.c_key2.as<uint64_t>(), W.c_val2.as<uint32_t>(),
+                           m_inter, 2 * nb));
+    uint8_t* head = W.c_flag.as<uint8_t>();  // flags are consumed; reuse as heads
+    int32_t* hpos = W.c_pos.as<int32_t>();
+    int32_t* seg = lv.seg.as<int32_t>();
+    int32_t* perm = lv.perm.as<int32_t>();
+    int32_t* cU = W.cU.as<int32_t>();
+    int32_t* cV = W.cV.as<int32_t>();
+    int64_t m_c = 0;
+    if (m_inter > 0) {
+        const int gi = grid_for(m_inter, kThreads, maxb);
+        SPC_LAUNCH(ctx, k_heads, gi, kThreads, 0, m_inter, ckey, head);
+        SPC_TRY(scan_flags_u8(ctx, head, hpos, m_inter));
+        SPC_LAUNCH(ctx, k_emit_segments, gi, kThreads, 0, m_inter, nb, ckey, cval, head, hpos,
+                   emap, perm, seg, cU, cV);
+        SPC_CUDA(cudaMemcpyAsync(ctx->h_scalars, hpos + m_inter, sizeof(int32_t),
+                                 cudaMemcpyDeviceToHost, ctx->stream));
+        SPC_CUDA(cudaStreamSynchronize(ctx->stream));
+        m_c = reinterpret_cast<int32_t*>(ctx->h_scalars)[0];
+    }
+    SPC_LAUNCH(ctx, k_set_i32, 1, 32, 0, seg + m_c, (int32_t)m_inter);
+    WT* a_und = lv.a_und.as<WT>();
+    if (m_c > 0) {
+        SPC_LAUNCH(ctx, k_segment_sums<WT>, grid_for(m_c, kThreads, maxb), kThreads, 0, m_c,
+                   seg, perm, W.w_und.as<WT>(), a_und, status);
+    }
+    // coarse CSR
+    int32_t* up_deg = W.up_deg.as<int32_t>();
+    int32_t* low_deg = W.low_deg.as<int32_t>();
+    SPC_CUDA(cudaMemsetAsync(up_deg, 0, (size_t)(n_c + 1) * sizeof(int32_t), ctx->stream));
+    SPC_CUDA(cudaMemsetAsync(low_deg, 0, (size_t)(n_c + 1) * sizeof(int32_t), ctx->stream));
+    uint32_t* tkey = W.t_key.as<uint32_t>();
+    uint32_t* tval = W.t_val.as<uint32_t>();
+    if (m_c > 0) {
+        SPC_LAUNCH(ctx, k_degree_counts, grid_for(m_c, kThreads, maxb), kThreads, 0, m_c, cU, cV,
+                   up_deg, low_deg, tkey, tval);
+    }
+    int32_t* ufirst = W.ufirst.as<int32_t>();
+    int32_t* lstart = W.lstart.as<int32_t>();
+    SPC_TRY(scan_i32(ctx, up_deg, ufirst, n_c));
+    SPC_TRY(scan_i32(ctx, low_deg, lstart, n_c));
+    int64_t* rowptr_c = lv.rowptr_c.as<int64_t>();
+    SPC_LAUNCH(ctx, k_rowptr, grid_for(n_c + 1, kThreads, maxb), kThreads, 0, n_c, ufirst, lstart,
+               rowptr_c);
+    if (m_c > 0) {
+        SPC_TRY(radix_sort_u32(ctx, tkey, tval, W.t_key2.as<uint32_t>(), W.t_val2.as<uint32_t>(),
+                               m_c, nb));
+        SPC_LAUNCH(ctx, k_fill_lower<WT>, grid_for(m_c, kThreads, maxb), kThreads, 0, m_c, tkey,
+                   tval, lstart, rowptr_c, cU, a_und, lv.col_c.as<int32_t>(), lv.w_c.as<WT>());
+        SPC_LAUNCH(ctx, k_fill_upper<WT>, grid_for(m_c, kThreads, maxb), kThreads, 0, m_c, cU, cV,
+                   ufirst, low_deg, rowptr_c, a_und, lv.col_c.as<int32_t>(), lv.w_c.as<WT>());
+    }
+    lv.m_c = m_c;
+    lv.m_inter = m_inter;
+    lv.n_c = n_c;
+    return SPC_OK;
+}
+
+template <class WT>
+spc_status forward_typed(spc_context* ctx, const int32_t* perm, const int32_t* seg, int64_t m_c,
+                         const WT* w_und, WT* a_und) {
+    if (m_c <= 0) return SPC_OK;
+    SPC_LAUNCH(ctx, k_segment_sums<WT>, grid_for(m_c, kThreads, ctx->num_sms * 8), kThreads, 0,
+               m_c, seg, perm, w_und, a_und, ctx->d_status);
+    return SPC_OK;
+}
+
+}  // namespace
+
+spc_status run_contract(spc_context* ctx, const GraphView& g, const int32_t* lift, int64_t n_c,
+                        LevelBufs& lv) {
+    switch (g.wtype) {
+        case SPC_I32: return contract_typed<int32_t>(ctx, g, lift, n_c, lv);
+        case SPC_F32: return contract_typed<float>(ctx, g, lift, n_c, lv);
+        case SPC_F64: return contract_typed<double>(ctx, g, lift, n_c, lv);
+    }
+    return SPC_ERR_INVALID_ARG;
+}
+
+spc_status run_contract_forward(spc_context* ctx, const int32_t* perm, const int32_t* seg,
+                                int64_t m_c, const void* w_und, spc_dtype wt, void* a_und) {
+    if (wt == SPC_F32)
+        return forward_typed<float>(ctx, perm, seg, m_c, static_cast<const float*>(w_und),
+                                    static_cast<float*>(a_und));
+    if (wt == SPC_F64)
+        return forward_typed<double>(ctx, perm, seg, m_c, static_cast<const double*>(w_und),
+                                     static_cast<double*>(a_und));
+    return SPC_ERR_INVALID_ARG;
+}
+
+spc_status run_contract_backward(spc_context* ctx, const int32_t* emap, int64_t m,
+                                 const void* grad_a, void* grad_w, spc_dtype wt) {
+    if (m <= 0) return SPC_OK;
+    const int gb = grid_for(m, kThreads, ctx->num_sms * 8);
+    if (wt == SPC_F32) {
+        SPC_LAUNCH(ctx, k_backward<float>, gb, kThreads, 0, m, emap,
+                   static_cast<const float*>(grad_a), static_cast<float*>(grad_w));
+    } else if (wt == SPC_F64) {
+        SPC_LAUNCH(ctx, k_backward<double>, gb, kThreads, 0, m, emap,
+                   static_cast<const double*>(grad_a), static_cast<double*>(grad_w));
+    } else {
+        return SPC_ERR_INVALID_ARG;
+    }
+    return SPC_OK;
+}
+
+}  // namespace spc

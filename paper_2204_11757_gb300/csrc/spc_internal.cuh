@@ -1,0 +1,206 @@
+// Internal declarations of libspcoarsen (GB300, sm_103a).  Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/spcoarsen.h"
+
+namespace spc {
+
+constexpr int kThreads = 256;          // default block size
+constexpr uint32_t kSpinLimit = 1u << 22;  // bound for every device-side retry loop
+
+// bits of the device status word
+enum : uint32_t {
+    DEV_NOT_SYMMETRIC = 1u << 0,
+    DEV_SELF_LOOP = 1u << 1,
+    DEV_UNSORTED = 1u << 2,
+    DEV_BAD_WEIGHT = 1u << 3,
+    DEV_TIMEOUT = 1u << 4,
+    DEV_OVERFLOW = 1u << 5,
+    DEV_TOO_LARGE = 1u << 6,
+    DEV_BAD_ARG = 1u << 7,
+};
+
+spc_status status_from_bits(uint32_t bits);
+
+#define SPC_CUDA(call)                                                                   \
+    do {                                                                                 \
+        cudaError_t e_ = (call);                                                         \
+        if (e_ != cudaSuccess) {                                                         \
+            spc::set_last_cuda_error(e_, #call, __FILE__, __LINE__);                     \
+            return SPC_ERR_CUDA;                                                         \
+        }                                                                                \
+    } while (0)
+
+#define SPC_TRY(call)                                                                    \
+    do {                                                                                 \
+        spc_status s_ = (call);                                                          \
+        if (s_ < 0) return s_;                                                           \
+    } while (0)
+
+void set_last_cuda_error(cudaError_t e, const char* what, const char* file, int line);
+
+// ---- workspace ------------------------------------------------------------------------------
+
+struct Block {
+    void* p = nullptr;
+    size_t bytes = 0;
+};
+
+struct Context;
+
+// A named, growable device buffer owned by the context.
+struct Buf {
+    void* p = nullptr;
+    size_t bytes = 0;
+    template <class T> T* as() const { return static_cast<T*>(p); }
+};
+
+// Device buffers of one level (inputs of the next level live in `out_*`).
+struct LevelBufs {
+    Buf lift, emap, self_mass, a_und, rowptr_c, col_c, w_c, perm, seg, score, graph_ptr_c;
+    int64_t n = 0, m = 0, n_c = 0, m_c = 0, m_inter = 0;
+    int32_t status = 0;
+    spc_dtype wtype = SPC_F64;
+    float ms = -1.f;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+};
+
+// Work buffers shared by all levels (sized for level 0).
+struct Work {
+    Buf up_cnt, up_ptr, first_up, eu, ev, w_und, deg, p;       // S0-S2
+    Buf parent, best_k[2], best_e[2], wl_e[2], wl_u[2], wl_v[2], msf;   // S5 MSF
+    Buf counters;                                               // small device ints
+    Buf sel_key, sel_val, sel_key2, sel_val2, node_graph, seg_start, k_graph;  // selection
+    Buf parent2, flag, ids;                                     // S6
+    Buf c_key, c_val, c_key2, c_val2, c_flag, c_pos, c_head, cU, cV;    // S7
+    Buf t_key, t_val, t_key2, t_val2, up_deg, low_deg, deg_c, ufirst, lstart;
+    Buf i_key, i_val, i_key2, i_val2;                           // intra edges (self-mass)
+    Buf sort_hist, scan_tmp;                                    // sort / scan temporaries
+    Buf stage_rowptr, stage_col, stage_w, stage_lift, stage_gptr;  // host staging
+};
+
+struct Timer {
+    std::string substr;
+    bool on = false;
+    int64_t launches = 0;
+    double total_ms = 0.0;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending;
+    std::vector<cudaEvent_t> pool;
+};
+
+}  // namespace spc
+
+struct spc_context {
+    cudaStream_t stream = nullptr;
+    spc_allocator allocator{};
+    bool has_allocator = false;
+    int device = 0;
+    int num_sms = 0;
+    uint32_t* d_status = nullptr;    // device status word
+    uint32_t* h_status = nullptr;    // pinned mirror
+    int64_t* h_scalars = nullptr;    // pinned readback area
+    std::vector<spc::Block> blocks;  // everything allocated, for destroy
+    spc::Work work;
+    std::vector<spc::LevelBufs> levels;
+    int32_t n_levels = 0;
+    spc::Timer timer;
+    int64_t launches = 0;
+};
+
+namespace spc {
+
+// allocation helpers (allocator callback or cudaMalloc)
+spc_status ensure(spc_context* ctx, Buf& b, size_t bytes);
+void free_all(spc_context* ctx);
+
+// launch accounting + optional timing of selected kernels
+void before_launch(spc_context* ctx, const char* name);
+void after_launch(spc_context* ctx, const char* name);
+
+inline int grid_for(int64_t items, int threads, int max_blocks) {
+    int64_t b = (items + threads - 1) / threads;
+    if (b < 1) b = 1;
+    if (b > max_blocks) b = max_blocks;
+    return static_cast<int>(b);
+}
+
+#define SPC_LAUNCH(ctx, kernel, grid, block, smem, ...)                                   \
+    do {                                                                                 \
+        spc::before_launch((ctx), #kernel);                                              \
+        kernel<<<(grid), (block), (smem), (ctx)->stream>>>(__VA_ARGS__);                 \
+        cudaError_t le_ = cudaGetLastError();                                            \
+        spc::after_launch((ctx), #kernel);                                               \
+        if (le_ != cudaSuccess) {                                                        \
+            spc::set_last_cuda_error(le_, #kernel, __FILE__, __LINE__);                  \
+            return SPC_ERR_CUDA;                                                         \
+        }                                                                                \
+    } while (0)
+
+// ---- device-wide primitives (spc_scan.cu, spc_sort.cu) -------------------------------------
+
+// Exclusive scan of n int32 values into out[0..n] (out[n] = total).  in and out may alias.
+spc_status scan_i32(spc_context* ctx, const int32_t* in, int32_t* out, int64_t n);
+// Same for int64 (out int64).
+spc_status scan_i64(spc_context* ctx, const int32_t* in, int64_t* out, int64_t n);
+// Exclusive scan of 0/1 bytes into int32 positions, out[n] = total.
+spc_status scan_flags_u8(spc_context* ctx, const uint8_t* in, int32_t* out, int64_t n);
+
+// Stable LSD radix sort of (key, value) pairs on key bits [0, end_bit).  The sorted result ends
+// in (keys, vals); (keys_alt, vals_alt) are scratch of the same size.  `count` is the number of
+// valid items (<= capacity).
+spc_status radix_sort_u64(spc_context* ctx, uint64_t* keys, uint32_t* vals, uint64_t* keys_alt,
+                          uint32_t* vals_alt, int64_t count, int end_bit);
+spc_status radix_sort_u32(spc_context* ctx, uint32_t* keys, uint32_t* vals, uint32_t* keys_alt,
+                          uint32_t* vals_alt, int64_t count, int end_bit);
+
+// ---- steps (spc_score.cu, spc_merge.cu, spc_contract.cu) ----------------------------------
+
+struct GraphView {
+    int64_t n = 0, nnz = 0, m = 0;
+    const int64_t* rowptr = nullptr;
+    const int32_t* col = nullptr;
+    const void* w = nullptr;
+    spc_dtype wtype = SPC_F64;
+};
+
+inline bool score_is_f32(spc_dtype wt) { return wt == SPC_F32; }
+inline size_t wsize(spc_dtype wt) { return wt == SPC_F64 ? 8 : 4; }
+inline size_t accsize(spc_dtype wt) { return wt == SPC_F32 ? 4 : 8; }
+
+// S0-S3.  Fills g.m (host) -- synchronises once.  Scores go to `score` (u64 bits or u32 bits).
+spc_status run_score(spc_context* ctx, GraphView& g, bool validate, void* score, int schedule);
+
+// S5-S6 for one graph or a batch.  targets: host value (B == 1) or device int64 per graph.
+struct SelectArgs {
+    int64_t B = 1;
+    const int64_t* d_graph_ptr = nullptr;  // device [B+1] (batched) or null
+    const int64_t* d_targets = nullptr;    // device [B] per-graph targets (batched) or null
+    int64_t target = 0;                    // single-graph target
+};
+spc_status run_select(spc_context* ctx, const GraphView& g, const void* score,
+                      const SelectArgs& sa, int32_t* lift, uint8_t* merged, int64_t* n_c,
+                      int64_t* graph_ptr_c, int32_t* status);
+
+// S7.  Writes into lv's buffers (allocated by the caller through ensure()).
+spc_status run_contract(spc_context* ctx, const GraphView& g, const int32_t* lift, int64_t n_c,
+                        LevelBufs& lv);
+
+// S4 (stand-alone fitness sort).
+spc_status run_sort_fitness(spc_context* ctx, int64_t m, const void* f, bool f32,
+                            int32_t* order_out);
+
+spc_status run_contract_forward(spc_context* ctx, const int32_t* perm, const int32_t* seg,
+                                int64_t m_c, const void* w_und, spc_dtype wt, void* a_und);
+spc_status run_contract_backward(spc_context* ctx, const int32_t* emap, int64_t m,
+                                 const void* grad_a, void* grad_w, spc_dtype wt);
+
+// read the status word (synchronises)
+spc_status sync_status(spc_context* ctx);
+
+}  // namespace spc

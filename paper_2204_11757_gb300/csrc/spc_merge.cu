@@ -1,0 +1,437 @@
+// S5-S6: the merge loop of Algorithm 1, done in parallel, and the relabelling.
+//
+// Algorithm 1 walks the edges in ascending (f, eid) order and merges the two super-nodes of
+// an edge unless they are already one, until n_c super-nodes remain.  Because the keys
+// (f, eid) are all distinct, that loop is Kruskal's algorithm stopped after n - n_c successful
+// merges: the merging edges are exactly the n - n_c lightest edges of the (unique) minimum
+// spanning forest, and the partition is the components of those edges.  So:
+//   1. Boruvka rounds build the minimum spanning forest: every component picks its lightest
+//      incident edge by atomicMin on the key (two phases for 64-bit scores: the score bits,
+//      then the edge id among the edges that tie), picked edges are forest edges (cut
+//      property) and are united in a lock-free union-find whose roots are always the smallest
+//      node id of their set; edges inside one component drop out of the work list, which is
+//      compacted with warp ballots.
+//   2. The forest edges are compacted in eid order, radix-sorted by score (stable, so ties stay
+//      in eid order) -- per graph for batches -- and the first n - n_c of each graph are
+//      united in a second union-find.
+//   3. Relabel: root = smallest member; flag roots, exclusive scan, id = scan[root] (Definition
+//      1's super-nodes, numbered by smallest member).
+// Every retry loop is bounded (kSpinLimit); giving up sets DEV_TIMEOUT in the status word.
+#include "spc_internal.cuh"
+
+namespace spc {
+
+namespace {
+
+__device__ __forceinline__ int32_t ld_parent(const int32_t* parent, int32_t x) {
+    return __ldcg(parent + x);
+}
+
+// find with path halving; parent pointers only ever move to an ancestor, so racing writes are
+// benign.  Bounded: the chain of a forest over n nodes is shorter than kSpinLimit.
+__device__ __forceinline__ int32_t uf_find(int32_t* parent, int32_t x, uint32_t* status) {
+    for (uint32_t it = 0; it < kSpinLimit; ++it) {
+        int32_t p = ld_parent(parent, x);
+        if (p == x) return x;
+        int32_t gp = ld_parent(parent, p);
+        if (gp != p) parent[x] = gp;
+        x = gp;
+    }
+    atomicOr(status, DEV_TIMEOUT);
+    return x;
+}
+
+// unite the sets of a and b; the larger root is hooked below the smaller one with a CAS, so a
+// root is always the smallest node id of its set.  Returns true if the sets were distinct.
+__device__ __forceinline__ bool uf_unite(int32_t* parent, int32_t a, int32_t b,
+                                         uint32_t* status) {
+    for (uint32_t it = 0; it < kSpinLimit; ++it) {
+        a = uf_find(parent, a, status);
+        b = uf_find(parent, b, status);
+        if (a == b) return false;
+        if (a > b) { int32_t t = a; a = b; b = t; }
+        int32_t old = atomicCAS(parent + b, b, a);
+        if (old == b) return true;
+    }
+    atomicOr(status, DEV_TIMEOUT);
+    return false;
+}
+
+__global__ void k_iota(int32_t* a, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        a[i] = (int32_t)i;
+}
+
+template <class KT> struct MinKey;
+// 64-bit scores: best_k holds the score bits, best_e the smallest edge id among the ties
+template <> struct MinKey<unsigned long long> {
+    static constexpr bool two_phase = true;
+    __device__ static unsigned long long pack(unsigned long long k, int32_t) { return k; }
+};
+// 32-bit scores: one atomicMin on (score bits << 32 | edge id)
+template <> struct MinKey<unsigned int> {
+    static constexpr bool two_phase = false;
+    __device__ static unsigned long long pack(unsigned int k, int32_t e) {
+        return ((unsigned long long)k << 32) | (uint32_t)e;
+    }
+};
+
+// warp-aggregated append of (e, ru, rv) to a work list
+__device__ __forceinline__ void wl_append(bool keep, int32_t e, int32_t ru, int32_t rv,
+                                          int32_t* wl_e, int32_t* wl_u, int32_t* wl_v,
+                                          int32_t* count) {
+    const unsigned lane = threadIdx.x & 31;
+    const unsigned act = __activemask();
+    const unsigned bal = __ballot_sync(act, keep);
+    if (bal == 0) return;
+    const int leader = __ffs(bal) - 1;
+    int32_t base = 0;
+    if ((int)lane == leader) base = atomicAdd(count, __popc(bal));
+    base = __shfl_sync(act, base, leader);
+    if (keep) {
+        const int32_t slot = base + __popc(bal & ((1u << lane) - 1u));
+        wl_e[slot] = e;
+        wl_u[slot] = ru;
+        wl_v[slot] = rv;
+    }
+}
+
+// Boruvka phase A: current roots of both ends; keep inter-component edges; lower the
+// component minima.  Round 0 reads every edge directly.
+template <class KT>
+__global__ void __launch_bounds__(kThreads)
+k_bv_minkey(int round0, int64_t m, const int32_t* __restrict__ in_count,
+            const int32_t* __restrict__ wi_e, const int32_t* __restrict__ wi_u,
+            const int32_t* __restrict__ wi_v, const int32_t* __restrict__ eu,
+            const int32_t* __restrict__ ev, const KT* __restrict__ key, int32_t* parent,
+            unsigned long long* best_k, int32_t* wo_e, int32_t* wo_u, int32_t* wo_v,
+            int32_t* out_count, uint32_t* status) {
+    const int64_t cnt = round0 ? m : (int64_t)*in_count;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    // uniform trip count per warp so the ballot in wl_append sees whole warps
+    const int64_t warp_base = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) & ~(int64_t)31;
+    for (int64_t base = warp_base; base < cnt; base += stride) {
+        const int64_t i = base + (threadIdx.x & 31);
+        bool keep = false;
+        int32_t e = 0, ru = 0, rv = 0;
+        if (i < cnt) {
+            int32_t u, v;
+            if (round0) { e = (int32_t)i; u = eu[i]; v = ev[i]; }
+            else { e = wi_e[i]; u = wi_u[i]; v = wi_v[i]; }
+            ru = uf_find(parent, u, status);
+            rv = uf_find(parent, v, status);
+            keep = ru != rv;
+            if (keep) {
+                const unsigned long long pk = MinKey<KT>::pack(key[e], e);
+                atomicMin(best_k + ru, pk);
+                atomicMin(best_k + rv, pk);
+            }
+        }
+        wl_append(keep, e, ru, rv, wo_e, wo_u, wo_v, out_count);
+    }
+}
+
+// Boruvka phase B (64-bit scores only): among the edges whose score equals the component
+// minimum, keep the smallest edge id.
+__global__ void __launch_bounds__(kThreads)
+k_bv_tiebreak(const int32_t* __restrict__ count, const int32_t* __restrict__ wl_e,
+              const int32_t* __restrict__ wl_u, const int32_t* __restrict__ wl_v,
+              const unsigned long long* __restrict__ key, const unsigned long long* best_k,
+              int32_t* best_e) {
+    const int64_t cnt = *count;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cnt;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t e = wl_e[i], ru = wl_u[i], rv = wl_v[i];
+        const unsigned long long k = key[e];
+        if (k == best_k[ru]) atomicMin(best_e + ru, e);
+        if (k == best_k[rv]) atomicMin(best_e + rv, e);
+    }
+}
+
+// Boruvka phase C: an edge picked by either end is a forest edge; unite.  Also clears the
+// other parity's minima at both ends, ready for the next round (the roots that next round
+// touches are all ends of this round's work list).
+template <class KT>
+__global__ void __launch_bounds__(kThreads)
+k_bv_hook(const int32_t* __restrict__ count, const int32_t* __restrict__ wl_e,
+          const int32_t* __restrict__ wl_u, const int32_t* __restrict__ wl_v,
+          const unsigned long long* __restrict__ best_k, const int32_t* __restrict__ best_e,
+          unsigned long long* other_k, int32_t* other_e, int32_t* parent, uint8_t* msf,
+          uint32_t* status) {
+    const int64_t cnt = *count;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cnt;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t e = wl_e[i], ru = wl_u[i], rv = wl_v[i];
+        bool picked;
+        if (MinKey<KT>::two_phase) {
+            picked = best_e[ru] == e || best_e[rv] == e;
+            other_e[ru] = INT32_MAX;
+            other_e[rv] = INT32_MAX;
+        } else {
+            picked = (int32_t)(uint32_t)best_k[ru] == e || (int32_t)(uint32_t)best_k[rv] == e;
+        }
+        other_k[ru] = ~0ull;
+        other_k[rv] = ~0ull;
+        if (picked) {
+            msf[e] = 1;
+            uf_unite(parent, ru, rv, status);
+        }
+    }
+}
+
+// forest edges -> (score key, eid) list in eid order
+template <class KT>
+__global__ void __launch_bounds__(kThreads)
+k_compact_msf(int64_t m, const uint8_t* __restrict__ msf, const int32_t* __restrict__ pos,
+              const KT* __restrict__ key, KT* __restrict__ out_k, uint32_t* __restrict__ out_v) {
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        if (msf[e]) {
+            const int32_t q = pos[e];
+            out_k[q] = key[e];
+            out_v[q] = (uint32_t)e;
+        }
+    }
+}
+
+// graph id of every node of a block-diagonal batch
+__global__ void k_node_graph(int64_t n, int64_t B, const int64_t* __restrict__ graph_ptr,
+                             int32_t* __restrict__ node_graph) {
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n;
+         x += (int64_t)gridDim.x * blockDim.x) {
+        int64_t lo = 0, hi = B;  // largest b with graph_ptr[b] <= x
+        while (hi - lo > 1) {
+            int64_t mid = (lo + hi) >> 1;
+            if (graph_ptr[mid] <= x) lo = mid; else hi = mid;
+        }
+        node_graph[x] = (int32_t)lo;
+    }
+}
+
+// second sort key for batches: graph of the edge's smaller end point
+__global__ void k_graph_keys(const int32_t* __restrict__ count, const uint32_t* __restrict__ eids,
+                             const int32_t* __restrict__ eu, const int32_t* __restrict__ node_graph,
+                             uint32_t* __restrict__ gkey) {
+    const int64_t cnt = *count;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cnt;
+         i += (int64_t)gridDim.x * blockDim.x)
+        gkey[i] = (uint32_t)node_graph[eu[eids[i]]];
+}
+
+// per graph: first forest edge position and the number of merges k_b = n_b - target_b
+__global__ void k_graph_segments(int64_t B, const int64_t* __restrict__ graph_ptr,
+                                 const int64_t* __restrict__ targets,
+                                 const int32_t* __restrict__ up_ptr,
+                                 const int32_t* __restrict__ msf_pos, int32_t* __restrict__ seg_start,
+                                 int32_t* __restrict__ k_graph) {
+    for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < B;
+         b += (int64_t)gridDim.x * blockDim.x) {
+        seg_start[b] = msf_pos[up_ptr[graph_ptr[b]]];
+        const int64_t nb = graph_ptr[b + 1] - graph_ptr[b];
+        int64_t k = nb - targets[b];
+        k_graph[b] = (int32_t)(k < 0 ? 0 : k);
+    }
+}
+
+// unite the ends of the first k forest edges of every graph (sorted by score)
+__global__ void __launch_bounds__(kThreads)
+k_select_unite(const int32_t* __restrict__ count, const uint32_t* __restrict__ eids,
+               const uint32_t* __restrict__ gkey, const int32_t* __restrict__ seg_start,
+               const int32_t* __restrict__ k_graph, int64_t k_single,
+               const int32_t* __restrict__ eu, const int32_t* __restrict__ ev, int32_t* parent,
+               uint8_t* merged, uint32_t* status) {
+    const int64_t cnt = *count;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cnt;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        int64_t rank = i, k = k_single;
+        if (gkey) {
+            const uint32_t b = gkey[i];
+            rank = i - seg_start[b];
+            k = k_graph[b];
+        }
+        if (rank < k) {
+            const int32_t e = (int32_t)eids[i];
+            uf_unite(parent, eu[e], ev[e], status);
+            if (merged) merged[e] = 1;
+        }
+    }
+}
+
+// root (= smallest member) of every node and the root flags
+__global__ void __launch_bounds__(kThreads)
+k_roots(int64_t n, int32_t* parent, int32_t* __restrict__ flag, uint32_t* status) {
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n;
+         x += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t r = uf_find(parent, (int32_t)x, status);
+        flag[x] = (r == (int32_t)x) ? 1 : 0;
+    }
+}
+
+__global__ void __launch_bounds__(kThreads)
+k_lift(int64_t n, int32_t* parent, const int32_t* __restrict__ ids, int32_t* __restrict__ lift,
+       uint32_t* status) {
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n;
+         x += (int64_t)gridDim.x * blockDim.x)
+        lift[x] = ids[uf_find(parent, (int32_t)x, status)];
+}
+
+__global__ void k_graph_ptr_c(int64_t B, const int64_t* __restrict__ graph_ptr,
+                              const int32_t* __restrict__ ids, const int64_t* __restrict__ targets,
+                              int64_t* __restrict__ graph_ptr_c, int32_t* __restrict__ warn) {
+    for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b <= B;
+         b += (int64_t)gridDim.x * blockDim.x) {
+        graph_ptr_c[b] = ids[graph_ptr[b]];
+        if (b < B) {
+            const int64_t nc = (int64_t)ids[graph_ptr[b + 1]] - ids[graph_ptr[b]];
+            if (nc > targets[b]) atomicOr(warn, 1);
+        }
+    }
+}
+
+template <class KT>
+spc_status select_typed(spc_context* ctx, const GraphView& g, const KT* key,
+                        const SelectArgs& sa, int32_t* lift, uint8_t* merged, int64_t* n_c_out,
+                        int64_t* graph_ptr_c, int32_t* status_out) {
+    Work& W = ctx->work;
+    const int64_t n = g.n, m = g.m;
+    const int maxb = ctx->num_sms * 8;
+    uint32_t* status = ctx->d_status;
+    int32_t* parent = W.parent.as<int32_t>();
+    int32_t* counters = W.counters.as<int32_t>();  // [0..1] work-list counts, [2] warn flag
+    const bool batched = sa.B > 1 || sa.d_graph_ptr != nullptr;
+
+    SPC_LAUNCH(ctx, k_iota, grid_for(n, kThreads, maxb), kThreads, 0, parent, n);
+    if (merged) SPC_CUDA(cudaMemsetAsync(merged, 0, (size_t)m, ctx->stream));
+    SPC_CUDA(cudaMemsetAsync(W.msf.p, 0, (size_t)(m + 1), ctx->stream));
+    SPC_CUDA(cudaMemsetAsync(W.best_k[0].p, 0xff, (size_t)n * 8, ctx->stream));
+    SPC_CUDA(cudaMemsetAsync(W.best_k[1].p, 0xff, (size_t)n * 8, ctx->stream));
+    if (MinKey<KT>::two_phase) {
+        SPC_CUDA(cudaMemsetAsync(W.best_e[0].p, 0x7f, (size_t)n * 4, ctx->stream));
+        SPC_CUDA(cudaMemsetAsync(W.best_e[1].p, 0x7f, (size_t)n * 4, ctx->stream));
+    }
+    // ---- 1. Boruvka minimum spanning forest -------------------------------------------
+    int64_t cur = m;
+    for (int round = 0; cur > 0; ++round) {
+        const int in = round & 1, out = in ^ 1;
+        const int par = round & 1;
+        SPC_CUDA(cudaMemsetAsync(counters + out, 0, sizeof(int32_t), ctx->stream));
+        SPC_LAUNCH(ctx, k_bv_minkey<KT>, grid_for(cur, kThreads, maxb), kThreads, 0,
+                   round == 0 ? 1 : 0, m, counters + in, W.wl_e[in].as<int32_t>(),
+                   W.wl_u[in].as<int32_t>(), W.wl_v[in].as<int32_t>(), W.eu.as<int32_t>(),
+                   W.ev.as<int32_t>(), key, parent, W.best_k[par].as<unsigned long long>(),
+                   W.wl_e[out].as<int32_t>(), W.wl_u[out].as<int32_t>(),
+                   W.wl_v[out].as<int32_t>(), counters + out, status);
+        if (MinKey<KT>::two_phase) {
+            SPC_LAUNCH(ctx, k_bv_tiebreak, grid_for(cur, kThreads, maxb), kThreads, 0,
+                       counters + out, W.wl_e[out].as<int32_t>(), W.wl_u[out].as<int32_t>(),
+                       W.wl_v[out].as<int32_t>(),
+                       reinterpret_cast<const unsigned long long*>(key),
+                       W.best_k[par].as<unsigned long long>(), W.best_e[par].as<int32_t>());
+        }
+        SPC_LAUNCH(ctx, k_bv_hook<KT>, grid_for(cur, kThreads, maxb), kThreads, 0,
+                   counters + out, W.wl_e[out].as<int32_t>(), W.wl_u[out].as<int32_t>(),
+                   W.wl_v[out].as<int32_t>(), W.best_k[par].as<unsigned long long>(),
+                   W.best_e[par].as<int32_t>(), W.best_k[par ^ 1].as<unsigned long long>(),
+                   W.best_e[par ^ 1].as<int32_t>(), parent, W.msf.as<uint8_t>(), status);
+        // next work-list size (host loop; the captured path keeps it on the device)
+        SPC_CUDA(cudaMemcpyAsync(ctx->h_scalars, counters + out, sizeof(int32_t),
+                                 cudaMemcpyDeviceToHost, ctx->stream));
+        SPC_CUDA(cudaStreamSynchronize(ctx->stream));
+        cur = *reinterpret_cast<int32_t*>(ctx->h_scalars);
+        // every round at least halves the components that still have edges
+        if (round > 64) return SPC_ERR_TIMEOUT;
+        // slot `out` (list and count) is the next round's input
+    }
+    // ---- 2. lightest forest edges per graph ---------------------------------------------
+    int32_t* pos = W.c_pos.as<int32_t>();
+    SPC_TRY(scan_flags_u8(ctx, W.msf.as<uint8_t>(), pos, m));
+    KT* sk = W.sel_key.as<KT>();
+    uint32_t* sv = W.sel_val.as<uint32_t>();
+    SPC_LAUNCH(ctx, k_compact_msf<KT>, grid_for(m, kThreads, maxb), kThreads, 0, m,
+               W.msf.as<uint8_t>(), pos, key, sk, sv);
+    SPC_CUDA(cudaMemcpyAsync(ctx->h_scalars, pos + m, sizeof(int32_t), cudaMemcpyDeviceToHost,
+                             ctx->stream));
+    SPC_CUDA(cudaStreamSynchronize(ctx->stream));
+    const int64_t n_msf = *reinterpret_cast<int32_t*>(ctx->h_scalars);
+    const int key_bits = sizeof(KT) == 8 ? 63 : 31;  // scores are >= +0: sign bit clear
+    if (sizeof(KT) == 8) {
+        SPC_TRY(radix_sort_u64(ctx, reinterpret_cast<uint64_t*>(sk), sv,
+                               W.sel_key2.as<uint64_t>(), W.sel_val2.as<uint32_t>(), n_msf,
+                               key_bits));
+    } else {
+        SPC_TRY(radix_sort_u32(ctx, reinterpret_cast<uint32_t*>(sk), sv,
+                               W.sel_key2.as<uint32_t>(), W.sel_val2.as<uint32_t>(), n_msf,
+                               key_bits));
+    }
+    uint32_t* gkey = nullptr;
+    int32_t* seg_start = nullptr;
+    int32_t* k_graph = nullptr;
+    int32_t* cnt_dev = counters + 3;
+    SPC_CUDA(cudaMemcpyAsync(cnt_dev, pos + m, sizeof(int32_t), cudaMemcpyDeviceToDevice,
+                             ctx->stream));
+    if (batched) {
+        int32_t* node_graph = W.node_graph.as<int32_t>();
+        SPC_LAUNCH(ctx, k_node_graph, grid_for(n, kThreads, maxb), kThreads, 0, n, sa.B,
+                   sa.d_graph_ptr, node_graph);
+        gkey = W.sel_key2.as<uint32_t>();  // reuse: free after the score sort
+        uint32_t* gval = sv;
+        SPC_LAUNCH(ctx, k_graph_keys, grid_for(n_msf, kThreads, maxb), kThreads, 0, cnt_dev,
+                   gval, W.eu.as<int32_t>(), node_graph, gkey);
+        int gbits = 1;
+        while ((1ll << gbits) < sa.B) ++gbits;
+        // stable sort by graph id keeps the score order inside every graph
+        SPC_TRY(radix_sort_u32(ctx, gkey, gval, W.t_key.as<uint32_t>(), W.t_val.as<uint32_t>(),
+                               n_msf, gbits));
+        seg_start = W.seg_start.as<int32_t>();
+        k_graph = W.k_graph.as<int32_t>();
+        SPC_LAUNCH(ctx, k_graph_segments, grid_for(sa.B, kThreads, maxb), kThreads, 0, sa.B,
+                   sa.d_graph_ptr, sa.d_targets, W.up_ptr.as<int32_t>(), pos, seg_start,
+                   k_graph);
+    }
+    int32_t* parent2 = W.parent2.as<int32_t>();
+    SPC_LAUNCH(ctx, k_iota, grid_for(n, kThreads, maxb), kThreads, 0, parent2, n);
+    const int64_t k_single = batched ? 0 : (n - sa.target > 0 ? n - sa.target : 0);
+    if (n_msf > 0) {
+        SPC_LAUNCH(ctx, k_select_unite, grid_for(n_msf, kThreads, maxb), kThreads, 0, cnt_dev,
+                   sv, gkey, seg_start, k_graph, k_single, W.eu.as<int32_t>(),
+                   W.ev.as<int32_t>(), parent2, merged, status);
+    }
+    // ---- 3. relabel ------------------------------------------------------------------
+    int32_t* flag = W.flag.as<int32_t>();
+    int32_t* ids = W.ids.as<int32_t>();
+    SPC_LAUNCH(ctx, k_roots, grid_for(n, kThreads, maxb), kThreads, 0, n, parent2, flag, status);
+    SPC_TRY(scan_i32(ctx, flag, ids, n));
+    SPC_LAUNCH(ctx, k_lift, grid_for(n, kThreads, maxb), kThreads, 0, n, parent2, ids, lift,
+               status);
+    int32_t* warn = counters + 2;
+    SPC_CUDA(cudaMemsetAsync(warn, 0, sizeof(int32_t), ctx->stream));
+    if (batched) {
+        SPC_LAUNCH(ctx, k_graph_ptr_c, grid_for(sa.B + 1, kThreads, maxb), kThreads, 0, sa.B,
+                   sa.d_graph_ptr, ids, sa.d_targets, graph_ptr_c, warn);
+    }
+    SPC_CUDA(cudaMemcpyAsync(ctx->h_scalars, ids + n, sizeof(int32_t), cudaMemcpyDeviceToHost,
+                             ctx->stream));
+    SPC_CUDA(cudaMemcpyAsync(ctx->h_scalars + 1, warn, sizeof(int32_t), cudaMemcpyDeviceToHost,
+                             ctx->stream));
+    SPC_CUDA(cudaStreamSynchronize(ctx->stream));
+    const int64_t n_c = *reinterpret_cast<int32_t*>(ctx->h_scalars);
+    const int32_t warn_b = *reinterpret_cast<int32_t*>(ctx->h_scalars + 1);
+    *n_c_out = n_c;
+    *status_out = (batched ? warn_b != 0 : n_c > sa.target) ? SPC_WARN_TARGET_NOT_REACHED : SPC_OK;
+    return SPC_OK;
+}
+
+}  // namespace
+
+spc_status run_select(spc_context* ctx, const GraphView& g, const void* score,
+                      const SelectArgs& sa, int32_t* lift, uint8_t* merged, int64_t* n_c,
+                      int64_t* graph_ptr_c, int32_t* status) {
+    if (score_is_f32(g.wtype))
+        return select_typed<unsigned int>(ctx, g, static_cast<const unsigned int*>(score), sa,
+                                          lift, merged, n_c, graph_ptr_c, status);
+    return select_typed<unsigned long long>(ctx, g, static_cast<const unsigned long long*>(score),
+                                            sa, lift, merged, n_c, graph_ptr_c, status);
+}
+
+}  // namespace spc

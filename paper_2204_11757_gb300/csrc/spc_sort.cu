@@ -1,0 +1,200 @@
+// Stable LSD radix sort of (key, uint32 value) pairs, 8-bit digits.
+//
+// Per digit: an upsweep builds one 256-bin histogram per 4096-item tile (digit-major), a
+// device-wide exclusive scan turns the histograms into output offsets, and a downsweep ranks
+// every item inside its tile (warp __match_any_sync ranks, per-warp counters, cross-warp
+// prefix), stages the tile in shared memory in digit order and writes it out so that items of
+// one digit leave the tile as one contiguous run.  Tiles keep input order and ranks are stable,
+// so equal keys keep their input order.  No inter-block waits.
+#include "spc_internal.cuh"
+
+namespace spc {
+
+namespace {
+
+constexpr int RT = 256;              // threads per block
+constexpr int RW = RT / 32;          // warps
+constexpr int RI = 16;               // items per lane
+constexpr int RTILE = RT * RI;       // 4096 items per tile
+constexpr int RADIX = 256;
+
+template <class K>
+__device__ __forceinline__ uint32_t digit_of(K key, int shift, uint32_t mask) {
+    return (uint32_t)(key >> shift) & mask;
+}
+
+template <class K>
+__global__ void __launch_bounds__(RT) k_rs_upsweep(const K* __restrict__ keys, int64_t count,
+                                                   int shift, uint32_t mask,
+                                                   int32_t* __restrict__ hist, int64_t tiles) {
+    __shared__ uint32_t h[RADIX];
+    h[threadIdx.x] = 0;
+    __syncthreads();
+    const int64_t base = (int64_t)blockIdx.x * RTILE;
+    const unsigned lane = threadIdx.x & 31;
+#pragma unroll 4
+    for (int k = 0; k < RI; ++k) {
+        int64_t i = base + (int64_t)k * RT + threadIdx.x;
+        bool valid = i < count;
+        uint32_t d = valid ? digit_of(keys[i], shift, mask) : (RADIX + lane);
+        unsigned peers = __match_any_sync(0xffffffffu, d);
+        if (valid && lane == (unsigned)(__ffs(peers) - 1)) atomicAdd(&h[d], (uint32_t)__popc(peers));
+    }
+    __syncthreads();
+    hist[(int64_t)threadIdx.x * tiles + blockIdx.x] = (int32_t)h[threadIdx.x];
+}
+
+template <class K>
+struct SortSmem {
+    K keys[RTILE];
+    uint32_t vals[RTILE];
+    uint32_t wcnt[RW][RADIX];
+    uint32_t tile_base[RADIX];
+    int32_t gofs[RADIX];
+};
+
+template <class K>
+__global__ void __launch_bounds__(RT) k_rs_downsweep(const K* __restrict__ kin,
+                                                     const uint32_t* __restrict__ vin,
+                                                     K* __restrict__ kout,
+                                                     uint32_t* __restrict__ vout, int64_t count,
+                                                     int shift, uint32_t mask,
+                                                     const int32_t* __restrict__ offs,
+                                                     int64_t tiles) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    SortSmem<K>& s = *reinterpret_cast<SortSmem<K>*>(smem_raw);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const unsigned lt_mask = (1u << lane) - 1u;
+    for (int d = lane; d < RADIX; d += 32) s.wcnt[warp][d] = 0;
+    __syncwarp();
+    const int64_t base = (int64_t)blockIdx.x * RTILE + (int64_t)warp * (32 * RI);
+    K key[RI];
+    uint32_t val[RI];
+    uint32_t dig[RI];
+    uint32_t rnk[RI];
+#pragma unroll
+    for (int k = 0; k < RI; ++k) {
+        int64_t i = base + k * 32 + lane;
+        bool valid = i < count;
+        key[k] = valid ? kin[i] : K(0);
+        val[k] = valid ? vin[i] : 0u;
+        uint32_t d = valid ? digit_of(key[k], shift, mask) : (RADIX + lane);
+        unsigned peers = __match_any_sync(0xffffffffu, d);
+        uint32_t before = valid ? s.wcnt[warp][d] : 0u;
+        rnk[k] = before + (uint32_t)__popc(peers & lt_mask);
+        dig[k] = d;
+        __syncwarp();
+        if (valid && lane == __ffs(peers) - 1) s.wcnt[warp][d] = before + (uint32_t)__popc(peers);
+        __syncwarp();
+    }
+    __syncthreads();
+    // cross-warp exclusive prefix per digit, then exclusive scan over digits
+    {
+        const int d = threadIdx.x;  // RT == RADIX
+        uint32_t run = 0;
+#pragma unroll
+        for (int w = 0; w < RW; ++w) {
+            uint32_t t = s.wcnt[w][d];
+            s.wcnt[w][d] = run;
+            run += t;
+        }
+        // block-wide exclusive scan of `run` over the 256 digits
+        uint32_t v = run;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t t = __shfl_up_sync(0xffffffffu, v, o);
+            if (lane >= o) v += t;
+        }
+        __shared__ uint32_t wsum[RW];
+        if (lane == 31) wsum[warp] = v;
+        __syncthreads();
+        if (warp == 0) {
+            uint32_t x = (lane < RW) ? wsum[lane] : 0u;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                uint32_t t = __shfl_up_sync(0xffffffffu, x, o);
+                if (lane >= o) x += t;
+            }
+            if (lane < RW) wsum[lane] = x;
+        }
+        __syncthreads();
+        uint32_t excl = v - run + (warp > 0 ? wsum[warp - 1] : 0u);
+        s.tile_base[d] = excl;
+        s.gofs[d] = offs[(int64_t)d * tiles + blockIdx.x];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < RI; ++k) {
+        if (dig[k] < RADIX) {
+            uint32_t pos = s.tile_base[dig[k]] + s.wcnt[warp][dig[k]] + rnk[k];
+            s.keys[pos] = key[k];
+            s.vals[pos] = val[k];
+        }
+    }
+    __syncthreads();
+    const int64_t tb = (int64_t)blockIdx.x * RTILE;
+    const int64_t rem = count - tb;
+    const int valid_n = rem < RTILE ? (int)rem : RTILE;
+    for (int i = threadIdx.x; i < valid_n; i += RT) {
+        K k = s.keys[i];
+        uint32_t d = digit_of(k, shift, mask);
+        int64_t o = (int64_t)s.gofs[d] + (i - (int64_t)s.tile_base[d]);
+        kout[o] = k;
+        vout[o] = s.vals[i];
+    }
+}
+
+template <class K>
+spc_status radix_sort_impl(spc_context* ctx, K* keys, uint32_t* vals, K* keys_alt,
+                           uint32_t* vals_alt, int64_t count, int end_bit) {
+    if (count <= 1 || end_bit <= 0) return SPC_OK;
+    const int64_t tiles = (count + RTILE - 1) / RTILE;
+    const size_t hist_bytes = ((size_t)RADIX * tiles + 1) * sizeof(int32_t);
+    SPC_TRY(ensure(ctx, ctx->work.sort_hist, hist_bytes));
+    int32_t* hist = ctx->work.sort_hist.as<int32_t>();
+    const size_t smem = sizeof(SortSmem<K>);
+    static bool attr_set = false;
+    if (!attr_set) {
+        SPC_CUDA(cudaFuncSetAttribute(k_rs_downsweep<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)smem));
+        attr_set = true;
+    }
+    K* ka = keys;
+    uint32_t* va = vals;
+    K* kb = keys_alt;
+    uint32_t* vb = vals_alt;
+    int passes = 0;
+    for (int shift = 0; shift < end_bit; shift += 8) {
+        const int bits = (end_bit - shift) < 8 ? (end_bit - shift) : 8;
+        const uint32_t mask = (1u << bits) - 1u;
+        SPC_LAUNCH(ctx, k_rs_upsweep<K>, (unsigned)tiles, RT, 0, ka, count, shift, mask, hist,
+                   tiles);
+        SPC_TRY(scan_i32(ctx, hist, hist, (int64_t)RADIX * tiles));
+        SPC_LAUNCH(ctx, k_rs_downsweep<K>, (unsigned)tiles, RT, smem, ka, va, kb, vb, count,
+                   shift, mask, hist, tiles);
+        K* tk = ka; ka = kb; kb = tk;
+        uint32_t* tv = va; va = vb; vb = tv;
+        ++passes;
+    }
+    if (passes & 1) {
+        SPC_CUDA(cudaMemcpyAsync(keys, ka, (size_t)count * sizeof(K), cudaMemcpyDeviceToDevice,
+                                 ctx->stream));
+        SPC_CUDA(cudaMemcpyAsync(vals, va, (size_t)count * sizeof(uint32_t),
+                                 cudaMemcpyDeviceToDevice, ctx->stream));
+    }
+    return SPC_OK;
+}
+
+}  // namespace
+
+spc_status radix_sort_u64(spc_context* ctx, uint64_t* keys, uint32_t* vals, uint64_t* keys_alt,
+                          uint32_t* vals_alt, int64_t count, int end_bit) {
+    return radix_sort_impl<uint64_t>(ctx, keys, vals, keys_alt, vals_alt, count, end_bit);
+}
+
+spc_status radix_sort_u32(spc_context* ctx, uint32_t* keys, uint32_t* vals, uint32_t* keys_alt,
+                          uint32_t* vals_alt, int64_t count, int end_bit) {
+    return radix_sort_impl<uint32_t>(ctx, keys, vals, keys_alt, vals_alt, count, end_bit);
+}
+
+}  // namespace spc

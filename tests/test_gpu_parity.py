@@ -1,0 +1,370 @@
+"""GPU path vs the CPU oracle, element by element, through the C ABI (needs a GB300).
+
+Integer, index and topology results must be bit-exact; scores are compared as bit patterns
+(the paper's order of operations is fixed, see the oracle); coarse weights are compared bit
+for bit too, because both sides sum in ascending fine edge id.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import oracle as O
+from paper_2204_11757_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import __graft_entry__ as ge
+    ge.build()
+    from paper_2204_11757_gb300 import api
+    c = api.Context()
+    yield c
+    c.close()
+
+
+def _api():
+    from paper_2204_11757_gb300 import api
+    return api
+
+
+def _bits(a):
+    a = np.ascontiguousarray(a)
+    return a.view(np.uint64) if a.dtype.itemsize == 8 else a.view(np.uint32)
+
+
+def _small_graphs():
+    gs = [I.path_graph(2), I.path_graph(7), I.cycle_graph(9), I.complete_graph(6)]
+    for seed in range(6):
+        wt = ["unit", "int", "float"][seed % 3]
+        dt = np.float64 if wt == "float" else np.int32
+        gs.append(I.random_graph(40 + 10 * seed, 0.1, seed, weight=wt, dtype=dt,
+                                 connected=seed % 2 == 0))
+    gs.append(I.random_graph(50, 0.2, 99, weight="float", dtype=np.float32, connected=True))
+    rows, _ = I.config_graph("c1_tri64_unit")
+    gs.append(rows)
+    return gs
+
+
+SMALL = _small_graphs()
+MID = ["s2_tri256_f64", "s3_tet33_f64", "s4_rgg64k_f32"]
+
+
+def _graph(name):
+    g, _ = I.config_graph(name)
+    return g
+
+
+# ---- S0-S3 -------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("gi", range(len(SMALL)))
+@pytest.mark.parametrize("schedule", [1, 2])
+def test_score_small_bitexact(ctx, gi, schedule):
+    g = SMALL[gi]
+    api = _api()
+    ref = O.score(g)
+    csr = api.CSR.from_graph(g)
+    if schedule == 1:
+        f = ctx.score(csr).cpu().numpy()
+    else:
+        ctx.coarsen(csr, g.n, levels=1, schedule=2)
+        f = ctx.level(0).score.cpu().numpy()
+    assert f.dtype == ref.dtype
+    assert np.array_equal(_bits(f), _bits(ref))
+
+
+@pytest.mark.parametrize("name", MID)
+def test_score_mid_bitexact(ctx, name):
+    g = _graph(name)
+    api = _api()
+    ref = O.score(g)
+    f = ctx.score(api.CSR.from_graph(g)).cpu().numpy()
+    assert np.array_equal(_bits(f), _bits(ref))
+
+
+# ---- S4 ------------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("name", ["c1_tri64_unit", "s2_tri256_f64", "s4_rgg64k_f32"])
+def test_sort_fitness(ctx, name):
+    g = _graph(name)
+    f = O.score(g)
+    ref = O.sort_fitness(f)
+    order = ctx.sort_fitness(torch.from_numpy(f).cuda()).cpu().numpy()
+    assert np.array_equal(order, ref)
+
+
+def test_sort_fitness_ties_and_ragged(ctx):
+    rng = np.random.default_rng(3)
+    for m in (1, 2, 4095, 4096, 4097, 20000):
+        f = rng.integers(0, 7, size=m).astype(np.float64) / 4.0  # many exact ties
+        ref = O.sort_fitness(f)
+        assert np.array_equal(ctx.sort_fitness(torch.from_numpy(f).cuda()).cpu().numpy(), ref)
+        f32 = f.astype(np.float32)
+        ref32 = O.sort_fitness(f32)
+        assert np.array_equal(ctx.sort_fitness(torch.from_numpy(f32).cuda()).cpu().numpy(), ref32)
+
+
+# ---- S5-S6 ---------------------------------------------------------------------------------------
+
+def _ref_select(g, n_c):
+    f = O.score(g)
+    order = O.sort_fitness(f)
+    rep, merged, s, rc = O.greedy_merge(g, order, n_c)
+    lift, nc = O.relabel(rep)
+    return f, lift, merged, nc, rc
+
+
+@pytest.mark.parametrize("gi", range(len(SMALL)))
+def test_select_small(ctx, gi):
+    g = SMALL[gi]
+    api = _api()
+    csr = api.CSR.from_graph(g)
+    for n_c in sorted({1, 2, max(1, g.n // 3), max(1, g.n // 2), g.n - 1 if g.n > 1 else 1,
+                       g.n, g.n + 5}):
+        f, lift_ref, merged_ref, nc_ref, rc = _ref_select(g, n_c)
+        lift, merged, nc, st = ctx.select_merges(csr, torch.from_numpy(f).cuda(), n_c)
+        assert nc == nc_ref
+        assert np.array_equal(lift.cpu().numpy(), lift_ref)
+        assert np.array_equal(merged.cpu().numpy().astype(bool), merged_ref)
+        assert st == rc
+
+
+@pytest.mark.parametrize("name", MID)
+def test_select_mid(ctx, name):
+    g = _graph(name)
+    api = _api()
+    f, lift_ref, merged_ref, nc_ref, rc = _ref_select(g, g.n // 2)
+    lift, merged, nc, st = ctx.select_merges(api.CSR.from_graph(g), torch.from_numpy(f).cuda(),
+                                             g.n // 2)
+    assert nc == nc_ref and st == rc
+    assert np.array_equal(lift.cpu().numpy(), lift_ref)
+    assert np.array_equal(merged.cpu().numpy().astype(bool), merged_ref)
+
+
+def test_select_disconnected_and_isolated(ctx):
+    api = _api()
+    # three components plus two isolated nodes
+    eu = np.array([0, 1, 3, 4, 5, 8]); ev = np.array([1, 2, 4, 5, 6, 9])
+    g = I.csr_from_edges(12, eu, ev, np.ones(6, np.int32))
+    csr = api.CSR.from_graph(g)
+    for n_c in (1, 3, 5, 6, 7, 12):
+        f, lift_ref, merged_ref, nc_ref, rc = _ref_select(g, n_c)
+        lift, merged, nc, st = ctx.select_merges(csr, torch.from_numpy(f).cuda(), n_c)
+        assert np.array_equal(lift.cpu().numpy(), lift_ref)
+        assert nc == nc_ref and st == rc
+    assert nc_ref == 12
+
+
+# ---- S7 --------------------------------------------------------------------------------------------
+
+def _check_level(lv, ref_level, exact_weights=True):
+    co = ref_level.coarse
+    assert lv.n_c == ref_level.n_c
+    assert lv.m_c == co.m_c
+    assert np.array_equal(lv.lift.cpu().numpy(), ref_level.lift)
+    assert np.array_equal(lv.emap.cpu().numpy(), co.emap)
+    assert np.array_equal(lv.rowptr_c.cpu().numpy(), co.graph.rowptr)
+    assert np.array_equal(lv.col_c.cpu().numpy(), co.graph.col)
+    for got, want in ((lv.w_c, co.graph.w), (lv.a_und, co.a_und), (lv.self_mass, co.self_mass)):
+        got = got.cpu().numpy()
+        assert got.dtype == want.dtype
+        assert np.array_equal(_bits(got) if got.dtype.kind == "f" else got,
+                              _bits(want) if want.dtype.kind == "f" else want)
+    # perm/seg describe each coarse edge's fine edges in ascending eid order
+    perm = lv.perm.cpu().numpy(); seg = lv.seg.cpu().numpy()
+    assert seg[0] == 0 and seg[-1] == lv.m_inter
+    em = co.emap
+    for k in np.linspace(0, max(lv.m_c - 1, 0), num=min(lv.m_c, 50)).astype(int):
+        es = perm[seg[k]:seg[k + 1]]
+        assert np.all(np.diff(es) > 0)
+        assert np.all(em[es] == k)
+
+
+@pytest.mark.parametrize("gi", range(len(SMALL)))
+def test_contract_small(ctx, gi):
+    g = SMALL[gi]
+    api = _api()
+    for n_c in sorted({1, max(1, g.n // 4), max(1, g.n // 2), g.n}):
+        ref = O.coarsen_level(g, n_c)
+        lv = ctx.contract(api.CSR.from_graph(g), torch.from_numpy(ref.lift).cuda(), ref.n_c)
+        _check_level(lv, ref)
+
+
+def test_contract_int_overflow_reported(ctx):
+    api = _api()
+    from paper_2204_11757_gb300 import native as N
+    g = I.csr_from_edges(3, np.array([0, 0]), np.array([1, 2]),
+                         np.array([2 ** 31 - 1, 2 ** 31 - 1], dtype=np.int32))
+    with pytest.raises(N.SpcError) as ei:
+        ctx.contract(api.CSR.from_graph(g), torch.tensor([0, 1, 1], dtype=torch.int32).cuda(), 2)
+    assert ei.value.status == -8
+
+
+# ---- full method ------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("name", ["c1_tri64_unit", "s2_tri256_f64", "s3_tet33_f64",
+                                  "s4_rgg64k_f32", "s4_rgg64k_f32_one"])
+def test_coarsen_levels_match_oracle(ctx, name):
+    g, cfg = I.config_graph(name)
+    api = _api()
+    levels_ref, total_ref = O.coarsen(g, cfg["ratio"], cfg["mode"])
+    L = len(levels_ref)
+    n_c = levels_ref[-1].target
+    lift, nca, st = ctx.coarsen(api.CSR.from_graph(g), n_c, levels=L)
+    assert nca == levels_ref[-1].n_c
+    assert np.array_equal(lift.cpu().numpy(), total_ref)
+    got = ctx.levels()
+    assert len(got) == L
+    for lv, ref in zip(got, levels_ref):
+        assert np.array_equal(_bits(lv.score.cpu().numpy()), _bits(ref.f))
+        _check_level(lv, ref)
+    em = ctx.compose_emap().cpu().numpy()
+    assert np.array_equal(em, O.compose_emaps(levels_ref))
+
+
+def test_coarsen_host_buffers_match_device(ctx):
+    api = _api()
+    g, cfg = I.config_graph("s2_tri256_f64")
+    dev_lift, nc1, _ = ctx.coarsen(api.CSR.from_graph(g), g.n // 64, levels=6)
+    host = api.CSR.from_graph(g, device="cpu", pin=True)
+    lift_h = torch.empty(g.n, dtype=torch.int32).pin_memory()
+    lift, nc2, _ = ctx.coarsen(host, g.n // 64, levels=6, lift_out=lift_h)
+    assert nc1 == nc2
+    assert np.array_equal(lift.numpy(), dev_lift.cpu().numpy())
+
+
+def test_coarsen_batched_matches_per_graph_oracle(ctx):
+    api = _api()
+    b, cfg = I.config_graph("s5_batch40_f32")
+    res = O.coarsen_batch(b, cfg["ratio"], cfg["mode"])
+    csr = api.CSR.from_graph(b.graph)
+    gp = torch.from_numpy(b.graph_ptr).cuda()
+    lift, gpc, st = ctx.coarsen_batched(csr, gp, cfg["ratio"], levels=3)
+    lift = lift.cpu().numpy(); gpc = gpc.cpu().numpy()
+    for bi, (levels_ref, total_ref) in enumerate(res):
+        n0, n1 = b.graph_ptr[bi], b.graph_ptr[bi + 1]
+        assert gpc[bi + 1] - gpc[bi] == levels_ref[-1].n_c
+        assert np.array_equal(lift[n0:n1] - gpc[bi], total_ref)
+    # the final coarse graphs, graph by graph
+    last = ctx.level(2, batched_B=b.B)
+    rp = last.rowptr_c.cpu().numpy(); cc = last.col_c.cpu().numpy(); wc = last.w_c.cpu().numpy()
+    for bi, (levels_ref, _) in enumerate(res):
+        cg = levels_ref[-1].coarse.graph
+        s0, s1 = gpc[bi], gpc[bi + 1]
+        seg_rp = rp[s0:s1 + 1] - rp[s0]
+        assert np.array_equal(seg_rp, cg.rowptr)
+        assert np.array_equal(cc[rp[s0]:rp[s1]] - s0, cg.col)
+        assert np.array_equal(_bits(wc[rp[s0]:rp[s1]]), _bits(cg.w))
+
+
+# ---- S9 and the autograd Function ---------------------------------------------------------------------
+
+def test_backward_and_autograd(ctx):
+    api = _api()
+    g, cfg = I.config_graph("s4_rgg64k_f32")
+    levels_ref, _ = O.coarsen(g, cfg["ratio"], cfg["mode"])
+    L = len(levels_ref)
+    ctx.coarsen(api.CSR.from_graph(g), levels_ref[-1].target, levels=L)
+    levels = ctx.levels()
+    plan = api.ContractionPlan.from_levels(ctx, levels)
+    w = torch.from_numpy(g.w_und).cuda().requires_grad_(True)
+    a = api.contract_weights(w, plan)
+    assert np.array_equal(_bits(a.detach().cpu().numpy()), _bits(levels_ref[-1].coarse.a_und))
+    gvec = torch.randn(a.shape[0], dtype=torch.float32, device="cuda",
+                       generator=torch.Generator("cuda").manual_seed(0))
+    (a * gvec).sum().backward()
+    em = O.compose_emaps(levels_ref)
+    ref = O.contract_backward(em, gvec.cpu().numpy())
+    assert np.array_equal(w.grad.cpu().numpy(), ref)
+
+
+def test_autograd_gradcheck_and_fd_float64(ctx):
+    api = _api()
+    g = I.random_graph(60, 0.1, 5, weight="float", dtype=np.float64, connected=True)
+    ctx.coarsen(api.CSR.from_graph(g), 9, levels=2)
+    plan = api.ContractionPlan.from_levels(ctx, ctx.levels())
+    w = torch.from_numpy(g.w_und).cuda().requires_grad_(True)
+    assert torch.autograd.gradcheck(lambda x: api.contract_weights(x, plan), (w,), eps=1e-6,
+                                    atol=1e-8)
+    # central finite differences of L(w) = <a(w), gvec>
+    a = api.contract_weights(w, plan)
+    gvec = torch.linspace(-2, 3, a.shape[0], dtype=torch.float64, device="cuda")
+    (a * gvec).sum().backward()
+    h = 1e-4
+    for e in (0, 7, 33, g.m - 1):
+        wp = w.detach().clone(); wp[e] += h
+        wm = w.detach().clone(); wm[e] -= h
+        fd = ((api.contract_weights(wp, plan) * gvec).sum()
+              - (api.contract_weights(wm, plan) * gvec).sum()) / (2 * h)
+        assert abs(fd.item() - w.grad[e].item()) < 1e-8
+
+
+# ---- error paths -----------------------------------------------------------------------------------
+
+def _bad(kind):
+    g = I.random_graph(30, 0.2, 1, weight="float", dtype=np.float64, connected=True)
+    rowptr, col, w = g.rowptr.copy(), g.col.copy(), g.w.copy()
+    if kind == "unsorted":
+        r = np.argmax(np.diff(rowptr) >= 3)
+        a = rowptr[r]
+        col[a], col[a + 1] = col[a + 1], col[a]
+    elif kind == "asym":
+        w[5] = w[5] * 1.5
+    elif kind == "weight":
+        w[3] = -1.0
+        # keep it symmetric so only the weight check can fire
+        r = np.searchsorted(rowptr, 3, side="right") - 1
+        y = col[3]
+        j = rowptr[y] + np.searchsorted(col[rowptr[y]:rowptr[y + 1]], r)
+        w[j] = -1.0
+    elif kind == "range":
+        col[-1] = 10 ** 6
+    return rowptr, col, w
+
+
+@pytest.mark.parametrize("kind,code", [("unsorted", -4), ("asym", -2), ("weight", -9),
+                                       ("range", -4)])
+def test_invalid_input_reported(ctx, kind, code):
+    api = _api()
+    from paper_2204_11757_gb300 import native as N
+    rowptr, col, w = _bad(kind)
+    csr = api.CSR.from_numpy(rowptr, col, w)
+    with pytest.raises(N.SpcError) as ei:
+        ctx.coarsen(csr, 5, levels=1)
+    assert ei.value.status == code
+    # the context stays usable
+    g = I.path_graph(5)
+    lift, nc, st = ctx.coarsen(api.CSR.from_graph(g), 2)
+    assert nc == 2
+
+
+def test_invalid_arguments(ctx):
+    api = _api()
+    from paper_2204_11757_gb300 import native as N
+    g = I.path_graph(5)
+    with pytest.raises(N.SpcError) as ei:
+        ctx.coarsen(api.CSR.from_graph(g), 0)
+    assert ei.value.status == -1
+
+
+def test_self_loop_reported(ctx):
+    api = _api()
+    from paper_2204_11757_gb300 import native as N
+    rowptr = np.array([0, 2, 3], dtype=np.int64)
+    col = np.array([0, 1, 0], dtype=np.int32)
+    w = np.ones(3, dtype=np.float64)
+    with pytest.raises(N.SpcError) as ei:
+        ctx.score(api.CSR.from_numpy(rowptr, col, w))
+    assert ei.value.status in (-3, -2)
+
+
+def test_contract_rejects_out_of_range_lift(ctx):
+    api = _api()
+    from paper_2204_11757_gb300 import native as N
+    g = I.path_graph(6)
+    bad = torch.tensor([0, 1, 2, 3, 4, 9], dtype=torch.int32, device="cuda")
+    with pytest.raises(N.SpcError) as ei:
+        ctx.contract(api.CSR.from_graph(g), bad, 5)
+    assert ei.value.status == -1
