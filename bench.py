@@ -1,0 +1,378 @@
+#!/usr/bin/env python
+"""Throughput of GB300 spectral-bound coarsening (M fine edges/s per coarsening level).
+
+One step = one full coarsening of the workload (every level: validation, degrees, normalised
+rows, scores, merge selection, relabel, contraction), inputs resident in HBM.  The default
+workload is the 2048x2048 jittered triangle mesh with FP64 1/length weights, coarsened by six
+halving levels to n/64.  value = (sum over levels of the fine edges that level processed) /
+(device time of a step).  Under torchrun each rank coarsens its own replica (the single-graph
+path does not shard), so value is the sum over ranks.
+
+--impl reference times the CPU oracle instead (test infrastructure, the only other use of it
+here), on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "M fine edges/s per coarsening level"
+UNIT = "M edges/s"
+
+WORKLOADS = {
+    # name: (config name, levels, description)
+    "c2_tri2048_f64": ("c2_tri2048_f64", 6, "2048x2048 jittered triangle mesh (4,194,304 nodes, "
+                       "12,574,721 edges), FP64 weights 1/edge-length, 6 halving levels to n/64"),
+    "c3_tet129_f64": ("c3_tet129_f64", 7, "129^3-vertex tetrahedral cube mesh (2,146,689 nodes, "
+                      "14,827,904 edges), FP64 1/edge-length, 7 halving levels to n/128"),
+    "c4_rgg8m_f32": ("c4_rgg8m_f32", 8, "random geometric graph, 2^23 points, mean degree 12, "
+                     "FP32 exp(-d^2/r^2), 8 halving levels to n/256"),
+    "c4_rgg8m_f32_one": ("c4_rgg8m_f32_one", 1, "random geometric graph, 2^23 points, mean "
+                         "degree 12, FP32 exp(-d^2/r^2), one level to n/256"),
+}
+# the CPU oracle's bounded sample: the same construction at a quarter of the side length
+SAMPLES = {
+    "c2_tri2048_f64": dict(kind="tri", nx=512, ny=512, jitter=0.3, weight="inv_len",
+                           dtype="float64", seed=2, ratio=64),
+    "c3_tet129_f64": dict(kind="tet", k=33, jitter=0.25, weight="inv_len", dtype="float64",
+                          seed=3, ratio=128),
+    "c4_rgg8m_f32": dict(kind="rgg", n=1 << 17, degree=12.0, dtype="float32", seed=4, ratio=256),
+    "c4_rgg8m_f32_one": dict(kind="rgg", n=1 << 17, degree=12.0, dtype="float32", seed=4,
+                             ratio=256, mode="one"),
+}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _sample_graph(spec):
+    from paper_2204_11757_gb300 import inputs as I
+    dt = np.dtype(spec["dtype"])
+    if spec["kind"] == "tri":
+        return I.tri_mesh_2d(spec["nx"], spec["ny"], spec["seed"], spec["jitter"], spec["weight"],
+                             dt)
+    if spec["kind"] == "tet":
+        return I.tet_mesh_3d(spec["k"], spec["seed"], spec["jitter"], spec["weight"], dt)
+    return I.rgg_3d(spec["n"], spec["degree"], spec["seed"], dt)
+
+
+def _oracle_step(g, spec):
+    """One oracle coarsening of the sample; returns (fine edges processed, seconds)."""
+    from oracle import oracle as O
+    t0 = time.perf_counter()
+    levels, _ = O.coarsen(g, spec["ratio"], spec.get("mode", "halving"))
+    dt = time.perf_counter() - t0
+    return sum(lv.f.shape[0] for lv in levels), dt
+
+
+def cpu_baseline(workload, budget_s=10.0):
+    spec = SAMPLES[workload]
+    g = _sample_graph(spec)
+    edges, dt, runs = 0, 0.0, 0
+    while dt < budget_s or runs == 0:
+        e, t = _oracle_step(g, spec)
+        edges += e
+        dt += t
+        runs += 1
+    return {"value": edges / dt / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"full {spec.get('mode', 'halving')} coarsening (ratio {spec['ratio']}) of "
+                      f"the same construction at reduced size: n={g.n}, m={g.m}; {runs} runs, "
+                      f"{dt:.1f} s single-threaded C"}
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    spec = SAMPLES[args.workload]
+    g = _sample_graph(spec)
+    for _ in range(args.warmup):
+        _oracle_step(g, spec)
+    times, edges = [], 0
+    for _ in range(args.steps):
+        e, dt = _oracle_step(g, spec)
+        edges += e
+        times.append(dt)
+    tot = sum(times)
+    value = edges / tot / 1e6
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": _dtype_of(spec),
+        "data": "synthetic",
+        "config": {"workload": args.workload, "sample_n": g.n, "sample_m": g.m},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{spec.get('mode', 'halving')} coarsening of the reduced "
+                                   f"construction (n={g.n}, m={g.m}) per step"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def _dtype_of(spec):
+    return {"float64": "f64", "float32": "f32", "int32": "i32"}[spec["dtype"]]
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-i", str(self.index), "-lms", "200"], stdout=open(self.path, "w"),
+                stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for nm, v in zip(names, r[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(rows)}
+
+
+# algorithmic bytes per launch of the kernels that can dominate a step
+def _score_bytes(n, m, s_p, s_f):
+    # eu/ev, rowptr, every row's columns and normalised weights once, the score write
+    return 8 * m + 8 * (n + 1) + 2 * m * (4 + s_p) + m * s_f
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["native", "reference"], default="native")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="c2_tri2048_f64")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile", action="store_true", help="print the per-kernel breakdown")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "native":
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import torch.distributed as dist
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+
+    import __graft_entry__ as ge
+    from paper_2204_11757_gb300 import api, inputs as I
+    if rank == 0:
+        ge.build()
+    if ws > 1:
+        dist.barrier()
+    cfg_name, L, desc = WORKLOADS[args.workload]
+    g, cfg = I.config_graph(cfg_name)
+    n_c = max(1, g.n // cfg["ratio"])
+    dev = torch.device("cuda", local)
+    csr = api.CSR.from_graph(g, dev)
+    ctx = api.Context(dev)
+    stream = ctx.stream
+    lift = torch.empty(g.n, dtype=torch.int32, device=dev)
+
+    def step():
+        ctx.coarsen(csr, n_c, levels=L, lift_out=lift)
+
+    for _ in range(args.warmup):
+        step()
+    levels = [ctx.level_info(l) for l in range(ctx.level_count())]
+    edges_per_step = sum(int(lv.m) for lv in levels)
+
+    # one profiled step: per-kernel device time, to find the dominant kernel
+    ctx.time_kernel("*")
+    step()
+    prof = ctx.kernel_profile()
+    step_prof_ms = sum(v[1] for v in prof.values())
+    dominant = max(prof.items(), key=lambda kv: kv[1][1])[0]
+
+    # ---- timed region ----------------------------------------------------------------------
+    sampler = ClockSampler(local)
+    if rank == 0:
+        sampler.start()
+        time.sleep(0.3)
+    ctx.time_kernel(dominant)
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    launches0 = ctx.launch_count
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    launches = ctx.launch_count - launches0
+    t_ms = ev0.elapsed_time(ev1) / args.steps
+    dom_launches, dom_ms = ctx.kernel_time()
+    ctx.time_kernel(None)
+    clocks = sampler.stop() if rank == 0 else None
+    level_ms = [float(ctx.level_info(l).ms) for l in range(len(levels))]
+    if ws > 1:
+        t = torch.tensor([t_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_ms = float(t.item())
+    value = ws * edges_per_step / (t_ms * 1e-3) / 1e6
+
+    # ---- roofline of the dominant kernel --------------------------------------------------------
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    s_p = 4 if g.w.dtype == np.float32 else 8
+    roof = None
+    if dominant.startswith("(k_score") or dominant.startswith("k_score"):
+        per_step = sum(_score_bytes(int(lv.n), int(lv.m), s_p, s_p) for lv in levels)
+        achieved = per_step * (dom_launches / max(1, len(levels))) / (dom_ms * 1e-3) / 1e9
+        roof = {"kernel": dominant, "bound": "hbm", "achieved": achieved, "peak": hbm,
+                "unit": "GB/s", "frac": achieved / hbm, "traffic": None,
+                "peak_source": "measured" if peaks else "fallback",
+                "launches": dom_launches, "avg_launch_ms": dom_ms / max(1, dom_launches)}
+    else:
+        roof = {"kernel": dominant, "bound": "hbm", "achieved": None, "peak": hbm, "unit": "GB/s",
+                "frac": None, "traffic": None, "launches": dom_launches,
+                "avg_launch_ms": dom_ms / max(1, dom_launches)}
+
+    # ---- end to end through host buffers -----------------------------------------------------------
+    e2e = None
+    if not args.no_e2e:
+        host = api.CSR.from_graph(g, device="cpu", pin=True)
+        lift_h = torch.empty(g.n, dtype=torch.int32).pin_memory()
+        last = levels[-1]
+        bufs = None
+
+        def e2e_step():
+            nonlocal bufs
+            ctx.coarsen(host, n_c, levels=L, lift_out=lift_h)
+            info = ctx.level_info(ctx.level_count() - 1)
+            if bufs is None or bufs[1].shape[0] < 2 * info.m_c:
+                bufs = (torch.empty(info.n_c + 1, dtype=torch.int64).pin_memory(),
+                        torch.empty(2 * info.m_c, dtype=torch.int32).pin_memory(),
+                        torch.empty(2 * info.m_c, dtype=csr.w.dtype).pin_memory())
+            for dst, src in zip(bufs, (info.rowptr_c, info.col_c, info.w_c)):
+                ctx.lib.spc_copy(ctx._handle, api._ptr(dst), src, dst.numel() * dst.element_size())
+            return info
+
+        info = e2e_step()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        ksteps = max(1, min(args.steps, 5))
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(ksteps):
+            info = e2e_step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        e_ms = e0.elapsed_time(e1) / ksteps
+        h2d = host.rowptr.numel() * 8 + host.col.numel() * 4 + host.w.numel() * host.w.element_size()
+        d2h = g.n * 4 + (info.n_c + 1) * 8 + 2 * info.m_c * (4 + csr.w.element_size())
+        e2e = {"value": ws * edges_per_step / (e_ms * 1e-3) / 1e6, "unit": UNIT,
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+               "ms_per_step": e_ms}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(args.workload)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": {np.dtype("float64"): "f64", np.dtype("float32"): "f32",
+                      np.dtype("int32"): "i32"}[g.w.dtype],
+            "data": "synthetic",
+            "config": {
+                "workload": f"{args.workload}: {desc}",
+                "n": g.n, "m": g.m, "n_c": n_c, "levels": L,
+                "parallelism": "replicas" if ws > 1 else "single GPU",
+                "l2": "inputs larger than L2 (%.0f MB resident CSR)" % (
+                    (csr.rowptr.numel() * 8 + csr.col.numel() * 4
+                     + csr.w.numel() * csr.w.element_size()) / 1e6),
+                "per_level": [{"n": int(lv.n), "m": int(lv.m), "n_c": int(lv.n_c),
+                               "m_c": int(lv.m_c), "ms": ms,
+                               "M_edges_s": (int(lv.m) / (ms * 1e-3) / 1e6) if ms > 0 else None}
+                              for lv, ms in zip(levels, level_ms)],
+            },
+            "roofline": roof,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "clocks": clocks,
+            "gpu_launches": int(launches),
+        }
+        if args.profile:
+            line["kernel_profile_ms"] = {k: round(v[1], 4) for k, v in
+                                         sorted(prof.items(), key=lambda kv: -kv[1][1])}
+            line["profiled_step_ms"] = step_prof_ms
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if ws > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -227,10 +227,15 @@ SPC_API spc_status spc_compose_emap(spc_context* ctx, int32_t* emap_out);
 /* ---- timing ------------------------------------------------------------------------------- */
 
 /* Record CUDA events around every launch of the kernels whose name contains `kernel_substr`
- * (NULL or "" switches it off); spc_kernel_time returns the launches seen and their summed
+ * ("*": every kernel; NULL or "" switches it off); spc_kernel_time returns the launches seen and their summed
  * device time since the last call to spc_time_kernel. */
 SPC_API spc_status spc_time_kernel(spc_context* ctx, const char* kernel_substr);
 SPC_API spc_status spc_kernel_time(spc_context* ctx, int64_t* launches, double* total_ms);
+
+/* Per-kernel breakdown of the timed launches since the last spc_time_kernel: one line per
+ * kernel, "name<TAB>launches<TAB>total_ms<LF>", NUL-terminated in buf[len].  Returns
+ * SPC_ERR_INVALID_ARG (with the text truncated) if len is too small. */
+SPC_API spc_status spc_kernel_profile(spc_context* ctx, char* buf, size_t len);
 
 /* Number of kernel launches issued by the context since it was created (replayed graph
  * launches count their kernel nodes). */

@@ -281,6 +281,16 @@ class Context:
                 "spc_kernel_time")
         return int(n.value), float(ms.value)
 
+    def kernel_profile(self):
+        """{kernel name: (launches, total ms)} for the launches timed since time_kernel()."""
+        buf = ctypes.create_string_buffer(1 << 16)
+        N.check(self.lib.spc_kernel_profile(self._handle, buf, len(buf)), "spc_kernel_profile")
+        out = {}
+        for line in buf.value.decode().splitlines():
+            name, cnt, ms = line.split("\t")
+            out[name] = (int(cnt), float(ms))
+        return out
+
     @property
     def launch_count(self) -> int:
         return int(self.lib.spc_launch_count(self._handle))

@@ -81,10 +81,14 @@ void free_all(spc_context* ctx) {
     while (!ctx->blocks.empty()) raw_free(ctx, ctx->blocks.back().p);
 }
 
+static bool timed(const Timer& t, const char* name) {
+    return t.on && (t.substr == "*" || strstr(name, t.substr.c_str()) != nullptr);
+}
+
 void before_launch(spc_context* ctx, const char* name) {
     Timer& t = ctx->timer;
     ctx->launches += 1;
-    if (!t.on || !strstr(name, t.substr.c_str())) return;
+    if (!timed(t, name)) return;
     cudaEvent_t a, b;
     if (t.pool.size() >= 2) {
         a = t.pool.back(); t.pool.pop_back();
@@ -94,13 +98,13 @@ void before_launch(spc_context* ctx, const char* name) {
         cudaEventCreate(&b);
     }
     cudaEventRecord(a, ctx->stream);
-    t.pending.push_back({a, b});
+    t.pending.push_back({name, a, b});
 }
 
 void after_launch(spc_context* ctx, const char* name) {
     Timer& t = ctx->timer;
-    if (!t.on || !strstr(name, t.substr.c_str())) return;
-    cudaEventRecord(t.pending.back().second, ctx->stream);
+    if (!timed(t, name)) return;
+    cudaEventRecord(t.pending.back().b, ctx->stream);
 }
 
 spc_status sync_status(spc_context* ctx) {
@@ -491,8 +495,8 @@ void spc_context_destroy(spc_context* ctx) {
         if (lv.ev1) cudaEventDestroy(lv.ev1);
     }
     for (auto& pr : ctx->timer.pending) {
-        cudaEventDestroy(pr.first);
-        cudaEventDestroy(pr.second);
+        cudaEventDestroy(pr.a);
+        cudaEventDestroy(pr.b);
     }
     for (auto ev : ctx->timer.pool) cudaEventDestroy(ev);
     cudaFree(ctx->d_status);
@@ -739,10 +743,11 @@ spc_status spc_time_kernel(spc_context* ctx, const char* kernel_substr) {
     Timer& t = ctx->timer;
     SPC_CUDA(cudaStreamSynchronize(ctx->stream));
     for (auto& pr : t.pending) {
-        t.pool.push_back(pr.first);
-        t.pool.push_back(pr.second);
+        t.pool.push_back(pr.a);
+        t.pool.push_back(pr.b);
     }
     t.pending.clear();
+    t.per_kernel.clear();
     t.launches = 0;
     t.total_ms = 0.0;
     t.on = kernel_substr && kernel_substr[0];
@@ -750,22 +755,55 @@ spc_status spc_time_kernel(spc_context* ctx, const char* kernel_substr) {
     return SPC_OK;
 }
 
-spc_status spc_kernel_time(spc_context* ctx, int64_t* launches, double* total_ms) {
-    if (!ctx) return SPC_ERR_INVALID_ARG;
+static spc_status drain_timer(spc_context* ctx) {
     Timer& t = ctx->timer;
     SPC_CUDA(cudaStreamSynchronize(ctx->stream));
     for (auto& pr : t.pending) {
         float ms = 0.f;
-        SPC_CUDA(cudaEventElapsedTime(&ms, pr.first, pr.second));
+        SPC_CUDA(cudaEventElapsedTime(&ms, pr.a, pr.b));
         t.total_ms += ms;
         t.launches += 1;
-        t.pool.push_back(pr.first);
-        t.pool.push_back(pr.second);
+        bool found = false;
+        for (auto& pk : t.per_kernel) {
+            if (pk.first == pr.name) {
+                pk.second.first += 1;
+                pk.second.second += ms;
+                found = true;
+                break;
+            }
+        }
+        if (!found) t.per_kernel.push_back({std::string(pr.name), {1, (double)ms}});
+        t.pool.push_back(pr.a);
+        t.pool.push_back(pr.b);
     }
     t.pending.clear();
-    if (launches) *launches = t.launches;
-    if (total_ms) *total_ms = t.total_ms;
     return SPC_OK;
+}
+
+spc_status spc_kernel_time(spc_context* ctx, int64_t* launches, double* total_ms) {
+    if (!ctx) return SPC_ERR_INVALID_ARG;
+    SPC_TRY(drain_timer(ctx));
+    if (launches) *launches = ctx->timer.launches;
+    if (total_ms) *total_ms = ctx->timer.total_ms;
+    return SPC_OK;
+}
+
+spc_status spc_kernel_profile(spc_context* ctx, char* buf, size_t len) {
+    if (!ctx || (!buf && len)) return SPC_ERR_INVALID_ARG;
+    SPC_TRY(drain_timer(ctx));
+    std::string out;
+    char line[512];
+    for (auto& pk : ctx->timer.per_kernel) {
+        snprintf(line, sizeof(line), "%s\t%lld\t%.6f\n", pk.first.c_str(),
+                 (long long)pk.second.first, pk.second.second);
+        out += line;
+    }
+    if (len) {
+        size_t k = out.size() < len - 1 ? out.size() : len - 1;
+        memcpy(buf, out.data(), k);
+        buf[k] = 0;
+    }
+    return out.size() < len ? SPC_OK : SPC_ERR_INVALID_ARG;
 }
 
 int64_t spc_launch_count(const spc_context* ctx) { return ctx ? ctx->launches : 0; }

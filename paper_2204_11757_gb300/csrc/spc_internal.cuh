@@ -86,12 +86,17 @@ struct Work {
 };
 
 struct Timer {
-    std::string substr;
+    std::string substr;      // kernels whose name contains it are timed; "*" times every kernel
     bool on = false;
     int64_t launches = 0;
     double total_ms = 0.0;
-    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending;
+    struct Pending {
+        const char* name;
+        cudaEvent_t a, b;
+    };
+    std::vector<Pending> pending;
     std::vector<cudaEvent_t> pool;
+    std::vector<std::pair<std::string, std::pair<int64_t, double>>> per_kernel;
 };
 
 }  // namespace spc
