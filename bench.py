@@ -42,6 +42,9 @@ WORKLOADS = {
                      "FP32 exp(-d^2/r^2), 8 halving levels to n/256"),
     "c4_rgg8m_f32_one": ("c4_rgg8m_f32_one", 1, "random geometric graph, 2^23 points, mean "
                          "degree 12, FP32 exp(-d^2/r^2), one level to n/256"),
+    # reduced case of the same construction, for profiler captures that must stay small
+    "p2_tri512_f64": ("p2_tri512_f64", 6, "512x512 jittered triangle mesh (262,144 nodes, "
+                      "784,385 edges), FP64 1/edge-length, 6 halving levels to n/64"),
 }
 # the CPU oracle's bounded sample: the same construction at a quarter of the side length
 SAMPLES = {
@@ -52,6 +55,8 @@ SAMPLES = {
     "c4_rgg8m_f32": dict(kind="rgg", n=1 << 17, degree=12.0, dtype="float32", seed=4, ratio=256),
     "c4_rgg8m_f32_one": dict(kind="rgg", n=1 << 17, degree=12.0, dtype="float32", seed=4,
                              ratio=256, mode="one"),
+    "p2_tri512_f64": dict(kind="tri", nx=256, ny=256, jitter=0.3, weight="inv_len",
+                          dtype="float64", seed=12, ratio=64),
 }
 
 

@@ -193,6 +193,12 @@ static spc_status reserve_work(spc_context* ctx, int64_t n, int64_t m, int64_t B
     SPC_TRY(ensure(ctx, W.w_und, M * 8));
     SPC_TRY(ensure(ctx, W.deg, N * 8));
     SPC_TRY(ensure(ctx, W.p, 2 * M * 8));
+    SPC_TRY(ensure(ctx, W.long_rows, N * 4));
+    SPC_TRY(ensure(ctx, W.hub_eblo, N * 4));
+    SPC_TRY(ensure(ctx, W.hub_size, N * 8));
+    SPC_TRY(ensure(ctx, W.hub_deg, N * 8));
+    SPC_TRY(ensure(ctx, W.hub_off, (N + 1) * 8));
+    SPC_TRY(ensure(ctx, W.hub_eoff, (N + 1) * 8));
     SPC_TRY(ensure(ctx, W.parent, N * 4));
     for (int i = 0; i < 2; ++i) {
         SPC_TRY(ensure(ctx, W.best_k[i], N * 8));
@@ -232,8 +238,9 @@ static spc_status reserve_work(spc_context* ctx, int64_t n, int64_t m, int64_t B
     SPC_TRY(ensure(ctx, W.lstart, (N + 1) * 4));
     SPC_TRY(ensure(ctx, W.i_key, M * 4));
     SPC_TRY(ensure(ctx, W.i_val, M * 4));
-    SPC_TRY(ensure(ctx, W.i_key2, M * 4));
-    SPC_TRY(ensure(ctx, W.i_val2, M * 4));
+    SPC_TRY(ensure(ctx, W.i_key2, (M + 1) * 4));
+    SPC_TRY(ensure(ctx, W.i_val2, (M + 1) * 4));
+    SPC_TRY(ensure(ctx, W.long_segs, (M + 1) * 4));
     // scan of up to max(n, m, 256 * tiles) items -> tile sums; radix histograms
     const size_t big = (N > M ? N : M) + 256 * ((M + 4095) / 4096) + 4096;
     SPC_TRY(ensure(ctx, W.scan_tmp, (big / 4096 + 4) * 8 + 256));

@@ -12,7 +12,7 @@
 // coarse-edge order), which leaves every row sorted.
 #include <type_traits>
 
-#include "spc_internal.cuh"
+#include "spc_seqsum.cuh"
 
 namespace spc {
 
@@ -72,8 +72,9 @@ __global__ void k_set_i32(int32_t* p, int32_t v) {
     if (threadIdx.x == 0) *p = v;
 }
 
+template <class K>
 __global__ void __launch_bounds__(kThreads)
-k_heads(int64_t cnt, const uint64_t* __restrict__ key, uint8_t* __restrict__ head) {
+k_heads(int64_t cnt, const K* __restrict__ key, uint8_t* __restrict__ head) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cnt;
          i += (int64_t)gridDim.x * blockDim.x)
         head[i] = (i == 0 || key[i] != key[i - 1]) ? 1 : 0;
@@ -101,34 +102,65 @@ k_emit_segments(int64_t cnt, int nb, const uint64_t* __restrict__ key,
     }
 }
 
-// a_und[k] = sum of w_und over perm[seg[k] .. seg[k+1]) in order
-template <class WT>
+// run r of a sorted key array starts at start[r]; start[n_runs] = cnt
 __global__ void __launch_bounds__(kThreads)
-k_segment_sums(int64_t m_c, const int32_t* __restrict__ seg, const int32_t* __restrict__ perm,
-               const WT* __restrict__ w_und, WT* __restrict__ a_und, uint32_t* status) {
-    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < m_c;
-         k += (int64_t)gridDim.x * blockDim.x) {
-        typename CT<WT>::Acc s = 0;
-        for (int32_t j = seg[k]; j < seg[k + 1]; ++j) s = CT<WT>::add(s, w_und[perm[j]]);
-        if constexpr (std::is_same<WT, int32_t>::value) {
-            if (s > 2147483647ll) atomicOr(status, DEV_OVERFLOW);
-        }
-        a_und[k] = (WT)s;
+k_run_starts(int64_t cnt, const uint8_t* __restrict__ head, const int32_t* __restrict__ hpos,
+             int32_t* __restrict__ start) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cnt;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        if (head[i]) start[hpos[i]] = (int32_t)i;
+        if (i == cnt - 1) start[hpos[i] + head[i]] = (int32_t)cnt;
     }
 }
 
-// self-mass: the head of every run of equal super-node ids sums its run in order
-template <class WT>
+// Segment sums: out[slot(r)] = sum of w_und[idx[j]] for j in [start[r], start[r+1]), left to
+// right.  slot(r) = r, or key[start[r]] when `key` is given (self-mass by super-node).  Short
+// segments: one thread each; segments longer than kLongRow go to a list for k_segsum_long.
+template <class WT, class Out>
 __global__ void __launch_bounds__(kThreads)
-k_self_mass(int64_t cnt, const uint32_t* __restrict__ ikey, const uint32_t* __restrict__ ival,
-            const WT* __restrict__ w_und, typename CT<WT>::Acc* __restrict__ self_mass) {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cnt;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const uint32_t U = ikey[i];
-        if (i > 0 && ikey[i - 1] == U) continue;
+k_segsum_short(int64_t nseg, const int32_t* __restrict__ start, const uint32_t* __restrict__ idx,
+               const uint32_t* __restrict__ key, const WT* __restrict__ w_und, Out* __restrict__ out,
+               int32_t* __restrict__ long_list, int32_t* __restrict__ long_count,
+               uint32_t* status) {
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < nseg;
+         r += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t j0 = start[r], j1 = start[r + 1];
+        if (j1 - j0 > kLongRow) {
+            long_list[atomicAdd(long_count, 1)] = (int32_t)r;
+            continue;
+        }
         typename CT<WT>::Acc s = 0;
-        for (int64_t j = i; j < cnt && ikey[j] == U; ++j) s = CT<WT>::add(s, w_und[ival[j]]);
-        self_mass[U] = s;
+        for (int32_t j = j0; j < j1; ++j) s = CT<WT>::add(s, w_und[idx[j]]);
+        if constexpr (std::is_same<WT, int32_t>::value && sizeof(Out) == 4) {
+            if (s > 2147483647ll) atomicOr(status, DEV_OVERFLOW);
+        }
+        out[key ? (int64_t)key[j0] : r] = (Out)s;
+    }
+}
+
+template <class WT, class Out>
+__global__ void __launch_bounds__(kThreads)
+k_segsum_long(const int32_t* __restrict__ start, const uint32_t* __restrict__ idx,
+              const uint32_t* __restrict__ key, const WT* __restrict__ w_und, Out* __restrict__ out,
+              const int32_t* __restrict__ long_list, const int32_t* __restrict__ long_count,
+              uint32_t* status) {
+    const int32_t cnt = *long_count;
+    for (int32_t q = blockIdx.x; q < cnt; q += gridDim.x) {
+        const int64_t r = long_list[q];
+        const int32_t j0 = start[r], j1 = start[r + 1];
+        typename CT<WT>::Acc s;
+        if constexpr (std::is_same<WT, int32_t>::value) {
+            s = cta_sum_i64(j1 - j0, [&](int64_t k) { return (long long)w_und[idx[j0 + k]]; });
+        } else {
+            s = cta_seqsum<8>(WT(0), j1 - j0, [&](int64_t k) { return w_und[idx[j0 + k]]; });
+        }
+        if (threadIdx.x == 0) {
+            if constexpr (std::is_same<WT, int32_t>::value && sizeof(Out) == 4) {
+                if (s > 2147483647ll) atomicOr(status, DEV_OVERFLOW);
+            }
+            out[key ? (int64_t)key[j0] : r] = (Out)s;
+        }
+        __syncthreads();
     }
 }
 
@@ -233,14 +265,32 @@ spc_status contract_typed(spc_context* ctx, const GraphView& g, const int32_t* l
     SPC_CUDA(cudaStreamSynchronize(ctx->stream));
     const int64_t m_inter = reinterpret_cast<int32_t*>(ctx->h_scalars)[0];
     const int64_t m_intra = reinterpret_cast<int32_t*>(ctx->h_scalars)[1];
-    // self-mass
+    // self-mass: runs of equal super-node ids after a stable sort, summed in eid order
     Acc* self_mass = lv.self_mass.as<Acc>();
     SPC_CUDA(cudaMemsetAsync(self_mass, 0, (size_t)n_c * sizeof(Acc), ctx->stream));
     SPC_TRY(radix_sort_u32(ctx, ikey, ival, W.i_key2.as<uint32_t>(), W.i_val2.as<uint32_t>(),
                            m_intra, nb));
+    int32_t* long_list = W.long_segs.as<int32_t>();
+    int32_t* long_cnt = W.counters.as<int32_t>() + 9;
+    const int persist = ctx->num_sms * 2;
     if (m_intra > 0) {
-        SPC_LAUNCH(ctx, k_self_mass<WT>, grid_for(m_intra, kThreads, maxb), kThreads, 0,
-                   m_intra, ikey, ival, W.w_und.as<WT>(), self_mass);
+        uint8_t* ihead = W.c_flag.as<uint8_t>() + (m + 1);  // intra flags are consumed
+        int32_t* ihpos = W.c_head.as<int32_t>();
+        int32_t* istart = W.i_key2.as<int32_t>();           // sort scratch is free again
+        const int gi = grid_for(m_intra, kThreads, maxb);
+        SPC_LAUNCH(ctx, k_heads<uint32_t>, gi, kThreads, 0, m_intra, ikey, ihead);
+        SPC_TRY(scan_flags_u8(ctx, ihead, ihpos, m_intra));
+        SPC_LAUNCH(ctx, k_run_starts, gi, kThreads, 0, m_intra, ihead, ihpos, istart);
+        SPC_CUDA(cudaMemcpyAsync(ctx->h_scalars, ihpos + m_intra, sizeof(int32_t),
+                                 cudaMemcpyDeviceToHost, ctx->stream));
+        SPC_CUDA(cudaMemsetAsync(long_cnt, 0, sizeof(int32_t), ctx->stream));
+        SPC_CUDA(cudaStreamSynchronize(ctx->stream));
+        const int64_t n_runs = reinterpret_cast<int32_t*>(ctx->h_scalars)[0];
+        SPC_LAUNCH(ctx, (k_segsum_short<WT, Acc>), grid_for(n_runs, kThreads, maxb), kThreads, 0,
+                   n_runs, istart, ival, ikey, W.w_und.as<WT>(), self_mass, long_list, long_cnt,
+                   status);
+        SPC_LAUNCH(ctx, (k_segsum_long<WT, Acc>), persist, kThreads, 0, istart, ival, ikey,
+                   W.w_und.as<WT>(), self_mass, long_list, long_cnt, status);
     }
     // coarse edges
     SPC_TRY(radix_sort_u64(ctx, ckey, cval, W.c_key2.as<uint64_t>(), W.c_val2.as<uint32_t>(),
@@ -254,7 +304,7 @@ spc_status contract_typed(spc_context* ctx, const GraphView& g, const int32_t* l
     int64_t m_c = 0;
     if (m_inter > 0) {
         const int gi = grid_for(m_inter, kThreads, maxb);
-        SPC_LAUNCH(ctx, k_heads, gi, kThreads, 0, m_inter, ckey, head);
+        SPC_LAUNCH(ctx, k_heads<uint64_t>, gi, kThreads, 0, m_inter, ckey, head);
         SPC_TRY(scan_flags_u8(ctx, head, hpos, m_inter));
         SPC_LAUNCH(ctx, k_emit_segments, gi, kThreads, 0, m_inter, nb, ckey, cval, head, hpos,
                    emap, perm, seg, cU, cV);
@@ -266,8 +316,13 @@ spc_status contract_typed(spc_context* ctx, const GraphView& g, const int32_t* l
     SPC_LAUNCH(ctx, k_set_i32, 1, 32, 0, seg + m_c, (int32_t)m_inter);
     WT* a_und = lv.a_und.as<WT>();
     if (m_c > 0) {
-        SPC_LAUNCH(ctx, k_segment_sums<WT>, grid_for(m_c, kThreads, maxb), kThreads, 0, m_c,
-                   seg, perm, W.w_und.as<WT>(), a_und, status);
+        SPC_CUDA(cudaMemsetAsync(long_cnt, 0, sizeof(int32_t), ctx->stream));
+        SPC_LAUNCH(ctx, (k_segsum_short<WT, WT>), grid_for(m_c, kThreads, maxb), kThreads, 0,
+                   m_c, seg, reinterpret_cast<const uint32_t*>(perm), nullptr, W.w_und.as<WT>(),
+                   a_und, long_list, long_cnt, status);
+        SPC_LAUNCH(ctx, (k_segsum_long<WT, WT>), persist, kThreads, 0, seg,
+                   reinterpret_cast<const uint32_t*>(perm), nullptr, W.w_und.as<WT>(), a_und,
+                   long_list, long_cnt, status);
     }
     // coarse CSR
     int32_t* up_deg = W.up_deg.as<int32_t>();
@@ -305,8 +360,17 @@ template <class WT>
 spc_status forward_typed(spc_context* ctx, const int32_t* perm, const int32_t* seg, int64_t m_c,
                          const WT* w_und, WT* a_und) {
     if (m_c <= 0) return SPC_OK;
-    SPC_LAUNCH(ctx, k_segment_sums<WT>, grid_for(m_c, kThreads, ctx->num_sms * 8), kThreads, 0,
-               m_c, seg, perm, w_und, a_und, ctx->d_status);
+    SPC_TRY(ensure(ctx, ctx->work.long_segs, (size_t)(m_c + 1) * 4));
+    SPC_TRY(ensure(ctx, ctx->work.counters, 64 * 4));
+    int32_t* long_list = ctx->work.long_segs.as<int32_t>();
+    int32_t* long_cnt = ctx->work.counters.as<int32_t>() + 9;
+    SPC_CUDA(cudaMemsetAsync(long_cnt, 0, sizeof(int32_t), ctx->stream));
+    SPC_LAUNCH(ctx, (k_segsum_short<WT, WT>), grid_for(m_c, kThreads, ctx->num_sms * 8), kThreads,
+               0, m_c, seg, reinterpret_cast<const uint32_t*>(perm), nullptr, w_und, a_und,
+               long_list, long_cnt, ctx->d_status);
+    SPC_LAUNCH(ctx, (k_segsum_long<WT, WT>), ctx->num_sms * 2, kThreads, 0, seg,
+               reinterpret_cast<const uint32_t*>(perm), nullptr, w_und, a_und, long_list,
+               long_cnt, ctx->d_status);
     return SPC_OK;
 }
 

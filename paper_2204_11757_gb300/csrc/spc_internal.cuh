@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/spcoarsen.h"
@@ -74,13 +75,14 @@ struct LevelBufs {
 // Work buffers shared by all levels (sized for level 0).
 struct Work {
     Buf up_cnt, up_ptr, first_up, eu, ev, w_und, deg, p;       // S0-S2
+    Buf long_rows, hub_eblo, hub_size, hub_deg, hub_off, hub_eoff, tab_p, tab_t;  // hub rows
     Buf parent, best_k[2], best_e[2], wl_e[2], wl_u[2], wl_v[2], msf;   // S5 MSF
     Buf counters;                                               // small device ints
     Buf sel_key, sel_val, sel_key2, sel_val2, node_graph, seg_start, k_graph;  // selection
     Buf parent2, flag, ids;                                     // S6
     Buf c_key, c_val, c_key2, c_val2, c_flag, c_pos, c_head, cU, cV;    // S7
     Buf t_key, t_val, t_key2, t_val2, up_deg, low_deg, deg_c, ufirst, lstart;
-    Buf i_key, i_val, i_key2, i_val2;                           // intra edges (self-mass)
+    Buf i_key, i_val, i_key2, i_val2, long_segs;                // intra edges (self-mass)
     Buf sort_hist, scan_tmp;                                    // sort / scan temporaries
     Buf stage_rowptr, stage_col, stage_w, stage_lift, stage_gptr;  // host staging
 };
@@ -153,6 +155,8 @@ inline int grid_for(int64_t items, int threads, int max_blocks) {
 spc_status scan_i32(spc_context* ctx, const int32_t* in, int32_t* out, int64_t n);
 // Same for int64 (out int64).
 spc_status scan_i64(spc_context* ctx, const int32_t* in, int64_t* out, int64_t n);
+// Same for int64 input.
+spc_status scan_i64_i64(spc_context* ctx, const int64_t* in, int64_t* out, int64_t n);
 // Exclusive scan of 0/1 bytes into int32 positions, out[n] = total.
 spc_status scan_flags_u8(spc_context* ctx, const uint8_t* in, int32_t* out, int64_t n);
 

@@ -147,6 +147,10 @@ spc_status scan_i64(spc_context* ctx, const int32_t* in, int64_t* out, int64_t n
     return scan_impl<int32_t, int64_t, int64_t>(ctx, in, out, n);
 }
 
+spc_status scan_i64_i64(spc_context* ctx, const int64_t* in, int64_t* out, int64_t n) {
+    return scan_impl<int64_t, int64_t, int64_t>(ctx, in, out, n);
+}
+
 spc_status scan_flags_u8(spc_context* ctx, const uint8_t* in, int32_t* out, int64_t n) {
     return scan_impl<uint8_t, int32_t, int32_t>(ctx, in, out, n);
 }

@@ -6,7 +6,7 @@
 // Every sum here runs sequentially in ascending column order with IEEE round-to-nearest adds
 // (__dadd_rn / __fadd_rn, no FMA), and p = w / d is one IEEE division per stored entry, so
 // the results are the same bits on every run and every schedule.
-#include "spc_internal.cuh"
+#include "spc_seqsum.cuh"
 
 namespace spc {
 
@@ -55,7 +55,8 @@ __global__ void __launch_bounds__(kThreads)
 k_rows_degree(int64_t n, int64_t nnz, const int64_t* __restrict__ rowptr,
               const int32_t* __restrict__ col, const WT* __restrict__ w, int validate,
               typename Tr<WT>::Acc* __restrict__ deg, int32_t* __restrict__ up_cnt,
-              int32_t* __restrict__ nlow_out, uint32_t* __restrict__ status) {
+              int32_t* __restrict__ nlow_out, int32_t* __restrict__ long_rows,
+              int32_t* __restrict__ long_count, uint32_t* __restrict__ status) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     if (validate && blockIdx.x == 0 && threadIdx.x == 0) {
         if (rowptr[0] != 0 || rowptr[n] != nnz) atomicOr(status, DEV_UNSORTED);
@@ -68,6 +69,10 @@ k_rows_degree(int64_t n, int64_t nnz, const int64_t* __restrict__ rowptr,
             deg[x] = 0;
             up_cnt[x] = 0;
             nlow_out[x] = 0;
+            continue;
+        }
+        if (r1 - r0 > kLongRow) {  // a whole CTA takes it (k_long_rows_degree)
+            long_rows[atomicAdd(long_count, 1)] = (int32_t)x;
             continue;
         }
         typename Tr<WT>::Acc acc = 0;
@@ -92,6 +97,95 @@ k_rows_degree(int64_t n, int64_t nnz, const int64_t* __restrict__ rowptr,
     }
 }
 
+// S0 + S1 for rows longer than kLongRow: one CTA per row.  The checks and the counts run over
+// the entries in parallel; the degree is the same left-to-right sum, evaluated exactly by
+// cta_seqsum (or an int64 reduction for integer weights).
+template <class WT>
+__global__ void __launch_bounds__(kThreads)
+k_long_rows_degree(int64_t n, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                   const WT* __restrict__ w, int validate, const int32_t* __restrict__ long_rows,
+                   const int32_t* __restrict__ long_count,
+                   typename Tr<WT>::Acc* __restrict__ deg, int32_t* __restrict__ up_cnt,
+                   int32_t* __restrict__ nlow_out, uint32_t* __restrict__ status) {
+    __shared__ int32_t sh_nlow;
+    const int32_t cnt = *long_count;
+    for (int32_t i = blockIdx.x; i < cnt; i += gridDim.x) {
+        const int64_t x = long_rows[i];
+        const int64_t r0 = rowptr[x], r1 = rowptr[x + 1];
+        if (threadIdx.x == 0) sh_nlow = 0;
+        __syncthreads();
+        uint32_t bits = 0;
+        int32_t nl = 0;
+        for (int64_t j = r0 + threadIdx.x; j < r1; j += blockDim.x) {
+            const int32_t y = col[j];
+            if (validate) {
+                if (y < 0 || (int64_t)y >= n || (j > r0 && col[j - 1] >= y)) bits |= DEV_UNSORTED;
+                if ((int64_t)y == x) bits |= DEV_SELF_LOOP;
+                if (!Tr<WT>::ok(w[j])) bits |= DEV_BAD_WEIGHT;
+            }
+            nl += ((int64_t)y < x) ? 1 : 0;
+        }
+        if (bits) atomicOr(status, bits);
+        if (nl) atomicAdd(&sh_nlow, nl);
+        typename Tr<WT>::Acc d;
+        if constexpr (std::is_same<WT, int32_t>::value) {
+            d = cta_sum_i64(r1 - r0, [&](int64_t k) { return (long long)w[r0 + k]; });
+        } else {
+            d = cta_seqsum<8>(WT(0), r1 - r0, [&](int64_t k) { return w[r0 + k]; });
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            deg[x] = d;
+            nlow_out[x] = sh_nlow;
+            up_cnt[x] = (int32_t)(r1 - r0) - sh_nlow;
+        }
+        __syncthreads();
+    }
+}
+
+// S2 + edge list for rows longer than kLongRow: one CTA per row, threads over the entries.
+template <class WT>
+__global__ void __launch_bounds__(kThreads)
+k_long_rows_edges(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                  const WT* __restrict__ w, int validate,
+                  const typename Tr<WT>::Acc* __restrict__ deg, const int32_t* __restrict__ nlow,
+                  const int32_t* __restrict__ up_ptr, const int32_t* __restrict__ long_rows,
+                  const int32_t* __restrict__ long_count, typename Tr<WT>::P* __restrict__ p,
+                  int32_t* __restrict__ eu, int32_t* __restrict__ ev, WT* __restrict__ w_und,
+                  uint32_t* __restrict__ status) {
+    if (*status) return;
+    const int32_t cnt = *long_count;
+    for (int32_t i = blockIdx.x; i < cnt; i += gridDim.x) {
+        const int64_t x = long_rows[i];
+        const int64_t r0 = rowptr[x], r1 = rowptr[x + 1];
+        const typename Tr<WT>::Acc d = deg[x];
+        const int64_t ubase = (int64_t)up_ptr[x] - (r0 + nlow[x]);
+        uint32_t bits = 0;
+        for (int64_t j = r0 + threadIdx.x; j < r1; j += blockDim.x) {
+            const int32_t y = col[j];
+            const WT wj = w[j];
+            p[j] = Tr<WT>::div(wj, d);
+            if (validate) {
+                int64_t lo = rowptr[y], hi = rowptr[y + 1];
+                while (lo < hi) {
+                    int64_t mid = (lo + hi) >> 1;
+                    if ((int64_t)col[mid] < x) lo = mid + 1; else hi = mid;
+                }
+                if (lo >= rowptr[y + 1] || (int64_t)col[lo] != x ||
+                    Tr<WT>::bits(w[lo]) != Tr<WT>::bits(wj))
+                    bits |= DEV_NOT_SYMMETRIC;
+            }
+            if ((int64_t)y > x) {
+                const int64_t e = ubase + j;
+                eu[e] = (int32_t)x;
+                ev[e] = y;
+                w_und[e] = wj;
+            }
+        }
+        if (bits) atomicOr(status, bits);
+    }
+}
+
 // S2 (+ the edge list): one thread per row.  p[j] = w[j] / d[x]; for the entries above the
 // diagonal writes the undirected edge (x, y) at its edge id; when `validate`, looks up the
 // mirror entry (y, x) by binary search and compares the weight bits.
@@ -106,6 +200,7 @@ k_rows_edges(int64_t n, const int64_t* __restrict__ rowptr, const int32_t* __res
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n; x += stride) {
         const int64_t r0 = rowptr[x], r1 = rowptr[x + 1];
+        if (r1 - r0 > kLongRow) continue;  // k_long_rows_edges
         const typename Tr<WT>::Acc d = deg[x];
         const int64_t ubase = (int64_t)up_ptr[x] - (r0 + nlow[x]);
         uint32_t bits = 0;
@@ -149,6 +244,7 @@ k_score_edges(int64_t m, const int32_t* __restrict__ eu, const int32_t* __restri
         const int64_t ie = rowptr[a + 1];
         int64_t j = rowptr[b];
         const int64_t je = rowptr[b + 1];
+        if (ie - i > kLongRow || je - j > kLongRow) continue;  // hub edge: k_score_hub
         PT s = PT(0);
         while (i < ie && j < je) {
             const int32_t ca = col[i], cb = col[j];
@@ -188,6 +284,7 @@ k_score_warp_row(int64_t n, const int64_t* __restrict__ rowptr, const int32_t* _
     for (int64_t a = (int64_t)blockIdx.x * (blockDim.x >> 5) + wib; a < n; a += warps) {
         const int64_t r0 = rowptr[a], r1 = rowptr[a + 1];
         const int64_t da = r1 - r0;
+        if (da > kLongRow) continue;  // hub row: k_score_hub
         const int64_t ufirst = r0 + nlow[a];
         const bool cached = da <= kRowCache;
         if (cached) {
@@ -203,6 +300,7 @@ k_score_warp_row(int64_t n, const int64_t* __restrict__ rowptr, const int32_t* _
             int64_t i = 0;
             int64_t j = rowptr[b];
             const int64_t je = rowptr[b + 1];
+            if (je - j > kLongRow) continue;  // hub edge: k_score_hub
             PT s = PT(0);
             while (i < da && j < je) {
                 const int32_t ca = cached ? s_col[wib][i] : col[r0 + i];
@@ -230,6 +328,211 @@ k_score_warp_row(int64_t n, const int64_t* __restrict__ rowptr, const int32_t* _
     }
 }
 
+// ---- hub edges ----------------------------------------------------------------------------------
+// An edge with an end point of more than kLongRow entries is scored from the larger row H (its
+// "hub"; ties go to the smaller id).  The score is the same left-to-right sum over the union of
+// the two rows, which reads as runs of plain H terms p_Hx (x not in the other row v) separated
+// by the few coordinates of v's row (an extra term p_vx, or |p_Hx - p_vx| where both rows have
+// x).  The runs are evaluated exactly with per-grid prefix tables of H's row: for every binade
+// exponent eb the running sum can have, P_eb[k] = sum_{t<k} round(p_Ht / grid(eb)) and
+// T_eb[k] = number of half-grid ties among the first k terms (see spc_seqsum.cuh).
+
+// per hub: the exponent range of its tables and their size
+template <class PT>
+__global__ void __launch_bounds__(kThreads)
+k_hub_meta(const int64_t* __restrict__ rowptr, const PT* __restrict__ p,
+           const int32_t* __restrict__ long_rows, const int32_t* __restrict__ long_count,
+           int32_t* __restrict__ hub_eblo, int64_t* __restrict__ hub_size,
+           int64_t* __restrict__ hub_deg) {
+    __shared__ unsigned long long sh_min;
+    const int32_t cnt = *long_count;
+    for (int32_t i = blockIdx.x; i < cnt; i += gridDim.x) {
+        const int64_t H = long_rows[i];
+        const int64_t r0 = rowptr[H], r1 = rowptr[H + 1];
+        if (threadIdx.x == 0) sh_min = ~0ull;
+        __syncthreads();
+        unsigned long long mn = ~0ull;
+        for (int64_t j = r0 + threadIdx.x; j < r1; j += blockDim.x) {
+            unsigned long long b = FB<PT>::bits(p[j]);
+            mn = b < mn ? b : mn;
+        }
+        atomicMin(&sh_min, mn);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int eb = (int)(sh_min >> FB<PT>::kMant);
+            const int lo_cap = FB<PT>::kEbHi - 63;
+            if (eb < lo_cap) eb = lo_cap;
+            if (eb < 1) eb = 1;
+            const int nE = FB<PT>::kEbHi - eb + 1;
+            hub_eblo[i] = eb;
+            hub_deg[i] = r1 - r0;
+            hub_size[i] = (int64_t)nE * (r1 - r0 + 1);
+        }
+        __syncthreads();
+    }
+}
+
+// tables: one CTA per (hub, grid); exclusive prefix over the row with a running carry
+template <class PT>
+__global__ void __launch_bounds__(kThreads)
+k_hub_tables(const int64_t* __restrict__ rowptr, const PT* __restrict__ p,
+             const int32_t* __restrict__ long_rows, const int32_t* __restrict__ long_count,
+             const int32_t* __restrict__ hub_eblo, const int64_t* __restrict__ hub_off,
+             unsigned long long* __restrict__ tabP, int32_t* __restrict__ tabT) {
+    __shared__ unsigned long long sh_w[kThreads / 32];
+    __shared__ int32_t sh_t[kThreads / 32];
+    const int32_t cnt = *long_count;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int64_t q = blockIdx.x; q < (int64_t)cnt * 64; q += gridDim.x) {
+        const int32_t i = (int32_t)(q >> 6);
+        const int e = (int)(q & 63);
+        const int eblo = hub_eblo[i];
+        const int nE = FB<PT>::kEbHi - eblo + 1;
+        if (e >= nE) continue;
+        const int eb = eblo + e;
+        const int64_t H = long_rows[i];
+        const int64_t r0 = rowptr[H], d = rowptr[H + 1] - r0;
+        unsigned long long* P = tabP + hub_off[i] + (int64_t)e * (d + 1);
+        int32_t* T = tabT + hub_off[i] + (int64_t)e * (d + 1);
+        if (threadIdx.x == 0) { P[0] = 0; T[0] = 0; }
+        unsigned long long carry = 0;
+        int32_t tcarry = 0;
+        for (int64_t base = 0; base < d; base += blockDim.x) {
+            const int64_t k = base + threadIdx.x;
+            bool tie = false;
+            unsigned long long r = 0;
+            if (k < d) r = grid_units<PT>(p[r0 + k], eb, &tie);
+            int32_t tv = tie ? 1 : 0;
+            unsigned long long v = r;
+            int32_t tt = tv;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                unsigned long long a = __shfl_up_sync(0xffffffffu, v, o);
+                int32_t b = __shfl_up_sync(0xffffffffu, tt, o);
+                if (lane >= o) { v = sat_add(v, a); tt += b; }
+            }
+            if (lane == 31) { sh_w[warp] = v; sh_t[warp] = tt; }
+            __syncthreads();
+            unsigned long long wpre = 0, wtot = 0;
+            int32_t tpre = 0, ttot = 0;
+            for (int w2 = 0; w2 < (int)(blockDim.x >> 5); ++w2) {
+                if (w2 < warp) { wpre = sat_add(wpre, sh_w[w2]); tpre += sh_t[w2]; }
+                wtot = sat_add(wtot, sh_w[w2]);
+                ttot += sh_t[w2];
+            }
+            if (k < d) {
+                P[k + 1] = sat_add(carry, sat_add(wpre, v));
+                T[k + 1] = tcarry + tpre + tt;
+            }
+            carry = sat_add(carry, wtot);
+            tcarry += ttot;
+            __syncthreads();
+        }
+    }
+}
+
+// the sum continued over the plain terms pH[a, b) of the hub row, from running value s
+template <class PT>
+__device__ PT hub_run(PT s, int64_t a, int64_t b, const PT* __restrict__ pH,
+                      const unsigned long long* __restrict__ P, const int32_t* __restrict__ T,
+                      int eblo, int64_t d1) {
+    const int nE = FB<PT>::kEbHi - eblo + 1;
+    while (a < b) {
+        if (s == PT(0)) { s = pH[a++]; continue; }
+        const unsigned long long sb = FB<PT>::bits(s);
+        const int eb = (int)(sb >> FB<PT>::kMant);
+        const int e = eb - eblo;
+        if (eb == 0 || e < 0 || e >= nE) { s = FB<PT>::add(s, pH[a++]); continue; }
+        const unsigned long long* Pe = P + (int64_t)e * d1;
+        const int32_t* Te = T + (int64_t)e * d1;
+        const unsigned long long base = Pe[a];
+        if (base >= kSat - (1ull << 55)) { s = FB<PT>::add(s, pH[a++]); continue; }
+        const unsigned long long S = (sb & ((1ull << FB<PT>::kMant) - 1ull)) | (1ull << FB<PT>::kMant);
+        const unsigned long long lim = (1ull << (FB<PT>::kMant + 1)) - S;
+        // largest k in [a, b] whose prefix stays on this grid
+        int64_t lo = a, hi = b;
+        while (lo < hi) {
+            const int64_t mid = (lo + hi + 1) >> 1;
+            if (Pe[mid] - base <= lim) lo = mid; else hi = mid - 1;
+        }
+        int64_t k = lo;
+        const int32_t ta = Te[a];
+        if (Te[k] > ta) {  // a half-grid tie inside: stop at the first one
+            int64_t l2 = a, h2 = k - 1;
+            while (l2 < h2) {
+                const int64_t mid = (l2 + h2) >> 1;
+                if (Te[mid + 1] > ta) h2 = mid; else l2 = mid + 1;
+            }
+            k = l2;
+        }
+        s = from_units<PT>(S + (Pe[k] - base), eb);
+        a = k;
+        if (a < b) s = FB<PT>::add(s, pH[a++]);  // binade crossing or tie: one native step
+    }
+    return s;
+}
+
+// S3 for hub edges: one thread per entry (H, v) of a hub row, flat over all hubs
+template <class PT, class KT>
+__global__ void __launch_bounds__(kThreads)
+k_score_hub(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+            const PT* __restrict__ p, const int32_t* __restrict__ up_ptr,
+            const int32_t* __restrict__ nlow, const int32_t* __restrict__ long_rows,
+            const int32_t* __restrict__ long_count, const int64_t* __restrict__ hub_eoff,
+            const int32_t* __restrict__ hub_eblo, const int64_t* __restrict__ hub_off,
+            const unsigned long long* __restrict__ tabP, const int32_t* __restrict__ tabT,
+            KT* __restrict__ score, const uint32_t* status) {
+    if (*status) return;
+    const int32_t cnt = *long_count;
+    const int64_t total = hub_eoff[cnt];
+    for (int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; f < total;
+         f += (int64_t)gridDim.x * blockDim.x) {
+        int32_t lo = 0, hi = cnt - 1;  // hub of flat entry f
+        while (lo < hi) {
+            const int32_t mid = (lo + hi + 1) >> 1;
+            if (hub_eoff[mid] <= f) lo = mid; else hi = mid - 1;
+        }
+        const int32_t i = lo;
+        const int64_t H = long_rows[i];
+        const int64_t rH = rowptr[H], dH = rowptr[H + 1] - rH;
+        const int64_t k = f - hub_eoff[i];
+        const int64_t v = col[rH + k];
+        const int64_t rv = rowptr[v], dv = rowptr[v + 1] - rv;
+        if (dv > dH || (dv == dH && v < H)) continue;  // v's row is the hub of this edge
+        const int32_t* cH = col + rH;
+        const PT* pH = p + rH;
+        const unsigned long long* P = tabP + hub_off[i];
+        const int32_t* T = tabT + hub_off[i];
+        const int eblo = hub_eblo[i];
+        PT s = PT(0);
+        int64_t a = 0;
+        int64_t jH = -1;  // position of H in v's row
+        for (int64_t j = 0; j < dv; ++j) {
+            const int32_t x = col[rv + j];
+            if ((int64_t)x == H) jH = j;
+            int64_t l2 = a, h2 = dH;  // first position >= a in H's row with column >= x
+            while (l2 < h2) {
+                const int64_t mid = (l2 + h2) >> 1;
+                if (cH[mid] < x) l2 = mid + 1; else h2 = mid;
+            }
+            s = hub_run<PT>(s, a, l2, pH, P, T, eblo, dH + 1);
+            PT t;
+            if (l2 < dH && cH[l2] == x) {
+                t = p_absdiff(pH[l2], p[rv + j]);
+                a = l2 + 1;
+            } else {
+                t = p[rv + j];
+                a = l2;
+            }
+            s = p_add(s, t);
+        }
+        s = hub_run<PT>(s, a, dH, pH, P, T, eblo, dH + 1);
+        const int64_t e = (H < v) ? (int64_t)up_ptr[H] + (k - nlow[H])
+                                  : (int64_t)up_ptr[v] + (jH - nlow[v]);
+        score[e] = key_bits(s);
+    }
+}
+
 template <class WT>
 static spc_status score_typed(spc_context* ctx, GraphView& g, bool validate, void* score,
                               int schedule) {
@@ -240,26 +543,44 @@ static spc_status score_typed(spc_context* ctx, GraphView& g, bool validate, voi
     const int64_t n = g.n;
     const int64_t nnz = g.nnz;
     const int maxb = ctx->num_sms * 8;
+    const int persist = ctx->num_sms * 2;
     uint32_t* status = ctx->d_status;
+    int32_t* long_count = W.counters.as<int32_t>() + 8;
+    int32_t* long_rows = W.long_rows.as<int32_t>();
     const int gb = grid_for(n, kThreads, maxb);
+    SPC_CUDA(cudaMemsetAsync(long_count, 0, sizeof(int32_t), ctx->stream));
     SPC_LAUNCH(ctx, k_rows_degree<WT>, gb, kThreads, 0, n, nnz, g.rowptr, g.col,
                static_cast<const WT*>(g.w), validate ? 1 : 0, W.deg.as<Acc>(),
-               W.up_cnt.as<int32_t>(), W.first_up.as<int32_t>(), status);
+               W.up_cnt.as<int32_t>(), W.first_up.as<int32_t>(), long_rows, long_count, status);
+    SPC_LAUNCH(ctx, k_long_rows_degree<WT>, persist, kThreads, 0, n, g.rowptr, g.col,
+               static_cast<const WT*>(g.w), validate ? 1 : 0, long_rows, long_count,
+               W.deg.as<Acc>(), W.up_cnt.as<int32_t>(), W.first_up.as<int32_t>(), status);
     SPC_TRY(scan_i32(ctx, W.up_cnt.as<int32_t>(), W.up_ptr.as<int32_t>(), n));
-    // one readback: the status word and the edge count
-    SPC_CUDA(cudaMemcpyAsync(ctx->h_scalars, W.up_ptr.as<int32_t>() + n, sizeof(int32_t),
+    // one readback: the status word, the edge count and the number of long rows
+    int32_t* hs = reinterpret_cast<int32_t*>(ctx->h_scalars);
+    SPC_CUDA(cudaMemcpyAsync(hs, W.up_ptr.as<int32_t>() + n, sizeof(int32_t),
                              cudaMemcpyDeviceToHost, ctx->stream));
+    SPC_CUDA(cudaMemcpyAsync(hs + 1, long_count, sizeof(int32_t), cudaMemcpyDeviceToHost,
+                             ctx->stream));
     SPC_CUDA(cudaMemcpyAsync(ctx->h_status, status, sizeof(uint32_t), cudaMemcpyDeviceToHost,
                              ctx->stream));
     SPC_CUDA(cudaStreamSynchronize(ctx->stream));
     if (*ctx->h_status) return status_from_bits(*ctx->h_status);
-    const int64_t m = *reinterpret_cast<int32_t*>(ctx->h_scalars);
+    const int64_t m = hs[0];
+    const int64_t n_long = hs[1];
     if (2 * m != nnz) return SPC_ERR_NOT_SYMMETRIC;
     g.m = m;
     SPC_LAUNCH(ctx, k_rows_edges<WT>, gb, kThreads, 0, n, g.rowptr, g.col,
                static_cast<const WT*>(g.w), validate ? 1 : 0, W.deg.as<Acc>(),
                W.first_up.as<int32_t>(), W.up_ptr.as<int32_t>(), W.p.as<P>(),
                W.eu.as<int32_t>(), W.ev.as<int32_t>(), W.w_und.as<WT>(), status);
+    if (n_long > 0) {
+        SPC_LAUNCH(ctx, k_long_rows_edges<WT>, persist, kThreads, 0, g.rowptr, g.col,
+                   static_cast<const WT*>(g.w), validate ? 1 : 0, W.deg.as<Acc>(),
+                   W.first_up.as<int32_t>(), W.up_ptr.as<int32_t>(), long_rows, long_count,
+                   W.p.as<P>(), W.eu.as<int32_t>(), W.ev.as<int32_t>(), W.w_und.as<WT>(),
+                   status);
+    }
     if (validate) SPC_TRY(sync_status(ctx));  // no later kernel runs on an asymmetric input
     if (score == nullptr || m == 0) return SPC_OK;
     if (schedule == 2) {
@@ -273,6 +594,30 @@ static spc_status score_typed(spc_context* ctx, GraphView& g, bool validate, voi
                    W.eu.as<int32_t>(), W.ev.as<int32_t>(), g.rowptr, g.col, W.p.as<P>(),
                    static_cast<Key*>(score), status);
     }
+    if (n_long == 0) return SPC_OK;
+    // hub edges: per-grid prefix tables of every hub row, then one thread per hub entry
+    SPC_LAUNCH(ctx, k_hub_meta<P>, persist, kThreads, 0, g.rowptr, W.p.as<P>(), long_rows,
+               long_count, W.hub_eblo.as<int32_t>(), W.hub_size.as<int64_t>(),
+               W.hub_deg.as<int64_t>());
+    SPC_TRY(scan_i64_i64(ctx, W.hub_size.as<int64_t>(), W.hub_off.as<int64_t>(), n_long));
+    SPC_TRY(scan_i64_i64(ctx, W.hub_deg.as<int64_t>(), W.hub_eoff.as<int64_t>(), n_long));
+    SPC_CUDA(cudaMemcpyAsync(ctx->h_scalars, W.hub_off.as<int64_t>() + n_long, sizeof(int64_t),
+                             cudaMemcpyDeviceToHost, ctx->stream));
+    SPC_CUDA(cudaMemcpyAsync(ctx->h_scalars + 1, W.hub_eoff.as<int64_t>() + n_long,
+                             sizeof(int64_t), cudaMemcpyDeviceToHost, ctx->stream));
+    SPC_CUDA(cudaStreamSynchronize(ctx->stream));
+    const int64_t tab_elems = ctx->h_scalars[0];
+    const int64_t hub_entries = ctx->h_scalars[1];
+    SPC_TRY(ensure(ctx, W.tab_p, (size_t)tab_elems * 8 + 256));
+    SPC_TRY(ensure(ctx, W.tab_t, (size_t)tab_elems * 4 + 256));
+    SPC_LAUNCH(ctx, k_hub_tables<P>, grid_for(n_long * 64, 1, maxb), kThreads, 0, g.rowptr,
+               W.p.as<P>(), long_rows, long_count, W.hub_eblo.as<int32_t>(),
+               W.hub_off.as<int64_t>(), W.tab_p.as<unsigned long long>(), W.tab_t.as<int32_t>());
+    SPC_LAUNCH(ctx, (k_score_hub<P, Key>), grid_for(hub_entries, kThreads, maxb), kThreads, 0,
+               g.rowptr, g.col, W.p.as<P>(), W.up_ptr.as<int32_t>(), W.first_up.as<int32_t>(),
+               long_rows, long_count, W.hub_eoff.as<int64_t>(), W.hub_eblo.as<int32_t>(),
+               W.hub_off.as<int64_t>(), W.tab_p.as<unsigned long long>(), W.tab_t.as<int32_t>(),
+               static_cast<Key*>(score), status);
     return SPC_OK;
 }
 

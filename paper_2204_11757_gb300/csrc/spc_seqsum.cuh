@@ -1,0 +1,188 @@
+// Exact, parallel evaluation of IEEE sequential summation of nonnegative terms.
+//
+// Every sum on the path (degrees, scores, coarse weights, self-mass) is defined as the
+// left-to-right IEEE round-to-nearest sum s_{k+1} = RN(s_k + t_k) in a fixed order.  A single
+// thread walking a long sequence serialises a whole launch (hub rows, giant super-nodes), so
+// long sums are evaluated in parallel without changing a single bit:
+//
+//   For s in the binade [2^E, 2^(E+1)) the representable numbers are the multiples of the grid
+//   g = 2^(E - p + 1) (p = 53 or 24 significand bits), and 2^(E+1) is one of them.  With
+//   s = S g, S integer, RN(s + t) = (S + round(t / g)) g as long as S + round(t / g) <= 2^p:
+//   the sum stays on the same grid and the step is an integer addition of the term rounded to
+//   the grid.  Only two kinds of steps fall outside that rule: a step whose result would pass
+//   2^(E+1) (it is rounded on the coarser grid above), and an exact half-grid tie (decided by
+//   the parity of S).  Both are done with one native IEEE addition.
+//
+//   So a run of terms is: integer prefix sums of the grid-rounded terms, a search for the
+//   first step that crosses the binade or is a tie, one native addition there, repeat.  The
+//   running sum only grows (terms >= 0), so a sum crosses at most ~60 binades.
+//
+// Two evaluators are built on it: cta_seqsum (one long sum by a whole CTA, chunk by chunk) and
+// per-grid prefix tables over a hub row, which let every edge of the hub evaluate its runs of
+// that row with a few binary searches (spc_score.cu).
+#pragma once
+
+#include "spc_internal.cuh"
+
+namespace spc {
+
+constexpr int kLongRow = 256;  // rows / segments longer than this are summed by a whole CTA
+constexpr unsigned long long kSat = 1ull << 62;
+
+template <class F> struct FB;
+template <> struct FB<double> {
+    static constexpr int kMant = 52;          // stored significand bits
+    static constexpr int kBiasM = 1075;       // exponent bias + kMant
+    static constexpr int kEbHi = 1025;        // biased exponent of the largest binade needed (s < 8)
+    __device__ static unsigned long long bits(double x) {
+        return (unsigned long long)__double_as_longlong(x);
+    }
+    __device__ static double from_bits(unsigned long long b) { return __longlong_as_double((long long)b); }
+    __device__ static double add(double a, double b) { return __dadd_rn(a, b); }
+};
+template <> struct FB<float> {
+    static constexpr int kMant = 23;
+    static constexpr int kBiasM = 150;
+    static constexpr int kEbHi = 129;
+    __device__ static unsigned long long bits(float x) { return __float_as_uint(x); }
+    __device__ static float from_bits(unsigned long long b) { return __uint_as_float((unsigned)b); }
+    __device__ static float add(float a, float b) { return __fadd_rn(a, b); }
+};
+
+__device__ __forceinline__ unsigned long long sat_add(unsigned long long a, unsigned long long b) {
+    unsigned long long c = a + b;
+    return c > kSat ? kSat : c;
+}
+
+// round(t / g) for the grid of binade `eb` (biased exponent of the running sum), t >= 0 finite;
+// an exact half-grid value rounds down and sets *tie.  Saturates at kSat.
+template <class F>
+__device__ __forceinline__ unsigned long long grid_units(F t, int eb, bool* tie) {
+    const unsigned long long b = FB<F>::bits(t);
+    int et = (int)(b >> FB<F>::kMant);
+    unsigned long long mt = b & ((1ull << FB<F>::kMant) - 1ull);
+    if (et == 0) et = 1; else mt |= (1ull << FB<F>::kMant);
+    const int d = eb - et;
+    *tie = false;
+    if (d <= 0) {
+        const int sh = -d;
+        if (sh >= 62 - FB<F>::kMant - 1) return mt ? kSat : 0ull;
+        return mt << sh;
+    }
+    if (d > FB<F>::kMant + 2) return 0ull;
+    const unsigned long long q = mt >> d;
+    const unsigned long long rem = mt & ((1ull << d) - 1ull);
+    const unsigned long long half = 1ull << (d - 1);
+    *tie = rem == half;
+    return q + (rem > half ? 1ull : 0ull);
+}
+
+// s = S * grid(eb), S in [2^kMant, 2^(kMant+1)]
+template <class F>
+__device__ __forceinline__ F from_units(unsigned long long S, int eb) {
+    return FB<F>::from_bits(((unsigned long long)eb << FB<F>::kMant) + (S - (1ull << FB<F>::kMant)));
+}
+
+// One long sequential sum by a whole CTA (all threads call it with the same arguments and
+// get the same result).  term(i), i in [0, L), must be >= 0.  kItems consecutive terms per
+// thread and chunk.
+template <int kItems, class F, class Term>
+__device__ F cta_seqsum(F s, int64_t L, const Term& term) {
+    __shared__ unsigned long long sh_tot[32];
+    __shared__ int sh_first;
+    __shared__ unsigned long long sh_excl;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int lane = tid & 31, warp = tid >> 5, nw = (nt + 31) >> 5;
+    int64_t k = 0;
+    while (k < L) {
+        const unsigned long long sb = FB<F>::bits(s);
+        const int eb = (int)(sb >> FB<F>::kMant);
+        if (s == F(0) || eb == 0) {  // zero or subnormal running sum: one native step
+            s = FB<F>::add(s, term(k));
+            ++k;
+            continue;
+        }
+        const unsigned long long S = (sb & ((1ull << FB<F>::kMant) - 1ull)) | (1ull << FB<F>::kMant);
+        const unsigned long long lim = (1ull << (FB<F>::kMant + 1)) - S;  // S + Q <= 2^(p) allowed
+        const int64_t chunk = (L - k) < (int64_t)nt * kItems ? (L - k) : (int64_t)nt * kItems;
+        unsigned long long r[kItems];
+        bool tie[kItems];
+        unsigned long long run = 0;
+#pragma unroll
+        for (int j = 0; j < kItems; ++j) {
+            const int64_t i = (int64_t)tid * kItems + j;
+            tie[j] = false;
+            r[j] = 0;
+            if (i < chunk) r[j] = grid_units<F>(term(k + i), eb, &tie[j]);
+            run = sat_add(run, r[j]);
+        }
+        // block exclusive scan of the per-thread totals (saturating)
+        unsigned long long v = run;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            unsigned long long t = __shfl_up_sync(0xffffffffu, v, o);
+            if (lane >= o) v = sat_add(v, t);
+        }
+        if (lane == 31) sh_tot[warp] = v;
+        if (tid == 0) sh_first = 0x7fffffff;
+        __syncthreads();
+        if (warp == 0) {
+            unsigned long long x = lane < nw ? sh_tot[lane] : 0ull;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                unsigned long long t = __shfl_up_sync(0xffffffffu, x, o);
+                if (lane >= o) x = sat_add(x, t);
+            }
+            sh_tot[lane] = x;
+        }
+        __syncthreads();
+        unsigned long long wex = __shfl_up_sync(0xffffffffu, v, 1);  // exclusive within warp
+        if (lane == 0) wex = 0ull;
+        unsigned long long excl = sat_add(warp > 0 ? sh_tot[warp - 1] : 0ull, wex);
+        const unsigned long long total = sh_tot[nw - 1];
+        // first step that leaves the binade or is a tie
+        int mine = 0x7fffffff;
+        unsigned long long pre = excl;
+#pragma unroll
+        for (int j = 0; j < kItems; ++j) {
+            const int64_t i = (int64_t)tid * kItems + j;
+            const unsigned long long q = sat_add(pre, r[j]);
+            if (i < chunk && mine == 0x7fffffff && (q > lim || tie[j])) mine = (int)i;
+            if (mine == 0x7fffffff) pre = q;
+        }
+        if (mine != 0x7fffffff) atomicMin(&sh_first, mine);
+        __syncthreads();
+        const int first = sh_first;
+        if (first != 0x7fffffff && first / kItems == tid && mine == first) sh_excl = pre;
+        __syncthreads();
+        if (first == 0x7fffffff) {
+            s = from_units<F>(S + total, eb);
+            k += chunk;
+        } else {
+            s = from_units<F>(S + sh_excl, eb);
+            s = FB<F>::add(s, term(k + first));
+            k += first + 1;
+        }
+        __syncthreads();
+    }
+    return s;
+}
+
+// Sum of int64 terms by a whole CTA (exact in any order).
+template <class Term>
+__device__ long long cta_sum_i64(int64_t L, const Term& term) {
+    __shared__ long long sh[32];
+    long long s = 0;
+    for (int64_t i = threadIdx.x; i < L; i += blockDim.x) s += term(i);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    if (lane == 0) sh[warp] = s;
+    __syncthreads();
+    long long t = 0;
+    for (int w = 0; w < nw; ++w) t += sh[w];
+    __syncthreads();
+    return t;
+}
+
+}  // namespace spc

@@ -383,6 +383,8 @@ CONFIGS = {
                              mode="one", ratio=256),
     "c5_batch10k_f32": dict(kind="batch", B=10000, dtype="float32", seed=5, mode="halving",
                             ratio=8),
+    "p2_tri512_f64": dict(kind="tri", nx=512, ny=512, jitter=0.3, weight="inv_len",
+                          dtype="float64", seed=2, mode="halving", ratio=64),
     # reduced versions (same construction, sizes the oracle handles in well under a second)
     "s2_tri256_f64": dict(kind="tri", nx=256, ny=256, jitter=0.3, weight="inv_len",
                           dtype="float64", seed=12, mode="halving", ratio=64),
@@ -412,3 +414,51 @@ def config_graph(name: str):
     else:
         raise ValueError(cfg["kind"])
     return g, cfg
+
+
+def star_ties(leaves_log2: int = 12, dtype=np.float64, chords: int = 0, seed: int = 0) -> Graph:
+    """A star whose hub weights alternate 1 + eps and 1 - eps (eps = 2^-41 in binary64, 2^-12 in
+    binary32): the hub's degree is an exact power of two and its normalised weights sit exactly
+    half a unit in the last place away from the grid of a running sum in [1, 2), so summing the
+    hub row hits exact rounding ties.  `chords` adds seeded leaf-leaf edges (weight 1)."""
+    L = 1 << leaves_log2
+    eps = 2.0 ** -41 if np.dtype(dtype) == np.float64 else 2.0 ** -12
+    w = np.where(np.arange(L) % 2 == 0, 1.0 + eps, 1.0 - eps).astype(dtype)
+    eu = np.zeros(L, dtype=np.int64)
+    ev = np.arange(1, L + 1, dtype=np.int64)
+    if chords:
+        rng = np.random.Generator(np.random.PCG64(seed))
+        a = rng.integers(1, L + 1, size=chords)
+        b = rng.integers(1, L + 1, size=chords)
+        keep = a != b
+        a, b = np.minimum(a[keep], b[keep]), np.maximum(a[keep], b[keep])
+        key = np.unique(a * (L + 1) + b)
+        a, b = key // (L + 1), key % (L + 1)
+        eu = np.concatenate([eu, a]); ev = np.concatenate([ev, b])
+        w = np.concatenate([w, np.ones(a.shape[0], dtype=dtype)])
+    return csr_from_edges(L + 1, eu, ev, w, name=f"star_ties_{L}")
+
+
+def hub_graph(n: int, hub_degrees, seed: int, weight: str = "float", dtype=np.float64,
+              base_p: float = 0.002) -> Graph:
+    """Sparse random graph plus a few hubs: node h < len(hub_degrees) is joined to
+    hub_degrees[h] random nodes (hubs also join each other).  Weights as in random_graph."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    m0 = int(base_p * n * (n - 1) / 2)
+    a = rng.integers(0, n, size=m0); b = rng.integers(0, n, size=m0)
+    us, vs = [a], [b]
+    for h, dh in enumerate(hub_degrees):
+        t = rng.choice(n, size=min(dh, n - 1), replace=False)
+        us.append(np.full(t.shape[0], h)); vs.append(t)
+    u = np.concatenate(us); v = np.concatenate(vs)
+    keep = u != v
+    u, v = np.minimum(u[keep], v[keep]), np.maximum(u[keep], v[keep])
+    key = np.unique(u.astype(np.int64) * n + v)
+    u, v = key // n, key % n
+    if weight == "unit":
+        w = np.ones(u.shape[0], dtype=dtype)
+    elif weight == "int":
+        w = rng.integers(1, 10, size=u.shape[0]).astype(dtype)
+    else:
+        w = rng.uniform(0.1, 2.0, size=u.shape[0]).astype(dtype)
+    return csr_from_edges(n, u, v, w, name=f"hubs{n}")

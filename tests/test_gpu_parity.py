@@ -368,3 +368,33 @@ def test_contract_rejects_out_of_range_lift(ctx):
     with pytest.raises(N.SpcError) as ei:
         ctx.contract(api.CSR.from_graph(g), bad, 5)
     assert ei.value.status == -1
+
+
+# ---- long rows and hubs (exact parallel evaluation of the sequential sums) -----------------------
+
+HUBS = [
+    ("star64", lambda: I.star_ties(12, np.float64)),
+    ("star32", lambda: I.star_ties(12, np.float32)),
+    ("star64_chords", lambda: I.star_ties(11, np.float64, chords=3000, seed=1)),
+    ("star32_chords", lambda: I.star_ties(11, np.float32, chords=3000, seed=2)),
+    ("hubs_f64", lambda: I.hub_graph(6000, [5000, 3000, 700, 300, 257], 3, "float", np.float64)),
+    ("hubs_f32", lambda: I.hub_graph(6000, [5000, 3000, 700, 300], 4, "float", np.float32)),
+    ("hubs_int", lambda: I.hub_graph(6000, [4000, 2500, 600], 5, "int", np.int32)),
+    ("hubs_unit", lambda: I.hub_graph(5000, [4999, 4000, 256, 257, 258], 6, "unit", np.int32)),
+]
+
+
+@pytest.mark.parametrize("name,make", HUBS, ids=[h[0] for h in HUBS])
+def test_hub_scores_and_level_bitexact(ctx, name, make):
+    g = make()
+    api = _api()
+    ref_f = O.score(g)
+    csr = api.CSR.from_graph(g)
+    f = ctx.score(csr).cpu().numpy()
+    bad = np.nonzero(_bits(f) != _bits(ref_f))[0]
+    assert bad.size == 0, (bad[:10], f[bad[:5]], ref_f[bad[:5]])
+    for n_c in (max(1, g.n // 2), max(1, g.n // 7)):
+        ref = O.coarsen_level(g, n_c)
+        lift, nc, st = ctx.coarsen(csr, n_c, levels=1)
+        assert nc == ref.n_c
+        _check_level(ctx.level(0), ref)
