@@ -224,6 +224,26 @@ SPC_API spc_status spc_contract_backward(spc_context* ctx, const int32_t* emap, 
  * super-node).  emap_out[m of level 0] int32, device or host. */
 SPC_API spc_status spc_compose_emap(spc_context* ctx, int32_t* emap_out);
 
+/* ---- allocation-free variant ---------------------------------------------------------------- */
+
+/* spc_sort_fitness without a context and without allocating: for callers that must not call
+ * cudaMalloc (a fixed memory budget owned by another framework, threads that cannot take
+ * cudaMalloc's implicit device synchronisation, memory reserved entirely up front).  The paper
+ * has no counterpart; it is the S4 sort of spc_sort_fitness with its temporaries in one
+ * file-scope device array of the library (22 MiB, held on every GPU that loads the library).
+ *   m           number of scores, 0 <= m <= 2^20 (larger: SPC_ERR_TOO_LARGE, nothing launched)
+ *   f           device pointer, m scores of type ftype (SPC_F32 or SPC_F64), values >= +0
+ *   order_out   device pointer, m int32: edge ids sorted by (f, eid), the same result as
+ *               spc_sort_fitness
+ *   stream      cudaStream_t the work is enqueued on (NULL: legacy default stream)
+ * Returns once the work is enqueued; the result is ready when the stream reaches it.  Host
+ * pointers are rejected with SPC_ERR_INVALID_ARG (staging them would need memory).  The first
+ * call on a device looks up the array's device address (cudaGetSymbolAddress) for that device;
+ * make it before any stream capture.  All calls share the array: calls that may execute
+ * concurrently on the GPU race and must be ordered by the caller. */
+SPC_API spc_status spc_sort_fitness_static(int64_t m, const void* f, spc_dtype ftype,
+                                           int32_t* order_out, void* stream);
+
 /* ---- timing ------------------------------------------------------------------------------- */
 
 /* Record CUDA events around every launch of the kernels whose name contains `kernel_substr`

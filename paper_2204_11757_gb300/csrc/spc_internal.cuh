@@ -168,6 +168,16 @@ spc_status radix_sort_u64(spc_context* ctx, uint64_t* keys, uint32_t* vals, uint
 spc_status radix_sort_u32(spc_context* ctx, uint32_t* keys, uint32_t* vals, uint32_t* keys_alt,
                           uint32_t* vals_alt, int64_t count, int end_bit);
 
+// Context-free variants (caller-owned scratch, explicit stream) used by the allocation-free
+// entry point in spc_static.cu.
+int64_t scan_raw_tmp_elems(int64_t n);
+cudaError_t scan_i32_raw(cudaStream_t stream, const int32_t* in, int32_t* out, int64_t n,
+                         int32_t* tmp);
+int64_t radix_raw_hist_elems(int64_t count);
+cudaError_t radix_sort_u64_raw(cudaStream_t stream, uint64_t* keys, uint32_t* vals,
+                               uint64_t* keys_alt, uint32_t* vals_alt, int64_t count,
+                               int end_bit, int32_t* hist, int32_t* scan_tmp);
+
 // ---- steps (spc_score.cu, spc_merge.cu, spc_contract.cu) ----------------------------------
 
 struct GraphView {

@@ -156,3 +156,23 @@ spc_status scan_flags_u8(spc_context* ctx, const uint8_t* in, int32_t* out, int6
 }
 
 }  // namespace spc
+
+namespace spc {
+
+// Context-free exclusive scan of n int32 values (out[n] = total) on `stream`, with caller-owned
+// temporaries: tmp must hold scan_raw_tmp_elems(n) int32 values.
+int64_t scan_raw_tmp_elems(int64_t n) { return (n + STILE - 1) / STILE + 1; }
+
+cudaError_t scan_i32_raw(cudaStream_t stream, const int32_t* in, int32_t* out, int64_t n,
+                         int32_t* tmp) {
+    const int64_t nt = (n + STILE - 1) / STILE;
+    int32_t* tiles = tmp;
+    int32_t* total = tmp + nt;
+    if (nt > 0) k_scan_reduce<int32_t, int32_t><<<(unsigned)nt, ST, 0, stream>>>(in, n, tiles);
+    k_scan_tiles<int32_t><<<1, ST, 0, stream>>>(tiles, nt, total);
+    if (nt > 0) k_scan_down<int32_t, int32_t, int32_t><<<(unsigned)nt, ST, 0, stream>>>(in, n, tiles, out);
+    k_copy_total<int32_t, int32_t><<<1, 32, 0, stream>>>(total, out + n);
+    return cudaGetLastError();
+}
+
+}  // namespace spc

@@ -198,3 +198,54 @@ spc_status radix_sort_u32(spc_context* ctx, uint32_t* keys, uint32_t* vals, uint
 }
 
 }  // namespace spc
+
+namespace spc {
+
+// Context-free stable LSD radix sort of (uint64 key, uint32 value) pairs on key bits
+// [0, end_bit), launched on `stream` with caller-owned scratch: keys_alt/vals_alt of `count`
+// items, hist of radix_raw_hist_elems(count) int32 and scan_tmp of
+// scan_raw_tmp_elems(256 * tiles) int32.  The result ends in (keys, vals).
+int64_t radix_raw_hist_elems(int64_t count) {
+    return (int64_t)RADIX * ((count + RTILE - 1) / RTILE) + 1;
+}
+
+cudaError_t radix_sort_u64_raw(cudaStream_t stream, uint64_t* keys, uint32_t* vals,
+                               uint64_t* keys_alt, uint32_t* vals_alt, int64_t count,
+                               int end_bit, int32_t* hist, int32_t* scan_tmp) {
+    if (count <= 1 || end_bit <= 0) return cudaSuccess;
+    const int64_t tiles = (count + RTILE - 1) / RTILE;
+    const size_t smem = sizeof(SortSmem<uint64_t>);
+    cudaError_t e = cudaFuncSetAttribute(k_rs_downsweep<uint64_t>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    uint64_t* ka = keys;
+    uint32_t* va = vals;
+    uint64_t* kb = keys_alt;
+    uint32_t* vb = vals_alt;
+    int passes = 0;
+    for (int shift = 0; shift < end_bit; shift += 8) {
+        const int bits = (end_bit - shift) < 8 ? (end_bit - shift) : 8;
+        const uint32_t mask = (1u << bits) - 1u;
+        k_rs_upsweep<uint64_t><<<(unsigned)tiles, RT, 0, stream>>>(ka, count, shift, mask, hist,
+                                                                  tiles);
+        e = scan_i32_raw(stream, hist, hist, (int64_t)RADIX * tiles, scan_tmp);
+        if (e != cudaSuccess) return e;
+        k_rs_downsweep<uint64_t><<<(unsigned)tiles, RT, smem, stream>>>(ka, va, kb, vb, count,
+                                                                       shift, mask, hist, tiles);
+        uint64_t* tk = ka; ka = kb; kb = tk;
+        uint32_t* tv = va; va = vb; vb = tv;
+        ++passes;
+    }
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if (passes & 1) {
+        e = cudaMemcpyAsync(keys, ka, (size_t)count * sizeof(uint64_t), cudaMemcpyDeviceToDevice,
+                            stream);
+        if (e != cudaSuccess) return e;
+        e = cudaMemcpyAsync(vals, va, (size_t)count * sizeof(uint32_t), cudaMemcpyDeviceToDevice,
+                            stream);
+    }
+    return e;
+}
+
+}  // namespace spc
