@@ -194,11 +194,15 @@ static spc_status reserve_work(spc_context* ctx, int64_t n, int64_t m, int64_t B
     SPC_TRY(ensure(ctx, W.deg, N * 8));
     SPC_TRY(ensure(ctx, W.p, 2 * M * 8));
     SPC_TRY(ensure(ctx, W.long_rows, N * 4));
-    SPC_TRY(ensure(ctx, W.hub_eblo, N * 4));
-    SPC_TRY(ensure(ctx, W.hub_size, N * 8));
-    SPC_TRY(ensure(ctx, W.hub_deg, N * 8));
-    SPC_TRY(ensure(ctx, W.hub_off, (N + 1) * 8));
-    SPC_TRY(ensure(ctx, W.hub_eoff, (N + 1) * 8));
+    SPC_TRY(ensure(ctx, W.lr_base, N * 8));
+    SPC_TRY(ensure(ctx, W.lr_len, N * 8));
+    SPC_TRY(ensure(ctx, W.lr_idx, N * 8));
+    SPC_TRY(ensure(ctx, W.lr_eoff, (N + 1) * 8));
+    SPC_TRY(ensure(ctx, W.heavy, M * 4));
+    SPC_TRY(ensure(ctx, W.seg_base, M * 8));
+    SPC_TRY(ensure(ctx, W.seg_len, M * 8));
+    SPC_TRY(ensure(ctx, W.seg_idx, M * 8));
+    SPC_TRY(ensure(ctx, W.seg_terms, M * 8));
     SPC_TRY(ensure(ctx, W.parent, N * 4));
     for (int i = 0; i < 2; ++i) {
         SPC_TRY(ensure(ctx, W.best_k[i], N * 8));

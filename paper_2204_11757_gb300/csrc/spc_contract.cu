@@ -164,6 +164,40 @@ k_segsum_long(const int32_t* __restrict__ start, const uint32_t* __restrict__ id
     }
 }
 
+// long segment q (segment r = long_list[q]): its length, and the slot its sum goes to
+__global__ void k_long_seg_prep(const int32_t* __restrict__ long_list,
+                                const int32_t* __restrict__ long_count,
+                                const int32_t* __restrict__ start, const uint32_t* __restrict__ key,
+                                int64_t* __restrict__ len, int64_t* __restrict__ out_idx) {
+    const int32_t cnt = *long_count;
+    for (int32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < cnt; q += gridDim.x * blockDim.x) {
+        const int32_t r = long_list[q];
+        len[q] = start[r + 1] - start[r];
+        out_idx[q] = key ? (int64_t)key[start[r]] : (int64_t)r;
+    }
+}
+
+// the terms of all long segments, gathered contiguously (segment q at base[q])
+template <class WT>
+__global__ void __launch_bounds__(kThreads)
+k_gather_long_terms(const int32_t* __restrict__ long_list, const int32_t* __restrict__ long_count,
+                    const int32_t* __restrict__ start, const uint32_t* __restrict__ idx,
+                    const WT* __restrict__ w_und, const int64_t* __restrict__ base,
+                    WT* __restrict__ terms) {
+    const int32_t cnt = *long_count;
+    const int64_t total = base[cnt];
+    for (int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; f < total;
+         f += (int64_t)gridDim.x * blockDim.x) {
+        int32_t lo = 0, hi = cnt - 1;
+        while (lo < hi) {
+            const int32_t mid = (lo + hi + 1) >> 1;
+            if (base[mid] <= f) lo = mid; else hi = mid - 1;
+        }
+        const int32_t r = long_list[lo];
+        terms[f] = w_und[idx[start[r] + (f - base[lo])]];
+    }
+}
+
 __global__ void __launch_bounds__(kThreads)
 k_degree_counts(int64_t m_c, const int32_t* __restrict__ cU, const int32_t* __restrict__ cV,
                 int32_t* up_deg, int32_t* low_deg, uint32_t* __restrict__ tkey,
@@ -228,6 +262,45 @@ k_backward(int64_t m, const int32_t* __restrict__ emap, const WT* __restrict__ g
     }
 }
 
+// Sums of the segments that k_segsum_short left to the long list: integer weights by CTA
+// reductions, floating point by per-binade tables (exact left-to-right sums).
+template <class WT, class Out>
+spc_status long_segment_sums(spc_context* ctx, const int32_t* start, const uint32_t* idx,
+                             const uint32_t* key, const WT* w_und, Out* out) {
+    Work& W = ctx->work;
+    int32_t* long_list = W.long_segs.as<int32_t>();
+    int32_t* long_cnt = W.counters.as<int32_t>() + 9;
+    if constexpr (std::is_same<WT, int32_t>::value) {
+        SPC_LAUNCH(ctx, (k_segsum_long<WT, Out>), ctx->num_sms * 2, kThreads, 0, start, idx, key,
+                   w_und, out, long_list, long_cnt, ctx->d_status);
+        return SPC_OK;
+    } else {
+        SPC_CUDA(cudaMemcpyAsync(ctx->h_scalars, long_cnt, sizeof(int32_t),
+                                 cudaMemcpyDeviceToHost, ctx->stream));
+        SPC_CUDA(cudaStreamSynchronize(ctx->stream));
+        const int64_t nlong = reinterpret_cast<int32_t*>(ctx->h_scalars)[0];
+        if (nlong == 0) return SPC_OK;
+        int64_t* len = W.seg_len.as<int64_t>();
+        int64_t* base = W.seg_base.as<int64_t>();
+        int64_t* oidx = W.seg_idx.as<int64_t>();
+        SPC_LAUNCH(ctx, k_long_seg_prep, grid_for(nlong, kThreads, ctx->num_sms * 8), kThreads, 0,
+                   long_list, long_cnt, start, key, len, oidx);
+        SPC_TRY(scan_i64_i64(ctx, len, base, nlong));
+        SPC_CUDA(cudaMemcpyAsync(ctx->h_scalars, base + nlong, sizeof(int64_t),
+                                 cudaMemcpyDeviceToHost, ctx->stream));
+        SPC_CUDA(cudaStreamSynchronize(ctx->stream));
+        const int64_t total = ctx->h_scalars[0];
+        SPC_TRY(ensure(ctx, W.seg_terms, (size_t)(total + 1) * sizeof(WT)));
+        WT* terms = W.seg_terms.as<WT>();
+        SPC_LAUNCH(ctx, k_gather_long_terms<WT>, grid_for(total, kThreads, ctx->num_sms * 8),
+                   kThreads, 0, long_list, long_cnt, start, idx, w_und, base, terms);
+        const bool f32 = std::is_same<WT, float>::value;
+        SPC_TRY(seqtab_build(ctx, terms, f32, nlong, base, len, true, W.tab_s));
+        SPC_TRY(seqtab_full_sums(ctx, terms, f32, base, len, W.tab_s, oidx, out));
+        return SPC_OK;
+    }
+}
+
 template <class WT>
 spc_status contract_typed(spc_context* ctx, const GraphView& g, const int32_t* lift,
                           int64_t n_c, LevelBufs& lv) {
@@ -272,7 +345,6 @@ spc_status contract_typed(spc_context* ctx, const GraphView& g, const int32_t* l
                            m_intra, nb));
     int32_t* long_list = W.long_segs.as<int32_t>();
     int32_t* long_cnt = W.counters.as<int32_t>() + 9;
-    const int persist = ctx->num_sms * 2;
     if (m_intra > 0) {
         uint8_t* ihead = W.c_flag.as<uint8_t>() + (m + 1);  // intra flags are consumed
         int32_t* ihpos = W.c_head.as<int32_t>();
@@ -289,8 +361,8 @@ spc_status contract_typed(spc_context* ctx, const GraphView& g, const int32_t* l
         SPC_LAUNCH(ctx, (k_segsum_short<WT, Acc>), grid_for(n_runs, kThreads, maxb), kThreads, 0,
                    n_runs, istart, ival, ikey, W.w_und.as<WT>(), self_mass, long_list, long_cnt,
                    status);
-        SPC_LAUNCH(ctx, (k_segsum_long<WT, Acc>), persist, kThreads, 0, istart, ival, ikey,
-                   W.w_und.as<WT>(), self_mass, long_list, long_cnt, status);
+        SPC_TRY((long_segment_sums<WT, Acc>(ctx, istart, ival, ikey, W.w_und.as<WT>(),
+                                             self_mass)));
     }
     // coarse edges
     SPC_TRY(radix_sort_u64(ctx, ckey, cval, W.c_key2.as<uint64_t>(), W.c_val2.as<uint32_t>(),
@@ -320,9 +392,8 @@ spc_status contract_typed(spc_context* ctx, const GraphView& g, const int32_t* l
         SPC_LAUNCH(ctx, (k_segsum_short<WT, WT>), grid_for(m_c, kThreads, maxb), kThreads, 0,
                    m_c, seg, reinterpret_cast<const uint32_t*>(perm), nullptr, W.w_und.as<WT>(),
                    a_und, long_list, long_cnt, status);
-        SPC_LAUNCH(ctx, (k_segsum_long<WT, WT>), persist, kThreads, 0, seg,
-                   reinterpret_cast<const uint32_t*>(perm), nullptr, W.w_und.as<WT>(), a_und,
-                   long_list, long_cnt, status);
+        SPC_TRY((long_segment_sums<WT, WT>(ctx, seg, reinterpret_cast<const uint32_t*>(perm),
+                                            nullptr, W.w_und.as<WT>(), a_und)));
     }
     // coarse CSR
     int32_t* up_deg = W.up_deg.as<int32_t>();
@@ -360,18 +431,21 @@ template <class WT>
 spc_status forward_typed(spc_context* ctx, const int32_t* perm, const int32_t* seg, int64_t m_c,
                          const WT* w_und, WT* a_und) {
     if (m_c <= 0) return SPC_OK;
-    SPC_TRY(ensure(ctx, ctx->work.long_segs, (size_t)(m_c + 1) * 4));
-    SPC_TRY(ensure(ctx, ctx->work.counters, 64 * 4));
-    int32_t* long_list = ctx->work.long_segs.as<int32_t>();
-    int32_t* long_cnt = ctx->work.counters.as<int32_t>() + 9;
+    Work& W = ctx->work;
+    const size_t M = (size_t)m_c + 1;
+    SPC_TRY(ensure(ctx, W.long_segs, M * 4));
+    SPC_TRY(ensure(ctx, W.counters, 64 * 4));
+    SPC_TRY(ensure(ctx, W.seg_len, M * 8));
+    SPC_TRY(ensure(ctx, W.seg_base, (M + 1) * 8));
+    SPC_TRY(ensure(ctx, W.seg_idx, M * 8));
+    int32_t* long_list = W.long_segs.as<int32_t>();
+    int32_t* long_cnt = W.counters.as<int32_t>() + 9;
     SPC_CUDA(cudaMemsetAsync(long_cnt, 0, sizeof(int32_t), ctx->stream));
     SPC_LAUNCH(ctx, (k_segsum_short<WT, WT>), grid_for(m_c, kThreads, ctx->num_sms * 8), kThreads,
                0, m_c, seg, reinterpret_cast<const uint32_t*>(perm), nullptr, w_und, a_und,
                long_list, long_cnt, ctx->d_status);
-    SPC_LAUNCH(ctx, (k_segsum_long<WT, WT>), ctx->num_sms * 2, kThreads, 0, seg,
-               reinterpret_cast<const uint32_t*>(perm), nullptr, w_und, a_und, long_list,
-               long_cnt, ctx->d_status);
-    return SPC_OK;
+    return long_segment_sums<WT, WT>(ctx, seg, reinterpret_cast<const uint32_t*>(perm), nullptr,
+                                     w_und, a_und);
 }
 
 }  // namespace

@@ -72,12 +72,19 @@ struct LevelBufs {
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
 };
 
+// Device buffers of per-binade prefix tables over a batch of long sequences (spc_seqtab.cu).
+struct SeqTabBufs {
+    Buf eblo, nE, tsize, tcnt, tab_off, trip_off, P, T, csum, ctie, loff, mn, mx;
+    int64_t nseq = 0;
+};
+
 // Work buffers shared by all levels (sized for level 0).
 struct Work {
     Buf up_cnt, up_ptr, first_up, eu, ev, w_und, deg, p;       // S0-S2
-    Buf long_rows, hub_eblo, hub_size, hub_deg, hub_off, hub_eoff, tab_p, tab_t;  // hub rows
+    Buf long_rows, lr_base, lr_len, lr_idx, lr_eoff, heavy, seg_base, seg_len, seg_idx, seg_terms;
+    SeqTabBufs tab_w, tab_p, tab_s;                             // long sums: degrees, hubs, segments
     Buf parent, best_k[2], best_e[2], wl_e[2], wl_u[2], wl_v[2], msf;   // S5 MSF
-    Buf counters;                                               // small device ints
+    Buf counters, key_hist;                                     // small device ints
     Buf sel_key, sel_val, sel_key2, sel_val2, node_graph, seg_start, k_graph;  // selection
     Buf parent2, flag, ids;                                     // S6
     Buf c_key, c_val, c_key2, c_val2, c_flag, c_pos, c_head, cU, cV;    // S7
@@ -177,6 +184,16 @@ int64_t radix_raw_hist_elems(int64_t count);
 cudaError_t radix_sort_u64_raw(cudaStream_t stream, uint64_t* keys, uint32_t* vals,
                                uint64_t* keys_alt, uint32_t* vals_alt, int64_t count,
                                int end_bit, int32_t* hist, int32_t* scan_tmp);
+
+// Per-binade prefix tables over nseq long sequences terms[base[q] .. base[q] + len[q])
+// (binary32 when f32, else binary64; all pointers device).  `full`: tables cover every binade
+// the whole sum can reach; otherwise the binades of a running sum below 8 (scores).
+spc_status seqtab_build(spc_context* ctx, const void* terms, bool f32, int64_t nseq,
+                        const int64_t* base, const int64_t* len, bool full, SeqTabBufs& tb);
+// out[out_idx[q]] (or out[q]) = the left-to-right sum of sequence q, from its tables.
+spc_status seqtab_full_sums(spc_context* ctx, const void* terms, bool f32, const int64_t* base,
+                            const int64_t* len, const SeqTabBufs& tb, const int64_t* out_idx,
+                            void* out);
 
 // ---- steps (spc_score.cu, spc_merge.cu, spc_contract.cu) ----------------------------------
 

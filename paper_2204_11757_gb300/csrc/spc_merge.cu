@@ -9,8 +9,11 @@
 //      incident edge by atomicMin on the key (two phases for 64-bit scores: the score bits,
 //      then the edge id among the edges that tie), picked edges are forest edges (cut
 //      property) and are united in a lock-free union-find whose roots are always the smallest
-//      node id of their set; edges inside one component drop out of the work list, which is
-//      compacted with warp ballots.
+//      node id of their set; edges inside one component drop out of the work list.  Only a
+//      prefix of the score order takes part: Kruskal's first n - n_c merges all lie among the
+//      lightest edges, so the rounds run on the edges up to a threshold chosen from a score
+//      histogram to hold about 1.5 (n - n_c) edges; if that prefix's forest has fewer than
+//      n - n_c edges, the rounds are run again on every edge.
 //   2. The forest edges are compacted in eid order, radix-sorted by score (stable, so ties stay
 //      in eid order) -- per graph for batches -- and the first n - n_c of each graph are
 //      united in a second union-find.
@@ -77,58 +80,136 @@ template <> struct MinKey<unsigned int> {
     }
 };
 
-// warp-aggregated append of (e, ru, rv) to a work list
-__device__ __forceinline__ void wl_append(bool keep, int32_t e, int32_t ru, int32_t rv,
-                                          int32_t* wl_e, int32_t* wl_u, int32_t* wl_v,
-                                          int32_t* count) {
-    const unsigned lane = threadIdx.x & 31;
-    const unsigned act = __activemask();
-    const unsigned bal = __ballot_sync(act, keep);
-    if (bal == 0) return;
-    const int leader = __ffs(bal) - 1;
-    int32_t base = 0;
-    if ((int)lane == leader) base = atomicAdd(count, __popc(bal));
-    base = __shfl_sync(act, base, leader);
-    if (keep) {
-        const int32_t slot = base + __popc(bal & ((1u << lane) - 1u));
-        wl_e[slot] = e;
-        wl_u[slot] = ru;
-        wl_v[slot] = rv;
-    }
-}
-
 // Boruvka phase A: current roots of both ends; keep inter-component edges; lower the
-// component minima.  Round 0 reads every edge directly.
+// component minima.  Round 0 reads every edge directly and keeps only the score prefix
+// (key >> tau_shift <= *tau_top).  Each thread takes kMkItems edges per pass (their loads
+// overlap), and the survivors are appended with one global atomic per block and pass.
+constexpr int kMkItems = 4;
+
 template <class KT>
 __global__ void __launch_bounds__(kThreads)
 k_bv_minkey(int round0, int64_t m, const int32_t* __restrict__ in_count,
             const int32_t* __restrict__ wi_e, const int32_t* __restrict__ wi_u,
             const int32_t* __restrict__ wi_v, const int32_t* __restrict__ eu,
-            const int32_t* __restrict__ ev, const KT* __restrict__ key, int32_t* parent,
-            unsigned long long* best_k, int32_t* wo_e, int32_t* wo_u, int32_t* wo_v,
-            int32_t* out_count, uint32_t* status) {
+            const int32_t* __restrict__ ev, const KT* __restrict__ key, int tau_shift,
+            const uint32_t* __restrict__ tau_top, int32_t* parent, unsigned long long* best_k,
+            int32_t* wo_e, int32_t* wo_u, int32_t* wo_v, int32_t* out_count, uint32_t* status) {
+    __shared__ int32_t sh_wsum[kThreads / 32];
+    __shared__ int32_t sh_base;
     const int64_t cnt = round0 ? m : (int64_t)*in_count;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    // uniform trip count per warp so the ballot in wl_append sees whole warps
-    const int64_t warp_base = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) & ~(int64_t)31;
-    for (int64_t base = warp_base; base < cnt; base += stride) {
-        const int64_t i = base + (threadIdx.x & 31);
-        bool keep = false;
-        int32_t e = 0, ru = 0, rv = 0;
-        if (i < cnt) {
-            int32_t u, v;
-            if (round0) { e = (int32_t)i; u = eu[i]; v = ev[i]; }
-            else { e = wi_e[i]; u = wi_u[i]; v = wi_v[i]; }
-            ru = uf_find(parent, u, status);
-            rv = uf_find(parent, v, status);
-            keep = ru != rv;
-            if (keep) {
-                const unsigned long long pk = MinKey<KT>::pack(key[e], e);
-                atomicMin(best_k + ru, pk);
-                atomicMin(best_k + rv, pk);
+    const uint32_t top = tau_top ? *tau_top : 0xffffffffu;
+    const int64_t per = (int64_t)blockDim.x * kMkItems;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int64_t base = (int64_t)blockIdx.x * per; base < cnt; base += (int64_t)gridDim.x * per) {
+        int32_t e[kMkItems], u[kMkItems], v[kMkItems];
+        bool in[kMkItems];
+#pragma unroll
+        for (int it = 0; it < kMkItems; ++it) {
+            const int64_t i = base + (int64_t)it * blockDim.x + threadIdx.x;
+            in[it] = i < cnt;
+            e[it] = 0; u[it] = 0; v[it] = 0;
+            if (in[it]) {
+                if (round0) { e[it] = (int32_t)i; u[it] = eu[i]; v[it] = ev[i]; }
+                else { e[it] = wi_e[i]; u[it] = wi_u[i]; v[it] = wi_v[i]; }
             }
         }
-        wl_append(keep, e, ru, rv, wo_e, wo_u, wo_v, out_count);
+        KT k[kMkItems];
+#pragma unroll
+        for (int it = 0; it < kMkItems; ++it) {
+            k[it] = in[it] ? key[e[it]] : KT(0);
+            if (round0 && in[it] && (uint32_t)(k[it] >> tau_shift) > top) in[it] = false;
+        }
+        int32_t ru[kMkItems], rv[kMkItems];
+        int32_t nkeep = 0;
+#pragma unroll
+        for (int it = 0; it < kMkItems; ++it) {
+            ru[it] = in[it] ? (round0 ? u[it] : uf_find(parent, u[it], status)) : 0;
+            rv[it] = in[it] ? (round0 ? v[it] : uf_find(parent, v[it], status)) : 0;
+            in[it] = in[it] && ru[it] != rv[it];
+            if (in[it]) {
+                const unsigned long long pk = MinKey<KT>::pack(k[it], e[it]);
+                atomicMin(best_k + ru[it], pk);
+                atomicMin(best_k + rv[it], pk);
+                ++nkeep;
+            }
+        }
+        // block-wide exclusive prefix of the survivors, one global atomic per block and pass
+        int32_t incl = nkeep;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += t;
+        }
+        if (lane == 31) sh_wsum[warp] = incl;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int32_t tot = 0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+                const int32_t t = sh_wsum[w];
+                sh_wsum[w] = tot;
+                tot += t;
+            }
+            sh_base = tot ? atomicAdd(out_count, tot) : 0;
+        }
+        __syncthreads();
+        int32_t slot = sh_base + sh_wsum[warp] + incl - nkeep;
+#pragma unroll
+        for (int it = 0; it < kMkItems; ++it) {
+            if (in[it]) {
+                wo_e[slot] = e[it];
+                wo_u[slot] = ru[it];
+                wo_v[slot] = rv[it];
+                ++slot;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// histogram of the top 15 bits of the scores (bits below the sign), per block in shared memory
+template <class KT>
+__global__ void __launch_bounds__(1024)
+k_key_hist(int64_t m, const KT* __restrict__ key, int shift, uint32_t* __restrict__ hist) {
+    extern __shared__ uint32_t sh_hist[];
+    for (int b = threadIdx.x; b < 32768; b += blockDim.x) sh_hist[b] = 0;
+    __syncthreads();
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t b = (uint32_t)(key[i] >> shift) & 32767u;
+        const unsigned peers = __match_any_sync(__activemask(), b);
+        if ((int)(threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&sh_hist[b], __popc(peers));
+    }
+    __syncthreads();
+    for (int b = threadIdx.x; b < 32768; b += blockDim.x)
+        if (sh_hist[b]) atomicAdd(hist + b, sh_hist[b]);
+}
+
+// smallest bin whose cumulative count reaches `need` (all bins when need >= m)
+__global__ void __launch_bounds__(1024)
+k_pick_tau(const uint32_t* __restrict__ hist, int64_t need, uint32_t* __restrict__ tau_top) {
+    __shared__ unsigned long long sh[1024];
+    constexpr int kPer = 32768 / 1024;
+    unsigned long long loc = 0;
+    for (int j = 0; j < kPer; ++j) loc += hist[threadIdx.x * kPer + j];
+    sh[threadIdx.x] = loc;
+    __syncthreads();
+    for (int o = 1; o < 1024; o <<= 1) {  // inclusive scan (Hillis-Steele)
+        unsigned long long t = threadIdx.x >= (unsigned)o ? sh[threadIdx.x - o] : 0ull;
+        __syncthreads();
+        sh[threadIdx.x] += t;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *tau_top = 32767u;
+    __syncthreads();
+    unsigned long long run = threadIdx.x ? sh[threadIdx.x - 1] : 0ull;
+    if (run < (unsigned long long)need && sh[threadIdx.x] >= (unsigned long long)need) {
+        for (int j = 0; j < kPer; ++j) {
+            run += hist[threadIdx.x * kPer + j];
+            if (run >= (unsigned long long)need) {
+                *tau_top = (uint32_t)(threadIdx.x * kPer + j);
+                break;
+            }
+        }
     }
 }
 
@@ -301,59 +382,86 @@ spc_status select_typed(spc_context* ctx, const GraphView& g, const KT* key,
     int32_t* counters = W.counters.as<int32_t>();  // [0..1] work-list counts, [2] warn flag
     const bool batched = sa.B > 1 || sa.d_graph_ptr != nullptr;
 
-    SPC_LAUNCH(ctx, k_iota, grid_for(n, kThreads, maxb), kThreads, 0, parent, n);
-    if (merged) SPC_CUDA(cudaMemsetAsync(merged, 0, (size_t)m, ctx->stream));
-    SPC_CUDA(cudaMemsetAsync(W.msf.p, 0, (size_t)(m + 1), ctx->stream));
-    SPC_CUDA(cudaMemsetAsync(W.best_k[0].p, 0xff, (size_t)n * 8, ctx->stream));
-    SPC_CUDA(cudaMemsetAsync(W.best_k[1].p, 0xff, (size_t)n * 8, ctx->stream));
-    if (MinKey<KT>::two_phase) {
-        SPC_CUDA(cudaMemsetAsync(W.best_e[0].p, 0x7f, (size_t)n * 4, ctx->stream));
-        SPC_CUDA(cudaMemsetAsync(W.best_e[1].p, 0x7f, (size_t)n * 4, ctx->stream));
-    }
-    // ---- 1. Boruvka minimum spanning forest -------------------------------------------
-    int64_t cur = m;
-    for (int round = 0; cur > 0; ++round) {
-        const int in = round & 1, out = in ^ 1;
-        const int par = round & 1;
-        SPC_CUDA(cudaMemsetAsync(counters + out, 0, sizeof(int32_t), ctx->stream));
-        SPC_LAUNCH(ctx, k_bv_minkey<KT>, grid_for(cur, kThreads, maxb), kThreads, 0,
-                   round == 0 ? 1 : 0, m, counters + in, W.wl_e[in].as<int32_t>(),
-                   W.wl_u[in].as<int32_t>(), W.wl_v[in].as<int32_t>(), W.eu.as<int32_t>(),
-                   W.ev.as<int32_t>(), key, parent, W.best_k[par].as<unsigned long long>(),
-                   W.wl_e[out].as<int32_t>(), W.wl_u[out].as<int32_t>(),
-                   W.wl_v[out].as<int32_t>(), counters + out, status);
-        if (MinKey<KT>::two_phase) {
-            SPC_LAUNCH(ctx, k_bv_tiebreak, grid_for(cur, kThreads, maxb), kThreads, 0,
-                       counters + out, W.wl_e[out].as<int32_t>(), W.wl_u[out].as<int32_t>(),
-                       W.wl_v[out].as<int32_t>(),
-                       reinterpret_cast<const unsigned long long*>(key),
-                       W.best_k[par].as<unsigned long long>(), W.best_e[par].as<int32_t>());
+    // ---- 0. score prefix (single graph): the lightest ~1.5 (n - n_c) edges ------------------
+    const int64_t k_need = batched ? 0 : (n - sa.target > 0 ? n - sa.target : 0);
+    const int tau_shift = sizeof(KT) == 8 ? 48 : 16;
+    uint32_t* tau_top = reinterpret_cast<uint32_t*>(counters + 12);
+    bool use_prefix = !batched && m > 65536 && k_need > 0 && (k_need + k_need / 2) < m;
+    if (use_prefix) {
+        SPC_TRY(ensure(ctx, W.key_hist, 32768 * 4));
+        SPC_CUDA(cudaMemsetAsync(W.key_hist.p, 0, 32768 * 4, ctx->stream));
+        static bool attr = false;
+        if (!attr) {
+            SPC_CUDA(cudaFuncSetAttribute(k_key_hist<KT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          32768 * 4));
+            attr = true;
         }
-        SPC_LAUNCH(ctx, k_bv_hook<KT>, grid_for(cur, kThreads, maxb), kThreads, 0,
-                   counters + out, W.wl_e[out].as<int32_t>(), W.wl_u[out].as<int32_t>(),
-                   W.wl_v[out].as<int32_t>(), W.best_k[par].as<unsigned long long>(),
-                   W.best_e[par].as<int32_t>(), W.best_k[par ^ 1].as<unsigned long long>(),
-                   W.best_e[par ^ 1].as<int32_t>(), parent, W.msf.as<uint8_t>(), status);
-        // next work-list size (host loop; the captured path keeps it on the device)
-        SPC_CUDA(cudaMemcpyAsync(ctx->h_scalars, counters + out, sizeof(int32_t),
-                                 cudaMemcpyDeviceToHost, ctx->stream));
+        SPC_LAUNCH(ctx, k_key_hist<KT>, ctx->num_sms, 1024, 32768 * 4, m, key, tau_shift,
+                   W.key_hist.as<uint32_t>());
+        SPC_LAUNCH(ctx, k_pick_tau, 1, 1024, 0, W.key_hist.as<uint32_t>(),
+                   k_need + k_need / 2, tau_top);
+    }
+    int32_t* pos = W.c_pos.as<int32_t>();
+    int64_t n_msf = 0;
+    for (int attempt = 0; attempt < 2; ++attempt) {
+        SPC_LAUNCH(ctx, k_iota, grid_for(n, kThreads, maxb), kThreads, 0, parent, n);
+        if (merged) SPC_CUDA(cudaMemsetAsync(merged, 0, (size_t)m, ctx->stream));
+        SPC_CUDA(cudaMemsetAsync(W.msf.p, 0, (size_t)(m + 1), ctx->stream));
+        SPC_CUDA(cudaMemsetAsync(W.best_k[0].p, 0xff, (size_t)n * 8, ctx->stream));
+        SPC_CUDA(cudaMemsetAsync(W.best_k[1].p, 0xff, (size_t)n * 8, ctx->stream));
+        if (MinKey<KT>::two_phase) {
+            SPC_CUDA(cudaMemsetAsync(W.best_e[0].p, 0x7f, (size_t)n * 4, ctx->stream));
+            SPC_CUDA(cudaMemsetAsync(W.best_e[1].p, 0x7f, (size_t)n * 4, ctx->stream));
+        }
+        // ---- 1. Boruvka minimum spanning forest (of the prefix) ---------------------------
+        int64_t cur = m;
+        for (int round = 0; cur > 0; ++round) {
+            const int in = round & 1, out = in ^ 1;
+            const int par = round & 1;
+            SPC_CUDA(cudaMemsetAsync(counters + out, 0, sizeof(int32_t), ctx->stream));
+            SPC_LAUNCH(ctx, k_bv_minkey<KT>,
+                       grid_for(cur, kThreads * kMkItems, maxb), kThreads, 0,
+                       round == 0 ? 1 : 0, m, counters + in, W.wl_e[in].as<int32_t>(),
+                       W.wl_u[in].as<int32_t>(), W.wl_v[in].as<int32_t>(), W.eu.as<int32_t>(),
+                       W.ev.as<int32_t>(), key, tau_shift, use_prefix ? tau_top : nullptr, parent,
+                       W.best_k[par].as<unsigned long long>(), W.wl_e[out].as<int32_t>(),
+                       W.wl_u[out].as<int32_t>(), W.wl_v[out].as<int32_t>(), counters + out,
+                       status);
+            if (MinKey<KT>::two_phase) {
+                SPC_LAUNCH(ctx, k_bv_tiebreak, grid_for(cur, kThreads, maxb), kThreads, 0,
+                           counters + out, W.wl_e[out].as<int32_t>(), W.wl_u[out].as<int32_t>(),
+                           W.wl_v[out].as<int32_t>(),
+                           reinterpret_cast<const unsigned long long*>(key),
+                           W.best_k[par].as<unsigned long long>(), W.best_e[par].as<int32_t>());
+            }
+            SPC_LAUNCH(ctx, k_bv_hook<KT>, grid_for(cur, kThreads, maxb), kThreads, 0,
+                       counters + out, W.wl_e[out].as<int32_t>(), W.wl_u[out].as<int32_t>(),
+                       W.wl_v[out].as<int32_t>(), W.best_k[par].as<unsigned long long>(),
+                       W.best_e[par].as<int32_t>(), W.best_k[par ^ 1].as<unsigned long long>(),
+                       W.best_e[par ^ 1].as<int32_t>(), parent, W.msf.as<uint8_t>(), status);
+            // next work-list size (host loop; the captured path keeps it on the device)
+            SPC_CUDA(cudaMemcpyAsync(ctx->h_scalars, counters + out, sizeof(int32_t),
+                                     cudaMemcpyDeviceToHost, ctx->stream));
+            SPC_CUDA(cudaStreamSynchronize(ctx->stream));
+            cur = *reinterpret_cast<int32_t*>(ctx->h_scalars);
+            // every round at least halves the components that still have edges
+            if (round > 64) return SPC_ERR_TIMEOUT;
+            // slot `out` (list and count) is the next round's input
+        }
+        SPC_TRY(scan_flags_u8(ctx, W.msf.as<uint8_t>(), pos, m));
+        SPC_CUDA(cudaMemcpyAsync(ctx->h_scalars, pos + m, sizeof(int32_t), cudaMemcpyDeviceToHost,
+                                 ctx->stream));
         SPC_CUDA(cudaStreamSynchronize(ctx->stream));
-        cur = *reinterpret_cast<int32_t*>(ctx->h_scalars);
-        // every round at least halves the components that still have edges
-        if (round > 64) return SPC_ERR_TIMEOUT;
-        // slot `out` (list and count) is the next round's input
+        n_msf = *reinterpret_cast<int32_t*>(ctx->h_scalars);
+        // the prefix's forest holds Kruskal's first n_msf merges; enough when >= n - n_c
+        if (!use_prefix || n_msf >= k_need) break;
+        use_prefix = false;
     }
     // ---- 2. lightest forest edges per graph ---------------------------------------------
-    int32_t* pos = W.c_pos.as<int32_t>();
-    SPC_TRY(scan_flags_u8(ctx, W.msf.as<uint8_t>(), pos, m));
     KT* sk = W.sel_key.as<KT>();
     uint32_t* sv = W.sel_val.as<uint32_t>();
     SPC_LAUNCH(ctx, k_compact_msf<KT>, grid_for(m, kThreads, maxb), kThreads, 0, m,
                W.msf.as<uint8_t>(), pos, key, sk, sv);
-    SPC_CUDA(cudaMemcpyAsync(ctx->h_scalars, pos + m, sizeof(int32_t), cudaMemcpyDeviceToHost,
-                             ctx->stream));
-    SPC_CUDA(cudaStreamSynchronize(ctx->stream));
-    const int64_t n_msf = *reinterpret_cast<int32_t*>(ctx->h_scalars);
     const int key_bits = sizeof(KT) == 8 ? 63 : 31;  // scores are >= +0: sign bit clear
     if (sizeof(KT) == 8) {
         SPC_TRY(radix_sort_u64(ctx, reinterpret_cast<uint64_t*>(sk), sv,

@@ -113,8 +113,62 @@ __global__ void k_copy_total(const T* total, Out* dst) {
     if (threadIdx.x == 0) *dst = (Out)*total;
 }
 
+// small inputs: one CTA scans everything in chunks of 4 items per thread with a carry, and
+// writes the total at out[n] (one launch instead of three plus a copy)
+constexpr int kSmallThreads = 1024;
+constexpr int64_t kSmallMax = 16384;
+
+template <class In, class T, class Out>
+__global__ void __launch_bounds__(kSmallThreads) k_scan_small(const In* in, int64_t n, Out* out) {
+    __shared__ T wsum[kSmallThreads / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    T carry = 0;
+    for (int64_t base = 0; base < n; base += (int64_t)kSmallThreads * 4) {
+        T v[4];
+        T run = 0;
+        const int64_t i0 = base + (int64_t)threadIdx.x * 4;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            v[j] = (i0 + j < n) ? (T)in[i0 + j] : T(0);
+            run += v[j];
+        }
+        T incl = run;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            T t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += t;
+        }
+        if (lane == 31) wsum[warp] = incl;
+        __syncthreads();
+        if (warp == 0) {
+            T s = wsum[lane];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                T t = __shfl_up_sync(0xffffffffu, s, o);
+                if (lane >= o) s += t;
+            }
+            wsum[lane] = s;
+        }
+        __syncthreads();
+        T pre = carry + (warp > 0 ? wsum[warp - 1] : T(0)) + incl - run;
+        const T tot = wsum[kSmallThreads / 32 - 1];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            if (i0 + j < n) out[i0 + j] = (Out)pre;
+            pre += v[j];
+        }
+        carry += tot;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[n] = (Out)carry;
+}
+
 template <class In, class T, class Out>
 spc_status scan_impl(spc_context* ctx, const In* in, Out* out, int64_t n) {
+    if (n <= kSmallMax) {
+        SPC_LAUNCH(ctx, (k_scan_small<In, T, Out>), 1, kSmallThreads, 0, in, n, out);
+        return SPC_OK;
+    }
     const int64_t nt = (n + STILE - 1) / STILE;
     const size_t need = (size_t)(nt + 1) * sizeof(T) + 256;
     SPC_TRY(ensure(ctx, ctx->work.scan_tmp, need));

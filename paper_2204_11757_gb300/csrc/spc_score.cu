@@ -97,16 +97,17 @@ k_rows_degree(int64_t n, int64_t nnz, const int64_t* __restrict__ rowptr,
     }
 }
 
-// S0 + S1 for rows longer than kLongRow: one CTA per row.  The checks and the counts run over
-// the entries in parallel; the degree is the same left-to-right sum, evaluated exactly by
-// cta_seqsum (or an int64 reduction for integer weights).
+// S0 + S1 for rows longer than kLongRow: one CTA per row checks the entries and counts them in
+// parallel, and records the row as a sequence (base, length) for the exact degree sum, which
+// the per-binade tables evaluate (spc_seqtab.cu); integer degrees are a plain reduction.
 template <class WT>
 __global__ void __launch_bounds__(kThreads)
-k_long_rows_degree(int64_t n, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
-                   const WT* __restrict__ w, int validate, const int32_t* __restrict__ long_rows,
-                   const int32_t* __restrict__ long_count,
-                   typename Tr<WT>::Acc* __restrict__ deg, int32_t* __restrict__ up_cnt,
-                   int32_t* __restrict__ nlow_out, uint32_t* __restrict__ status) {
+k_long_rows_check(int64_t n, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                  const WT* __restrict__ w, int validate, const int32_t* __restrict__ long_rows,
+                  const int32_t* __restrict__ long_count, typename Tr<WT>::Acc* __restrict__ deg,
+                  int32_t* __restrict__ up_cnt, int32_t* __restrict__ nlow_out,
+                  int64_t* __restrict__ lr_base, int64_t* __restrict__ lr_len,
+                  int64_t* __restrict__ lr_idx, uint32_t* __restrict__ status) {
     __shared__ int32_t sh_nlow;
     const int32_t cnt = *long_count;
     for (int32_t i = blockIdx.x; i < cnt; i += gridDim.x) {
@@ -127,62 +128,64 @@ k_long_rows_degree(int64_t n, const int64_t* __restrict__ rowptr, const int32_t*
         }
         if (bits) atomicOr(status, bits);
         if (nl) atomicAdd(&sh_nlow, nl);
-        typename Tr<WT>::Acc d;
         if constexpr (std::is_same<WT, int32_t>::value) {
-            d = cta_sum_i64(r1 - r0, [&](int64_t k) { return (long long)w[r0 + k]; });
-        } else {
-            d = cta_seqsum<8>(WT(0), r1 - r0, [&](int64_t k) { return w[r0 + k]; });
+            const long long d = cta_sum_i64(r1 - r0, [&](int64_t k) { return (long long)w[r0 + k]; });
+            if (threadIdx.x == 0) deg[x] = d;
         }
         __syncthreads();
         if (threadIdx.x == 0) {
-            deg[x] = d;
             nlow_out[x] = sh_nlow;
             up_cnt[x] = (int32_t)(r1 - r0) - sh_nlow;
+            lr_base[i] = r0;
+            lr_len[i] = r1 - r0;
+            lr_idx[i] = x;
         }
         __syncthreads();
     }
 }
 
-// S2 + edge list for rows longer than kLongRow: one CTA per row, threads over the entries.
+// S2 + edge list for rows longer than kLongRow: one thread per entry, flat over all long rows.
 template <class WT>
 __global__ void __launch_bounds__(kThreads)
 k_long_rows_edges(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
                   const WT* __restrict__ w, int validate,
                   const typename Tr<WT>::Acc* __restrict__ deg, const int32_t* __restrict__ nlow,
                   const int32_t* __restrict__ up_ptr, const int32_t* __restrict__ long_rows,
-                  const int32_t* __restrict__ long_count, typename Tr<WT>::P* __restrict__ p,
-                  int32_t* __restrict__ eu, int32_t* __restrict__ ev, WT* __restrict__ w_und,
-                  uint32_t* __restrict__ status) {
+                  const int32_t* __restrict__ long_count, const int64_t* __restrict__ lr_eoff,
+                  typename Tr<WT>::P* __restrict__ p, int32_t* __restrict__ eu,
+                  int32_t* __restrict__ ev, WT* __restrict__ w_und, uint32_t* __restrict__ status) {
     if (*status) return;
     const int32_t cnt = *long_count;
-    for (int32_t i = blockIdx.x; i < cnt; i += gridDim.x) {
-        const int64_t x = long_rows[i];
-        const int64_t r0 = rowptr[x], r1 = rowptr[x + 1];
-        const typename Tr<WT>::Acc d = deg[x];
-        const int64_t ubase = (int64_t)up_ptr[x] - (r0 + nlow[x]);
-        uint32_t bits = 0;
-        for (int64_t j = r0 + threadIdx.x; j < r1; j += blockDim.x) {
-            const int32_t y = col[j];
-            const WT wj = w[j];
-            p[j] = Tr<WT>::div(wj, d);
-            if (validate) {
-                int64_t lo = rowptr[y], hi = rowptr[y + 1];
-                while (lo < hi) {
-                    int64_t mid = (lo + hi) >> 1;
-                    if ((int64_t)col[mid] < x) lo = mid + 1; else hi = mid;
-                }
-                if (lo >= rowptr[y + 1] || (int64_t)col[lo] != x ||
-                    Tr<WT>::bits(w[lo]) != Tr<WT>::bits(wj))
-                    bits |= DEV_NOT_SYMMETRIC;
-            }
-            if ((int64_t)y > x) {
-                const int64_t e = ubase + j;
-                eu[e] = (int32_t)x;
-                ev[e] = y;
-                w_und[e] = wj;
-            }
+    const int64_t total = lr_eoff[cnt];
+    for (int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; f < total;
+         f += (int64_t)gridDim.x * blockDim.x) {
+        int32_t lo = 0, hi = cnt - 1;
+        while (lo < hi) {
+            const int32_t mid = (lo + hi + 1) >> 1;
+            if (lr_eoff[mid] <= f) lo = mid; else hi = mid - 1;
         }
-        if (bits) atomicOr(status, bits);
+        const int64_t x = long_rows[lo];
+        const int64_t r0 = rowptr[x];
+        const int64_t j = r0 + (f - lr_eoff[lo]);
+        const int32_t y = col[j];
+        const WT wj = w[j];
+        p[j] = Tr<WT>::div(wj, deg[x]);
+        if (validate) {
+            int64_t l2 = rowptr[y], h2 = rowptr[y + 1];
+            while (l2 < h2) {
+                int64_t mid = (l2 + h2) >> 1;
+                if ((int64_t)col[mid] < x) l2 = mid + 1; else h2 = mid;
+            }
+            if (l2 >= rowptr[y + 1] || (int64_t)col[l2] != x ||
+                Tr<WT>::bits(w[l2]) != Tr<WT>::bits(wj))
+                atomicOr(status, DEV_NOT_SYMMETRIC);
+        }
+        if ((int64_t)y > x) {
+            const int64_t e = (int64_t)up_ptr[x] + (j - (r0 + nlow[x]));
+            eu[e] = (int32_t)x;
+            ev[e] = y;
+            w_und[e] = wj;
+        }
     }
 }
 
@@ -332,178 +335,46 @@ k_score_warp_row(int64_t n, const int64_t* __restrict__ rowptr, const int32_t* _
 // An edge with an end point of more than kLongRow entries is scored from the larger row H (its
 // "hub"; ties go to the smaller id).  The score is the same left-to-right sum over the union of
 // the two rows, which reads as runs of plain H terms p_Hx (x not in the other row v) separated
-// by the few coordinates of v's row (an extra term p_vx, or |p_Hx - p_vx| where both rows have
-// x).  The runs are evaluated exactly with per-grid prefix tables of H's row: for every binade
-// exponent eb the running sum can have, P_eb[k] = sum_{t<k} round(p_Ht / grid(eb)) and
-// T_eb[k] = number of half-grid ties among the first k terms (see spc_seqsum.cuh).
+// by the coordinates of v's row ("specials": an extra term p_vx, or |p_Hx - p_vx| where both
+// rows have x).  Runs are evaluated exactly from per-binade prefix tables of H's row.
 
-// per hub: the exponent range of its tables and their size
-template <class PT>
-__global__ void __launch_bounds__(kThreads)
-k_hub_meta(const int64_t* __restrict__ rowptr, const PT* __restrict__ p,
-           const int32_t* __restrict__ long_rows, const int32_t* __restrict__ long_count,
-           int32_t* __restrict__ hub_eblo, int64_t* __restrict__ hub_size,
-           int64_t* __restrict__ hub_deg) {
-    __shared__ unsigned long long sh_min;
-    const int32_t cnt = *long_count;
-    for (int32_t i = blockIdx.x; i < cnt; i += gridDim.x) {
-        const int64_t H = long_rows[i];
-        const int64_t r0 = rowptr[H], r1 = rowptr[H + 1];
-        if (threadIdx.x == 0) sh_min = ~0ull;
-        __syncthreads();
-        unsigned long long mn = ~0ull;
-        for (int64_t j = r0 + threadIdx.x; j < r1; j += blockDim.x) {
-            unsigned long long b = FB<PT>::bits(p[j]);
-            mn = b < mn ? b : mn;
-        }
-        atomicMin(&sh_min, mn);
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            int eb = (int)(sh_min >> FB<PT>::kMant);
-            const int lo_cap = FB<PT>::kEbHi - 63;
-            if (eb < lo_cap) eb = lo_cap;
-            if (eb < 1) eb = 1;
-            const int nE = FB<PT>::kEbHi - eb + 1;
-            hub_eblo[i] = eb;
-            hub_deg[i] = r1 - r0;
-            hub_size[i] = (int64_t)nE * (r1 - r0 + 1);
-        }
-        __syncthreads();
-    }
-}
+constexpr int kHeavySpecials = 32;  // edges whose other row is longer go to the warp kernel
 
-// tables: one CTA per (hub, grid); exclusive prefix over the row with a running carry
-template <class PT>
-__global__ void __launch_bounds__(kThreads)
-k_hub_tables(const int64_t* __restrict__ rowptr, const PT* __restrict__ p,
-             const int32_t* __restrict__ long_rows, const int32_t* __restrict__ long_count,
-             const int32_t* __restrict__ hub_eblo, const int64_t* __restrict__ hub_off,
-             unsigned long long* __restrict__ tabP, int32_t* __restrict__ tabT) {
-    __shared__ unsigned long long sh_w[kThreads / 32];
-    __shared__ int32_t sh_t[kThreads / 32];
-    const int32_t cnt = *long_count;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int64_t q = blockIdx.x; q < (int64_t)cnt * 64; q += gridDim.x) {
-        const int32_t i = (int32_t)(q >> 6);
-        const int e = (int)(q & 63);
-        const int eblo = hub_eblo[i];
-        const int nE = FB<PT>::kEbHi - eblo + 1;
-        if (e >= nE) continue;
-        const int eb = eblo + e;
-        const int64_t H = long_rows[i];
-        const int64_t r0 = rowptr[H], d = rowptr[H + 1] - r0;
-        unsigned long long* P = tabP + hub_off[i] + (int64_t)e * (d + 1);
-        int32_t* T = tabT + hub_off[i] + (int64_t)e * (d + 1);
-        if (threadIdx.x == 0) { P[0] = 0; T[0] = 0; }
-        unsigned long long carry = 0;
-        int32_t tcarry = 0;
-        for (int64_t base = 0; base < d; base += blockDim.x) {
-            const int64_t k = base + threadIdx.x;
-            bool tie = false;
-            unsigned long long r = 0;
-            if (k < d) r = grid_units<PT>(p[r0 + k], eb, &tie);
-            int32_t tv = tie ? 1 : 0;
-            unsigned long long v = r;
-            int32_t tt = tv;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                unsigned long long a = __shfl_up_sync(0xffffffffu, v, o);
-                int32_t b = __shfl_up_sync(0xffffffffu, tt, o);
-                if (lane >= o) { v = sat_add(v, a); tt += b; }
-            }
-            if (lane == 31) { sh_w[warp] = v; sh_t[warp] = tt; }
-            __syncthreads();
-            unsigned long long wpre = 0, wtot = 0;
-            int32_t tpre = 0, ttot = 0;
-            for (int w2 = 0; w2 < (int)(blockDim.x >> 5); ++w2) {
-                if (w2 < warp) { wpre = sat_add(wpre, sh_w[w2]); tpre += sh_t[w2]; }
-                wtot = sat_add(wtot, sh_w[w2]);
-                ttot += sh_t[w2];
-            }
-            if (k < d) {
-                P[k + 1] = sat_add(carry, sat_add(wpre, v));
-                T[k + 1] = tcarry + tpre + tt;
-            }
-            carry = sat_add(carry, wtot);
-            tcarry += ttot;
-            __syncthreads();
-        }
-    }
-}
-
-// the sum continued over the plain terms pH[a, b) of the hub row, from running value s
-template <class PT>
-__device__ PT hub_run(PT s, int64_t a, int64_t b, const PT* __restrict__ pH,
-                      const unsigned long long* __restrict__ P, const int32_t* __restrict__ T,
-                      int eblo, int64_t d1) {
-    const int nE = FB<PT>::kEbHi - eblo + 1;
-    while (a < b) {
-        if (s == PT(0)) { s = pH[a++]; continue; }
-        const unsigned long long sb = FB<PT>::bits(s);
-        const int eb = (int)(sb >> FB<PT>::kMant);
-        const int e = eb - eblo;
-        if (eb == 0 || e < 0 || e >= nE) { s = FB<PT>::add(s, pH[a++]); continue; }
-        const unsigned long long* Pe = P + (int64_t)e * d1;
-        const int32_t* Te = T + (int64_t)e * d1;
-        const unsigned long long base = Pe[a];
-        if (base >= kSat - (1ull << 55)) { s = FB<PT>::add(s, pH[a++]); continue; }
-        const unsigned long long S = (sb & ((1ull << FB<PT>::kMant) - 1ull)) | (1ull << FB<PT>::kMant);
-        const unsigned long long lim = (1ull << (FB<PT>::kMant + 1)) - S;
-        // largest k in [a, b] whose prefix stays on this grid
-        int64_t lo = a, hi = b;
-        while (lo < hi) {
-            const int64_t mid = (lo + hi + 1) >> 1;
-            if (Pe[mid] - base <= lim) lo = mid; else hi = mid - 1;
-        }
-        int64_t k = lo;
-        const int32_t ta = Te[a];
-        if (Te[k] > ta) {  // a half-grid tie inside: stop at the first one
-            int64_t l2 = a, h2 = k - 1;
-            while (l2 < h2) {
-                const int64_t mid = (l2 + h2) >> 1;
-                if (Te[mid + 1] > ta) h2 = mid; else l2 = mid + 1;
-            }
-            k = l2;
-        }
-        s = from_units<PT>(S + (Pe[k] - base), eb);
-        a = k;
-        if (a < b) s = FB<PT>::add(s, pH[a++]);  // binade crossing or tie: one native step
-    }
-    return s;
-}
-
-// S3 for hub edges: one thread per entry (H, v) of a hub row, flat over all hubs
+// light hub edges: one thread per entry (H, v) of a hub row, flat over all hubs
 template <class PT, class KT>
 __global__ void __launch_bounds__(kThreads)
 k_score_hub(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
             const PT* __restrict__ p, const int32_t* __restrict__ up_ptr,
             const int32_t* __restrict__ nlow, const int32_t* __restrict__ long_rows,
-            const int32_t* __restrict__ long_count, const int64_t* __restrict__ hub_eoff,
-            const int32_t* __restrict__ hub_eblo, const int64_t* __restrict__ hub_off,
-            const unsigned long long* __restrict__ tabP, const int32_t* __restrict__ tabT,
-            KT* __restrict__ score, const uint32_t* status) {
+            const int32_t* __restrict__ long_count, const int64_t* __restrict__ lr_eoff,
+            SeqTabView tab, KT* __restrict__ score, int32_t* __restrict__ heavy,
+            int32_t* __restrict__ heavy_count, const uint32_t* status) {
     if (*status) return;
     const int32_t cnt = *long_count;
-    const int64_t total = hub_eoff[cnt];
+    const int64_t total = lr_eoff[cnt];
     for (int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; f < total;
          f += (int64_t)gridDim.x * blockDim.x) {
         int32_t lo = 0, hi = cnt - 1;  // hub of flat entry f
         while (lo < hi) {
             const int32_t mid = (lo + hi + 1) >> 1;
-            if (hub_eoff[mid] <= f) lo = mid; else hi = mid - 1;
+            if (lr_eoff[mid] <= f) lo = mid; else hi = mid - 1;
         }
         const int32_t i = lo;
         const int64_t H = long_rows[i];
         const int64_t rH = rowptr[H], dH = rowptr[H + 1] - rH;
-        const int64_t k = f - hub_eoff[i];
+        const int64_t k = f - lr_eoff[i];
         const int64_t v = col[rH + k];
         const int64_t rv = rowptr[v], dv = rowptr[v + 1] - rv;
         if (dv > dH || (dv == dH && v < H)) continue;  // v's row is the hub of this edge
+        if (dv > kHeavySpecials) {                       // many specials: warp kernel
+            heavy[atomicAdd(heavy_count, 1)] = (int32_t)f;
+            continue;
+        }
         const int32_t* cH = col + rH;
         const PT* pH = p + rH;
-        const unsigned long long* P = tabP + hub_off[i];
-        const int32_t* T = tabT + hub_off[i];
-        const int eblo = hub_eblo[i];
+        const unsigned long long* P = tab.P + tab.tab_off[i];
+        const int32_t* T = tab.T + tab.tab_off[i];
+        const int eblo = tab.eblo[i], nE = tab.nE[i];
         PT s = PT(0);
         int64_t a = 0;
         int64_t jH = -1;  // position of H in v's row
@@ -515,7 +386,7 @@ k_score_hub(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
                 const int64_t mid = (l2 + h2) >> 1;
                 if (cH[mid] < x) l2 = mid + 1; else h2 = mid;
             }
-            s = hub_run<PT>(s, a, l2, pH, P, T, eblo, dH + 1);
+            s = tab_run<PT>(s, a, l2, pH, P, T, eblo, nE, dH + 1);
             PT t;
             if (l2 < dH && cH[l2] == x) {
                 t = p_absdiff(pH[l2], p[rv + j]);
@@ -526,10 +397,165 @@ k_score_hub(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
             }
             s = p_add(s, t);
         }
-        s = hub_run<PT>(s, a, dH, pH, P, T, eblo, dH + 1);
+        s = tab_run<PT>(s, a, dH, pH, P, T, eblo, nE, dH + 1);
         const int64_t e = (H < v) ? (int64_t)up_ptr[H] + (k - nlow[H])
                                   : (int64_t)up_ptr[v] + (jH - nlow[v]);
         score[e] = key_bits(s);
+    }
+}
+
+// heavy hub edges: one warp per edge.  Lanes take 32 specials at a time: each finds its
+// position in H's row; then, inside the running sum's binade, the whole group advances as one
+// integer prefix sum over (run before special j, special j) pairs -- the run's increment read
+// from H's tables, the special's as its grid-rounded value.  The first pair that crosses the
+// binade or holds a tie is finished exactly (tab_run / one native add) and the group restarts.
+template <class PT, class KT>
+__global__ void __launch_bounds__(kThreads)
+k_score_hub_heavy(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                  const PT* __restrict__ p, const int32_t* __restrict__ up_ptr,
+                  const int32_t* __restrict__ nlow, const int32_t* __restrict__ long_rows,
+                  const int32_t* __restrict__ long_count, const int64_t* __restrict__ lr_eoff,
+                  SeqTabView tab, const int32_t* __restrict__ heavy,
+                  const int32_t* __restrict__ heavy_count, KT* __restrict__ score,
+                  const uint32_t* status) {
+    if (*status) return;
+    const int lane = threadIdx.x & 31;
+    const int32_t cnt = *long_count;
+    const int32_t nheavy = *heavy_count;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t hq = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); hq < nheavy;
+         hq += warps) {
+        const int64_t f = heavy[hq];
+        int32_t lo = 0, hi = cnt - 1;
+        while (lo < hi) {
+            const int32_t mid = (lo + hi + 1) >> 1;
+            if (lr_eoff[mid] <= f) lo = mid; else hi = mid - 1;
+        }
+        const int32_t i = lo;
+        const int64_t H = long_rows[i];
+        const int64_t rH = rowptr[H], dH = rowptr[H + 1] - rH;
+        const int64_t k = f - lr_eoff[i];
+        const int64_t v = col[rH + k];
+        const int64_t rv = rowptr[v], dv = rowptr[v + 1] - rv;
+        const int32_t* cH = col + rH;
+        const PT* pH = p + rH;
+        const unsigned long long* P = tab.P + tab.tab_off[i];
+        const int32_t* T = tab.T + tab.tab_off[i];
+        const int eblo = tab.eblo[i], nE = tab.nE[i];
+        const int64_t d1 = dH + 1;
+        PT s = PT(0);
+        int64_t a = 0;      // next unread position of H's row
+        int64_t jH = -1;
+        int64_t j0 = 0;     // next special
+        while (j0 < dv) {
+            const int64_t j = j0 + lane;
+            const bool act = j < dv;
+            int32_t x = 0;
+            int64_t pos = dH;
+            bool common = false;
+            PT t = PT(0);
+            if (act) {
+                x = col[rv + j];
+                int64_t l2 = a, h2 = dH;
+                while (l2 < h2) {
+                    const int64_t mid = (l2 + h2) >> 1;
+                    if (cH[mid] < x) l2 = mid + 1; else h2 = mid;
+                }
+                pos = l2;
+                common = pos < dH && cH[pos] == x;
+                t = common ? p_absdiff(pH[pos], p[rv + j]) : p[rv + j];
+                if ((int64_t)x == H) jH = j;
+            }
+            // start of the run before special j: after special j-1 (or `a` for the first)
+            int64_t after = pos + (common ? 1 : 0);
+            int64_t start = __shfl_up_sync(0xffffffffu, after, 1);
+            if (lane == 0) start = a;
+            const int nact = (dv - j0) < 32 ? (int)(dv - j0) : 32;
+            // advance through the group, restarting after every exact step
+            int g = 0;  // first lane of the group not yet added
+            while (g < nact) {
+                bool done_fast = false;
+                if (s != PT(0)) {
+                    const unsigned long long sb = FB<PT>::bits(s);
+                    const int eb = (int)(sb >> FB<PT>::kMant);
+                    const int e = eb - eblo;
+                    if (eb != 0 && e >= 0 && e < nE) {
+                        const unsigned long long* Pe = P + (int64_t)e * d1;
+                        const int32_t* Te = T + (int64_t)e * d1;
+                        const unsigned long long S =
+                            (sb & ((1ull << FB<PT>::kMant) - 1ull)) | (1ull << FB<PT>::kMant);
+                        const unsigned long long lim = (1ull << (FB<PT>::kMant + 1)) - S;
+                        unsigned long long dr = 0, ds = 0;
+                        bool tr = false, ts = false, sat = false;
+                        if (lane >= g && lane < nact) {
+                            const unsigned long long pb = Pe[start];
+                            sat = pb >= kSat - (1ull << 55);
+                            dr = Pe[pos] - pb;
+                            tr = Te[pos] != Te[start];
+                            ds = grid_units<PT>(t, eb, &ts);
+                        }
+                        // inclusive prefix of (dr + ds) over lanes g..nact-1
+                        unsigned long long both = sat_add(dr, ds);
+                        unsigned long long incl = both;
+#pragma unroll
+                        for (int o = 1; o < 32; o <<= 1) {
+                            const unsigned long long u = __shfl_up_sync(0xffffffffu, incl, o);
+                            if (lane >= o) incl = sat_add(incl, u);
+                        }
+                        unsigned long long excl = __shfl_up_sync(0xffffffffu, incl, 1);
+                        if (lane == 0) excl = 0ull;
+                        const bool bad_run = (lane >= g && lane < nact) &&
+                                             (sat || tr || sat_add(excl, dr) > lim);
+                        const bool bad_sp = (lane >= g && lane < nact) &&
+                                            (ts || sat_add(sat_add(excl, dr), ds) > lim);
+                        const unsigned bal = __ballot_sync(0xffffffffu, bad_run || bad_sp);
+                        if (bal == 0) {
+                            const unsigned long long tot =
+                                __shfl_sync(0xffffffffu, incl, nact - 1);
+                            s = from_units<PT>(S + tot, eb);
+                            g = nact;
+                            done_fast = true;
+                        } else {
+                            const int fl = __ffs(bal) - 1;
+                            const unsigned long long ex = __shfl_sync(0xffffffffu, excl, fl);
+                            const unsigned long long drf = __shfl_sync(0xffffffffu, dr, fl);
+                            const bool run_bad = __shfl_sync(0xffffffffu, bad_run, fl);
+                            const int64_t st_f = __shfl_sync(0xffffffffu, start, fl);
+                            const int64_t pos_f = __shfl_sync(0xffffffffu, pos, fl);
+                            const PT t_f = __shfl_sync(0xffffffffu, t, fl);
+                            if (run_bad) {
+                                s = from_units<PT>(S + ex, eb);
+                                s = tab_run<PT>(s, st_f, pos_f, pH, P, T, eblo, nE, d1);
+                            } else {
+                                s = from_units<PT>(S + ex + drf, eb);
+                            }
+                            s = p_add(s, t_f);
+                            g = fl + 1;
+                            done_fast = true;
+                        }
+                    }
+                }
+                if (!done_fast) {  // running sum outside the tables: one pair exactly
+                    const int64_t st_g = __shfl_sync(0xffffffffu, start, g);
+                    const int64_t pos_g = __shfl_sync(0xffffffffu, pos, g);
+                    const PT t_g = __shfl_sync(0xffffffffu, t, g);
+                    s = tab_run<PT>(s, st_g, pos_g, pH, P, T, eblo, nE, d1);
+                    s = p_add(s, t_g);
+                    ++g;
+                }
+            }
+            a = __shfl_sync(0xffffffffu, after, nact - 1);
+            j0 += nact;
+        }
+        s = tab_run_warp<PT>(s, a, dH, pH, P, T, eblo, nE, d1);
+        // jH: the lane that saw x == H
+        const unsigned hb = __ballot_sync(0xffffffffu, jH >= 0);
+        if (hb) jH = __shfl_sync(0xffffffffu, jH, __ffs(hb) - 1);
+        if (lane == 0) {
+            const int64_t e = (H < v) ? (int64_t)up_ptr[H] + (k - nlow[H])
+                                      : (int64_t)up_ptr[v] + (jH - nlow[v]);
+            score[e] = key_bits(s);
+        }
     }
 }
 
@@ -544,17 +570,20 @@ static spc_status score_typed(spc_context* ctx, GraphView& g, bool validate, voi
     const int64_t nnz = g.nnz;
     const int maxb = ctx->num_sms * 8;
     const int persist = ctx->num_sms * 2;
+    const bool fp = !std::is_same<WT, int32_t>::value;
     uint32_t* status = ctx->d_status;
     int32_t* long_count = W.counters.as<int32_t>() + 8;
+    int32_t* heavy_count = W.counters.as<int32_t>() + 10;
     int32_t* long_rows = W.long_rows.as<int32_t>();
     const int gb = grid_for(n, kThreads, maxb);
     SPC_CUDA(cudaMemsetAsync(long_count, 0, sizeof(int32_t), ctx->stream));
     SPC_LAUNCH(ctx, k_rows_degree<WT>, gb, kThreads, 0, n, nnz, g.rowptr, g.col,
                static_cast<const WT*>(g.w), validate ? 1 : 0, W.deg.as<Acc>(),
                W.up_cnt.as<int32_t>(), W.first_up.as<int32_t>(), long_rows, long_count, status);
-    SPC_LAUNCH(ctx, k_long_rows_degree<WT>, persist, kThreads, 0, n, g.rowptr, g.col,
+    SPC_LAUNCH(ctx, k_long_rows_check<WT>, persist, kThreads, 0, n, g.rowptr, g.col,
                static_cast<const WT*>(g.w), validate ? 1 : 0, long_rows, long_count,
-               W.deg.as<Acc>(), W.up_cnt.as<int32_t>(), W.first_up.as<int32_t>(), status);
+               W.deg.as<Acc>(), W.up_cnt.as<int32_t>(), W.first_up.as<int32_t>(),
+               W.lr_base.as<int64_t>(), W.lr_len.as<int64_t>(), W.lr_idx.as<int64_t>(), status);
     SPC_TRY(scan_i32(ctx, W.up_cnt.as<int32_t>(), W.up_ptr.as<int32_t>(), n));
     // one readback: the status word, the edge count and the number of long rows
     int32_t* hs = reinterpret_cast<int32_t*>(ctx->h_scalars);
@@ -570,16 +599,26 @@ static spc_status score_typed(spc_context* ctx, GraphView& g, bool validate, voi
     const int64_t n_long = hs[1];
     if (2 * m != nnz) return SPC_ERR_NOT_SYMMETRIC;
     g.m = m;
+    if (n_long > 0) {
+        SPC_TRY(scan_i64_i64(ctx, W.lr_len.as<int64_t>(), W.lr_eoff.as<int64_t>(), n_long));
+        if (fp) {  // exact degrees of the long rows from per-binade tables of their weights
+            SPC_TRY(seqtab_build(ctx, g.w, std::is_same<WT, float>::value, n_long,
+                                 W.lr_base.as<int64_t>(), W.lr_len.as<int64_t>(), true, W.tab_w));
+            SPC_TRY(seqtab_full_sums(ctx, g.w, std::is_same<WT, float>::value,
+                                     W.lr_base.as<int64_t>(), W.lr_len.as<int64_t>(), W.tab_w,
+                                     W.lr_idx.as<int64_t>(), W.deg.p));
+        }
+    }
     SPC_LAUNCH(ctx, k_rows_edges<WT>, gb, kThreads, 0, n, g.rowptr, g.col,
                static_cast<const WT*>(g.w), validate ? 1 : 0, W.deg.as<Acc>(),
                W.first_up.as<int32_t>(), W.up_ptr.as<int32_t>(), W.p.as<P>(),
                W.eu.as<int32_t>(), W.ev.as<int32_t>(), W.w_und.as<WT>(), status);
     if (n_long > 0) {
-        SPC_LAUNCH(ctx, k_long_rows_edges<WT>, persist, kThreads, 0, g.rowptr, g.col,
+        SPC_LAUNCH(ctx, k_long_rows_edges<WT>, maxb, kThreads, 0, g.rowptr, g.col,
                    static_cast<const WT*>(g.w), validate ? 1 : 0, W.deg.as<Acc>(),
                    W.first_up.as<int32_t>(), W.up_ptr.as<int32_t>(), long_rows, long_count,
-                   W.p.as<P>(), W.eu.as<int32_t>(), W.ev.as<int32_t>(), W.w_und.as<WT>(),
-                   status);
+                   W.lr_eoff.as<int64_t>(), W.p.as<P>(), W.eu.as<int32_t>(),
+                   W.ev.as<int32_t>(), W.w_und.as<WT>(), status);
     }
     if (validate) SPC_TRY(sync_status(ctx));  // no later kernel runs on an asymmetric input
     if (score == nullptr || m == 0) return SPC_OK;
@@ -595,28 +634,19 @@ static spc_status score_typed(spc_context* ctx, GraphView& g, bool validate, voi
                    static_cast<Key*>(score), status);
     }
     if (n_long == 0) return SPC_OK;
-    // hub edges: per-grid prefix tables of every hub row, then one thread per hub entry
-    SPC_LAUNCH(ctx, k_hub_meta<P>, persist, kThreads, 0, g.rowptr, W.p.as<P>(), long_rows,
-               long_count, W.hub_eblo.as<int32_t>(), W.hub_size.as<int64_t>(),
-               W.hub_deg.as<int64_t>());
-    SPC_TRY(scan_i64_i64(ctx, W.hub_size.as<int64_t>(), W.hub_off.as<int64_t>(), n_long));
-    SPC_TRY(scan_i64_i64(ctx, W.hub_deg.as<int64_t>(), W.hub_eoff.as<int64_t>(), n_long));
-    SPC_CUDA(cudaMemcpyAsync(ctx->h_scalars, W.hub_off.as<int64_t>() + n_long, sizeof(int64_t),
-                             cudaMemcpyDeviceToHost, ctx->stream));
-    SPC_CUDA(cudaMemcpyAsync(ctx->h_scalars + 1, W.hub_eoff.as<int64_t>() + n_long,
-                             sizeof(int64_t), cudaMemcpyDeviceToHost, ctx->stream));
-    SPC_CUDA(cudaStreamSynchronize(ctx->stream));
-    const int64_t tab_elems = ctx->h_scalars[0];
-    const int64_t hub_entries = ctx->h_scalars[1];
-    SPC_TRY(ensure(ctx, W.tab_p, (size_t)tab_elems * 8 + 256));
-    SPC_TRY(ensure(ctx, W.tab_t, (size_t)tab_elems * 4 + 256));
-    SPC_LAUNCH(ctx, k_hub_tables<P>, grid_for(n_long * 64, 1, maxb), kThreads, 0, g.rowptr,
-               W.p.as<P>(), long_rows, long_count, W.hub_eblo.as<int32_t>(),
-               W.hub_off.as<int64_t>(), W.tab_p.as<unsigned long long>(), W.tab_t.as<int32_t>());
-    SPC_LAUNCH(ctx, (k_score_hub<P, Key>), grid_for(hub_entries, kThreads, maxb), kThreads, 0,
-               g.rowptr, g.col, W.p.as<P>(), W.up_ptr.as<int32_t>(), W.first_up.as<int32_t>(),
-               long_rows, long_count, W.hub_eoff.as<int64_t>(), W.hub_eblo.as<int32_t>(),
-               W.hub_off.as<int64_t>(), W.tab_p.as<unsigned long long>(), W.tab_t.as<int32_t>(),
+    // hub edges: per-binade tables of every hub row's normalised weights, then one thread per
+    // hub entry (one warp per entry whose other row is long)
+    SPC_TRY(seqtab_build(ctx, W.p.p, std::is_same<P, float>::value, n_long,
+                         W.lr_base.as<int64_t>(), W.lr_len.as<int64_t>(), false, W.tab_p));
+    const SeqTabView tv = seqtab_view(W.tab_p, W.lr_base.as<int64_t>(), W.lr_len.as<int64_t>());
+    SPC_CUDA(cudaMemsetAsync(heavy_count, 0, sizeof(int32_t), ctx->stream));
+    SPC_LAUNCH(ctx, (k_score_hub<P, Key>), maxb, kThreads, 0, g.rowptr, g.col, W.p.as<P>(),
+               W.up_ptr.as<int32_t>(), W.first_up.as<int32_t>(), long_rows, long_count,
+               W.lr_eoff.as<int64_t>(), tv, static_cast<Key*>(score), W.heavy.as<int32_t>(),
+               heavy_count, status);
+    SPC_LAUNCH(ctx, (k_score_hub_heavy<P, Key>), persist, kThreads, 0, g.rowptr, g.col,
+               W.p.as<P>(), W.up_ptr.as<int32_t>(), W.first_up.as<int32_t>(), long_rows,
+               long_count, W.lr_eoff.as<int64_t>(), tv, W.heavy.as<int32_t>(), heavy_count,
                static_cast<Key*>(score), status);
     return SPC_OK;
 }

@@ -186,3 +186,110 @@ __device__ long long cta_sum_i64(int64_t L, const Term& term) {
 }
 
 }  // namespace spc
+
+namespace spc {
+
+// ---- per-binade prefix tables over long sequences (built by spc_seqtab.cu) ---------------------
+// Sequence q has terms[base[q] .. base[q] + len[q]).  For every binade eb in [eblo[q],
+// eblo[q] + nE[q]) the tables hold, at tab_off[q] + (eb - eblo[q]) * (len[q] + 1) + k,
+//   P = sum of grid_units(term_t, eb) over t < k  (saturating at kSat)
+//   T = number of half-grid ties among t < k.
+struct SeqTabView {
+    const int64_t* base;
+    const int64_t* len;
+    const int32_t* eblo;
+    const int32_t* nE;
+    const int64_t* tab_off;
+    const unsigned long long* P;
+    const int32_t* T;
+};
+
+SeqTabView seqtab_view(const SeqTabBufs& tb, const int64_t* base, const int64_t* len);
+
+// The left-to-right sum continued over terms x[a, b) of one tabled sequence from running value
+// s (x = the sequence's first term).  Identical to adding the terms one by one.
+template <class F>
+__device__ F tab_run(F s, int64_t a, int64_t b, const F* __restrict__ x,
+                     const unsigned long long* __restrict__ P, const int32_t* __restrict__ T,
+                     int eblo, int nE, int64_t d1) {
+    while (a < b) {
+        if (s == F(0)) { s = x[a++]; continue; }
+        const unsigned long long sb = FB<F>::bits(s);
+        const int eb = (int)(sb >> FB<F>::kMant);
+        const int e = eb - eblo;
+        if (eb == 0 || e < 0 || e >= nE) { s = FB<F>::add(s, x[a++]); continue; }
+        const unsigned long long* Pe = P + (int64_t)e * d1;
+        const int32_t* Te = T + (int64_t)e * d1;
+        const unsigned long long base = Pe[a];
+        if (base >= kSat - (1ull << 55)) { s = FB<F>::add(s, x[a++]); continue; }
+        const unsigned long long S = (sb & ((1ull << FB<F>::kMant) - 1ull)) | (1ull << FB<F>::kMant);
+        const unsigned long long lim = (1ull << (FB<F>::kMant + 1)) - S;
+        int64_t lo = a, hi = b;  // largest k in [a, b] whose prefix stays on this grid
+        while (lo < hi) {
+            const int64_t mid = (lo + hi + 1) >> 1;
+            if (Pe[mid] - base <= lim) lo = mid; else hi = mid - 1;
+        }
+        int64_t k = lo;
+        const int32_t ta = Te[a];
+        if (Te[k] > ta) {  // a half-grid tie inside: stop at the first one
+            int64_t l2 = a, h2 = k - 1;
+            while (l2 < h2) {
+                const int64_t mid = (l2 + h2) >> 1;
+                if (Te[mid + 1] > ta) h2 = mid; else l2 = mid + 1;
+            }
+            k = l2;
+        }
+        s = from_units<F>(S + (Pe[k] - base), eb);
+        a = k;
+        if (a < b) s = FB<F>::add(s, x[a++]);  // binade crossing or tie: one native step
+    }
+    return s;
+}
+
+// Warp-cooperative version of tab_run (all 32 lanes call it with the same arguments and get
+// the same result): each search probes 32 positions at once.
+template <class F>
+__device__ F tab_run_warp(F s, int64_t a, int64_t b, const F* __restrict__ x,
+                          const unsigned long long* __restrict__ P, const int32_t* __restrict__ T,
+                          int eblo, int nE, int64_t d1) {
+    const int lane = threadIdx.x & 31;
+    while (a < b) {
+        if (s == F(0)) { s = x[a++]; continue; }
+        const unsigned long long sb = FB<F>::bits(s);
+        const int eb = (int)(sb >> FB<F>::kMant);
+        const int e = eb - eblo;
+        if (eb == 0 || e < 0 || e >= nE) { s = FB<F>::add(s, x[a++]); continue; }
+        const unsigned long long* Pe = P + (int64_t)e * d1;
+        const int32_t* Te = T + (int64_t)e * d1;
+        const unsigned long long base = Pe[a];
+        if (base >= kSat - (1ull << 55)) { s = FB<F>::add(s, x[a++]); continue; }
+        const unsigned long long S = (sb & ((1ull << FB<F>::kMant) - 1ull)) | (1ull << FB<F>::kMant);
+        const unsigned long long lim = (1ull << (FB<F>::kMant + 1)) - S;
+        const int32_t ta = Te[a];
+        // largest k in [a, b] with Pe[k] - base <= lim and no tie among [a, k)
+        int64_t lo = a, hi = b;  // invariant: lo is good; answer in [lo, hi]
+        while (hi - lo > 0) {
+            const int64_t span = hi - lo;
+            const int64_t step = (span + 31) / 32;
+            const int64_t probe = lo + (int64_t)(lane + 1) * step;
+            bool good = false;
+            if (probe <= hi) good = (Pe[probe] - base <= lim) && (Te[probe] == ta);
+            const unsigned bal = __ballot_sync(0xffffffffu, good && probe <= hi);
+            // good positions form a prefix of the probes (both conditions are monotone)
+            const int ngood = __popc(bal);
+            const int64_t new_lo = lo + (int64_t)ngood * step;
+            int64_t new_hi = lo + (int64_t)(ngood + 1) * step - 1;
+            if (new_hi > hi) new_hi = hi;
+            lo = new_lo > hi ? hi : new_lo;
+            hi = new_hi;
+            if (step == 1) break;
+        }
+        const int64_t k = lo;
+        s = from_units<F>(S + (Pe[k] - base), eb);
+        a = k;
+        if (a < b) s = FB<F>::add(s, x[a++]);
+    }
+    return s;
+}
+
+}  // namespace spc

@@ -462,3 +462,19 @@ def hub_graph(n: int, hub_degrees, seed: int, weight: str = "float", dtype=np.fl
     else:
         w = rng.uniform(0.1, 2.0, size=u.shape[0]).astype(dtype)
     return csr_from_edges(n, u, v, w, name=f"hubs{n}")
+
+
+def clique_ring(B: int, size: int, seed: int, dtype=np.float64) -> Graph:
+    """B disjoint cliques K_size with random weights U(1, 1.1), joined into a ring by one edge
+    of weight 0.05 between consecutive cliques.  Coarsening to n/size needs every clique merged
+    completely, which the lightest few edges alone cannot do (they close cycles)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    iu, iv = np.triu_indices(size, 1)
+    off = (np.arange(B) * size)[:, None]
+    eu = (off + iu[None, :]).ravel(); ev = (off + iv[None, :]).ravel()
+    w = rng.uniform(1.0, 1.1, size=eu.shape[0])
+    ru = np.arange(B) * size
+    rv = (np.arange(B) * size + size + 1) % (B * size)
+    eu = np.concatenate([eu, ru]); ev = np.concatenate([ev, rv])
+    w = np.concatenate([w, np.full(B, 0.05)]).astype(dtype)
+    return csr_from_edges(B * size, eu, ev, w, name=f"cliques{B}x{size}")

@@ -398,3 +398,17 @@ def test_hub_scores_and_level_bitexact(ctx, name, make):
         lift, nc, st = ctx.coarsen(csr, n_c, levels=1)
         assert nc == ref.n_c
         _check_level(ctx.level(0), ref)
+
+
+def test_prefix_filter_retry_on_cliques(ctx):
+    """Merging to n/4 on disjoint K4s needs all 3n/4 clique merges; the score prefix that the
+    spanning-forest rounds start from cannot hold them (its edges close cycles), so the rounds
+    are rerun on all edges -- the result must still be the oracle's."""
+    api = _api()
+    for dt in (np.float64, np.float32):
+        g = I.clique_ring(20000, 4, 8, dt)
+        for n_c in (g.n // 4, g.n // 2, g.n // 3):
+            ref = O.coarsen_level(g, n_c)
+            lift, nc, st = ctx.coarsen(api.CSR.from_graph(g), n_c, levels=1)
+            assert nc == ref.n_c
+            _check_level(ctx.level(0), ref)
