@@ -102,10 +102,47 @@ def cpu_baseline(workload, budget_s=10.0):
                       f"{dt:.1f} s single-threaded C"}
 
 
+def run_reference_batched(args):
+    """The oracle on a bounded sample of the 10,000-mesh batch: graphs/s of coarsening each
+    sampled graph (3 levels) and its contraction gradient."""
+    from oracle import oracle as O
+    from paper_2204_11757_gb300 import inputs as I
+    full, cfg = I.config_graph("c5_batch10k_f32")
+    rng = np.random.default_rng(0)
+    sub = I.subsample_batch(full, np.sort(rng.choice(full.B, size=60, replace=False)))
+
+    def one():
+        t0 = time.perf_counter()
+        for levels, _ in O.coarsen_batch(sub, cfg["ratio"], cfg["mode"]):
+            em = O.compose_emaps(levels)
+            O.contract_backward(em, np.ones(levels[-1].coarse.m_c, dtype=np.float32))
+        return time.perf_counter() - t0
+
+    for _ in range(args.warmup):
+        one()
+    tot = sum(one() for _ in range(args.steps))
+    value = sub.B * args.steps / tot
+    line = {
+        "impl": "reference", "metric": "batched fwd+bwd graphs/s", "value": value,
+        "unit": "graphs/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True, "scaling": "strong",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "c5_batch10k_f32", "sample_graphs": sub.B},
+        "cpu_baseline": {"value": value, "unit": "graphs/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{sub.B} sampled graphs of the batch per step"},
+        "e2e": {"value": value, "unit": "graphs/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_reference(args):
     ws, rank, _ = _dist()
     if rank != 0:
         return 0
+    if args.workload == "c5_batch10k_f32":
+        return run_reference_batched(args)
     spec = SAMPLES[args.workload]
     g = _sample_graph(spec)
     for _ in range(args.warmup):
@@ -194,13 +231,123 @@ def _score_bytes(n, m, s_p, s_f):
     return 8 * m + 8 * (n + 1) + 2 * m * (4 + s_p) + m * s_f
 
 
+def run_batched(args):
+    """Batched forward + backward: one coarsening of every graph of the batch (3 halving levels,
+    one set of launches for all graphs), the coarse weights through the differentiable
+    contraction, loss sum(a * g), backward to the fine weights.  graphs/s = B / step time,
+    against a loop that coarsens the graphs one by one with the single-graph entry point."""
+    import torch
+    import torch.distributed as dist
+    import __graft_entry__ as ge
+    from paper_2204_11757_gb300 import api, inputs as I, shard as S
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    if rank == 0:
+        ge.build()
+    if ws > 1:
+        dist.barrier()
+    full, cfg = I.config_graph("c5_batch10k_f32")
+    batch, (g0, g1) = S.local_batch(full, rank, ws) if ws > 1 else (full, (0, full.B))
+    dev = torch.device("cuda", local)
+    csr = api.CSR.from_graph(batch.graph, dev)
+    gptr = torch.from_numpy(batch.graph_ptr).to(dev)
+    w_und = torch.from_numpy(batch.graph.w_und).to(dev)
+    ctx = api.Context(dev)
+    L = 3
+
+    def step():
+        ctx.coarsen_batched(csr, gptr, cfg["ratio"], L)
+        plan = api.ContractionPlan.from_levels(ctx, ctx.levels())
+        w = w_und.detach().requires_grad_(True)
+        a = api.contract_weights(w, plan)
+        gvec = torch.ones_like(a)
+        (a * gvec).sum().backward()
+        return w.grad
+
+    for _ in range(args.warmup):
+        step()
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    launches0 = ctx.launch_count
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    sampler = ClockSampler(local)
+    if rank == 0:
+        sampler.start()
+        time.sleep(0.3)
+    ev0.record(ctx.stream)
+    for _ in range(args.steps):
+        step()
+    ev1.record(ctx.stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop() if rank == 0 else None
+    t_ms = ev0.elapsed_time(ev1) / args.steps
+    launches = ctx.launch_count - launches0
+    if ws > 1:
+        t = torch.tensor([t_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_ms = float(t.item())
+    value = full.B / (t_ms * 1e-3)
+    # per-graph loop of the single-graph coarsener on a sample, same work per graph
+    loop = None
+    if rank == 0:
+        rng = np.random.default_rng(0)
+        idx = np.sort(rng.choice(batch.B, size=min(100, batch.B), replace=False))
+        subs = [I.subsample_batch(batch, [i]) for i in idx]
+        gs = [(api.CSR.from_graph(s.graph, dev), torch.from_numpy(s.graph.w_und).to(dev),
+               s.graph.n) for s in subs]
+
+        def one(gc, wu, n):
+            ctx.coarsen(gc, max(1, n // cfg["ratio"]), levels=L)
+            plan = api.ContractionPlan.from_levels(ctx, ctx.levels())
+            w = wu.detach().requires_grad_(True)
+            a = api.contract_weights(w, plan)
+            (a * torch.ones_like(a)).sum().backward()
+
+        for gc, wu, n in gs[:5]:
+            one(gc, wu, n)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for gc, wu, n in gs:
+            one(gc, wu, n)
+        torch.cuda.synchronize()
+        loop_s = (time.perf_counter() - t0) / len(gs)
+        loop = {"graphs_s": 1.0 / loop_s, "sample_graphs": len(gs)}
+    if rank == 0:
+        line = {
+            "metric": "batched fwd+bwd graphs/s", "value": value, "unit": "graphs/s",
+            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_ms,
+            "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": "c5_batch10k_f32: 10,000 jittered 2D/3D meshes, node counts "
+                                   "log-uniform 200-20,000, FP32 1/edge-length, 3 halving "
+                                   "levels to n_b/8 each, forward + backward through the "
+                                   "contraction", "B": full.B, "n": full.graph.n,
+                       "m": full.graph.m, "parallelism": f"graphs sharded over {ws} rank(s)",
+                       "per_graph_loop": loop,
+                       "speedup_vs_per_graph_loop": (value / loop["graphs_s"]) if loop else None},
+            "clocks": clocks, "gpu_launches": int(launches),
+        }
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if ws > 1:
+        dist.destroy_process_group()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="c2_tri2048_f64")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["c5_batch10k_f32"],
+                    default="c2_tri2048_f64")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile", action="store_true", help="print the per-kernel breakdown")
@@ -209,6 +356,8 @@ def main():
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "c5_batch10k_f32":
+        return run_batched(args)
 
     import torch
     import torch.distributed as dist

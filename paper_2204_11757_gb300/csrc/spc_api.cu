@@ -248,7 +248,8 @@ static spc_status reserve_work(spc_context* ctx, int64_t n, int64_t m, int64_t B
     // scan of up to max(n, m, 256 * tiles) items -> tile sums; radix histograms
     const size_t big = (N > M ? N : M) + 256 * ((M + 4095) / 4096) + 4096;
     SPC_TRY(ensure(ctx, W.scan_tmp, (big / 4096 + 4) * 8 + 256));
-    SPC_TRY(ensure(ctx, W.sort_hist, (256 * ((M + 4095) / 4096) + 4) * 4));
+    // one-sweep sort: 8 passes x (tiles x 256) look-back words + histograms
+    SPC_TRY(ensure(ctx, W.sort_hist, (8 * 256 * ((M + 4095) / 4096) + 8 * 512 + 64) * 4));
     return SPC_OK;
 }
 

@@ -339,6 +339,136 @@ k_select_unite(const int32_t* __restrict__ count, const uint32_t* __restrict__ e
     }
 }
 
+// ---- exact selection of the k lightest forest edges (single graph) ------------------------------
+// Composite key (score bits, eid) is unique.  Round r histograms an 11-bit digit (most
+// significant first: the score's digits, then the eid's) over the items whose earlier digits
+// match the ones picked so far.  The last block of a round to finish (ticket counter after a
+// fence) picks that round's digit -- the bin holding the remaining rank -- and stores it with
+// the rank left inside the bin, for the next round.
+constexpr int kSelBits = 11;
+constexpr int kSelBins = 1 << kSelBits;
+
+template <class KT> struct SelBits {
+    static constexpr int kKeyBits = sizeof(KT) == 8 ? 63 : 31;  // sign bit always clear
+    static constexpr int kHiRounds = (kKeyBits + kSelBits - 1) / kSelBits;
+    static constexpr int kRounds = kHiRounds + 3;                 // eid: 32 bits = 11 + 11 + 10
+};
+
+// digit r of (hi, lo) and its width
+template <class KT>
+__device__ __forceinline__ uint32_t sel_digit(KT hi, uint32_t lo, int r) {
+    constexpr int H = SelBits<KT>::kHiRounds, KB = SelBits<KT>::kKeyBits;
+    if (r < H) {
+        const int top = KB - kSelBits * r;                 // exclusive upper bit of digit r
+        const int lowb = top - kSelBits > 0 ? top - kSelBits : 0;
+        return (uint32_t)(hi >> lowb) & ((1u << (top - lowb)) - 1u);
+    }
+    const int q = r - H;
+    const int top = 32 - kSelBits * q;
+    const int lowb = top - kSelBits > 0 ? top - kSelBits : 0;
+    return (lo >> lowb) & ((1u << (top - lowb)) - 1u);
+}
+
+struct SelState {
+    unsigned long long need;     // rank (1-based) still to find among the matching items
+    uint32_t dig[16];
+    uint32_t ticket[16];
+};
+
+template <class KT>
+__global__ void __launch_bounds__(kThreads)
+k_rsel_round(int r, int64_t n, const KT* __restrict__ keys, const uint32_t* __restrict__ vals,
+             uint32_t* __restrict__ hist, SelState* st) {
+    __shared__ uint32_t sh_h[kSelBins];
+    __shared__ uint32_t sh_dig[16];
+    __shared__ bool sh_last;
+    for (int b = threadIdx.x; b < kSelBins; b += blockDim.x) sh_h[b] = 0;
+    if (threadIdx.x < 16) sh_dig[threadIdx.x] = st->dig[threadIdx.x];
+    __syncthreads();
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const KT hi = keys[i];
+        const uint32_t lo = vals[i];
+        bool match = true;
+        for (int q = 0; q < r; ++q) match = match && sel_digit<KT>(hi, lo, q) == sh_dig[q];
+        if (match) atomicAdd(&sh_h[sel_digit<KT>(hi, lo, r)], 1u);
+    }
+    __syncthreads();
+    for (int b = threadIdx.x; b < kSelBins; b += blockDim.x)
+        if (sh_h[b]) atomicAdd(hist + r * kSelBins + b, sh_h[b]);
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) sh_last = atomicAdd(&st->ticket[r], 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!sh_last) return;
+    // the last block: pick the bin holding rank `need`
+    __threadfence();
+    constexpr int kPer = kSelBins / kThreads;
+    const uint32_t* h = hist + r * kSelBins;
+    unsigned long long loc = 0;
+    uint32_t c[kPer];
+    for (int j = 0; j < kPer; ++j) {
+        c[j] = __ldcg(h + threadIdx.x * kPer + j);
+        loc += c[j];
+    }
+    __shared__ unsigned long long sh_s[kThreads];
+    sh_s[threadIdx.x] = loc;
+    __syncthreads();
+    for (int o = 1; o < kThreads; o <<= 1) {
+        const unsigned long long t = threadIdx.x >= (unsigned)o ? sh_s[threadIdx.x - o] : 0ull;
+        __syncthreads();
+        sh_s[threadIdx.x] += t;
+        __syncthreads();
+    }
+    const unsigned long long need = st->need;
+    unsigned long long run = threadIdx.x ? sh_s[threadIdx.x - 1] : 0ull;
+    if (run < need && sh_s[threadIdx.x] >= need) {
+        for (int j = 0; j < kPer; ++j) {
+            if (run + c[j] >= need) {
+                st->dig[r] = (uint32_t)(threadIdx.x * kPer + j);
+                st->need = need - run;
+                break;
+            }
+            run += c[j];
+        }
+    }
+}
+
+// unite the ends of every forest edge whose (score, eid) is at most the k-th smallest
+template <class KT>
+__global__ void __launch_bounds__(kThreads)
+k_rsel_unite(int64_t n, const KT* __restrict__ keys, const uint32_t* __restrict__ vals,
+             const SelState* __restrict__ st, const int32_t* __restrict__ eu,
+             const int32_t* __restrict__ ev, int32_t* parent, uint8_t* merged, uint32_t* status) {
+    constexpr int H = SelBits<KT>::kHiRounds, KB = SelBits<KT>::kKeyBits;
+    KT thi = 0;
+    for (int q = 0; q < H; ++q) {
+        const int top = KB - kSelBits * q;
+        const int lowb = top - kSelBits > 0 ? top - kSelBits : 0;
+        thi |= (KT)st->dig[q] << lowb;
+    }
+    uint32_t tlo = 0;
+    for (int q = 0; q < 3; ++q) {
+        const int top = 32 - kSelBits * q;
+        const int lowb = top - kSelBits > 0 ? top - kSelBits : 0;
+        tlo |= st->dig[H + q] << lowb;
+    }
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const KT hi = keys[i];
+        const uint32_t lo = vals[i];
+        if (hi < thi || (hi == thi && lo <= tlo)) {
+            uf_unite(parent, eu[lo], ev[lo], status);
+            if (merged) merged[lo] = 1;
+        }
+    }
+}
+
+__global__ void k_rsel_init(SelState* st, unsigned long long k) {
+    if (threadIdx.x == 0) st->need = k;
+    if (threadIdx.x < 16) { st->dig[threadIdx.x] = 0; st->ticket[threadIdx.x] = 0; }
+}
+
 // root (= smallest member) of every node and the root flags
 __global__ void __launch_bounds__(kThreads)
 k_roots(int64_t n, int32_t* parent, int32_t* __restrict__ flag, uint32_t* status) {
@@ -368,6 +498,41 @@ __global__ void k_graph_ptr_c(int64_t B, const int64_t* __restrict__ graph_ptr,
             if (nc > targets[b]) atomicOr(warn, 1);
         }
     }
+}
+
+// relabel (S6) from the second union-find in W.parent2, plus per-graph offsets and the status
+spc_status finish_select(spc_context* ctx, const GraphView& g, const SelectArgs& sa, int32_t* lift,
+                         int64_t* n_c_out, int64_t* graph_ptr_c, int32_t* status_out,
+                         bool batched) {
+    Work& W = ctx->work;
+    const int64_t n = g.n;
+    const int maxb = ctx->num_sms * 8;
+    uint32_t* status = ctx->d_status;
+    int32_t* counters = W.counters.as<int32_t>();
+    int32_t* parent2 = W.parent2.as<int32_t>();
+    // ---- 3. relabel ------------------------------------------------------------------
+    int32_t* flag = W.flag.as<int32_t>();
+    int32_t* ids = W.ids.as<int32_t>();
+    SPC_LAUNCH(ctx, k_roots, grid_for(n, kThreads, maxb), kThreads, 0, n, parent2, flag, status);
+    SPC_TRY(scan_i32(ctx, flag, ids, n));
+    SPC_LAUNCH(ctx, k_lift, grid_for(n, kThreads, maxb), kThreads, 0, n, parent2, ids, lift,
+               status);
+    int32_t* warn = counters + 2;
+    SPC_CUDA(cudaMemsetAsync(warn, 0, sizeof(int32_t), ctx->stream));
+    if (batched) {
+        SPC_LAUNCH(ctx, k_graph_ptr_c, grid_for(sa.B + 1, kThreads, maxb), kThreads, 0, sa.B,
+                   sa.d_graph_ptr, ids, sa.d_targets, graph_ptr_c, warn);
+    }
+    SPC_CUDA(cudaMemcpyAsync(ctx->h_scalars, ids + n, sizeof(int32_t), cudaMemcpyDeviceToHost,
+                             ctx->stream));
+    SPC_CUDA(cudaMemcpyAsync(ctx->h_scalars + 1, warn, sizeof(int32_t), cudaMemcpyDeviceToHost,
+                             ctx->stream));
+    SPC_CUDA(cudaStreamSynchronize(ctx->stream));
+    const int64_t n_c = *reinterpret_cast<int32_t*>(ctx->h_scalars);
+    const int32_t warn_b = *reinterpret_cast<int32_t*>(ctx->h_scalars + 1);
+    *n_c_out = n_c;
+    *status_out = (batched ? warn_b != 0 : n_c > sa.target) ? SPC_WARN_TARGET_NOT_REACHED : SPC_OK;
+    return SPC_OK;
 }
 
 template <class KT>
@@ -463,6 +628,25 @@ spc_status select_typed(spc_context* ctx, const GraphView& g, const KT* key,
     SPC_LAUNCH(ctx, k_compact_msf<KT>, grid_for(m, kThreads, maxb), kThreads, 0, m,
                W.msf.as<uint8_t>(), pos, key, sk, sv);
     const int key_bits = sizeof(KT) == 8 ? 63 : 31;  // scores are >= +0: sign bit clear
+    const int64_t k_single_sel = batched ? 0 : (n - sa.target > 0 ? n - sa.target : 0);
+    if (!batched && k_single_sel > 0 && k_single_sel < n_msf) {
+        // single graph, proper subset: exact radix select of the k lightest, no sort
+        constexpr int R = SelBits<KT>::kRounds;
+        SPC_TRY(ensure(ctx, W.key_hist, 32768 * 4));
+        uint32_t* hist = W.key_hist.as<uint32_t>();
+        SelState* sst = reinterpret_cast<SelState*>(counters + 16);
+        SPC_CUDA(cudaMemsetAsync(hist, 0, (size_t)R * kSelBins * 4, ctx->stream));
+        SPC_LAUNCH(ctx, k_rsel_init, 1, 32, 0, sst, (unsigned long long)k_single_sel);
+        const int gsel = grid_for(n_msf, kThreads, ctx->num_sms * 2);
+        for (int r = 0; r < R; ++r) {
+            SPC_LAUNCH(ctx, k_rsel_round<KT>, gsel, kThreads, 0, r, n_msf, sk, sv, hist, sst);
+        }
+        int32_t* parent2 = W.parent2.as<int32_t>();
+        SPC_LAUNCH(ctx, k_iota, grid_for(n, kThreads, maxb), kThreads, 0, parent2, n);
+        SPC_LAUNCH(ctx, k_rsel_unite<KT>, grid_for(n_msf, kThreads, maxb), kThreads, 0, n_msf, sk,
+                   sv, sst, W.eu.as<int32_t>(), W.ev.as<int32_t>(), parent2, merged, status);
+        return finish_select(ctx, g, sa, lift, n_c_out, graph_ptr_c, status_out, batched);
+    }
     if (sizeof(KT) == 8) {
         SPC_TRY(radix_sort_u64(ctx, reinterpret_cast<uint64_t*>(sk), sv,
                                W.sel_key2.as<uint64_t>(), W.sel_val2.as<uint32_t>(), n_msf,
@@ -505,29 +689,7 @@ spc_status select_typed(spc_context* ctx, const GraphView& g, const KT* key,
                    sv, gkey, seg_start, k_graph, k_single, W.eu.as<int32_t>(),
                    W.ev.as<int32_t>(), parent2, merged, status);
     }
-    // ---- 3. relabel ------------------------------------------------------------------
-    int32_t* flag = W.flag.as<int32_t>();
-    int32_t* ids = W.ids.as<int32_t>();
-    SPC_LAUNCH(ctx, k_roots, grid_for(n, kThreads, maxb), kThreads, 0, n, parent2, flag, status);
-    SPC_TRY(scan_i32(ctx, flag, ids, n));
-    SPC_LAUNCH(ctx, k_lift, grid_for(n, kThreads, maxb), kThreads, 0, n, parent2, ids, lift,
-               status);
-    int32_t* warn = counters + 2;
-    SPC_CUDA(cudaMemsetAsync(warn, 0, sizeof(int32_t), ctx->stream));
-    if (batched) {
-        SPC_LAUNCH(ctx, k_graph_ptr_c, grid_for(sa.B + 1, kThreads, maxb), kThreads, 0, sa.B,
-                   sa.d_graph_ptr, ids, sa.d_targets, graph_ptr_c, warn);
-    }
-    SPC_CUDA(cudaMemcpyAsync(ctx->h_scalars, ids + n, sizeof(int32_t), cudaMemcpyDeviceToHost,
-                             ctx->stream));
-    SPC_CUDA(cudaMemcpyAsync(ctx->h_scalars + 1, warn, sizeof(int32_t), cudaMemcpyDeviceToHost,
-                             ctx->stream));
-    SPC_CUDA(cudaStreamSynchronize(ctx->stream));
-    const int64_t n_c = *reinterpret_cast<int32_t*>(ctx->h_scalars);
-    const int32_t warn_b = *reinterpret_cast<int32_t*>(ctx->h_scalars + 1);
-    *n_c_out = n_c;
-    *status_out = (batched ? warn_b != 0 : n_c > sa.target) ? SPC_WARN_TARGET_NOT_REACHED : SPC_OK;
-    return SPC_OK;
+    return finish_select(ctx, g, sa, lift, n_c_out, graph_ptr_c, status_out, batched);
 }
 
 }  // namespace

@@ -10,6 +10,19 @@
 
 namespace spc {
 
+// w / d for every entry of a row that shares the degree d, with y = RN(1/d) computed once per row:
+// Markstein's theorem (IBM J. Res. Dev. 34(1), 1990; also Muller et al., Handbook of
+// Floating-Point Arithmetic, ch. 4): if y is within half an ulp of 1/d and q0 within one ulp of
+// w/d, then r = w - d*q0 is exact (one FMA) and RN(q0 + r*y) = RN(w/d).  q0 = RN(w*y) is within
+// one ulp.  Outside the range where no intermediate can underflow or overflow the IEEE division
+// is used directly.
+__device__ __forceinline__ double div_row(double w, double d, double y) {
+    const double q0 = __dmul_rn(w, y);
+    if (!(q0 > 0x1p-960 && q0 < 0x1p960 && d > 0x1p-960 && d < 0x1p960)) return __ddiv_rn(w, d);
+    const double r = __fma_rn(-d, q0, w);
+    return __fma_rn(r, y, q0);
+}
+
 template <class WT> struct Tr;
 template <> struct Tr<int32_t> {
     using Acc = long long;
@@ -206,11 +219,18 @@ k_rows_edges(int64_t n, const int64_t* __restrict__ rowptr, const int32_t* __res
         if (r1 - r0 > kLongRow) continue;  // k_long_rows_edges
         const typename Tr<WT>::Acc d = deg[x];
         const int64_t ubase = (int64_t)up_ptr[x] - (r0 + nlow[x]);
+        // binary64 rows: one correctly rounded reciprocal per row, Markstein per entry
+        double dd = 0.0, rcp = 0.0;
+        if constexpr (!std::is_same<WT, float>::value) {
+            dd = (double)d;
+            rcp = __drcp_rn(dd);
+        }
         uint32_t bits = 0;
         for (int64_t j = r0; j < r1; ++j) {
             const int32_t y = col[j];
             const WT wj = w[j];
-            p[j] = Tr<WT>::div(wj, d);
+            if constexpr (std::is_same<WT, float>::value) p[j] = Tr<WT>::div(wj, d);
+            else p[j] = div_row((double)wj, dd, rcp);
             if (validate) {
                 int64_t lo = rowptr[y], hi = rowptr[y + 1];
                 while (lo < hi) {
@@ -248,22 +268,20 @@ k_score_edges(int64_t m, const int32_t* __restrict__ eu, const int32_t* __restri
         int64_t j = rowptr[b];
         const int64_t je = rowptr[b + 1];
         if (ie - i > kLongRow || je - j > kLongRow) continue;  // hub edge: k_score_hub
+        // one uniform step per coordinate of the union: t = |pa - pb| with the missing side
+        // read as 0 (exact: |x - 0| = x), so every lane issues the same two FP64 operations
         PT s = PT(0);
-        while (i < ie && j < je) {
-            const int32_t ca = col[i], cb = col[j];
-            PT t;
-            if (ca < cb) {
-                t = p[i++];
-            } else if (cb < ca) {
-                t = p[j++];
-            } else {
-                t = p_absdiff(p[i], p[j]);
-                ++i; ++j;
-            }
-            s = p_add(s, t);
+        constexpr int32_t kEnd = 0x7fffffff;
+        int32_t ca = i < ie ? col[i] : kEnd;
+        int32_t cb = j < je ? col[j] : kEnd;
+        while (ca != kEnd || cb != kEnd) {
+            const bool ta = ca <= cb, tb = cb <= ca;
+            const PT pa = ta ? p[i] : PT(0);
+            const PT pb = tb ? p[j] : PT(0);
+            s = p_add(s, p_absdiff(pa, pb));
+            if (ta) { ++i; ca = i < ie ? col[i] : kEnd; }
+            if (tb) { ++j; cb = j < je ? col[j] : kEnd; }
         }
-        while (i < ie) s = p_add(s, p[i++]);
-        while (j < je) s = p_add(s, p[j++]);
         score[e] = key_bits(s);
     }
 }

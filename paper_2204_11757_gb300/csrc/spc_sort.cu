@@ -144,39 +144,212 @@ __global__ void __launch_bounds__(RT) k_rs_downsweep(const K* __restrict__ kin,
     }
 }
 
+// ---- one-sweep passes ---------------------------------------------------------------------------
+// All digit histograms in one read of the keys; then one kernel per digit in which every tile
+// ranks its items, publishes its per-digit counts and finds its output offsets by looking back
+// over the tiles before it (decoupled look-back).  Tiles take ids in launch order from a
+// counter, so every tile a tile waits for is already running; each wait is bounded.
+constexpr uint32_t kFlagAgg = 1u << 30;
+constexpr uint32_t kFlagInc = 2u << 30;
+constexpr uint32_t kValMask = (1u << 30) - 1u;
+constexpr int kMaxPasses = 8;
+
+template <class K>
+__global__ void __launch_bounds__(RT) k_os_hist(const K* __restrict__ keys, int64_t count,
+                                                int npass, int end_bit,
+                                                uint32_t* __restrict__ hist) {
+    constexpr int kCopies = 2;  // two copies (warps 0-3, 4-7) halve the contention on a bin
+    __shared__ uint32_t h[kCopies][kMaxPasses][RADIX];
+    const int warp = (threadIdx.x >> 5) * kCopies / RW;
+    for (int i = threadIdx.x; i < kCopies * kMaxPasses * RADIX; i += RT) (&h[0][0][0])[i] = 0;
+    __syncthreads();
+    for (int64_t i = (int64_t)blockIdx.x * RT + threadIdx.x; i < count;
+         i += (int64_t)gridDim.x * RT) {
+        const K k = keys[i];
+        for (int p = 0; p < npass; ++p) {
+            const int shift = 8 * p;
+            const int bits = (end_bit - shift) < 8 ? (end_bit - shift) : 8;
+            atomicAdd(&h[warp][p][(uint32_t)(k >> shift) & ((1u << bits) - 1u)], 1u);
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < npass * RADIX; i += RT) {
+        uint32_t s = 0;
+        for (int w = 0; w < kCopies; ++w) s += h[w][i / RADIX][i % RADIX];
+        if (s) atomicAdd(hist + i, s);
+    }
+}
+
+// exclusive scan of every pass's 256 bins (one block, one thread per bin)
+__global__ void k_os_bases(int npass, const uint32_t* __restrict__ hist, uint32_t* __restrict__ base) {
+    __shared__ uint32_t sh[RADIX];
+    for (int p = 0; p < npass; ++p) {
+        sh[threadIdx.x] = hist[p * RADIX + threadIdx.x];
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            uint32_t run = 0;
+            for (int d = 0; d < RADIX; ++d) {
+                const uint32_t c = sh[d];
+                sh[d] = run;
+                run += c;
+            }
+        }
+        __syncthreads();
+        base[p * RADIX + threadIdx.x] = sh[threadIdx.x];
+        __syncthreads();
+    }
+}
+
+template <class K>
+__global__ void __launch_bounds__(RT) k_os_pass(const K* __restrict__ kin,
+                                                const uint32_t* __restrict__ vin,
+                                                K* __restrict__ kout, uint32_t* __restrict__ vout,
+                                                int64_t count, int shift, uint32_t mask,
+                                                const uint32_t* __restrict__ base,
+                                                uint32_t* status, uint32_t* tile_counter,
+                                                uint32_t* err) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    SortSmem<K>& s = *reinterpret_cast<SortSmem<K>*>(smem_raw);
+    __shared__ uint32_t sh_tile;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const unsigned lt_mask = (1u << lane) - 1u;
+    if (threadIdx.x == 0) sh_tile = atomicAdd(tile_counter, 1u);
+    for (int d = lane; d < RADIX; d += 32) s.wcnt[warp][d] = 0;
+    __syncthreads();
+    const int64_t tile = sh_tile;
+    const int64_t wbase = tile * RTILE + (int64_t)warp * (32 * RI);
+    K key[RI];
+    uint32_t val[RI];
+    uint32_t dig[RI];
+    uint32_t rnk[RI];
+#pragma unroll
+    for (int k = 0; k < RI; ++k) {
+        const int64_t i = wbase + k * 32 + lane;
+        const bool valid = i < count;
+        key[k] = valid ? kin[i] : K(0);
+        val[k] = valid ? vin[i] : 0u;
+        const uint32_t d = valid ? digit_of(key[k], shift, mask) : (RADIX + lane);
+        const unsigned peers = __match_any_sync(0xffffffffu, d);
+        const uint32_t before = valid ? s.wcnt[warp][d] : 0u;
+        rnk[k] = before + (uint32_t)__popc(peers & lt_mask);
+        dig[k] = d;
+        __syncwarp();
+        if (valid && lane == __ffs(peers) - 1) s.wcnt[warp][d] = before + (uint32_t)__popc(peers);
+        __syncwarp();
+    }
+    __syncthreads();
+    const int d = threadIdx.x;  // RT == RADIX: one digit per thread from here
+    uint32_t tcount = 0;
+#pragma unroll
+    for (int w = 0; w < RW; ++w) {
+        const uint32_t t = s.wcnt[w][d];
+        s.wcnt[w][d] = tcount;
+        tcount += t;
+    }
+    // publish this tile's count, then look back for the items of digit d in earlier tiles
+    uint32_t* my = status + tile * RADIX + d;
+    atomicExch(my, kFlagAgg | tcount);
+    uint32_t prefix = 0;
+    for (int64_t t = tile - 1; t >= 0;) {
+        const uint32_t v = *reinterpret_cast<volatile uint32_t*>(status + t * RADIX + d);
+        if (v & kFlagInc) { prefix += v & kValMask; break; }
+        if (v & kFlagAgg) { prefix += v & kValMask; --t; continue; }
+        uint32_t spins = 0;  // predecessor not published yet: wait, bounded
+        while ((*reinterpret_cast<volatile uint32_t*>(status + t * RADIX + d) &
+                (kFlagAgg | kFlagInc)) == 0u) {
+            if (++spins > kSpinLimit) { atomicOr(err, DEV_TIMEOUT); t = -1; break; }
+        }
+    }
+    atomicExch(my, kFlagInc | (prefix + tcount));
+    // exclusive scan over digits of the tile counts: positions in the staged tile
+    {
+        uint32_t v = tcount;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(0xffffffffu, v, o);
+            if (lane >= o) v += t;
+        }
+        __shared__ uint32_t wsum[RW];
+        if (lane == 31) wsum[warp] = v;
+        __syncthreads();
+        if (warp == 0) {
+            uint32_t x = (lane < RW) ? wsum[lane] : 0u;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t t = __shfl_up_sync(0xffffffffu, x, o);
+                if (lane >= o) x += t;
+            }
+            if (lane < RW) wsum[lane] = x;
+        }
+        __syncthreads();
+        s.tile_base[d] = v - tcount + (warp > 0 ? wsum[warp - 1] : 0u);
+        s.gofs[d] = (int32_t)(base[d] + prefix);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < RI; ++k) {
+        if (dig[k] < RADIX) {
+            const uint32_t pos = s.tile_base[dig[k]] + s.wcnt[warp][dig[k]] + rnk[k];
+            s.keys[pos] = key[k];
+            s.vals[pos] = val[k];
+        }
+    }
+    __syncthreads();
+    const int64_t rem = count - tile * RTILE;
+    const int valid_n = rem < RTILE ? (int)rem : RTILE;
+    for (int i = threadIdx.x; i < valid_n; i += RT) {
+        const K k = s.keys[i];
+        const uint32_t dd = digit_of(k, shift, mask);
+        const int64_t o = (int64_t)s.gofs[dd] + (i - (int64_t)s.tile_base[dd]);
+        if (o >= 0 && o < count) {
+            kout[o] = k;
+            vout[o] = s.vals[i];
+        } else {
+            atomicOr(err, DEV_TIMEOUT);
+        }
+    }
+}
+
 template <class K>
 spc_status radix_sort_impl(spc_context* ctx, K* keys, uint32_t* vals, K* keys_alt,
                            uint32_t* vals_alt, int64_t count, int end_bit) {
     if (count <= 1 || end_bit <= 0) return SPC_OK;
     const int64_t tiles = (count + RTILE - 1) / RTILE;
-    const size_t hist_bytes = ((size_t)RADIX * tiles + 1) * sizeof(int32_t);
-    SPC_TRY(ensure(ctx, ctx->work.sort_hist, hist_bytes));
-    int32_t* hist = ctx->work.sort_hist.as<int32_t>();
+    const int npass = (end_bit + 7) / 8;
+    if (npass > kMaxPasses || count >= (int64_t)kValMask) return SPC_ERR_TOO_LARGE;
+    // hist [npass][256] | base [npass][256] | tile counters [npass] | status [npass][tiles][256]
+    const size_t words = (size_t)npass * RADIX * 2 + 32 + (size_t)npass * tiles * RADIX;
+    SPC_TRY(ensure(ctx, ctx->work.sort_hist, words * 4));
+    uint32_t* hist = ctx->work.sort_hist.as<uint32_t>();
+    uint32_t* base = hist + (size_t)npass * RADIX;
+    uint32_t* tctr = base + (size_t)npass * RADIX;
+    uint32_t* stat = tctr + 32;
+    SPC_CUDA(cudaMemsetAsync(hist, 0, words * 4, ctx->stream));
     const size_t smem = sizeof(SortSmem<K>);
     static bool attr_set = false;
     if (!attr_set) {
-        SPC_CUDA(cudaFuncSetAttribute(k_rs_downsweep<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        SPC_CUDA(cudaFuncSetAttribute(k_os_pass<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)smem));
         attr_set = true;
     }
+    SPC_LAUNCH(ctx, k_os_hist<K>, grid_for(count, RT, ctx->num_sms * 4), RT, 0, keys, count,
+               npass, end_bit, hist);
+    SPC_LAUNCH(ctx, k_os_bases, 1, RADIX, 0, npass, hist, base);
     K* ka = keys;
     uint32_t* va = vals;
     K* kb = keys_alt;
     uint32_t* vb = vals_alt;
-    int passes = 0;
-    for (int shift = 0; shift < end_bit; shift += 8) {
+    for (int p = 0; p < npass; ++p) {
+        const int shift = 8 * p;
         const int bits = (end_bit - shift) < 8 ? (end_bit - shift) : 8;
         const uint32_t mask = (1u << bits) - 1u;
-        SPC_LAUNCH(ctx, k_rs_upsweep<K>, (unsigned)tiles, RT, 0, ka, count, shift, mask, hist,
-                   tiles);
-        SPC_TRY(scan_i32(ctx, hist, hist, (int64_t)RADIX * tiles));
-        SPC_LAUNCH(ctx, k_rs_downsweep<K>, (unsigned)tiles, RT, smem, ka, va, kb, vb, count,
-                   shift, mask, hist, tiles);
+        SPC_LAUNCH(ctx, k_os_pass<K>, (unsigned)tiles, RT, smem, ka, va, kb, vb, count, shift,
+                   mask, base + (size_t)p * RADIX, stat + (size_t)p * tiles * RADIX, tctr + p,
+                   ctx->d_status);
         K* tk = ka; ka = kb; kb = tk;
         uint32_t* tv = va; va = vb; vb = tv;
-        ++passes;
     }
-    if (passes & 1) {
+    if (npass & 1) {
         SPC_CUDA(cudaMemcpyAsync(keys, ka, (size_t)count * sizeof(K), cudaMemcpyDeviceToDevice,
                                  ctx->stream));
         SPC_CUDA(cudaMemcpyAsync(vals, va, (size_t)count * sizeof(uint32_t),

@@ -412,3 +412,19 @@ def test_prefix_filter_retry_on_cliques(ctx):
             lift, nc, st = ctx.coarsen(api.CSR.from_graph(g), n_c, levels=1)
             assert nc == ref.n_c
             _check_level(ctx.level(0), ref)
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_scores_with_extreme_weight_ranges(ctx, seed):
+    """Weights spanning 1e-300 .. 1e300: normalised weights reach the subnormal range, which the
+    per-row reciprocal division must hand to the IEEE division."""
+    api = _api()
+    g0 = I.random_graph(300, 0.05, 40 + seed, weight="float", dtype=np.float64, connected=True)
+    rng = np.random.default_rng(seed)
+    w = 10.0 ** rng.uniform(-300, 300, size=g0.m)
+    g = I.csr_from_edges(g0.n, g0.eu, g0.ev, w)
+    ref = O.score(g)
+    f = ctx.score(api.CSR.from_graph(g)).cpu().numpy()
+    assert np.array_equal(_bits(f), _bits(ref))
+    p_ref = O.normalise(g, O.degree(g))
+    assert (p_ref[p_ref > 0] < 2.0 ** -1000).any()  # the fallback range is exercised
