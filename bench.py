@@ -404,6 +404,9 @@ def main():
         sampler.start()
         time.sleep(0.3)
     ctx.time_kernel(dominant)
+    step()  # untimed: re-captures the schedule with the dominant kernel's events in it
+    ctx.kernel_time()
+    ctx.time_kernel(dominant)
     if ws > 1:
         dist.barrier()
     torch.cuda.synchronize()

@@ -195,10 +195,13 @@ class Context:
 
     # ---- the method ----------------------------------------------------------------------
     def coarsen(self, g: CSR, n_c: int, levels: int = 1, validate: bool = True,
-                schedule: int = 0, lift_out: Optional[torch.Tensor] = None):
-        """Coarsen to n_c super-nodes in `levels` levels; returns (lift, n_c_actual, status)."""
+                schedule: int = 0, lift_out: Optional[torch.Tensor] = None,
+                use_graph: bool = True):
+        """Coarsen to n_c super-nodes in `levels` levels; returns (lift, n_c_actual, status).
+        With use_graph, a call that repeats the previous one on unchanged input replays the
+        recorded schedule as one CUDA graph."""
         c = self._csr(g)
-        opts = N.spc_options(int(levels), int(bool(validate)), 0, int(schedule))
+        opts = N.spc_options(int(levels), int(bool(validate)), int(bool(use_graph)), int(schedule))
         lift = lift_out if lift_out is not None else torch.empty(g.n, dtype=torch.int32,
                                                                  device=g.col.device)
         nca = ctypes.c_int64(0)
@@ -208,11 +211,11 @@ class Context:
         return lift, int(nca.value), st
 
     def coarsen_batched(self, g: CSR, graph_ptr: torch.Tensor, ratio: int, levels: int,
-                        validate: bool = True, schedule: int = 0):
+                        validate: bool = True, schedule: int = 0, use_graph: bool = True):
         """Coarsen every graph of a block-diagonal batch to floor(n_b / ratio) super-nodes."""
         c = self._csr(g)
         B = int(graph_ptr.shape[0] - 1)
-        opts = N.spc_options(int(levels), int(bool(validate)), 0, int(schedule))
+        opts = N.spc_options(int(levels), int(bool(validate)), int(bool(use_graph)), int(schedule))
         lift = torch.empty(g.n, dtype=torch.int32, device=g.col.device)
         gpc = torch.empty(B + 1, dtype=torch.int64, device=g.col.device)
         st = N.check(self.lib.spc_coarsen_batched(self._handle, ctypes.byref(c), _ptr(graph_ptr),

@@ -62,6 +62,7 @@ spc_status ensure(spc_context* ctx, Buf& b, size_t bytes) {
     bytes = (bytes + 255) & ~(size_t)255;
     if (bytes == 0) bytes = 256;
     if (b.p && b.bytes >= bytes) return SPC_OK;
+    if (capturing(ctx)) return SPC_ERR_CUDA;  // a capture replays a recorded run: no growth
     if (b.p) {
         // the old block may still be read by queued work
         SPC_CUDA(cudaStreamSynchronize(ctx->stream));
@@ -85,6 +86,11 @@ static bool timed(const Timer& t, const char* name) {
     return t.on && (t.substr == "*" || strstr(name, t.substr.c_str()) != nullptr);
 }
 
+cudaError_t record_event(spc_context* ctx, cudaEvent_t ev) {
+    if (capturing(ctx)) return cudaEventRecordWithFlags(ev, ctx->stream, cudaEventRecordExternal);
+    return cudaEventRecord(ev, ctx->stream);
+}
+
 void before_launch(spc_context* ctx, const char* name) {
     Timer& t = ctx->timer;
     ctx->launches += 1;
@@ -97,14 +103,78 @@ void before_launch(spc_context* ctx, const char* name) {
         cudaEventCreate(&a);
         cudaEventCreate(&b);
     }
-    cudaEventRecord(a, ctx->stream);
-    t.pending.push_back({name, a, b});
+    record_event(ctx, a);
+    if (capturing(ctx)) ctx->replay.timed.push_back({name, {a, b}});
+    else t.pending.push_back({name, a, b});
 }
 
 void after_launch(spc_context* ctx, const char* name) {
     Timer& t = ctx->timer;
     if (!timed(t, name)) return;
-    cudaEventRecord(t.pending.back().b, ctx->stream);
+    if (capturing(ctx)) record_event(ctx, ctx->replay.timed.back().second.second);
+    else record_event(ctx, t.pending.back().b);
+}
+
+static void timer_add(Timer& t, const char* name, double ms) {
+    t.total_ms += ms;
+    t.launches += 1;
+    for (auto& pk : t.per_kernel) {
+        if (pk.first == name) {
+            pk.second.first += 1;
+            pk.second.second += ms;
+            return;
+        }
+    }
+    t.per_kernel.push_back({std::string(name), {1, ms}});
+}
+
+__global__ void k_expect(const void* dev, int bytes, long long want, int32_t* mismatch) {
+    if (threadIdx.x != 0) return;
+    const long long got = bytes == 8 ? *static_cast<const long long*>(dev)
+                                     : (long long)*static_cast<const int32_t*>(dev);
+    if (got != want) *mismatch = 1;
+}
+
+spc_status read_vals(spc_context* ctx, int count, const void* const* dev, const int* bytes,
+                     int64_t* out) {
+    Replay& R = ctx->replay;
+    if (R.mode == Replay::kCapture) {
+        for (int i = 0; i < count; ++i) {
+            if (R.pos >= R.log.size()) return SPC_ERR_CUDA;  // control flow left the record
+            out[i] = R.log[R.pos++];
+            SPC_LAUNCH(ctx, k_expect, 1, 32, 0, dev[i], bytes[i], (long long)out[i],
+                       R.d_mismatch);
+        }
+        return SPC_OK;
+    }
+    for (int i = 0; i < count; ++i) {
+        SPC_CUDA(cudaMemcpyAsync(ctx->h_scalars + 16 + i, dev[i], bytes[i], cudaMemcpyDeviceToHost,
+                                 ctx->stream));
+    }
+    SPC_CUDA(cudaStreamSynchronize(ctx->stream));
+    for (int i = 0; i < count; ++i) {
+        out[i] = bytes[i] == 8 ? ctx->h_scalars[16 + i]
+                               : (int64_t)*reinterpret_cast<int32_t*>(ctx->h_scalars + 16 + i);
+        if (R.mode == Replay::kRecord) R.log.push_back(out[i]);
+    }
+    return SPC_OK;
+}
+
+spc_status read_i32(spc_context* ctx, const int32_t* dev, int64_t* out) {
+    const void* p = dev;
+    const int b = 4;
+    return read_vals(ctx, 1, &p, &b, out);
+}
+
+spc_status read_i64(spc_context* ctx, const int64_t* dev, int64_t* out) {
+    const void* p = dev;
+    const int b = 8;
+    return read_vals(ctx, 1, &p, &b, out);
+}
+
+spc_status check_status(spc_context* ctx) {
+    if (capturing(ctx)) return SPC_OK;
+    return sync_status(ctx);
 }
 
 spc_status sync_status(spc_context* ctx) {
@@ -351,12 +421,6 @@ struct Schedule {
     int64_t ratio = 1;
 };
 
-static int pick_schedule(const GraphView& g, int requested) {
-    if (requested == 1 || requested == 2) return requested;
-    // rows with many upper neighbours favour a warp per row; meshes favour edge tiles
-    const double avg = g.n > 0 ? (double)g.nnz / (double)g.n : 0.0;
-    return avg > 48.0 ? 2 : 1;
-}
 
 static spc_status run_levels(spc_context* ctx, const GraphView& g0, const Schedule& S,
                              int32_t* lift_total_dev, int64_t* n_c_final, int32_t* warn) {
@@ -378,7 +442,7 @@ static spc_status run_levels(spc_context* ctx, const GraphView& g0, const Schedu
     ctx->n_levels = 0;
     for (int l = 0; l < L; ++l) {
         LevelBufs& lv = ctx->levels[l];
-        SPC_CUDA(cudaEventRecord(lv.ev0, ctx->stream));
+        SPC_CUDA(record_event(ctx, lv.ev0));
         SelectArgs sa;
         if (batched) {
             const int64_t div = (l == L - 1) ? S.ratio : (1ll << (l + 1));
@@ -394,7 +458,7 @@ static spc_status run_levels(spc_context* ctx, const GraphView& g0, const Schedu
             if (t < 1) t = 1;
             sa.target = t;
         }
-        SPC_TRY(run_score(ctx, cur, S.validate && l == 0, lv.score.p, pick_schedule(cur, S.schedule)));
+        SPC_TRY(run_score(ctx, cur, S.validate && l == 0, lv.score.p, S.schedule));
         lv.n = cur.n;
         lv.m = cur.m;
         int64_t n_c = 0;
@@ -402,7 +466,7 @@ static spc_status run_levels(spc_context* ctx, const GraphView& g0, const Schedu
         SPC_TRY(run_select(ctx, cur, lv.score.p, sa, lv.lift.as<int32_t>(), nullptr, &n_c,
                            lv.graph_ptr_c.as<int64_t>(), &st));
         SPC_TRY(run_contract(ctx, cur, lv.lift.as<int32_t>(), n_c, lv));
-        SPC_CUDA(cudaEventRecord(lv.ev1, ctx->stream));
+        SPC_CUDA(record_event(ctx, lv.ev1));
         lv.status = st;
         lv.wtype = cur.wtype;
         if (st == SPC_WARN_TARGET_NOT_REACHED) *warn = 1;
@@ -426,6 +490,7 @@ static spc_status run_levels(spc_context* ctx, const GraphView& g0, const Schedu
                    ctx->levels[l].lift.as<int32_t>(), lift_total_dev);
     }
     *n_c_final = cur.n;
+    if (capturing(ctx)) return SPC_OK;
     SPC_TRY(sync_status(ctx));
     for (int l = 0; l < L; ++l) {
         float ms = -1.f;
@@ -435,6 +500,198 @@ static spc_status run_levels(spc_context* ctx, const GraphView& g0, const Schedu
             (void)cudaGetLastError();
     }
     return SPC_OK;
+}
+
+// ---- recorded schedule, captured once, replayed ---------------------------------------------
+
+__device__ __forceinline__ unsigned long long mix64(unsigned long long x) {
+    x += 0x9E3779B97F4A7C15ull;
+    x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+    x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+    return x ^ (x >> 31);
+}
+
+// position-sensitive checksum of `bytes` bytes (a multiple of 4), added into *acc
+__global__ void k_checksum(const uint32_t* __restrict__ w, int64_t words, unsigned long long salt,
+                           unsigned long long* acc) {
+    unsigned long long s = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < words;
+         i += (int64_t)gridDim.x * blockDim.x)
+        s += mix64(((unsigned long long)w[i] << 32) ^ (unsigned long long)i ^ salt);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0 && s) atomicAdd(acc, s);
+}
+
+static spc_status input_checksum(spc_context* ctx, const GraphView& v, const Schedule& S,
+                                 unsigned long long* out) {
+    Replay& R = ctx->replay;
+    if (!R.d_hash) SPC_CUDA(cudaMalloc(&R.d_hash, 256));
+    SPC_CUDA(cudaMemsetAsync(R.d_hash, 0, 8, ctx->stream));
+    const int maxb = ctx->num_sms * 4;
+    struct Arr { const void* p; int64_t bytes; unsigned long long salt; };
+    const Arr arrs[4] = {{v.rowptr, (v.n + 1) * 8, 0x1111ull << 40},
+                         {v.col, v.nnz * 4, 0x2222ull << 40},
+                         {v.w, v.nnz * (int64_t)wsize(v.wtype), 0x3333ull << 40},
+                         {S.d_graph_ptr, S.d_graph_ptr ? (S.B + 1) * 8 : 0, 0x4444ull << 40}};
+    for (const Arr& ar : arrs) {
+        if (!ar.p || ar.bytes <= 0) continue;
+        const int64_t words = ar.bytes / 4;
+        SPC_LAUNCH(ctx, k_checksum, grid_for(words, kThreads, maxb), kThreads, 0,
+                   static_cast<const uint32_t*>(ar.p), words, ar.salt, R.d_hash);
+    }
+    SPC_CUDA(cudaMemcpyAsync(ctx->h_scalars + 24, R.d_hash, 8, cudaMemcpyDeviceToHost,
+                             ctx->stream));
+    SPC_CUDA(cudaStreamSynchronize(ctx->stream));
+    *out = (unsigned long long)ctx->h_scalars[24];
+    return SPC_OK;
+}
+
+static void drop_graph(Replay& R) {
+    if (R.exec) cudaGraphExecDestroy(R.exec);
+    if (R.graph) cudaGraphDestroy(R.graph);
+    R.exec = nullptr;
+    R.graph = nullptr;
+}
+
+static std::vector<int64_t> call_key(const GraphView& v, const Schedule& S) {
+    return {(int64_t)(intptr_t)v.rowptr, (int64_t)(intptr_t)v.col, (int64_t)(intptr_t)v.w, v.n,
+            v.nnz, (int64_t)v.wtype, S.levels, S.validate ? 1 : 0, S.schedule, S.n_c, S.B,
+            (int64_t)(intptr_t)S.d_graph_ptr, S.ratio};
+}
+
+static spc_status capture_graph(spc_context* ctx, const GraphView& v, const Schedule& S,
+                                int32_t* lift_int) {
+    Replay& R = ctx->replay;
+    if (!R.cap_stream) SPC_CUDA(cudaStreamCreateWithFlags(&R.cap_stream, cudaStreamNonBlocking));
+    if (!R.d_mismatch) SPC_CUDA(cudaMalloc(&R.d_mismatch, 256));
+    for (auto& pr : R.timed) {
+        ctx->timer.pool.push_back(pr.second.first);
+        ctx->timer.pool.push_back(pr.second.second);
+    }
+    R.timed.clear();
+    cudaStream_t user = ctx->stream;
+    ctx->stream = R.cap_stream;
+    R.mode = Replay::kCapture;
+    R.pos = 0;
+    const int64_t l0 = ctx->launches;
+    cudaError_t e = cudaStreamBeginCapture(R.cap_stream, cudaStreamCaptureModeThreadLocal);
+    spc_status st = SPC_ERR_CUDA;
+    int64_t ncf = 0;
+    int32_t warn = 0;
+    if (e == cudaSuccess) st = run_levels(ctx, v, S, lift_int, &ncf, &warn);
+    cudaGraph_t g = nullptr;
+    if (e == cudaSuccess) e = cudaStreamEndCapture(R.cap_stream, &g);
+    ctx->stream = user;
+    R.mode = Replay::kDirect;
+    const int64_t kernels = ctx->launches - l0;
+    ctx->launches = l0;
+    if (st != SPC_OK || e != cudaSuccess || R.pos != R.log.size() || g == nullptr) {
+        (void)cudaGetLastError();
+        if (g) cudaGraphDestroy(g);
+        return SPC_ERR_CUDA;
+    }
+    e = cudaGraphInstantiate(&R.exec, g, 0);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        cudaGraphDestroy(g);
+        R.exec = nullptr;
+        return SPC_ERR_CUDA;
+    }
+    R.graph = g;
+    R.graph_kernels = kernels;
+    R.timer_substr = ctx->timer.on ? ctx->timer.substr : "";
+    return SPC_OK;
+}
+
+// launch the captured schedule; > 0 return: the in-graph checks disagreed with the record
+static spc_status replay_graph(spc_context* ctx, bool* mismatch) {
+    Replay& R = ctx->replay;
+    SPC_CUDA(cudaMemsetAsync(R.d_mismatch, 0, 4, ctx->stream));
+    SPC_CUDA(cudaGraphLaunch(R.exec, ctx->stream));
+    ctx->launches += R.graph_kernels;
+    SPC_CUDA(cudaMemcpyAsync(ctx->h_scalars + 25, R.d_mismatch, 4, cudaMemcpyDeviceToHost,
+                             ctx->stream));
+    SPC_CUDA(cudaMemcpyAsync(ctx->h_status, ctx->d_status, 4, cudaMemcpyDeviceToHost,
+                             ctx->stream));
+    SPC_CUDA(cudaStreamSynchronize(ctx->stream));
+    *mismatch = *reinterpret_cast<int32_t*>(ctx->h_scalars + 25) != 0;
+    if (ctx->timer.on && ctx->timer.substr == R.timer_substr) {
+        for (auto& pr : R.timed) {
+            float ms = 0.f;
+            SPC_CUDA(cudaEventElapsedTime(&ms, pr.second.first, pr.second.second));
+            timer_add(ctx->timer, pr.first, ms);
+        }
+    }
+    return status_from_bits(*ctx->h_status);
+}
+
+// One coarsening call: replay the captured graph when this call repeats the recorded one on
+// unchanged input, otherwise run host-driven (recording it when graphs are enabled).
+static spc_status drive(spc_context* ctx, const GraphView& v, const Schedule& S, bool use_graph,
+                        int64_t* ncf, int32_t* warn) {
+    Replay& R = ctx->replay;
+    SPC_TRY(ensure(ctx, ctx->work.lift_final, ((size_t)v.n + 1) * 4));
+    int32_t* lift_int = ctx->work.lift_final.as<int32_t>();
+    const std::vector<int64_t> key = call_key(v, S);
+    const std::string tsub = ctx->timer.on ? ctx->timer.substr : "";
+    unsigned long long hsh = 0;
+    if (use_graph) SPC_TRY(input_checksum(ctx, v, S, &hsh));
+    if (use_graph && R.recorded && R.key == key && R.hash == hsh) {
+        if (R.exec && R.timer_substr != tsub) drop_graph(R);
+        if (!R.exec && capture_graph(ctx, v, S, lift_int) != SPC_OK) {
+            drop_graph(R);
+            R.recorded = false;
+        }
+        if (R.exec) {
+            bool mismatch = false;
+            const spc_status st = replay_graph(ctx, &mismatch);
+            if (st < 0) return st;
+            if (!mismatch) {
+                const int L = (int)R.metas.size();
+                for (int l = 0; l < L; ++l) {
+                    LevelBufs& lv = ctx->levels[l];
+                    lv.n = R.metas[l].n; lv.m = R.metas[l].m; lv.n_c = R.metas[l].n_c;
+                    lv.m_c = R.metas[l].m_c; lv.m_inter = R.metas[l].m_inter;
+                    lv.status = R.metas[l].status; lv.wtype = R.metas[l].wtype;
+                    float ms = -1.f;
+                    if (cudaEventElapsedTime(&ms, lv.ev0, lv.ev1) != cudaSuccess) {
+                        (void)cudaGetLastError();
+                        ms = -1.f;
+                    }
+                    lv.ms = ms;
+                }
+                ctx->n_levels = L;
+                *ncf = R.n_c_final;
+                *warn = R.warn;
+                return SPC_OK;
+            }
+            drop_graph(R);  // the device disagreed with the record: run host-driven again
+            R.recorded = false;
+        }
+    }
+    R.mode = use_graph ? Replay::kRecord : Replay::kDirect;
+    R.log.clear();
+    const spc_status st = run_levels(ctx, v, S, lift_int, ncf, warn);
+    R.mode = Replay::kDirect;
+    drop_graph(R);
+    R.recorded = false;
+    if (st == SPC_OK && use_graph) {
+        R.recorded = true;
+        R.key = key;
+        R.hash = hsh;
+        R.metas.clear();
+        for (int l = 0; l < ctx->n_levels; ++l) {
+            const LevelBufs& lv = ctx->levels[l];
+            LevelMeta mt;
+            mt.n = lv.n; mt.m = lv.m; mt.n_c = lv.n_c; mt.m_c = lv.m_c; mt.m_inter = lv.m_inter;
+            mt.status = lv.status; mt.wtype = lv.wtype;
+            R.metas.push_back(mt);
+        }
+        R.n_c_final = *ncf;
+        R.warn = *warn;
+    }
+    return st;
 }
 
 }  // namespace spc
@@ -511,6 +768,16 @@ void spc_context_destroy(spc_context* ctx) {
         cudaEventDestroy(pr.b);
     }
     for (auto ev : ctx->timer.pool) cudaEventDestroy(ev);
+    for (auto& pr : ctx->replay.timed) {
+        cudaEventDestroy(pr.second.first);
+        cudaEventDestroy(pr.second.second);
+    }
+    drop_graph(ctx->replay);
+    if (ctx->replay.d_mismatch) cudaFree(ctx->replay.d_mismatch);
+    if (ctx->replay.d_hash) cudaFree(ctx->replay.d_hash);
+    if (ctx->replay.cap_stream) cudaStreamDestroy(ctx->replay.cap_stream);
+    for (auto ev : ctx->tune_ev)
+        if (ev) cudaEventDestroy(ev);
     cudaFree(ctx->d_status);
     cudaFreeHost(ctx->h_status);
     cudaFreeHost(ctx->h_scalars);
@@ -639,13 +906,10 @@ spc_status spc_coarsen(spc_context* ctx, const spc_csr* g, int64_t n_c, const sp
     S.validate = o.validate != 0;
     S.schedule = o.schedule;
     S.n_c = n_c;
-    const bool dev_lift = is_device_ptr(lift_out);
-    SPC_TRY(ensure(ctx, ctx->work.stage_lift, ((size_t)v.n + 1) * 4));
-    int32_t* lift = dev_lift ? lift_out : ctx->work.stage_lift.as<int32_t>();
     int64_t ncf = 0;
     int32_t warn = 0;
-    SPC_TRY(run_levels(ctx, v, S, lift, &ncf, &warn));
-    if (!dev_lift) SPC_TRY(copy_out(ctx, lift_out, lift, (size_t)v.n * 4));
+    SPC_TRY(drive(ctx, v, S, o.use_graph != 0, &ncf, &warn));
+    SPC_TRY(copy_out(ctx, lift_out, ctx->work.lift_final.p, (size_t)v.n * 4));
     SPC_CUDA(cudaStreamSynchronize(ctx->stream));
     if (n_c_actual) *n_c_actual = ncf;
     return warn ? SPC_WARN_TARGET_NOT_REACHED : SPC_OK;
@@ -676,13 +940,10 @@ spc_status spc_coarsen_batched(spc_context* ctx, const spc_csr* g, const int64_t
     S.B = B;
     S.d_graph_ptr = gp_dev;
     S.ratio = ratio;
-    const bool dev_lift = is_device_ptr(lift_out);
-    SPC_TRY(ensure(ctx, ctx->work.stage_lift, ((size_t)v.n + 1) * 4));
-    int32_t* lift = dev_lift ? lift_out : ctx->work.stage_lift.as<int32_t>();
     int64_t ncf = 0;
     int32_t warn = 0;
-    SPC_TRY(run_levels(ctx, v, S, lift, &ncf, &warn));
-    if (!dev_lift) SPC_TRY(copy_out(ctx, lift_out, lift, (size_t)v.n * 4));
+    SPC_TRY(drive(ctx, v, S, o.use_graph != 0, &ncf, &warn));
+    SPC_TRY(copy_out(ctx, lift_out, ctx->work.lift_final.p, (size_t)v.n * 4));
     if (graph_ptr_c_out)
         SPC_TRY(copy_out(ctx, graph_ptr_c_out, ctx->levels[L - 1].graph_ptr_c.p,
                          ((size_t)B + 1) * 8));

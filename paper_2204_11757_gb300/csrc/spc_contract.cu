@@ -275,10 +275,8 @@ spc_status long_segment_sums(spc_context* ctx, const int32_t* start, const uint3
                    w_und, out, long_list, long_cnt, ctx->d_status);
         return SPC_OK;
     } else {
-        SPC_CUDA(cudaMemcpyAsync(ctx->h_scalars, long_cnt, sizeof(int32_t),
-                                 cudaMemcpyDeviceToHost, ctx->stream));
-        SPC_CUDA(cudaStreamSynchronize(ctx->stream));
-        const int64_t nlong = reinterpret_cast<int32_t*>(ctx->h_scalars)[0];
+        int64_t nlong = 0;
+        SPC_TRY(read_i32(ctx, long_cnt, &nlong));
         if (nlong == 0) return SPC_OK;
         int64_t* len = W.seg_len.as<int64_t>();
         int64_t* base = W.seg_base.as<int64_t>();
@@ -286,10 +284,8 @@ spc_status long_segment_sums(spc_context* ctx, const int32_t* start, const uint3
         SPC_LAUNCH(ctx, k_long_seg_prep, grid_for(nlong, kThreads, ctx->num_sms * 8), kThreads, 0,
                    long_list, long_cnt, start, key, len, oidx);
         SPC_TRY(scan_i64_i64(ctx, len, base, nlong));
-        SPC_CUDA(cudaMemcpyAsync(ctx->h_scalars, base + nlong, sizeof(int64_t),
-                                 cudaMemcpyDeviceToHost, ctx->stream));
-        SPC_CUDA(cudaStreamSynchronize(ctx->stream));
-        const int64_t total = ctx->h_scalars[0];
+        int64_t total = 0;
+        SPC_TRY(read_i64(ctx, base + nlong, &total));
         SPC_TRY(ensure(ctx, W.seg_terms, (size_t)(total + 1) * sizeof(WT)));
         WT* terms = W.seg_terms.as<WT>();
         SPC_LAUNCH(ctx, k_gather_long_terms<WT>, grid_for(total, kThreads, ctx->num_sms * 8),
@@ -331,13 +327,14 @@ spc_status contract_typed(spc_context* ctx, const GraphView& g, const int32_t* l
         SPC_LAUNCH(ctx, k_scatter_keys, gm, kThreads, 0, m, nb, W.eu.as<int32_t>(),
                    W.ev.as<int32_t>(), lift, inter_pos, intra_pos, ckey, cval, ikey, ival, emap);
     }
-    SPC_CUDA(cudaMemcpyAsync(ctx->h_scalars, inter_pos + m, sizeof(int32_t),
-                             cudaMemcpyDeviceToHost, ctx->stream));
-    SPC_CUDA(cudaMemcpyAsync(reinterpret_cast<int32_t*>(ctx->h_scalars) + 1, intra_pos + m,
-                             sizeof(int32_t), cudaMemcpyDeviceToHost, ctx->stream));
-    SPC_CUDA(cudaStreamSynchronize(ctx->stream));
-    const int64_t m_inter = reinterpret_cast<int32_t*>(ctx->h_scalars)[0];
-    const int64_t m_intra = reinterpret_cast<int32_t*>(ctx->h_scalars)[1];
+    int64_t cnts[2];
+    {
+        const void* ptrs[2] = {inter_pos + m, intra_pos + m};
+        const int bytes[2] = {4, 4};
+        SPC_TRY(read_vals(ctx, 2, ptrs, bytes, cnts));
+    }
+    const int64_t m_inter = cnts[0];
+    const int64_t m_intra = cnts[1];
     // self-mass: runs of equal super-node ids after a stable sort, summed in eid order
     Acc* self_mass = lv.self_mass.as<Acc>();
     SPC_CUDA(cudaMemsetAsync(self_mass, 0, (size_t)n_c * sizeof(Acc), ctx->stream));
@@ -353,11 +350,9 @@ spc_status contract_typed(spc_context* ctx, const GraphView& g, const int32_t* l
         SPC_LAUNCH(ctx, k_heads<uint32_t>, gi, kThreads, 0, m_intra, ikey, ihead);
         SPC_TRY(scan_flags_u8(ctx, ihead, ihpos, m_intra));
         SPC_LAUNCH(ctx, k_run_starts, gi, kThreads, 0, m_intra, ihead, ihpos, istart);
-        SPC_CUDA(cudaMemcpyAsync(ctx->h_scalars, ihpos + m_intra, sizeof(int32_t),
-                                 cudaMemcpyDeviceToHost, ctx->stream));
         SPC_CUDA(cudaMemsetAsync(long_cnt, 0, sizeof(int32_t), ctx->stream));
-        SPC_CUDA(cudaStreamSynchronize(ctx->stream));
-        const int64_t n_runs = reinterpret_cast<int32_t*>(ctx->h_scalars)[0];
+        int64_t n_runs = 0;
+        SPC_TRY(read_i32(ctx, ihpos + m_intra, &n_runs));
         SPC_LAUNCH(ctx, (k_segsum_short<WT, Acc>), grid_for(n_runs, kThreads, maxb), kThreads, 0,
                    n_runs, istart, ival, ikey, W.w_und.as<WT>(), self_mass, long_list, long_cnt,
                    status);
@@ -380,10 +375,7 @@ spc_status contract_typed(spc_context* ctx, const GraphView& g, const int32_t* l
         SPC_TRY(scan_flags_u8(ctx, head, hpos, m_inter));
         SPC_LAUNCH(ctx, k_emit_segments, gi, kThreads, 0, m_inter, nb, ckey, cval, head, hpos,
                    emap, perm, seg, cU, cV);
-        SPC_CUDA(cudaMemcpyAsync(ctx->h_scalars, hpos + m_inter, sizeof(int32_t),
-                                 cudaMemcpyDeviceToHost, ctx->stream));
-        SPC_CUDA(cudaStreamSynchronize(ctx->stream));
-        m_c = reinterpret_cast<int32_t*>(ctx->h_scalars)[0];
+        SPC_TRY(read_i32(ctx, hpos + m_inter, &m_c));
     }
     SPC_LAUNCH(ctx, k_set_i32, 1, 32, 0, seg + m_c, (int32_t)m_inter);
     WT* a_und = lv.a_und.as<WT>();

@@ -92,6 +92,7 @@ struct Work {
     Buf i_key, i_val, i_key2, i_val2, long_segs;                // intra edges (self-mass)
     Buf sort_hist, scan_tmp;                                    // sort / scan temporaries
     Buf stage_rowptr, stage_col, stage_w, stage_lift, stage_gptr;  // host staging
+    Buf lift_final;                                             // composed lift of a call
 };
 
 struct Timer {
@@ -106,6 +107,36 @@ struct Timer {
     std::vector<Pending> pending;
     std::vector<cudaEvent_t> pool;
     std::vector<std::pair<std::string, std::pair<int64_t, double>>> per_kernel;
+};
+
+// Recorded schedule for graph replay: every value the host driver reads back from the device
+// during a host-driven run is logged; a capture replays the same control flow from the log and
+// enqueues a device-side check of each logged value instead of the read.
+struct LevelMeta {
+    int64_t n = 0, m = 0, n_c = 0, m_c = 0, m_inter = 0;
+    int32_t status = 0;
+    spc_dtype wtype = SPC_F64;
+};
+
+struct Replay {
+    enum Mode { kDirect = 0, kRecord = 1, kCapture = 2 };
+    Mode mode = kDirect;
+    std::vector<int64_t> log;
+    size_t pos = 0;
+    std::vector<int64_t> key;        // the call the log belongs to
+    bool recorded = false;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int64_t graph_kernels = 0;       // kernel nodes in the captured graph
+    std::string timer_substr;        // kernels timed inside the captured graph
+    std::vector<std::pair<const char*, std::pair<cudaEvent_t, cudaEvent_t>>> timed;
+    std::vector<LevelMeta> metas;
+    int64_t n_c_final = 0;
+    int32_t warn = 0;
+    int32_t* d_mismatch = nullptr;   // set by the checks of a replay
+    unsigned long long* d_hash = nullptr;
+    unsigned long long hash = 0;     // checksum of the recorded call's input arrays
+    cudaStream_t cap_stream = nullptr;
 };
 
 }  // namespace spc
@@ -125,6 +156,10 @@ struct spc_context {
     int32_t n_levels = 0;
     spc::Timer timer;
     int64_t launches = 0;
+    spc::Replay replay;
+    // score-schedule autotuner: (dtype, log2 mean row length, log2 m) -> 1 edge tiles, 2 warp/row
+    std::vector<std::pair<int64_t, int>> tuned;
+    cudaEvent_t tune_ev[3] = {nullptr, nullptr, nullptr};
 };
 
 namespace spc {
@@ -238,5 +273,19 @@ spc_status run_contract_backward(spc_context* ctx, const int32_t* emap, int64_t 
 
 // read the status word (synchronises)
 spc_status sync_status(spc_context* ctx);
+
+// A device value the host driver needs (int32 or int64 at `dev`).  Direct and recording runs
+// copy it back (synchronising; a recording run logs it); a capture returns the logged value and
+// enqueues a check that flags a replay whose device value differs.
+spc_status read_vals(spc_context* ctx, int count, const void* const* dev, const int* bytes,
+                     int64_t* out);
+spc_status read_i32(spc_context* ctx, const int32_t* dev, int64_t* out);
+spc_status read_i64(spc_context* ctx, const int64_t* dev, int64_t* out);
+// Mid-pipeline status check: synchronises and returns the status (0 during a capture, whose
+// status is read after the replay).
+spc_status check_status(spc_context* ctx);
+inline bool capturing(const spc_context* ctx) { return ctx->replay.mode == Replay::kCapture; }
+// record an event (an external event node during a capture)
+cudaError_t record_event(spc_context* ctx, cudaEvent_t ev);
 
 }  // namespace spc

@@ -523,13 +523,14 @@ spc_status finish_select(spc_context* ctx, const GraphView& g, const SelectArgs&
         SPC_LAUNCH(ctx, k_graph_ptr_c, grid_for(sa.B + 1, kThreads, maxb), kThreads, 0, sa.B,
                    sa.d_graph_ptr, ids, sa.d_targets, graph_ptr_c, warn);
     }
-    SPC_CUDA(cudaMemcpyAsync(ctx->h_scalars, ids + n, sizeof(int32_t), cudaMemcpyDeviceToHost,
-                             ctx->stream));
-    SPC_CUDA(cudaMemcpyAsync(ctx->h_scalars + 1, warn, sizeof(int32_t), cudaMemcpyDeviceToHost,
-                             ctx->stream));
-    SPC_CUDA(cudaStreamSynchronize(ctx->stream));
-    const int64_t n_c = *reinterpret_cast<int32_t*>(ctx->h_scalars);
-    const int32_t warn_b = *reinterpret_cast<int32_t*>(ctx->h_scalars + 1);
+    int64_t vals[2];
+    {
+        const void* ptrs[2] = {ids + n, warn};
+        const int bytes[2] = {4, 4};
+        SPC_TRY(read_vals(ctx, 2, ptrs, bytes, vals));
+    }
+    const int64_t n_c = vals[0];
+    const int32_t warn_b = (int32_t)vals[1];
     *n_c_out = n_c;
     *status_out = (batched ? warn_b != 0 : n_c > sa.target) ? SPC_WARN_TARGET_NOT_REACHED : SPC_OK;
     return SPC_OK;
@@ -604,20 +605,14 @@ spc_status select_typed(spc_context* ctx, const GraphView& g, const KT* key,
                        W.wl_v[out].as<int32_t>(), W.best_k[par].as<unsigned long long>(),
                        W.best_e[par].as<int32_t>(), W.best_k[par ^ 1].as<unsigned long long>(),
                        W.best_e[par ^ 1].as<int32_t>(), parent, W.msf.as<uint8_t>(), status);
-            // next work-list size (host loop; the captured path keeps it on the device)
-            SPC_CUDA(cudaMemcpyAsync(ctx->h_scalars, counters + out, sizeof(int32_t),
-                                     cudaMemcpyDeviceToHost, ctx->stream));
-            SPC_CUDA(cudaStreamSynchronize(ctx->stream));
-            cur = *reinterpret_cast<int32_t*>(ctx->h_scalars);
+            // next work-list size (a capture replays the recorded round count)
+            SPC_TRY(read_i32(ctx, counters + out, &cur));
             // every round at least halves the components that still have edges
             if (round > 64) return SPC_ERR_TIMEOUT;
             // slot `out` (list and count) is the next round's input
         }
         SPC_TRY(scan_flags_u8(ctx, W.msf.as<uint8_t>(), pos, m));
-        SPC_CUDA(cudaMemcpyAsync(ctx->h_scalars, pos + m, sizeof(int32_t), cudaMemcpyDeviceToHost,
-                                 ctx->stream));
-        SPC_CUDA(cudaStreamSynchronize(ctx->stream));
-        n_msf = *reinterpret_cast<int32_t*>(ctx->h_scalars);
+        SPC_TRY(read_i32(ctx, pos + m, &n_msf));
         // the prefix's forest holds Kruskal's first n_msf merges; enough when >= n - n_c
         if (!use_prefix || n_msf >= k_need) break;
         use_prefix = false;

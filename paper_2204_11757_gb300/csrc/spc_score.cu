@@ -577,6 +577,10 @@ k_score_hub_heavy(const int64_t* __restrict__ rowptr, const int32_t* __restrict_
     }
 }
 
+static int pick_default_schedule(int64_t n, int64_t nnz) {
+    return (n > 0 && nnz / n > 48) ? 2 : 1;  // long rows favour a warp per row
+}
+
 template <class WT>
 static spc_status score_typed(spc_context* ctx, GraphView& g, bool validate, void* score,
                               int schedule) {
@@ -603,18 +607,16 @@ static spc_status score_typed(spc_context* ctx, GraphView& g, bool validate, voi
                W.deg.as<Acc>(), W.up_cnt.as<int32_t>(), W.first_up.as<int32_t>(),
                W.lr_base.as<int64_t>(), W.lr_len.as<int64_t>(), W.lr_idx.as<int64_t>(), status);
     SPC_TRY(scan_i32(ctx, W.up_cnt.as<int32_t>(), W.up_ptr.as<int32_t>(), n));
-    // one readback: the status word, the edge count and the number of long rows
-    int32_t* hs = reinterpret_cast<int32_t*>(ctx->h_scalars);
-    SPC_CUDA(cudaMemcpyAsync(hs, W.up_ptr.as<int32_t>() + n, sizeof(int32_t),
-                             cudaMemcpyDeviceToHost, ctx->stream));
-    SPC_CUDA(cudaMemcpyAsync(hs + 1, long_count, sizeof(int32_t), cudaMemcpyDeviceToHost,
-                             ctx->stream));
-    SPC_CUDA(cudaMemcpyAsync(ctx->h_status, status, sizeof(uint32_t), cudaMemcpyDeviceToHost,
-                             ctx->stream));
-    SPC_CUDA(cudaStreamSynchronize(ctx->stream));
-    if (*ctx->h_status) return status_from_bits(*ctx->h_status);
-    const int64_t m = hs[0];
-    const int64_t n_long = hs[1];
+    // the edge count and the number of long rows (and the input checks so far)
+    SPC_TRY(check_status(ctx));
+    int64_t sizes[2];
+    {
+        const void* ptrs[2] = {W.up_ptr.as<int32_t>() + n, long_count};
+        const int bytes[2] = {4, 4};
+        SPC_TRY(read_vals(ctx, 2, ptrs, bytes, sizes));
+    }
+    const int64_t m = sizes[0];
+    const int64_t n_long = sizes[1];
     if (2 * m != nnz) return SPC_ERR_NOT_SYMMETRIC;
     g.m = m;
     if (n_long > 0) {
@@ -638,8 +640,39 @@ static spc_status score_typed(spc_context* ctx, GraphView& g, bool validate, voi
                    W.lr_eoff.as<int64_t>(), W.p.as<P>(), W.eu.as<int32_t>(),
                    W.ev.as<int32_t>(), W.w_und.as<WT>(), status);
     }
-    if (validate) SPC_TRY(sync_status(ctx));  // no later kernel runs on an asymmetric input
+    if (validate) SPC_TRY(check_status(ctx));  // no later kernel runs on an asymmetric input
     if (score == nullptr || m == 0) return SPC_OK;
+    if (schedule != 1 && schedule != 2) {
+        // autotuned: both schedules compute the same bits; time each once per shape bucket
+        int lg_deg = 0, lg_m = 0;
+        while ((1ll << (lg_deg + 1)) <= (n > 0 ? nnz / n : 0)) ++lg_deg;
+        while ((1ll << (lg_m + 1)) <= m) ++lg_m;
+        const int64_t tkey = ((int64_t)g.wtype << 16) | (lg_deg << 8) | lg_m;
+        schedule = 0;
+        for (const auto& tk : ctx->tuned)
+            if (tk.first == tkey) schedule = tk.second;
+        if (schedule == 0 && !capturing(ctx)) {
+            if (!ctx->tune_ev[0])
+                for (auto& ev : ctx->tune_ev) SPC_CUDA(cudaEventCreate(&ev));
+            const int gw = grid_for(n, kThreads / 32, maxb);
+            SPC_CUDA(cudaEventRecord(ctx->tune_ev[0], ctx->stream));
+            SPC_LAUNCH(ctx, (k_score_edges<P, Key>), grid_for(m, kThreads, maxb), kThreads, 0, m,
+                       W.eu.as<int32_t>(), W.ev.as<int32_t>(), g.rowptr, g.col, W.p.as<P>(),
+                       static_cast<Key*>(score), status);
+            SPC_CUDA(cudaEventRecord(ctx->tune_ev[1], ctx->stream));
+            SPC_LAUNCH(ctx, (k_score_warp_row<P, Key>), gw, kThreads, 0, n, g.rowptr, g.col,
+                       W.p.as<P>(), W.up_ptr.as<int32_t>(), W.first_up.as<int32_t>(),
+                       static_cast<Key*>(score), status);
+            SPC_CUDA(cudaEventRecord(ctx->tune_ev[2], ctx->stream));
+            SPC_CUDA(cudaEventSynchronize(ctx->tune_ev[2]));
+            float t_edges = 0.f, t_rows = 0.f;
+            SPC_CUDA(cudaEventElapsedTime(&t_edges, ctx->tune_ev[0], ctx->tune_ev[1]));
+            SPC_CUDA(cudaEventElapsedTime(&t_rows, ctx->tune_ev[1], ctx->tune_ev[2]));
+            schedule = t_rows < t_edges ? 2 : 1;
+            ctx->tuned.push_back({tkey, schedule});
+        }
+        if (schedule == 0) schedule = pick_default_schedule(n, nnz);
+    }
     if (schedule == 2) {
         const int warps_per_block = kThreads / 32;
         const int gw = grid_for(n, warps_per_block, maxb);

@@ -287,13 +287,14 @@ spc_status build_typed(spc_context* ctx, const F* terms, int64_t nseq, const int
                tb.tcnt.as<int64_t>());
     SPC_TRY(scan_i64_i64(ctx, tb.tsize.as<int64_t>(), tb.tab_off.as<int64_t>(), nseq));
     SPC_TRY(scan_i64_i64(ctx, tb.tcnt.as<int64_t>(), tb.trip_off.as<int64_t>(), nseq));
-    SPC_CUDA(cudaMemcpyAsync(ctx->h_scalars, tb.tab_off.as<int64_t>() + nseq, 8,
-                             cudaMemcpyDeviceToHost, ctx->stream));
-    SPC_CUDA(cudaMemcpyAsync(ctx->h_scalars + 1, tb.trip_off.as<int64_t>() + nseq, 8,
-                             cudaMemcpyDeviceToHost, ctx->stream));
-    SPC_CUDA(cudaStreamSynchronize(ctx->stream));
-    const int64_t elems = ctx->h_scalars[0];
-    const int64_t ntrip = ctx->h_scalars[1];
+    int64_t vals[2];
+    {
+        const void* ptrs[2] = {tb.tab_off.as<int64_t>() + nseq, tb.trip_off.as<int64_t>() + nseq};
+        const int bytes[2] = {8, 8};
+        SPC_TRY(read_vals(ctx, 2, ptrs, bytes, vals));
+    }
+    const int64_t elems = vals[0];
+    const int64_t ntrip = vals[1];
     SPC_TRY(ensure(ctx, tb.P, (size_t)elems * 8 + 256));
     SPC_TRY(ensure(ctx, tb.T, (size_t)elems * 4 + 256));
     SPC_TRY(ensure(ctx, tb.csum, (size_t)ntrip * 8 + 256));

@@ -428,3 +428,60 @@ def test_scores_with_extreme_weight_ranges(ctx, seed):
     assert np.array_equal(_bits(f), _bits(ref))
     p_ref = O.normalise(g, O.degree(g))
     assert (p_ref[p_ref > 0] < 2.0 ** -1000).any()  # the fallback range is exercised
+
+
+# ---- the recorded schedule replayed as a CUDA graph ---------------------------------------------
+
+def _levels_equal(a, b):
+    for x, y in zip(a, b):
+        for f in ("lift", "emap", "rowptr_c", "col_c", "w_c", "a_und", "self_mass", "score",
+                  "perm", "seg"):
+            assert torch.equal(getattr(x, f), getattr(y, f)), f
+
+
+def test_graph_replay_matches_host_driven(ctx):
+    """Call 1 runs host-driven and records, call 2 captures and replays, call 3 replays; all
+    three must equal the oracle.  Then the weights change in place: the checksum sends the
+    call back to the host-driven path, which must give the new oracle result."""
+    api = _api()
+    g, cfg = I.config_graph("s2_tri256_f64")
+    levels_ref, total_ref = O.coarsen(g, cfg["ratio"], cfg["mode"])
+    csr = api.CSR.from_graph(g)
+    n0 = ctx.launch_count
+    runs = []
+    for call in range(3):
+        lift, nc, st = ctx.coarsen(csr, g.n // 64, levels=6)
+        assert np.array_equal(lift.cpu().numpy(), total_ref)
+        got = ctx.levels()
+        for lv, ref in zip(got, levels_ref):
+            _check_level(lv, ref)
+        runs.append(got)
+    _levels_equal(runs[0], runs[1])
+    _levels_equal(runs[0], runs[2])
+    assert ctx.launch_count > n0
+    # new weights in the same buffers (scaled unevenly: a different coarsening)
+    rng = np.random.default_rng(3)
+    w_und = g.w_und * rng.uniform(0.5, 2.0, size=g.m)
+    g2 = I.csr_from_edges(g.n, g.eu, g.ev, w_und)
+    csr.w.copy_(torch.from_numpy(g2.w).cuda())
+    levels2, total2 = O.coarsen(g2, cfg["ratio"], cfg["mode"])
+    for call in range(2):
+        lift, nc, st = ctx.coarsen(csr, g.n // 64, levels=6)
+        assert np.array_equal(lift.cpu().numpy(), total2)
+        for lv, ref in zip(ctx.levels(), levels2):
+            _check_level(lv, ref)
+
+
+def test_graph_replay_batched(ctx):
+    api = _api()
+    b, cfg = I.config_graph("s5_batch40_f32")
+    csr = api.CSR.from_graph(b.graph)
+    gp = torch.from_numpy(b.graph_ptr).cuda()
+    outs = [ctx.coarsen_batched(csr, gp, cfg["ratio"], levels=3) for _ in range(3)]
+    for lift, gpc, st in outs[1:]:
+        assert torch.equal(lift, outs[0][0]) and torch.equal(gpc, outs[0][1])
+    res = O.coarsen_batch(b, cfg["ratio"], cfg["mode"])
+    lift = outs[2][0].cpu().numpy(); gpc = outs[2][1].cpu().numpy()
+    for bi, (levels_ref, total_ref) in enumerate(res):
+        n0, n1 = b.graph_ptr[bi], b.graph_ptr[bi + 1]
+        assert np.array_equal(lift[n0:n1] - gpc[bi], total_ref)
