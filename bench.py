@@ -225,10 +225,9 @@ class ClockSampler:
                 "samples": len(rows)}
 
 
-# algorithmic bytes per launch of the kernels that can dominate a step
-def _score_bytes(n, m, s_p, s_f):
-    # eu/ev, rowptr, every row's columns and normalised weights once, the score write
-    return 8 * m + 8 * (n + 1) + 2 * m * (4 + s_p) + m * s_f
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the dominant kernel,
+# from an ncu capture of the same kernel; None where no capture of the current kernel exists
+TRAFFIC = {}
 
 
 def run_batched(args):
@@ -422,6 +421,7 @@ def main():
         dist.barrier()
     launches = ctx.launch_count - launches0
     t_ms = ev0.elapsed_time(ev1) / args.steps
+    dom_prof = ctx.kernel_profile()
     dom_launches, dom_ms = ctx.kernel_time()
     ctx.time_kernel(None)
     clocks = sampler.stop() if rank == 0 else None
@@ -433,25 +433,23 @@ def main():
     value = ws * edges_per_step / (t_ms * 1e-3) / 1e6
 
     # ---- roofline of the dominant kernel --------------------------------------------------------
+    # algorithmic bytes per launch come from the library's per-launch byte models (every input
+    # the operation needs read once, every output written once); the time is the same launches'
+    # CUDA-event durations inside the timed region
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except (OSError, ValueError):
         pass
     hbm = float(peaks.get("hbm_gbs", 6800.0))
-    s_p = 4 if g.w.dtype == np.float32 else 8
-    roof = None
-    if dominant.startswith("(k_score") or dominant.startswith("k_score"):
-        per_step = sum(_score_bytes(int(lv.n), int(lv.m), s_p, s_p) for lv in levels)
-        achieved = per_step * (dom_launches / max(1, len(levels))) / (dom_ms * 1e-3) / 1e9
-        roof = {"kernel": dominant, "bound": "hbm", "achieved": achieved, "peak": hbm,
-                "unit": "GB/s", "frac": achieved / hbm, "traffic": None,
-                "peak_source": "measured" if peaks else "fallback",
-                "launches": dom_launches, "avg_launch_ms": dom_ms / max(1, dom_launches)}
-    else:
-        roof = {"kernel": dominant, "bound": "hbm", "achieved": None, "peak": hbm, "unit": "GB/s",
-                "frac": None, "traffic": None, "launches": dom_launches,
-                "avg_launch_ms": dom_ms / max(1, dom_launches)}
+    dom_bytes = dom_prof.get(dominant, (0, 0.0, 0.0))[2]
+    achieved = dom_bytes / (dom_ms * 1e-3) / 1e9 if dom_bytes > 0 and dom_ms > 0 else None
+    roof = {"kernel": dominant, "bound": "hbm", "achieved": achieved, "peak": hbm,
+            "unit": "GB/s", "frac": achieved / hbm if achieved else None,
+            "traffic": TRAFFIC.get((args.workload, dominant)),
+            "peak_source": "measured" if peaks else "fallback",
+            "launches": dom_launches, "avg_launch_ms": dom_ms / max(1, dom_launches),
+            "algorithmic_bytes_per_launch": dom_bytes / max(1, dom_launches)}
 
     # ---- end to end through host buffers -----------------------------------------------------------
     e2e = None
@@ -521,8 +519,8 @@ def main():
             "gpu_launches": int(launches),
         }
         if args.profile:
-            line["kernel_profile_ms"] = {k: round(v[1], 4) for k, v in
-                                         sorted(prof.items(), key=lambda kv: -kv[1][1])}
+            line["kernel_profile"] = {k: [v[0], round(v[1], 4)] for k, v in
+                                      sorted(prof.items(), key=lambda kv: -kv[1][1])}
             line["profiled_step_ms"] = step_prof_ms
         print(json.dumps(line), flush=True)
     ctx.close()

@@ -253,8 +253,10 @@ SPC_API spc_status spc_time_kernel(spc_context* ctx, const char* kernel_substr);
 SPC_API spc_status spc_kernel_time(spc_context* ctx, int64_t* launches, double* total_ms);
 
 /* Per-kernel breakdown of the timed launches since the last spc_time_kernel: one line per
- * kernel, "name<TAB>launches<TAB>total_ms<LF>", NUL-terminated in buf[len].  Returns
- * SPC_ERR_INVALID_ARG (with the text truncated) if len is too small. */
+ * kernel, "name<TAB>launches<TAB>total_ms<TAB>bytes<LF>", NUL-terminated in buf[len].  bytes is
+ * the sum over those launches of each launch's algorithmic DRAM bytes (every input the
+ * operation needs read once, every output written once), 0 for launches without such a
+ * model.  Returns SPC_ERR_INVALID_ARG (with the text truncated) if len is too small. */
 SPC_API spc_status spc_kernel_profile(spc_context* ctx, char* buf, size_t len);
 
 /* Number of kernel launches issued by the context since it was created (replayed graph

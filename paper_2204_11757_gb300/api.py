@@ -285,13 +285,15 @@ class Context:
         return int(n.value), float(ms.value)
 
     def kernel_profile(self):
-        """{kernel name: (launches, total ms)} for the launches timed since time_kernel()."""
+        """{kernel name: (launches, total ms, algorithmic bytes)} for the launches timed since
+        time_kernel(); bytes are the summed per-launch algorithmic DRAM bytes of the launches
+        that carry a byte model (0 for the others)."""
         buf = ctypes.create_string_buffer(1 << 16)
         N.check(self.lib.spc_kernel_profile(self._handle, buf, len(buf)), "spc_kernel_profile")
         out = {}
         for line in buf.value.decode().splitlines():
-            name, cnt, ms = line.split("\t")
-            out[name] = (int(cnt), float(ms))
+            name, cnt, ms, nbytes = line.split("\t")
+            out[name] = (int(cnt), float(ms), float(nbytes))
         return out
 
     @property

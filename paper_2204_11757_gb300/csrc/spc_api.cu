@@ -94,6 +94,8 @@ cudaError_t record_event(spc_context* ctx, cudaEvent_t ev) {
 void before_launch(spc_context* ctx, const char* name) {
     Timer& t = ctx->timer;
     ctx->launches += 1;
+    const double bytes = t.next_bytes;
+    t.next_bytes = 0.0;
     if (!timed(t, name)) return;
     cudaEvent_t a, b;
     if (t.pool.size() >= 2) {
@@ -104,28 +106,29 @@ void before_launch(spc_context* ctx, const char* name) {
         cudaEventCreate(&b);
     }
     record_event(ctx, a);
-    if (capturing(ctx)) ctx->replay.timed.push_back({name, {a, b}});
-    else t.pending.push_back({name, a, b});
+    if (capturing(ctx)) ctx->replay.timed.push_back({name, a, b, bytes});
+    else t.pending.push_back({name, a, b, bytes});
 }
 
 void after_launch(spc_context* ctx, const char* name) {
     Timer& t = ctx->timer;
     if (!timed(t, name)) return;
-    if (capturing(ctx)) record_event(ctx, ctx->replay.timed.back().second.second);
+    if (capturing(ctx)) record_event(ctx, ctx->replay.timed.back().b);
     else record_event(ctx, t.pending.back().b);
 }
 
-static void timer_add(Timer& t, const char* name, double ms) {
+static void timer_add(Timer& t, const char* name, double ms, double bytes) {
     t.total_ms += ms;
     t.launches += 1;
     for (auto& pk : t.per_kernel) {
-        if (pk.first == name) {
-            pk.second.first += 1;
-            pk.second.second += ms;
+        if (pk.name == name) {
+            pk.launches += 1;
+            pk.ms += ms;
+            pk.bytes += bytes;
             return;
         }
     }
-    t.per_kernel.push_back({std::string(name), {1, ms}});
+    t.per_kernel.push_back({std::string(name), 1, ms, bytes});
 }
 
 __global__ void k_expect(const void* dev, int bytes, long long want, int32_t* mismatch) {
@@ -164,6 +167,20 @@ spc_status read_i32(spc_context* ctx, const int32_t* dev, int64_t* out) {
     const void* p = dev;
     const int b = 4;
     return read_vals(ctx, 1, &p, &b, out);
+}
+
+spc_status read_loop_count(spc_context* ctx, const int32_t* dev, int64_t* out) {
+    Replay& R = ctx->replay;
+    if (R.mode == Replay::kCapture) {
+        if (R.pos >= R.log.size()) return SPC_ERR_CUDA;
+        *out = R.log[R.pos++];
+        // only the count that ends the loop is checked: the loop's kernels take the count from
+        // the device, so a different intermediate count changes no result
+        if (*out == 0)
+            SPC_LAUNCH(ctx, k_expect, 1, 32, 0, dev, 4, 0ll, R.d_mismatch);
+        return SPC_OK;
+    }
+    return read_i32(ctx, dev, out);
 }
 
 spc_status read_i64(spc_context* ctx, const int64_t* dev, int64_t* out) {
@@ -566,8 +583,8 @@ static spc_status capture_graph(spc_context* ctx, const GraphView& v, const Sche
     if (!R.cap_stream) SPC_CUDA(cudaStreamCreateWithFlags(&R.cap_stream, cudaStreamNonBlocking));
     if (!R.d_mismatch) SPC_CUDA(cudaMalloc(&R.d_mismatch, 256));
     for (auto& pr : R.timed) {
-        ctx->timer.pool.push_back(pr.second.first);
-        ctx->timer.pool.push_back(pr.second.second);
+        ctx->timer.pool.push_back(pr.a);
+        ctx->timer.pool.push_back(pr.b);
     }
     R.timed.clear();
     cudaStream_t user = ctx->stream;
@@ -619,8 +636,8 @@ static spc_status replay_graph(spc_context* ctx, bool* mismatch) {
     if (ctx->timer.on && ctx->timer.substr == R.timer_substr) {
         for (auto& pr : R.timed) {
             float ms = 0.f;
-            SPC_CUDA(cudaEventElapsedTime(&ms, pr.second.first, pr.second.second));
-            timer_add(ctx->timer, pr.first, ms);
+            SPC_CUDA(cudaEventElapsedTime(&ms, pr.a, pr.b));
+            timer_add(ctx->timer, pr.name, ms, pr.bytes);
         }
     }
     return status_from_bits(*ctx->h_status);
@@ -769,8 +786,8 @@ void spc_context_destroy(spc_context* ctx) {
     }
     for (auto ev : ctx->timer.pool) cudaEventDestroy(ev);
     for (auto& pr : ctx->replay.timed) {
-        cudaEventDestroy(pr.second.first);
-        cudaEventDestroy(pr.second.second);
+        cudaEventDestroy(pr.a);
+        cudaEventDestroy(pr.b);
     }
     drop_graph(ctx->replay);
     if (ctx->replay.d_mismatch) cudaFree(ctx->replay.d_mismatch);
@@ -1034,18 +1051,7 @@ static spc_status drain_timer(spc_context* ctx) {
     for (auto& pr : t.pending) {
         float ms = 0.f;
         SPC_CUDA(cudaEventElapsedTime(&ms, pr.a, pr.b));
-        t.total_ms += ms;
-        t.launches += 1;
-        bool found = false;
-        for (auto& pk : t.per_kernel) {
-            if (pk.first == pr.name) {
-                pk.second.first += 1;
-                pk.second.second += ms;
-                found = true;
-                break;
-            }
-        }
-        if (!found) t.per_kernel.push_back({std::string(pr.name), {1, (double)ms}});
+        timer_add(t, pr.name, ms, pr.bytes);
         t.pool.push_back(pr.a);
         t.pool.push_back(pr.b);
     }
@@ -1067,8 +1073,8 @@ spc_status spc_kernel_profile(spc_context* ctx, char* buf, size_t len) {
     std::string out;
     char line[512];
     for (auto& pk : ctx->timer.per_kernel) {
-        snprintf(line, sizeof(line), "%s\t%lld\t%.6f\n", pk.first.c_str(),
-                 (long long)pk.second.first, pk.second.second);
+        snprintf(line, sizeof(line), "%s\t%lld\t%.6f\t%.0f\n", pk.name.c_str(),
+                 (long long)pk.launches, pk.ms, pk.bytes);
         out += line;
     }
     if (len) {

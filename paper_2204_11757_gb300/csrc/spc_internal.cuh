@@ -100,13 +100,22 @@ struct Timer {
     bool on = false;
     int64_t launches = 0;
     double total_ms = 0.0;
+    // algorithmic bytes of the next launch (set by note_bytes just before it, 0: no model)
+    double next_bytes = 0.0;
     struct Pending {
         const char* name;
         cudaEvent_t a, b;
+        double bytes;
     };
     std::vector<Pending> pending;
     std::vector<cudaEvent_t> pool;
-    std::vector<std::pair<std::string, std::pair<int64_t, double>>> per_kernel;
+    struct PerKernel {
+        std::string name;
+        int64_t launches;
+        double ms;
+        double bytes;
+    };
+    std::vector<PerKernel> per_kernel;
 };
 
 // Recorded schedule for graph replay: every value the host driver reads back from the device
@@ -129,7 +138,7 @@ struct Replay {
     cudaGraphExec_t exec = nullptr;
     int64_t graph_kernels = 0;       // kernel nodes in the captured graph
     std::string timer_substr;        // kernels timed inside the captured graph
-    std::vector<std::pair<const char*, std::pair<cudaEvent_t, cudaEvent_t>>> timed;
+    std::vector<Timer::Pending> timed;
     std::vector<LevelMeta> metas;
     int64_t n_c_final = 0;
     int32_t warn = 0;
@@ -171,6 +180,11 @@ void free_all(spc_context* ctx);
 // launch accounting + optional timing of selected kernels
 void before_launch(spc_context* ctx, const char* name);
 void after_launch(spc_context* ctx, const char* name);
+
+// Algorithmic DRAM bytes of the next SPC_LAUNCH (the bytes the operation must move at minimum:
+// each input read once, each output written once), reported with the kernel's timed launches
+// so a roofline fraction can be formed from live timings.
+inline void note_bytes(spc_context* ctx, double bytes) { ctx->timer.next_bytes = bytes; }
 
 inline int grid_for(int64_t items, int threads, int max_blocks) {
     int64_t b = (items + threads - 1) / threads;
@@ -280,6 +294,9 @@ spc_status sync_status(spc_context* ctx);
 spc_status read_vals(spc_context* ctx, int count, const void* const* dev, const int* bytes,
                      int64_t* out);
 spc_status read_i32(spc_context* ctx, const int32_t* dev, int64_t* out);
+// a work-list count that drives a loop whose kernels read the count from the device: under
+// capture only the final (zero) count is checked on the device
+spc_status read_loop_count(spc_context* ctx, const int32_t* dev, int64_t* out);
 spc_status read_i64(spc_context* ctx, const int64_t* dev, int64_t* out);
 // Mid-pipeline status check: synchronises and returns the status (0 during a capture, whose
 // status is read after the replay).

@@ -81,9 +81,10 @@ template <> struct MinKey<unsigned int> {
 };
 
 // Boruvka phase A: current roots of both ends; keep inter-component edges; lower the
-// component minima.  Round 0 reads every edge directly and keeps only the score prefix
-// (key >> tau_shift <= *tau_top).  Each thread takes kMkItems edges per pass (their loads
-// overlap), and the survivors are appended with one global atomic per block and pass.
+// component minima.  The first Boruvka pass reads every edge directly and keeps only the
+// score prefix (key >> tau_shift <= *tau_top).  Each thread takes kMkItems edges per pass
+// (their loads overlap), and the survivors are appended with one global atomic per block
+// and pass.
 constexpr int kMkItems = 4;
 
 template <class KT>
@@ -375,13 +376,18 @@ struct SelState {
     uint32_t ticket[16];
 };
 
+// One select round: histogram of digit r over the items whose digits 0..r-1 are the ones
+// picked so far; the last block to finish picks digit r.  n_dev, when given, holds the item
+// count (a candidate list compacted on the device).
 template <class KT>
 __global__ void __launch_bounds__(kThreads)
-k_rsel_round(int r, int64_t n, const KT* __restrict__ keys, const uint32_t* __restrict__ vals,
+k_rsel_round(int r, int64_t n_host, const int32_t* __restrict__ n_dev,
+             const KT* __restrict__ keys, const uint32_t* __restrict__ vals,
              uint32_t* __restrict__ hist, SelState* st) {
     __shared__ uint32_t sh_h[kSelBins];
     __shared__ uint32_t sh_dig[16];
     __shared__ bool sh_last;
+    const int64_t n = n_dev ? (int64_t)*n_dev : n_host;
     for (int b = threadIdx.x; b < kSelBins; b += blockDim.x) sh_h[b] = 0;
     if (threadIdx.x < 16) sh_dig[threadIdx.x] = st->dig[threadIdx.x];
     __syncthreads();
@@ -431,6 +437,48 @@ k_rsel_round(int r, int64_t n, const KT* __restrict__ keys, const uint32_t* __re
             }
             run += c[j];
         }
+    }
+}
+
+// keep the items whose digits 0..r are the ones picked so far (order is irrelevant to the
+// select); one global atomic per block and pass
+template <class KT>
+__global__ void __launch_bounds__(kThreads)
+k_rsel_compact(int r, int64_t n, const KT* __restrict__ keys, const uint32_t* __restrict__ vals,
+               const SelState* __restrict__ st, KT* __restrict__ out_k,
+               uint32_t* __restrict__ out_v, int32_t* __restrict__ out_n) {
+    __shared__ uint32_t sh_dig[16];
+    __shared__ int32_t sh_cnt, sh_base;
+    const int lane = threadIdx.x & 31;
+    if (threadIdx.x < 16) sh_dig[threadIdx.x] = st->dig[threadIdx.x];
+    __syncthreads();
+    for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x; i0 < n;
+         i0 += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = i0 + threadIdx.x;
+        bool keep = false;
+        KT hi = 0;
+        uint32_t lo = 0;
+        if (i < n) {
+            hi = keys[i];
+            lo = vals[i];
+            keep = true;
+            for (int q = 0; q <= r; ++q) keep = keep && sel_digit<KT>(hi, lo, q) == sh_dig[q];
+        }
+        const unsigned b = __ballot_sync(0xffffffffu, keep);
+        if (threadIdx.x == 0) sh_cnt = 0;
+        __syncthreads();
+        int wofs = 0;
+        if (lane == 0 && b) wofs = atomicAdd(&sh_cnt, __popc(b));
+        wofs = __shfl_sync(0xffffffffu, wofs, 0);
+        __syncthreads();
+        if (threadIdx.x == 0) sh_base = sh_cnt ? atomicAdd(out_n, sh_cnt) : 0;
+        __syncthreads();
+        if (keep) {
+            const int pos = sh_base + wofs + __popc(b & ((1u << lane) - 1u));
+            out_k[pos] = hi;
+            out_v[pos] = lo;
+        }
+        __syncthreads();
     }
 }
 
@@ -606,7 +654,7 @@ spc_status select_typed(spc_context* ctx, const GraphView& g, const KT* key,
                        W.best_e[par].as<int32_t>(), W.best_k[par ^ 1].as<unsigned long long>(),
                        W.best_e[par ^ 1].as<int32_t>(), parent, W.msf.as<uint8_t>(), status);
             // next work-list size (a capture replays the recorded round count)
-            SPC_TRY(read_i32(ctx, counters + out, &cur));
+            SPC_TRY(read_loop_count(ctx, counters + out, &cur));
             // every round at least halves the components that still have edges
             if (round > 64) return SPC_ERR_TIMEOUT;
             // slot `out` (list and count) is the next round's input
@@ -633,8 +681,24 @@ spc_status select_typed(spc_context* ctx, const GraphView& g, const KT* key,
         SPC_CUDA(cudaMemsetAsync(hist, 0, (size_t)R * kSelBins * 4, ctx->stream));
         SPC_LAUNCH(ctx, k_rsel_init, 1, 32, 0, sst, (unsigned long long)k_single_sel);
         const int gsel = grid_for(n_msf, kThreads, ctx->num_sms * 2);
+        // two rounds over the whole forest, then the rest over the items still matching
+        constexpr int kFull = 2;
+        KT* ck = W.sel_key2.as<KT>();
+        uint32_t* cv = W.sel_val2.as<uint32_t>();
+        int32_t* cn = counters + 52;
         for (int r = 0; r < R; ++r) {
-            SPC_LAUNCH(ctx, k_rsel_round<KT>, gsel, kThreads, 0, r, n_msf, sk, sv, hist, sst);
+            if (r < kFull) {
+                SPC_LAUNCH(ctx, k_rsel_round<KT>, gsel, kThreads, 0, r, n_msf, nullptr, sk, sv,
+                           hist, sst);
+                continue;
+            }
+            if (r == kFull) {
+                SPC_CUDA(cudaMemsetAsync(cn, 0, sizeof(int32_t), ctx->stream));
+                SPC_LAUNCH(ctx, k_rsel_compact<KT>, gsel, kThreads, 0, kFull - 1, n_msf, sk, sv,
+                           sst, ck, cv, cn);
+            }
+            SPC_LAUNCH(ctx, k_rsel_round<KT>, ctx->num_sms, kThreads, 0, r, 0, cn, ck, cv, hist,
+                       sst);
         }
         int32_t* parent2 = W.parent2.as<int32_t>();
         SPC_LAUNCH(ctx, k_iota, grid_for(n, kThreads, maxb), kThreads, 0, parent2, n);

@@ -1,5 +1,10 @@
-// Device-wide exclusive scan (reduce -> scan of tile sums -> downsweep).  No inter-block waits:
-// the three phases are separate launches, so nothing here can spin.
+// Device-wide exclusive scan.  With a context: one pass with decoupled look-back (Merrill and
+// Garland, "Single-pass parallel prefix scan with decoupled look-back", 2016): each tile of
+// 4096 items publishes its sum, reads its predecessors' published sums (a warp looks at 32
+// at a time) and publishes its inclusive prefix, so the input is read once and the output
+// written once.  Every wait on a predecessor is bounded.  Without a context (the
+// allocation-free entry point): three launches (reduce, scan of tile sums, downsweep) with no
+// inter-block waits.
 #include "spc_internal.cuh"
 
 namespace spc {
@@ -163,6 +168,100 @@ __global__ void __launch_bounds__(kSmallThreads) k_scan_small(const In* in, int6
     if (threadIdx.x == 0) out[n] = (Out)carry;
 }
 
+// Tile status words: 2 flag bits over a 62-bit sum (every scanned value is >= 0).
+constexpr unsigned long long kScanAgg = 1ull << 62;   // the tile's own sum is published
+constexpr unsigned long long kScanInc = 2ull << 62;   // the sum of all tiles up to it
+constexpr unsigned long long kScanVal = (1ull << 62) - 1ull;
+
+// One pass: tiles take ids in launch order from *tile_ctr, so every tile a tile waits for has
+// already started.  status[0..nt) and *tile_ctr start at zero.  Works in place (in == out):
+// a tile reads all of its items before it writes any, and reads no other tile's items.
+template <class In, class T, class Out>
+__global__ void __launch_bounds__(ST) k_scan_onepass(const In* in, int64_t n, Out* out,
+                                                     unsigned long long* status,
+                                                     uint32_t* tile_ctr, int64_t nt,
+                                                     uint32_t* err) {
+    __shared__ T buf[STILE + STILE / 32];
+    __shared__ uint32_t sh_tile;
+    __shared__ T sh_prefix;
+    if (threadIdx.x == 0) sh_tile = atomicAdd(tile_ctr, 1u);
+    __syncthreads();
+    const int64_t tile = sh_tile;
+    const int64_t base = tile * STILE;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    In v[SI];
+#pragma unroll
+    for (int k = 0; k < SI; ++k) {  // all loads in flight before the first use
+        const int64_t g = base + (int64_t)k * ST + threadIdx.x;
+        v[k] = (g < n) ? in[g] : In(0);
+    }
+#pragma unroll
+    for (int k = 0; k < SI; ++k) {
+        const int i = k * ST + threadIdx.x;
+        buf[i + (i >> 5)] = (T)v[k];
+    }
+    __syncthreads();
+    T loc[SI];
+    T run = 0;
+#pragma unroll
+    for (int j = 0; j < SI; ++j) {
+        const int i = threadIdx.x * SI + j;
+        loc[j] = run;
+        run += buf[i + (i >> 5)];
+    }
+    T tot;
+    const T pre = block_excl_scan<T>(run, &tot);
+    if (warp == 0) {
+        unsigned long long prefix = 0;
+        if (tile > 0) {
+            if (lane == 0) atomicExch(status + tile, kScanAgg | (unsigned long long)tot);
+            int64_t top = tile - 1;
+            bool done = false;
+            while (!done) {
+                const int64_t idx = top - lane;
+                unsigned long long w = kScanInc;  // before tile 0: an inclusive zero
+                if (idx >= 0) w = *reinterpret_cast<volatile unsigned long long*>(status + idx);
+                uint32_t spins = 0;
+                while (__any_sync(0xffffffffu, (w >> 62) == 0ull)) {
+                    if ((w >> 62) == 0ull)
+                        w = *reinterpret_cast<volatile unsigned long long*>(status + idx);
+                    if (++spins > kSpinLimit) {
+                        if (lane == 0) atomicOr(err, DEV_TIMEOUT);
+                        w = kScanInc;  // give up; the call reports the timeout
+                    }
+                }
+                const unsigned inc = __ballot_sync(0xffffffffu, (w >> 62) == 2ull);
+                const int stop = inc ? __ffs(inc) - 1 : 31;
+                unsigned long long part = (lane <= stop) ? (w & kScanVal) : 0ull;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+                prefix += part;
+                done = inc != 0u;
+                top -= 32;
+            }
+        }
+        if (lane == 0) {
+            atomicExch(status + tile, kScanInc | (prefix + (unsigned long long)tot));
+            sh_prefix = (T)prefix;
+        }
+    }
+    __syncthreads();
+    const T off = sh_prefix + pre;
+#pragma unroll
+    for (int j = 0; j < SI; ++j) {
+        const int i = threadIdx.x * SI + j;
+        buf[i + (i >> 5)] = off + loc[j];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < SI; ++k) {
+        const int i = k * ST + threadIdx.x;
+        const int64_t g = base + i;
+        if (g < n) out[g] = (Out)buf[i + (i >> 5)];
+    }
+    if (tile == nt - 1 && threadIdx.x == 0) out[n] = (Out)(sh_prefix + tot);
+}
+
 template <class In, class T, class Out>
 spc_status scan_impl(spc_context* ctx, const In* in, Out* out, int64_t n) {
     if (n <= kSmallMax) {
@@ -170,24 +269,14 @@ spc_status scan_impl(spc_context* ctx, const In* in, Out* out, int64_t n) {
         return SPC_OK;
     }
     const int64_t nt = (n + STILE - 1) / STILE;
-    const size_t need = (size_t)(nt + 1) * sizeof(T) + 256;
+    const size_t need = (size_t)(nt + 1) * 8;
     SPC_TRY(ensure(ctx, ctx->work.scan_tmp, need));
-    T* tiles = ctx->work.scan_tmp.as<T>();
-    T* total = tiles + nt;
-    if (nt > 0) {
-        SPC_LAUNCH(ctx, (k_scan_reduce<In, T>), (unsigned)nt, ST, 0, in, n, tiles);
-    }
-    SPC_LAUNCH(ctx, (k_scan_tiles<T>), 1, ST, 0, tiles, nt, total);
-    if (nt > 0) {
-        SPC_LAUNCH(ctx, (k_scan_down<In, T, Out>), (unsigned)nt, ST, 0, in, n, tiles, out);
-    }
-    // out[n] = total (device to device copy keeps everything on the stream)
-    if (sizeof(T) == sizeof(Out)) {
-        SPC_CUDA(cudaMemcpyAsync(out + n, total, sizeof(Out), cudaMemcpyDeviceToDevice,
-                                 ctx->stream));
-    } else {
-        SPC_LAUNCH(ctx, (k_copy_total<T, Out>), 1, 32, 0, total, out + n);
-    }
+    unsigned long long* status = ctx->work.scan_tmp.as<unsigned long long>();
+    uint32_t* tile_ctr = reinterpret_cast<uint32_t*>(status + nt);
+    SPC_CUDA(cudaMemsetAsync(status, 0, need, ctx->stream));
+    note_bytes(ctx, (double)n * (sizeof(In) + sizeof(Out)));  // input read, output written
+    SPC_LAUNCH(ctx, (k_scan_onepass<In, T, Out>), (unsigned)nt, ST, 0, in, n, out, status,
+               tile_ctr, nt, ctx->d_status);
     return SPC_OK;
 }
 

@@ -1,6 +1,6 @@
 // S0-S3: input checks, weighted degrees, normalised rows and the per-edge score.
 //
-// Score (Theorem 1; Algorithm 1 fitness loop; Section 2 "one norm per edge, O(d_u + d_v)"):
+// Score (Theorem 1; the fitness loop of Algorithm 1, one norm per edge, Section 2):
 //   f(a, b) = || w_a / d_a - w_b / d_b ||_1 = sum over x in N(a) u N(b) of |p_ax - p_bx|,
 // the union taken in ascending x and containing a and b themselves (p_aa = p_bb = 0).
 // Every sum here runs sequentially in ascending column order with IEEE round-to-nearest adds
@@ -598,7 +598,10 @@ static spc_status score_typed(spc_context* ctx, GraphView& g, bool validate, voi
     int32_t* heavy_count = W.counters.as<int32_t>() + 10;
     int32_t* long_rows = W.long_rows.as<int32_t>();
     const int gb = grid_for(n, kThreads, maxb);
+    const double s_w = sizeof(WT), s_p = sizeof(P), s_acc = sizeof(Acc), s_key = sizeof(Key);
     SPC_CUDA(cudaMemsetAsync(long_count, 0, sizeof(int32_t), ctx->stream));
+    // rowptr, columns and weights read once; degree and the two per-row counts written once
+    note_bytes(ctx, 8.0 * (n + 1) + nnz * (4 + s_w) + n * (s_acc + 8));
     SPC_LAUNCH(ctx, k_rows_degree<WT>, gb, kThreads, 0, n, nnz, g.rowptr, g.col,
                static_cast<const WT*>(g.w), validate ? 1 : 0, W.deg.as<Acc>(),
                W.up_cnt.as<int32_t>(), W.first_up.as<int32_t>(), long_rows, long_count, status);
@@ -629,6 +632,11 @@ static spc_status score_typed(spc_context* ctx, GraphView& g, bool validate, voi
                                      W.lr_idx.as<int64_t>(), W.deg.p));
         }
     }
+    // rowptr, columns, weights, degrees and row counts read once; p and the undirected edge
+    // list written once (no model on levels with long rows: another kernel takes their part)
+    if (n_long == 0)
+        note_bytes(ctx, 8.0 * (n + 1) + nnz * (4 + s_w) + n * (s_acc + 8) + nnz * s_p +
+                            m * (8 + s_w));
     SPC_LAUNCH(ctx, k_rows_edges<WT>, gb, kThreads, 0, n, g.rowptr, g.col,
                static_cast<const WT*>(g.w), validate ? 1 : 0, W.deg.as<Acc>(),
                W.first_up.as<int32_t>(), W.up_ptr.as<int32_t>(), W.p.as<P>(),
@@ -673,13 +681,18 @@ static spc_status score_typed(spc_context* ctx, GraphView& g, bool validate, voi
         }
         if (schedule == 0) schedule = pick_default_schedule(n, nnz);
     }
+    // rowptr, every stored column and p read once, every score written once (no model on
+    // levels with long rows: the hub kernels take their edges)
+    const double score_bytes = n_long == 0 ? 8.0 * (n + 1) + nnz * (4 + s_p) + m * s_key : 0.0;
     if (schedule == 2) {
         const int warps_per_block = kThreads / 32;
+        note_bytes(ctx, score_bytes);
         const int gw = grid_for(n, warps_per_block, maxb);
         SPC_LAUNCH(ctx, (k_score_warp_row<P, Key>), gw, kThreads, 0, n, g.rowptr, g.col,
                    W.p.as<P>(), W.up_ptr.as<int32_t>(), W.first_up.as<int32_t>(),
                    static_cast<Key*>(score), status);
     } else {
+        note_bytes(ctx, score_bytes);
         SPC_LAUNCH(ctx, (k_score_edges<P, Key>), grid_for(m, kThreads, maxb), kThreads, 0, m,
                    W.eu.as<int32_t>(), W.ev.as<int32_t>(), g.rowptr, g.col, W.p.as<P>(),
                    static_cast<Key*>(score), status);

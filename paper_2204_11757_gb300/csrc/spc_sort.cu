@@ -222,12 +222,18 @@ __global__ void __launch_bounds__(RT) k_os_pass(const K* __restrict__ kin,
     uint32_t val[RI];
     uint32_t dig[RI];
     uint32_t rnk[RI];
+    // every load of the tile is issued before the first is used (all in flight at once)
 #pragma unroll
     for (int k = 0; k < RI; ++k) {
         const int64_t i = wbase + k * 32 + lane;
         const bool valid = i < count;
-        key[k] = valid ? kin[i] : K(0);
-        val[k] = valid ? vin[i] : 0u;
+        key[k] = valid ? __ldcs(kin + i) : K(0);
+        val[k] = valid ? __ldcs(vin + i) : 0u;
+    }
+#pragma unroll
+    for (int k = 0; k < RI; ++k) {
+        const int64_t i = wbase + k * 32 + lane;
+        const bool valid = i < count;
         const uint32_t d = valid ? digit_of(key[k], shift, mask) : (RADIX + lane);
         const unsigned peers = __match_any_sync(0xffffffffu, d);
         const uint32_t before = valid ? s.wcnt[warp][d] : 0u;
@@ -332,6 +338,7 @@ spc_status radix_sort_impl(spc_context* ctx, K* keys, uint32_t* vals, K* keys_al
                                       (int)smem));
         attr_set = true;
     }
+    note_bytes(ctx, (double)count * sizeof(K));  // every key read once
     SPC_LAUNCH(ctx, k_os_hist<K>, grid_for(count, RT, ctx->num_sms * 4), RT, 0, keys, count,
                npass, end_bit, hist);
     SPC_LAUNCH(ctx, k_os_bases, 1, RADIX, 0, npass, hist, base);
@@ -343,6 +350,7 @@ spc_status radix_sort_impl(spc_context* ctx, K* keys, uint32_t* vals, K* keys_al
         const int shift = 8 * p;
         const int bits = (end_bit - shift) < 8 ? (end_bit - shift) : 8;
         const uint32_t mask = (1u << bits) - 1u;
+        note_bytes(ctx, 2.0 * (double)count * (sizeof(K) + 4));  // pairs read once, written once
         SPC_LAUNCH(ctx, k_os_pass<K>, (unsigned)tiles, RT, smem, ka, va, kb, vb, count, shift,
                    mask, base + (size_t)p * RADIX, stat + (size_t)p * tiles * RADIX, tctr + p,
                    ctx->d_status);
