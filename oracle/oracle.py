@@ -44,8 +44,11 @@ def build(force: bool = False) -> str:
             and os.path.getmtime(LIB_PATH) >= os.path.getmtime(SRC)):
         return LIB_PATH
     tmp = LIB_PATH + f".tmp{os.getpid()}"
-    subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
-                           "-shared", "-o", tmp, SRC])
+    base = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared", "-o", tmp]
+    try:  # OpenMP only for the parallel CPU baseline; without it that loop runs on one thread
+        subprocess.check_call(base + ["-fopenmp", SRC], stderr=subprocess.DEVNULL)
+    except subprocess.CalledProcessError:
+        subprocess.check_call(base + [SRC])
     os.replace(tmp, LIB_PATH)
     return LIB_PATH
 
@@ -61,11 +64,15 @@ def lib():
         L.orc_normalise.argtypes = [i64, P, P, ctypes.c_int, P, P]
         L.orc_score.argtypes = [i64, P, P, P, ctypes.c_int, P]
         L.orc_score.restype = i64
+        L.orc_score_parallel.argtypes = [i64, P, P, P, ctypes.c_int, P, P]
+        L.orc_score_parallel.restype = i64
         L.orc_sort_fitness.argtypes = [i64, P, ctypes.c_int, P]
         L.orc_greedy_merge.argtypes = [i64, i64, P, P, P, i64, P, P, P]
         L.orc_relabel.argtypes = [i64, P, P, P]
         L.orc_contract.argtypes = [i64, i64, P, P, P, ctypes.c_int, P, i64, P, P, P, P, P, P, P]
         L.orc_contract_backward.argtypes = [i64, P, P, ctypes.c_int, P]
+        L.orc_pool_features.argtypes = [i64, P, i64, i64, P, ctypes.c_int, P]
+        L.orc_pool_backward.argtypes = [i64, P, i64, i64, P, ctypes.c_int, P]
         _lib = L
     return _lib
 
@@ -109,6 +116,19 @@ def normalise(g, d: np.ndarray) -> np.ndarray:
     p = np.empty(g.nnz, dtype=score_dtype(g.w))
     lib().orc_normalise(g.n, _ptr(g.rowptr), _ptr(g.w), wtype_of(g.w), _ptr(d), _ptr(p))
     return p
+
+
+def score_parallel(g):
+    """Scores with the edges split over the host's threads (OpenMP); returns (f, threads).
+    Same bits as score(): only the edges are shared out."""
+    m = (g.nnz) // 2
+    f = np.empty(m, dtype=score_dtype(g.w))
+    th = np.zeros(1, dtype=np.int32)
+    got = lib().orc_score_parallel(g.n, _ptr(g.rowptr), _ptr(g.col), _ptr(g.w), wtype_of(g.w),
+                                   _ptr(f), _ptr(th))
+    if got != m:
+        raise RuntimeError(f"orc_score_parallel returned {got}, expected {m}")
+    return f, int(th[0])
 
 
 def score(g) -> np.ndarray:
@@ -205,6 +225,34 @@ def contract_backward(emap: np.ndarray, grad_a: np.ndarray) -> np.ndarray:
     lib().orc_contract_backward(emap.shape[0], _ptr(emap), _ptr(grad_a),
                                 F32 if grad_a.dtype == np.float32 else F64, _ptr(grad_w))
     return grad_w
+
+
+def pool_features(lift: np.ndarray, n_c: int, x: np.ndarray) -> np.ndarray:
+    """Mean of each super-node's member features (Definition 2's averaging over super-node
+    sizes, for node features): members summed in ascending id, sequentially, then divided by
+    the member count.  x is n-by-F (float32 or float64)."""
+    x = np.ascontiguousarray(x)
+    n, F = x.shape
+    lift = np.ascontiguousarray(lift, dtype=np.int32)
+    xc = np.empty((n_c, F), dtype=x.dtype)
+    rc = lib().orc_pool_features(n, _ptr(lift), n_c, F, _ptr(x),
+                                 F32 if x.dtype == np.float32 else F64, _ptr(xc))
+    if rc != 0:
+        raise ValueError(f"orc_pool_features: {rc}")
+    return xc
+
+
+def pool_backward(lift: np.ndarray, n_c: int, grad_xc: np.ndarray) -> np.ndarray:
+    """Gradient of pool_features with the lift held fixed: grad_x[v] = grad_xc[c(v)] / |c(v)|."""
+    grad_xc = np.ascontiguousarray(grad_xc)
+    F = grad_xc.shape[1]
+    lift = np.ascontiguousarray(lift, dtype=np.int32)
+    gx = np.empty((lift.shape[0], F), dtype=grad_xc.dtype)
+    rc = lib().orc_pool_backward(lift.shape[0], _ptr(lift), n_c, F, _ptr(grad_xc),
+                                 F32 if grad_xc.dtype == np.float32 else F64, _ptr(gx))
+    if rc != 0:
+        raise ValueError(f"orc_pool_backward: {rc}")
+    return gx
 
 
 # ---- one level, multilevel, batch --------------------------------------------------------

@@ -6,7 +6,7 @@
  * of the benchmark load it.  It shares no code, header, table or helper with the CUDA library,
  * and the CUDA library never calls it.
  *
- * Build: cc -O2 -ffp-contract=off -fno-fast-math -shared -fPIC (no FMA contraction, IEEE
+ * Build: cc -O2 -ffp-contract=off -fno-fast-math -shared -fPIC [-fopenmp] (no FMA contraction, IEEE
  * binary32/binary64 with round-to-nearest; there are no multiplications in the arithmetic below,
  * only additions, subtractions, absolute values and divisions).
  *
@@ -20,6 +20,8 @@
  *                   i.e. over the sorted union N(a) u N(b), which contains a and b themselves
  *                   (coordinates b of row a and a of row b).  Summed in ascending coordinate
  *                   order, starting from 0.
+ *   orc_score_parallel  the same scores with the edges split over the host's threads
+ *                   (Algorithm 1's parallel fitness loop); a CPU baseline, same bits.
  *   orc_sort_fitness Algorithm 1 (sort of the fitness list): ascending f, ties by edge id.
  *   orc_greedy_merge Algorithm 1 (merge loop): walk the sorted list, merge the two super-nodes
  *                   of each edge unless they are already one, stop when n_c super-nodes remain
@@ -27,6 +29,9 @@
  *                   loop of the explicit greedy algorithm is removed).
  *   orc_relabel     Definition 1 (super-nodes): super-node ids numbered by ascending smallest
  *                   member node id.
+ *   orc_pool_features / orc_pool_backward  Definition 2's averaging over super-node sizes,
+ *                   for node features: the mean over a super-node's members (ascending member
+ *                   id, sequential), and its gradient with the assignment held fixed.
  *   orc_contract    Definition 1: a_{v_c x} = sum over members v_i of w_{v_i x}, generalised to
  *                   pairs of super-nodes; edges inside one super-node leave the coarse graph and
  *                   their weight is reported as the super-node's self-mass (Definition 2 needs
@@ -36,6 +41,9 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 enum { ORC_I32 = 0, ORC_F32 = 1, ORC_F64 = 2 };
 enum { ORC_OK = 0, ORC_WARN_TARGET_NOT_REACHED = 1, ORC_ERR_ARG = -1, ORC_ERR_OVERFLOW = -8,
@@ -166,6 +174,52 @@ int64_t orc_score(int64_t n, const int64_t* rowptr, const int32_t* col, const vo
     }
     free(d); free(p);
     return e;
+}
+
+/* S1-S3 with the edges split evenly over the host's threads (OpenMP, static schedule): the
+ * edge-partitioned parallel loop of Algorithm 1 on a CPU.  Every edge's norm is the same
+ * sequential walk as in orc_score, so the scores are the same bits; only the edges are shared
+ * out.  Used as a parallel CPU baseline.  Returns the number of edges; *threads_out is the
+ * number of threads the loop ran on (1 without OpenMP). */
+int64_t orc_score_parallel(int64_t n, const int64_t* rowptr, const int32_t* col, const void* w,
+                           int wtype, void* f_out, int32_t* threads_out)
+{
+    int64_t nnz = rowptr[n];
+    size_t dsz = (wtype == ORC_F32) ? sizeof(float) : (wtype == ORC_I32 ? sizeof(int64_t)
+                                                                       : sizeof(double));
+    size_t psz = (wtype == ORC_F32) ? sizeof(float) : sizeof(double);
+    int64_t m = 0;
+    for (int64_t a = 0; a < n; ++a)
+        for (int64_t j = rowptr[a]; j < rowptr[a + 1]; ++j) m += col[j] > a ? 1 : 0;
+    void* d = malloc((size_t)(n > 0 ? n : 1) * dsz);
+    void* p = malloc((size_t)(nnz > 0 ? nnz : 1) * psz);
+    int32_t* eu = (int32_t*)malloc((size_t)(m > 0 ? m : 1) * sizeof(int32_t));
+    int64_t* ej = (int64_t*)malloc((size_t)(m > 0 ? m : 1) * sizeof(int64_t));
+    if (!d || !p || !eu || !ej) { free(d); free(p); free(eu); free(ej); return ORC_ERR_NOMEM; }
+    int rc = orc_degree(n, rowptr, w, wtype, d);
+    if (rc == ORC_OK) rc = orc_normalise(n, rowptr, w, wtype, d, p);
+    if (rc != ORC_OK) { free(d); free(p); free(eu); free(ej); return rc; }
+    int64_t e = 0;
+    for (int64_t a = 0; a < n; ++a)
+        for (int64_t j = rowptr[a]; j < rowptr[a + 1]; ++j)
+            if (col[j] > a) { eu[e] = (int32_t)a; ej[e] = j; ++e; }
+    int32_t threads = 1;
+#ifdef _OPENMP
+    threads = (int32_t)omp_get_max_threads();
+#endif
+#pragma omp parallel for schedule(static)
+    for (int64_t k = 0; k < m; ++k) {
+        const int64_t a = eu[k], b = col[ej[k]];
+        if (wtype == ORC_F32)
+            ((float*)f_out)[k] = norm1_f32(col, (const float*)p, rowptr[a], rowptr[a + 1],
+                                           rowptr[b], rowptr[b + 1]);
+        else
+            ((double*)f_out)[k] = norm1_f64(col, (const double*)p, rowptr[a], rowptr[a + 1],
+                                            rowptr[b], rowptr[b + 1]);
+    }
+    if (threads_out) *threads_out = threads;
+    free(d); free(p); free(eu); free(ej);
+    return m;
 }
 
 /* ---------------------------------------------------------------------------------------- */
@@ -398,5 +452,72 @@ int orc_contract_backward(int64_t m, const int32_t* emap, const void* grad_a, in
         else if (ftype == ORC_F64) ((double*)grad_w)[e] = (k < 0) ? 0.0 : ((const double*)grad_a)[k];
         else return ORC_ERR_ARG;
     }
+    return ORC_OK;
+}
+
+/* ---------------------------------------------------------------------------------------- */
+/* Node-feature pooling onto the super-nodes and its gradient (a graph-pooling layer built on
+ * the coarsening).  Definition 2's lift averages over the member pairs of two super-nodes
+ * (divides by |u_c| |v_c|); its node counterpart is the mean over a super-node's members:
+ *   xc[U][f] = (sum of x[v][f] over the members v of U, in ascending v) / |U|
+ * summed sequentially in the feature type, then one IEEE division by |U| (converted to the
+ * feature type).  x is n-by-F row-major, xc n_c-by-F.  A super-node without members gets 0.
+ * Gradient (lift held fixed): grad_x[v][f] = grad_xc[c(v)][f] / |c(v)|.                    */
+static int64_t* pool_counts(int64_t n, const int32_t* lift, int64_t n_c)
+{
+    int64_t* cnt = (int64_t*)calloc((size_t)(n_c > 0 ? n_c : 1), sizeof(int64_t));
+    if (!cnt) return NULL;
+    for (int64_t v = 0; v < n; ++v) {
+        if (lift[v] < 0 || lift[v] >= n_c) { free(cnt); return NULL; }
+        cnt[lift[v]] += 1;
+    }
+    return cnt;
+}
+
+int orc_pool_features(int64_t n, const int32_t* lift, int64_t n_c, int64_t F, const void* x,
+                      int ftype, void* xc_out)
+{
+    if (ftype != ORC_F32 && ftype != ORC_F64) return ORC_ERR_ARG;
+    int64_t* cnt = pool_counts(n, lift, n_c);
+    if (!cnt) return ORC_ERR_ARG;
+    for (int64_t k = 0; k < n_c * F; ++k) {
+        if (ftype == ORC_F32) ((float*)xc_out)[k] = 0.0f;
+        else ((double*)xc_out)[k] = 0.0;
+    }
+    /* ascending v: every super-node's sum runs over its members in ascending id */
+    for (int64_t v = 0; v < n; ++v) {
+        const int64_t u = lift[v];
+        for (int64_t f = 0; f < F; ++f) {
+            if (ftype == ORC_F32) ((float*)xc_out)[u * F + f] += ((const float*)x)[v * F + f];
+            else ((double*)xc_out)[u * F + f] += ((const double*)x)[v * F + f];
+        }
+    }
+    for (int64_t u = 0; u < n_c; ++u) {
+        if (cnt[u] == 0) continue;
+        for (int64_t f = 0; f < F; ++f) {
+            if (ftype == ORC_F32) ((float*)xc_out)[u * F + f] /= (float)cnt[u];
+            else ((double*)xc_out)[u * F + f] /= (double)cnt[u];
+        }
+    }
+    free(cnt);
+    return ORC_OK;
+}
+
+int orc_pool_backward(int64_t n, const int32_t* lift, int64_t n_c, int64_t F,
+                      const void* grad_xc, int ftype, void* grad_x)
+{
+    if (ftype != ORC_F32 && ftype != ORC_F64) return ORC_ERR_ARG;
+    int64_t* cnt = pool_counts(n, lift, n_c);
+    if (!cnt) return ORC_ERR_ARG;
+    for (int64_t v = 0; v < n; ++v) {
+        const int64_t u = lift[v];
+        for (int64_t f = 0; f < F; ++f) {
+            if (ftype == ORC_F32)
+                ((float*)grad_x)[v * F + f] = ((const float*)grad_xc)[u * F + f] / (float)cnt[u];
+            else
+                ((double*)grad_x)[v * F + f] = ((const double*)grad_xc)[u * F + f] / (double)cnt[u];
+        }
+    }
+    free(cnt);
     return ORC_OK;
 }

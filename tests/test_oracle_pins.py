@@ -485,3 +485,80 @@ def test_batch_oracle_is_per_graph():
     for gi, (levels, total) in enumerate(res):
         n = int(b.graph_ptr[gi + 1] - b.graph_ptr[gi])
         assert levels[-1].n_c == n // 8
+
+
+def test_parallel_score_is_the_sequential_score():
+    """The edge-partitioned parallel score (the CPU baseline) only shares out the edges: the
+    same bits as the sequential score on a mesh, a binary32 random graph, integer weights and
+    a heavy-tailed graph."""
+    graphs = [I.tri_mesh_2d(40, 30, 1, jitter=0.3, weight="inv_len", dtype=np.float64),
+              I.random_graph(300, 0.05, 2, weight="float", dtype=np.float32, connected=True),
+              I.random_graph(200, 0.08, 3, weight="int", dtype=np.int32, connected=True),
+              I.powerlaw_graph(800, 6, 4, "float", np.float64)]
+    for g in graphs:
+        f = O.score(g)
+        fp, threads = O.score_parallel(g)
+        assert threads >= 1
+        bits = np.uint64 if f.dtype.itemsize == 8 else np.uint32
+        assert fp.dtype == f.dtype and np.array_equal(f.view(bits), fp.view(bits))
+
+
+# ---- node-feature pooling (mean over super-node members) ----------------------------------------
+
+def _round_f32(q: Fraction) -> np.float32:
+    """The binary32 value nearest to q (ties to even), found from exact comparisons."""
+    c = np.float32(float(q))
+    best = None
+    for cand in (np.nextafter(c, np.float32(-np.inf)), c, np.nextafter(c, np.float32(np.inf))):
+        d = abs(Fraction(float(cand)) - q)
+        even = (int(np.array(cand).view(np.uint32)) & 1) == 0
+        if best is None or d < best[0] or (d == best[0] and even):
+            best = (d, cand)
+    return best[1]
+
+
+@pytest.mark.parametrize("dtype", [np.float64, np.float32])
+def test_pool_features_exact_means(dtype):
+    """Dyadic features (exact sums): every pooled value is the correctly rounded quotient of
+    the exact member sum by the member count, computed with rationals."""
+    rng = np.random.default_rng(11)
+    n, n_c, F = 500, 37, 5
+    lift = np.sort(rng.integers(0, n_c, size=n)).astype(np.int32)
+    lift[:n_c] = np.arange(n_c)  # every super-node used
+    rng.shuffle(lift)
+    x = (rng.integers(-1000, 1000, size=(n, F)) / 256.0).astype(dtype)
+    xc = O.pool_features(lift, n_c, x)
+    for u in range(n_c):
+        mem = np.nonzero(lift == u)[0]
+        for f in range(F):
+            q = sum(Fraction(float(x[v, f])) for v in mem) / len(mem)
+            want = float(q) if dtype == np.float64 else _round_f32(q)
+            assert xc[u, f] == want, (u, f)
+
+
+def test_pool_features_sums_in_ascending_member_order():
+    """Members 3 < 8 < 20 hold 1e16, 1, -1e16: in ascending order 1e16 + 1 rounds back to
+    1e16 and the mean is 0; any other order that adds the 1 last gives 1/3."""
+    lift = np.zeros(25, dtype=np.int32)
+    lift[[3, 8, 20]] = 1
+    x = np.zeros((25, 1))
+    x[3, 0], x[8, 0], x[20, 0] = 1e16, 1.0, -1e16
+    xc = O.pool_features(lift, 2, x)
+    assert xc[1, 0] == 0.0 and xc[0, 0] == 0.0
+
+
+def test_pool_backward_is_the_adjoint():
+    """<pool(x), g> = <x, pool_backward(g)>: exact for dyadic values and power-of-two member
+    counts; and the pooled-then-lifted features keep the total mass."""
+    rng = np.random.default_rng(12)
+    n_c, F = 16, 3
+    sizes = 2 ** rng.integers(0, 5, size=n_c)
+    lift = np.repeat(np.arange(n_c), sizes).astype(np.int32)
+    rng.shuffle(lift)
+    n = lift.shape[0]
+    x = rng.integers(-64, 64, size=(n, F)) / 8.0
+    g = rng.integers(-64, 64, size=(n_c, F)) / 8.0
+    xc = O.pool_features(lift, n_c, x)
+    gx = O.pool_backward(lift, n_c, g)
+    assert float(np.sum(xc * g)) == float(np.sum(x * gx))
+    assert np.array_equal((xc * sizes[:, None]).sum(0), x.sum(0))
