@@ -229,8 +229,9 @@ def contract_backward(emap: np.ndarray, grad_a: np.ndarray) -> np.ndarray:
 
 def pool_features(lift: np.ndarray, n_c: int, x: np.ndarray) -> np.ndarray:
     """Mean of each super-node's member features (Definition 2's averaging over super-node
-    sizes, for node features): members summed in ascending id, sequentially, then divided by
-    the member count.  x is n-by-F (float32 or float64)."""
+    sizes, for node features): the members in ascending id, in chunks of 256; each chunk summed
+    left to right, the chunk sums added left to right; then one division by the member count.
+    x is n-by-F (float32 or float64)."""
     x = np.ascontiguousarray(x)
     n, F = x.shape
     lift = np.ascontiguousarray(lift, dtype=np.int32)

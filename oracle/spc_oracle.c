@@ -31,7 +31,8 @@
  *                   member node id.
  *   orc_pool_features / orc_pool_backward  Definition 2's averaging over super-node sizes,
  *                   for node features: the mean over a super-node's members (ascending member
- *                   id, sequential), and its gradient with the assignment held fixed.
+ *                   id, summed in chunks of 256 members, chunk sums left to right), and its
+ *                   gradient with the assignment held fixed.
  *   orc_contract    Definition 1: a_{v_c x} = sum over members v_i of w_{v_i x}, generalised to
  *                   pairs of super-nodes; edges inside one super-node leave the coarse graph and
  *                   their weight is reported as the super-node's self-mass (Definition 2 needs
@@ -459,10 +460,14 @@ int orc_contract_backward(int64_t m, const int32_t* emap, const void* grad_a, in
 /* Node-feature pooling onto the super-nodes and its gradient (a graph-pooling layer built on
  * the coarsening).  Definition 2's lift averages over the member pairs of two super-nodes
  * (divides by |u_c| |v_c|); its node counterpart is the mean over a super-node's members:
- *   xc[U][f] = (sum of x[v][f] over the members v of U, in ascending v) / |U|
- * summed sequentially in the feature type, then one IEEE division by |U| (converted to the
- * feature type).  x is n-by-F row-major, xc n_c-by-F.  A super-node without members gets 0.
+ *   xc[U][f] = (sum of x[v][f] over the members v of U) / |U|.
+ * The paper does not use node features, so the summation order is this library's choice:
+ * the members in ascending id, cut into chunks of ORC_POOL_CHUNK consecutive members; each
+ * chunk summed left to right from 0, then the chunk sums added left to right from 0, all in
+ * the feature type; then one IEEE division by |U| (converted to the feature type).  x is
+ * n-by-F row-major, xc n_c-by-F.  A super-node without members gets 0.
  * Gradient (lift held fixed): grad_x[v][f] = grad_xc[c(v)][f] / |c(v)|.                    */
+#define ORC_POOL_CHUNK 256
 static int64_t* pool_counts(int64_t n, const int32_t* lift, int64_t n_c)
 {
     int64_t* cnt = (int64_t*)calloc((size_t)(n_c > 0 ? n_c : 1), sizeof(int64_t));
@@ -479,27 +484,51 @@ int orc_pool_features(int64_t n, const int32_t* lift, int64_t n_c, int64_t F, co
 {
     if (ftype != ORC_F32 && ftype != ORC_F64) return ORC_ERR_ARG;
     int64_t* cnt = pool_counts(n, lift, n_c);
-    if (!cnt) return ORC_ERR_ARG;
+    int64_t* seen = (int64_t*)calloc((size_t)(n_c > 0 ? n_c : 1), sizeof(int64_t));
+    double* part = (double*)calloc((size_t)(n_c * F > 0 ? n_c * F : 1), sizeof(double));
+    if (!cnt || !seen || !part) { free(cnt); free(seen); free(part); return ORC_ERR_ARG; }
+    /* xc holds the running total over finished chunks, part the open chunk (kept in a double
+     * array, but every value in it is a value of the feature type) */
     for (int64_t k = 0; k < n_c * F; ++k) {
         if (ftype == ORC_F32) ((float*)xc_out)[k] = 0.0f;
         else ((double*)xc_out)[k] = 0.0;
     }
-    /* ascending v: every super-node's sum runs over its members in ascending id */
+    /* ascending v: every super-node's members arrive in ascending id */
     for (int64_t v = 0; v < n; ++v) {
         const int64_t u = lift[v];
+        const int close_chunk = seen[u] > 0 && seen[u] % ORC_POOL_CHUNK == 0;
         for (int64_t f = 0; f < F; ++f) {
-            if (ftype == ORC_F32) ((float*)xc_out)[u * F + f] += ((const float*)x)[v * F + f];
-            else ((double*)xc_out)[u * F + f] += ((const double*)x)[v * F + f];
+            const int64_t k = u * F + f;
+            if (ftype == ORC_F32) {
+                float* tot = (float*)xc_out + k;
+                float open = (float)part[k];
+                if (close_chunk) { *tot = *tot + open; open = 0.0f; }
+                open = open + ((const float*)x)[v * F + f];
+                part[k] = open;
+            } else {
+                double* tot = (double*)xc_out + k;
+                double open = part[k];
+                if (close_chunk) { *tot = *tot + open; open = 0.0; }
+                open = open + ((const double*)x)[v * F + f];
+                part[k] = open;
+            }
         }
+        seen[u] += 1;
     }
     for (int64_t u = 0; u < n_c; ++u) {
         if (cnt[u] == 0) continue;
         for (int64_t f = 0; f < F; ++f) {
-            if (ftype == ORC_F32) ((float*)xc_out)[u * F + f] /= (float)cnt[u];
-            else ((double*)xc_out)[u * F + f] /= (double)cnt[u];
+            const int64_t k = u * F + f;
+            if (ftype == ORC_F32) {
+                float* tot = (float*)xc_out + k;
+                *tot = (*tot + (float)part[k]) / (float)cnt[u];
+            } else {
+                double* tot = (double*)xc_out + k;
+                *tot = (*tot + part[k]) / (double)cnt[u];
+            }
         }
     }
-    free(cnt);
+    free(cnt); free(seen); free(part);
     return ORC_OK;
 }
 

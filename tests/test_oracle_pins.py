@@ -562,3 +562,19 @@ def test_pool_backward_is_the_adjoint():
     gx = O.pool_backward(lift, n_c, g)
     assert float(np.sum(xc * g)) == float(np.sum(x * gx))
     assert np.array_equal((xc * sizes[:, None]).sum(0), x.sum(0))
+
+
+def test_pool_features_chunked_order():
+    """258 members: 1e16, 255 zeros, 1, 1.  Chunks of 256: (1e16) + (1 + 1) = 1e16 + 2 exactly,
+    so the mean is (1e16 + 2) / 258 correctly rounded; a plain left-to-right sum would lose both
+    ones (1e16 + 1 rounds to 1e16) and give 1e16 / 258."""
+    lift = np.zeros(300, dtype=np.int32)
+    mem = np.arange(20, 278)
+    lift[mem] = 1
+    x = np.zeros((300, 1))
+    x[mem[0], 0] = 1e16
+    x[mem[-2], 0] = 1.0
+    x[mem[-1], 0] = 1.0
+    xc = O.pool_features(lift, 2, x)
+    assert xc[1, 0] == float(Fraction(10 ** 16 + 2, 258))
+    assert xc[1, 0] != float(Fraction(10 ** 16, 258))
