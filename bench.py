@@ -45,6 +45,8 @@ WORKLOADS = {
     # reduced case of the same construction, for profiler captures that must stay small
     "p2_tri512_f64": ("p2_tri512_f64", 6, "512x512 jittered triangle mesh (262,144 nodes, "
                       "784,385 edges), FP64 1/edge-length, 6 halving levels to n/64"),
+    "p4_rgg2m_f32": ("p4_rgg2m_f32", 8, "random geometric graph, 2^21 points, mean degree 12, "
+                     "FP32 exp(-d^2/r^2), 8 halving levels to n/256"),
 }
 # the CPU oracle's bounded sample: the same construction at a quarter of the side length
 SAMPLES = {
@@ -57,6 +59,7 @@ SAMPLES = {
                              ratio=256, mode="one"),
     "p2_tri512_f64": dict(kind="tri", nx=256, ny=256, jitter=0.3, weight="inv_len",
                           dtype="float64", seed=12, ratio=64),
+    "p4_rgg2m_f32": dict(kind="rgg", n=1 << 16, degree=12.0, dtype="float32", seed=4, ratio=256),
 }
 
 
@@ -87,7 +90,20 @@ def _oracle_step(g, spec):
     return sum(lv.f.shape[0] for lv in levels), dt
 
 
+def _score_rate(g, fn, budget_s):
+    """M edges/s of one score function (S1-S3) repeated for about budget_s on the sample."""
+    done, t, runs = 0, 0.0, 0
+    while t < budget_s or runs == 0:
+        t0 = time.perf_counter()
+        out = fn(g)
+        t += time.perf_counter() - t0
+        done += g.m
+        runs += 1
+    return done / t / 1e6, out
+
+
 def cpu_baseline(workload, budget_s=10.0):
+    from oracle import oracle as O
     spec = SAMPLES[workload]
     g = _sample_graph(spec)
     edges, dt, runs = 0, 0.0, 0
@@ -96,10 +112,17 @@ def cpu_baseline(workload, budget_s=10.0):
         edges += e
         dt += t
         runs += 1
+    # the score step alone: sequential, and with the edges split over every host thread (the
+    # parallel fitness loop of Algorithm 1 on a CPU; same bits)
+    seq, _ = _score_rate(g, O.score, 2.0)
+    par, (_, threads) = _score_rate(g, O.score_parallel, 2.0)
     return {"value": edges / dt / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"full {spec.get('mode', 'halving')} coarsening (ratio {spec['ratio']}) of "
                       f"the same construction at reduced size: n={g.n}, m={g.m}; {runs} runs, "
-                      f"{dt:.1f} s single-threaded C"}
+                      f"{dt:.1f} s single-threaded C",
+            "score_step": {"unit": "M edges/s", "sequential": seq, "parallel": par,
+                           "parallel_threads": threads,
+                           "sample": f"level-0 scores (S1-S3) of the same sample, ~2 s each"}}
 
 
 def run_reference_batched(args):
@@ -224,6 +247,10 @@ class ClockSampler:
                 "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
                 "samples": len(rows)}
 
+
+# GB300's nominal FP64 rate is 1.25 TFLOP/s counting a fused multiply-add as two operations:
+# 625 G plain FP64 additions or subtractions per second (152 SMs at up to 2.07 GHz)
+FP64_PEAK_GOPS = 625.0
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the dominant kernel,
 # from an ncu capture of the same kernel; None where no capture of the current kernel exists
@@ -350,6 +377,9 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile", action="store_true", help="print the per-kernel breakdown")
+    ap.add_argument("--pool", type=int, default=64,
+                    help="also time node-feature pooling of this many binary32 features on the "
+                         "final lift (0: off)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "native":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
@@ -442,7 +472,8 @@ def main():
     except (OSError, ValueError):
         pass
     hbm = float(peaks.get("hbm_gbs", 6800.0))
-    dom_bytes = dom_prof.get(dominant, (0, 0.0, 0.0))[2]
+    dom_bytes = dom_prof.get(dominant, (0, 0.0, 0.0, 0.0))[2]
+    dom_ops = dom_prof.get(dominant, (0, 0.0, 0.0, 0.0))[3]
     achieved = dom_bytes / (dom_ms * 1e-3) / 1e9 if dom_bytes > 0 and dom_ms > 0 else None
     roof = {"kernel": dominant, "bound": "hbm", "achieved": achieved, "peak": hbm,
             "unit": "GB/s", "frac": achieved / hbm if achieved else None,
@@ -450,6 +481,14 @@ def main():
             "peak_source": "measured" if peaks else "fallback",
             "launches": dom_launches, "avg_launch_ms": dom_ms / max(1, dom_launches),
             "algorithmic_bytes_per_launch": dom_bytes / max(1, dom_launches)}
+    if dom_ops > 0 and g.w.dtype != np.float32:
+        # binary64 score arithmetic: bound by the FP64 pipe, not by HBM
+        roof.update({"bound": "alu", "achieved": dom_ops / (dom_ms * 1e-3) / 1e9,
+                     "peak": FP64_PEAK_GOPS, "unit": "GFLOP/s",
+                     "peak_source": "nominal FP64 rate (1.25 TFLOP/s counting an FMA as 2)",
+                     "fp64_ops_per_launch": dom_ops / max(1, dom_launches),
+                     "hbm_achieved_gbs": achieved})
+        roof["frac"] = roof["achieved"] / FP64_PEAK_GOPS
 
     # ---- end to end through host buffers -----------------------------------------------------------
     e2e = None
@@ -488,6 +527,44 @@ def main():
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                "ms_per_step": e_ms}
 
+    # ---- node-feature pooling on the final lift (forward + backward), kernels timed live ----------
+    pooling = None
+    if args.pool > 0:
+        F = args.pool
+        n_c_f = int(ctx.level_info(ctx.level_count() - 1).n_c)
+        gen = torch.Generator(device=dev).manual_seed(0)
+        x = torch.randn(g.n, F, dtype=torch.float32, device=dev, generator=gen)
+        gxc = torch.randn(n_c_f, F, dtype=torch.float32, device=dev, generator=gen)
+        for _ in range(2):
+            ctx.pool_features(lift, n_c_f, x)
+            ctx.pool_features_backward(lift, n_c_f, gxc)
+        ctx.time_kernel("k_pool")
+        reps = 5
+        p0 = torch.cuda.Event(enable_timing=True)
+        p1 = torch.cuda.Event(enable_timing=True)
+        p2 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        p0.record(stream)
+        for _ in range(reps):
+            ctx.pool_features(lift, n_c_f, x)
+        p1.record(stream)
+        for _ in range(reps):
+            ctx.pool_features_backward(lift, n_c_f, gxc)
+        p2.record(stream)
+        torch.cuda.synchronize()
+        kp = ctx.kernel_profile()
+        ctx.time_kernel(None)
+        kern = {k: {"launches": v[0], "ms": v[1] / max(1, v[0]),
+                    "GBps": (v[2] / (v[1] * 1e-3) / 1e9) if v[2] > 0 else None}
+                for k, v in kp.items()}
+        top = max(kp.items(), key=lambda kv: kv[1][1])
+        ach = top[1][2] / (top[1][1] * 1e-3) / 1e9 if top[1][2] > 0 else None
+        pooling = {"features": F, "dtype": "f32", "n": g.n, "n_c": n_c_f,
+                   "forward_ms": p0.elapsed_time(p1) / reps,
+                   "backward_ms": p1.elapsed_time(p2) / reps, "kernels": kern,
+                   "roofline": {"kernel": top[0], "bound": "hbm", "achieved": ach, "peak": hbm,
+                                "unit": "GB/s", "frac": ach / hbm if ach else None}}
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(args.workload)
@@ -518,6 +595,8 @@ def main():
             "clocks": clocks,
             "gpu_launches": int(launches),
         }
+        if pooling is not None:
+            line["pooling"] = pooling
         if args.profile:
             line["kernel_profile"] = {k: [v[0], round(v[1], 4)] for k, v in
                                       sorted(prof.items(), key=lambda kv: -kv[1][1])}

@@ -244,6 +244,30 @@ SPC_API spc_status spc_compose_emap(spc_context* ctx, int32_t* emap_out);
 SPC_API spc_status spc_sort_fitness_static(int64_t m, const void* f, spc_dtype ftype,
                                            int32_t* order_out, void* stream);
 
+/* ---- node-feature pooling (graph-pooling layer on the coarsening) -------------------------- */
+
+/* Mean of every super-node's member features.  Definition 2's lift averages over the member
+ * pairs of two super-nodes (it divides by |u_c| |v_c|); for node features the same averaging
+ * is the mean over members:
+ *   xc[U][f] = (sum over the members v of U, in ascending v, of x[v][f]) / |U|
+ * summed left to right in the feature type, then one IEEE division by |U|; 0 for a super-node
+ * without members.
+ *   lift[n]      int32 super-node of every node, values in [0, n_c) (e.g. a composed lift)
+ *   x[n * F]     features, row-major, dtype SPC_F32 or SPC_F64
+ *   xc_out[n_c * F]  result, row-major, same dtype
+ * Device pointers, owned by the caller.  A lift value outside [0, n_c) returns
+ * SPC_ERR_INVALID_ARG with xc_out unspecified. */
+SPC_API spc_status spc_pool_features(spc_context* ctx, int64_t n, const int32_t* lift, int64_t n_c,
+                                     int64_t F, spc_dtype dtype, const void* x, void* xc_out);
+
+/* Gradient of spc_pool_features with the lift held fixed:
+ *   grad_x[v][f] = grad_xc[lift[v]][f] / |lift[v]|   (one IEEE division).
+ * grad_xc[n_c * F] and grad_x_out[n * F] row-major, dtype SPC_F32 or SPC_F64, device
+ * pointers.  Errors as spc_pool_features. */
+SPC_API spc_status spc_pool_features_backward(spc_context* ctx, int64_t n, const int32_t* lift,
+                                              int64_t n_c, int64_t F, spc_dtype dtype,
+                                              const void* grad_xc, void* grad_x_out);
+
 /* ---- timing ------------------------------------------------------------------------------- */
 
 /* Record CUDA events around every launch of the kernels whose name contains `kernel_substr`
@@ -253,10 +277,13 @@ SPC_API spc_status spc_time_kernel(spc_context* ctx, const char* kernel_substr);
 SPC_API spc_status spc_kernel_time(spc_context* ctx, int64_t* launches, double* total_ms);
 
 /* Per-kernel breakdown of the timed launches since the last spc_time_kernel: one line per
- * kernel, "name<TAB>launches<TAB>total_ms<TAB>bytes<LF>", NUL-terminated in buf[len].  bytes is
- * the sum over those launches of each launch's algorithmic DRAM bytes (every input the
- * operation needs read once, every output written once), 0 for launches without such a
- * model.  Returns SPC_ERR_INVALID_ARG (with the text truncated) if len is too small. */
+ * kernel, "name<TAB>launches<TAB>total_ms<TAB>bytes<TAB>fp_ops<LF>", NUL-terminated in
+ * buf[len].  bytes is the sum over those launches of each launch's algorithmic DRAM bytes
+ * (every input the operation needs read once, every output written once), 0 for launches
+ * without such a model.  fp_ops, for the score kernels, is the arithmetic the score needs:
+ * one addition per coordinate of N(a) u N(b) and one subtraction per coordinate in both rows,
+ * summed over the timed launches (0 for other kernels).  Returns SPC_ERR_INVALID_ARG (with the
+ * text truncated) if len is too small. */
 SPC_API spc_status spc_kernel_profile(spc_context* ctx, char* buf, size_t len);
 
 /* Number of kernel launches issued by the context since it was created (replayed graph

@@ -272,6 +272,29 @@ class Context:
                 "spc_contract_backward")
         return out
 
+    def pool_features(self, lift: torch.Tensor, n_c: int, x: torch.Tensor) -> torch.Tensor:
+        """Mean of every super-node's member features (x: n-by-F, float32 or float64)."""
+        x = x.contiguous()
+        lift = lift.to(torch.int32).contiguous()
+        F = x.shape[1]
+        out = torch.empty((n_c, F), dtype=x.dtype, device=x.device)
+        N.check(self.lib.spc_pool_features(self._handle, lift.shape[0], _ptr(lift), n_c, F,
+                                           _DT[x.dtype], _ptr(x), _ptr(out)),
+                "spc_pool_features")
+        return out
+
+    def pool_features_backward(self, lift: torch.Tensor, n_c: int,
+                               grad_xc: torch.Tensor) -> torch.Tensor:
+        grad_xc = grad_xc.contiguous()
+        lift = lift.to(torch.int32).contiguous()
+        F = grad_xc.shape[1]
+        out = torch.empty((lift.shape[0], F), dtype=grad_xc.dtype, device=grad_xc.device)
+        N.check(self.lib.spc_pool_features_backward(self._handle, lift.shape[0], _ptr(lift), n_c,
+                                                    F, _DT[grad_xc.dtype], _ptr(grad_xc),
+                                                    _ptr(out)),
+                "spc_pool_features_backward")
+        return out
+
     # ---- timing / accounting --------------------------------------------------------------------
     def time_kernel(self, substr: Optional[str]):
         N.check(self.lib.spc_time_kernel(self._handle, substr.encode() if substr else None),
@@ -285,15 +308,16 @@ class Context:
         return int(n.value), float(ms.value)
 
     def kernel_profile(self):
-        """{kernel name: (launches, total ms, algorithmic bytes)} for the launches timed since
-        time_kernel(); bytes are the summed per-launch algorithmic DRAM bytes of the launches
-        that carry a byte model (0 for the others)."""
+        """{kernel name: (launches, total ms, algorithmic bytes, fp ops)} for the launches
+        timed since time_kernel(); bytes are the summed per-launch algorithmic DRAM bytes of
+        the launches that carry a byte model (0 for the others), fp ops the score kernels'
+        required additions and subtractions (0 for the others)."""
         buf = ctypes.create_string_buffer(1 << 16)
         N.check(self.lib.spc_kernel_profile(self._handle, buf, len(buf)), "spc_kernel_profile")
         out = {}
         for line in buf.value.decode().splitlines():
-            name, cnt, ms, nbytes = line.split("\t")
-            out[name] = (int(cnt), float(ms), float(nbytes))
+            name, cnt, ms, nbytes, ops = line.split("\t")
+            out[name] = (int(cnt), float(ms), float(nbytes), float(ops))
         return out
 
     @property
@@ -341,3 +365,22 @@ class ContractWeights(torch.autograd.Function):
 
 def contract_weights(w_und: torch.Tensor, plan: ContractionPlan) -> torch.Tensor:
     return ContractWeights.apply(w_und, plan)
+
+
+class PoolFeatures(torch.autograd.Function):
+    """xc = mean of each super-node's member features (the node counterpart of Definition 2's
+    averaging over super-node sizes); backward divides every coarse gradient by the member
+    count and hands it to the members (the lift is held fixed)."""
+
+    @staticmethod
+    def forward(ctx, x: torch.Tensor, lift: torch.Tensor, n_c: int, context: Context):
+        ctx.lift, ctx.n_c, ctx.context = lift, n_c, context
+        return context.pool_features(lift, n_c, x)
+
+    @staticmethod
+    def backward(ctx, grad_xc: torch.Tensor):
+        return ctx.context.pool_features_backward(ctx.lift, ctx.n_c, grad_xc), None, None, None
+
+
+def pool_features(x: torch.Tensor, lift: torch.Tensor, n_c: int, context: Context) -> torch.Tensor:
+    return PoolFeatures.apply(x, lift, n_c, context)

@@ -91,6 +91,11 @@ cudaError_t record_event(spc_context* ctx, cudaEvent_t ev) {
     return cudaEventRecord(ev, ctx->stream);
 }
 
+unsigned long long* op_counter(spc_context* ctx, const char* kernel_name, int slot) {
+    if (!ctx->d_ops || !timed(ctx->timer, kernel_name)) return nullptr;
+    return ctx->d_ops + slot;
+}
+
 void before_launch(spc_context* ctx, const char* name) {
     Timer& t = ctx->timer;
     ctx->launches += 1;
@@ -792,6 +797,7 @@ void spc_context_destroy(spc_context* ctx) {
     drop_graph(ctx->replay);
     if (ctx->replay.d_mismatch) cudaFree(ctx->replay.d_mismatch);
     if (ctx->replay.d_hash) cudaFree(ctx->replay.d_hash);
+    if (ctx->d_ops) cudaFree(ctx->d_ops);
     if (ctx->replay.cap_stream) cudaStreamDestroy(ctx->replay.cap_stream);
     for (auto ev : ctx->tune_ev)
         if (ev) cudaEventDestroy(ev);
@@ -1012,6 +1018,29 @@ spc_status spc_contract_backward(spc_context* ctx, const int32_t* emap, int64_t 
     return sync_status(ctx);
 }
 
+spc_status spc_pool_features(spc_context* ctx, int64_t n, const int32_t* lift, int64_t n_c,
+                             int64_t F, spc_dtype dtype, const void* x, void* xc_out) {
+    SPC_TRY(begin_call(ctx));
+    if (n < 0 || n_c < 1 || F < 1 || n_c > INT32_MAX || n >= (int64_t)INT32_MAX ||
+        (dtype != SPC_F32 && dtype != SPC_F64) || (n > 0 && (!lift || !x)) || !xc_out)
+        return SPC_ERR_INVALID_ARG;
+    if (n > (int64_t(1) << 62) / F || n_c > (int64_t(1) << 62) / F) return SPC_ERR_TOO_LARGE;
+    SPC_TRY(run_pool_forward(ctx, n, lift, n_c, F, dtype, x, xc_out));
+    return sync_status(ctx);
+}
+
+spc_status spc_pool_features_backward(spc_context* ctx, int64_t n, const int32_t* lift,
+                                      int64_t n_c, int64_t F, spc_dtype dtype,
+                                      const void* grad_xc, void* grad_x_out) {
+    SPC_TRY(begin_call(ctx));
+    if (n < 0 || n_c < 1 || F < 1 || n_c > INT32_MAX || n >= (int64_t)INT32_MAX ||
+        (dtype != SPC_F32 && dtype != SPC_F64) || (n > 0 && (!lift || !grad_x_out)) || !grad_xc)
+        return SPC_ERR_INVALID_ARG;
+    if (n > (int64_t(1) << 62) / F || n_c > (int64_t(1) << 62) / F) return SPC_ERR_TOO_LARGE;
+    SPC_TRY(run_pool_backward(ctx, n, lift, n_c, F, dtype, grad_xc, grad_x_out));
+    return sync_status(ctx);
+}
+
 spc_status spc_compose_emap(spc_context* ctx, int32_t* emap_out) {
     SPC_TRY(begin_call(ctx));
     if (!emap_out || ctx->n_levels < 1) return SPC_ERR_INVALID_ARG;
@@ -1042,6 +1071,10 @@ spc_status spc_time_kernel(spc_context* ctx, const char* kernel_substr) {
     t.total_ms = 0.0;
     t.on = kernel_substr && kernel_substr[0];
     t.substr = t.on ? kernel_substr : "";
+    if (t.on) {
+        if (!ctx->d_ops) SPC_CUDA(cudaMalloc(&ctx->d_ops, 4 * sizeof(unsigned long long)));
+        SPC_CUDA(cudaMemset(ctx->d_ops, 0, 4 * sizeof(unsigned long long)));
+    }
     return SPC_OK;
 }
 
@@ -1070,11 +1103,16 @@ spc_status spc_kernel_time(spc_context* ctx, int64_t* launches, double* total_ms
 spc_status spc_kernel_profile(spc_context* ctx, char* buf, size_t len) {
     if (!ctx || (!buf && len)) return SPC_ERR_INVALID_ARG;
     SPC_TRY(drain_timer(ctx));
+    unsigned long long ops[4] = {0, 0, 0, 0};
+    if (ctx->d_ops) SPC_CUDA(cudaMemcpy(ops, ctx->d_ops, sizeof(ops), cudaMemcpyDeviceToHost));
     std::string out;
     char line[512];
     for (auto& pk : ctx->timer.per_kernel) {
-        snprintf(line, sizeof(line), "%s\t%lld\t%.6f\t%.0f\n", pk.name.c_str(),
-                 (long long)pk.launches, pk.ms, pk.bytes);
+        unsigned long long fp = 0;
+        if (pk.name.find("k_score_edges") != std::string::npos) fp = ops[0] + ops[1];
+        if (pk.name.find("k_score_warp_row") != std::string::npos) fp = ops[2] + ops[3];
+        snprintf(line, sizeof(line), "%s\t%lld\t%.6f\t%.0f\t%llu\n", pk.name.c_str(),
+                 (long long)pk.launches, pk.ms, pk.bytes, fp);
         out += line;
     }
     if (len) {

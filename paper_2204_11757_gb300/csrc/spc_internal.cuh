@@ -92,6 +92,8 @@ struct Work {
     Buf i_key, i_val, i_key2, i_val2, long_segs;                // intra edges (self-mass)
     Buf sort_hist, scan_tmp;                                    // sort / scan temporaries
     Buf stage_rowptr, stage_col, stage_w, stage_lift, stage_gptr;  // host staging
+    Buf pool_key, pool_val, pool_key2, pool_val2, pool_cnt, pool_off;  // feature pooling
+    Buf pool_nch, pool_choff, pool_owner, pool_part;
     Buf lift_final;                                             // composed lift of a call
 };
 
@@ -169,6 +171,9 @@ struct spc_context {
     // score-schedule autotuner: (dtype, log2 mean row length, log2 m) -> 1 edge tiles, 2 warp/row
     std::vector<std::pair<int64_t, int>> tuned;
     cudaEvent_t tune_ev[3] = {nullptr, nullptr, nullptr};
+    // arithmetic counts of the timed score launches: [0..1] edge tiles (adds, subtractions),
+    // [2..3] warp per row
+    unsigned long long* d_ops = nullptr;
 };
 
 namespace spc {
@@ -180,6 +185,9 @@ void free_all(spc_context* ctx);
 // launch accounting + optional timing of selected kernels
 void before_launch(spc_context* ctx, const char* name);
 void after_launch(spc_context* ctx, const char* name);
+
+// Device counters for a kernel's arithmetic count while that kernel is being timed, else null.
+unsigned long long* op_counter(spc_context* ctx, const char* kernel_name, int slot);
 
 // Algorithmic DRAM bytes of the next SPC_LAUNCH (the bytes the operation must move at minimum:
 // each input read once, each output written once), reported with the kernel's timed launches
@@ -282,6 +290,10 @@ spc_status run_sort_fitness(spc_context* ctx, int64_t m, const void* f, bool f32
 
 spc_status run_contract_forward(spc_context* ctx, const int32_t* perm, const int32_t* seg,
                                 int64_t m_c, const void* w_und, spc_dtype wt, void* a_und);
+spc_status run_pool_forward(spc_context* ctx, int64_t n, const int32_t* lift, int64_t n_c,
+                            int64_t F, spc_dtype dt, const void* x, void* xc);
+spc_status run_pool_backward(spc_context* ctx, int64_t n, const int32_t* lift, int64_t n_c,
+                             int64_t F, spc_dtype dt, const void* grad_xc, void* grad_x);
 spc_status run_contract_backward(spc_context* ctx, const int32_t* emap, int64_t m,
                                  const void* grad_a, void* grad_w, spc_dtype wt);
 

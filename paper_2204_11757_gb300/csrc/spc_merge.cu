@@ -14,12 +14,16 @@
 //      lightest edges, so the rounds run on the edges up to a threshold chosen from a score
 //      histogram to hold about 1.5 (n - n_c) edges; if that prefix's forest has fewer than
 //      n - n_c edges, the rounds are run again on every edge.
-//   2. The forest edges are compacted in eid order, radix-sorted by score (stable, so ties stay
-//      in eid order) -- per graph for batches -- and the first n - n_c of each graph are
-//      united in a second union-find.
+//   2. The forest edges are compacted in eid order.  For one graph an exact radix select on
+//      11-bit digits of (score, eid) finds the (n - n_c)-th lightest and every forest edge up to
+//      it is united in a second union-find; for batches the forest edges are radix-sorted by
+//      score and then by graph (stable, so ties stay in eid order) and the first
+//      n_b - target_b of each graph are united.
 //   3. Relabel: root = smallest member; flag roots, exclusive scan, id = scan[root] (Definition
 //      1's super-nodes, numbered by smallest member).
 // Every retry loop is bounded (kSpinLimit); giving up sets DEV_TIMEOUT in the status word.
+#include <atomic>
+
 #include "spc_internal.cuh"
 
 namespace spc {
@@ -42,6 +46,41 @@ __device__ __forceinline__ int32_t uf_find(int32_t* parent, int32_t x, uint32_t*
     }
     atomicOr(status, DEV_TIMEOUT);
     return x;
+}
+
+// atomicMin of v into a[idx] by every active lane of the warp (all 32 lanes call it).  When
+// neighbouring lanes target the same slot -- the edges of a hub component -- the lanes of each
+// slot first take their minimum together and one lane issues the atomic.
+__device__ __forceinline__ void warp_atomic_min_u64(unsigned long long* a, int32_t idx,
+                                                    unsigned long long v, bool act) {
+    const int lane = threadIdx.x & 31;
+    const int32_t key = act ? idx : -1;
+    const int32_t prev = __shfl_up_sync(0xffffffffu, key, 1);
+    if (!__any_sync(0xffffffffu, act && lane > 0 && prev == key)) {
+        if (act) atomicMin(a + idx, v);
+        return;
+    }
+    const unsigned peers = __match_any_sync(0xffffffffu, key);
+    if (!act) return;  // inactive lanes form their own group
+    const unsigned hi = (unsigned)(v >> 32), lo = (unsigned)v;
+    const unsigned hmin = __reduce_min_sync(peers, hi);
+    const unsigned lmin = __reduce_min_sync(peers, hi == hmin ? lo : 0xffffffffu);
+    if (lane == __ffs(peers) - 1) atomicMin(a + idx, ((unsigned long long)hmin << 32) | lmin);
+}
+
+__device__ __forceinline__ void warp_atomic_min_i32(int32_t* a, int32_t idx, int32_t v,
+                                                    bool act) {
+    const int lane = threadIdx.x & 31;
+    const int32_t key = act ? idx : -1;
+    const int32_t prev = __shfl_up_sync(0xffffffffu, key, 1);
+    if (!__any_sync(0xffffffffu, act && lane > 0 && prev == key)) {
+        if (act) atomicMin(a + idx, v);
+        return;
+    }
+    const unsigned peers = __match_any_sync(0xffffffffu, key);
+    if (!act) return;
+    const int32_t vmin = __reduce_min_sync(peers, v);
+    if (lane == __ffs(peers) - 1) atomicMin(a + idx, vmin);
 }
 
 // unite the sets of a and b; the larger root is hooked below the smaller one with a CAS, so a
@@ -127,12 +166,10 @@ k_bv_minkey(int round0, int64_t m, const int32_t* __restrict__ in_count,
             ru[it] = in[it] ? (round0 ? u[it] : uf_find(parent, u[it], status)) : 0;
             rv[it] = in[it] ? (round0 ? v[it] : uf_find(parent, v[it], status)) : 0;
             in[it] = in[it] && ru[it] != rv[it];
-            if (in[it]) {
-                const unsigned long long pk = MinKey<KT>::pack(k[it], e[it]);
-                atomicMin(best_k + ru[it], pk);
-                atomicMin(best_k + rv[it], pk);
-                ++nkeep;
-            }
+            const unsigned long long pk = MinKey<KT>::pack(k[it], e[it]);
+            warp_atomic_min_u64(best_k, ru[it], pk, in[it]);
+            warp_atomic_min_u64(best_k, rv[it], pk, in[it]);
+            nkeep += in[it] ? 1 : 0;
         }
         // block-wide exclusive prefix of the survivors, one global atomic per block and pass
         int32_t incl = nkeep;
@@ -222,12 +259,18 @@ k_bv_tiebreak(const int32_t* __restrict__ count, const int32_t* __restrict__ wl_
               const unsigned long long* __restrict__ key, const unsigned long long* best_k,
               int32_t* best_e) {
     const int64_t cnt = *count;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cnt;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const int32_t e = wl_e[i], ru = wl_u[i], rv = wl_v[i];
-        const unsigned long long k = key[e];
-        if (k == best_k[ru]) atomicMin(best_e + ru, e);
-        if (k == best_k[rv]) atomicMin(best_e + rv, e);
+    for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x; i0 < cnt;
+         i0 += (int64_t)gridDim.x * blockDim.x) {  // uniform per warp: the helpers need it
+        const int64_t i = i0 + threadIdx.x;
+        const bool act = i < cnt;
+        int32_t e = 0, ru = 0, rv = 0;
+        unsigned long long k = 0;
+        if (act) {
+            e = wl_e[i]; ru = wl_u[i]; rv = wl_v[i];
+            k = key[e];
+        }
+        warp_atomic_min_i32(best_e, ru, e, act && k == best_k[ru]);
+        warp_atomic_min_i32(best_e, rv, e, act && k == best_k[rv]);
     }
 }
 
@@ -242,19 +285,28 @@ k_bv_hook(const int32_t* __restrict__ count, const int32_t* __restrict__ wl_e,
           unsigned long long* other_k, int32_t* other_e, int32_t* parent, uint8_t* msf,
           uint32_t* status) {
     const int64_t cnt = *count;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cnt;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const int32_t e = wl_e[i], ru = wl_u[i], rv = wl_v[i];
+    const int lane = threadIdx.x & 31;
+    for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x; i0 < cnt;
+         i0 += (int64_t)gridDim.x * blockDim.x) {  // uniform per warp
+        const int64_t i = i0 + threadIdx.x;
+        const bool act = i < cnt;
+        int32_t e = 0, ru = -1, rv = -1;
+        if (act) { e = wl_e[i]; ru = wl_u[i]; rv = wl_v[i]; }
+        // a slot shared with the previous lane (a hub component) is cleared by that lane
+        const int32_t pu = __shfl_up_sync(0xffffffffu, ru, 1);
+        const int32_t pv = __shfl_up_sync(0xffffffffu, rv, 1);
+        if (!act) continue;
+        const bool clr_u = lane == 0 || pu != ru, clr_v = lane == 0 || pv != rv;
         bool picked;
         if (MinKey<KT>::two_phase) {
             picked = best_e[ru] == e || best_e[rv] == e;
-            other_e[ru] = INT32_MAX;
-            other_e[rv] = INT32_MAX;
+            if (clr_u) other_e[ru] = INT32_MAX;
+            if (clr_v) other_e[rv] = INT32_MAX;
         } else {
             picked = (int32_t)(uint32_t)best_k[ru] == e || (int32_t)(uint32_t)best_k[rv] == e;
         }
-        other_k[ru] = ~0ull;
-        other_k[rv] = ~0ull;
+        if (clr_u) other_k[ru] = ~0ull;
+        if (clr_v) other_k[rv] = ~0ull;
         if (picked) {
             msf[e] = 1;
             uf_unite(parent, ru, rv, status);
@@ -604,11 +656,12 @@ spc_status select_typed(spc_context* ctx, const GraphView& g, const KT* key,
     if (use_prefix) {
         SPC_TRY(ensure(ctx, W.key_hist, 32768 * 4));
         SPC_CUDA(cudaMemsetAsync(W.key_hist.p, 0, 32768 * 4, ctx->stream));
-        static bool attr = false;
-        if (!attr) {
+        static std::atomic<unsigned long long> attr_devs{0};  // devices already set up
+        const unsigned long long bit = 1ull << (ctx->device & 63);
+        if (!(attr_devs.load() & bit)) {
             SPC_CUDA(cudaFuncSetAttribute(k_key_hist<KT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           32768 * 4));
-            attr = true;
+            attr_devs.fetch_or(bit);
         }
         SPC_LAUNCH(ctx, k_key_hist<KT>, ctx->num_sms, 1024, 32768 * 4, m, key, tau_shift,
                    W.key_hist.as<uint32_t>());

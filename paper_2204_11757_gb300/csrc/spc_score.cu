@@ -110,50 +110,99 @@ k_rows_degree(int64_t n, int64_t nnz, const int64_t* __restrict__ rowptr,
     }
 }
 
-// S0 + S1 for rows longer than kLongRow: one CTA per row checks the entries and counts them in
-// parallel, and records the row as a sequence (base, length) for the exact degree sum, which
-// the per-binade tables evaluate (spc_seqtab.cu); integer degrees are a plain reduction.
+// S0 for rows longer than kLongRow, part 1: one warp per row records the row as a sequence
+// (base, length) for the exact degree sum (the per-binade tables of spc_seqtab.cu evaluate
+// it) and counts its lower neighbours by a 32-way search for x among the sorted columns.  On
+// an unsorted row the count is wrong but in range; part 2 reports the row.
 template <class WT>
 __global__ void __launch_bounds__(kThreads)
-k_long_rows_check(int64_t n, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
-                  const WT* __restrict__ w, int validate, const int32_t* __restrict__ long_rows,
-                  const int32_t* __restrict__ long_count, typename Tr<WT>::Acc* __restrict__ deg,
-                  int32_t* __restrict__ up_cnt, int32_t* __restrict__ nlow_out,
-                  int64_t* __restrict__ lr_base, int64_t* __restrict__ lr_len,
-                  int64_t* __restrict__ lr_idx, uint32_t* __restrict__ status) {
-    __shared__ int32_t sh_nlow;
+k_long_rows_meta(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                 const int32_t* __restrict__ long_rows, const int32_t* __restrict__ long_count,
+                 typename Tr<WT>::Acc* __restrict__ deg, int32_t* __restrict__ up_cnt,
+                 int32_t* __restrict__ nlow_out, int64_t* __restrict__ lr_base,
+                 int64_t* __restrict__ lr_len, int64_t* __restrict__ lr_idx) {
     const int32_t cnt = *long_count;
-    for (int32_t i = blockIdx.x; i < cnt; i += gridDim.x) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < cnt;
+         i += warps) {
         const int64_t x = long_rows[i];
         const int64_t r0 = rowptr[x], r1 = rowptr[x + 1];
-        if (threadIdx.x == 0) sh_nlow = 0;
-        __syncthreads();
-        uint32_t bits = 0;
-        int32_t nl = 0;
-        for (int64_t j = r0 + threadIdx.x; j < r1; j += blockDim.x) {
-            const int32_t y = col[j];
-            if (validate) {
-                if (y < 0 || (int64_t)y >= n || (j > r0 && col[j - 1] >= y)) bits |= DEV_UNSORTED;
-                if ((int64_t)y == x) bits |= DEV_SELF_LOOP;
-                if (!Tr<WT>::ok(w[j])) bits |= DEV_BAD_WEIGHT;
-            }
-            nl += ((int64_t)y < x) ? 1 : 0;
+        // first position in [r0, r1] whose column is >= x
+        int64_t lo = r0, hi = r1;  // answer in [lo, hi]
+        while (hi > lo) {
+            const int64_t step = (hi - lo + 31) / 32;
+            const int64_t probe = lo + (int64_t)lane * step;  // lane 0 probes lo itself
+            const bool below = probe < hi && (int64_t)col[probe] < x;
+            const int nb = __popc(__ballot_sync(0xffffffffu, below));
+            // columns below x form a prefix of the probes
+            if (nb == 0) { hi = lo; break; }
+            lo = lo + (int64_t)(nb - 1) * step + 1;
+            const int64_t cap = lo - 1 + step;
+            hi = cap < hi ? cap : hi;
         }
-        if (bits) atomicOr(status, bits);
-        if (nl) atomicAdd(&sh_nlow, nl);
-        if constexpr (std::is_same<WT, int32_t>::value) {
-            const long long d = cta_sum_i64(r1 - r0, [&](int64_t k) { return (long long)w[r0 + k]; });
-            if (threadIdx.x == 0) deg[x] = d;
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            nlow_out[x] = sh_nlow;
-            up_cnt[x] = (int32_t)(r1 - r0) - sh_nlow;
+        if (lane == 0) {
+            const int32_t nl = (int32_t)(lo - r0);
+            nlow_out[x] = nl;
+            up_cnt[x] = (int32_t)(r1 - r0) - nl;
             lr_base[i] = r0;
             lr_len[i] = r1 - r0;
             lr_idx[i] = x;
+            if constexpr (std::is_same<WT, int32_t>::value) deg[x] = 0;
         }
-        __syncthreads();
+    }
+}
+
+// S0 (+ S1 for integer weights) for rows longer than kLongRow, part 2: one thread per entry,
+// flat over all long rows (lr_eoff: exclusive prefix of the row lengths).  Checks every entry
+// and, for integer weights, adds the row's weights into its degree (exact in any order).
+template <class WT>
+__global__ void __launch_bounds__(kThreads)
+k_long_rows_flat(int64_t n, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                 const WT* __restrict__ w, int validate, const int32_t* __restrict__ long_rows,
+                 const int32_t* __restrict__ long_count, const int64_t* __restrict__ lr_eoff,
+                 typename Tr<WT>::Acc* __restrict__ deg, uint32_t* __restrict__ status) {
+    constexpr bool kInt = std::is_same<WT, int32_t>::value;
+    const int32_t cnt = *long_count;
+    const int64_t total = lr_eoff[cnt];
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t f0 = (int64_t)blockIdx.x * blockDim.x; f0 < total; f0 += stride) {
+        const int64_t f = f0 + threadIdx.x;
+        const bool act = f < total;
+        int32_t row = 0;
+        long long wsum = 0;
+        if (act) {
+            int32_t lo = 0, hi = cnt - 1;
+            while (lo < hi) {
+                const int32_t mid = (lo + hi + 1) >> 1;
+                if (lr_eoff[mid] <= f) lo = mid; else hi = mid - 1;
+            }
+            row = lo;
+            const int64_t x = long_rows[lo];
+            const int64_t r0 = rowptr[x];
+            const int64_t j = r0 + (f - lr_eoff[lo]);
+            const int32_t y = col[j];
+            const WT wj = w[j];
+            if (validate) {
+                uint32_t bits = 0;
+                if (y < 0 || (int64_t)y >= n || (j > r0 && col[j - 1] >= y)) bits |= DEV_UNSORTED;
+                if ((int64_t)y == x) bits |= DEV_SELF_LOOP;
+                if (!Tr<WT>::ok(wj)) bits |= DEV_BAD_WEIGHT;
+                if (bits) atomicOr(status, bits);
+            }
+            if constexpr (kInt) wsum = (long long)wj;
+        }
+        if constexpr (kInt) {
+            // lanes of one row add up first, one atomic per row and warp
+            const unsigned peers = __match_any_sync(0xffffffffu, act ? row : -1);
+            const int lane = threadIdx.x & 31;
+            long long part = 0;
+            for (unsigned m = peers; m; m &= m - 1)
+                part += __shfl_sync(peers, wsum, __ffs(m) - 1);
+            if (act && lane == __ffs(peers) - 1)
+                atomicAdd(reinterpret_cast<unsigned long long*>(deg + long_rows[row]),
+                          (unsigned long long)part);
+        }
     }
 }
 
@@ -203,7 +252,8 @@ k_long_rows_edges(const int64_t* __restrict__ rowptr, const int32_t* __restrict_
 }
 
 // S2 (+ the edge list): one thread per row.  p[j] = w[j] / d[x]; for the entries above the
-// diagonal writes the undirected edge (x, y) at its edge id; when `validate`, looks up the
+// diagonal writes the undirected edge (x, y) at its edge id; when `validate` (set only when no
+// score kernel follows: those check every upper entry's mirror on their walks), looks up the
 // mirror entry (y, x) by binary search and compares the weight bits.
 template <class WT>
 __global__ void __launch_bounds__(kThreads)
@@ -252,38 +302,91 @@ k_rows_edges(int64_t n, const int64_t* __restrict__ rowptr, const int32_t* __res
     }
 }
 
+// Arithmetic count of a score launch, for the roofline: ops[0] += additions into the running
+// sums (one per union coordinate), ops[1] += subtractions (one per coordinate present in both
+// rows).  One atomic per warp; every lane of the block reaches it.
+__device__ __forceinline__ void count_ops(unsigned long long* ops, uint32_t n_add,
+                                          uint32_t n_sub) {
+    if (!ops) return;
+    const uint32_t a = __reduce_add_sync(0xffffffffu, n_add);
+    const uint32_t b = __reduce_add_sync(0xffffffffu, n_sub);
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(ops, (unsigned long long)a);
+        atomicAdd(ops + 1, (unsigned long long)b);
+    }
+}
+
+// raw bits of entry j of a weight array of wsize-byte elements (int32, binary32 or binary64)
+__device__ __forceinline__ uint64_t weight_bits(const void* w, int wsize, int64_t j) {
+    return wsize == 8 ? static_cast<const unsigned long long*>(w)[j]
+                      : (uint64_t)static_cast<const unsigned int*>(w)[j];
+}
+
+// true if row [j0, j1) (sorted) holds column a with weight bits wb: the mirror of entry (a, .)
+__device__ __forceinline__ bool has_mirror(const int32_t* __restrict__ col, const void* w,
+                                           int wsize, int64_t j0, int64_t j1, int64_t a,
+                                           uint64_t wb) {
+    int64_t lo = j0, hi = j1;
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if ((int64_t)col[mid] < a) lo = mid + 1; else hi = mid;
+    }
+    return lo < j1 && (int64_t)col[lo] == a && weight_bits(w, wsize, lo) == wb;
+}
+
 // S3, edge-tile schedule: one thread per undirected edge; consecutive threads take consecutive
 // edge ids, which mostly share row a (cached), and walk rows a and b in step.
 template <class PT, class KT>
 __global__ void __launch_bounds__(kThreads)
 k_score_edges(int64_t m, const int32_t* __restrict__ eu, const int32_t* __restrict__ ev,
               const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
-              const PT* __restrict__ p, KT* __restrict__ score, const uint32_t* status) {
+              const PT* __restrict__ p, KT* __restrict__ score, const void* __restrict__ w,
+              const void* __restrict__ w_und, int wsize, int validate, uint32_t* status,
+              unsigned long long* __restrict__ ops) {
     if (*status) return;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    uint32_t n_add = 0, n_sub = 0;  // union coordinates, coordinates in both rows
+    bool asym = false;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += stride) {
         const int32_t a = eu[e], b = ev[e];
         int64_t i = rowptr[a];
         const int64_t ie = rowptr[a + 1];
         int64_t j = rowptr[b];
         const int64_t je = rowptr[b + 1];
-        if (ie - i > kLongRow || je - j > kLongRow) continue;  // hub edge: k_score_hub
+        if (ie - i > kLongRow || je - j > kLongRow) {  // hub edge: k_score_hub
+            // a long row a has its mirrors checked with the long rows; a long row b only
+            // holds the mirror of this entry, so it is looked up here
+            if (validate && ie - i <= kLongRow)
+                asym = asym || !has_mirror(col, w, wsize, j, je, a,
+                                           weight_bits(w_und, wsize, e));
+            continue;
+        }
         // one uniform step per coordinate of the union: t = |pa - pb| with the missing side
-        // read as 0 (exact: |x - 0| = x), so every lane issues the same two FP64 operations
+        // read as 0 (exact: |x - 0| = x), so every lane issues the same two FP operations
         PT s = PT(0);
         constexpr int32_t kEnd = 0x7fffffff;
         int32_t ca = i < ie ? col[i] : kEnd;
         int32_t cb = j < je ? col[j] : kEnd;
+        // S0's symmetry check rides on the walk: coordinate a of row b is the mirror entry of
+        // (a, b), and its weight must have the same bits
+        bool mirror = false;
         while (ca != kEnd || cb != kEnd) {
             const bool ta = ca <= cb, tb = cb <= ca;
+            if (validate && tb && cb == a)
+                mirror = weight_bits(w, wsize, j) == weight_bits(w_und, wsize, e);
             const PT pa = ta ? p[i] : PT(0);
             const PT pb = tb ? p[j] : PT(0);
             s = p_add(s, p_absdiff(pa, pb));
+            ++n_add;
+            n_sub += (ta && tb) ? 1u : 0u;
             if (ta) { ++i; ca = i < ie ? col[i] : kEnd; }
             if (tb) { ++j; cb = j < je ? col[j] : kEnd; }
         }
         score[e] = key_bits(s);
+        asym = asym || (validate && !mirror);
     }
+    if (asym) atomicOr(status, DEV_NOT_SYMMETRIC);
+    count_ops(ops, n_add, n_sub);
 }
 
 // S3, warp-per-row schedule: a warp owns row a, keeps its columns and p values in shared
@@ -296,8 +399,11 @@ __global__ void __launch_bounds__(kThreads)
 k_score_warp_row(int64_t n, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
                  const PT* __restrict__ p, const int32_t* __restrict__ up_ptr,
                  const int32_t* __restrict__ nlow, KT* __restrict__ score,
-                 const uint32_t* status) {
+                 const void* __restrict__ w, const void* __restrict__ w_und, int wsize,
+                 int validate, uint32_t* status, unsigned long long* __restrict__ ops) {
     if (*status) return;
+    uint32_t n_add = 0, n_sub = 0;
+    bool asym = false;
     __shared__ int32_t s_col[kThreads / 32][kRowCache];
     __shared__ PT s_p[kThreads / 32][kRowCache];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -321,7 +427,26 @@ k_score_warp_row(int64_t n, const int64_t* __restrict__ rowptr, const int32_t* _
             int64_t i = 0;
             int64_t j = rowptr[b];
             const int64_t je = rowptr[b + 1];
-            if (je - j > kLongRow) continue;  // hub edge: k_score_hub
+            const int64_t e = e0 + (jb - ufirst);
+            if (je - j > kLongRow) {  // hub edge: k_score_hub; the mirror sits in the long row
+                if (validate)
+                    asym = asym || !has_mirror(col, w, wsize, j, je, a,
+                                               weight_bits(w_und, wsize, e));
+                continue;
+            }
+            // the mirror entry (b, a) is where row b holds column a; its weight bits must match
+            bool mirror = false;
+            if (validate) {
+                for (int64_t q = j; q < je; ++q) {
+                    const int32_t c = col[q];
+                    if ((int64_t)c >= a) {
+                        mirror = (int64_t)c == a &&
+                                 weight_bits(w, wsize, q) == weight_bits(w_und, wsize, e);
+                        break;
+                    }
+                }
+                asym = asym || !mirror;
+            }
             PT s = PT(0);
             while (i < da && j < je) {
                 const int32_t ca = cached ? s_col[wib][i] : col[r0 + i];
@@ -335,18 +460,23 @@ k_score_warp_row(int64_t n, const int64_t* __restrict__ rowptr, const int32_t* _
                 } else {
                     t = p_absdiff(cached ? s_p[wib][i] : p[r0 + i], p[j]);
                     ++i; ++j;
+                    ++n_sub;
                 }
                 s = p_add(s, t);
+                ++n_add;
             }
+            n_add += (uint32_t)(da - i) + (uint32_t)(je - j);
             while (i < da) {
                 s = p_add(s, cached ? s_p[wib][i] : p[r0 + i]);
                 ++i;
             }
             while (j < je) s = p_add(s, p[j++]);
-            score[e0 + (jb - ufirst)] = key_bits(s);
+            score[e] = key_bits(s);
         }
         __syncwarp();
     }
+    if (asym) atomicOr(status, DEV_NOT_SYMMETRIC);
+    count_ops(ops, n_add, n_sub);
 }
 
 // ---- hub edges ----------------------------------------------------------------------------------
@@ -605,13 +735,11 @@ static spc_status score_typed(spc_context* ctx, GraphView& g, bool validate, voi
     SPC_LAUNCH(ctx, k_rows_degree<WT>, gb, kThreads, 0, n, nnz, g.rowptr, g.col,
                static_cast<const WT*>(g.w), validate ? 1 : 0, W.deg.as<Acc>(),
                W.up_cnt.as<int32_t>(), W.first_up.as<int32_t>(), long_rows, long_count, status);
-    SPC_LAUNCH(ctx, k_long_rows_check<WT>, persist, kThreads, 0, n, g.rowptr, g.col,
-               static_cast<const WT*>(g.w), validate ? 1 : 0, long_rows, long_count,
-               W.deg.as<Acc>(), W.up_cnt.as<int32_t>(), W.first_up.as<int32_t>(),
-               W.lr_base.as<int64_t>(), W.lr_len.as<int64_t>(), W.lr_idx.as<int64_t>(), status);
+    SPC_LAUNCH(ctx, k_long_rows_meta<WT>, persist, kThreads, 0, g.rowptr, g.col, long_rows,
+               long_count, W.deg.as<Acc>(), W.up_cnt.as<int32_t>(), W.first_up.as<int32_t>(),
+               W.lr_base.as<int64_t>(), W.lr_len.as<int64_t>(), W.lr_idx.as<int64_t>());
     SPC_TRY(scan_i32(ctx, W.up_cnt.as<int32_t>(), W.up_ptr.as<int32_t>(), n));
-    // the edge count and the number of long rows (and the input checks so far)
-    SPC_TRY(check_status(ctx));
+    // the edge count and the number of long rows
     int64_t sizes[2];
     {
         const void* ptrs[2] = {W.up_ptr.as<int32_t>() + n, long_count};
@@ -620,25 +748,35 @@ static spc_status score_typed(spc_context* ctx, GraphView& g, bool validate, voi
     }
     const int64_t m = sizes[0];
     const int64_t n_long = sizes[1];
-    if (2 * m != nnz) return SPC_ERR_NOT_SYMMETRIC;
-    g.m = m;
     if (n_long > 0) {
         SPC_TRY(scan_i64_i64(ctx, W.lr_len.as<int64_t>(), W.lr_eoff.as<int64_t>(), n_long));
-        if (fp) {  // exact degrees of the long rows from per-binade tables of their weights
-            SPC_TRY(seqtab_build(ctx, g.w, std::is_same<WT, float>::value, n_long,
-                                 W.lr_base.as<int64_t>(), W.lr_len.as<int64_t>(), true, W.tab_w));
-            SPC_TRY(seqtab_full_sums(ctx, g.w, std::is_same<WT, float>::value,
-                                     W.lr_base.as<int64_t>(), W.lr_len.as<int64_t>(), W.tab_w,
-                                     W.lr_idx.as<int64_t>(), W.deg.p));
-        }
+        SPC_LAUNCH(ctx, k_long_rows_flat<WT>, maxb, kThreads, 0, n, g.rowptr, g.col,
+                   static_cast<const WT*>(g.w), validate ? 1 : 0, long_rows, long_count,
+                   W.lr_eoff.as<int64_t>(), W.deg.as<Acc>(), status);
+    }
+    // every input check of every row so far
+    SPC_TRY(check_status(ctx));
+    if (2 * m != nnz) return SPC_ERR_NOT_SYMMETRIC;
+    g.m = m;
+    if (n_long > 0 && fp) {  // exact degrees of the long rows from per-binade tables
+        SPC_TRY(seqtab_build(ctx, g.w, std::is_same<WT, float>::value, n_long,
+                             W.lr_base.as<int64_t>(), W.lr_len.as<int64_t>(), true, W.tab_w));
+        SPC_TRY(seqtab_full_sums(ctx, g.w, std::is_same<WT, float>::value,
+                                 W.lr_base.as<int64_t>(), W.lr_len.as<int64_t>(), W.tab_w,
+                                 W.lr_idx.as<int64_t>(), W.deg.p));
     }
     // rowptr, columns, weights, degrees and row counts read once; p and the undirected edge
     // list written once (no model on levels with long rows: another kernel takes their part)
     if (n_long == 0)
         note_bytes(ctx, 8.0 * (n + 1) + nnz * (4 + s_w) + n * (s_acc + 8) + nnz * s_p +
                             m * (8 + s_w));
+    // the symmetry of rows up to kLongRow is checked by the score kernels' walks when scores
+    // are computed; without scores, here
+    const int vflag = validate ? 1 : 0;
+    const int wsize = (int)sizeof(WT);
+    const bool mirror_here = validate && (score == nullptr || m == 0);
     SPC_LAUNCH(ctx, k_rows_edges<WT>, gb, kThreads, 0, n, g.rowptr, g.col,
-               static_cast<const WT*>(g.w), validate ? 1 : 0, W.deg.as<Acc>(),
+               static_cast<const WT*>(g.w), mirror_here ? 1 : 0, W.deg.as<Acc>(),
                W.first_up.as<int32_t>(), W.up_ptr.as<int32_t>(), W.p.as<P>(),
                W.eu.as<int32_t>(), W.ev.as<int32_t>(), W.w_und.as<WT>(), status);
     if (n_long > 0) {
@@ -648,8 +786,10 @@ static spc_status score_typed(spc_context* ctx, GraphView& g, bool validate, voi
                    W.lr_eoff.as<int64_t>(), W.p.as<P>(), W.eu.as<int32_t>(),
                    W.ev.as<int32_t>(), W.w_und.as<WT>(), status);
     }
-    if (validate) SPC_TRY(check_status(ctx));  // no later kernel runs on an asymmetric input
-    if (score == nullptr || m == 0) return SPC_OK;
+    if (score == nullptr || m == 0) {
+        if (validate) SPC_TRY(check_status(ctx));
+        return SPC_OK;
+    }
     if (schedule != 1 && schedule != 2) {
         // autotuned: both schedules compute the same bits; time each once per shape bucket
         int lg_deg = 0, lg_m = 0;
@@ -666,11 +806,11 @@ static spc_status score_typed(spc_context* ctx, GraphView& g, bool validate, voi
             SPC_CUDA(cudaEventRecord(ctx->tune_ev[0], ctx->stream));
             SPC_LAUNCH(ctx, (k_score_edges<P, Key>), grid_for(m, kThreads, maxb), kThreads, 0, m,
                        W.eu.as<int32_t>(), W.ev.as<int32_t>(), g.rowptr, g.col, W.p.as<P>(),
-                       static_cast<Key*>(score), status);
+                       static_cast<Key*>(score), g.w, W.w_und.p, wsize, vflag, status, nullptr);
             SPC_CUDA(cudaEventRecord(ctx->tune_ev[1], ctx->stream));
             SPC_LAUNCH(ctx, (k_score_warp_row<P, Key>), gw, kThreads, 0, n, g.rowptr, g.col,
                        W.p.as<P>(), W.up_ptr.as<int32_t>(), W.first_up.as<int32_t>(),
-                       static_cast<Key*>(score), status);
+                       static_cast<Key*>(score), g.w, W.w_und.p, wsize, vflag, status, nullptr);
             SPC_CUDA(cudaEventRecord(ctx->tune_ev[2], ctx->stream));
             SPC_CUDA(cudaEventSynchronize(ctx->tune_ev[2]));
             float t_edges = 0.f, t_rows = 0.f;
@@ -690,14 +830,16 @@ static spc_status score_typed(spc_context* ctx, GraphView& g, bool validate, voi
         const int gw = grid_for(n, warps_per_block, maxb);
         SPC_LAUNCH(ctx, (k_score_warp_row<P, Key>), gw, kThreads, 0, n, g.rowptr, g.col,
                    W.p.as<P>(), W.up_ptr.as<int32_t>(), W.first_up.as<int32_t>(),
-                   static_cast<Key*>(score), status);
+                   static_cast<Key*>(score), g.w, W.w_und.p, wsize, vflag, status,
+                   op_counter(ctx, "(k_score_warp_row<P, Key>)", 2));
     } else {
         note_bytes(ctx, score_bytes);
         SPC_LAUNCH(ctx, (k_score_edges<P, Key>), grid_for(m, kThreads, maxb), kThreads, 0, m,
                    W.eu.as<int32_t>(), W.ev.as<int32_t>(), g.rowptr, g.col, W.p.as<P>(),
-                   static_cast<Key*>(score), status);
+                   static_cast<Key*>(score), g.w, W.w_und.p, wsize, vflag, status,
+                   op_counter(ctx, "(k_score_edges<P, Key>)", 0));
     }
-    if (n_long == 0) return SPC_OK;
+    if (n_long == 0) return validate ? check_status(ctx) : SPC_OK;
     // hub edges: per-binade tables of every hub row's normalised weights, then one thread per
     // hub entry (one warp per entry whose other row is long)
     SPC_TRY(seqtab_build(ctx, W.p.p, std::is_same<P, float>::value, n_long,
@@ -712,7 +854,7 @@ static spc_status score_typed(spc_context* ctx, GraphView& g, bool validate, voi
                W.p.as<P>(), W.up_ptr.as<int32_t>(), W.first_up.as<int32_t>(), long_rows,
                long_count, W.lr_eoff.as<int64_t>(), tv, W.heavy.as<int32_t>(), heavy_count,
                static_cast<Key*>(score), status);
-    return SPC_OK;
+    return validate ? check_status(ctx) : SPC_OK;  // every input check, symmetry included
 }
 
 spc_status run_score(spc_context* ctx, GraphView& g, bool validate, void* score, int schedule) {

@@ -6,6 +6,8 @@
 // prefix), stages the tile in shared memory in digit order and writes it out so that items of
 // one digit leave the tile as one contiguous run.  Tiles keep input order and ranks are stable,
 // so equal keys keep their input order.  No inter-block waits.
+#include <atomic>
+
 #include "spc_internal.cuh"
 
 namespace spc {
@@ -201,7 +203,7 @@ __global__ void k_os_bases(int npass, const uint32_t* __restrict__ hist, uint32_
 }
 
 template <class K>
-__global__ void __launch_bounds__(RT) k_os_pass(const K* __restrict__ kin,
+__global__ void __launch_bounds__(RT, 2) k_os_pass(const K* __restrict__ kin,
                                                 const uint32_t* __restrict__ vin,
                                                 K* __restrict__ kout, uint32_t* __restrict__ vout,
                                                 int64_t count, int shift, uint32_t mask,
@@ -220,8 +222,7 @@ __global__ void __launch_bounds__(RT) k_os_pass(const K* __restrict__ kin,
     const int64_t wbase = tile * RTILE + (int64_t)warp * (32 * RI);
     K key[RI];
     uint32_t val[RI];
-    uint32_t dig[RI];
-    uint32_t rnk[RI];
+    uint32_t dr[RI];  // digit (low 16 bits; RADIX + lane when invalid) | rank in warp << 16
     // every load of the tile is issued before the first is used (all in flight at once)
 #pragma unroll
     for (int k = 0; k < RI; ++k) {
@@ -237,8 +238,7 @@ __global__ void __launch_bounds__(RT) k_os_pass(const K* __restrict__ kin,
         const uint32_t d = valid ? digit_of(key[k], shift, mask) : (RADIX + lane);
         const unsigned peers = __match_any_sync(0xffffffffu, d);
         const uint32_t before = valid ? s.wcnt[warp][d] : 0u;
-        rnk[k] = before + (uint32_t)__popc(peers & lt_mask);
-        dig[k] = d;
+        dr[k] = d | ((before + (uint32_t)__popc(peers & lt_mask)) << 16);
         __syncwarp();
         if (valid && lane == __ffs(peers) - 1) s.wcnt[warp][d] = before + (uint32_t)__popc(peers);
         __syncwarp();
@@ -294,8 +294,9 @@ __global__ void __launch_bounds__(RT) k_os_pass(const K* __restrict__ kin,
     __syncthreads();
 #pragma unroll
     for (int k = 0; k < RI; ++k) {
-        if (dig[k] < RADIX) {
-            const uint32_t pos = s.tile_base[dig[k]] + s.wcnt[warp][dig[k]] + rnk[k];
+        const uint32_t dk = dr[k] & 0xffffu;
+        if (dk < RADIX) {
+            const uint32_t pos = s.tile_base[dk] + s.wcnt[warp][dk] + (dr[k] >> 16);
             s.keys[pos] = key[k];
             s.vals[pos] = val[k];
         }
@@ -332,11 +333,12 @@ spc_status radix_sort_impl(spc_context* ctx, K* keys, uint32_t* vals, K* keys_al
     uint32_t* stat = tctr + 32;
     SPC_CUDA(cudaMemsetAsync(hist, 0, words * 4, ctx->stream));
     const size_t smem = sizeof(SortSmem<K>);
-    static bool attr_set = false;
-    if (!attr_set) {
+    static std::atomic<unsigned long long> attr_devs{0};  // devices already set up
+    const unsigned long long bit = 1ull << (ctx->device & 63);
+    if (!(attr_devs.load() & bit)) {
         SPC_CUDA(cudaFuncSetAttribute(k_os_pass<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)smem));
-        attr_set = true;
+        attr_devs.fetch_or(bit);
     }
     note_bytes(ctx, (double)count * sizeof(K));  // every key read once
     SPC_LAUNCH(ctx, k_os_hist<K>, grid_for(count, RT, ctx->num_sms * 4), RT, 0, keys, count,

@@ -33,7 +33,7 @@ import numpy as np
 __all__ = [
     "Graph", "Batch", "csr_from_edges", "upper_edges", "tri_mesh_2d", "tet_mesh_3d", "rgg_3d",
     "mesh_batch", "config_graph", "CONFIGS", "path_graph", "cycle_graph", "complete_graph",
-    "random_graph", "subsample_batch",
+    "random_graph", "subsample_batch", "powerlaw_graph",
 ]
 
 
@@ -385,6 +385,9 @@ CONFIGS = {
                             ratio=8),
     "p2_tri512_f64": dict(kind="tri", nx=512, ny=512, jitter=0.3, weight="inv_len",
                           dtype="float64", seed=2, mode="halving", ratio=64),
+    # the c4 construction at 2^21 points (its arrays still larger than L2): profiler captures
+    "p4_rgg2m_f32": dict(kind="rgg", n=1 << 21, degree=12.0, dtype="float32", seed=4,
+                         mode="halving", ratio=256),
     # reduced versions (same construction, sizes the oracle handles in well under a second)
     "s2_tri256_f64": dict(kind="tri", nx=256, ny=256, jitter=0.3, weight="inv_len",
                           dtype="float64", seed=12, mode="halving", ratio=64),
@@ -478,3 +481,34 @@ def clique_ring(B: int, size: int, seed: int, dtype=np.float64) -> Graph:
     eu = np.concatenate([eu, ru]); ev = np.concatenate([ev, rv])
     w = np.concatenate([w, np.full(B, 0.05)]).astype(dtype)
     return csr_from_edges(B * size, eu, ev, w, name=f"cliques{B}x{size}")
+
+
+def powerlaw_graph(n: int, k: int, seed: int, weight: str = "float", dtype=np.float64) -> Graph:
+    """Preferential attachment: nodes k+1.. each join k distinct earlier nodes drawn with
+    probability proportional to degree (nodes 0..k start as a clique).  Heavy-tailed degrees,
+    the oldest (smallest) ids the largest: the shape of a social network such as the
+    ego-Facebook graph (n = 4039, mean degree about 44) at n = 4039, k = 22.
+    Weights as in random_graph."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    iu, iv = np.triu_indices(k + 1, 1)
+    us, vs = [iu.astype(np.int64)], [iv.astype(np.int64)]
+    # every edge end point once: drawing an entry uniformly is drawing a node by degree
+    ends = np.empty(2 * (len(iu) + (n - k - 1) * k), dtype=np.int64)
+    ne = 2 * len(iu)
+    ends[:len(iu)] = iu; ends[len(iu):ne] = iv
+    for x in range(k + 1, n):
+        chosen = set()
+        while len(chosen) < k:
+            chosen.add(int(ends[rng.integers(0, ne)]))
+        t = np.fromiter(sorted(chosen), dtype=np.int64, count=k)
+        us.append(t); vs.append(np.full(k, x, dtype=np.int64))
+        ends[ne:ne + k] = t; ends[ne + k:ne + 2 * k] = x
+        ne += 2 * k
+    u = np.concatenate(us); v = np.concatenate(vs)
+    if weight == "unit":
+        w = np.ones(u.shape[0], dtype=dtype)
+    elif weight == "int":
+        w = rng.integers(1, 10, size=u.shape[0]).astype(dtype)
+    else:
+        w = rng.uniform(0.1, 2.0, size=u.shape[0]).astype(dtype)
+    return csr_from_edges(n, u, v, w, name=f"powerlaw{n}k{k}")

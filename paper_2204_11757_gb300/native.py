@@ -81,6 +81,8 @@ SIGNATURES = {
     "spc_contract_forward": (ctypes.c_int, [P, P, P, I64, P, ctypes.c_int, P]),
     "spc_contract_backward": (ctypes.c_int, [P, P, I64, P, P, ctypes.c_int]),
     "spc_compose_emap": (ctypes.c_int, [P, P]),
+    "spc_pool_features": (ctypes.c_int, [P, I64, P, I64, I64, ctypes.c_int, P, P]),
+    "spc_pool_features_backward": (ctypes.c_int, [P, I64, P, I64, I64, ctypes.c_int, P, P]),
     "spc_sort_fitness_static": (ctypes.c_int, [I64, P, ctypes.c_int, P, P]),
     "spc_time_kernel": (ctypes.c_int, [P, ctypes.c_char_p]),
     "spc_kernel_time": (ctypes.c_int, [P, PI64, ctypes.POINTER(ctypes.c_double)]),

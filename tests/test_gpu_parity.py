@@ -224,6 +224,28 @@ def test_coarsen_levels_match_oracle(ctx, name):
     assert np.array_equal(em, O.compose_emaps(levels_ref))
 
 
+POWERLAW = [("f64", "float", np.float64), ("f32", "float", np.float32),
+            ("int", "int", np.int32), ("unit", "unit", np.int32)]
+
+
+@pytest.mark.parametrize("name,weight,dt", POWERLAW, ids=[p[0] for p in POWERLAW])
+def test_powerlaw_multilevel_bitexact(ctx, name, weight, dt):
+    """Heavy-tailed degrees shaped like a social network (n = 4039, mean degree 44, 46 rows
+    longer than 256 entries, hubs adjacent to hubs): every level of a coarsening to n/8 in three
+    halving levels, scores included, bit-exact with the oracle."""
+    g = I.powerlaw_graph(4039, 22, 7, weight, dt)
+    assert int(np.max(np.diff(g.rowptr))) > 256
+    api = _api()
+    levels_ref, total_ref = O.coarsen(g, 8, "halving")
+    L = len(levels_ref)
+    lift, nca, st = ctx.coarsen(api.CSR.from_graph(g), levels_ref[-1].target, levels=L)
+    assert nca == levels_ref[-1].n_c
+    assert np.array_equal(lift.cpu().numpy(), total_ref)
+    for lv, ref in zip(ctx.levels(), levels_ref):
+        assert np.array_equal(_bits(lv.score.cpu().numpy()), _bits(ref.f))
+        _check_level(lv, ref)
+
+
 def test_coarsen_host_buffers_match_device(ctx):
     api = _api()
     g, cfg = I.config_graph("s2_tri256_f64")
@@ -278,6 +300,31 @@ def test_backward_and_autograd(ctx):
     em = O.compose_emaps(levels_ref)
     ref = O.contract_backward(em, gvec.cpu().numpy())
     assert np.array_equal(w.grad.cpu().numpy(), ref)
+
+
+def test_rgg64k_contraction_finite_differences(ctx):
+    """The 2^16-point RGG coarsened to n/256 in 8 levels, its contraction differentiated with
+    the assignment held fixed: central differences of L(w) = <a(w), g> along random directions
+    match <grad, direction> from the backward kernel -- in binary64 (the same plan applied to
+    binary64 weights) to 1e-9, and in the configured binary32 to the rounding of the sums."""
+    api = _api()
+    g, cfg = I.config_graph("s4_rgg64k_f32")
+    levels_ref, _ = O.coarsen(g, cfg["ratio"], cfg["mode"])
+    ctx.coarsen(api.CSR.from_graph(g), levels_ref[-1].target, levels=len(levels_ref))
+    plan = api.ContractionPlan.from_levels(ctx, ctx.levels())
+    gen = torch.Generator("cuda").manual_seed(3)
+    for dt, h, rtol in ((torch.float64, 1e-3, 1e-9), (torch.float32, 5e-2, 1e-3)):
+        w = torch.from_numpy(g.w_und.astype(np.float64)).to("cuda", dt).requires_grad_(True)
+        a = api.contract_weights(w, plan)
+        gvec = torch.randn(a.shape[0], dtype=dt, device="cuda", generator=gen)
+        (a * gvec).sum().backward()
+        for _ in range(3):
+            d = torch.randint(0, 2, w.shape, device="cuda", generator=gen).to(dt) * 2 - 1
+            lp = (api.contract_weights(w.detach() + h * d, plan).double() * gvec.double()).sum()
+            lm = (api.contract_weights(w.detach() - h * d, plan).double() * gvec.double()).sum()
+            fd = ((lp - lm) / (2 * h)).item()
+            dot = (w.grad.double() * d.double()).sum().item()
+            assert abs(fd - dot) <= rtol * max(1.0, abs(dot)), (dt, fd, dot)
 
 
 def test_autograd_gradcheck_and_fd_float64(ctx):
@@ -338,6 +385,52 @@ def test_invalid_input_reported(ctx, kind, code):
     g = I.path_graph(5)
     lift, nc, st = ctx.coarsen(api.CSR.from_graph(g), 2)
     assert nc == 2
+
+
+def _balanced_asymmetric():
+    """Symmetric graph with a long row (node 599, 400 neighbours), then two defects that keep
+    the entry count even and every row sorted: an upper entry (450, 599) whose mirror the long
+    row lacks, and an upper entry (x, y) between short rows removed while its mirror (y, x)
+    stays."""
+    n = 600
+    rng = np.random.default_rng(21)
+    edges = {(int(a), 599) for a in range(400)}
+    while len(edges) < 1400:
+        a, b = sorted(rng.integers(0, 599, size=2))
+        if a != b:
+            edges.add((int(a), int(b)))
+    eu = np.array([e[0] for e in sorted(edges)]); ev = np.array([e[1] for e in sorted(edges)])
+    g = I.csr_from_edges(n, eu, ev, rng.uniform(0.5, 1.5, size=eu.shape[0]))
+    rows = [list(zip(g.col[g.rowptr[x]:g.rowptr[x + 1]], g.w[g.rowptr[x]:g.rowptr[x + 1]]))
+            for x in range(n)]
+    assert all(c != 599 for c, _ in rows[450])
+    rows[450].append((599, 1.0))
+    x = next(x for x in range(420, 598) if any(c > x and c != 599 for c, _ in rows[x]))
+    drop = next(c for c, _ in rows[x] if c > x and c != 599)
+    rows[x] = [(c, wv) for c, wv in rows[x] if c != drop]
+    rowptr = np.zeros(n + 1, dtype=np.int64)
+    rowptr[1:] = np.cumsum([len(r) for r in rows])
+    col = np.array([c for r in rows for c, _ in r], dtype=np.int32)
+    w = np.array([wv for r in rows for _, wv in r], dtype=np.float64)
+    assert rowptr[-1] == g.nnz
+    return rowptr, col, w
+
+
+def test_asymmetry_hidden_by_balanced_counts_is_reported(ctx):
+    """Equal numbers of entries above and below the diagonal, yet not symmetric: the missing
+    mirror of an entry pointing into a long row must be found (by the score kernels' lookup in
+    the long row), with and without graph replay."""
+    api = _api()
+    from paper_2204_11757_gb300 import native as N
+    rowptr, col, w = _balanced_asymmetric()
+    csr = api.CSR.from_numpy(rowptr, col, w)
+    for _ in range(3):
+        with pytest.raises(N.SpcError) as ei:
+            ctx.coarsen(csr, 50, levels=1)
+        assert ei.value.status == -2
+    with pytest.raises(N.SpcError) as ei:
+        ctx.score(csr)
+    assert ei.value.status == -2
 
 
 def test_invalid_arguments(ctx):
