@@ -229,8 +229,9 @@ def contract_backward(emap: np.ndarray, grad_a: np.ndarray) -> np.ndarray:
 
 def pool_features(lift: np.ndarray, n_c: int, x: np.ndarray) -> np.ndarray:
     """Mean of each super-node's member features (Definition 2's averaging over super-node
-    sizes, for node features): the members in ascending id, in chunks of 256; each chunk summed
-    left to right, the chunk sums added left to right; then one division by the member count.
+    sizes, for node features): the members in ascending id summed by a 256-ary tree (a list of
+    at most 256 items is summed left to right from 0; a longer one is replaced by the sums of
+    its consecutive chunks of 256, recursively); then one division by the member count.
     x is n-by-F (float32 or float64)."""
     x = np.ascontiguousarray(x)
     n, F = x.shape

@@ -31,8 +31,8 @@
  *                   member node id.
  *   orc_pool_features / orc_pool_backward  Definition 2's averaging over super-node sizes,
  *                   for node features: the mean over a super-node's members (ascending member
- *                   id, summed in chunks of 256 members, chunk sums left to right), and its
- *                   gradient with the assignment held fixed.
+ *                   id, summed by a 256-ary tree of left-to-right sums), and its gradient with
+ *                   the assignment held fixed.
  *   orc_contract    Definition 1: a_{v_c x} = sum over members v_i of w_{v_i x}, generalised to
  *                   pairs of super-nodes; edges inside one super-node leave the coarse graph and
  *                   their weight is reported as the super-node's self-mass (Definition 2 needs
@@ -460,14 +460,49 @@ int orc_contract_backward(int64_t m, const int32_t* emap, const void* grad_a, in
 /* Node-feature pooling onto the super-nodes and its gradient (a graph-pooling layer built on
  * the coarsening).  Definition 2's lift averages over the member pairs of two super-nodes
  * (divides by |u_c| |v_c|); its node counterpart is the mean over a super-node's members:
- *   xc[U][f] = (sum of x[v][f] over the members v of U) / |U|.
- * The paper does not use node features, so the summation order is this library's choice:
- * the members in ascending id, cut into chunks of ORC_POOL_CHUNK consecutive members; each
- * chunk summed left to right from 0, then the chunk sums added left to right from 0, all in
- * the feature type; then one IEEE division by |U| (converted to the feature type).  x is
- * n-by-F row-major, xc n_c-by-F.  A super-node without members gets 0.
+ *   xc[U][f] = S(x[v][f] for the members v of U in ascending v) / |U|.
+ * The paper does not use node features, so the summation order S is this library's choice, a
+ * 256-ary tree over the list:
+ *   S(list) = ((0 + t_0) + t_1) + ... + t_(k-1)        if k <= ORC_POOL_CHUNK,
+ *   S(list) = S([S(chunk_0), S(chunk_1), ...])          otherwise,
+ * where chunk_i are the consecutive groups of ORC_POOL_CHUNK items; every addition in the
+ * feature type; then one IEEE division by |U| (converted to the feature type).  x is n-by-F
+ * row-major, xc n_c-by-F.  A super-node without members gets 0.
  * Gradient (lift held fixed): grad_x[v][f] = grad_xc[c(v)][f] / |c(v)|.                    */
 #define ORC_POOL_CHUNK 256
+
+static double pool_tree_f64(double* t, int64_t k)
+{
+    while (k > ORC_POOL_CHUNK) {  /* replace the list by its chunk sums, in place */
+        int64_t m = 0;
+        for (int64_t c = 0; c < k; c += ORC_POOL_CHUNK) {
+            double s = 0.0;
+            for (int64_t i = c; i < k && i < c + ORC_POOL_CHUNK; ++i) s = s + t[i];
+            t[m++] = s;
+        }
+        k = m;
+    }
+    double s = 0.0;
+    for (int64_t i = 0; i < k; ++i) s = s + t[i];
+    return s;
+}
+
+static float pool_tree_f32(float* t, int64_t k)
+{
+    while (k > ORC_POOL_CHUNK) {
+        int64_t m = 0;
+        for (int64_t c = 0; c < k; c += ORC_POOL_CHUNK) {
+            float s = 0.0f;
+            for (int64_t i = c; i < k && i < c + ORC_POOL_CHUNK; ++i) s = s + t[i];
+            t[m++] = s;
+        }
+        k = m;
+    }
+    float s = 0.0f;
+    for (int64_t i = 0; i < k; ++i) s = s + t[i];
+    return s;
+}
+
 static int64_t* pool_counts(int64_t n, const int32_t* lift, int64_t n_c)
 {
     int64_t* cnt = (int64_t*)calloc((size_t)(n_c > 0 ? n_c : 1), sizeof(int64_t));
@@ -484,51 +519,36 @@ int orc_pool_features(int64_t n, const int32_t* lift, int64_t n_c, int64_t F, co
 {
     if (ftype != ORC_F32 && ftype != ORC_F64) return ORC_ERR_ARG;
     int64_t* cnt = pool_counts(n, lift, n_c);
-    int64_t* seen = (int64_t*)calloc((size_t)(n_c > 0 ? n_c : 1), sizeof(int64_t));
-    double* part = (double*)calloc((size_t)(n_c * F > 0 ? n_c * F : 1), sizeof(double));
-    if (!cnt || !seen || !part) { free(cnt); free(seen); free(part); return ORC_ERR_ARG; }
-    /* xc holds the running total over finished chunks, part the open chunk (kept in a double
-     * array, but every value in it is a value of the feature type) */
-    for (int64_t k = 0; k < n_c * F; ++k) {
-        if (ftype == ORC_F32) ((float*)xc_out)[k] = 0.0f;
-        else ((double*)xc_out)[k] = 0.0;
+    int64_t* start = (int64_t*)malloc((size_t)(n_c + 1) * sizeof(int64_t));
+    int64_t* fill = (int64_t*)calloc((size_t)(n_c > 0 ? n_c : 1), sizeof(int64_t));
+    int32_t* members = (int32_t*)malloc((size_t)(n > 0 ? n : 1) * sizeof(int32_t));
+    const size_t esz = ftype == ORC_F32 ? sizeof(float) : sizeof(double);
+    void* t = malloc((size_t)(n > 0 ? n : 1) * esz);
+    if (!cnt || !start || !fill || !members || !t) {
+        free(cnt); free(start); free(fill); free(members); free(t);
+        return ORC_ERR_ARG;
     }
-    /* ascending v: every super-node's members arrive in ascending id */
-    for (int64_t v = 0; v < n; ++v) {
-        const int64_t u = lift[v];
-        const int close_chunk = seen[u] > 0 && seen[u] % ORC_POOL_CHUNK == 0;
-        for (int64_t f = 0; f < F; ++f) {
-            const int64_t k = u * F + f;
-            if (ftype == ORC_F32) {
-                float* tot = (float*)xc_out + k;
-                float open = (float)part[k];
-                if (close_chunk) { *tot = *tot + open; open = 0.0f; }
-                open = open + ((const float*)x)[v * F + f];
-                part[k] = open;
-            } else {
-                double* tot = (double*)xc_out + k;
-                double open = part[k];
-                if (close_chunk) { *tot = *tot + open; open = 0.0; }
-                open = open + ((const double*)x)[v * F + f];
-                part[k] = open;
-            }
-        }
-        seen[u] += 1;
-    }
+    /* every super-node's members in ascending id */
+    start[0] = 0;
+    for (int64_t u = 0; u < n_c; ++u) start[u + 1] = start[u] + cnt[u];
+    for (int64_t v = 0; v < n; ++v) members[start[lift[v]] + fill[lift[v]]++] = (int32_t)v;
     for (int64_t u = 0; u < n_c; ++u) {
-        if (cnt[u] == 0) continue;
+        const int64_t k = cnt[u];
         for (int64_t f = 0; f < F; ++f) {
-            const int64_t k = u * F + f;
             if (ftype == ORC_F32) {
-                float* tot = (float*)xc_out + k;
-                *tot = (*tot + (float)part[k]) / (float)cnt[u];
+                float* tf = (float*)t;
+                for (int64_t i = 0; i < k; ++i)
+                    tf[i] = ((const float*)x)[members[start[u] + i] * F + f];
+                ((float*)xc_out)[u * F + f] = k ? pool_tree_f32(tf, k) / (float)k : 0.0f;
             } else {
-                double* tot = (double*)xc_out + k;
-                *tot = (*tot + part[k]) / (double)cnt[u];
+                double* td = (double*)t;
+                for (int64_t i = 0; i < k; ++i)
+                    td[i] = ((const double*)x)[members[start[u] + i] * F + f];
+                ((double*)xc_out)[u * F + f] = k ? pool_tree_f64(td, k) / (double)k : 0.0;
             }
         }
     }
-    free(cnt); free(seen); free(part);
+    free(cnt); free(start); free(fill); free(members); free(t);
     return ORC_OK;
 }
 

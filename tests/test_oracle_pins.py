@@ -564,7 +564,7 @@ def test_pool_backward_is_the_adjoint():
     assert np.array_equal((xc * sizes[:, None]).sum(0), x.sum(0))
 
 
-def test_pool_features_chunked_order():
+def test_pool_features_tree_order():
     """258 members: 1e16, 255 zeros, 1, 1.  Chunks of 256: (1e16) + (1 + 1) = 1e16 + 2 exactly,
     so the mean is (1e16 + 2) / 258 correctly rounded; a plain left-to-right sum would lose both
     ones (1e16 + 1 rounds to 1e16) and give 1e16 / 258."""
@@ -578,3 +578,20 @@ def test_pool_features_chunked_order():
     xc = O.pool_features(lift, 2, x)
     assert xc[1, 0] == float(Fraction(10 ** 16 + 2, 258))
     assert xc[1, 0] != float(Fraction(10 ** 16, 258))
+
+
+def test_pool_features_three_tree_levels():
+    """258 * 256 members: 1e16 first, a 1 at the start of chunks 256 and 257, zeros elsewhere.
+    The 258 chunk sums exceed 256, so they are summed in two groups: (1e16 + 0 ...) and
+    (1 + 1), then 1e16 + 2 exactly.  Adding the 258 chunk sums left to right instead would
+    round both ones away."""
+    L = 258 * 256
+    lift = np.ones(L + 5, dtype=np.int32)
+    lift[:5] = 0
+    x = np.zeros((L + 5, 1))
+    x[5, 0] = 1e16
+    x[5 + 256 * 256, 0] = 1.0
+    x[5 + 257 * 256, 0] = 1.0
+    xc = O.pool_features(lift, 2, x)
+    assert xc[1, 0] == float(Fraction(10 ** 16 + 2, L))
+    assert xc[0, 0] == 0.0
