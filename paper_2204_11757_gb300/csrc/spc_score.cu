@@ -14,11 +14,18 @@ namespace spc {
 // Markstein's theorem (IBM J. Res. Dev. 34(1), 1990; also Muller et al., Handbook of
 // Floating-Point Arithmetic, ch. 4): if y is within half an ulp of 1/d and q0 within one ulp of
 // w/d, then r = w - d*q0 is exact (one FMA) and RN(q0 + r*y) = RN(w/d).  q0 = RN(w*y) is within
-// one ulp.  Outside the range where no intermediate can underflow or overflow the IEEE division
-// is used directly.
-__device__ __forceinline__ double div_row(double w, double d, double y) {
+// one ulp.  With w and d in [2^-400, 2^400) every intermediate is a normal number (q0 within
+// (2^-800, 2^800), the residual a multiple of about 2^-505 or 0); outside that range the IEEE
+// division is used directly.  The range tests read the exponent fields with integer
+// instructions: GB300's FP64 pipe is narrow, and the divisions of a level are bound by it.
+__device__ __forceinline__ bool mid_range(double v) {
+    const unsigned e = ((unsigned)__double2hiint(v) >> 20) & 0x7ffu;
+    return e - (1023u - 400u) < 800u;
+}
+
+__device__ __forceinline__ double div_row(double w, double d, double y, bool d_mid) {
+    if (!(d_mid && mid_range(w))) return __ddiv_rn(w, d);
     const double q0 = __dmul_rn(w, y);
-    if (!(q0 > 0x1p-960 && q0 < 0x1p960 && d > 0x1p-960 && d < 0x1p960)) return __ddiv_rn(w, d);
     const double r = __fma_rn(-d, q0, w);
     return __fma_rn(r, y, q0);
 }
@@ -39,7 +46,11 @@ template <> struct Tr<float> {
     using Key = unsigned int;
     __device__ static Acc add(Acc a, float w) { return __fadd_rn(a, w); }
     __device__ static P div(float w, Acc d) { return __fdiv_rn(w, d); }
-    __device__ static bool ok(float w) { return w > 0.f && !isinf(w); }
+    // finite and > 0, tested on the bits (no floating-point compare)
+    __device__ static bool ok(float w) {
+        const int b = __float_as_int(w);
+        return b > 0 && b < 0x7f800000;
+    }
     __device__ static uint64_t bits(float w) { return __float_as_uint(w); }
 };
 template <> struct Tr<double> {
@@ -48,7 +59,11 @@ template <> struct Tr<double> {
     using Key = unsigned long long;
     __device__ static Acc add(Acc a, double w) { return __dadd_rn(a, w); }
     __device__ static P div(double w, Acc d) { return __ddiv_rn(w, d); }
-    __device__ static bool ok(double w) { return w > 0.0 && !isinf(w); }
+    // finite and > 0, tested on the bits (no FP64 compare)
+    __device__ static bool ok(double w) {
+        const long long b = __double_as_longlong(w);
+        return b > 0 && b < 0x7ff0000000000000ll;
+    }
     __device__ static uint64_t bits(double w) { return (uint64_t)__double_as_longlong(w); }
 };
 
@@ -271,16 +286,18 @@ k_rows_edges(int64_t n, const int64_t* __restrict__ rowptr, const int32_t* __res
         const int64_t ubase = (int64_t)up_ptr[x] - (r0 + nlow[x]);
         // binary64 rows: one correctly rounded reciprocal per row, Markstein per entry
         double dd = 0.0, rcp = 0.0;
+        bool d_mid = false;
         if constexpr (!std::is_same<WT, float>::value) {
             dd = (double)d;
-            rcp = __drcp_rn(dd);
+            d_mid = mid_range(dd);
+            rcp = d_mid ? __drcp_rn(dd) : 0.0;
         }
         uint32_t bits = 0;
         for (int64_t j = r0; j < r1; ++j) {
             const int32_t y = col[j];
             const WT wj = w[j];
             if constexpr (std::is_same<WT, float>::value) p[j] = Tr<WT>::div(wj, d);
-            else p[j] = div_row((double)wj, dd, rcp);
+            else p[j] = div_row((double)wj, dd, rcp, d_mid);
             if (validate) {
                 int64_t lo = rowptr[y], hi = rowptr[y + 1];
                 while (lo < hi) {
