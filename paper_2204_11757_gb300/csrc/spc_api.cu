@@ -91,6 +91,31 @@ cudaError_t record_event(spc_context* ctx, cudaEvent_t ev) {
     return cudaEventRecord(ev, ctx->stream);
 }
 
+SideBranch::SideBranch(spc_context* ctx) : ctx_(ctx), main_(ctx->stream) {
+    cudaError_t e = cudaSuccess;
+    if (!ctx->side_stream) e = cudaStreamCreateWithFlags(&ctx->side_stream, cudaStreamNonBlocking);
+    for (int i = 0; i < 2 && e == cudaSuccess; ++i)
+        if (!ctx->branch_ev[i]) e = cudaEventCreateWithFlags(&ctx->branch_ev[i], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventRecord(ctx->branch_ev[0], main_);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->side_stream, ctx->branch_ev[0], 0);
+    if (e != cudaSuccess) {
+        set_last_cuda_error(e, "SideBranch", __FILE__, __LINE__);
+        st_ = SPC_ERR_CUDA;
+        return;
+    }
+    forked_ = true;
+    ctx->stream = ctx->side_stream;
+}
+
+void SideBranch::leave() { ctx_->stream = main_; }
+
+SideBranch::~SideBranch() {
+    ctx_->stream = main_;
+    if (!forked_) return;
+    if (cudaEventRecord(ctx_->branch_ev[1], ctx_->side_stream) == cudaSuccess)
+        cudaStreamWaitEvent(main_, ctx_->branch_ev[1], 0);
+}
+
 unsigned long long* op_counter(spc_context* ctx, const char* kernel_name, int slot) {
     if (!ctx->d_ops || !timed(ctx->timer, kernel_name)) return nullptr;
     return ctx->d_ops + slot;
@@ -533,13 +558,33 @@ __device__ __forceinline__ unsigned long long mix64(unsigned long long x) {
     return x ^ (x >> 31);
 }
 
-// position-sensitive checksum of `bytes` bytes (a multiple of 4), added into *acc
-__global__ void k_checksum(const uint32_t* __restrict__ w, int64_t words, unsigned long long salt,
+constexpr unsigned long long kPosMul = 0xD6E8FEB86659FD93ull;  // odd: positions stay distinct
+
+// position-sensitive sum of mixed 8-byte words (4-byte words when the array is not 8-byte
+// aligned or sized); four loads in flight per thread
+__global__ void k_checksum(const void* __restrict__ p, int64_t bytes, unsigned long long salt,
                            unsigned long long* acc) {
     unsigned long long s = 0;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < words;
-         i += (int64_t)gridDim.x * blockDim.x)
-        s += mix64(((unsigned long long)w[i] << 32) ^ (unsigned long long)i ^ salt);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (((uintptr_t)p & 7) == 0 && (bytes & 7) == 0) {
+        const unsigned long long* w = static_cast<const unsigned long long*>(p);
+        const int64_t words = bytes >> 3;
+        int64_t i = t0;
+        for (; i + 3 * stride < words; i += 4 * stride) {
+            const unsigned long long a = w[i], b = w[i + stride], c = w[i + 2 * stride],
+                                     d = w[i + 3 * stride];
+            s += mix64(a ^ (kPosMul * (unsigned long long)i + salt));
+            s += mix64(b ^ (kPosMul * (unsigned long long)(i + stride) + salt));
+            s += mix64(c ^ (kPosMul * (unsigned long long)(i + 2 * stride) + salt));
+            s += mix64(d ^ (kPosMul * (unsigned long long)(i + 3 * stride) + salt));
+        }
+        for (; i < words; i += stride) s += mix64(w[i] ^ (kPosMul * (unsigned long long)i + salt));
+    } else {
+        const uint32_t* w = static_cast<const uint32_t*>(p);
+        for (int64_t i = t0; i < (bytes >> 2); i += stride)
+            s += mix64((unsigned long long)w[i] ^ (kPosMul * (unsigned long long)i + salt + 1ull));
+    }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if ((threadIdx.x & 31) == 0 && s) atomicAdd(acc, s);
@@ -550,7 +595,7 @@ static spc_status input_checksum(spc_context* ctx, const GraphView& v, const Sch
     Replay& R = ctx->replay;
     if (!R.d_hash) SPC_CUDA(cudaMalloc(&R.d_hash, 256));
     SPC_CUDA(cudaMemsetAsync(R.d_hash, 0, 8, ctx->stream));
-    const int maxb = ctx->num_sms * 4;
+    const int maxb = ctx->num_sms * 8;
     struct Arr { const void* p; int64_t bytes; unsigned long long salt; };
     const Arr arrs[4] = {{v.rowptr, (v.n + 1) * 8, 0x1111ull << 40},
                          {v.col, v.nnz * 4, 0x2222ull << 40},
@@ -558,9 +603,8 @@ static spc_status input_checksum(spc_context* ctx, const GraphView& v, const Sch
                          {S.d_graph_ptr, S.d_graph_ptr ? (S.B + 1) * 8 : 0, 0x4444ull << 40}};
     for (const Arr& ar : arrs) {
         if (!ar.p || ar.bytes <= 0) continue;
-        const int64_t words = ar.bytes / 4;
-        SPC_LAUNCH(ctx, k_checksum, grid_for(words, kThreads, maxb), kThreads, 0,
-                   static_cast<const uint32_t*>(ar.p), words, ar.salt, R.d_hash);
+        SPC_LAUNCH(ctx, k_checksum, grid_for(ar.bytes / 32, kThreads, maxb), kThreads, 0, ar.p,
+                   ar.bytes, ar.salt, R.d_hash);
     }
     SPC_CUDA(cudaMemcpyAsync(ctx->h_scalars + 24, R.d_hash, 8, cudaMemcpyDeviceToHost,
                              ctx->stream));
@@ -799,6 +843,9 @@ void spc_context_destroy(spc_context* ctx) {
     if (ctx->replay.d_hash) cudaFree(ctx->replay.d_hash);
     if (ctx->d_ops) cudaFree(ctx->d_ops);
     if (ctx->replay.cap_stream) cudaStreamDestroy(ctx->replay.cap_stream);
+    if (ctx->side_stream) cudaStreamDestroy(ctx->side_stream);
+    for (auto ev : ctx->branch_ev)
+        if (ev) cudaEventDestroy(ev);
     for (auto ev : ctx->tune_ev)
         if (ev) cudaEventDestroy(ev);
     cudaFree(ctx->d_status);

@@ -198,16 +198,28 @@ k_gather_long_terms(const int32_t* __restrict__ long_list, const int32_t* __rest
     }
 }
 
+// atomicAdd(cnt + key, 1) by every active lane (all 32 lanes call it): lanes with the same
+// key (the edges of a hub super-node) add their count with one atomic
+__device__ __forceinline__ void warp_count(int32_t* cnt, int32_t key, bool act) {
+    const unsigned peers = __match_any_sync(0xffffffffu, act ? key : -1);
+    if (act && (int)(threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(cnt + key, __popc(peers));
+}
+
 __global__ void __launch_bounds__(kThreads)
 k_degree_counts(int64_t m_c, const int32_t* __restrict__ cU, const int32_t* __restrict__ cV,
                 int32_t* up_deg, int32_t* low_deg, uint32_t* __restrict__ tkey,
                 uint32_t* __restrict__ tval) {
-    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < m_c;
-         k += (int64_t)gridDim.x * blockDim.x) {
-        atomicAdd(up_deg + cU[k], 1);
-        atomicAdd(low_deg + cV[k], 1);
-        tkey[k] = (uint32_t)cV[k];
-        tval[k] = (uint32_t)k;
+    for (int64_t k0 = (int64_t)blockIdx.x * blockDim.x; k0 < m_c;
+         k0 += (int64_t)gridDim.x * blockDim.x) {  // uniform per warp
+        const int64_t k = k0 + threadIdx.x;
+        const bool act = k < m_c;
+        const int32_t u = act ? cU[k] : 0, v = act ? cV[k] : 0;
+        warp_count(up_deg, u, act);
+        warp_count(low_deg, v, act);
+        if (act) {
+            tkey[k] = (uint32_t)v;
+            tval[k] = (uint32_t)k;
+        }
     }
 }
 

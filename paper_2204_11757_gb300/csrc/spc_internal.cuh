@@ -174,9 +174,31 @@ struct spc_context {
     // arithmetic counts of the timed score launches: [0..1] edge tiles (adds, subtractions),
     // [2..3] warp per row
     unsigned long long* d_ops = nullptr;
+    // second stream for independent work inside a level (parallel branches of a captured graph)
+    cudaStream_t side_stream = nullptr;
+    cudaEvent_t branch_ev[2] = {nullptr, nullptr};
 };
 
 namespace spc {
+
+// Work that does not depend on what the main stream does next runs on the context's second
+// stream: the constructor makes that stream wait for everything enqueued so far and sends the
+// following launches there; leave() sends launches back to the main stream; the destructor
+// makes the main stream wait for the side's work (also on an early error return).  Inside a
+// stream capture this forms two parallel branches of the graph.  Scratch that both streams
+// could use at once (the scan and sort temporaries) is used by one branch only.
+class SideBranch {
+public:
+    explicit SideBranch(spc_context* ctx);
+    ~SideBranch();
+    spc_status status() const { return st_; }
+    void leave();
+private:
+    spc_context* ctx_;
+    cudaStream_t main_;
+    spc_status st_ = SPC_OK;
+    bool forked_ = false;
+};
 
 // allocation helpers (allocator callback or cudaMalloc)
 spc_status ensure(spc_context* ctx, Buf& b, size_t bytes);

@@ -6,6 +6,8 @@
 // Every sum here runs sequentially in ascending column order with IEEE round-to-nearest adds
 // (__dadd_rn / __fadd_rn, no FMA), and p = w / d is one IEEE division per stored entry, so
 // the results are the same bits on every run and every schedule.
+#include <memory>
+
 #include "spc_seqsum.cuh"
 
 namespace spc {
@@ -775,13 +777,6 @@ static spc_status score_typed(spc_context* ctx, GraphView& g, bool validate, voi
     SPC_TRY(check_status(ctx));
     if (2 * m != nnz) return SPC_ERR_NOT_SYMMETRIC;
     g.m = m;
-    if (n_long > 0 && fp) {  // exact degrees of the long rows from per-binade tables
-        SPC_TRY(seqtab_build(ctx, g.w, std::is_same<WT, float>::value, n_long,
-                             W.lr_base.as<int64_t>(), W.lr_len.as<int64_t>(), true, W.tab_w));
-        SPC_TRY(seqtab_full_sums(ctx, g.w, std::is_same<WT, float>::value,
-                                 W.lr_base.as<int64_t>(), W.lr_len.as<int64_t>(), W.tab_w,
-                                 W.lr_idx.as<int64_t>(), W.deg.p));
-    }
     // rowptr, columns, weights, degrees and row counts read once; p and the undirected edge
     // list written once (no model on levels with long rows: another kernel takes their part)
     if (n_long == 0)
@@ -792,17 +787,33 @@ static spc_status score_typed(spc_context* ctx, GraphView& g, bool validate, voi
     const int vflag = validate ? 1 : 0;
     const int wsize = (int)sizeof(WT);
     const bool mirror_here = validate && (score == nullptr || m == 0);
-    SPC_LAUNCH(ctx, k_rows_edges<WT>, gb, kThreads, 0, n, g.rowptr, g.col,
-               static_cast<const WT*>(g.w), mirror_here ? 1 : 0, W.deg.as<Acc>(),
-               W.first_up.as<int32_t>(), W.up_ptr.as<int32_t>(), W.p.as<P>(),
-               W.eu.as<int32_t>(), W.ev.as<int32_t>(), W.w_und.as<WT>(), status);
-    if (n_long > 0) {
-        SPC_LAUNCH(ctx, k_long_rows_edges<WT>, maxb, kThreads, 0, g.rowptr, g.col,
-                   static_cast<const WT*>(g.w), validate ? 1 : 0, W.deg.as<Acc>(),
-                   W.first_up.as<int32_t>(), W.up_ptr.as<int32_t>(), long_rows, long_count,
-                   W.lr_eoff.as<int64_t>(), W.p.as<P>(), W.eu.as<int32_t>(),
-                   W.ev.as<int32_t>(), W.w_und.as<WT>(), status);
-    }
+    {
+        // long rows (exact degrees from per-binade tables, then p and their edges) on the
+        // second stream while the short rows run here
+        std::unique_ptr<SideBranch> side;
+        if (n_long > 0) {
+            side.reset(new SideBranch(ctx));
+            SPC_TRY(side->status());
+            if (fp) {
+                SPC_TRY(seqtab_build(ctx, g.w, std::is_same<WT, float>::value, n_long,
+                                     W.lr_base.as<int64_t>(), W.lr_len.as<int64_t>(), true,
+                                     W.tab_w));
+                SPC_TRY(seqtab_full_sums(ctx, g.w, std::is_same<WT, float>::value,
+                                         W.lr_base.as<int64_t>(), W.lr_len.as<int64_t>(),
+                                         W.tab_w, W.lr_idx.as<int64_t>(), W.deg.p));
+            }
+            SPC_LAUNCH(ctx, k_long_rows_edges<WT>, maxb, kThreads, 0, g.rowptr, g.col,
+                       static_cast<const WT*>(g.w), validate ? 1 : 0, W.deg.as<Acc>(),
+                       W.first_up.as<int32_t>(), W.up_ptr.as<int32_t>(), long_rows, long_count,
+                       W.lr_eoff.as<int64_t>(), W.p.as<P>(), W.eu.as<int32_t>(),
+                       W.ev.as<int32_t>(), W.w_und.as<WT>(), status);
+            side->leave();
+        }
+        SPC_LAUNCH(ctx, k_rows_edges<WT>, gb, kThreads, 0, n, g.rowptr, g.col,
+                   static_cast<const WT*>(g.w), mirror_here ? 1 : 0, W.deg.as<Acc>(),
+                   W.first_up.as<int32_t>(), W.up_ptr.as<int32_t>(), W.p.as<P>(),
+                   W.eu.as<int32_t>(), W.ev.as<int32_t>(), W.w_und.as<WT>(), status);
+    }  // the main stream waits for the long rows here
     if (score == nullptr || m == 0) {
         if (validate) SPC_TRY(check_status(ctx));
         return SPC_OK;
@@ -841,6 +852,17 @@ static spc_status score_typed(spc_context* ctx, GraphView& g, bool validate, voi
     // rowptr, every stored column and p read once, every score written once (no model on
     // levels with long rows: the hub kernels take their edges)
     const double score_bytes = n_long == 0 ? 8.0 * (n + 1) + nnz * (4 + s_p) + m * s_key : 0.0;
+    // hub edges: per-binade tables of every hub row's normalised weights (on the second
+    // stream, while the other edges are scored here), then one thread per hub entry (one warp
+    // per entry whose other row is long)
+    std::unique_ptr<SideBranch> side;
+    if (n_long > 0) {
+        side.reset(new SideBranch(ctx));
+        SPC_TRY(side->status());
+        SPC_TRY(seqtab_build(ctx, W.p.p, std::is_same<P, float>::value, n_long,
+                             W.lr_base.as<int64_t>(), W.lr_len.as<int64_t>(), false, W.tab_p));
+        side->leave();
+    }
     if (schedule == 2) {
         const int warps_per_block = kThreads / 32;
         note_bytes(ctx, score_bytes);
@@ -857,10 +879,7 @@ static spc_status score_typed(spc_context* ctx, GraphView& g, bool validate, voi
                    op_counter(ctx, "(k_score_edges<P, Key>)", 0));
     }
     if (n_long == 0) return validate ? check_status(ctx) : SPC_OK;
-    // hub edges: per-binade tables of every hub row's normalised weights, then one thread per
-    // hub entry (one warp per entry whose other row is long)
-    SPC_TRY(seqtab_build(ctx, W.p.p, std::is_same<P, float>::value, n_long,
-                         W.lr_base.as<int64_t>(), W.lr_len.as<int64_t>(), false, W.tab_p));
+    side.reset();  // the main stream waits for the tables
     const SeqTabView tv = seqtab_view(W.tab_p, W.lr_base.as<int64_t>(), W.lr_len.as<int64_t>());
     SPC_CUDA(cudaMemsetAsync(heavy_count, 0, sizeof(int32_t), ctx->stream));
     SPC_LAUNCH(ctx, (k_score_hub<P, Key>), maxb, kThreads, 0, g.rowptr, g.col, W.p.as<P>(),
