@@ -12,6 +12,8 @@
 // coarse-edge order), which leaves every row sorted.
 #include <type_traits>
 
+#include <memory>
+
 #include "spc_seqsum.cuh"
 
 namespace spc {
@@ -280,8 +282,9 @@ template <class WT, class Out>
 spc_status long_segment_sums(spc_context* ctx, const int32_t* start, const uint32_t* idx,
                              const uint32_t* key, const WT* w_und, Out* out) {
     Work& W = ctx->work;
-    int32_t* long_list = W.long_segs.as<int32_t>();
-    int32_t* long_cnt = W.counters.as<int32_t>() + 9;
+    const bool side = on_side(ctx);
+    int32_t* long_list = (side ? W.long_segs_side : W.long_segs).as<int32_t>();
+    int32_t* long_cnt = W.counters.as<int32_t>() + (side ? 11 : 9);
     if constexpr (std::is_same<WT, int32_t>::value) {
         SPC_LAUNCH(ctx, (k_segsum_long<WT, Out>), ctx->num_sms * 2, kThreads, 0, start, idx, key,
                    w_und, out, long_list, long_cnt, ctx->d_status);
@@ -290,21 +293,23 @@ spc_status long_segment_sums(spc_context* ctx, const int32_t* start, const uint3
         int64_t nlong = 0;
         SPC_TRY(read_i32(ctx, long_cnt, &nlong));
         if (nlong == 0) return SPC_OK;
-        int64_t* len = W.seg_len.as<int64_t>();
-        int64_t* base = W.seg_base.as<int64_t>();
-        int64_t* oidx = W.seg_idx.as<int64_t>();
+        int64_t* len = (side ? W.seg_len_side : W.seg_len).as<int64_t>();
+        int64_t* base = (side ? W.seg_base_side : W.seg_base).as<int64_t>();
+        int64_t* oidx = (side ? W.seg_idx_side : W.seg_idx).as<int64_t>();
         SPC_LAUNCH(ctx, k_long_seg_prep, grid_for(nlong, kThreads, ctx->num_sms * 8), kThreads, 0,
                    long_list, long_cnt, start, key, len, oidx);
         SPC_TRY(scan_i64_i64(ctx, len, base, nlong));
         int64_t total = 0;
         SPC_TRY(read_i64(ctx, base + nlong, &total));
-        SPC_TRY(ensure(ctx, W.seg_terms, (size_t)(total + 1) * sizeof(WT)));
-        WT* terms = W.seg_terms.as<WT>();
+        Buf& tbuf = side ? W.seg_terms_side : W.seg_terms;
+        SPC_TRY(ensure(ctx, tbuf, (size_t)(total + 1) * sizeof(WT)));
+        WT* terms = tbuf.as<WT>();
         SPC_LAUNCH(ctx, k_gather_long_terms<WT>, grid_for(total, kThreads, ctx->num_sms * 8),
                    kThreads, 0, long_list, long_cnt, start, idx, w_und, base, terms);
         const bool f32 = std::is_same<WT, float>::value;
-        SPC_TRY(seqtab_build(ctx, terms, f32, nlong, base, len, true, W.tab_s));
-        SPC_TRY(seqtab_full_sums(ctx, terms, f32, base, len, W.tab_s, oidx, out));
+        SeqTabBufs& tab = side ? W.tab_s_side : W.tab_s;
+        SPC_TRY(seqtab_build(ctx, terms, f32, nlong, base, len, true, tab));
+        SPC_TRY(seqtab_full_sums(ctx, terms, f32, base, len, tab, oidx, out));
         return SPC_OK;
     }
 }
@@ -347,14 +352,22 @@ spc_status contract_typed(spc_context* ctx, const GraphView& g, const int32_t* l
     }
     const int64_t m_inter = cnts[0];
     const int64_t m_intra = cnts[1];
+    // The self-mass (intra edges) and the coarse edges are independent from here: the
+    // self-mass runs on the second stream with its own temporaries, the coarse edges here.
+    SPC_TRY(ensure(ctx, W.long_segs_side, (size_t)(m + 1) * 4));
+    SPC_TRY(ensure(ctx, W.seg_len_side, (size_t)(m + 1) * 8));
+    SPC_TRY(ensure(ctx, W.seg_base_side, (size_t)(m + 2) * 8));
+    SPC_TRY(ensure(ctx, W.seg_idx_side, (size_t)(m + 1) * 8));
+    std::unique_ptr<SideBranch> side(new SideBranch(ctx));
+    SPC_TRY(side->status());
     // self-mass: runs of equal super-node ids after a stable sort, summed in eid order
     Acc* self_mass = lv.self_mass.as<Acc>();
     SPC_CUDA(cudaMemsetAsync(self_mass, 0, (size_t)n_c * sizeof(Acc), ctx->stream));
     SPC_TRY(radix_sort_u32(ctx, ikey, ival, W.i_key2.as<uint32_t>(), W.i_val2.as<uint32_t>(),
                            m_intra, nb));
-    int32_t* long_list = W.long_segs.as<int32_t>();
-    int32_t* long_cnt = W.counters.as<int32_t>() + 9;
     if (m_intra > 0) {
+        int32_t* long_list = W.long_segs_side.as<int32_t>();
+        int32_t* long_cnt = W.counters.as<int32_t>() + 11;
         uint8_t* ihead = W.c_flag.as<uint8_t>() + (m + 1);  // intra flags are consumed
         int32_t* ihpos = W.c_head.as<int32_t>();
         int32_t* istart = W.i_key2.as<int32_t>();           // sort scratch is free again
@@ -371,7 +384,10 @@ spc_status contract_typed(spc_context* ctx, const GraphView& g, const int32_t* l
         SPC_TRY((long_segment_sums<WT, Acc>(ctx, istart, ival, ikey, W.w_und.as<WT>(),
                                              self_mass)));
     }
+    side->leave();
     // coarse edges
+    int32_t* long_list = W.long_segs.as<int32_t>();
+    int32_t* long_cnt = W.counters.as<int32_t>() + 9;
     SPC_TRY(radix_sort_u64(ctx, ckey, cval, W.c_key2.as<uint64_t>(), W.c_val2.as<uint32_t>(),
                            m_inter, 2 * nb));
     uint8_t* head = W.c_flag.as<uint8_t>();  // flags are consumed; reuse as heads

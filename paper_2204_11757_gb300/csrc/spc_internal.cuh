@@ -94,6 +94,10 @@ struct Work {
     Buf stage_rowptr, stage_col, stage_w, stage_lift, stage_gptr;  // host staging
     Buf pool_key, pool_val, pool_key2, pool_val2, pool_cnt, pool_off;  // feature pooling
     Buf pool_nch, pool_choff, pool_owner, pool_part;
+    // the same temporaries for work running on the second stream (SideBranch)
+    Buf sort_hist_side, scan_tmp_side, long_segs_side;
+    Buf seg_base_side, seg_len_side, seg_idx_side, seg_terms_side;
+    SeqTabBufs tab_s_side;
     Buf lift_final;                                             // composed lift of a call
 };
 
@@ -187,6 +191,11 @@ namespace spc {
 // makes the main stream wait for the side's work (also on an early error return).  Inside a
 // stream capture this forms two parallel branches of the graph.  Scratch that both streams
 // could use at once (the scan and sort temporaries) is used by one branch only.
+// true while launches go to the second stream: such work uses the *_side temporaries
+inline bool on_side(const spc_context* ctx) {
+    return ctx->side_stream != nullptr && ctx->stream == ctx->side_stream;
+}
+
 class SideBranch {
 public:
     explicit SideBranch(spc_context* ctx);

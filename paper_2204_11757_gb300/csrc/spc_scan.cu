@@ -270,8 +270,9 @@ spc_status scan_impl(spc_context* ctx, const In* in, Out* out, int64_t n) {
     }
     const int64_t nt = (n + STILE - 1) / STILE;
     const size_t need = (size_t)(nt + 1) * 8;
-    SPC_TRY(ensure(ctx, ctx->work.scan_tmp, need));
-    unsigned long long* status = ctx->work.scan_tmp.as<unsigned long long>();
+    Buf& tmp = on_side(ctx) ? ctx->work.scan_tmp_side : ctx->work.scan_tmp;
+    SPC_TRY(ensure(ctx, tmp, need));
+    unsigned long long* status = tmp.as<unsigned long long>();
     uint32_t* tile_ctr = reinterpret_cast<uint32_t*>(status + nt);
     SPC_CUDA(cudaMemsetAsync(status, 0, need, ctx->stream));
     note_bytes(ctx, (double)n * (sizeof(In) + sizeof(Out)));  // input read, output written

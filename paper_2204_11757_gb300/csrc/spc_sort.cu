@@ -326,8 +326,9 @@ spc_status radix_sort_impl(spc_context* ctx, K* keys, uint32_t* vals, K* keys_al
     if (npass > kMaxPasses || count >= (int64_t)kValMask) return SPC_ERR_TOO_LARGE;
     // hist [npass][256] | base [npass][256] | tile counters [npass] | status [npass][tiles][256]
     const size_t words = (size_t)npass * RADIX * 2 + 32 + (size_t)npass * tiles * RADIX;
-    SPC_TRY(ensure(ctx, ctx->work.sort_hist, words * 4));
-    uint32_t* hist = ctx->work.sort_hist.as<uint32_t>();
+    Buf& hbuf = on_side(ctx) ? ctx->work.sort_hist_side : ctx->work.sort_hist;
+    SPC_TRY(ensure(ctx, hbuf, words * 4));
+    uint32_t* hist = hbuf.as<uint32_t>();
     uint32_t* base = hist + (size_t)npass * RADIX;
     uint32_t* tctr = base + (size_t)npass * RADIX;
     uint32_t* stat = tctr + 32;
