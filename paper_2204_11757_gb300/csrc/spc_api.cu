@@ -161,22 +161,37 @@ static void timer_add(Timer& t, const char* name, double ms, double bytes) {
     t.per_kernel.push_back({std::string(name), 1, ms, bytes});
 }
 
-__global__ void k_expect(const void* dev, int bytes, long long want, int32_t* mismatch) {
-    if (threadIdx.x != 0) return;
-    const long long got = bytes == 8 ? *static_cast<const long long*>(dev)
-                                     : (long long)*static_cast<const int32_t*>(dev);
-    if (got != want) *mismatch = 1;
+// in-graph check of up to four logged values (one launch for all values a read took)
+struct Expect {
+    const void* dev[4];
+    long long want[4];
+    int bytes[4];
+    int count;
+};
+
+__global__ void k_expect(Expect x, int32_t* mismatch) {
+    const int i = threadIdx.x;
+    if (i >= x.count) return;
+    const long long got = x.bytes[i] == 8 ? *static_cast<const long long*>(x.dev[i])
+                                          : (long long)*static_cast<const int32_t*>(x.dev[i]);
+    if (got != x.want[i]) *mismatch = 1;
 }
 
 spc_status read_vals(spc_context* ctx, int count, const void* const* dev, const int* bytes,
                      int64_t* out) {
     Replay& R = ctx->replay;
     if (R.mode == Replay::kCapture) {
-        for (int i = 0; i < count; ++i) {
-            if (R.pos >= R.log.size()) return SPC_ERR_CUDA;  // control flow left the record
-            out[i] = R.log[R.pos++];
-            SPC_LAUNCH(ctx, k_expect, 1, 32, 0, dev[i], bytes[i], (long long)out[i],
-                       R.d_mismatch);
+        for (int i0 = 0; i0 < count; i0 += 4) {
+            Expect x{};
+            x.count = count - i0 < 4 ? count - i0 : 4;
+            for (int i = 0; i < x.count; ++i) {
+                if (R.pos >= R.log.size()) return SPC_ERR_CUDA;  // control flow left the record
+                out[i0 + i] = R.log[R.pos++];
+                x.dev[i] = dev[i0 + i];
+                x.bytes[i] = bytes[i0 + i];
+                x.want[i] = (long long)out[i0 + i];
+            }
+            SPC_LAUNCH(ctx, k_expect, 1, 32, 0, x, R.d_mismatch);
         }
         return SPC_OK;
     }
@@ -206,8 +221,14 @@ spc_status read_loop_count(spc_context* ctx, const int32_t* dev, int64_t* out) {
         *out = R.log[R.pos++];
         // only the count that ends the loop is checked: the loop's kernels take the count from
         // the device, so a different intermediate count changes no result
-        if (*out == 0)
-            SPC_LAUNCH(ctx, k_expect, 1, 32, 0, dev, 4, 0ll, R.d_mismatch);
+        if (*out == 0) {
+            Expect x{};
+            x.count = 1;
+            x.dev[0] = dev;
+            x.bytes[0] = 4;
+            x.want[0] = 0;
+            SPC_LAUNCH(ctx, k_expect, 1, 32, 0, x, R.d_mismatch);
+        }
         return SPC_OK;
     }
     return read_i32(ctx, dev, out);

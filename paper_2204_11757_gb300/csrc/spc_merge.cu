@@ -283,7 +283,10 @@ k_bv_hook(const int32_t* __restrict__ count, const int32_t* __restrict__ wl_e,
           const int32_t* __restrict__ wl_u, const int32_t* __restrict__ wl_v,
           const unsigned long long* __restrict__ best_k, const int32_t* __restrict__ best_e,
           unsigned long long* other_k, int32_t* other_e, int32_t* parent, uint8_t* msf,
-          uint32_t* status) {
+          int32_t* spent_count, uint32_t* status) {
+    // this round's input count is read by nobody after phase A: zero it here, it is the
+    // next round's output count
+    if (blockIdx.x == 0 && threadIdx.x == 0) *spent_count = 0;
     const int64_t cnt = *count;
     const int lane = threadIdx.x & 31;
     for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x; i0 < cnt;
@@ -492,6 +495,78 @@ k_rsel_round(int r, int64_t n_host, const int32_t* __restrict__ n_dev,
     }
 }
 
+// Rounds r0 .. R-1 of the select in one CTA, over the candidates still matching after the
+// full-width rounds (usually few): per round a shared-memory histogram of digit r over the
+// items whose digits 0..r-1 are the picked ones, a block scan, the pick.
+constexpr int kRestThreads = 1024;
+constexpr int64_t kRestMax = 16384;  // candidates a single CTA takes
+
+template <class KT>
+__global__ void __launch_bounds__(kRestThreads)
+k_rsel_rest(int r0, const int32_t* __restrict__ n_dev, const KT* __restrict__ keys,
+            const uint32_t* __restrict__ vals, SelState* st) {
+    constexpr int R = SelBits<KT>::kRounds;
+    constexpr int kPer = kSelBins / kRestThreads;
+    __shared__ uint32_t sh_h[kSelBins];
+    __shared__ uint32_t sh_dig[16];
+    __shared__ unsigned long long sh_s[kRestThreads];
+    __shared__ unsigned long long sh_need;
+    const int64_t n = *n_dev;
+    if (threadIdx.x < 16) sh_dig[threadIdx.x] = st->dig[threadIdx.x];
+    if (threadIdx.x == 0) sh_need = st->need;
+    for (int r = r0; r < R; ++r) {
+        for (int b = threadIdx.x; b < kSelBins; b += blockDim.x) sh_h[b] = 0;
+        __syncthreads();
+        // candidates often share their digits (exactly equal scores): lanes holding the same
+        // digit add with one shared-memory atomic
+        for (int64_t i0 = 0; i0 < n; i0 += blockDim.x) {
+            const int64_t i = i0 + threadIdx.x;
+            bool match = i < n;
+            uint32_t d = 0;
+            if (match) {
+                const KT hi = keys[i];
+                const uint32_t lo = vals[i];
+                for (int q = 0; q < r; ++q) match = match && sel_digit<KT>(hi, lo, q) == sh_dig[q];
+                d = sel_digit<KT>(hi, lo, r);
+            }
+            const unsigned peers = __match_any_sync(0xffffffffu, match ? d : 0xffffffffu);
+            if (match && (int)(threadIdx.x & 31) == __ffs(peers) - 1)
+                atomicAdd(&sh_h[d], (uint32_t)__popc(peers));
+        }
+        __syncthreads();
+        unsigned long long loc = 0;
+        uint32_t c[kPer];
+        for (int j = 0; j < kPer; ++j) {
+            c[j] = sh_h[threadIdx.x * kPer + j];
+            loc += c[j];
+        }
+        sh_s[threadIdx.x] = loc;
+        __syncthreads();
+        for (int o = 1; o < kRestThreads; o <<= 1) {
+            const unsigned long long t = threadIdx.x >= (unsigned)o ? sh_s[threadIdx.x - o] : 0ull;
+            __syncthreads();
+            sh_s[threadIdx.x] += t;
+            __syncthreads();
+        }
+        const unsigned long long need = sh_need;
+        unsigned long long run = threadIdx.x ? sh_s[threadIdx.x - 1] : 0ull;
+        __syncthreads();  // every thread has read sh_need
+        if (run < need && sh_s[threadIdx.x] >= need) {
+            for (int j = 0; j < kPer; ++j) {
+                if (run + c[j] >= need) {
+                    sh_dig[r] = (uint32_t)(threadIdx.x * kPer + j);
+                    sh_need = need - run;
+                    break;
+                }
+                run += c[j];
+            }
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x < 16) st->dig[threadIdx.x] = sh_dig[threadIdx.x];
+    if (threadIdx.x == 0) st->need = sh_need;
+}
+
 // keep the items whose digits 0..r are the ones picked so far (order is irrelevant to the
 // select); one global atomic per block and pass
 template <class KT>
@@ -682,10 +757,10 @@ spc_status select_typed(spc_context* ctx, const GraphView& g, const KT* key,
         }
         // ---- 1. Boruvka minimum spanning forest (of the prefix) ---------------------------
         int64_t cur = m;
+        SPC_CUDA(cudaMemsetAsync(counters, 0, 2 * sizeof(int32_t), ctx->stream));
         for (int round = 0; cur > 0; ++round) {
             const int in = round & 1, out = in ^ 1;
             const int par = round & 1;
-            SPC_CUDA(cudaMemsetAsync(counters + out, 0, sizeof(int32_t), ctx->stream));
             SPC_LAUNCH(ctx, k_bv_minkey<KT>,
                        grid_for(cur, kThreads * kMkItems, maxb), kThreads, 0,
                        round == 0 ? 1 : 0, m, counters + in, W.wl_e[in].as<int32_t>(),
@@ -705,7 +780,8 @@ spc_status select_typed(spc_context* ctx, const GraphView& g, const KT* key,
                        counters + out, W.wl_e[out].as<int32_t>(), W.wl_u[out].as<int32_t>(),
                        W.wl_v[out].as<int32_t>(), W.best_k[par].as<unsigned long long>(),
                        W.best_e[par].as<int32_t>(), W.best_k[par ^ 1].as<unsigned long long>(),
-                       W.best_e[par ^ 1].as<int32_t>(), parent, W.msf.as<uint8_t>(), status);
+                       W.best_e[par ^ 1].as<int32_t>(), parent, W.msf.as<uint8_t>(),
+                       counters + in, status);
             // next work-list size (a capture replays the recorded round count)
             SPC_TRY(read_loop_count(ctx, counters + out, &cur));
             // every round at least halves the components that still have edges
@@ -739,19 +815,23 @@ spc_status select_typed(spc_context* ctx, const GraphView& g, const KT* key,
         KT* ck = W.sel_key2.as<KT>();
         uint32_t* cv = W.sel_val2.as<uint32_t>();
         int32_t* cn = counters + 52;
-        for (int r = 0; r < R; ++r) {
-            if (r < kFull) {
-                SPC_LAUNCH(ctx, k_rsel_round<KT>, gsel, kThreads, 0, r, n_msf, nullptr, sk, sv,
-                           hist, sst);
-                continue;
-            }
-            if (r == kFull) {
-                SPC_CUDA(cudaMemsetAsync(cn, 0, sizeof(int32_t), ctx->stream));
-                SPC_LAUNCH(ctx, k_rsel_compact<KT>, gsel, kThreads, 0, kFull - 1, n_msf, sk, sv,
-                           sst, ck, cv, cn);
-            }
-            SPC_LAUNCH(ctx, k_rsel_round<KT>, ctx->num_sms, kThreads, 0, r, 0, cn, ck, cv, hist,
-                       sst);
+        for (int r = 0; r < kFull; ++r) {
+            SPC_LAUNCH(ctx, k_rsel_round<KT>, gsel, kThreads, 0, r, n_msf, nullptr, sk, sv,
+                       hist, sst);
+        }
+        SPC_CUDA(cudaMemsetAsync(cn, 0, sizeof(int32_t), ctx->stream));
+        SPC_LAUNCH(ctx, k_rsel_compact<KT>, gsel, kThreads, 0, kFull - 1, n_msf, sk, sv, sst,
+                   ck, cv, cn);
+        // few candidates (the usual case): the remaining rounds in one CTA; many (a level
+        // where a large share of the forest has exactly equal scores): a launch per round
+        int64_t ncand = 0;
+        SPC_TRY(read_i32(ctx, cn, &ncand));
+        if (ncand <= kRestMax) {
+            SPC_LAUNCH(ctx, k_rsel_rest<KT>, 1, kRestThreads, 0, kFull, cn, ck, cv, sst);
+        } else {
+            for (int r = kFull; r < R; ++r)
+                SPC_LAUNCH(ctx, k_rsel_round<KT>, grid_for(ncand, kThreads, ctx->num_sms * 2),
+                           kThreads, 0, r, 0, cn, ck, cv, hist, sst);
         }
         int32_t* parent2 = W.parent2.as<int32_t>();
         SPC_LAUNCH(ctx, k_iota, grid_for(n, kThreads, maxb), kThreads, 0, parent2, n);

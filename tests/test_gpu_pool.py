@@ -80,6 +80,21 @@ def test_pool_on_coarsening_lifts(ctx, name, F):
         assert np.bincount(lift).max() > 256  # super-nodes of several chunks are covered
 
 
+@pytest.mark.parametrize("dtype", [np.float32, np.float64])
+def test_pool_extreme_magnitudes(ctx, dtype):
+    """Features and gradients from the subnormal range to near overflow, so that the
+    divisions take both the reciprocal path and the IEEE division."""
+    rng = np.random.default_rng(9)
+    n, n_c, F = 6000, 333, 7
+    lift = rng.integers(0, n_c, size=n).astype(np.int32)
+    info = np.finfo(dtype)
+    lo, hi = np.log2(float(info.tiny)) - 10, np.log2(float(info.max)) - 12
+    def vals(shape):
+        e = rng.uniform(lo, hi, size=shape)
+        return (rng.choice([-1.0, 1.0], size=shape) * np.exp2(e)).astype(dtype)
+    _check(ctx, lift, n_c, vals((n, F)), vals((n_c, F)))
+
+
 def test_pool_autograd(ctx):
     api = _api()
     rng = np.random.default_rng(4)
