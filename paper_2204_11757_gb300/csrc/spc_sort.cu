@@ -202,8 +202,22 @@ __global__ void k_os_bases(int npass, const uint32_t* __restrict__ hist, uint32_
     }
 }
 
+// One-sweep scatter pass: OT threads (OW warps) per tile of RTILE items, OI items per lane.
+constexpr int OT = 512;
+constexpr int OW = OT / 32;
+constexpr int OI = RTILE / OT;
+
 template <class K>
-__global__ void __launch_bounds__(RT, 2) k_os_pass(const K* __restrict__ kin,
+struct OsSmem {
+    K keys[RTILE];
+    uint32_t vals[RTILE];
+    uint32_t wcnt[OW][RADIX];
+    uint32_t tile_base[RADIX];
+    int32_t gofs[RADIX];
+};
+
+template <class K>
+__global__ void __launch_bounds__(OT, 2) k_os_pass(const K* __restrict__ kin,
                                                 const uint32_t* __restrict__ vin,
                                                 K* __restrict__ kout, uint32_t* __restrict__ vout,
                                                 int64_t count, int shift, uint32_t mask,
@@ -211,28 +225,29 @@ __global__ void __launch_bounds__(RT, 2) k_os_pass(const K* __restrict__ kin,
                                                 uint32_t* status, uint32_t* tile_counter,
                                                 uint32_t* err) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    SortSmem<K>& s = *reinterpret_cast<SortSmem<K>*>(smem_raw);
+    OsSmem<K>& s = *reinterpret_cast<OsSmem<K>*>(smem_raw);
     __shared__ uint32_t sh_tile;
+    __shared__ uint32_t wsum[RADIX / 32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const unsigned lt_mask = (1u << lane) - 1u;
     if (threadIdx.x == 0) sh_tile = atomicAdd(tile_counter, 1u);
     for (int d = lane; d < RADIX; d += 32) s.wcnt[warp][d] = 0;
     __syncthreads();
     const int64_t tile = sh_tile;
-    const int64_t wbase = tile * RTILE + (int64_t)warp * (32 * RI);
-    K key[RI];
-    uint32_t val[RI];
-    uint32_t dr[RI];  // digit (low 16 bits; RADIX + lane when invalid) | rank in warp << 16
+    const int64_t wbase = tile * RTILE + (int64_t)warp * (32 * OI);
+    K key[OI];
+    uint32_t val[OI];
+    uint32_t dr[OI];  // digit (low 16 bits; RADIX + lane when invalid) | rank in warp << 16
     // every load of the tile is issued before the first is used (all in flight at once)
 #pragma unroll
-    for (int k = 0; k < RI; ++k) {
+    for (int k = 0; k < OI; ++k) {
         const int64_t i = wbase + k * 32 + lane;
         const bool valid = i < count;
         key[k] = valid ? __ldcs(kin + i) : K(0);
         val[k] = valid ? __ldcs(vin + i) : 0u;
     }
 #pragma unroll
-    for (int k = 0; k < RI; ++k) {
+    for (int k = 0; k < OI; ++k) {
         const int64_t i = wbase + k * 32 + lane;
         const bool valid = i < count;
         const uint32_t d = valid ? digit_of(key[k], shift, mask) : (RADIX + lane);
@@ -244,56 +259,58 @@ __global__ void __launch_bounds__(RT, 2) k_os_pass(const K* __restrict__ kin,
         __syncwarp();
     }
     __syncthreads();
-    const int d = threadIdx.x;  // RT == RADIX: one digit per thread from here
-    uint32_t tcount = 0;
+    // from here the first RADIX threads own one digit each
+    const bool digit_thread = threadIdx.x < RADIX;
+    const int d = digit_thread ? threadIdx.x : 0;
+    uint32_t tcount = 0, prefix = 0;
+    if (digit_thread) {
 #pragma unroll
-    for (int w = 0; w < RW; ++w) {
-        const uint32_t t = s.wcnt[w][d];
-        s.wcnt[w][d] = tcount;
-        tcount += t;
-    }
-    // publish this tile's count, then look back for the items of digit d in earlier tiles
-    uint32_t* my = status + tile * RADIX + d;
-    atomicExch(my, kFlagAgg | tcount);
-    uint32_t prefix = 0;
-    for (int64_t t = tile - 1; t >= 0;) {
-        const uint32_t v = *reinterpret_cast<volatile uint32_t*>(status + t * RADIX + d);
-        if (v & kFlagInc) { prefix += v & kValMask; break; }
-        if (v & kFlagAgg) { prefix += v & kValMask; --t; continue; }
-        uint32_t spins = 0;  // predecessor not published yet: wait, bounded
-        while ((*reinterpret_cast<volatile uint32_t*>(status + t * RADIX + d) &
-                (kFlagAgg | kFlagInc)) == 0u) {
-            if (++spins > kSpinLimit) { atomicOr(err, DEV_TIMEOUT); t = -1; break; }
+        for (int w = 0; w < OW; ++w) {
+            const uint32_t t = s.wcnt[w][d];
+            s.wcnt[w][d] = tcount;
+            tcount += t;
         }
+        // publish this tile's count, then look back for the items of digit d in earlier tiles
+        uint32_t* my = status + tile * RADIX + d;
+        atomicExch(my, kFlagAgg | tcount);
+        for (int64_t t = tile - 1; t >= 0;) {
+            const uint32_t v = *reinterpret_cast<volatile uint32_t*>(status + t * RADIX + d);
+            if (v & kFlagInc) { prefix += v & kValMask; break; }
+            if (v & kFlagAgg) { prefix += v & kValMask; --t; continue; }
+            uint32_t spins = 0;  // predecessor not published yet: wait, bounded
+            while ((*reinterpret_cast<volatile uint32_t*>(status + t * RADIX + d) &
+                    (kFlagAgg | kFlagInc)) == 0u) {
+                if (++spins > kSpinLimit) { atomicOr(err, DEV_TIMEOUT); t = -1; break; }
+            }
+        }
+        atomicExch(my, kFlagInc | (prefix + tcount));
     }
-    atomicExch(my, kFlagInc | (prefix + tcount));
     // exclusive scan over digits of the tile counts: positions in the staged tile
-    {
-        uint32_t v = tcount;
+    uint32_t v = tcount;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += t;
+    }
+    if (digit_thread && lane == 31) wsum[warp] = v;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t x = (lane < RADIX / 32) ? wsum[lane] : 0u;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t t = __shfl_up_sync(0xffffffffu, v, o);
-            if (lane >= o) v += t;
+            const uint32_t t = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += t;
         }
-        __shared__ uint32_t wsum[RW];
-        if (lane == 31) wsum[warp] = v;
-        __syncthreads();
-        if (warp == 0) {
-            uint32_t x = (lane < RW) ? wsum[lane] : 0u;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const uint32_t t = __shfl_up_sync(0xffffffffu, x, o);
-                if (lane >= o) x += t;
-            }
-            if (lane < RW) wsum[lane] = x;
-        }
-        __syncthreads();
+        if (lane < RADIX / 32) wsum[lane] = x;
+    }
+    __syncthreads();
+    if (digit_thread) {
         s.tile_base[d] = v - tcount + (warp > 0 ? wsum[warp - 1] : 0u);
         s.gofs[d] = (int32_t)(base[d] + prefix);
     }
     __syncthreads();
 #pragma unroll
-    for (int k = 0; k < RI; ++k) {
+    for (int k = 0; k < OI; ++k) {
         const uint32_t dk = dr[k] & 0xffffu;
         if (dk < RADIX) {
             const uint32_t pos = s.tile_base[dk] + s.wcnt[warp][dk] + (dr[k] >> 16);
@@ -304,7 +321,7 @@ __global__ void __launch_bounds__(RT, 2) k_os_pass(const K* __restrict__ kin,
     __syncthreads();
     const int64_t rem = count - tile * RTILE;
     const int valid_n = rem < RTILE ? (int)rem : RTILE;
-    for (int i = threadIdx.x; i < valid_n; i += RT) {
+    for (int i = threadIdx.x; i < valid_n; i += OT) {
         const K k = s.keys[i];
         const uint32_t dd = digit_of(k, shift, mask);
         const int64_t o = (int64_t)s.gofs[dd] + (i - (int64_t)s.tile_base[dd]);
@@ -333,7 +350,7 @@ spc_status radix_sort_impl(spc_context* ctx, K* keys, uint32_t* vals, K* keys_al
     uint32_t* tctr = base + (size_t)npass * RADIX;
     uint32_t* stat = tctr + 32;
     SPC_CUDA(cudaMemsetAsync(hist, 0, words * 4, ctx->stream));
-    const size_t smem = sizeof(SortSmem<K>);
+    const size_t smem = sizeof(OsSmem<K>);
     static std::atomic<unsigned long long> attr_devs{0};  // devices already set up
     const unsigned long long bit = 1ull << (ctx->device & 63);
     if (!(attr_devs.load() & bit)) {
@@ -354,7 +371,7 @@ spc_status radix_sort_impl(spc_context* ctx, K* keys, uint32_t* vals, K* keys_al
         const int bits = (end_bit - shift) < 8 ? (end_bit - shift) : 8;
         const uint32_t mask = (1u << bits) - 1u;
         note_bytes(ctx, 2.0 * (double)count * (sizeof(K) + 4));  // pairs read once, written once
-        SPC_LAUNCH(ctx, k_os_pass<K>, (unsigned)tiles, RT, smem, ka, va, kb, vb, count, shift,
+        SPC_LAUNCH(ctx, k_os_pass<K>, (unsigned)tiles, OT, smem, ka, va, kb, vb, count, shift,
                    mask, base + (size_t)p * RADIX, stat + (size_t)p * tiles * RADIX, tctr + p,
                    ctx->d_status);
         K* tk = ka; ka = kb; kb = tk;
