@@ -170,6 +170,7 @@ struct Expect {
 };
 
 __global__ void k_expect(Expect x, int32_t* mismatch) {
+    spc::pdl_wait();
     const int i = threadIdx.x;
     if (i >= x.count) return;
     const long long got = x.bytes[i] == 8 ? *static_cast<const long long*>(x.dev[i])
@@ -255,12 +256,14 @@ spc_status sync_status(spc_context* ctx) {
 // ---- small kernels of the driver ------------------------------------------------------------
 
 __global__ void k_compose(int64_t n, const int32_t* __restrict__ next, int32_t* __restrict__ cur) {
+    spc::pdl_wait();
     for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n;
          x += (int64_t)gridDim.x * blockDim.x)
         cur[x] = next[cur[x]];
 }
 
 __global__ void k_compose_emap(int64_t m, const int32_t* __restrict__ next, int32_t* __restrict__ cur) {
+    spc::pdl_wait();
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m;
          e += (int64_t)gridDim.x * blockDim.x) {
         const int32_t k = cur[e];
@@ -271,6 +274,7 @@ __global__ void k_compose_emap(int64_t m, const int32_t* __restrict__ next, int3
 template <class KT>
 __global__ void k_sort_prep(int64_t m, const KT* __restrict__ f, KT* __restrict__ key,
                             uint32_t* __restrict__ val) {
+    spc::pdl_wait();
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m;
          e += (int64_t)gridDim.x * blockDim.x) {
         key[e] = f[e];
@@ -281,6 +285,7 @@ __global__ void k_sort_prep(int64_t m, const KT* __restrict__ f, KT* __restrict_
 // caller-supplied lift: every value in [0, n_c)
 __global__ void k_check_lift(int64_t n, const int32_t* __restrict__ lift, int64_t n_c,
                              uint32_t* status) {
+    spc::pdl_wait();
     for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n;
          x += (int64_t)gridDim.x * blockDim.x) {
         const int32_t c = lift[x];
@@ -290,6 +295,7 @@ __global__ void k_check_lift(int64_t n, const int32_t* __restrict__ lift, int64_
 
 __global__ void k_targets(int64_t B, const int64_t* __restrict__ graph_ptr, int64_t divisor,
                           int64_t* __restrict__ targets) {
+    spc::pdl_wait();
     for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < B;
          b += (int64_t)gridDim.x * blockDim.x) {
         int64_t t = (graph_ptr[b + 1] - graph_ptr[b]) / divisor;
@@ -585,6 +591,7 @@ constexpr unsigned long long kPosMul = 0xD6E8FEB86659FD93ull;  // odd: positions
 // aligned or sized); four loads in flight per thread
 __global__ void k_checksum(const void* __restrict__ p, int64_t bytes, unsigned long long salt,
                            unsigned long long* acc) {
+    spc::pdl_wait();
     unsigned long long s = 0;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;

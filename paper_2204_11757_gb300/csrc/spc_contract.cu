@@ -39,6 +39,7 @@ __global__ void __launch_bounds__(kThreads)
 k_classify(int64_t m, const int32_t* __restrict__ eu, const int32_t* __restrict__ ev,
            const int32_t* __restrict__ lift, uint8_t* __restrict__ inter,
            uint8_t* __restrict__ intra) {
+    spc::pdl_wait();
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m;
          e += (int64_t)gridDim.x * blockDim.x) {
         const bool x = lift[eu[e]] != lift[ev[e]];
@@ -53,6 +54,7 @@ k_scatter_keys(int64_t m, int nb, const int32_t* __restrict__ eu, const int32_t*
                const int32_t* __restrict__ intra_pos, uint64_t* __restrict__ ckey,
                uint32_t* __restrict__ cval, uint32_t* __restrict__ ikey,
                uint32_t* __restrict__ ival, int32_t* __restrict__ emap) {
+    spc::pdl_wait();
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m;
          e += (int64_t)gridDim.x * blockDim.x) {
         const int32_t U = lift[eu[e]], V = lift[ev[e]];
@@ -71,12 +73,14 @@ k_scatter_keys(int64_t m, int nb, const int32_t* __restrict__ eu, const int32_t*
 }
 
 __global__ void k_set_i32(int32_t* p, int32_t v) {
+    spc::pdl_wait();
     if (threadIdx.x == 0) *p = v;
 }
 
 template <class K>
 __global__ void __launch_bounds__(kThreads)
 k_heads(int64_t cnt, const K* __restrict__ key, uint8_t* __restrict__ head) {
+    spc::pdl_wait();
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cnt;
          i += (int64_t)gridDim.x * blockDim.x)
         head[i] = (i == 0 || key[i] != key[i - 1]) ? 1 : 0;
@@ -89,6 +93,7 @@ k_emit_segments(int64_t cnt, int nb, const uint64_t* __restrict__ key,
                 const int32_t* __restrict__ hpos, int32_t* __restrict__ emap,
                 int32_t* __restrict__ perm, int32_t* __restrict__ seg, int32_t* __restrict__ cU,
                 int32_t* __restrict__ cV) {
+    spc::pdl_wait();
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cnt;
          i += (int64_t)gridDim.x * blockDim.x) {
         const int32_t ce = hpos[i] + head[i] - 1;
@@ -108,6 +113,7 @@ k_emit_segments(int64_t cnt, int nb, const uint64_t* __restrict__ key,
 __global__ void __launch_bounds__(kThreads)
 k_run_starts(int64_t cnt, const uint8_t* __restrict__ head, const int32_t* __restrict__ hpos,
              int32_t* __restrict__ start) {
+    spc::pdl_wait();
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cnt;
          i += (int64_t)gridDim.x * blockDim.x) {
         if (head[i]) start[hpos[i]] = (int32_t)i;
@@ -124,6 +130,7 @@ k_segsum_short(int64_t nseg, const int32_t* __restrict__ start, const uint32_t* 
                const uint32_t* __restrict__ key, const WT* __restrict__ w_und, Out* __restrict__ out,
                int32_t* __restrict__ long_list, int32_t* __restrict__ long_count,
                uint32_t* status) {
+    spc::pdl_wait();
     for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < nseg;
          r += (int64_t)gridDim.x * blockDim.x) {
         const int32_t j0 = start[r], j1 = start[r + 1];
@@ -146,6 +153,7 @@ k_segsum_long(const int32_t* __restrict__ start, const uint32_t* __restrict__ id
               const uint32_t* __restrict__ key, const WT* __restrict__ w_und, Out* __restrict__ out,
               const int32_t* __restrict__ long_list, const int32_t* __restrict__ long_count,
               uint32_t* status) {
+    spc::pdl_wait();
     const int32_t cnt = *long_count;
     for (int32_t q = blockIdx.x; q < cnt; q += gridDim.x) {
         const int64_t r = long_list[q];
@@ -171,6 +179,7 @@ __global__ void k_long_seg_prep(const int32_t* __restrict__ long_list,
                                 const int32_t* __restrict__ long_count,
                                 const int32_t* __restrict__ start, const uint32_t* __restrict__ key,
                                 int64_t* __restrict__ len, int64_t* __restrict__ out_idx) {
+    spc::pdl_wait();
     const int32_t cnt = *long_count;
     for (int32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < cnt; q += gridDim.x * blockDim.x) {
         const int32_t r = long_list[q];
@@ -186,6 +195,7 @@ k_gather_long_terms(const int32_t* __restrict__ long_list, const int32_t* __rest
                     const int32_t* __restrict__ start, const uint32_t* __restrict__ idx,
                     const WT* __restrict__ w_und, const int64_t* __restrict__ base,
                     WT* __restrict__ terms) {
+    spc::pdl_wait();
     const int32_t cnt = *long_count;
     const int64_t total = base[cnt];
     for (int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; f < total;
@@ -211,6 +221,7 @@ __global__ void __launch_bounds__(kThreads)
 k_degree_counts(int64_t m_c, const int32_t* __restrict__ cU, const int32_t* __restrict__ cV,
                 int32_t* up_deg, int32_t* low_deg, uint32_t* __restrict__ tkey,
                 uint32_t* __restrict__ tval) {
+    spc::pdl_wait();
     for (int64_t k0 = (int64_t)blockIdx.x * blockDim.x; k0 < m_c;
          k0 += (int64_t)gridDim.x * blockDim.x) {  // uniform per warp
         const int64_t k = k0 + threadIdx.x;
@@ -228,6 +239,7 @@ k_degree_counts(int64_t m_c, const int32_t* __restrict__ cU, const int32_t* __re
 __global__ void __launch_bounds__(kThreads)
 k_rowptr(int64_t n_c, const int32_t* __restrict__ ufirst, const int32_t* __restrict__ lstart,
          int64_t* __restrict__ rowptr_c) {
+    spc::pdl_wait();
     for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u <= n_c;
          u += (int64_t)gridDim.x * blockDim.x)
         rowptr_c[u] = (int64_t)ufirst[u] + (int64_t)lstart[u];
@@ -240,6 +252,7 @@ k_fill_lower(int64_t m_c, const uint32_t* __restrict__ tkey, const uint32_t* __r
              const int32_t* __restrict__ lstart, const int64_t* __restrict__ rowptr_c,
              const int32_t* __restrict__ cU, const WT* __restrict__ a_und,
              int32_t* __restrict__ col_c, WT* __restrict__ w_c) {
+    spc::pdl_wait();
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m_c;
          i += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t V = tkey[i], k = tval[i];
@@ -256,6 +269,7 @@ k_fill_upper(int64_t m_c, const int32_t* __restrict__ cU, const int32_t* __restr
              const int32_t* __restrict__ ufirst, const int32_t* __restrict__ low_deg,
              const int64_t* __restrict__ rowptr_c, const WT* __restrict__ a_und,
              int32_t* __restrict__ col_c, WT* __restrict__ w_c) {
+    spc::pdl_wait();
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < m_c;
          k += (int64_t)gridDim.x * blockDim.x) {
         const int32_t U = cU[k];
@@ -269,6 +283,7 @@ template <class WT>
 __global__ void __launch_bounds__(kThreads)
 k_backward(int64_t m, const int32_t* __restrict__ emap, const WT* __restrict__ grad_a,
            WT* __restrict__ grad_w) {
+    spc::pdl_wait();
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m;
          e += (int64_t)gridDim.x * blockDim.x) {
         const int32_t k = emap[e];

@@ -6,6 +6,7 @@
 
 #include <string>
 #include <type_traits>
+#include <utility>
 #include <vector>
 
 #include "../../include/spcoarsen.h"
@@ -232,11 +233,40 @@ inline int grid_for(int64_t items, int threads, int max_blocks) {
     return static_cast<int>(b);
 }
 
+// Kernels of the library are launched with programmatic stream serialization: a kernel may
+// be scheduled while its predecessor on the stream is still finishing, and waits in
+// pdl_wait() -- the first statement of every kernel -- until that predecessor has completed
+// and its writes are visible.  This hides the launch gap between dependent kernels (many of a
+// coarsening level's kernels are small).  Launched without the attribute, pdl_wait() returns
+// at once.
+__device__ __forceinline__ void pdl_wait() {
+#if defined(__CUDA_ARCH__) && __CUDA_ARCH__ >= 900
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+#endif
+}
+
+template <typename... Params, typename... Args>
+cudaError_t launch_pdl(cudaStream_t stream, dim3 grid, dim3 block, size_t smem,
+                       void (*kernel)(Params...), Args&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
+
 #define SPC_LAUNCH(ctx, kernel, grid, block, smem, ...)                                   \
     do {                                                                                 \
         spc::before_launch((ctx), #kernel);                                              \
-        kernel<<<(grid), (block), (smem), (ctx)->stream>>>(__VA_ARGS__);                 \
-        cudaError_t le_ = cudaGetLastError();                                            \
+        cudaError_t le_ = spc::launch_pdl((ctx)->stream, dim3(grid), dim3(block), (smem), \
+                                          kernel, __VA_ARGS__);                          \
+        if (le_ == cudaSuccess) le_ = cudaGetLastError();                                \
         spc::after_launch((ctx), #kernel);                                               \
         if (le_ != cudaSuccess) {                                                        \
             spc::set_last_cuda_error(le_, #kernel, __FILE__, __LINE__);                  \

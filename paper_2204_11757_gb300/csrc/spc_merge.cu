@@ -100,6 +100,7 @@ __device__ __forceinline__ bool uf_unite(int32_t* parent, int32_t a, int32_t b,
 }
 
 __global__ void k_iota(int32_t* a, int64_t n) {
+    spc::pdl_wait();
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x)
         a[i] = (int32_t)i;
@@ -134,6 +135,7 @@ k_bv_minkey(int round0, int64_t m, const int32_t* __restrict__ in_count,
             const int32_t* __restrict__ ev, const KT* __restrict__ key, int tau_shift,
             const uint32_t* __restrict__ tau_top, int32_t* parent, unsigned long long* best_k,
             int32_t* wo_e, int32_t* wo_u, int32_t* wo_v, int32_t* out_count, uint32_t* status) {
+    spc::pdl_wait();
     __shared__ int32_t sh_wsum[kThreads / 32];
     __shared__ int32_t sh_base;
     const int64_t cnt = round0 ? m : (int64_t)*in_count;
@@ -208,6 +210,7 @@ k_bv_minkey(int round0, int64_t m, const int32_t* __restrict__ in_count,
 template <class KT>
 __global__ void __launch_bounds__(1024)
 k_key_hist(int64_t m, const KT* __restrict__ key, int shift, uint32_t* __restrict__ hist) {
+    spc::pdl_wait();
     extern __shared__ uint32_t sh_hist[];
     for (int b = threadIdx.x; b < 32768; b += blockDim.x) sh_hist[b] = 0;
     __syncthreads();
@@ -225,6 +228,7 @@ k_key_hist(int64_t m, const KT* __restrict__ key, int shift, uint32_t* __restric
 // smallest bin whose cumulative count reaches `need` (all bins when need >= m)
 __global__ void __launch_bounds__(1024)
 k_pick_tau(const uint32_t* __restrict__ hist, int64_t need, uint32_t* __restrict__ tau_top) {
+    spc::pdl_wait();
     __shared__ unsigned long long sh[1024];
     constexpr int kPer = 32768 / 1024;
     unsigned long long loc = 0;
@@ -258,6 +262,7 @@ k_bv_tiebreak(const int32_t* __restrict__ count, const int32_t* __restrict__ wl_
               const int32_t* __restrict__ wl_u, const int32_t* __restrict__ wl_v,
               const unsigned long long* __restrict__ key, const unsigned long long* best_k,
               int32_t* best_e) {
+    spc::pdl_wait();
     const int64_t cnt = *count;
     for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x; i0 < cnt;
          i0 += (int64_t)gridDim.x * blockDim.x) {  // uniform per warp: the helpers need it
@@ -284,6 +289,7 @@ k_bv_hook(const int32_t* __restrict__ count, const int32_t* __restrict__ wl_e,
           const unsigned long long* __restrict__ best_k, const int32_t* __restrict__ best_e,
           unsigned long long* other_k, int32_t* other_e, int32_t* parent, uint8_t* msf,
           int32_t* spent_count, uint32_t* status) {
+    spc::pdl_wait();
     // this round's input count is read by nobody after phase A: zero it here, it is the
     // next round's output count
     if (blockIdx.x == 0 && threadIdx.x == 0) *spent_count = 0;
@@ -322,6 +328,7 @@ template <class KT>
 __global__ void __launch_bounds__(kThreads)
 k_compact_msf(int64_t m, const uint8_t* __restrict__ msf, const int32_t* __restrict__ pos,
               const KT* __restrict__ key, KT* __restrict__ out_k, uint32_t* __restrict__ out_v) {
+    spc::pdl_wait();
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m;
          e += (int64_t)gridDim.x * blockDim.x) {
         if (msf[e]) {
@@ -335,6 +342,7 @@ k_compact_msf(int64_t m, const uint8_t* __restrict__ msf, const int32_t* __restr
 // graph id of every node of a block-diagonal batch
 __global__ void k_node_graph(int64_t n, int64_t B, const int64_t* __restrict__ graph_ptr,
                              int32_t* __restrict__ node_graph) {
+    spc::pdl_wait();
     for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n;
          x += (int64_t)gridDim.x * blockDim.x) {
         int64_t lo = 0, hi = B;  // largest b with graph_ptr[b] <= x
@@ -350,6 +358,7 @@ __global__ void k_node_graph(int64_t n, int64_t B, const int64_t* __restrict__ g
 __global__ void k_graph_keys(const int32_t* __restrict__ count, const uint32_t* __restrict__ eids,
                              const int32_t* __restrict__ eu, const int32_t* __restrict__ node_graph,
                              uint32_t* __restrict__ gkey) {
+    spc::pdl_wait();
     const int64_t cnt = *count;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cnt;
          i += (int64_t)gridDim.x * blockDim.x)
@@ -362,6 +371,7 @@ __global__ void k_graph_segments(int64_t B, const int64_t* __restrict__ graph_pt
                                  const int32_t* __restrict__ up_ptr,
                                  const int32_t* __restrict__ msf_pos, int32_t* __restrict__ seg_start,
                                  int32_t* __restrict__ k_graph) {
+    spc::pdl_wait();
     for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b < B;
          b += (int64_t)gridDim.x * blockDim.x) {
         seg_start[b] = msf_pos[up_ptr[graph_ptr[b]]];
@@ -378,6 +388,7 @@ k_select_unite(const int32_t* __restrict__ count, const uint32_t* __restrict__ e
                const int32_t* __restrict__ k_graph, int64_t k_single,
                const int32_t* __restrict__ eu, const int32_t* __restrict__ ev, int32_t* parent,
                uint8_t* merged, uint32_t* status) {
+    spc::pdl_wait();
     const int64_t cnt = *count;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cnt;
          i += (int64_t)gridDim.x * blockDim.x) {
@@ -439,6 +450,7 @@ __global__ void __launch_bounds__(kThreads)
 k_rsel_round(int r, int64_t n_host, const int32_t* __restrict__ n_dev,
              const KT* __restrict__ keys, const uint32_t* __restrict__ vals,
              uint32_t* __restrict__ hist, SelState* st) {
+    spc::pdl_wait();
     __shared__ uint32_t sh_h[kSelBins];
     __shared__ uint32_t sh_dig[16];
     __shared__ bool sh_last;
@@ -505,6 +517,7 @@ template <class KT>
 __global__ void __launch_bounds__(kRestThreads)
 k_rsel_rest(int r0, const int32_t* __restrict__ n_dev, const KT* __restrict__ keys,
             const uint32_t* __restrict__ vals, SelState* st) {
+    spc::pdl_wait();
     constexpr int R = SelBits<KT>::kRounds;
     constexpr int kPer = kSelBins / kRestThreads;
     __shared__ uint32_t sh_h[kSelBins];
@@ -574,6 +587,7 @@ __global__ void __launch_bounds__(kThreads)
 k_rsel_compact(int r, int64_t n, const KT* __restrict__ keys, const uint32_t* __restrict__ vals,
                const SelState* __restrict__ st, KT* __restrict__ out_k,
                uint32_t* __restrict__ out_v, int32_t* __restrict__ out_n) {
+    spc::pdl_wait();
     __shared__ uint32_t sh_dig[16];
     __shared__ int32_t sh_cnt, sh_base;
     const int lane = threadIdx.x & 31;
@@ -615,6 +629,7 @@ __global__ void __launch_bounds__(kThreads)
 k_rsel_unite(int64_t n, const KT* __restrict__ keys, const uint32_t* __restrict__ vals,
              const SelState* __restrict__ st, const int32_t* __restrict__ eu,
              const int32_t* __restrict__ ev, int32_t* parent, uint8_t* merged, uint32_t* status) {
+    spc::pdl_wait();
     constexpr int H = SelBits<KT>::kHiRounds, KB = SelBits<KT>::kKeyBits;
     KT thi = 0;
     for (int q = 0; q < H; ++q) {
@@ -640,6 +655,7 @@ k_rsel_unite(int64_t n, const KT* __restrict__ keys, const uint32_t* __restrict_
 }
 
 __global__ void k_rsel_init(SelState* st, unsigned long long k) {
+    spc::pdl_wait();
     if (threadIdx.x == 0) st->need = k;
     if (threadIdx.x < 16) { st->dig[threadIdx.x] = 0; st->ticket[threadIdx.x] = 0; }
 }
@@ -647,6 +663,7 @@ __global__ void k_rsel_init(SelState* st, unsigned long long k) {
 // root (= smallest member) of every node and the root flags
 __global__ void __launch_bounds__(kThreads)
 k_roots(int64_t n, int32_t* parent, int32_t* __restrict__ flag, uint32_t* status) {
+    spc::pdl_wait();
     for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n;
          x += (int64_t)gridDim.x * blockDim.x) {
         const int32_t r = uf_find(parent, (int32_t)x, status);
@@ -657,6 +674,7 @@ k_roots(int64_t n, int32_t* parent, int32_t* __restrict__ flag, uint32_t* status
 __global__ void __launch_bounds__(kThreads)
 k_lift(int64_t n, int32_t* parent, const int32_t* __restrict__ ids, int32_t* __restrict__ lift,
        uint32_t* status) {
+    spc::pdl_wait();
     for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n;
          x += (int64_t)gridDim.x * blockDim.x)
         lift[x] = ids[uf_find(parent, (int32_t)x, status)];
@@ -665,6 +683,7 @@ k_lift(int64_t n, int32_t* parent, const int32_t* __restrict__ ids, int32_t* __r
 __global__ void k_graph_ptr_c(int64_t B, const int64_t* __restrict__ graph_ptr,
                               const int32_t* __restrict__ ids, const int64_t* __restrict__ targets,
                               int64_t* __restrict__ graph_ptr_c, int32_t* __restrict__ warn) {
+    spc::pdl_wait();
     for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; b <= B;
          b += (int64_t)gridDim.x * blockDim.x) {
         graph_ptr_c[b] = ids[graph_ptr[b]];

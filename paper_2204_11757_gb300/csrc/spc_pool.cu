@@ -41,6 +41,7 @@ constexpr int kPoolRows = 8;  // units (rows, chunks, super-nodes) per block; 32
 __global__ void __launch_bounds__(kThreads)
 k_pool_counts(int64_t n, const int32_t* __restrict__ lift, int64_t n_c,
               int32_t* __restrict__ cnt, uint32_t* __restrict__ status) {
+    spc::pdl_wait();
     __shared__ int32_t sh_first;
     const int lane = threadIdx.x & 31;
     for (int64_t b0 = (int64_t)blockIdx.x * blockDim.x; b0 < n;
@@ -72,6 +73,7 @@ k_pool_counts(int64_t n, const int32_t* __restrict__ lift, int64_t n_c,
 // ascending ids inside every super-node)
 __global__ void k_pool_keys(int64_t n, const int32_t* __restrict__ lift,
                             uint32_t* __restrict__ key, uint32_t* __restrict__ val) {
+    spc::pdl_wait();
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
          v += (int64_t)gridDim.x * blockDim.x) {
         key[v] = (uint32_t)lift[v];
@@ -82,6 +84,7 @@ __global__ void k_pool_keys(int64_t n, const int32_t* __restrict__ lift,
 // chunks of every super-node's list at the next tree level
 __global__ void k_pool_nchunks(int64_t n_c, const int32_t* __restrict__ items,
                                int32_t* __restrict__ nch) {
+    spc::pdl_wait();
     for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n_c;
          u += (int64_t)gridDim.x * blockDim.x)
         nch[u] = (int32_t)((items[u] + kPoolChunk - 1) / kPoolChunk);
@@ -89,6 +92,7 @@ __global__ void k_pool_nchunks(int64_t n_c, const int32_t* __restrict__ items,
 
 __global__ void k_pool_owner(int64_t n_c, const int32_t* __restrict__ choff,
                              int32_t* __restrict__ owner) {
+    spc::pdl_wait();
     for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n_c;
          u += (int64_t)gridDim.x * blockDim.x)
         for (int32_t c = choff[u]; c < choff[u + 1]; ++c) owner[c] = (int32_t)u;
@@ -104,6 +108,7 @@ k_pool_level(int64_t n_c, int64_t F, const int32_t* __restrict__ ioff,
              const int32_t* __restrict__ owner, const uint32_t* __restrict__ members,
              const T* __restrict__ x, const T* __restrict__ prev, T* __restrict__ part,
              const uint32_t* status) {
+    spc::pdl_wait();
     if (*status) return;
     const int64_t nchunks = choff[n_c];
     for (int64_t c = (int64_t)blockIdx.x * kPoolRows + threadIdx.y; c < nchunks;
@@ -141,6 +146,7 @@ __global__ void __launch_bounds__(32 * kPoolRows)
 k_pool_mean(int64_t n_c, int64_t F, const int32_t* __restrict__ cnt,
             const int32_t* __restrict__ off, const T* __restrict__ part, T* __restrict__ xc,
             const uint32_t* status) {
+    spc::pdl_wait();
     if (*status) return;
     for (int64_t u = (int64_t)blockIdx.x * kPoolRows + threadIdx.y; u < n_c;
          u += (int64_t)gridDim.x * kPoolRows) {
@@ -155,6 +161,7 @@ __global__ void __launch_bounds__(32 * kPoolRows)
 k_pool_backward(int64_t n, int64_t F, const int32_t* __restrict__ lift,
                 const int32_t* __restrict__ cnt, const T* __restrict__ grad_xc,
                 T* __restrict__ grad_x, const uint32_t* status) {
+    spc::pdl_wait();
     if (*status) return;
     for (int64_t v = (int64_t)blockIdx.x * kPoolRows + threadIdx.y; v < n;
          v += (int64_t)gridDim.x * kPoolRows) {

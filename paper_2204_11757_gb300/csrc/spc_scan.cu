@@ -48,6 +48,7 @@ __device__ __forceinline__ T block_excl_scan(T v, T* total) {
 
 template <class In, class T>
 __global__ void __launch_bounds__(ST) k_scan_reduce(const In* in, int64_t n, T* tile_sums) {
+    spc::pdl_wait();
     const int64_t base = (int64_t)blockIdx.x * STILE;
     T s = 0;
 #pragma unroll 4
@@ -63,6 +64,7 @@ __global__ void __launch_bounds__(ST) k_scan_reduce(const In* in, int64_t n, T* 
 // single block: exclusive scan of nt tile sums in place, writes the grand total to *total_out
 template <class T>
 __global__ void __launch_bounds__(ST) k_scan_tiles(T* tile_sums, int64_t nt, T* total_out) {
+    spc::pdl_wait();
     T carry = 0;
     for (int64_t base = 0; base < nt; base += ST) {
         int64_t i = base + threadIdx.x;
@@ -78,6 +80,7 @@ __global__ void __launch_bounds__(ST) k_scan_tiles(T* tile_sums, int64_t nt, T* 
 template <class In, class T, class Out>
 __global__ void __launch_bounds__(ST) k_scan_down(const In* in, int64_t n, const T* tile_offs,
                                                   Out* out) {
+    spc::pdl_wait();
     // padded shared tile: index i -> i + i/32 avoids bank conflicts on the blocked reads
     __shared__ T buf[STILE + STILE / 32];
     const int64_t base = (int64_t)blockIdx.x * STILE;
@@ -115,6 +118,7 @@ __global__ void __launch_bounds__(ST) k_scan_down(const In* in, int64_t n, const
 
 template <class T, class Out>
 __global__ void k_copy_total(const T* total, Out* dst) {
+    spc::pdl_wait();
     if (threadIdx.x == 0) *dst = (Out)*total;
 }
 
@@ -125,6 +129,7 @@ constexpr int64_t kSmallMax = 16384;
 
 template <class In, class T, class Out>
 __global__ void __launch_bounds__(kSmallThreads) k_scan_small(const In* in, int64_t n, Out* out) {
+    spc::pdl_wait();
     __shared__ T wsum[kSmallThreads / 32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     T carry = 0;
@@ -181,6 +186,7 @@ __global__ void __launch_bounds__(ST) k_scan_onepass(const In* in, int64_t n, Ou
                                                      unsigned long long* status,
                                                      uint32_t* tile_ctr, int64_t nt,
                                                      uint32_t* err) {
+    spc::pdl_wait();
     __shared__ T buf[STILE + STILE / 32];
     __shared__ uint32_t sh_tile;
     __shared__ T sh_prefix;

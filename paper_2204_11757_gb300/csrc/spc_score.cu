@@ -87,6 +87,7 @@ k_rows_degree(int64_t n, int64_t nnz, const int64_t* __restrict__ rowptr,
               typename Tr<WT>::Acc* __restrict__ deg, int32_t* __restrict__ up_cnt,
               int32_t* __restrict__ nlow_out, int32_t* __restrict__ long_rows,
               int32_t* __restrict__ long_count, uint32_t* __restrict__ status) {
+    spc::pdl_wait();
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     if (validate && blockIdx.x == 0 && threadIdx.x == 0) {
         if (rowptr[0] != 0 || rowptr[n] != nnz) atomicOr(status, DEV_UNSORTED);
@@ -138,6 +139,7 @@ k_long_rows_meta(const int64_t* __restrict__ rowptr, const int32_t* __restrict__
                  typename Tr<WT>::Acc* __restrict__ deg, int32_t* __restrict__ up_cnt,
                  int32_t* __restrict__ nlow_out, int64_t* __restrict__ lr_base,
                  int64_t* __restrict__ lr_len, int64_t* __restrict__ lr_idx) {
+    spc::pdl_wait();
     const int32_t cnt = *long_count;
     const int lane = threadIdx.x & 31;
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
@@ -179,6 +181,7 @@ k_long_rows_flat(int64_t n, const int64_t* __restrict__ rowptr, const int32_t* _
                  const WT* __restrict__ w, int validate, const int32_t* __restrict__ long_rows,
                  const int32_t* __restrict__ long_count, const int64_t* __restrict__ lr_eoff,
                  typename Tr<WT>::Acc* __restrict__ deg, uint32_t* __restrict__ status) {
+    spc::pdl_wait();
     constexpr bool kInt = std::is_same<WT, int32_t>::value;
     const int32_t cnt = *long_count;
     const int64_t total = lr_eoff[cnt];
@@ -233,6 +236,7 @@ k_long_rows_edges(const int64_t* __restrict__ rowptr, const int32_t* __restrict_
                   const int32_t* __restrict__ long_count, const int64_t* __restrict__ lr_eoff,
                   typename Tr<WT>::P* __restrict__ p, int32_t* __restrict__ eu,
                   int32_t* __restrict__ ev, WT* __restrict__ w_und, uint32_t* __restrict__ status) {
+    spc::pdl_wait();
     if (*status) return;
     const int32_t cnt = *long_count;
     const int64_t total = lr_eoff[cnt];
@@ -279,6 +283,7 @@ k_rows_edges(int64_t n, const int64_t* __restrict__ rowptr, const int32_t* __res
              const int32_t* __restrict__ nlow, const int32_t* __restrict__ up_ptr,
              typename Tr<WT>::P* __restrict__ p, int32_t* __restrict__ eu,
              int32_t* __restrict__ ev, WT* __restrict__ w_und, uint32_t* __restrict__ status) {
+    spc::pdl_wait();
     if (*status) return;  // invalid input: nothing below may index with it
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n; x += stride) {
@@ -362,6 +367,7 @@ k_score_edges(int64_t m, const int32_t* __restrict__ eu, const int32_t* __restri
               const PT* __restrict__ p, KT* __restrict__ score, const void* __restrict__ w,
               const void* __restrict__ w_und, int wsize, int validate, uint32_t* status,
               unsigned long long* __restrict__ ops) {
+    spc::pdl_wait();
     if (*status) return;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     uint32_t n_add = 0, n_sub = 0;  // union coordinates, coordinates in both rows
@@ -420,6 +426,7 @@ k_score_warp_row(int64_t n, const int64_t* __restrict__ rowptr, const int32_t* _
                  const int32_t* __restrict__ nlow, KT* __restrict__ score,
                  const void* __restrict__ w, const void* __restrict__ w_und, int wsize,
                  int validate, uint32_t* status, unsigned long long* __restrict__ ops) {
+    spc::pdl_wait();
     if (*status) return;
     uint32_t n_add = 0, n_sub = 0;
     bool asym = false;
@@ -516,6 +523,7 @@ k_score_hub(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
             const int32_t* __restrict__ long_count, const int64_t* __restrict__ lr_eoff,
             SeqTabView tab, KT* __restrict__ score, int32_t* __restrict__ heavy,
             int32_t* __restrict__ heavy_count, const uint32_t* status) {
+    spc::pdl_wait();
     if (*status) return;
     const int32_t cnt = *long_count;
     const int64_t total = lr_eoff[cnt];
@@ -585,6 +593,7 @@ k_score_hub_heavy(const int64_t* __restrict__ rowptr, const int32_t* __restrict_
                   SeqTabView tab, const int32_t* __restrict__ heavy,
                   const int32_t* __restrict__ heavy_count, KT* __restrict__ score,
                   const uint32_t* status) {
+    spc::pdl_wait();
     if (*status) return;
     const int lane = threadIdx.x & 31;
     const int32_t cnt = *long_count;

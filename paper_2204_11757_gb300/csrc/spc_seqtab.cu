@@ -21,6 +21,7 @@ __global__ void __launch_bounds__(kCT)
 k_seq_minmax(int64_t nseq, const F* __restrict__ terms, const int64_t* __restrict__ base,
              const int64_t* __restrict__ loff, unsigned long long* __restrict__ mn,
              unsigned long long* __restrict__ mx) {
+    spc::pdl_wait();
     const int64_t total = loff[nseq];
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const int64_t wbase = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) & ~(int64_t)31;
@@ -64,6 +65,7 @@ __global__ void k_seq_meta(int64_t nseq, const int64_t* __restrict__ len,
                            const unsigned long long* __restrict__ mx, int full,
                            int32_t* __restrict__ eblo, int32_t* __restrict__ nE,
                            int64_t* __restrict__ tsize, int64_t* __restrict__ tcnt) {
+    spc::pdl_wait();
     for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nseq;
          q += (int64_t)gridDim.x * blockDim.x) {
         const int64_t L = len[q];
@@ -124,6 +126,7 @@ k_seq_chunk_sums(int64_t nseq, int64_t ntrip, const F* __restrict__ terms,
                  const int64_t* __restrict__ base, const int64_t* __restrict__ len,
                  const int32_t* __restrict__ eblo, const int64_t* __restrict__ trip_off,
                  unsigned long long* __restrict__ csum, int32_t* __restrict__ ctie) {
+    spc::pdl_wait();
     __shared__ unsigned long long sh_s[kCT / 32];
     __shared__ int32_t sh_t[kCT / 32];
     for (int64_t t = blockIdx.x; t < ntrip; t += gridDim.x) {
@@ -163,6 +166,7 @@ __global__ void k_seq_chunk_scan(int64_t nseq, const int64_t* __restrict__ len,
                                  const int32_t* __restrict__ nE,
                                  const int64_t* __restrict__ trip_off,
                                  unsigned long long* __restrict__ csum, int32_t* __restrict__ ctie) {
+    spc::pdl_wait();
     for (int64_t q = blockIdx.x; q < nseq; q += gridDim.x) {
         const int64_t nch = (len[q] + kChunk - 1) / kChunk;
         for (int e = threadIdx.x; e < nE[q]; e += blockDim.x) {
@@ -189,6 +193,7 @@ k_seq_chunk_write(int64_t nseq, int64_t ntrip, const F* __restrict__ terms,
                   const int64_t* __restrict__ tab_off, const unsigned long long* __restrict__ csum,
                   const int32_t* __restrict__ ctie, unsigned long long* __restrict__ P,
                   int32_t* __restrict__ T) {
+    spc::pdl_wait();
     constexpr int kItems = kChunk / kCT;
     __shared__ unsigned long long sh_s[kCT / 32];
     __shared__ int32_t sh_t[kCT / 32];
@@ -252,6 +257,7 @@ __global__ void k_seq_full_sums(int64_t nseq, const F* __restrict__ terms,
                                 const unsigned long long* __restrict__ P,
                                 const int32_t* __restrict__ T, const int64_t* __restrict__ out_idx,
                                 Out* __restrict__ out) {
+    spc::pdl_wait();
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
     for (int64_t q = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); q < nseq;
          q += warps) {

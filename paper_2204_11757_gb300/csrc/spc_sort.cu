@@ -29,6 +29,7 @@ template <class K>
 __global__ void __launch_bounds__(RT) k_rs_upsweep(const K* __restrict__ keys, int64_t count,
                                                    int shift, uint32_t mask,
                                                    int32_t* __restrict__ hist, int64_t tiles) {
+    spc::pdl_wait();
     __shared__ uint32_t h[RADIX];
     h[threadIdx.x] = 0;
     __syncthreads();
@@ -63,6 +64,7 @@ __global__ void __launch_bounds__(RT) k_rs_downsweep(const K* __restrict__ kin,
                                                      int shift, uint32_t mask,
                                                      const int32_t* __restrict__ offs,
                                                      int64_t tiles) {
+    spc::pdl_wait();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     SortSmem<K>& s = *reinterpret_cast<SortSmem<K>*>(smem_raw);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -160,6 +162,7 @@ template <class K>
 __global__ void __launch_bounds__(RT) k_os_hist(const K* __restrict__ keys, int64_t count,
                                                 int npass, int end_bit,
                                                 uint32_t* __restrict__ hist) {
+    spc::pdl_wait();
     constexpr int kCopies = 2;  // two copies (warps 0-3, 4-7) halve the contention on a bin
     __shared__ uint32_t h[kCopies][kMaxPasses][RADIX];
     const int warp = (threadIdx.x >> 5) * kCopies / RW;
@@ -184,6 +187,7 @@ __global__ void __launch_bounds__(RT) k_os_hist(const K* __restrict__ keys, int6
 
 // exclusive scan of every pass's 256 bins (one block, one thread per bin)
 __global__ void k_os_bases(int npass, const uint32_t* __restrict__ hist, uint32_t* __restrict__ base) {
+    spc::pdl_wait();
     __shared__ uint32_t sh[RADIX];
     for (int p = 0; p < npass; ++p) {
         sh[threadIdx.x] = hist[p * RADIX + threadIdx.x];
@@ -224,6 +228,7 @@ __global__ void __launch_bounds__(OT, 2) k_os_pass(const K* __restrict__ kin,
                                                 const uint32_t* __restrict__ base,
                                                 uint32_t* status, uint32_t* tile_counter,
                                                 uint32_t* err) {
+    spc::pdl_wait();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     OsSmem<K>& s = *reinterpret_cast<OsSmem<K>*>(smem_raw);
     __shared__ uint32_t sh_tile;

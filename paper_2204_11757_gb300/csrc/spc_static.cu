@@ -73,6 +73,7 @@ bool on_device(const void* p) {
 template <class KT>
 __global__ void k_static_prep(int64_t m, const KT* __restrict__ f, uint64_t* __restrict__ key,
                               uint32_t* __restrict__ val) {
+    spc::pdl_wait();
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m;
          e += (int64_t)gridDim.x * blockDim.x) {
         key[e] = (uint64_t)f[e];
