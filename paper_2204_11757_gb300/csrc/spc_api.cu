@@ -391,7 +391,11 @@ static spc_status reserve_work(spc_context* ctx, int64_t n, int64_t m, int64_t B
     SPC_TRY(ensure(ctx, W.long_segs, (M + 1) * 4));
     // scan of up to max(n, m, 256 * tiles) items -> tile sums; radix histograms
     const size_t big = (N > M ? N : M) + 256 * ((M + 4095) / 4096) + 4096;
+    const void* scan_before = W.scan_tmp.p;
     SPC_TRY(ensure(ctx, W.scan_tmp, (big / 4096 + 4) * 8 + 256));
+    // the scans keep their statuses zero between calls; a new block starts zeroed
+    if (W.scan_tmp.p != scan_before)
+        SPC_CUDA(cudaMemsetAsync(W.scan_tmp.p, 0, W.scan_tmp.bytes, ctx->stream));
     // one-sweep sort: 8 passes x (tiles x 256) look-back words + histograms
     SPC_TRY(ensure(ctx, W.sort_hist, (8 * 256 * ((M + 4095) / 4096) + 8 * 512 + 64) * 4));
     return SPC_OK;

@@ -190,6 +190,8 @@ __global__ void __launch_bounds__(ST) k_scan_onepass(const In* in, int64_t n, Ou
     __shared__ T buf[STILE + STILE / 32];
     __shared__ uint32_t sh_tile;
     __shared__ T sh_prefix;
+    __shared__ bool sh_last;
+    uint32_t* done_ctr = tile_ctr + 1;
     if (threadIdx.x == 0) sh_tile = atomicAdd(tile_ctr, 1u);
     __syncthreads();
     const int64_t tile = sh_tile;
@@ -266,6 +268,22 @@ __global__ void __launch_bounds__(ST) k_scan_onepass(const In* in, int64_t n, Ou
         if (g < n) out[g] = (Out)buf[i + (i >> 5)];
     }
     if (tile == nt - 1 && threadIdx.x == 0) out[n] = (Out)(sh_prefix + tot);
+    // The tile that finishes last resets the statuses and counters for the next scan: every
+    // other tile has counted itself done after its look-back, so none reads them again.
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        sh_last = atomicAdd(done_ctr, 1u) == (uint32_t)(nt - 1);
+    }
+    __syncthreads();
+    if (sh_last) {
+        __threadfence();
+        for (int64_t t = threadIdx.x; t < nt; t += blockDim.x) status[t] = 0ull;
+        if (threadIdx.x == 0) {
+            *tile_ctr = 0u;
+            *done_ctr = 0u;
+        }
+    }
 }
 
 template <class In, class T, class Out>
@@ -275,12 +293,15 @@ spc_status scan_impl(spc_context* ctx, const In* in, Out* out, int64_t n) {
         return SPC_OK;
     }
     const int64_t nt = (n + STILE - 1) / STILE;
+    // statuses [nt] | tile counter, done counter: all zero between scans (each scan resets
+    // them at its end); zeroed here only when the block is new
     const size_t need = (size_t)(nt + 1) * 8;
     Buf& tmp = on_side(ctx) ? ctx->work.scan_tmp_side : ctx->work.scan_tmp;
+    const void* before = tmp.p;
     SPC_TRY(ensure(ctx, tmp, need));
+    if (tmp.p != before) SPC_CUDA(cudaMemsetAsync(tmp.p, 0, tmp.bytes, ctx->stream));
     unsigned long long* status = tmp.as<unsigned long long>();
     uint32_t* tile_ctr = reinterpret_cast<uint32_t*>(status + nt);
-    SPC_CUDA(cudaMemsetAsync(status, 0, need, ctx->stream));
     note_bytes(ctx, (double)n * (sizeof(In) + sizeof(Out)));  // input read, output written
     SPC_LAUNCH(ctx, (k_scan_onepass<In, T, Out>), (unsigned)nt, ST, 0, in, n, out, status,
                tile_ctr, nt, ctx->d_status);
