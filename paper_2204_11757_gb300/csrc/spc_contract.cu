@@ -38,13 +38,27 @@ template <> struct CT<double> {
 __global__ void __launch_bounds__(kThreads)
 k_classify(int64_t m, const int32_t* __restrict__ eu, const int32_t* __restrict__ ev,
            const int32_t* __restrict__ lift, uint8_t* __restrict__ inter,
-           uint8_t* __restrict__ intra) {
+           uint8_t* __restrict__ intra, uint32_t* __restrict__ zero_a, int64_t words_a,
+           uint32_t* __restrict__ zero_b, uint32_t* __restrict__ zero_c, int64_t words_bc,
+           int32_t* __restrict__ counters) {
     spc::pdl_wait();
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m;
-         e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    for (int64_t e = t0; e < m; e += stride) {
         const bool x = lift[eu[e]] != lift[ev[e]];
         inter[e] = x ? 1 : 0;
         intra[e] = x ? 0 : 1;
+    }
+    // the accumulators the contraction adds into start at zero: the self-mass, the coarse
+    // degree counts, the long-segment list counts of both streams
+    for (int64_t i = t0; i < words_a; i += stride) zero_a[i] = 0u;
+    for (int64_t i = t0; i < words_bc; i += stride) {
+        zero_b[i] = 0u;
+        zero_c[i] = 0u;
+    }
+    if (t0 == 0) {
+        counters[9] = 0;
+        counters[11] = 0;
     }
 }
 
@@ -344,10 +358,15 @@ spc_status contract_typed(spc_context* ctx, const GraphView& g, const int32_t* l
     int32_t* inter_pos = W.c_pos.as<int32_t>();
     int32_t* intra_pos = W.c_head.as<int32_t>();
     const int gm = grid_for(m, kThreads, maxb);
-    if (m > 0) {
-        SPC_LAUNCH(ctx, k_classify, gm, kThreads, 0, m, W.eu.as<int32_t>(), W.ev.as<int32_t>(),
-                   lift, inter, intra);
-    }
+    // zeroed by k_classify: self-mass [n_c] | up_deg [n_c + 1] and low_deg [n_c + 1]
+    Acc* self_mass = lv.self_mass.as<Acc>();
+    int32_t* up_deg = W.up_deg.as<int32_t>();
+    int32_t* low_deg = W.low_deg.as<int32_t>();
+    SPC_LAUNCH(ctx, k_classify, gm, kThreads, 0, m, W.eu.as<int32_t>(), W.ev.as<int32_t>(), lift,
+               inter, intra, reinterpret_cast<uint32_t*>(self_mass),
+               (int64_t)(n_c * sizeof(Acc) / 4), reinterpret_cast<uint32_t*>(up_deg),
+               reinterpret_cast<uint32_t*>(low_deg), (int64_t)(n_c + 1),
+               W.counters.as<int32_t>());
     SPC_TRY(scan_flags_u8(ctx, inter, inter_pos, m));
     SPC_TRY(scan_flags_u8(ctx, intra, intra_pos, m));
     uint64_t* ckey = W.c_key.as<uint64_t>();
@@ -376,8 +395,6 @@ spc_status contract_typed(spc_context* ctx, const GraphView& g, const int32_t* l
     std::unique_ptr<SideBranch> side(new SideBranch(ctx));
     SPC_TRY(side->status());
     // self-mass: runs of equal super-node ids after a stable sort, summed in eid order
-    Acc* self_mass = lv.self_mass.as<Acc>();
-    SPC_CUDA(cudaMemsetAsync(self_mass, 0, (size_t)n_c * sizeof(Acc), ctx->stream));
     SPC_TRY(radix_sort_u32(ctx, ikey, ival, W.i_key2.as<uint32_t>(), W.i_val2.as<uint32_t>(),
                            m_intra, nb));
     if (m_intra > 0) {
@@ -390,7 +407,6 @@ spc_status contract_typed(spc_context* ctx, const GraphView& g, const int32_t* l
         SPC_LAUNCH(ctx, k_heads<uint32_t>, gi, kThreads, 0, m_intra, ikey, ihead);
         SPC_TRY(scan_flags_u8(ctx, ihead, ihpos, m_intra));
         SPC_LAUNCH(ctx, k_run_starts, gi, kThreads, 0, m_intra, ihead, ihpos, istart);
-        SPC_CUDA(cudaMemsetAsync(long_cnt, 0, sizeof(int32_t), ctx->stream));
         int64_t n_runs = 0;
         SPC_TRY(read_i32(ctx, ihpos + m_intra, &n_runs));
         SPC_LAUNCH(ctx, (k_segsum_short<WT, Acc>), grid_for(n_runs, kThreads, maxb), kThreads, 0,
@@ -423,7 +439,6 @@ spc_status contract_typed(spc_context* ctx, const GraphView& g, const int32_t* l
     SPC_LAUNCH(ctx, k_set_i32, 1, 32, 0, seg + m_c, (int32_t)m_inter);
     WT* a_und = lv.a_und.as<WT>();
     if (m_c > 0) {
-        SPC_CUDA(cudaMemsetAsync(long_cnt, 0, sizeof(int32_t), ctx->stream));
         SPC_LAUNCH(ctx, (k_segsum_short<WT, WT>), grid_for(m_c, kThreads, maxb), kThreads, 0,
                    m_c, seg, reinterpret_cast<const uint32_t*>(perm), nullptr, W.w_und.as<WT>(),
                    a_und, long_list, long_cnt, status);
@@ -431,10 +446,7 @@ spc_status contract_typed(spc_context* ctx, const GraphView& g, const int32_t* l
                                             nullptr, W.w_und.as<WT>(), a_und)));
     }
     // coarse CSR
-    int32_t* up_deg = W.up_deg.as<int32_t>();
-    int32_t* low_deg = W.low_deg.as<int32_t>();
-    SPC_CUDA(cudaMemsetAsync(up_deg, 0, (size_t)(n_c + 1) * sizeof(int32_t), ctx->stream));
-    SPC_CUDA(cudaMemsetAsync(low_deg, 0, (size_t)(n_c + 1) * sizeof(int32_t), ctx->stream));
+
     uint32_t* tkey = W.t_key.as<uint32_t>();
     uint32_t* tval = W.t_val.as<uint32_t>();
     if (m_c > 0) {

@@ -106,6 +106,33 @@ __global__ void k_iota(int32_t* a, int64_t n) {
         a[i] = (int32_t)i;
 }
 
+// Start state of the spanning-forest rounds in one launch: parent[i] = i, both parities'
+// best-key slots "none", best-edge slots "none" (64-bit scores), forest flags and merge marks
+// cleared, the two work-list counts zero.
+__global__ void k_bv_init(int64_t n, int64_t m, int32_t* __restrict__ parent,
+                          unsigned long long* __restrict__ bk0, unsigned long long* __restrict__ bk1,
+                          int32_t* __restrict__ be0, int32_t* __restrict__ be1,
+                          uint8_t* __restrict__ msf, uint8_t* __restrict__ merged,
+                          int32_t* __restrict__ counts) {
+    spc::pdl_wait();
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    for (int64_t i = t0; i < n; i += stride) {
+        parent[i] = (int32_t)i;
+        bk0[i] = ~0ull;
+        bk1[i] = ~0ull;
+        if (be0) {
+            be0[i] = INT32_MAX;
+            be1[i] = INT32_MAX;
+        }
+    }
+    for (int64_t e = t0; e <= m; e += stride) {
+        msf[e] = 0;
+        if (merged && e < m) merged[e] = 0;
+    }
+    if (t0 < 2) counts[t0] = 0;
+}
+
 template <class KT> struct MinKey;
 // 64-bit scores: best_k holds the score bits, best_e the smallest edge id among the ties
 template <> struct MinKey<unsigned long long> {
@@ -765,18 +792,14 @@ spc_status select_typed(spc_context* ctx, const GraphView& g, const KT* key,
     int32_t* pos = W.c_pos.as<int32_t>();
     int64_t n_msf = 0;
     for (int attempt = 0; attempt < 2; ++attempt) {
-        SPC_LAUNCH(ctx, k_iota, grid_for(n, kThreads, maxb), kThreads, 0, parent, n);
-        if (merged) SPC_CUDA(cudaMemsetAsync(merged, 0, (size_t)m, ctx->stream));
-        SPC_CUDA(cudaMemsetAsync(W.msf.p, 0, (size_t)(m + 1), ctx->stream));
-        SPC_CUDA(cudaMemsetAsync(W.best_k[0].p, 0xff, (size_t)n * 8, ctx->stream));
-        SPC_CUDA(cudaMemsetAsync(W.best_k[1].p, 0xff, (size_t)n * 8, ctx->stream));
-        if (MinKey<KT>::two_phase) {
-            SPC_CUDA(cudaMemsetAsync(W.best_e[0].p, 0x7f, (size_t)n * 4, ctx->stream));
-            SPC_CUDA(cudaMemsetAsync(W.best_e[1].p, 0x7f, (size_t)n * 4, ctx->stream));
-        }
+        const bool two = MinKey<KT>::two_phase;
+        SPC_LAUNCH(ctx, k_bv_init, grid_for(n > m ? n : m + 1, kThreads, maxb), kThreads, 0, n,
+                   m, parent, W.best_k[0].as<unsigned long long>(),
+                   W.best_k[1].as<unsigned long long>(), two ? W.best_e[0].as<int32_t>() : nullptr,
+                   two ? W.best_e[1].as<int32_t>() : nullptr, W.msf.as<uint8_t>(), merged,
+                   counters);
         // ---- 1. Boruvka minimum spanning forest (of the prefix) ---------------------------
         int64_t cur = m;
-        SPC_CUDA(cudaMemsetAsync(counters, 0, 2 * sizeof(int32_t), ctx->stream));
         for (int round = 0; cur > 0; ++round) {
             const int in = round & 1, out = in ^ 1;
             const int par = round & 1;
