@@ -77,6 +77,14 @@ spc_status ensure(spc_context* ctx, Buf& b, size_t bytes) {
     return SPC_OK;
 }
 
+spc_status ensure_zeroed(spc_context* ctx, Buf& b, size_t bytes) {
+    // a new block can land on the old one's address: compare sizes, not pointers
+    const size_t had = b.p ? b.bytes : 0;
+    SPC_TRY(ensure(ctx, b, bytes));
+    if (b.bytes != had) SPC_CUDA(cudaMemsetAsync(b.p, 0, b.bytes, ctx->stream));
+    return SPC_OK;
+}
+
 void free_all(spc_context* ctx) {
     cudaStreamSynchronize(ctx->stream);
     while (!ctx->blocks.empty()) raw_free(ctx, ctx->blocks.back().p);
@@ -391,11 +399,8 @@ static spc_status reserve_work(spc_context* ctx, int64_t n, int64_t m, int64_t B
     SPC_TRY(ensure(ctx, W.long_segs, (M + 1) * 4));
     // scan of up to max(n, m, 256 * tiles) items -> tile sums; radix histograms
     const size_t big = (N > M ? N : M) + 256 * ((M + 4095) / 4096) + 4096;
-    const void* scan_before = W.scan_tmp.p;
-    SPC_TRY(ensure(ctx, W.scan_tmp, (big / 4096 + 4) * 8 + 256));
     // the scans keep their statuses zero between calls; a new block starts zeroed
-    if (W.scan_tmp.p != scan_before)
-        SPC_CUDA(cudaMemsetAsync(W.scan_tmp.p, 0, W.scan_tmp.bytes, ctx->stream));
+    SPC_TRY(ensure_zeroed(ctx, W.scan_tmp, (big / 4096 + 4) * 8 + 256));
     // one-sweep sort: 8 passes x (tiles x 256) look-back words + histograms
     SPC_TRY(ensure(ctx, W.sort_hist, (8 * 256 * ((M + 4095) / 4096) + 8 * 512 + 64) * 4));
     return SPC_OK;

@@ -212,6 +212,8 @@ private:
 
 // allocation helpers (allocator callback or cudaMalloc)
 spc_status ensure(spc_context* ctx, Buf& b, size_t bytes);
+// ensure(), and zero the block whenever it is (re)allocated
+spc_status ensure_zeroed(spc_context* ctx, Buf& b, size_t bytes);
 void free_all(spc_context* ctx);
 
 // launch accounting + optional timing of selected kernels

@@ -254,7 +254,7 @@ k_key_hist(int64_t m, const KT* __restrict__ key, int shift, uint32_t* __restric
 
 // smallest bin whose cumulative count reaches `need` (all bins when need >= m)
 __global__ void __launch_bounds__(1024)
-k_pick_tau(const uint32_t* __restrict__ hist, int64_t need, uint32_t* __restrict__ tau_top) {
+k_pick_tau(uint32_t* __restrict__ hist, int64_t need, uint32_t* __restrict__ tau_top) {
     spc::pdl_wait();
     __shared__ unsigned long long sh[1024];
     constexpr int kPer = 32768 / 1024;
@@ -280,6 +280,8 @@ k_pick_tau(const uint32_t* __restrict__ hist, int64_t need, uint32_t* __restrict
             }
         }
     }
+    // leave the histogram zero for the next level (only this thread reads its slice)
+    for (int j = 0; j < kPer; ++j) hist[threadIdx.x * kPer + j] = 0;
 }
 
 // Boruvka phase B (64-bit scores only): among the edges whose score equals the component
@@ -681,16 +683,21 @@ k_rsel_unite(int64_t n, const KT* __restrict__ keys, const uint32_t* __restrict_
     }
 }
 
-__global__ void k_rsel_init(SelState* st, unsigned long long k) {
+// selection state, the per-round histograms (`words` of them) and the candidate count
+__global__ void k_rsel_init(SelState* st, unsigned long long k, uint32_t* __restrict__ hist,
+                            int words, int32_t* __restrict__ cand) {
     spc::pdl_wait();
-    if (threadIdx.x == 0) st->need = k;
+    if (threadIdx.x == 0) { st->need = k; *cand = 0; }
     if (threadIdx.x < 16) { st->dig[threadIdx.x] = 0; st->ticket[threadIdx.x] = 0; }
+    for (int i = threadIdx.x; i < words; i += blockDim.x) hist[i] = 0;
 }
 
 // root (= smallest member) of every node and the root flags
 __global__ void __launch_bounds__(kThreads)
-k_roots(int64_t n, int32_t* parent, int32_t* __restrict__ flag, uint32_t* status) {
+k_roots(int64_t n, int32_t* parent, int32_t* __restrict__ flag, int32_t* __restrict__ warn,
+        uint32_t* status) {
     spc::pdl_wait();
+    if (blockIdx.x == 0 && threadIdx.x == 0) *warn = 0;
     for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n;
          x += (int64_t)gridDim.x * blockDim.x) {
         const int32_t r = uf_find(parent, (int32_t)x, status);
@@ -734,12 +741,12 @@ spc_status finish_select(spc_context* ctx, const GraphView& g, const SelectArgs&
     // ---- 3. relabel ------------------------------------------------------------------
     int32_t* flag = W.flag.as<int32_t>();
     int32_t* ids = W.ids.as<int32_t>();
-    SPC_LAUNCH(ctx, k_roots, grid_for(n, kThreads, maxb), kThreads, 0, n, parent2, flag, status);
+    int32_t* warn = counters + 2;
+    SPC_LAUNCH(ctx, k_roots, grid_for(n, kThreads, maxb), kThreads, 0, n, parent2, flag, warn,
+               status);
     SPC_TRY(scan_i32(ctx, flag, ids, n));
     SPC_LAUNCH(ctx, k_lift, grid_for(n, kThreads, maxb), kThreads, 0, n, parent2, ids, lift,
                status);
-    int32_t* warn = counters + 2;
-    SPC_CUDA(cudaMemsetAsync(warn, 0, sizeof(int32_t), ctx->stream));
     if (batched) {
         SPC_LAUNCH(ctx, k_graph_ptr_c, grid_for(sa.B + 1, kThreads, maxb), kThreads, 0, sa.B,
                    sa.d_graph_ptr, ids, sa.d_targets, graph_ptr_c, warn);
@@ -755,6 +762,14 @@ spc_status finish_select(spc_context* ctx, const GraphView& g, const SelectArgs&
     *n_c_out = n_c;
     *status_out = (batched ? warn_b != 0 : n_c > sa.target) ? SPC_WARN_TARGET_NOT_REACHED : SPC_OK;
     return SPC_OK;
+}
+
+// key_hist: the score-prefix histogram (kTauBins words, left zero by k_pick_tau), then the
+// radix-select histograms of every round (zeroed by k_rsel_init); zeroed once on allocation
+constexpr int kTauBins = 32768;
+constexpr size_t kKeyHistBytes = (size_t)(kTauBins + SelBits<uint64_t>::kRounds * kSelBins) * 4;
+static spc_status ensure_key_hist(spc_context* ctx) {
+    return ensure_zeroed(ctx, ctx->work.key_hist, kKeyHistBytes);
 }
 
 template <class KT>
@@ -775,8 +790,7 @@ spc_status select_typed(spc_context* ctx, const GraphView& g, const KT* key,
     uint32_t* tau_top = reinterpret_cast<uint32_t*>(counters + 12);
     bool use_prefix = !batched && m > 65536 && k_need > 0 && (k_need + k_need / 2) < m;
     if (use_prefix) {
-        SPC_TRY(ensure(ctx, W.key_hist, 32768 * 4));
-        SPC_CUDA(cudaMemsetAsync(W.key_hist.p, 0, 32768 * 4, ctx->stream));
+        SPC_TRY(ensure_key_hist(ctx));
         static std::atomic<unsigned long long> attr_devs{0};  // devices already set up
         const unsigned long long bit = 1ull << (ctx->device & 63);
         if (!(attr_devs.load() & bit)) {
@@ -846,22 +860,21 @@ spc_status select_typed(spc_context* ctx, const GraphView& g, const KT* key,
     if (!batched && k_single_sel > 0 && k_single_sel < n_msf) {
         // single graph, proper subset: exact radix select of the k lightest, no sort
         constexpr int R = SelBits<KT>::kRounds;
-        SPC_TRY(ensure(ctx, W.key_hist, 32768 * 4));
-        uint32_t* hist = W.key_hist.as<uint32_t>();
+        SPC_TRY(ensure_key_hist(ctx));
+        uint32_t* hist = W.key_hist.as<uint32_t>() + kTauBins;
         SelState* sst = reinterpret_cast<SelState*>(counters + 16);
-        SPC_CUDA(cudaMemsetAsync(hist, 0, (size_t)R * kSelBins * 4, ctx->stream));
-        SPC_LAUNCH(ctx, k_rsel_init, 1, 32, 0, sst, (unsigned long long)k_single_sel);
+        int32_t* cn = counters + 52;
+        SPC_LAUNCH(ctx, k_rsel_init, 1, 1024, 0, sst, (unsigned long long)k_single_sel, hist,
+                   R * kSelBins, cn);
         const int gsel = grid_for(n_msf, kThreads, ctx->num_sms * 2);
         // two rounds over the whole forest, then the rest over the items still matching
         constexpr int kFull = 2;
         KT* ck = W.sel_key2.as<KT>();
         uint32_t* cv = W.sel_val2.as<uint32_t>();
-        int32_t* cn = counters + 52;
         for (int r = 0; r < kFull; ++r) {
             SPC_LAUNCH(ctx, k_rsel_round<KT>, gsel, kThreads, 0, r, n_msf, nullptr, sk, sv,
                        hist, sst);
         }
-        SPC_CUDA(cudaMemsetAsync(cn, 0, sizeof(int32_t), ctx->stream));
         SPC_LAUNCH(ctx, k_rsel_compact<KT>, gsel, kThreads, 0, kFull - 1, n_msf, sk, sv, sst,
                    ck, cv, cn);
         // few candidates (the usual case): the remaining rounds in one CTA; many (a level

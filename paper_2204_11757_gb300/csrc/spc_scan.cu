@@ -297,9 +297,7 @@ spc_status scan_impl(spc_context* ctx, const In* in, Out* out, int64_t n) {
     // them at its end); zeroed here only when the block is new
     const size_t need = (size_t)(nt + 1) * 8;
     Buf& tmp = on_side(ctx) ? ctx->work.scan_tmp_side : ctx->work.scan_tmp;
-    const void* before = tmp.p;
-    SPC_TRY(ensure(ctx, tmp, need));
-    if (tmp.p != before) SPC_CUDA(cudaMemsetAsync(tmp.p, 0, tmp.bytes, ctx->stream));
+    SPC_TRY(ensure_zeroed(ctx, tmp, need));
     unsigned long long* status = tmp.as<unsigned long long>();
     uint32_t* tile_ctr = reinterpret_cast<uint32_t*>(status + nt);
     note_bytes(ctx, (double)n * (sizeof(In) + sizeof(Out)));  // input read, output written

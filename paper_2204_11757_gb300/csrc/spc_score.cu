@@ -138,8 +138,10 @@ k_long_rows_meta(const int64_t* __restrict__ rowptr, const int32_t* __restrict__
                  const int32_t* __restrict__ long_rows, const int32_t* __restrict__ long_count,
                  typename Tr<WT>::Acc* __restrict__ deg, int32_t* __restrict__ up_cnt,
                  int32_t* __restrict__ nlow_out, int64_t* __restrict__ lr_base,
-                 int64_t* __restrict__ lr_len, int64_t* __restrict__ lr_idx) {
+                 int64_t* __restrict__ lr_len, int64_t* __restrict__ lr_idx,
+                 int32_t* __restrict__ heavy_count) {
     spc::pdl_wait();
+    if (blockIdx.x == 0 && threadIdx.x == 0) *heavy_count = 0;  // for k_score_hub
     const int32_t cnt = *long_count;
     const int lane = threadIdx.x & 31;
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
@@ -765,7 +767,8 @@ static spc_status score_typed(spc_context* ctx, GraphView& g, bool validate, voi
                W.up_cnt.as<int32_t>(), W.first_up.as<int32_t>(), long_rows, long_count, status);
     SPC_LAUNCH(ctx, k_long_rows_meta<WT>, persist, kThreads, 0, g.rowptr, g.col, long_rows,
                long_count, W.deg.as<Acc>(), W.up_cnt.as<int32_t>(), W.first_up.as<int32_t>(),
-               W.lr_base.as<int64_t>(), W.lr_len.as<int64_t>(), W.lr_idx.as<int64_t>());
+               W.lr_base.as<int64_t>(), W.lr_len.as<int64_t>(), W.lr_idx.as<int64_t>(),
+               heavy_count);
     SPC_TRY(scan_i32(ctx, W.up_cnt.as<int32_t>(), W.up_ptr.as<int32_t>(), n));
     // the edge count and the number of long rows
     int64_t sizes[2];
@@ -890,7 +893,6 @@ static spc_status score_typed(spc_context* ctx, GraphView& g, bool validate, voi
     if (n_long == 0) return validate ? check_status(ctx) : SPC_OK;
     side.reset();  // the main stream waits for the tables
     const SeqTabView tv = seqtab_view(W.tab_p, W.lr_base.as<int64_t>(), W.lr_len.as<int64_t>());
-    SPC_CUDA(cudaMemsetAsync(heavy_count, 0, sizeof(int32_t), ctx->stream));
     SPC_LAUNCH(ctx, (k_score_hub<P, Key>), maxb, kThreads, 0, g.rowptr, g.col, W.p.as<P>(),
                W.up_ptr.as<int32_t>(), W.first_up.as<int32_t>(), long_rows, long_count,
                W.lr_eoff.as<int64_t>(), tv, static_cast<Key*>(score), W.heavy.as<int32_t>(),
