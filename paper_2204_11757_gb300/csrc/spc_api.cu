@@ -397,6 +397,10 @@ static spc_status reserve_work(spc_context* ctx, int64_t n, int64_t m, int64_t B
     SPC_TRY(ensure(ctx, W.i_key2, (M + 1) * 4));
     SPC_TRY(ensure(ctx, W.i_val2, (M + 1) * 4));
     SPC_TRY(ensure(ctx, W.long_segs, (M + 1) * 4));
+    SPC_TRY(ensure_zeroed(ctx, W.b_cnt, 2 * N * 4));
+    SPC_TRY(ensure(ctx, W.b_off, 2 * N * 4));
+    SPC_TRY(ensure_zeroed(ctx, W.b_stats, 8 * 8));
+    SPC_TRY(ensure(ctx, W.b_list, (2 * (M / 64 + 1) + 16) * 4));  // long-bucket lists
     // scan of up to max(n, m, 256 * tiles) items -> tile sums; radix histograms
     const size_t big = (N > M ? N : M) + 256 * ((M + 4095) / 4096) + 4096;
     // the scans keep their statuses zero between calls; a new block starts zeroed

@@ -12,6 +12,7 @@
 // coarse-edge order), which leaves every row sorted.
 #include <type_traits>
 
+#include <atomic>
 #include <memory>
 
 #include "spc_seqsum.cuh"
@@ -86,6 +87,254 @@ k_scatter_keys(int64_t m, int nb, const int32_t* __restrict__ eu, const int32_t*
     }
 }
 
+// atomicAdd(cnt + key, 1) by every active lane (all 32 lanes call it): lanes with the same
+// key (the edges of a hub super-node) add their count with one atomic
+__device__ __forceinline__ void warp_count(int32_t* cnt, int32_t key, bool act) {
+    const unsigned peers = __match_any_sync(0xffffffffu, act ? key : -1);
+    if (act && (int)(threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(cnt + key, __popc(peers));
+}
+
+// ---- grouping by buckets --------------------------------------------------------------
+// The coarse edges need the inter edges in (lower super-node a, upper super-node b, eid)
+// order, the self-masses the intra edges in (super-node, eid) order.  Both orders are
+// reached without a global sort: the items are counted per bucket (a for an inter edge, the
+// super-node for an intra edge), scattered into their bucket's range in any order, and each
+// item then moves to its rank within its bucket.  The ranking costs the sum over buckets of
+// the squared bucket size; the host takes this path only while that stays a small multiple
+// of the item count (and every bucket is short), else it sorts by radix.
+
+// Buckets of at most kSmallBucket items: each item is ranked by one thread (at most
+// kSmallBucket comparisons per item).  Longer ones, up to kBlockBucket items: one CTA sorts the
+// bucket in shared memory (bitonic network); they are listed by the counting kernel.
+constexpr int kSmallBucket = 64;
+constexpr int kBlockBucket = 8192;
+constexpr int kBlockSortThreads = 512;
+
+// bucket of fine edge e: (inter, bucket id); one tag per (array, bucket) for warp matching
+__device__ __forceinline__ unsigned long long bucket_tag(int32_t U, int32_t V, bool act) {
+    if (!act) return ~0ull;
+    return U != V ? (1ull << 32) | (uint32_t)(U < V ? U : V) : (2ull << 32) | (uint32_t)U;
+}
+
+// Step 1: the bucket sizes (one atomic per group of equal buckets in a warp), with per block
+// the sum of squared sizes and the largest size, inter buckets in stats[0..1], intra buckets
+// in stats[2..3]; buckets longer than kSmallBucket are listed (counts in stats[6..7]).  Also zeroes what the contraction adds into later: the coarse degree
+// counts and the long-segment list counts of both streams.
+__global__ void __launch_bounds__(kThreads)
+k_bucket_count(int64_t m, const int32_t* __restrict__ eu, const int32_t* __restrict__ ev,
+               const int32_t* __restrict__ lift, int32_t* cnt_c, int32_t* cnt_i,
+               unsigned long long* stats, int32_t* __restrict__ list_c,
+               int32_t* __restrict__ list_i, uint32_t* __restrict__ zero_b,
+               uint32_t* __restrict__ zero_c, int64_t words_bc, int32_t* __restrict__ counters) {
+    spc::pdl_wait();
+    __shared__ unsigned long long sh[4];
+    if (threadIdx.x < 4) sh[threadIdx.x] = 0ull;
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned long long sq[2] = {0ull, 0ull}, mx[2] = {0ull, 0ull};
+    for (int64_t e0 = (int64_t)blockIdx.x * blockDim.x; e0 < m; e0 += stride) {  // warp-uniform
+        const int64_t e = e0 + threadIdx.x;
+        const bool act = e < m;
+        int32_t U = 0, V = 0;
+        if (act) {
+            U = lift[eu[e]];
+            V = lift[ev[e]];
+        }
+        const unsigned long long tag = bucket_tag(U, V, act);
+        const unsigned peers = __match_any_sync(0xffffffffu, tag);
+        if (act && lane == __ffs(peers) - 1) {
+            const int k = __popc(peers);
+            const int side = U != V ? 0 : 1;
+            const int32_t b = (int32_t)(uint32_t)tag;
+            const int32_t old = atomicAdd((side ? cnt_i : cnt_c) + b, k);
+            // (old + k)^2 - old^2: the squares telescope to the final size squared
+            sq[side] += (unsigned long long)k * (2ull * (unsigned long long)old + k);
+            const unsigned long long now = (unsigned long long)old + k;
+            mx[side] = now > mx[side] ? now : mx[side];
+            if (old <= kSmallBucket && now > kSmallBucket)  // the bucket just became long
+                (side ? list_i : list_c)[atomicAdd(stats + 6 + side, 1ull)] = b;
+        }
+    }
+    for (int i = 0; i < 2; ++i) {
+        if (sq[i]) atomicAdd(&sh[2 * i], sq[i]);
+        if (mx[i]) atomicMax(&sh[2 * i + 1], mx[i]);
+    }
+    for (int64_t i = t0; i < words_bc; i += stride) {
+        zero_b[i] = 0u;
+        zero_c[i] = 0u;
+    }
+    if (t0 == 0) {
+        counters[9] = 0;
+        counters[11] = 0;
+        stats[4] = 0ull;  // the lower rows' statistics, added by k_emit_segments
+        stats[5] = 0ull;
+    }
+    __syncthreads();
+    if (threadIdx.x < 4 && sh[threadIdx.x]) {
+        if (threadIdx.x & 1) atomicMax(stats + threadIdx.x, sh[threadIdx.x]);
+        else atomicAdd(stats + threadIdx.x, sh[threadIdx.x]);
+    }
+}
+
+// Step 2 (after the exclusive scans off_c, off_i of the sizes): every edge takes a slot of
+// its bucket by counting the bucket's size down, which leaves the counts zero for the next
+// call; the statistics (already read by the host) are zeroed too.  Inter edges store the key
+// (a << nb) | b and their eid, intra edges the super-node and their eid (emap -1).
+__global__ void __launch_bounds__(kThreads)
+k_bucket_scatter(int64_t m, int nb, const int32_t* __restrict__ eu,
+                 const int32_t* __restrict__ ev, const int32_t* __restrict__ lift,
+                 const int32_t* __restrict__ off_c, const int32_t* __restrict__ off_i,
+                 int32_t* cnt_c, int32_t* cnt_i, unsigned long long* __restrict__ stats,
+                 uint64_t* __restrict__ ckey, uint32_t* __restrict__ cval,
+                 uint32_t* __restrict__ ikey, uint32_t* __restrict__ ival,
+                 int32_t* __restrict__ emap) {
+    spc::pdl_wait();
+    if (blockIdx.x == 0 && threadIdx.x < 4) stats[threadIdx.x] = 0ull;
+    const int lane = threadIdx.x & 31;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t e0 = (int64_t)blockIdx.x * blockDim.x; e0 < m; e0 += stride) {  // warp-uniform
+        const int64_t e = e0 + threadIdx.x;
+        const bool act = e < m;
+        int32_t U = 0, V = 0;
+        if (act) {
+            U = lift[eu[e]];
+            V = lift[ev[e]];
+        }
+        const unsigned long long tag = bucket_tag(U, V, act);
+        const unsigned peers = __match_any_sync(0xffffffffu, tag);
+        const int leader = __ffs(peers) - 1;
+        const bool inter = U != V;
+        const int32_t b = (int32_t)(uint32_t)tag;
+        int32_t old = 0;
+        if (act && lane == leader) old = atomicSub((inter ? cnt_c : cnt_i) + b, __popc(peers));
+        old = __shfl_sync(0xffffffffu, old, leader);
+        if (!act) continue;
+        const int below = __popc(peers & ((1u << lane) - 1u));
+        const int32_t q = (inter ? off_c : off_i)[b] + old - 1 - below;
+        if (inter) {
+            const uint64_t hi = (uint64_t)(U < V ? V : U);
+            ckey[q] = ((uint64_t)b << nb) | hi;
+            cval[q] = (uint32_t)e;
+        } else {
+            ikey[q] = (uint32_t)U;
+            ival[q] = (uint32_t)e;
+            emap[e] = -1;
+        }
+    }
+}
+
+// Step 3, long buckets (listed by k_bucket_count): one CTA per bucket sorts the bucket's
+// items in shared memory by one 64-bit key -- (b << 32) | eid for inter edges (a is the
+// bucket), the eid for intra edges -- with a bitonic network over the next power of two
+// (padding keys all ones), then writes them back in order: inter edges as (key, eid) with
+// their head flags, intra edges as eids.
+template <bool kInter>
+__global__ void __launch_bounds__(kBlockSortThreads)
+k_bucket_sort_long(const int32_t* __restrict__ list, const unsigned long long* __restrict__ list_cnt,
+                   const int32_t* __restrict__ off, int nb, const uint64_t* __restrict__ key,
+                   const uint32_t* __restrict__ val, uint64_t* __restrict__ key2,
+                   uint32_t* __restrict__ val2, uint8_t* __restrict__ head) {
+    spc::pdl_wait();
+    extern __shared__ unsigned long long sk[];  // kBlockBucket keys
+    const int64_t cnt = (int64_t)*list_cnt;
+    const uint64_t bmask = (1ull << nb) - 1ull;
+    for (int64_t q = blockIdx.x; q < cnt; q += gridDim.x) {
+        const int32_t bkt = list[q];
+        const int32_t lo = off[bkt];
+        const int s = off[bkt + 1] - lo;  // kSmallBucket < s <= kBlockBucket (host checked)
+        int P = 1;
+        while (P < s) P <<= 1;
+        for (int i = threadIdx.x; i < P; i += blockDim.x) {
+            unsigned long long k = ~0ull;
+            if (i < s) {
+                if constexpr (kInter) k = ((key[lo + i] & bmask) << 32) | val[lo + i];
+                else k = val[lo + i];
+            }
+            sk[i] = k;
+        }
+        __syncthreads();
+        for (int len = 2; len <= P; len <<= 1) {
+            for (int j = len >> 1; j > 0; j >>= 1) {
+                for (int t = threadIdx.x; t < (P >> 1); t += blockDim.x) {
+                    const int i = ((t & ~(j - 1)) << 1) | (t & (j - 1));  // bit j of i is 0
+                    const unsigned long long x = sk[i], y = sk[i + j];
+                    const bool up = (i & len) == 0;
+                    if ((x > y) == up) {
+                        sk[i] = y;
+                        sk[i + j] = x;
+                    }
+                }
+                __syncthreads();
+            }
+        }
+        for (int i = threadIdx.x; i < s; i += blockDim.x) {
+            const unsigned long long k = sk[i];
+            if constexpr (kInter) {
+                const uint64_t b = k >> 32;
+                key2[lo + i] = ((uint64_t)bkt << nb) | b;
+                val2[lo + i] = (uint32_t)k;
+                head[lo + i] = (i == 0 || (sk[i - 1] >> 32) != b) ? 1 : 0;
+            } else {
+                val2[lo + i] = (uint32_t)k;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// Step 3, inter edges in short buckets: the item at p goes to its rank by (key, eid) within
+// its bucket [off_c[a], off_c[a + 1]); head marks the first item (smallest eid) of every
+// coarse edge.  Runs after k_bucket_sort_long, whose list it then empties.
+__global__ void __launch_bounds__(kThreads)
+k_bucket_rank_inter(int64_t cnt, int nb, const int32_t* __restrict__ off_c,
+                    const uint64_t* __restrict__ key, const uint32_t* __restrict__ val,
+                    uint64_t* __restrict__ key2, uint32_t* __restrict__ val2,
+                    uint8_t* __restrict__ head, unsigned long long* __restrict__ list_cnt) {
+    spc::pdl_wait();
+    if (blockIdx.x == 0 && threadIdx.x == 0) *list_cnt = 0ull;  // long buckets are sorted
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < cnt;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t k = key[p];
+        const uint32_t v = val[p];
+        const int64_t a = (int64_t)(k >> nb);
+        const int32_t lo = off_c[a], hi = off_c[a + 1];
+        if (hi - lo > kSmallBucket) continue;
+        int32_t r = 0;
+        bool first = true;
+        for (int32_t j = lo; j < hi; ++j) {
+            const uint64_t kj = key[j];
+            const uint32_t vj = val[j];
+            const bool same_before = kj == k && vj < v;
+            r += (kj < k || same_before) ? 1 : 0;
+            first = first && !same_before;
+        }
+        key2[lo + r] = k;
+        val2[lo + r] = v;
+        head[lo + r] = first ? 1 : 0;
+    }
+}
+
+// Step 3, intra edges in short buckets: the eid at p goes to its rank within its super-node's
+// bucket.  Runs after k_bucket_sort_long, whose list it then empties.
+__global__ void __launch_bounds__(kThreads)
+k_bucket_rank_intra(int64_t cnt, const int32_t* __restrict__ off_i,
+                    const uint32_t* __restrict__ ikey, const uint32_t* __restrict__ ival,
+                    uint32_t* __restrict__ ival2, unsigned long long* __restrict__ list_cnt) {
+    spc::pdl_wait();
+    if (blockIdx.x == 0 && threadIdx.x == 0) *list_cnt = 0ull;  // long buckets are sorted
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < cnt;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t U = ikey[p], v = ival[p];
+        const int32_t lo = off_i[U], hi = off_i[U + 1];
+        if (hi - lo > kSmallBucket) continue;
+        int32_t r = 0;
+        for (int32_t j = lo; j < hi; ++j) r += ival[j] < v ? 1 : 0;
+        ival2[lo + r] = v;
+    }
+}
+
 __global__ void k_set_i32(int32_t* p, int32_t v) {
     spc::pdl_wait();
     if (threadIdx.x == 0) *p = v;
@@ -100,27 +349,58 @@ k_heads(int64_t cnt, const K* __restrict__ key, uint8_t* __restrict__ head) {
         head[i] = (i == 0 || key[i] != key[i - 1]) ? 1 : 0;
 }
 
-// coarse edge id of every sorted item; emap, perm; segment starts and end points at heads
+// coarse edge id of every sorted item; emap, perm; segment starts and end points at heads.
+// Every coarse edge (U, V) also counts into up_deg[U] and low_deg[V]; the lower rows (buckets
+// by V) get their ranking statistics in stats[0] (sum of squared sizes), stats[1] (largest).
 __global__ void __launch_bounds__(kThreads)
 k_emit_segments(int64_t cnt, int nb, const uint64_t* __restrict__ key,
                 const uint32_t* __restrict__ val, const uint8_t* __restrict__ head,
                 const int32_t* __restrict__ hpos, int32_t* __restrict__ emap,
                 int32_t* __restrict__ perm, int32_t* __restrict__ seg, int32_t* __restrict__ cU,
-                int32_t* __restrict__ cV) {
+                int32_t* __restrict__ cV, int32_t* up_deg, int32_t* low_deg,
+                unsigned long long* stats) {
     spc::pdl_wait();
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cnt;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const int32_t ce = hpos[i] + head[i] - 1;
-        const uint32_t e = val[i];
-        emap[e] = ce;
-        perm[i] = (int32_t)e;
-        if (head[i]) {
-            seg[ce] = (int32_t)i;
-            const uint64_t k = key[i];
-            cU[ce] = (int32_t)(k >> nb);
-            cV[ce] = (int32_t)(k & ((1ull << nb) - 1ull));
+    __shared__ unsigned long long sh[2];
+    if (threadIdx.x < 2) sh[threadIdx.x] = 0ull;
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    unsigned long long sq = 0ull, mx = 0ull;
+    for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x; i0 < cnt;
+         i0 += (int64_t)gridDim.x * blockDim.x) {  // warp-uniform
+        const int64_t i = i0 + threadIdx.x;
+        const bool act = i < cnt;
+        bool h = false;
+        int32_t U = 0, V = 0;
+        if (act) {
+            const int32_t ce = hpos[i] + head[i] - 1;
+            const uint32_t e = val[i];
+            emap[e] = ce;
+            perm[i] = (int32_t)e;
+            h = head[i] != 0;
+            if (h) {
+                seg[ce] = (int32_t)i;
+                const uint64_t k = key[i];
+                U = (int32_t)(k >> nb);
+                V = (int32_t)(k & ((1ull << nb) - 1ull));
+                cU[ce] = U;
+                cV[ce] = V;
+            }
+        }
+        warp_count(up_deg, U, h);
+        const unsigned peers = __match_any_sync(0xffffffffu, h ? V : -1);
+        if (h && lane == __ffs(peers) - 1) {
+            const int k = __popc(peers);
+            const int32_t old = atomicAdd(low_deg + V, k);
+            sq += (unsigned long long)k * (2ull * (unsigned long long)old + k);
+            const unsigned long long now = (unsigned long long)old + k;
+            mx = now > mx ? now : mx;
         }
     }
+    if (sq) atomicAdd(&sh[0], sq);
+    if (mx) atomicMax(&sh[1], mx);
+    __syncthreads();
+    if (threadIdx.x == 0 && sh[0]) atomicAdd(stats, sh[0]);
+    if (threadIdx.x == 1 && sh[1]) atomicMax(stats + 1, sh[1]);
 }
 
 // run r of a sorted key array starts at start[r]; start[n_runs] = cnt
@@ -224,29 +504,59 @@ k_gather_long_terms(const int32_t* __restrict__ long_list, const int32_t* __rest
     }
 }
 
-// atomicAdd(cnt + key, 1) by every active lane (all 32 lanes call it): lanes with the same
-// key (the edges of a hub super-node) add their count with one atomic
-__device__ __forceinline__ void warp_count(int32_t* cnt, int32_t key, bool act) {
-    const unsigned peers = __match_any_sync(0xffffffffu, act ? key : -1);
-    if (act && (int)(threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(cnt + key, __popc(peers));
+// lower rows by radix sort: key V, value the coarse edge id
+__global__ void __launch_bounds__(kThreads)
+k_transpose_keys(int64_t m_c, const int32_t* __restrict__ cV, uint32_t* __restrict__ tkey,
+                 uint32_t* __restrict__ tval) {
+    spc::pdl_wait();
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < m_c;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        tkey[k] = (uint32_t)cV[k];
+        tval[k] = (uint32_t)k;
+    }
 }
 
+// lower rows by buckets, step 1: coarse edge k takes a slot of row V's lower range by counting
+// low_deg[V] down (zero afterwards)
 __global__ void __launch_bounds__(kThreads)
-k_degree_counts(int64_t m_c, const int32_t* __restrict__ cU, const int32_t* __restrict__ cV,
-                int32_t* up_deg, int32_t* low_deg, uint32_t* __restrict__ tkey,
-                uint32_t* __restrict__ tval) {
+k_lower_scatter(int64_t m_c, const int32_t* __restrict__ cV, const int32_t* __restrict__ lstart,
+                int32_t* low_deg, uint32_t* __restrict__ slot) {
     spc::pdl_wait();
+    const int lane = threadIdx.x & 31;
     for (int64_t k0 = (int64_t)blockIdx.x * blockDim.x; k0 < m_c;
-         k0 += (int64_t)gridDim.x * blockDim.x) {  // uniform per warp
+         k0 += (int64_t)gridDim.x * blockDim.x) {  // warp-uniform
         const int64_t k = k0 + threadIdx.x;
         const bool act = k < m_c;
-        const int32_t u = act ? cU[k] : 0, v = act ? cV[k] : 0;
-        warp_count(up_deg, u, act);
-        warp_count(low_deg, v, act);
-        if (act) {
-            tkey[k] = (uint32_t)v;
-            tval[k] = (uint32_t)k;
-        }
+        const int32_t V = act ? cV[k] : -1;
+        const unsigned peers = __match_any_sync(0xffffffffu, V);
+        const int leader = __ffs(peers) - 1;
+        int32_t old = 0;
+        if (act && lane == leader) old = atomicSub(low_deg + V, __popc(peers));
+        old = __shfl_sync(0xffffffffu, old, leader);
+        if (act) slot[lstart[V] + old - 1 - __popc(peers & ((1u << lane) - 1u))] = (uint32_t)k;
+    }
+}
+
+// lower rows by buckets, step 2: coarse edge k = (U, V) at slot p goes to its rank by k (the
+// order of U) within row V's lower part
+template <class WT>
+__global__ void __launch_bounds__(kThreads)
+k_fill_lower_ranked(int64_t m_c, const uint32_t* __restrict__ slot,
+                    const int32_t* __restrict__ lstart, const int64_t* __restrict__ rowptr_c,
+                    const int32_t* __restrict__ cU, const int32_t* __restrict__ cV,
+                    const WT* __restrict__ a_und, int32_t* __restrict__ col_c,
+                    WT* __restrict__ w_c) {
+    spc::pdl_wait();
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < m_c;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t k = slot[p];
+        const int32_t V = cV[k];
+        const int32_t lo = lstart[V], hi = lstart[V + 1];
+        int32_t r = 0;
+        for (int32_t j = lo; j < hi; ++j) r += slot[j] < k ? 1 : 0;
+        const int64_t pos = rowptr_c[V] + r;
+        col_c[pos] = cU[k];
+        w_c[pos] = a_und[k];
     }
 }
 
@@ -280,14 +590,15 @@ k_fill_lower(int64_t m_c, const uint32_t* __restrict__ tkey, const uint32_t* __r
 template <class WT>
 __global__ void __launch_bounds__(kThreads)
 k_fill_upper(int64_t m_c, const int32_t* __restrict__ cU, const int32_t* __restrict__ cV,
-             const int32_t* __restrict__ ufirst, const int32_t* __restrict__ low_deg,
-             const int64_t* __restrict__ rowptr_c, const WT* __restrict__ a_und,
+             const int32_t* __restrict__ lstart, const WT* __restrict__ a_und,
              int32_t* __restrict__ col_c, WT* __restrict__ w_c) {
     spc::pdl_wait();
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < m_c;
          k += (int64_t)gridDim.x * blockDim.x) {
+        // row U starts at ufirst[U] + lstart[U]; its lower part has lstart[U+1] - lstart[U]
+        // entries, then its upper entries in coarse-edge order from k = ufirst[U]
         const int32_t U = cU[k];
-        const int64_t pos = rowptr_c[U] + low_deg[U] + (k - ufirst[U]);
+        const int64_t pos = (int64_t)lstart[U + 1] + k;
         col_c[pos] = cV[k];
         w_c[pos] = a_und[k];
     }
@@ -343,6 +654,39 @@ spc_status long_segment_sums(spc_context* ctx, const int32_t* start, const uint3
     }
 }
 
+// The lower rows of the coarse CSR take the bucket path while every row holds at most
+// kRankMax lower entries and the ranking work (the sum of squared row sizes) is at most
+// kRankWork per coarse edge; the inter and intra buckets while none is longer than
+// kBlockBucket.
+constexpr int64_t kRankMax = 1024;
+constexpr int64_t kRankWork = 48;
+
+// one CTA per long bucket, each with kBlockBucket keys of shared memory
+static spc_status sort_long_buckets(spc_context* ctx, bool inter, const int32_t* list,
+                                    const unsigned long long* list_cnt, const int32_t* off,
+                                    int nb, const uint64_t* key, const uint32_t* val,
+                                    uint64_t* key2, uint32_t* val2, uint8_t* head) {
+    constexpr int smem = kBlockBucket * 8;
+    static std::atomic<unsigned long long> attr_devs{0};  // devices already set up
+    const unsigned long long bit = 1ull << (ctx->device & 63);
+    if (!(attr_devs.load() & bit)) {
+        SPC_CUDA(cudaFuncSetAttribute(k_bucket_sort_long<true>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        SPC_CUDA(cudaFuncSetAttribute(k_bucket_sort_long<false>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        attr_devs.fetch_or(bit);
+    }
+    const int grid = ctx->num_sms * 3;
+    if (inter) {
+        SPC_LAUNCH(ctx, k_bucket_sort_long<true>, grid, kBlockSortThreads, smem, list, list_cnt,
+                   off, nb, key, val, key2, val2, head);
+    } else {
+        SPC_LAUNCH(ctx, k_bucket_sort_long<false>, grid, kBlockSortThreads, smem, list, list_cnt,
+                   off, nb, key, val, key2, val2, head);
+    }
+    return SPC_OK;
+}
+
 template <class WT>
 spc_status contract_typed(spc_context* ctx, const GraphView& g, const int32_t* lift,
                           int64_t n_c, LevelBufs& lv) {
@@ -353,39 +697,75 @@ spc_status contract_typed(spc_context* ctx, const GraphView& g, const int32_t* l
     uint32_t* status = ctx->d_status;
     int nb = 1;
     while ((1ll << nb) < n_c) ++nb;
-    uint8_t* inter = W.c_flag.as<uint8_t>();
-    uint8_t* intra = inter + (m + 1);
-    int32_t* inter_pos = W.c_pos.as<int32_t>();
-    int32_t* intra_pos = W.c_head.as<int32_t>();
     const int gm = grid_for(m, kThreads, maxb);
-    // zeroed by k_classify: self-mass [n_c] | up_deg [n_c + 1] and low_deg [n_c + 1]
     Acc* self_mass = lv.self_mass.as<Acc>();
     int32_t* up_deg = W.up_deg.as<int32_t>();
     int32_t* low_deg = W.low_deg.as<int32_t>();
-    SPC_LAUNCH(ctx, k_classify, gm, kThreads, 0, m, W.eu.as<int32_t>(), W.ev.as<int32_t>(), lift,
-               inter, intra, reinterpret_cast<uint32_t*>(self_mass),
-               (int64_t)(n_c * sizeof(Acc) / 4), reinterpret_cast<uint32_t*>(up_deg),
-               reinterpret_cast<uint32_t*>(low_deg), (int64_t)(n_c + 1),
-               W.counters.as<int32_t>());
-    SPC_TRY(scan_flags_u8(ctx, inter, inter_pos, m));
-    SPC_TRY(scan_flags_u8(ctx, intra, intra_pos, m));
     uint64_t* ckey = W.c_key.as<uint64_t>();
     uint32_t* cval = W.c_val.as<uint32_t>();
     uint32_t* ikey = W.i_key.as<uint32_t>();
     uint32_t* ival = W.i_val.as<uint32_t>();
     int32_t* emap = lv.emap.as<int32_t>();
-    if (m > 0) {
-        SPC_LAUNCH(ctx, k_scatter_keys, gm, kThreads, 0, m, nb, W.eu.as<int32_t>(),
-                   W.ev.as<int32_t>(), lift, inter_pos, intra_pos, ckey, cval, ikey, ival, emap);
+    // ---- bucket sizes, offsets and ranking work ------------------------------------------
+    // the counts are zero between calls (the scatter counts them down); a call that stopped
+    // in between leaves them dirty
+    int32_t* cnt_c = W.b_cnt.as<int32_t>();
+    int32_t* cnt_i = cnt_c + (n_c + 1);
+    int32_t* off_c = W.b_off.as<int32_t>();
+    int32_t* off_i = off_c + (n_c + 1);
+    unsigned long long* bstats = W.b_stats.as<unsigned long long>();
+    int32_t* list_c = W.b_list.as<int32_t>();  // long buckets (at most m / kSmallBucket each)
+    int32_t* list_i = list_c + (m / kSmallBucket + 1);
+    if (W.b_dirty) {
+        SPC_CUDA(cudaMemsetAsync(W.b_cnt.p, 0, W.b_cnt.bytes, ctx->stream));
+        SPC_CUDA(cudaMemsetAsync(W.b_stats.p, 0, W.b_stats.bytes, ctx->stream));
     }
-    int64_t cnts[2];
+    W.b_dirty = true;
+    SPC_LAUNCH(ctx, k_bucket_count, gm, kThreads, 0, m, W.eu.as<int32_t>(), W.ev.as<int32_t>(),
+               lift, cnt_c, cnt_i, bstats, list_c, list_i, reinterpret_cast<uint32_t*>(up_deg),
+               reinterpret_cast<uint32_t*>(low_deg), (int64_t)(n_c + 1),
+               W.counters.as<int32_t>());
+    SPC_TRY(scan_i32(ctx, cnt_c, off_c, n_c));
+    SPC_TRY(scan_i32(ctx, cnt_i, off_i, n_c));
+    int64_t bv[8];
     {
-        const void* ptrs[2] = {inter_pos + m, intra_pos + m};
-        const int bytes[2] = {4, 4};
-        SPC_TRY(read_vals(ctx, 2, ptrs, bytes, cnts));
+        const void* ptrs[8] = {off_c + n_c, off_i + n_c, bstats, bstats + 1, bstats + 2,
+                               bstats + 3, bstats + 6, bstats + 7};
+        const int bytes[8] = {4, 4, 8, 8, 8, 8, 8, 8};
+        SPC_TRY(read_vals(ctx, 8, ptrs, bytes, bv));
     }
-    const int64_t m_inter = cnts[0];
-    const int64_t m_intra = cnts[1];
+    const int64_t long_c = bv[6], long_i = bv[7];  // buckets longer than kSmallBucket
+    const int64_t m_inter = bv[0];
+    const int64_t m_intra = bv[1];
+    const bool buckets = bv[3] <= kBlockBucket && bv[5] <= kBlockBucket;
+    if (buckets) {
+        if (m > 0) {
+            SPC_LAUNCH(ctx, k_bucket_scatter, gm, kThreads, 0, m, nb, W.eu.as<int32_t>(),
+                       W.ev.as<int32_t>(), lift, off_c, off_i, cnt_c, cnt_i, bstats, ckey, cval,
+                       ikey, ival, emap);
+        }
+    } else {
+        SPC_CUDA(cudaMemsetAsync(cnt_c, 0, (size_t)(n_c + 1) * 8, ctx->stream));
+        SPC_CUDA(cudaMemsetAsync(W.b_stats.p, 0, W.b_stats.bytes, ctx->stream));
+        // radix path: compaction by flag scans (self-mass zeroed here, all its sums add in)
+        uint8_t* inter = W.c_flag.as<uint8_t>();
+        uint8_t* intra = inter + (m + 1);
+        int32_t* inter_pos = W.c_pos.as<int32_t>();
+        int32_t* intra_pos = W.c_head.as<int32_t>();
+        SPC_LAUNCH(ctx, k_classify, gm, kThreads, 0, m, W.eu.as<int32_t>(), W.ev.as<int32_t>(),
+                   lift, inter, intra, reinterpret_cast<uint32_t*>(self_mass),
+                   (int64_t)(n_c * sizeof(Acc) / 4), reinterpret_cast<uint32_t*>(up_deg),
+                   reinterpret_cast<uint32_t*>(low_deg), (int64_t)(n_c + 1),
+                   W.counters.as<int32_t>());
+        SPC_TRY(scan_flags_u8(ctx, inter, inter_pos, m));
+        SPC_TRY(scan_flags_u8(ctx, intra, intra_pos, m));
+        if (m > 0) {
+            SPC_LAUNCH(ctx, k_scatter_keys, gm, kThreads, 0, m, nb, W.eu.as<int32_t>(),
+                       W.ev.as<int32_t>(), lift, inter_pos, intra_pos, ckey, cval, ikey, ival,
+                       emap);
+        }
+    }
+    W.b_dirty = false;
     // The self-mass (intra edges) and the coarse edges are independent from here: the
     // self-mass runs on the second stream with its own temporaries, the coarse edges here.
     SPC_TRY(ensure(ctx, W.long_segs_side, (size_t)(m + 1) * 4));
@@ -394,47 +774,89 @@ spc_status contract_typed(spc_context* ctx, const GraphView& g, const int32_t* l
     SPC_TRY(ensure(ctx, W.seg_idx_side, (size_t)(m + 1) * 8));
     std::unique_ptr<SideBranch> side(new SideBranch(ctx));
     SPC_TRY(side->status());
-    // self-mass: runs of equal super-node ids after a stable sort, summed in eid order
-    SPC_TRY(radix_sort_u32(ctx, ikey, ival, W.i_key2.as<uint32_t>(), W.i_val2.as<uint32_t>(),
-                           m_intra, nb));
-    if (m_intra > 0) {
-        int32_t* long_list = W.long_segs_side.as<int32_t>();
-        int32_t* long_cnt = W.counters.as<int32_t>() + 11;
-        uint8_t* ihead = W.c_flag.as<uint8_t>() + (m + 1);  // intra flags are consumed
-        int32_t* ihpos = W.c_head.as<int32_t>();
-        int32_t* istart = W.i_key2.as<int32_t>();           // sort scratch is free again
-        const int gi = grid_for(m_intra, kThreads, maxb);
-        SPC_LAUNCH(ctx, k_heads<uint32_t>, gi, kThreads, 0, m_intra, ikey, ihead);
-        SPC_TRY(scan_flags_u8(ctx, ihead, ihpos, m_intra));
-        SPC_LAUNCH(ctx, k_run_starts, gi, kThreads, 0, m_intra, ihead, ihpos, istart);
-        int64_t n_runs = 0;
-        SPC_TRY(read_i32(ctx, ihpos + m_intra, &n_runs));
-        SPC_LAUNCH(ctx, (k_segsum_short<WT, Acc>), grid_for(n_runs, kThreads, maxb), kThreads, 0,
-                   n_runs, istart, ival, ikey, W.w_und.as<WT>(), self_mass, long_list, long_cnt,
-                   status);
-        SPC_TRY((long_segment_sums<WT, Acc>(ctx, istart, ival, ikey, W.w_und.as<WT>(),
+    if (buckets) {
+        // self-mass of super-node U: its bucket, in eid order (empty buckets give zero)
+        uint32_t* ival2 = W.i_val2.as<uint32_t>();
+        if (m_intra > 0) {
+            if (long_i > 0)
+                SPC_TRY(sort_long_buckets(ctx, false, list_i, bstats + 7, off_i, nb, nullptr,
+                                          ival, nullptr, ival2, nullptr));
+            SPC_LAUNCH(ctx, k_bucket_rank_intra, grid_for(m_intra, kThreads, maxb), kThreads, 0,
+                       m_intra, off_i, ikey, ival, ival2, bstats + 7);
+        }
+        SPC_LAUNCH(ctx, (k_segsum_short<WT, Acc>), grid_for(n_c, kThreads, maxb), kThreads, 0,
+                   n_c, off_i, ival2, nullptr, W.w_und.as<WT>(), self_mass,
+                   W.long_segs_side.as<int32_t>(), W.counters.as<int32_t>() + 11, status);
+        SPC_TRY((long_segment_sums<WT, Acc>(ctx, off_i, ival2, nullptr, W.w_und.as<WT>(),
                                              self_mass)));
+    } else {
+        // self-mass: runs of equal super-node ids after a stable sort, summed in eid order
+        SPC_TRY(radix_sort_u32(ctx, ikey, ival, W.i_key2.as<uint32_t>(),
+                               W.i_val2.as<uint32_t>(), m_intra, nb));
+        if (m_intra > 0) {
+            int32_t* long_list = W.long_segs_side.as<int32_t>();
+            int32_t* long_cnt = W.counters.as<int32_t>() + 11;
+            uint8_t* ihead = W.c_flag.as<uint8_t>() + (m + 1);  // intra flags are consumed
+            int32_t* ihpos = W.c_head.as<int32_t>();
+            int32_t* istart = W.i_key2.as<int32_t>();           // sort scratch is free again
+            const int gi = grid_for(m_intra, kThreads, maxb);
+            SPC_LAUNCH(ctx, k_heads<uint32_t>, gi, kThreads, 0, m_intra, ikey, ihead);
+            SPC_TRY(scan_flags_u8(ctx, ihead, ihpos, m_intra));
+            SPC_LAUNCH(ctx, k_run_starts, gi, kThreads, 0, m_intra, ihead, ihpos, istart);
+            int64_t n_runs = 0;
+            SPC_TRY(read_i32(ctx, ihpos + m_intra, &n_runs));
+            SPC_LAUNCH(ctx, (k_segsum_short<WT, Acc>), grid_for(n_runs, kThreads, maxb),
+                       kThreads, 0, n_runs, istart, ival, ikey, W.w_und.as<WT>(), self_mass,
+                       long_list, long_cnt, status);
+            SPC_TRY((long_segment_sums<WT, Acc>(ctx, istart, ival, ikey, W.w_und.as<WT>(),
+                                                 self_mass)));
+        }
     }
     side->leave();
-    // coarse edges
+    // coarse edges: the inter edges in (a, b, eid) order with a head flag per coarse edge
     int32_t* long_list = W.long_segs.as<int32_t>();
     int32_t* long_cnt = W.counters.as<int32_t>() + 9;
-    SPC_TRY(radix_sort_u64(ctx, ckey, cval, W.c_key2.as<uint64_t>(), W.c_val2.as<uint32_t>(),
-                           m_inter, 2 * nb));
     uint8_t* head = W.c_flag.as<uint8_t>();  // flags are consumed; reuse as heads
     int32_t* hpos = W.c_pos.as<int32_t>();
+    const uint64_t* skey = ckey;
+    const uint32_t* sval = cval;
+    if (buckets) {
+        if (m_inter > 0) {
+            if (long_c > 0)
+                SPC_TRY(sort_long_buckets(ctx, true, list_c, bstats + 6, off_c, nb, ckey, cval,
+                                          W.c_key2.as<uint64_t>(), W.c_val2.as<uint32_t>(),
+                                          head));
+            SPC_LAUNCH(ctx, k_bucket_rank_inter, grid_for(m_inter, kThreads, maxb), kThreads, 0,
+                       m_inter, nb, off_c, ckey, cval, W.c_key2.as<uint64_t>(),
+                       W.c_val2.as<uint32_t>(), head, bstats + 6);
+        }
+        skey = W.c_key2.as<uint64_t>();
+        sval = W.c_val2.as<uint32_t>();
+    } else {
+        SPC_TRY(radix_sort_u64(ctx, ckey, cval, W.c_key2.as<uint64_t>(), W.c_val2.as<uint32_t>(),
+                               m_inter, 2 * nb));
+        if (m_inter > 0) {
+            SPC_LAUNCH(ctx, k_heads<uint64_t>, grid_for(m_inter, kThreads, maxb), kThreads, 0,
+                       m_inter, ckey, head);
+        }
+    }
     int32_t* seg = lv.seg.as<int32_t>();
     int32_t* perm = lv.perm.as<int32_t>();
     int32_t* cU = W.cU.as<int32_t>();
     int32_t* cV = W.cV.as<int32_t>();
     int64_t m_c = 0;
+    bool lower_buckets = true;
     if (m_inter > 0) {
         const int gi = grid_for(m_inter, kThreads, maxb);
-        SPC_LAUNCH(ctx, k_heads<uint64_t>, gi, kThreads, 0, m_inter, ckey, head);
         SPC_TRY(scan_flags_u8(ctx, head, hpos, m_inter));
-        SPC_LAUNCH(ctx, k_emit_segments, gi, kThreads, 0, m_inter, nb, ckey, cval, head, hpos,
-                   emap, perm, seg, cU, cV);
-        SPC_TRY(read_i32(ctx, hpos + m_inter, &m_c));
+        SPC_LAUNCH(ctx, k_emit_segments, gi, kThreads, 0, m_inter, nb, skey, sval, head, hpos,
+                   emap, perm, seg, cU, cV, up_deg, low_deg, bstats + 4);
+        int64_t ev[3];
+        const void* ptrs[3] = {hpos + m_inter, bstats + 4, bstats + 5};
+        const int bytes[3] = {4, 8, 8};
+        SPC_TRY(read_vals(ctx, 3, ptrs, bytes, ev));
+        m_c = ev[0];
+        lower_buckets = ev[2] <= kRankMax && ev[1] <= kRankWork * m_c;
     }
     SPC_LAUNCH(ctx, k_set_i32, 1, 32, 0, seg + m_c, (int32_t)m_inter);
     WT* a_und = lv.a_und.as<WT>();
@@ -445,14 +867,8 @@ spc_status contract_typed(spc_context* ctx, const GraphView& g, const int32_t* l
         SPC_TRY((long_segment_sums<WT, WT>(ctx, seg, reinterpret_cast<const uint32_t*>(perm),
                                             nullptr, W.w_und.as<WT>(), a_und)));
     }
-    // coarse CSR
-
-    uint32_t* tkey = W.t_key.as<uint32_t>();
-    uint32_t* tval = W.t_val.as<uint32_t>();
-    if (m_c > 0) {
-        SPC_LAUNCH(ctx, k_degree_counts, grid_for(m_c, kThreads, maxb), kThreads, 0, m_c, cU, cV,
-                   up_deg, low_deg, tkey, tval);
-    }
+    // coarse CSR: row U holds its lower entries (coarse edges (U', U), ascending U') and then
+    // its upper entries (coarse edges (U, V), contiguous in coarse-edge order)
     int32_t* ufirst = W.ufirst.as<int32_t>();
     int32_t* lstart = W.lstart.as<int32_t>();
     SPC_TRY(scan_i32(ctx, up_deg, ufirst, n_c));
@@ -461,12 +877,22 @@ spc_status contract_typed(spc_context* ctx, const GraphView& g, const int32_t* l
     SPC_LAUNCH(ctx, k_rowptr, grid_for(n_c + 1, kThreads, maxb), kThreads, 0, n_c, ufirst, lstart,
                rowptr_c);
     if (m_c > 0) {
-        SPC_TRY(radix_sort_u32(ctx, tkey, tval, W.t_key2.as<uint32_t>(), W.t_val2.as<uint32_t>(),
-                               m_c, nb));
-        SPC_LAUNCH(ctx, k_fill_lower<WT>, grid_for(m_c, kThreads, maxb), kThreads, 0, m_c, tkey,
-                   tval, lstart, rowptr_c, cU, a_und, lv.col_c.as<int32_t>(), lv.w_c.as<WT>());
-        SPC_LAUNCH(ctx, k_fill_upper<WT>, grid_for(m_c, kThreads, maxb), kThreads, 0, m_c, cU, cV,
-                   ufirst, low_deg, rowptr_c, a_und, lv.col_c.as<int32_t>(), lv.w_c.as<WT>());
+        const int gc = grid_for(m_c, kThreads, maxb);
+        uint32_t* tkey = W.t_key.as<uint32_t>();
+        uint32_t* tval = W.t_val.as<uint32_t>();
+        if (lower_buckets) {
+            SPC_LAUNCH(ctx, k_lower_scatter, gc, kThreads, 0, m_c, cV, lstart, low_deg, tval);
+            SPC_LAUNCH(ctx, k_fill_lower_ranked<WT>, gc, kThreads, 0, m_c, tval, lstart,
+                       rowptr_c, cU, cV, a_und, lv.col_c.as<int32_t>(), lv.w_c.as<WT>());
+        } else {
+            SPC_LAUNCH(ctx, k_transpose_keys, gc, kThreads, 0, m_c, cV, tkey, tval);
+            SPC_TRY(radix_sort_u32(ctx, tkey, tval, W.t_key2.as<uint32_t>(),
+                                   W.t_val2.as<uint32_t>(), m_c, nb));
+            SPC_LAUNCH(ctx, k_fill_lower<WT>, gc, kThreads, 0, m_c, tkey, tval, lstart, rowptr_c,
+                       cU, a_und, lv.col_c.as<int32_t>(), lv.w_c.as<WT>());
+        }
+        SPC_LAUNCH(ctx, k_fill_upper<WT>, gc, kThreads, 0, m_c, cU, cV, lstart, a_und,
+                   lv.col_c.as<int32_t>(), lv.w_c.as<WT>());
     }
     lv.m_c = m_c;
     lv.m_inter = m_inter;

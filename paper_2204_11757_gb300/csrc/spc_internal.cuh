@@ -91,6 +91,9 @@ struct Work {
     Buf c_key, c_val, c_key2, c_val2, c_flag, c_pos, c_head, cU, cV;    // S7
     Buf t_key, t_val, t_key2, t_val2, up_deg, low_deg, deg_c, ufirst, lstart;
     Buf i_key, i_val, i_key2, i_val2, long_segs;                // intra edges (self-mass)
+    // contraction buckets: sizes (zero between calls), offsets, ranking statistics
+    Buf b_cnt, b_off, b_stats, b_list;
+    bool b_dirty = true;
     Buf sort_hist, scan_tmp;                                    // sort / scan temporaries
     Buf stage_rowptr, stage_col, stage_w, stage_lift, stage_gptr;  // host staging
     Buf pool_key, pool_val, pool_key2, pool_val2, pool_cnt, pool_off;  // feature pooling

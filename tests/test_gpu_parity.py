@@ -202,6 +202,90 @@ def test_contract_int_overflow_reported(ctx):
     assert ei.value.status == -8
 
 
+def _bucket_graph(k_clique, kb, n_cycle, dtype, seed):
+    """A clique on k_clique nodes lifted to super-node 0 (one long self-mass sum), a complete
+    bipartite K_{kb,kb} between super-nodes 1 and 2 (one coarse edge of kb^2 fine edges, all in
+    bucket 1), and a cycle of n_cycle nodes lifted in pairs (many buckets of one item)."""
+    rng = np.random.default_rng(seed)
+    iu, iv = np.triu_indices(k_clique, 1)
+    A = k_clique + np.arange(kb)
+    B = k_clique + kb + np.arange(kb)
+    C = k_clique + 2 * kb + np.arange(n_cycle)
+    bu, bv = np.meshgrid(A, B, indexing="ij")
+    eu = np.concatenate([iu, bu.ravel(), C, [0, A[0]]])
+    ev = np.concatenate([iv, bv.ravel(), np.roll(C, -1), [A[0], C[0]]])
+    n = k_clique + 2 * kb + n_cycle
+    if np.dtype(dtype).kind == "f":
+        w = rng.uniform(0.25, 4.0, eu.size).astype(dtype)
+    else:
+        w = rng.integers(1, 1000, eu.size).astype(dtype)
+    g = I.csr_from_edges(n, eu, ev, w)
+    lift = np.concatenate([np.zeros(k_clique), np.ones(kb), np.full(kb, 2),
+                           3 + np.arange(n_cycle) // 2]).astype(np.int32)
+    return g, lift, 3 + n_cycle // 2
+
+
+@pytest.mark.parametrize("dt", [np.float64, np.float32, np.int32])
+@pytest.mark.parametrize("kb,bucket_path", [(5, True), (17, True), (33, True), (91, False)])
+def test_contract_bucket_and_radix_paths(ctx, dt, kb, bucket_path):
+    """The contraction groups edges by buckets (ranked per item when short, sorted by one CTA
+    when long) while no bucket exceeds 8192 items, by radix sorts otherwise (K_{91,91} puts 8281
+    edges in one bucket).  Both give the oracle's coarse graph bit for bit, including segments
+    longer than one thread's share (the clique's 300 intra edges, the bipartite coarse edge)."""
+    api = _api()
+    g, lift, n_c = _bucket_graph(25, kb, 4000, dt, kb)
+    ref = O.contract(g, lift, n_c)
+    ctx.time_kernel("*")
+    try:
+        lv = ctx.contract(api.CSR.from_graph(g), torch.from_numpy(lift).cuda(), n_c)
+        prof = ctx.kernel_profile()
+    finally:
+        ctx.time_kernel(None)
+    ranked = any("k_bucket_rank_inter" in k for k in prof)
+    radix = any("k_classify" in k for k in prof)  # the radix path's compaction
+    assert ranked == bucket_path and radix != bucket_path, sorted(prof)
+    _check_level(lv, O.Level(n_c=n_c, lift=lift, coarse=ref))
+
+
+@pytest.mark.parametrize("dt", [np.float64, np.int32])
+@pytest.mark.parametrize("center_last", [False, True])
+def test_contract_star_rows_paths(ctx, dt, center_last):
+    """A star of 2000 leaves, each node its own super-node after a relabelling.  With the
+    centre numbered last, its coarse row has 2000 lower entries (ascending U'), which the
+    lower-row buckets refuse (radix path); numbered first, its 2000 coarse edges share one
+    inter bucket instead (sorted by one CTA) while every lower row holds one entry."""
+    api = _api()
+    rng = np.random.default_rng(7)
+    leaves = 2000
+    n = leaves + 1
+    center = n - 1 if center_last else 0
+    others = np.array([x for x in range(n) if x != center])
+    w = (rng.uniform(0.5, 2.0, leaves) if dt == np.float64
+         else rng.integers(1, 100, leaves)).astype(dt)
+    # a few leaf-leaf chords so that coarse rows differ in length
+    cu = others[:-1:7]
+    cv = others[1::7][:cu.size]
+    wc = np.ones(cu.size, dtype=dt)
+    g = I.csr_from_edges(n, np.concatenate([np.full(leaves, center), cu]),
+                         np.concatenate([others, cv]), np.concatenate([w, wc]))
+    lift = np.empty(n, dtype=np.int32)
+    lift[center] = n - 1 if center_last else 0
+    lift[others] = rng.permutation(n - 1) + (0 if center_last else 1)
+    ref = O.contract(g, lift, n)
+    ctx.time_kernel("*")
+    try:
+        lv = ctx.contract(api.CSR.from_graph(g), torch.from_numpy(lift).cuda(), n)
+        prof = ctx.kernel_profile()
+    finally:
+        ctx.time_kernel(None)
+    lower_ranked = any("k_lower_scatter" in k for k in prof)
+    long_sorted = any("k_bucket_sort_long" in k for k in prof)
+    assert lower_ranked == (not center_last), sorted(prof)
+    assert long_sorted == (not center_last), sorted(prof)
+    assert any("k_bucket_rank_inter" in k for k in prof), sorted(prof)
+    _check_level(lv, O.Level(n_c=n, lift=lift, coarse=ref))
+
+
 # ---- full method ------------------------------------------------------------------------------------
 
 @pytest.mark.parametrize("name", ["c1_tri64_unit", "s2_tri256_f64", "s3_tet33_f64",
