@@ -648,8 +648,7 @@ spc_status long_segment_sums(spc_context* ctx, const int32_t* start, const uint3
                    kThreads, 0, long_list, long_cnt, start, idx, w_und, base, terms);
         const bool f32 = std::is_same<WT, float>::value;
         SeqTabBufs& tab = side ? W.tab_s_side : W.tab_s;
-        SPC_TRY(seqtab_build(ctx, terms, f32, nlong, base, len, true, tab));
-        SPC_TRY(seqtab_full_sums(ctx, terms, f32, base, len, tab, oidx, out));
+        SPC_TRY(seqtab_full(ctx, terms, f32, nlong, base, len, oidx, out, tab));
         return SPC_OK;
     }
 }

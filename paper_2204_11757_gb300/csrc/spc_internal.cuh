@@ -76,6 +76,9 @@ struct LevelBufs {
 // Device buffers of per-binade prefix tables over a batch of long sequences (spc_seqtab.cu).
 struct SeqTabBufs {
     Buf eblo, nE, tsize, tcnt, tab_off, trip_off, P, T, csum, ctie, loff, mn, mx;
+    // full sums: units of the terms and their prefix, per-sequence scale, and per (sequence,
+    // binade) pair its window of positions, table offset and chunk offset
+    Buf units, cunits, gexp, npe, poff, pw0, plen, pnch, pq, pe, ptoff, pcoff;
     int64_t nseq = 0;
 };
 
@@ -309,14 +312,15 @@ cudaError_t radix_sort_u64_raw(cudaStream_t stream, uint64_t* keys, uint32_t* va
                                int end_bit, int32_t* hist, int32_t* scan_tmp);
 
 // Per-binade prefix tables over nseq long sequences terms[base[q] .. base[q] + len[q])
-// (binary32 when f32, else binary64; all pointers device).  `full`: tables cover every binade
-// the whole sum can reach; otherwise the binades of a running sum below 8 (scores).
+// (binary32 when f32, else binary64; all pointers device), over every position and the binades
+// of a running sum below 8 (the score walks of hub rows, from any start).
 spc_status seqtab_build(spc_context* ctx, const void* terms, bool f32, int64_t nseq,
-                        const int64_t* base, const int64_t* len, bool full, SeqTabBufs& tb);
-// out[out_idx[q]] (or out[q]) = the left-to-right sum of sequence q, from its tables.
-spc_status seqtab_full_sums(spc_context* ctx, const void* terms, bool f32, const int64_t* base,
-                            const int64_t* len, const SeqTabBufs& tb, const int64_t* out_idx,
-                            void* out);
+                        const int64_t* base, const int64_t* len, SeqTabBufs& tb);
+// out[out_idx[q]] (or out[q]) = the left-to-right sum from zero of sequence q, through tables
+// restricted to the positions where the running sum can lie in each binade.
+spc_status seqtab_full(spc_context* ctx, const void* terms, bool f32, int64_t nseq,
+                       const int64_t* base, const int64_t* len, const int64_t* out_idx, void* out,
+                       SeqTabBufs& tb);
 
 // ---- steps (spc_score.cu, spc_merge.cu, spc_contract.cu) ----------------------------------
 

@@ -807,12 +807,9 @@ static spc_status score_typed(spc_context* ctx, GraphView& g, bool validate, voi
             side.reset(new SideBranch(ctx));
             SPC_TRY(side->status());
             if (fp) {
-                SPC_TRY(seqtab_build(ctx, g.w, std::is_same<WT, float>::value, n_long,
-                                     W.lr_base.as<int64_t>(), W.lr_len.as<int64_t>(), true,
-                                     W.tab_w));
-                SPC_TRY(seqtab_full_sums(ctx, g.w, std::is_same<WT, float>::value,
-                                         W.lr_base.as<int64_t>(), W.lr_len.as<int64_t>(),
-                                         W.tab_w, W.lr_idx.as<int64_t>(), W.deg.p));
+                SPC_TRY(seqtab_full(ctx, g.w, std::is_same<WT, float>::value, n_long,
+                                    W.lr_base.as<int64_t>(), W.lr_len.as<int64_t>(),
+                                    W.lr_idx.as<int64_t>(), W.deg.p, W.tab_w));
             }
             SPC_LAUNCH(ctx, k_long_rows_edges<WT>, maxb, kThreads, 0, g.rowptr, g.col,
                        static_cast<const WT*>(g.w), validate ? 1 : 0, W.deg.as<Acc>(),
@@ -872,7 +869,7 @@ static spc_status score_typed(spc_context* ctx, GraphView& g, bool validate, voi
         side.reset(new SideBranch(ctx));
         SPC_TRY(side->status());
         SPC_TRY(seqtab_build(ctx, W.p.p, std::is_same<P, float>::value, n_long,
-                             W.lr_base.as<int64_t>(), W.lr_len.as<int64_t>(), false, W.tab_p));
+                             W.lr_base.as<int64_t>(), W.lr_len.as<int64_t>(), W.tab_p));
         side->leave();
     }
     if (schedule == 2) {

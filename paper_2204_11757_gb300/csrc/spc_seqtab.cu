@@ -1,10 +1,20 @@
 // Per-binade prefix tables over long sequences, built by the whole GPU, and the exact
 // evaluation of long left-to-right sums from them (see spc_seqsum.cuh).
 //
-// Build, for a batch of sequences: (1) one CTA per sequence finds the binade range its running
-// sum can visit; (2) one CTA per (sequence, binade, 4096-term chunk) reduces the chunk's
-// grid-rounded terms; (3) one thread per (sequence, binade) scans its chunk sums; (4) one CTA
-// per (sequence, binade, chunk) scans the chunk again and writes the tables.
+// Build, for a batch of sequences: (1) the binade range each running sum can visit; (2) one CTA
+// per (sequence, binade, 4096-term chunk) reduces the chunk's grid-rounded terms; (3) one
+// thread per (sequence, binade) scans its chunk sums; (4) one CTA per (sequence, binade, chunk)
+// scans the chunk again and writes the tables.
+//
+// Hub rows (the score walks) need every position of every binade, since the walks start from
+// many running values.  A full sum from zero does not: its running sum s_k after k terms is
+// within gamma_k A_k of the exact prefix sum A_k (recursive summation of non-negative terms,
+// N. J. Higham, Accuracy and Stability of Numerical Algorithms, 2nd ed., Section 4.2,
+// gamma_k = k u / (1 - k u)), so binade E can hold s_k only where that interval meets
+// [2^E, 2^(E+1)).  Integer bounds of A_k (terms truncated to a per-sequence grid, prefix-summed
+// exactly) give each binade a window of positions; the windows together hold about one entry
+// per term instead of one per term and binade.  The walk adds natively at any position outside
+// a window, so the windows only decide speed, never the result.
 #include "spc_seqsum.cuh"
 
 namespace spc {
@@ -58,11 +68,10 @@ k_seq_minmax(int64_t nseq, const F* __restrict__ terms, const int64_t* __restric
     }
 }
 
-// binade range and table sizes of every sequence
+// binade range and table sizes of every sequence (running sums below 8)
 template <class F>
 __global__ void k_seq_meta(int64_t nseq, const int64_t* __restrict__ len,
                            const unsigned long long* __restrict__ mn,
-                           const unsigned long long* __restrict__ mx, int full,
                            int32_t* __restrict__ eblo, int32_t* __restrict__ nE,
                            int64_t* __restrict__ tsize, int64_t* __restrict__ tcnt) {
     spc::pdl_wait();
@@ -70,22 +79,7 @@ __global__ void k_seq_meta(int64_t nseq, const int64_t* __restrict__ len,
          q += (int64_t)gridDim.x * blockDim.x) {
         const int64_t L = len[q];
         int lo = (int)(mn[q] >> FB<F>::kMant);
-        int hi;
-        if (full) {
-            // the sum is below L * max term: its binade is at most that of the bound
-            const double bound = (double)L * (double)FB<F>::from_bits(mx[q]) * 1.0000001;
-            const int top = (1 << (sizeof(F) == 8 ? 11 : 8)) - 2;
-            if (isfinite(bound)) {
-                int ex = 0;
-                frexp(bound, &ex);  // bound = f * 2^ex, f in [0.5, 1)
-                hi = ex - 1 + (FB<F>::kBiasM - FB<F>::kMant) + 1;
-                if (hi > top) hi = top;
-            } else {
-                hi = top;
-            }
-        } else {
-            hi = FB<F>::kEbHi;
-        }
+        const int hi = FB<F>::kEbHi;
         if (lo < 1) lo = 1;
         if (lo < hi - 63) lo = hi - 63;
         if (lo > hi) lo = hi;
@@ -248,29 +242,9 @@ k_seq_chunk_write(int64_t nseq, int64_t ntrip, const F* __restrict__ terms,
     }
 }
 
-// one full sum per sequence, by a warp: out[out_idx[q]] = left-to-right sum of its terms
-template <class F, class Out>
-__global__ void k_seq_full_sums(int64_t nseq, const F* __restrict__ terms,
-                                const int64_t* __restrict__ base, const int64_t* __restrict__ len,
-                                const int32_t* __restrict__ eblo, const int32_t* __restrict__ nE,
-                                const int64_t* __restrict__ tab_off,
-                                const unsigned long long* __restrict__ P,
-                                const int32_t* __restrict__ T, const int64_t* __restrict__ out_idx,
-                                Out* __restrict__ out) {
-    spc::pdl_wait();
-    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    for (int64_t q = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); q < nseq;
-         q += warps) {
-        const int64_t L = len[q];
-        const F s = tab_run_warp<F>(F(0), 0, L, terms + base[q], P + tab_off[q], T + tab_off[q],
-                                    eblo[q], nE[q], L + 1);
-        if ((threadIdx.x & 31) == 0) out[out_idx ? out_idx[q] : q] = (Out)s;
-    }
-}
-
 template <class F>
 spc_status build_typed(spc_context* ctx, const F* terms, int64_t nseq, const int64_t* base,
-                       const int64_t* len, bool full, SeqTabBufs& tb) {
+                       const int64_t* len, SeqTabBufs& tb) {
     if (nseq <= 0) return SPC_OK;
     const int maxb = ctx->num_sms * 8;
     SPC_TRY(ensure(ctx, tb.eblo, (size_t)nseq * 4));
@@ -288,9 +262,8 @@ spc_status build_typed(spc_context* ctx, const F* terms, int64_t nseq, const int
     SPC_LAUNCH(ctx, k_seq_minmax<F>, maxb, kCT, 0, nseq, terms, base, tb.loff.as<int64_t>(),
                tb.mn.as<unsigned long long>(), tb.mx.as<unsigned long long>());
     SPC_LAUNCH(ctx, k_seq_meta<F>, grid_for(nseq, kThreads, maxb), kThreads, 0, nseq, len,
-               tb.mn.as<unsigned long long>(), tb.mx.as<unsigned long long>(), full ? 1 : 0,
-               tb.eblo.as<int32_t>(), tb.nE.as<int32_t>(), tb.tsize.as<int64_t>(),
-               tb.tcnt.as<int64_t>());
+               tb.mn.as<unsigned long long>(), tb.eblo.as<int32_t>(), tb.nE.as<int32_t>(),
+               tb.tsize.as<int64_t>(), tb.tcnt.as<int64_t>());
     SPC_TRY(scan_i64_i64(ctx, tb.tsize.as<int64_t>(), tb.tab_off.as<int64_t>(), nseq));
     SPC_TRY(scan_i64_i64(ctx, tb.tcnt.as<int64_t>(), tb.trip_off.as<int64_t>(), nseq));
     int64_t vals[2];
@@ -319,34 +292,445 @@ spc_status build_typed(spc_context* ctx, const F* terms, int64_t nseq, const int
     return SPC_OK;
 }
 
-template <class F, class Out>
-spc_status full_typed(spc_context* ctx, const F* terms, const int64_t* base, const int64_t* len,
-                      const SeqTabBufs& tb, const int64_t* out_idx, Out* out) {
-    if (tb.nseq <= 0) return SPC_OK;
-    const int warps_per_block = kThreads / 32;
-    SPC_LAUNCH(ctx, (k_seq_full_sums<F, Out>), grid_for(tb.nseq, warps_per_block, ctx->num_sms * 8),
-               kThreads, 0, tb.nseq, terms, base, len, tb.eblo.as<int32_t>(), tb.nE.as<int32_t>(),
-               tb.tab_off.as<int64_t>(), tb.P.as<unsigned long long>(), tb.T.as<int32_t>(), out_idx,
-               out);
+// ---- full sums through windowed tables -----------------------------------------------------
+
+// binade range, grid exponent and pair count of every sequence.  The sum (and every term) is
+// at most L * max term < 2^ex; the grid G = 2^gexp makes that at most 2^(61 - lg_nseq) units, so
+// the exact prefix of all sequences' units stays below 2^61.  All terms zero: no binades.
+template <class F>
+__global__ void k_fs_meta(int64_t nseq, const int64_t* __restrict__ len,
+                          const unsigned long long* __restrict__ mn,
+                          const unsigned long long* __restrict__ mx, int lg_nseq,
+                          int32_t* __restrict__ eblo, int32_t* __restrict__ nE,
+                          int64_t* __restrict__ npe, int32_t* __restrict__ gexp) {
+    spc::pdl_wait();
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nseq;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t L = len[q];
+        const double mxv = (double)FB<F>::from_bits(mx[q]);
+        if (!(mxv > 0.0)) {
+            eblo[q] = 1;
+            nE[q] = 0;
+            npe[q] = 0;
+            gexp[q] = 0;
+            continue;
+        }
+        const double bound = (double)L * mxv * (1.0 + 0x1p-40);
+        constexpr int kBias = FB<F>::kBiasM - FB<F>::kMant;
+        constexpr int kTop = (1 << (sizeof(F) == 8 ? 11 : 8)) - 2;  // largest finite binade
+        int ex = kTop - kBias + 2;  // bound beyond the finite range: 2^ex above every term
+        if (isfinite(bound)) frexp(bound, &ex);  // bound < 2^ex
+        int hi = ex + kBias;  // s_k <= A_L (1 + gamma) < 2^(ex + 1)
+        if (hi > kTop) hi = kTop;
+        int lo = (int)(mn[q] >> FB<F>::kMant);
+        if (lo < 1) lo = 1;
+        if (lo < hi - 63) lo = hi - 63;
+        if (lo > hi) lo = hi;
+        eblo[q] = lo;
+        nE[q] = hi - lo + 1;
+        npe[q] = hi - lo + 1;
+        gexp[q] = ex - (61 - lg_nseq);
+    }
+}
+
+// units of every term: floor(x / 2^gexp), exact integer arithmetic on the bits
+template <class F>
+__global__ void __launch_bounds__(kThreads)
+k_fs_units(int64_t nseq, int64_t total, const F* __restrict__ terms,
+           const int64_t* __restrict__ base, const int64_t* __restrict__ loff,
+           const int32_t* __restrict__ gexp, long long* __restrict__ units) {
+    spc::pdl_wait();
+    for (int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; f < total;
+         f += (int64_t)gridDim.x * blockDim.x) {
+        int64_t lo = 0, hi = nseq - 1;
+        while (lo < hi) {
+            const int64_t mid = (lo + hi + 1) >> 1;
+            if (loff[mid] <= f) lo = mid; else hi = mid - 1;
+        }
+        const unsigned long long b = FB<F>::bits(terms[base[lo] + (f - loff[lo])]);
+        int et = (int)(b >> FB<F>::kMant);
+        unsigned long long mant = b & ((1ull << FB<F>::kMant) - 1ull);
+        if (et == 0) et = 1; else mant |= 1ull << FB<F>::kMant;
+        const int sh = et - FB<F>::kBiasM - gexp[lo];  // x = mant 2^(et - kBiasM)
+        unsigned long long u;
+        if (sh >= 0) u = mant << sh;  // < 2^61 by the choice of gexp
+        else u = sh > -64 ? mant >> -sh : 0ull;
+        units[f] = (long long)u;
+    }
+}
+
+// the window of pair (q, e): the steps k at which the running sum can lie in binade
+// eblo[q] + e, from monotone integer bounds C_k <= A_k / G < C_k + k + 1
+template <class F>
+__global__ void __launch_bounds__(kThreads)
+k_fs_windows(int64_t nseq, const int64_t* __restrict__ len, const int64_t* __restrict__ loff,
+             const long long* __restrict__ cu, const int32_t* __restrict__ eblo,
+             const int32_t* __restrict__ nE, const int64_t* __restrict__ poff,
+             const int32_t* __restrict__ gexp, int64_t* __restrict__ pw0,
+             int64_t* __restrict__ plen, int64_t* __restrict__ pnch, int32_t* __restrict__ pq,
+             int32_t* __restrict__ pe) {
+    spc::pdl_wait();
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nseq * 64;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t q = t >> 6;
+        const int e = (int)(t & 63);
+        if (e >= nE[q]) continue;
+        const int64_t r = poff[q] + e;
+        const int64_t L = len[q];
+        const long long* C = cu + loff[q];
+        const long long c0 = C[0];
+        int64_t kmin = 0, kmax = L;  // steps k in [kmin, kmax]; empty when kmin > kmax
+        const double g = (double)L * (sizeof(F) == 8 ? 0x1p-53 : 0x1p-24);
+        const double gam = g / (1.0 - g);
+        if (gam <= 0.25) {
+            constexpr int kBias = FB<F>::kBiasM - FB<F>::kMant;
+            const int E2 = eblo[q] + e - kBias - gexp[q];  // binade [2^E2, 2^(E2+1)) in units
+            constexpr double kCap = 0x1p62;
+            double lo_t = ldexp(1.0, E2) * (1.0 - gam) * (1.0 - 0x1p-40);
+            double hi_t = ldexp(1.0, E2 + 1) * (1.0 + 2.0 * gam) * (1.0 + 0x1p-40);
+            lo_t = lo_t > kCap ? kCap : floor(lo_t);
+            hi_t = hi_t > kCap ? kCap : ceil(hi_t);
+            const long long thr_lo = (long long)lo_t, thr_hi = (long long)hi_t;
+            // kmin: first k in [0, L] with C_k + k >= thr_lo (none: L + 1)
+            int64_t a = 0, b = L + 1;
+            while (a < b) {
+                const int64_t mid = (a + b) >> 1;
+                if ((C[mid] - c0) + mid >= thr_lo) b = mid; else a = mid + 1;
+            }
+            kmin = a;
+            // kmax: last k in [0, L] with C_k < thr_hi (none: -1)
+            a = -1;
+            b = L;
+            while (a < b) {
+                const int64_t mid = (a + b + 1) >> 1;
+                if (C[mid] - c0 < thr_hi) a = mid; else b = mid - 1;
+            }
+            kmax = a;
+        }
+        if (kmax > L - 1) kmax = L - 1;
+        const int64_t nst = kmax >= kmin ? kmax - kmin + 1 : 0;
+        pw0[r] = kmin;
+        plen[r] = nst ? nst + 1 : 0;  // table entries: prefix positions kmin .. kmax + 1
+        pnch[r] = (nst + kChunk - 1) / kChunk;
+        pq[r] = (int32_t)q;
+        pe[r] = e;
+    }
+}
+
+// pair r of trip t (pcoff: exclusive prefix of the pairs' chunk counts)
+__device__ __forceinline__ int64_t pair_of(int64_t t, int64_t npair, const int64_t* pcoff) {
+    int64_t lo = 0, hi = npair - 1;
+    while (lo < hi) {
+        const int64_t mid = (lo + hi + 1) >> 1;
+        if (pcoff[mid] <= t) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// grid-rounded sums (and half-grid ties) of the 4096-step chunks of every window
+template <class F>
+__global__ void __launch_bounds__(kCT)
+k_fs_chunk_sums(int64_t ntrip, int64_t npair, const int64_t* __restrict__ pcoff,
+                const int32_t* __restrict__ pq, const int32_t* __restrict__ pe,
+                const int64_t* __restrict__ pw0, const int64_t* __restrict__ plen,
+                const F* __restrict__ terms, const int64_t* __restrict__ base,
+                const int32_t* __restrict__ eblo, unsigned long long* __restrict__ csum,
+                int32_t* __restrict__ ctie) {
+    spc::pdl_wait();
+    __shared__ unsigned long long sh_s[kCT / 32];
+    __shared__ int32_t sh_t[kCT / 32];
+    for (int64_t t = blockIdx.x; t < ntrip; t += gridDim.x) {
+        const int64_t r = pair_of(t, npair, pcoff);
+        const int64_t q = pq[r];
+        const int eb = eblo[q] + pe[r];
+        const F* x = terms + base[q];
+        const int64_t k0 = pw0[r] + (t - pcoff[r]) * kChunk;
+        const int64_t kend = pw0[r] + plen[r] - 1;
+        const int64_t k1 = k0 + kChunk < kend ? k0 + kChunk : kend;
+        unsigned long long s = 0;
+        int32_t ties = 0;
+        for (int64_t k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
+            bool tie;
+            s = sat_add(s, grid_units<F>(x[k], eb, &tie));
+            ties += tie ? 1 : 0;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            s = sat_add(s, __shfl_xor_sync(0xffffffffu, s, o));
+            ties += __shfl_xor_sync(0xffffffffu, ties, o);
+        }
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        if (lane == 0) { sh_s[warp] = s; sh_t[warp] = ties; }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            unsigned long long a = 0;
+            int32_t tt = 0;
+            for (int w = 0; w < kCT / 32; ++w) { a = sat_add(a, sh_s[w]); tt += sh_t[w]; }
+            csum[t] = a;
+            ctie[t] = tt;
+        }
+        __syncthreads();
+    }
+}
+
+// exclusive scan of every window's chunk sums, in place (one thread per pair)
+__global__ void k_fs_chunk_scan(int64_t npair, const int64_t* __restrict__ pcoff,
+                                unsigned long long* __restrict__ csum, int32_t* __restrict__ ctie) {
+    spc::pdl_wait();
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < npair;
+         r += (int64_t)gridDim.x * blockDim.x) {
+        unsigned long long run = 0;
+        int32_t tr = 0;
+        for (int64_t c = pcoff[r]; c < pcoff[r + 1]; ++c) {
+            const unsigned long long v = csum[c];
+            const int32_t tv = ctie[c];
+            csum[c] = run;
+            ctie[c] = tr;
+            run = sat_add(run, v);
+            tr += tv;
+        }
+    }
+}
+
+// table entries of every window: entry i of pair r (at ptoff[r] + i) is the prefix over the
+// window's steps pw0 .. pw0 + i - 1
+template <class F>
+__global__ void __launch_bounds__(kCT)
+k_fs_chunk_write(int64_t ntrip, int64_t npair, const int64_t* __restrict__ pcoff,
+                 const int32_t* __restrict__ pq, const int32_t* __restrict__ pe,
+                 const int64_t* __restrict__ pw0, const int64_t* __restrict__ plen,
+                 const int64_t* __restrict__ ptoff, const F* __restrict__ terms,
+                 const int64_t* __restrict__ base, const int32_t* __restrict__ eblo,
+                 const unsigned long long* __restrict__ csum, const int32_t* __restrict__ ctie,
+                 unsigned long long* __restrict__ P, int32_t* __restrict__ T) {
+    spc::pdl_wait();
+    constexpr int kItems = kChunk / kCT;
+    __shared__ unsigned long long sh_s[kCT / 32];
+    __shared__ int32_t sh_t[kCT / 32];
+    for (int64_t t = blockIdx.x; t < ntrip; t += gridDim.x) {
+        const int64_t r = pair_of(t, npair, pcoff);
+        const int64_t q = pq[r];
+        const int eb = eblo[q] + pe[r];
+        const F* x = terms + base[q];
+        const int64_t w0 = pw0[r];
+        const int64_t kend = w0 + plen[r] - 1;
+        unsigned long long* Pr = P + ptoff[r];
+        int32_t* Tr = T + ptoff[r];
+        const int64_t c = t - pcoff[r];
+        const int64_t k0 = w0 + c * kChunk + (int64_t)threadIdx.x * kItems;
+        unsigned long long rr[kItems];
+        int32_t ti[kItems];
+        unsigned long long run = 0;
+        int32_t trun = 0;
+#pragma unroll
+        for (int j = 0; j < kItems; ++j) {
+            const int64_t k = k0 + j;
+            bool tie = false;
+            rr[j] = (k < kend) ? grid_units<F>(x[k], eb, &tie) : 0ull;
+            ti[j] = tie ? 1 : 0;
+            run = sat_add(run, rr[j]);
+            trun += ti[j];
+        }
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        unsigned long long v = run;
+        int32_t tv = trun;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long a = __shfl_up_sync(0xffffffffu, v, o);
+            const int32_t cc = __shfl_up_sync(0xffffffffu, tv, o);
+            if (lane >= o) { v = sat_add(v, a); tv += cc; }
+        }
+        if (lane == 31) { sh_s[warp] = v; sh_t[warp] = tv; }
+        __syncthreads();
+        unsigned long long pre = csum[t];
+        int32_t tpre = ctie[t];
+        for (int w = 0; w < warp; ++w) { pre = sat_add(pre, sh_s[w]); tpre += sh_t[w]; }
+        unsigned long long wex = __shfl_up_sync(0xffffffffu, v, 1);
+        int32_t tex = __shfl_up_sync(0xffffffffu, tv, 1);
+        if (lane == 0) { wex = 0; tex = 0; }
+        pre = sat_add(pre, wex);
+        tpre += tex;
+        if (c == 0 && threadIdx.x == 0) { Pr[0] = 0; Tr[0] = 0; }
+#pragma unroll
+        for (int j = 0; j < kItems; ++j) {
+            const int64_t k = k0 + j;
+            pre = sat_add(pre, rr[j]);
+            tpre += ti[j];
+            if (k < kend) { Pr[k - w0 + 1] = pre; Tr[k - w0 + 1] = tpre; }
+        }
+        __syncthreads();
+    }
+}
+
+// one full sum per sequence, by a warp: binade by binade through the windows (32 probes per
+// search round), one native addition at every binade crossing, tie, or position outside the
+// current binade's window
+template <class F>
+__global__ void k_fs_walk(int64_t nseq, const F* __restrict__ terms,
+                          const int64_t* __restrict__ base, const int64_t* __restrict__ len,
+                          const int32_t* __restrict__ eblo, const int32_t* __restrict__ nE,
+                          const int64_t* __restrict__ poff, const int64_t* __restrict__ pw0,
+                          const int64_t* __restrict__ plen, const int64_t* __restrict__ ptoff,
+                          const unsigned long long* __restrict__ P,
+                          const int32_t* __restrict__ T, const int64_t* __restrict__ out_idx,
+                          F* __restrict__ out) {
+    spc::pdl_wait();
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t q = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); q < nseq;
+         q += warps) {
+        const int64_t L = len[q];
+        const F* x = terms + base[q];
+        const int lo_eb = eblo[q], ne = nE[q];
+        F s = F(0);
+        int64_t a = 0;
+        while (ne > 0 && a < L) {
+            if (s == F(0)) { s = x[a++]; continue; }
+            const unsigned long long sb = FB<F>::bits(s);
+            const int eb = (int)(sb >> FB<F>::kMant);
+            const int e = eb - lo_eb;
+            if (eb == 0 || e < 0 || e >= ne) { s = FB<F>::add(s, x[a++]); continue; }
+            const int64_t r = poff[q] + e;
+            const int64_t w0 = pw0[r], nent = plen[r];
+            if (nent == 0 || a < w0 || a > w0 + nent - 2) { s = FB<F>::add(s, x[a++]); continue; }
+            const unsigned long long* Pr = P + ptoff[r];
+            const int32_t* Tr = T + ptoff[r];
+            const unsigned long long pa = Pr[a - w0];
+            if (pa >= kSat - (1ull << 55)) { s = FB<F>::add(s, x[a++]); continue; }
+            const unsigned long long S =
+                (sb & ((1ull << FB<F>::kMant) - 1ull)) | (1ull << FB<F>::kMant);
+            const unsigned long long lim = (1ull << (FB<F>::kMant + 1)) - S;
+            const int32_t ta = Tr[a - w0];
+            // largest k in [a, w0 + nent - 1] with P_k - P_a <= lim and no tie in [a, k)
+            int64_t lo = a, hi = w0 + nent - 1;
+            while (hi > lo) {
+                const int64_t step = (hi - lo + 31) / 32;
+                const int64_t probe = lo + (int64_t)(lane + 1) * step;
+                bool good = false;
+                if (probe <= hi) good = (Pr[probe - w0] - pa <= lim) && (Tr[probe - w0] == ta);
+                const int ngood = __popc(__ballot_sync(0xffffffffu, good));
+                // good positions form a prefix of the probes (both conditions are monotone)
+                const int64_t new_lo = lo + (int64_t)ngood * step;
+                int64_t new_hi = lo + (int64_t)(ngood + 1) * step - 1;
+                if (new_hi > hi) new_hi = hi;
+                lo = new_lo > hi ? hi : new_lo;
+                hi = new_hi;
+                if (step == 1) break;
+            }
+            s = from_units<F>(S + (Pr[lo - w0] - pa), eb);
+            a = lo;
+            if (a < L) s = FB<F>::add(s, x[a++]);  // crossing, tie or window end: native step
+        }
+        if (lane == 0) out[out_idx ? out_idx[q] : q] = s;
+    }
+}
+
+template <class F>
+spc_status full_windowed(spc_context* ctx, const F* terms, int64_t nseq, const int64_t* base,
+                         const int64_t* len, const int64_t* out_idx, F* out, SeqTabBufs& tb) {
+    if (nseq <= 0) return SPC_OK;
+    const int maxb = ctx->num_sms * 8;
+    int lg = 0;
+    while ((1ll << lg) < nseq) ++lg;
+    SPC_TRY(ensure(ctx, tb.eblo, (size_t)nseq * 4));
+    SPC_TRY(ensure(ctx, tb.nE, (size_t)nseq * 4));
+    SPC_TRY(ensure(ctx, tb.gexp, (size_t)nseq * 4));
+    SPC_TRY(ensure(ctx, tb.npe, (size_t)nseq * 8));
+    SPC_TRY(ensure(ctx, tb.poff, (size_t)(nseq + 1) * 8));
+    SPC_TRY(ensure(ctx, tb.loff, (size_t)(nseq + 1) * 8));
+    SPC_TRY(ensure(ctx, tb.mn, (size_t)nseq * 8));
+    SPC_TRY(ensure(ctx, tb.mx, (size_t)nseq * 8));
+    SPC_TRY(scan_i64_i64(ctx, len, tb.loff.as<int64_t>(), nseq));
+    SPC_CUDA(cudaMemsetAsync(tb.mn.p, 0xff, (size_t)nseq * 8, ctx->stream));
+    SPC_CUDA(cudaMemsetAsync(tb.mx.p, 0, (size_t)nseq * 8, ctx->stream));
+    SPC_LAUNCH(ctx, k_seq_minmax<F>, maxb, kCT, 0, nseq, terms, base, tb.loff.as<int64_t>(),
+               tb.mn.as<unsigned long long>(), tb.mx.as<unsigned long long>());
+    SPC_LAUNCH(ctx, k_fs_meta<F>, grid_for(nseq, kThreads, maxb), kThreads, 0, nseq, len,
+               tb.mn.as<unsigned long long>(), tb.mx.as<unsigned long long>(), lg,
+               tb.eblo.as<int32_t>(), tb.nE.as<int32_t>(), tb.npe.as<int64_t>(),
+               tb.gexp.as<int32_t>());
+    SPC_TRY(scan_i64_i64(ctx, tb.npe.as<int64_t>(), tb.poff.as<int64_t>(), nseq));
+    int64_t v1[2];
+    {
+        const void* ptrs[2] = {tb.loff.as<int64_t>() + nseq, tb.poff.as<int64_t>() + nseq};
+        const int bytes[2] = {8, 8};
+        SPC_TRY(read_vals(ctx, 2, ptrs, bytes, v1));
+    }
+    const int64_t total = v1[0], npair = v1[1];
+    const long long* cu = nullptr;
+    if (npair > 0) {
+        SPC_TRY(ensure(ctx, tb.units, (size_t)(total + 1) * 8));
+        SPC_TRY(ensure(ctx, tb.cunits, (size_t)(total + 1) * 8));
+        SPC_TRY(ensure(ctx, tb.pw0, (size_t)npair * 8));
+        SPC_TRY(ensure(ctx, tb.plen, (size_t)npair * 8));
+        SPC_TRY(ensure(ctx, tb.pnch, (size_t)npair * 8));
+        SPC_TRY(ensure(ctx, tb.pq, (size_t)npair * 4));
+        SPC_TRY(ensure(ctx, tb.pe, (size_t)npair * 4));
+        SPC_TRY(ensure(ctx, tb.ptoff, (size_t)(npair + 1) * 8));
+        SPC_TRY(ensure(ctx, tb.pcoff, (size_t)(npair + 1) * 8));
+        SPC_LAUNCH(ctx, k_fs_units<F>, grid_for(total, kThreads, maxb), kThreads, 0, nseq, total,
+                   terms, base, tb.loff.as<int64_t>(), tb.gexp.as<int32_t>(),
+                   tb.units.as<long long>());
+        SPC_TRY(scan_i64_i64(ctx, tb.units.as<int64_t>(), tb.cunits.as<int64_t>(), total));
+        cu = tb.cunits.as<long long>();
+        SPC_LAUNCH(ctx, k_fs_windows<F>, grid_for(nseq * 64, kThreads, maxb), kThreads, 0, nseq,
+                   len, tb.loff.as<int64_t>(), cu, tb.eblo.as<int32_t>(), tb.nE.as<int32_t>(),
+                   tb.poff.as<int64_t>(), tb.gexp.as<int32_t>(), tb.pw0.as<int64_t>(),
+                   tb.plen.as<int64_t>(), tb.pnch.as<int64_t>(), tb.pq.as<int32_t>(),
+                   tb.pe.as<int32_t>());
+        SPC_TRY(scan_i64_i64(ctx, tb.plen.as<int64_t>(), tb.ptoff.as<int64_t>(), npair));
+        SPC_TRY(scan_i64_i64(ctx, tb.pnch.as<int64_t>(), tb.pcoff.as<int64_t>(), npair));
+        int64_t v2[2];
+        {
+            const void* ptrs[2] = {tb.ptoff.as<int64_t>() + npair, tb.pcoff.as<int64_t>() + npair};
+            const int bytes[2] = {8, 8};
+            SPC_TRY(read_vals(ctx, 2, ptrs, bytes, v2));
+        }
+        const int64_t elems = v2[0], ntrip = v2[1];
+        SPC_TRY(ensure(ctx, tb.P, (size_t)elems * 8 + 256));
+        SPC_TRY(ensure(ctx, tb.T, (size_t)elems * 4 + 256));
+        SPC_TRY(ensure(ctx, tb.csum, (size_t)ntrip * 8 + 256));
+        SPC_TRY(ensure(ctx, tb.ctie, (size_t)ntrip * 4 + 256));
+        if (ntrip > 0) {
+            SPC_LAUNCH(ctx, k_fs_chunk_sums<F>, grid_for(ntrip, 1, maxb), kCT, 0, ntrip, npair,
+                       tb.pcoff.as<int64_t>(), tb.pq.as<int32_t>(), tb.pe.as<int32_t>(),
+                       tb.pw0.as<int64_t>(), tb.plen.as<int64_t>(), terms, base,
+                       tb.eblo.as<int32_t>(), tb.csum.as<unsigned long long>(),
+                       tb.ctie.as<int32_t>());
+            SPC_LAUNCH(ctx, k_fs_chunk_scan, grid_for(npair, 64, maxb), 64, 0, npair,
+                       tb.pcoff.as<int64_t>(), tb.csum.as<unsigned long long>(),
+                       tb.ctie.as<int32_t>());
+            SPC_LAUNCH(ctx, k_fs_chunk_write<F>, grid_for(ntrip, 1, maxb), kCT, 0, ntrip, npair,
+                       tb.pcoff.as<int64_t>(), tb.pq.as<int32_t>(), tb.pe.as<int32_t>(),
+                       tb.pw0.as<int64_t>(), tb.plen.as<int64_t>(), tb.ptoff.as<int64_t>(), terms,
+                       base, tb.eblo.as<int32_t>(), tb.csum.as<unsigned long long>(),
+                       tb.ctie.as<int32_t>(), tb.P.as<unsigned long long>(), tb.T.as<int32_t>());
+        }
+    }
+    tb.nseq = nseq;
+    SPC_LAUNCH(ctx, k_fs_walk<F>, grid_for(nseq, kThreads / 32, maxb), kThreads, 0, nseq, terms,
+               base, len, tb.eblo.as<int32_t>(), tb.nE.as<int32_t>(), tb.poff.as<int64_t>(),
+               tb.pw0.as<int64_t>(), tb.plen.as<int64_t>(), tb.ptoff.as<int64_t>(),
+               tb.P.as<unsigned long long>(), tb.T.as<int32_t>(), out_idx, out);
     return SPC_OK;
 }
 
 }  // namespace
 
 spc_status seqtab_build(spc_context* ctx, const void* terms, bool f32, int64_t nseq,
-                        const int64_t* base, const int64_t* len, bool full, SeqTabBufs& tb) {
-    if (f32) return build_typed<float>(ctx, static_cast<const float*>(terms), nseq, base, len, full, tb);
-    return build_typed<double>(ctx, static_cast<const double*>(terms), nseq, base, len, full, tb);
+                        const int64_t* base, const int64_t* len, SeqTabBufs& tb) {
+    if (f32) return build_typed<float>(ctx, static_cast<const float*>(terms), nseq, base, len, tb);
+    return build_typed<double>(ctx, static_cast<const double*>(terms), nseq, base, len, tb);
 }
 
-spc_status seqtab_full_sums(spc_context* ctx, const void* terms, bool f32, const int64_t* base,
-                            const int64_t* len, const SeqTabBufs& tb, const int64_t* out_idx,
-                            void* out) {
+spc_status seqtab_full(spc_context* ctx, const void* terms, bool f32, int64_t nseq,
+                       const int64_t* base, const int64_t* len, const int64_t* out_idx, void* out,
+                       SeqTabBufs& tb) {
     if (f32)
-        return full_typed<float, float>(ctx, static_cast<const float*>(terms), base, len, tb,
-                                        out_idx, static_cast<float*>(out));
-    return full_typed<double, double>(ctx, static_cast<const double*>(terms), base, len, tb,
-                                      out_idx, static_cast<double*>(out));
+        return full_windowed<float>(ctx, static_cast<const float*>(terms), nseq, base, len,
+                                    out_idx, static_cast<float*>(out), tb);
+    return full_windowed<double>(ctx, static_cast<const double*>(terms), nseq, base, len, out_idx,
+                                 static_cast<double*>(out), tb);
 }
 
 SeqTabView seqtab_view(const SeqTabBufs& tb, const int64_t* base, const int64_t* len) {
