@@ -252,36 +252,88 @@ k_key_hist(int64_t m, const KT* __restrict__ key, int shift, uint32_t* __restric
         if (sh_hist[b]) atomicAdd(hist + b, sh_hist[b]);
 }
 
-// smallest bin whose cumulative count reaches `need` (all bins when need >= m)
+// inclusive scan of x over the block (blockDim.x a multiple of 32, at most 1024), by warp
+// shuffles and one pass over the warp totals; ws: 32 words of shared memory.  All threads call
+// it; ws may be reused after it returns.
+__device__ __forceinline__ unsigned long long block_incl_scan(unsigned long long x,
+                                                               unsigned long long* ws) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) ws[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        unsigned long long y = lane < nw ? ws[lane] : 0ull;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long z = __shfl_up_sync(0xffffffffu, y, o);
+            if (lane >= o) y += z;
+        }
+        ws[lane] = y;
+    }
+    __syncthreads();
+    const unsigned long long r = x + (w ? ws[w - 1] : 0ull);
+    __syncthreads();
+    return r;
+}
+
+// smallest bin whose cumulative count reaches `need` (all bins when need >= m); leaves the
+// histogram zero for the next level.  Each thread holds 32 consecutive bins in registers; the
+// block scan of the thread totals is two rounds of warp shuffles.
 __global__ void __launch_bounds__(1024)
 k_pick_tau(uint32_t* __restrict__ hist, int64_t need, uint32_t* __restrict__ tau_top) {
     spc::pdl_wait();
-    __shared__ unsigned long long sh[1024];
     constexpr int kPer = 32768 / 1024;
+    __shared__ unsigned long long wsum[32];
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    uint4* h4 = reinterpret_cast<uint4*>(hist) + (int64_t)t * (kPer / 4);
+    uint32_t v[kPer];
     unsigned long long loc = 0;
-    for (int j = 0; j < kPer; ++j) loc += hist[threadIdx.x * kPer + j];
-    sh[threadIdx.x] = loc;
-    __syncthreads();
-    for (int o = 1; o < 1024; o <<= 1) {  // inclusive scan (Hillis-Steele)
-        unsigned long long t = threadIdx.x >= (unsigned)o ? sh[threadIdx.x - o] : 0ull;
-        __syncthreads();
-        sh[threadIdx.x] += t;
-        __syncthreads();
+#pragma unroll
+    for (int j = 0; j < kPer / 4; ++j) {
+        const uint4 q = h4[j];
+        v[4 * j] = q.x;
+        v[4 * j + 1] = q.y;
+        v[4 * j + 2] = q.z;
+        v[4 * j + 3] = q.w;
+        loc += (unsigned long long)q.x + q.y + q.z + q.w;
     }
-    if (threadIdx.x == 0) *tau_top = 32767u;
+#pragma unroll
+    for (int j = 0; j < kPer / 4; ++j) h4[j] = make_uint4(0u, 0u, 0u, 0u);
+    unsigned long long x = loc;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[w] = x;
+    if (t == 0) *tau_top = 32767u;
     __syncthreads();
-    unsigned long long run = threadIdx.x ? sh[threadIdx.x - 1] : 0ull;
-    if (run < (unsigned long long)need && sh[threadIdx.x] >= (unsigned long long)need) {
+    if (w == 0) {
+        unsigned long long y = wsum[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long z = __shfl_up_sync(0xffffffffu, y, o);
+            if (lane >= o) y += z;
+        }
+        wsum[lane] = y;
+    }
+    __syncthreads();
+    const unsigned long long incl = x + (w ? wsum[w - 1] : 0ull);
+    unsigned long long run = incl - loc;
+    if (run < (unsigned long long)need && incl >= (unsigned long long)need) {
+#pragma unroll
         for (int j = 0; j < kPer; ++j) {
-            run += hist[threadIdx.x * kPer + j];
+            run += v[j];
             if (run >= (unsigned long long)need) {
-                *tau_top = (uint32_t)(threadIdx.x * kPer + j);
+                *tau_top = (uint32_t)(t * kPer + j);
                 break;
             }
         }
     }
-    // leave the histogram zero for the next level (only this thread reads its slice)
-    for (int j = 0; j < kPer; ++j) hist[threadIdx.x * kPer + j] = 0;
 }
 
 // Boruvka phase B (64-bit scores only): among the edges whose score equals the component
@@ -513,18 +565,11 @@ k_rsel_round(int r, int64_t n_host, const int32_t* __restrict__ n_dev,
         c[j] = __ldcg(h + threadIdx.x * kPer + j);
         loc += c[j];
     }
-    __shared__ unsigned long long sh_s[kThreads];
-    sh_s[threadIdx.x] = loc;
-    __syncthreads();
-    for (int o = 1; o < kThreads; o <<= 1) {
-        const unsigned long long t = threadIdx.x >= (unsigned)o ? sh_s[threadIdx.x - o] : 0ull;
-        __syncthreads();
-        sh_s[threadIdx.x] += t;
-        __syncthreads();
-    }
+    __shared__ unsigned long long sh_ws[32];
+    const unsigned long long incl = block_incl_scan(loc, sh_ws);
     const unsigned long long need = st->need;
-    unsigned long long run = threadIdx.x ? sh_s[threadIdx.x - 1] : 0ull;
-    if (run < need && sh_s[threadIdx.x] >= need) {
+    unsigned long long run = incl - loc;
+    if (run < need && incl >= need) {
         for (int j = 0; j < kPer; ++j) {
             if (run + c[j] >= need) {
                 st->dig[r] = (uint32_t)(threadIdx.x * kPer + j);
@@ -551,7 +596,7 @@ k_rsel_rest(int r0, const int32_t* __restrict__ n_dev, const KT* __restrict__ ke
     constexpr int kPer = kSelBins / kRestThreads;
     __shared__ uint32_t sh_h[kSelBins];
     __shared__ uint32_t sh_dig[16];
-    __shared__ unsigned long long sh_s[kRestThreads];
+    __shared__ unsigned long long sh_ws[32];
     __shared__ unsigned long long sh_need;
     const int64_t n = *n_dev;
     if (threadIdx.x < 16) sh_dig[threadIdx.x] = st->dig[threadIdx.x];
@@ -582,18 +627,11 @@ k_rsel_rest(int r0, const int32_t* __restrict__ n_dev, const KT* __restrict__ ke
             c[j] = sh_h[threadIdx.x * kPer + j];
             loc += c[j];
         }
-        sh_s[threadIdx.x] = loc;
-        __syncthreads();
-        for (int o = 1; o < kRestThreads; o <<= 1) {
-            const unsigned long long t = threadIdx.x >= (unsigned)o ? sh_s[threadIdx.x - o] : 0ull;
-            __syncthreads();
-            sh_s[threadIdx.x] += t;
-            __syncthreads();
-        }
+        const unsigned long long incl = block_incl_scan(loc, sh_ws);
         const unsigned long long need = sh_need;
-        unsigned long long run = threadIdx.x ? sh_s[threadIdx.x - 1] : 0ull;
+        unsigned long long run = incl - loc;
         __syncthreads();  // every thread has read sh_need
-        if (run < need && sh_s[threadIdx.x] >= need) {
+        if (run < need && incl >= need) {
             for (int j = 0; j < kPer; ++j) {
                 if (run + c[j] >= need) {
                     sh_dig[r] = (uint32_t)(threadIdx.x * kPer + j);
