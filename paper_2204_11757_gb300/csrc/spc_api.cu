@@ -351,6 +351,7 @@ static spc_status reserve_work(spc_context* ctx, int64_t n, int64_t m, int64_t B
     SPC_TRY(ensure(ctx, W.lr_idx, N * 8));
     SPC_TRY(ensure(ctx, W.lr_eoff, (N + 1) * 8));
     SPC_TRY(ensure(ctx, W.heavy, M * 4));
+    SPC_TRY(ensure(ctx, W.hub_leaf, N * 8));
     SPC_TRY(ensure(ctx, W.seg_base, M * 8));
     SPC_TRY(ensure(ctx, W.seg_len, M * 8));
     SPC_TRY(ensure(ctx, W.seg_idx, M * 8));

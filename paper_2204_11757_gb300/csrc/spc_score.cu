@@ -514,17 +514,48 @@ k_score_warp_row(int64_t n, const int64_t* __restrict__ rowptr, const int32_t* _
 // by the coordinates of v's row ("specials": an extra term p_vx, or |p_Hx - p_vx| where both
 // rows have x).  Runs are evaluated exactly from per-binade prefix tables of H's row.
 
-constexpr int kHeavySpecials = 32;  // edges whose other row is longer go to the warp kernel
+constexpr int kHeavySpecials = 8;  // edges whose other row is longer go to the warp kernel
 
 // light hub edges: one thread per entry (H, v) of a hub row, flat over all hubs
+// Hub edge (H, v) where v's only neighbour is H: the union of the two rows is H's row with the
+// single term |0 - p_v[H]| = 1 (p_v[H] = w / w) inserted at H's own column position, so every
+// such edge of H has the same score.  A warp evaluates it once per hub.
+template <class PT>
+__global__ void __launch_bounds__(kThreads)
+k_hub_leaf_score(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                 const PT* __restrict__ p, const int32_t* __restrict__ long_rows,
+                 const int32_t* __restrict__ long_count, SeqTabView tab, PT* __restrict__ leaf) {
+    spc::pdl_wait();
+    const int32_t cnt = *long_count;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < cnt;
+         i += warps) {
+        const int64_t H = long_rows[i];
+        const int64_t rH = rowptr[H], dH = rowptr[H + 1] - rH;
+        const int32_t* cH = col + rH;
+        int64_t lo = 0, hi = dH;  // first position whose column is above H
+        while (lo < hi) {
+            const int64_t mid = (lo + hi) >> 1;
+            if ((int64_t)cH[mid] < H) lo = mid + 1; else hi = mid;
+        }
+        const unsigned long long* P = tab.P + tab.tab_off[i];
+        const int32_t* T = tab.T + tab.tab_off[i];
+        PT s = tab_run_warp<PT>(PT(0), 0, lo, p + rH, P, T, tab.eblo[i], tab.nE[i], dH + 1);
+        s = p_add(s, PT(1));
+        s = tab_run_warp<PT>(s, lo, dH, p + rH, P, T, tab.eblo[i], tab.nE[i], dH + 1);
+        if ((threadIdx.x & 31) == 0) leaf[i] = s;
+    }
+}
+
 template <class PT, class KT>
 __global__ void __launch_bounds__(kThreads)
 k_score_hub(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
             const PT* __restrict__ p, const int32_t* __restrict__ up_ptr,
             const int32_t* __restrict__ nlow, const int32_t* __restrict__ long_rows,
             const int32_t* __restrict__ long_count, const int64_t* __restrict__ lr_eoff,
-            SeqTabView tab, KT* __restrict__ score, int32_t* __restrict__ heavy,
-            int32_t* __restrict__ heavy_count, const uint32_t* status) {
+            SeqTabView tab, const PT* __restrict__ leaf, KT* __restrict__ score,
+            int32_t* __restrict__ heavy, int32_t* __restrict__ heavy_count,
+            const uint32_t* status) {
     spc::pdl_wait();
     if (*status) return;
     const int32_t cnt = *long_count;
@@ -543,6 +574,12 @@ k_score_hub(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
         const int64_t v = col[rH + k];
         const int64_t rv = rowptr[v], dv = rowptr[v + 1] - rv;
         if (dv > dH || (dv == dH && v < H)) continue;  // v's row is the hub of this edge
+        if (dv == 1 && key_bits(p[rv]) == key_bits(PT(1))) {  // v a leaf of H: the hub's value
+            const int64_t e = (H < v) ? (int64_t)up_ptr[H] + (k - nlow[H])
+                                      : (int64_t)up_ptr[v] - nlow[v];
+            score[e] = key_bits(leaf[i]);
+            continue;
+        }
         if (dv > kHeavySpecials) {                       // many specials: warp kernel
             heavy[atomicAdd(heavy_count, 1)] = (int32_t)f;
             continue;
@@ -890,10 +927,12 @@ static spc_status score_typed(spc_context* ctx, GraphView& g, bool validate, voi
     if (n_long == 0) return validate ? check_status(ctx) : SPC_OK;
     side.reset();  // the main stream waits for the tables
     const SeqTabView tv = seqtab_view(W.tab_p, W.lr_base.as<int64_t>(), W.lr_len.as<int64_t>());
+    SPC_LAUNCH(ctx, k_hub_leaf_score<P>, grid_for(n_long, kThreads / 32, maxb), kThreads, 0,
+               g.rowptr, g.col, W.p.as<P>(), long_rows, long_count, tv, W.hub_leaf.as<P>());
     SPC_LAUNCH(ctx, (k_score_hub<P, Key>), maxb, kThreads, 0, g.rowptr, g.col, W.p.as<P>(),
                W.up_ptr.as<int32_t>(), W.first_up.as<int32_t>(), long_rows, long_count,
-               W.lr_eoff.as<int64_t>(), tv, static_cast<Key*>(score), W.heavy.as<int32_t>(),
-               heavy_count, status);
+               W.lr_eoff.as<int64_t>(), tv, W.hub_leaf.as<P>(), static_cast<Key*>(score),
+               W.heavy.as<int32_t>(), heavy_count, status);
     SPC_LAUNCH(ctx, (k_score_hub_heavy<P, Key>), persist, kThreads, 0, g.rowptr, g.col,
                W.p.as<P>(), W.up_ptr.as<int32_t>(), W.first_up.as<int32_t>(), long_rows,
                long_count, W.lr_eoff.as<int64_t>(), tv, W.heavy.as<int32_t>(), heavy_count,

@@ -603,6 +603,13 @@ __global__ void k_fs_walk(int64_t nseq, const F* __restrict__ terms,
             const int32_t ta = Tr[a - w0];
             // largest k in [a, w0 + nent - 1] with P_k - P_a <= lim and no tie in [a, k)
             int64_t lo = a, hi = w0 + nent - 1;
+            // The sum cannot reach the next binade before that binade's window starts, so the
+            // answer is usually at or after the step before it (the last binade: the end).
+            // One probe there, if it is good, leaves only the windows' overlap to search.
+            int64_t hint = hi;
+            if (e + 1 < ne && plen[r + 1] > 0) hint = pw0[r + 1] - 1;
+            if (hint > lo && hint <= hi && Pr[hint - w0] - pa <= lim && Tr[hint - w0] == ta)
+                lo = hint;
             while (hi > lo) {
                 const int64_t step = (hi - lo + 31) / 32;
                 const int64_t probe = lo + (int64_t)(lane + 1) * step;
