@@ -6,6 +6,7 @@ to this file.  The library exports only the C ABI of include/spcoarsen.h.
 from __future__ import annotations
 
 import concurrent.futures as cf
+import glob
 import os
 import shutil
 import subprocess
@@ -39,8 +40,8 @@ def _stale(out: str, deps) -> bool:
 
 def build(force: bool = False, verbose: bool = False, extra=()) -> str:
     os.makedirs(BUILD, exist_ok=True)
-    headers = [os.path.join(CSRC, "spc_internal.cuh"), os.path.join(ROOT, "include", "spcoarsen.h"),
-               os.path.abspath(__file__)]
+    headers = sorted(glob.glob(os.path.join(CSRC, "*.cuh"))) + [
+        os.path.join(ROOT, "include", "spcoarsen.h"), os.path.abspath(__file__)]
     cc = nvcc()
     jobs = []
     objs = []

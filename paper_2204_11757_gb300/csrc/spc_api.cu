@@ -263,11 +263,22 @@ spc_status sync_status(spc_context* ctx) {
 
 // ---- small kernels of the driver ------------------------------------------------------------
 
-__global__ void k_compose(int64_t n, const int32_t* __restrict__ next, int32_t* __restrict__ cur) {
+// the lifts of up to kComposeMax levels, applied in order
+constexpr int kComposeMax = 64;
+struct LiftChain {
+    const int32_t* lift[kComposeMax];
+    int levels;
+};
+
+// out[x] = lift_{L-1}[ ... lift_1[lift_0[x]] ... ]: every node's super-node after all levels
+__global__ void k_compose_all(int64_t n, LiftChain ch, int32_t* __restrict__ out) {
     spc::pdl_wait();
     for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n;
-         x += (int64_t)gridDim.x * blockDim.x)
-        cur[x] = next[cur[x]];
+         x += (int64_t)gridDim.x * blockDim.x) {
+        int32_t y = ch.lift[0][x];
+        for (int l = 1; l < ch.levels; ++l) y = ch.lift[l][y];
+        out[x] = y;
+    }
 }
 
 __global__ void k_compose_emap(int64_t m, const int32_t* __restrict__ next, int32_t* __restrict__ cur) {
@@ -571,11 +582,14 @@ static spc_status run_levels(spc_context* ctx, const GraphView& g0, const Schedu
         cur_gptr = lv.graph_ptr_c.as<int64_t>();
     }
     // composed lift
-    SPC_CUDA(cudaMemcpyAsync(lift_total_dev, ctx->levels[0].lift.p, (size_t)g0.n * 4,
-                             cudaMemcpyDeviceToDevice, ctx->stream));
-    for (int l = 1; l < L; ++l) {
-        SPC_LAUNCH(ctx, k_compose, grid_for(g0.n, kThreads, maxb), kThreads, 0, g0.n,
-                   ctx->levels[l].lift.as<int32_t>(), lift_total_dev);
+    for (int l = 0; l < L;) {  // chains of up to kComposeMax lifts, continuing in place
+        LiftChain ch{};
+        ch.levels = 0;
+        if (l > 0) ch.lift[ch.levels++] = lift_total_dev;
+        while (l < L && ch.levels < kComposeMax)
+            ch.lift[ch.levels++] = ctx->levels[l++].lift.as<int32_t>();
+        SPC_LAUNCH(ctx, k_compose_all, grid_for(g0.n, kThreads, maxb), kThreads, 0, g0.n, ch,
+                   lift_total_dev);
     }
     *n_c_final = cur.n;
     if (capturing(ctx)) return SPC_OK;

@@ -15,6 +15,7 @@
 #include <atomic>
 #include <memory>
 
+#include "spc_scan.cuh"
 #include "spc_seqsum.cuh"
 
 namespace spc {
@@ -93,6 +94,52 @@ __device__ __forceinline__ void warp_count(int32_t* cnt, int32_t key, bool act) 
     const unsigned peers = __match_any_sync(0xffffffffu, act ? key : -1);
     if (act && (int)(threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(cnt + key, __popc(peers));
 }
+
+// scan storer of two packed counts (spc_scan.cuh PairLd): both exclusive prefixes and totals
+struct PairOffSt {
+    int32_t* oa;
+    int32_t* ob;
+    int64_t n;
+    struct Local {};
+    __device__ Local begin() const { return Local{}; }
+    __device__ void operator()(Local&, int64_t g, bool valid, unsigned long long excl,
+                               unsigned long long) const {
+        if (!valid) return;
+        oa[g] = (int32_t)(excl >> 31);
+        ob[g] = (int32_t)(excl & 0x7fffffffull);
+    }
+    __device__ void finish(Local&) const {}
+    __device__ void total(unsigned long long tot) const {
+        oa[n] = (int32_t)(tot >> 31);
+        ob[n] = (int32_t)(tot & 0x7fffffffull);
+    }
+};
+
+// the same for the coarse degrees (upper, lower), plus the coarse row pointers: row U starts
+// after every upper and lower entry of the rows before it
+struct RowPtrSt {
+    int32_t* ufirst;
+    int32_t* lstart;
+    int64_t* rowptr;
+    int64_t n;
+    struct Local {};
+    __device__ Local begin() const { return Local{}; }
+    __device__ void operator()(Local&, int64_t g, bool valid, unsigned long long excl,
+                               unsigned long long) const {
+        if (!valid) return;
+        const int32_t u = (int32_t)(excl >> 31), l = (int32_t)(excl & 0x7fffffffull);
+        ufirst[g] = u;
+        lstart[g] = l;
+        rowptr[g] = (int64_t)u + l;
+    }
+    __device__ void finish(Local&) const {}
+    __device__ void total(unsigned long long tot) const {
+        const int32_t u = (int32_t)(tot >> 31), l = (int32_t)(tot & 0x7fffffffull);
+        ufirst[n] = u;
+        lstart[n] = l;
+        rowptr[n] = (int64_t)u + l;
+    }
+};
 
 // ---- grouping by buckets --------------------------------------------------------------
 // The coarse edges need the inter edges in (lower super-node a, upper super-node b, eid)
@@ -560,15 +607,6 @@ k_fill_lower_ranked(int64_t m_c, const uint32_t* __restrict__ slot,
     }
 }
 
-__global__ void __launch_bounds__(kThreads)
-k_rowptr(int64_t n_c, const int32_t* __restrict__ ufirst, const int32_t* __restrict__ lstart,
-         int64_t* __restrict__ rowptr_c) {
-    spc::pdl_wait();
-    for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u <= n_c;
-         u += (int64_t)gridDim.x * blockDim.x)
-        rowptr_c[u] = (int64_t)ufirst[u] + (int64_t)lstart[u];
-}
-
 // row V, lower part: coarse edges (U, V), U < V, in transpose-sorted order
 template <class WT>
 __global__ void __launch_bounds__(kThreads)
@@ -724,8 +762,8 @@ spc_status contract_typed(spc_context* ctx, const GraphView& g, const int32_t* l
                lift, cnt_c, cnt_i, bstats, list_c, list_i, reinterpret_cast<uint32_t*>(up_deg),
                reinterpret_cast<uint32_t*>(low_deg), (int64_t)(n_c + 1),
                W.counters.as<int32_t>());
-    SPC_TRY(scan_i32(ctx, cnt_c, off_c, n_c));
-    SPC_TRY(scan_i32(ctx, cnt_i, off_i, n_c));
+    SPC_TRY(scan_fused<unsigned long long>(ctx, n_c, PairLd{cnt_c, cnt_i},
+                                           PairOffSt{off_c, off_i, n_c}, (double)n_c * 16.0));
     int64_t bv[8];
     {
         const void* ptrs[8] = {off_c + n_c, off_i + n_c, bstats, bstats + 1, bstats + 2,
@@ -870,11 +908,10 @@ spc_status contract_typed(spc_context* ctx, const GraphView& g, const int32_t* l
     // its upper entries (coarse edges (U, V), contiguous in coarse-edge order)
     int32_t* ufirst = W.ufirst.as<int32_t>();
     int32_t* lstart = W.lstart.as<int32_t>();
-    SPC_TRY(scan_i32(ctx, up_deg, ufirst, n_c));
-    SPC_TRY(scan_i32(ctx, low_deg, lstart, n_c));
     int64_t* rowptr_c = lv.rowptr_c.as<int64_t>();
-    SPC_LAUNCH(ctx, k_rowptr, grid_for(n_c + 1, kThreads, maxb), kThreads, 0, n_c, ufirst, lstart,
-               rowptr_c);
+    SPC_TRY(scan_fused<unsigned long long>(ctx, n_c, PairLd{up_deg, low_deg},
+                                           RowPtrSt{ufirst, lstart, rowptr_c, n_c},
+                                           (double)n_c * 24.0));
     if (m_c > 0) {
         const int gc = grid_for(m_c, kThreads, maxb);
         uint32_t* tkey = W.t_key.as<uint32_t>();

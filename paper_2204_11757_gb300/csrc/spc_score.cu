@@ -514,7 +514,7 @@ k_score_warp_row(int64_t n, const int64_t* __restrict__ rowptr, const int32_t* _
 // by the coordinates of v's row ("specials": an extra term p_vx, or |p_Hx - p_vx| where both
 // rows have x).  Runs are evaluated exactly from per-binade prefix tables of H's row.
 
-constexpr int kHeavySpecials = 8;  // edges whose other row is longer go to the warp kernel
+constexpr int kHeavySpecials = 32;  // edges whose other row is longer go to the warp kernel
 
 // light hub edges: one thread per entry (H, v) of a hub row, flat over all hubs
 // Hub edge (H, v) where v's only neighbour is H: the union of the two rows is H's row with the
