@@ -95,23 +95,60 @@ __device__ __forceinline__ void warp_count(int32_t* cnt, int32_t key, bool act) 
     if (act && (int)(threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(cnt + key, __popc(peers));
 }
 
-// scan storer of two packed counts (spc_scan.cuh PairLd): both exclusive prefixes and totals
-struct PairOffSt {
-    int32_t* oa;
-    int32_t* ob;
+// Buckets of at most kSmallBucket items: each item is ranked by one thread (at most
+// kSmallBucket comparisons per item).  Longer ones, up to kBlockBucket items: one CTA sorts the
+// bucket in shared memory (bitonic network); they are listed by the scan of
+// the bucket sizes.
+constexpr int kSmallBucket = 64;
+constexpr int kBlockBucket = 8192;
+constexpr int kBlockSortThreads = 512;
+
+// scan storer of the two packed bucket sizes (spc_scan.cuh PairLd: inter, intra): both
+// exclusive prefixes and totals, and per side the ranking statistics -- sum of squared sizes in
+// stats[0] / stats[2], largest size in stats[1] / stats[3] -- and the list of buckets longer
+// than kSmallBucket (counts in stats[6] / stats[7]).
+struct BucketOffSt {
+    int32_t* off_c;
+    int32_t* off_i;
     int64_t n;
-    struct Local {};
-    __device__ Local begin() const { return Local{}; }
-    __device__ void operator()(Local&, int64_t g, bool valid, unsigned long long excl,
-                               unsigned long long) const {
+    unsigned long long* stats;
+    int32_t* list_c;
+    int32_t* list_i;
+    struct Local {
+        unsigned long long sq[2], mx[2];
+    };
+    __device__ Local begin() const { return Local{{0ull, 0ull}, {0ull, 0ull}}; }
+    __device__ void operator()(Local& L, int64_t g, bool valid, unsigned long long excl,
+                               unsigned long long val) const {
         if (!valid) return;
-        oa[g] = (int32_t)(excl >> 31);
-        ob[g] = (int32_t)(excl & 0x7fffffffull);
+        off_c[g] = (int32_t)(excl >> 31);
+        off_i[g] = (int32_t)(excl & 0x7fffffffull);
+        const unsigned long long c[2] = {val >> 31, val & 0x7fffffffull};
+#pragma unroll
+        for (int side = 0; side < 2; ++side) {
+            L.sq[side] += c[side] * c[side];
+            L.mx[side] = c[side] > L.mx[side] ? c[side] : L.mx[side];
+            if (c[side] > (unsigned long long)kSmallBucket)
+                (side ? list_i : list_c)[atomicAdd(stats + 6 + side, 1ull)] = (int32_t)g;
+        }
     }
-    __device__ void finish(Local&) const {}
+    __device__ void finish(Local& L) const {
+        __shared__ unsigned long long sh[4];
+        if (threadIdx.x < 4) sh[threadIdx.x] = 0ull;
+        __syncthreads();
+        for (int side = 0; side < 2; ++side) {
+            if (L.sq[side]) atomicAdd(&sh[2 * side], L.sq[side]);
+            if (L.mx[side]) atomicMax(&sh[2 * side + 1], L.mx[side]);
+        }
+        __syncthreads();
+        if (threadIdx.x < 4 && sh[threadIdx.x]) {
+            if (threadIdx.x & 1) atomicMax(stats + threadIdx.x, sh[threadIdx.x]);
+            else atomicAdd(stats + threadIdx.x, sh[threadIdx.x]);
+        }
+    }
     __device__ void total(unsigned long long tot) const {
-        oa[n] = (int32_t)(tot >> 31);
-        ob[n] = (int32_t)(tot & 0x7fffffffull);
+        off_c[n] = (int32_t)(tot >> 31);
+        off_i[n] = (int32_t)(tot & 0x7fffffffull);
     }
 };
 
@@ -150,37 +187,26 @@ struct RowPtrSt {
 // the squared bucket size; the host takes this path only while that stays a small multiple
 // of the item count (and every bucket is short), else it sorts by radix.
 
-// Buckets of at most kSmallBucket items: each item is ranked by one thread (at most
-// kSmallBucket comparisons per item).  Longer ones, up to kBlockBucket items: one CTA sorts the
-// bucket in shared memory (bitonic network); they are listed by the counting kernel.
-constexpr int kSmallBucket = 64;
-constexpr int kBlockBucket = 8192;
-constexpr int kBlockSortThreads = 512;
-
-// bucket of fine edge e: (inter, bucket id); one tag per (array, bucket) for warp matching
-__device__ __forceinline__ unsigned long long bucket_tag(int32_t U, int32_t V, bool act) {
-    if (!act) return ~0ull;
-    return U != V ? (1ull << 32) | (uint32_t)(U < V ? U : V) : (2ull << 32) | (uint32_t)U;
+// bucket of fine edge e, one 32-bit tag per (array, bucket) for warp matching: an inter edge's
+// lower super-node, an intra edge's super-node with the top bit set (ids are below 2^31);
+// inactive lanes all-ones
+__device__ __forceinline__ uint32_t bucket_tag(int32_t U, int32_t V, bool act) {
+    if (!act) return 0xffffffffu;
+    return U != V ? (uint32_t)(U < V ? U : V) : (0x80000000u | (uint32_t)U);
 }
 
-// Step 1: the bucket sizes (one atomic per group of equal buckets in a warp), with per block
-// the sum of squared sizes and the largest size, inter buckets in stats[0..1], intra buckets
-// in stats[2..3]; buckets longer than kSmallBucket are listed (counts in stats[6..7]).  Also zeroes what the contraction adds into later: the coarse degree
-// counts and the long-segment list counts of both streams.
+// Step 1: the bucket sizes, one atomic (without a result) per group of equal buckets in a
+// warp.  Also zeroes what the contraction adds into later: the coarse degree counts and the
+// long-segment list counts of both streams.
 __global__ void __launch_bounds__(kThreads)
 k_bucket_count(int64_t m, const int32_t* __restrict__ eu, const int32_t* __restrict__ ev,
                const int32_t* __restrict__ lift, int32_t* cnt_c, int32_t* cnt_i,
-               unsigned long long* stats, int32_t* __restrict__ list_c,
-               int32_t* __restrict__ list_i, uint32_t* __restrict__ zero_b,
+               unsigned long long* stats, uint32_t* __restrict__ zero_b,
                uint32_t* __restrict__ zero_c, int64_t words_bc, int32_t* __restrict__ counters) {
     spc::pdl_wait();
-    __shared__ unsigned long long sh[4];
-    if (threadIdx.x < 4) sh[threadIdx.x] = 0ull;
-    __syncthreads();
     const int lane = threadIdx.x & 31;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    unsigned long long sq[2] = {0ull, 0ull}, mx[2] = {0ull, 0ull};
     for (int64_t e0 = (int64_t)blockIdx.x * blockDim.x; e0 < m; e0 += stride) {  // warp-uniform
         const int64_t e = e0 + threadIdx.x;
         const bool act = e < m;
@@ -189,24 +215,10 @@ k_bucket_count(int64_t m, const int32_t* __restrict__ eu, const int32_t* __restr
             U = lift[eu[e]];
             V = lift[ev[e]];
         }
-        const unsigned long long tag = bucket_tag(U, V, act);
+        const uint32_t tag = bucket_tag(U, V, act);
         const unsigned peers = __match_any_sync(0xffffffffu, tag);
-        if (act && lane == __ffs(peers) - 1) {
-            const int k = __popc(peers);
-            const int side = U != V ? 0 : 1;
-            const int32_t b = (int32_t)(uint32_t)tag;
-            const int32_t old = atomicAdd((side ? cnt_i : cnt_c) + b, k);
-            // (old + k)^2 - old^2: the squares telescope to the final size squared
-            sq[side] += (unsigned long long)k * (2ull * (unsigned long long)old + k);
-            const unsigned long long now = (unsigned long long)old + k;
-            mx[side] = now > mx[side] ? now : mx[side];
-            if (old <= kSmallBucket && now > kSmallBucket)  // the bucket just became long
-                (side ? list_i : list_c)[atomicAdd(stats + 6 + side, 1ull)] = b;
-        }
-    }
-    for (int i = 0; i < 2; ++i) {
-        if (sq[i]) atomicAdd(&sh[2 * i], sq[i]);
-        if (mx[i]) atomicMax(&sh[2 * i + 1], mx[i]);
+        if (act && lane == __ffs(peers) - 1)
+            atomicAdd((U != V ? cnt_c : cnt_i) + (tag & 0x7fffffffu), __popc(peers));
     }
     for (int64_t i = t0; i < words_bc; i += stride) {
         zero_b[i] = 0u;
@@ -217,11 +229,6 @@ k_bucket_count(int64_t m, const int32_t* __restrict__ eu, const int32_t* __restr
         counters[11] = 0;
         stats[4] = 0ull;  // the lower rows' statistics, added by k_emit_segments
         stats[5] = 0ull;
-    }
-    __syncthreads();
-    if (threadIdx.x < 4 && sh[threadIdx.x]) {
-        if (threadIdx.x & 1) atomicMax(stats + threadIdx.x, sh[threadIdx.x]);
-        else atomicAdd(stats + threadIdx.x, sh[threadIdx.x]);
     }
 }
 
@@ -249,11 +256,11 @@ k_bucket_scatter(int64_t m, int nb, const int32_t* __restrict__ eu,
             U = lift[eu[e]];
             V = lift[ev[e]];
         }
-        const unsigned long long tag = bucket_tag(U, V, act);
+        const uint32_t tag = bucket_tag(U, V, act);
         const unsigned peers = __match_any_sync(0xffffffffu, tag);
         const int leader = __ffs(peers) - 1;
         const bool inter = U != V;
-        const int32_t b = (int32_t)(uint32_t)tag;
+        const int32_t b = (int32_t)(tag & 0x7fffffffu);
         int32_t old = 0;
         if (act && lane == leader) old = atomicSub((inter ? cnt_c : cnt_i) + b, __popc(peers));
         old = __shfl_sync(0xffffffffu, old, leader);
@@ -272,7 +279,7 @@ k_bucket_scatter(int64_t m, int nb, const int32_t* __restrict__ eu,
     }
 }
 
-// Step 3, long buckets (listed by k_bucket_count): one CTA per bucket sorts the bucket's
+// Step 3, long buckets (listed by the scan of the sizes): one CTA per bucket sorts the bucket's
 // items in shared memory by one 64-bit key -- (b << 32) | eid for inter edges (a is the
 // bucket), the eid for intra edges -- with a bitonic network over the next power of two
 // (padding keys all ones), then writes them back in order: inter edges as (key, eid) with
@@ -759,11 +766,12 @@ spc_status contract_typed(spc_context* ctx, const GraphView& g, const int32_t* l
     }
     W.b_dirty = true;
     SPC_LAUNCH(ctx, k_bucket_count, gm, kThreads, 0, m, W.eu.as<int32_t>(), W.ev.as<int32_t>(),
-               lift, cnt_c, cnt_i, bstats, list_c, list_i, reinterpret_cast<uint32_t*>(up_deg),
+               lift, cnt_c, cnt_i, bstats, reinterpret_cast<uint32_t*>(up_deg),
                reinterpret_cast<uint32_t*>(low_deg), (int64_t)(n_c + 1),
                W.counters.as<int32_t>());
-    SPC_TRY(scan_fused<unsigned long long>(ctx, n_c, PairLd{cnt_c, cnt_i},
-                                           PairOffSt{off_c, off_i, n_c}, (double)n_c * 16.0));
+    SPC_TRY(scan_fused<unsigned long long>(
+        ctx, n_c, PairLd{cnt_c, cnt_i}, BucketOffSt{off_c, off_i, n_c, bstats, list_c, list_i},
+        (double)n_c * 16.0));
     int64_t bv[8];
     {
         const void* ptrs[8] = {off_c + n_c, off_i + n_c, bstats, bstats + 1, bstats + 2,

@@ -404,28 +404,21 @@ k_bv_hook(const int32_t* __restrict__ count, const int32_t* __restrict__ wl_e,
     }
 }
 
-// scan storer of the forest flags: pos[e] = forest edges before e, and the forest edges as a
-// (score key, eid) list in eid order
+// forest edges -> (score key, eid) list in eid order
 template <class KT>
-struct MsfCompactSt {
-    int32_t* pos;
-    int64_t m;
-    const KT* key;
-    KT* out_k;
-    uint32_t* out_v;
-    struct Local {};
-    __device__ Local begin() const { return Local{}; }
-    __device__ void operator()(Local&, int64_t e, bool valid, int32_t excl, int32_t f) const {
-        if (!valid) return;
-        pos[e] = excl;
-        if (f) {
-            out_k[excl] = key[e];
-            out_v[excl] = (uint32_t)e;
+__global__ void __launch_bounds__(kThreads)
+k_compact_msf(int64_t m, const uint8_t* __restrict__ msf, const int32_t* __restrict__ pos,
+              const KT* __restrict__ key, KT* __restrict__ out_k, uint32_t* __restrict__ out_v) {
+    spc::pdl_wait();
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        if (msf[e]) {
+            const int32_t q = pos[e];
+            out_k[q] = key[e];
+            out_v[q] = (uint32_t)e;
         }
     }
-    __device__ void finish(Local&) const {}
-    __device__ void total(int32_t tot) const { pos[m] = tot; }
-};
+}
 
 // graph id of every node of a block-diagonal batch
 __global__ void k_node_graph(int64_t n, int64_t B, const int64_t* __restrict__ graph_ptr,
@@ -889,19 +882,17 @@ spc_status select_typed(spc_context* ctx, const GraphView& g, const KT* key,
             if (round > 64) return SPC_ERR_TIMEOUT;
             // slot `out` (list and count) is the next round's input
         }
-        // forest flags scanned and the forest edges compacted in the same pass
-        SPC_TRY(scan_fused<int32_t>(
-            ctx, m, ArrayLd<uint8_t, int32_t>{W.msf.as<uint8_t>()},
-            MsfCompactSt<KT>{pos, m, key, W.sel_key.as<KT>(), W.sel_val.as<uint32_t>()},
-            (double)m * (1.0 + 4.0)));
+        SPC_TRY(scan_flags_u8(ctx, W.msf.as<uint8_t>(), pos, m));
         SPC_TRY(read_i32(ctx, pos + m, &n_msf));
         // the prefix's forest holds Kruskal's first n_msf merges; enough when >= n - n_c
         if (!use_prefix || n_msf >= k_need) break;
         use_prefix = false;
     }
     // ---- 2. lightest forest edges per graph ---------------------------------------------
-    KT* sk = W.sel_key.as<KT>();  // filled by the forest-flag scan
+    KT* sk = W.sel_key.as<KT>();
     uint32_t* sv = W.sel_val.as<uint32_t>();
+    SPC_LAUNCH(ctx, k_compact_msf<KT>, grid_for(m, kThreads, maxb), kThreads, 0, m,
+               W.msf.as<uint8_t>(), pos, key, sk, sv);
     const int key_bits = sizeof(KT) == 8 ? 63 : 31;  // scores are >= +0: sign bit clear
     const int64_t k_single_sel = batched ? 0 : (n - sa.target > 0 ? n - sa.target : 0);
     if (!batched && k_single_sel > 0 && k_single_sel < n_msf) {
