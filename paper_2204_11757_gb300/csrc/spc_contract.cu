@@ -357,6 +357,7 @@ k_bucket_rank_inter(int64_t cnt, int nb, const int32_t* __restrict__ off_c,
         if (hi - lo > kSmallBucket) continue;
         int32_t r = 0;
         bool first = true;
+#pragma unroll 4
         for (int32_t j = lo; j < hi; ++j) {
             const uint64_t kj = key[j];
             const uint32_t vj = val[j];
@@ -384,6 +385,7 @@ k_bucket_rank_intra(int64_t cnt, const int32_t* __restrict__ off_i,
         const int32_t lo = off_i[U], hi = off_i[U + 1];
         if (hi - lo > kSmallBucket) continue;
         int32_t r = 0;
+#pragma unroll 4
         for (int32_t j = lo; j < hi; ++j) r += ival[j] < v ? 1 : 0;
         ival2[lo + r] = v;
     }
@@ -487,7 +489,22 @@ k_segsum_short(int64_t nseg, const int32_t* __restrict__ start, const uint32_t* 
             continue;
         }
         typename CT<WT>::Acc s = 0;
-        for (int32_t j = j0; j < j1; ++j) s = CT<WT>::add(s, w_und[idx[j]]);
+        if (j1 - j0 <= 4) {
+            // short segment: every index and term in flight before the left-to-right sum
+            uint32_t ix[4];
+            WT t[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                if (j0 + q < j1) ix[q] = idx[j0 + q];
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                if (j0 + q < j1) t[q] = w_und[ix[q]];
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                if (j0 + q < j1) s = CT<WT>::add(s, t[q]);
+        } else {
+            for (int32_t j = j0; j < j1; ++j) s = CT<WT>::add(s, w_und[idx[j]]);
+        }
         if constexpr (std::is_same<WT, int32_t>::value && sizeof(Out) == 4) {
             if (s > 2147483647ll) atomicOr(status, DEV_OVERFLOW);
         }
@@ -607,6 +624,7 @@ k_fill_lower_ranked(int64_t m_c, const uint32_t* __restrict__ slot,
         const int32_t V = cV[k];
         const int32_t lo = lstart[V], hi = lstart[V + 1];
         int32_t r = 0;
+#pragma unroll 4
         for (int32_t j = lo; j < hi; ++j) r += slot[j] < k ? 1 : 0;
         const int64_t pos = rowptr_c[V] + r;
         col_c[pos] = cU[k];

@@ -913,8 +913,8 @@ spc_status select_typed(spc_context* ctx, const GraphView& g, const KT* key,
             SPC_LAUNCH(ctx, k_rsel_round<KT>, gsel, kThreads, 0, r, n_msf, nullptr, sk, sv,
                        hist, sst);
         }
-        SPC_LAUNCH(ctx, k_rsel_compact<KT>, gsel, kThreads, 0, kFull - 1, n_msf, sk, sv, sst,
-                   ck, cv, cn);
+        SPC_LAUNCH(ctx, k_rsel_compact<KT>, grid_for(n_msf, kThreads, maxb), kThreads, 0,
+                   kFull - 1, n_msf, sk, sv, sst, ck, cv, cn);
         // few candidates (the usual case): the remaining rounds in one CTA; many (a level
         // where a large share of the forest has exactly equal scores): a launch per round
         int64_t ncand = 0;
