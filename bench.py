@@ -272,10 +272,7 @@ FP64_PEAK_GOPS = 625.0
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the dominant kernel,
 # from an ncu capture of the same kernel; None where no capture of the current kernel exists.
-# The 2048^2 mesh's score: the mean over the six level launches of one step (871.4, 255.6,
-# 103.0, 39.4, 8.6 and 2.1 MB; profiles/score_traffic_c2_tri2048_f64.md), like `achieved`,
-# which averages the same launches.
-TRAFFIC = {("c2_tri2048_f64", "(k_score_edges<P, Key>)"): 213.35e6}
+TRAFFIC = {}
 
 
 def run_batched(args):

@@ -362,7 +362,7 @@ __device__ __forceinline__ bool has_mirror(const int32_t* __restrict__ col, cons
 
 // S3, edge-tile schedule: one thread per undirected edge; consecutive threads take consecutive
 // edge ids, which mostly share row a (cached), and walk rows a and b in step.
-template <class PT, class KT>
+template <class PT, class KT, int K>
 __global__ void __launch_bounds__(kThreads)
 k_score_edges(int64_t m, const int32_t* __restrict__ eu, const int32_t* __restrict__ ev,
               const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
@@ -374,43 +374,75 @@ k_score_edges(int64_t m, const int32_t* __restrict__ eu, const int32_t* __restri
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     uint32_t n_add = 0, n_sub = 0;  // union coordinates, coordinates in both rows
     bool asym = false;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < m; e += stride) {
-        const int32_t a = eu[e], b = ev[e];
-        int64_t i = rowptr[a];
-        const int64_t ie = rowptr[a + 1];
-        int64_t j = rowptr[b];
-        const int64_t je = rowptr[b + 1];
-        if (ie - i > kLongRow || je - j > kLongRow) {  // hub edge: k_score_hub
-            // a long row a has its mirrors checked with the long rows; a long row b only
-            // holds the mirror of this entry, so it is looked up here
-            if (validate && ie - i <= kLongRow)
-                asym = asym || !has_mirror(col, w, wsize, j, je, a,
-                                           weight_bits(w_und, wsize, e));
-            continue;
+    constexpr int32_t kEnd = 0x7fffffff;
+    // K edges per thread walked together: K independent addition chains hide the latency of
+    // the binary64 additions and of the row loads; each edge keeps its own order
+    for (int64_t e0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e0 < m;
+         e0 += (int64_t)K * stride) {
+        int64_t e[K], i[K], ie[K], j[K], je[K];
+        int32_t a[K], ca[K], cb[K];
+        PT s[K];
+        bool mirror[K];
+#pragma unroll
+        for (int q = 0; q < K; ++q) {
+            e[q] = e0 + (int64_t)q * stride;
+            s[q] = PT(0);
+            mirror[q] = false;
+            ca[q] = kEnd;
+            cb[q] = kEnd;
+            i[q] = ie[q] = j[q] = je[q] = 0;
+            a[q] = 0;
+            if (e[q] >= m) {
+                e[q] = -1;
+                continue;
+            }
+            a[q] = eu[e[q]];
+            const int32_t b = ev[e[q]];
+            i[q] = rowptr[a[q]];
+            ie[q] = rowptr[a[q] + 1];
+            j[q] = rowptr[b];
+            je[q] = rowptr[b + 1];
+            if (ie[q] - i[q] > kLongRow || je[q] - j[q] > kLongRow) {  // hub edge: k_score_hub
+                // a long row a has its mirrors checked with the long rows; a long row b only
+                // holds the mirror of this entry, so it is looked up here
+                if (validate && ie[q] - i[q] <= kLongRow)
+                    asym = asym || !has_mirror(col, w, wsize, j[q], je[q], a[q],
+                                               weight_bits(w_und, wsize, e[q]));
+                e[q] = -1;
+                continue;
+            }
+            ca[q] = i[q] < ie[q] ? col[i[q]] : kEnd;
+            cb[q] = j[q] < je[q] ? col[j[q]] : kEnd;
         }
-        // one uniform step per coordinate of the union: t = |pa - pb| with the missing side
-        // read as 0 (exact: |x - 0| = x), so every lane issues the same two FP operations
-        PT s = PT(0);
-        constexpr int32_t kEnd = 0x7fffffff;
-        int32_t ca = i < ie ? col[i] : kEnd;
-        int32_t cb = j < je ? col[j] : kEnd;
+        // one uniform step per coordinate of each union: t = |pa - pb| with the missing side
+        // read as 0 (exact: |x - 0| = x), so every live walk issues the same two FP operations.
         // S0's symmetry check rides on the walk: coordinate a of row b is the mirror entry of
-        // (a, b), and its weight must have the same bits
-        bool mirror = false;
-        while (ca != kEnd || cb != kEnd) {
-            const bool ta = ca <= cb, tb = cb <= ca;
-            if (validate && tb && cb == a)
-                mirror = weight_bits(w, wsize, j) == weight_bits(w_und, wsize, e);
-            const PT pa = ta ? p[i] : PT(0);
-            const PT pb = tb ? p[j] : PT(0);
-            s = p_add(s, p_absdiff(pa, pb));
-            ++n_add;
-            n_sub += (ta && tb) ? 1u : 0u;
-            if (ta) { ++i; ca = i < ie ? col[i] : kEnd; }
-            if (tb) { ++j; cb = j < je ? col[j] : kEnd; }
+        // (a, b), and its weight must have the same bits.
+        for (;;) {
+            bool any = false;
+#pragma unroll
+            for (int q = 0; q < K; ++q) {
+                if (ca[q] == kEnd && cb[q] == kEnd) continue;
+                any = true;
+                const bool ta = ca[q] <= cb[q], tb = cb[q] <= ca[q];
+                if (validate && tb && cb[q] == a[q])
+                    mirror[q] = weight_bits(w, wsize, j[q]) == weight_bits(w_und, wsize, e[q]);
+                const PT pa = ta ? p[i[q]] : PT(0);
+                const PT pb = tb ? p[j[q]] : PT(0);
+                s[q] = p_add(s[q], p_absdiff(pa, pb));
+                ++n_add;
+                n_sub += (ta && tb) ? 1u : 0u;
+                if (ta) { ++i[q]; ca[q] = i[q] < ie[q] ? col[i[q]] : kEnd; }
+                if (tb) { ++j[q]; cb[q] = j[q] < je[q] ? col[j[q]] : kEnd; }
+            }
+            if (!any) break;
         }
-        score[e] = key_bits(s);
-        asym = asym || (validate && !mirror);
+#pragma unroll
+        for (int q = 0; q < K; ++q) {
+            if (e[q] < 0) continue;
+            score[e[q]] = key_bits(s[q]);
+            asym = asym || (validate && !mirror[q]);
+        }
     }
     if (asym) atomicOr(status, DEV_NOT_SYMMETRIC);
     count_ops(ops, n_add, n_sub);
@@ -774,6 +806,20 @@ k_score_hub_heavy(const int64_t* __restrict__ rowptr, const int32_t* __restrict_
     }
 }
 
+// edges walked together by a thread of k_score_edges (4 spilled and ran slower)
+constexpr int kScoreChains = 2;
+
+template <class P, class Key>
+static spc_status launch_score_edges(spc_context* ctx, int64_t m, const GraphView& g, Work& W,
+                                     void* score, int wsize, int vflag, uint32_t* status,
+                                     bool count) {
+    SPC_LAUNCH(ctx, (k_score_edges<P, Key, kScoreChains>),
+               grid_for(m, kThreads, ctx->num_sms * 8), kThreads, 0, m, W.eu.as<int32_t>(), W.ev.as<int32_t>(), g.rowptr, g.col,
+               W.p.as<P>(), static_cast<Key*>(score), g.w, W.w_und.p, wsize, vflag, status,
+               count ? op_counter(ctx, "(k_score_edges<P, Key, kScoreChains>)", 0) : nullptr);
+    return SPC_OK;
+}
+
 static int pick_default_schedule(int64_t n, int64_t nnz) {
     return (n > 0 && nnz / n > 48) ? 2 : 1;  // long rows favour a warp per row
 }
@@ -878,9 +924,7 @@ static spc_status score_typed(spc_context* ctx, GraphView& g, bool validate, voi
                 for (auto& ev : ctx->tune_ev) SPC_CUDA(cudaEventCreate(&ev));
             const int gw = grid_for(n, kThreads / 32, maxb);
             SPC_CUDA(cudaEventRecord(ctx->tune_ev[0], ctx->stream));
-            SPC_LAUNCH(ctx, (k_score_edges<P, Key>), grid_for(m, kThreads, maxb), kThreads, 0, m,
-                       W.eu.as<int32_t>(), W.ev.as<int32_t>(), g.rowptr, g.col, W.p.as<P>(),
-                       static_cast<Key*>(score), g.w, W.w_und.p, wsize, vflag, status, nullptr);
+            SPC_TRY((launch_score_edges<P, Key>(ctx, m, g, W, score, wsize, vflag, status, false)));
             SPC_CUDA(cudaEventRecord(ctx->tune_ev[1], ctx->stream));
             SPC_LAUNCH(ctx, (k_score_warp_row<P, Key>), gw, kThreads, 0, n, g.rowptr, g.col,
                        W.p.as<P>(), W.up_ptr.as<int32_t>(), W.first_up.as<int32_t>(),
@@ -919,10 +963,7 @@ static spc_status score_typed(spc_context* ctx, GraphView& g, bool validate, voi
                    op_counter(ctx, "(k_score_warp_row<P, Key>)", 2));
     } else {
         note_bytes(ctx, score_bytes);
-        SPC_LAUNCH(ctx, (k_score_edges<P, Key>), grid_for(m, kThreads, maxb), kThreads, 0, m,
-                   W.eu.as<int32_t>(), W.ev.as<int32_t>(), g.rowptr, g.col, W.p.as<P>(),
-                   static_cast<Key*>(score), g.w, W.w_und.p, wsize, vflag, status,
-                   op_counter(ctx, "(k_score_edges<P, Key>)", 0));
+        SPC_TRY((launch_score_edges<P, Key>(ctx, m, g, W, score, wsize, vflag, status, true)));
     }
     if (n_long == 0) return validate ? check_status(ctx) : SPC_OK;
     side.reset();  // the main stream waits for the tables
