@@ -272,7 +272,10 @@ FP64_PEAK_GOPS = 625.0
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the dominant kernel,
 # from an ncu capture of the same kernel; None where no capture of the current kernel exists.
-TRAFFIC = {}
+# The 2048^2 mesh's score: the mean over the six level launches of one step (852.4, 257.4,
+# 104.6, 39.5, 8.6 and 2.1 MB; profiles/score_traffic_c2_tri2048_f64.md), the same launches
+# that `achieved` averages.
+TRAFFIC = {("c2_tri2048_f64", "(k_score_edges<P, Key, kScoreChains>)"): 210.80e6}
 
 
 def run_batched(args):
