@@ -152,24 +152,40 @@ struct BucketOffSt {
     }
 };
 
-// the same for the coarse degrees (upper, lower), plus the coarse row pointers: row U starts
-// after every upper and lower entry of the rows before it
+// the same for the coarse degrees (upper, lower), plus the coarse row pointers -- row U starts
+// after every upper and lower entry of the rows before it -- and the lower rows' ranking
+// statistics: sum of squared sizes in stats[0], largest size in stats[1]
 struct RowPtrSt {
     int32_t* ufirst;
     int32_t* lstart;
     int64_t* rowptr;
     int64_t n;
-    struct Local {};
-    __device__ Local begin() const { return Local{}; }
-    __device__ void operator()(Local&, int64_t g, bool valid, unsigned long long excl,
-                               unsigned long long) const {
+    unsigned long long* stats;
+    struct Local {
+        unsigned long long sq, mx;
+    };
+    __device__ Local begin() const { return Local{0ull, 0ull}; }
+    __device__ void operator()(Local& L, int64_t g, bool valid, unsigned long long excl,
+                               unsigned long long val) const {
         if (!valid) return;
         const int32_t u = (int32_t)(excl >> 31), l = (int32_t)(excl & 0x7fffffffull);
         ufirst[g] = u;
         lstart[g] = l;
         rowptr[g] = (int64_t)u + l;
+        const unsigned long long low = val & 0x7fffffffull;
+        L.sq += low * low;
+        L.mx = low > L.mx ? low : L.mx;
     }
-    __device__ void finish(Local&) const {}
+    __device__ void finish(Local& L) const {
+        __shared__ unsigned long long sh[2];
+        if (threadIdx.x < 2) sh[threadIdx.x] = 0ull;
+        __syncthreads();
+        if (L.sq) atomicAdd(&sh[0], L.sq);
+        if (L.mx) atomicMax(&sh[1], L.mx);
+        __syncthreads();
+        if (threadIdx.x == 0 && sh[0]) atomicAdd(stats, sh[0]);
+        if (threadIdx.x == 1 && sh[1]) atomicMax(stats + 1, sh[1]);
+    }
     __device__ void total(unsigned long long tot) const {
         const int32_t u = (int32_t)(tot >> 31), l = (int32_t)(tot & 0x7fffffffull);
         ufirst[n] = u;
@@ -227,7 +243,7 @@ k_bucket_count(int64_t m, const int32_t* __restrict__ eu, const int32_t* __restr
     if (t0 == 0) {
         counters[9] = 0;
         counters[11] = 0;
-        stats[4] = 0ull;  // the lower rows' statistics, added by k_emit_segments
+        stats[4] = 0ull;  // the lower rows' statistics, added by the row-pointer scan
         stats[5] = 0ull;
     }
 }
@@ -406,21 +422,15 @@ k_heads(int64_t cnt, const K* __restrict__ key, uint8_t* __restrict__ head) {
 }
 
 // coarse edge id of every sorted item; emap, perm; segment starts and end points at heads.
-// Every coarse edge (U, V) also counts into up_deg[U] and low_deg[V]; the lower rows (buckets
-// by V) get their ranking statistics in stats[0] (sum of squared sizes), stats[1] (largest).
+// Every coarse edge (U, V) also counts into up_deg[U] and low_deg[V] (result-free atomics, one
+// per group of equal rows in a warp).
 __global__ void __launch_bounds__(kThreads)
 k_emit_segments(int64_t cnt, int nb, const uint64_t* __restrict__ key,
                 const uint32_t* __restrict__ val, const uint8_t* __restrict__ head,
                 const int32_t* __restrict__ hpos, int32_t* __restrict__ emap,
                 int32_t* __restrict__ perm, int32_t* __restrict__ seg, int32_t* __restrict__ cU,
-                int32_t* __restrict__ cV, int32_t* up_deg, int32_t* low_deg,
-                unsigned long long* stats) {
+                int32_t* __restrict__ cV, int32_t* up_deg, int32_t* low_deg) {
     spc::pdl_wait();
-    __shared__ unsigned long long sh[2];
-    if (threadIdx.x < 2) sh[threadIdx.x] = 0ull;
-    __syncthreads();
-    const int lane = threadIdx.x & 31;
-    unsigned long long sq = 0ull, mx = 0ull;
     for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x; i0 < cnt;
          i0 += (int64_t)gridDim.x * blockDim.x) {  // warp-uniform
         const int64_t i = i0 + threadIdx.x;
@@ -443,20 +453,8 @@ k_emit_segments(int64_t cnt, int nb, const uint64_t* __restrict__ key,
             }
         }
         warp_count(up_deg, U, h);
-        const unsigned peers = __match_any_sync(0xffffffffu, h ? V : -1);
-        if (h && lane == __ffs(peers) - 1) {
-            const int k = __popc(peers);
-            const int32_t old = atomicAdd(low_deg + V, k);
-            sq += (unsigned long long)k * (2ull * (unsigned long long)old + k);
-            const unsigned long long now = (unsigned long long)old + k;
-            mx = now > mx ? now : mx;
-        }
+        warp_count(low_deg, V, h);
     }
-    if (sq) atomicAdd(&sh[0], sq);
-    if (mx) atomicMax(&sh[1], mx);
-    __syncthreads();
-    if (threadIdx.x == 0 && sh[0]) atomicAdd(stats, sh[0]);
-    if (threadIdx.x == 1 && sh[1]) atomicMax(stats + 1, sh[1]);
 }
 
 // run r of a sorted key array starts at start[r]; start[n_runs] = cnt
@@ -913,7 +911,17 @@ spc_status contract_typed(spc_context* ctx, const GraphView& g, const int32_t* l
         const int gi = grid_for(m_inter, kThreads, maxb);
         SPC_TRY(scan_flags_u8(ctx, head, hpos, m_inter));
         SPC_LAUNCH(ctx, k_emit_segments, gi, kThreads, 0, m_inter, nb, skey, sval, head, hpos,
-                   emap, perm, seg, cU, cV, up_deg, low_deg, bstats + 4);
+                   emap, perm, seg, cU, cV, up_deg, low_deg);
+    }
+    // coarse CSR: row U holds its lower entries (coarse edges (U', U), ascending U') and then
+    // its upper entries (coarse edges (U, V), contiguous in coarse-edge order)
+    int32_t* ufirst = W.ufirst.as<int32_t>();
+    int32_t* lstart = W.lstart.as<int32_t>();
+    int64_t* rowptr_c = lv.rowptr_c.as<int64_t>();
+    SPC_TRY(scan_fused<unsigned long long>(ctx, n_c, PairLd{up_deg, low_deg},
+                                           RowPtrSt{ufirst, lstart, rowptr_c, n_c, bstats + 4},
+                                           (double)n_c * 24.0));
+    if (m_inter > 0) {
         int64_t ev[3];
         const void* ptrs[3] = {hpos + m_inter, bstats + 4, bstats + 5};
         const int bytes[3] = {4, 8, 8};
@@ -930,14 +938,6 @@ spc_status contract_typed(spc_context* ctx, const GraphView& g, const int32_t* l
         SPC_TRY((long_segment_sums<WT, WT>(ctx, seg, reinterpret_cast<const uint32_t*>(perm),
                                             nullptr, W.w_und.as<WT>(), a_und)));
     }
-    // coarse CSR: row U holds its lower entries (coarse edges (U', U), ascending U') and then
-    // its upper entries (coarse edges (U, V), contiguous in coarse-edge order)
-    int32_t* ufirst = W.ufirst.as<int32_t>();
-    int32_t* lstart = W.lstart.as<int32_t>();
-    int64_t* rowptr_c = lv.rowptr_c.as<int64_t>();
-    SPC_TRY(scan_fused<unsigned long long>(ctx, n_c, PairLd{up_deg, low_deg},
-                                           RowPtrSt{ufirst, lstart, rowptr_c, n_c},
-                                           (double)n_c * 24.0));
     if (m_c > 0) {
         const int gc = grid_for(m_c, kThreads, maxb);
         uint32_t* tkey = W.t_key.as<uint32_t>();
