@@ -582,19 +582,38 @@ __global__ void k_fs_walk(int64_t nseq, const F* __restrict__ terms,
         const int64_t L = len[q];
         const F* x = terms + base[q];
         const int lo_eb = eblo[q], ne = nE[q];
+        // every binade's window (start, entries, table offset): lane l holds binades l and
+        // l + 32 (at most 64), fetched by shuffles instead of dependent loads in the walk
+        int64_t mw0[2] = {0, 0}, mlen[2] = {0, 0}, mtoff[2] = {0, 0};
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int e = lane + 32 * h;
+            if (e < ne) {
+                const int64_t r = poff[q] + e;
+                mw0[h] = pw0[r];
+                mlen[h] = plen[r];
+                mtoff[h] = ptoff[r];
+            }
+        }
         F s = F(0);
         int64_t a = 0;
         while (ne > 0 && a < L) {
             if (s == F(0)) { s = x[a++]; continue; }
             const unsigned long long sb = FB<F>::bits(s);
             const int eb = (int)(sb >> FB<F>::kMant);
-            const int e = eb - lo_eb;
+            const int e = eb - lo_eb;  // the same in every lane
             if (eb == 0 || e < 0 || e >= ne) { s = FB<F>::add(s, x[a++]); continue; }
-            const int64_t r = poff[q] + e;
-            const int64_t w0 = pw0[r], nent = plen[r];
+            const int eh = e >> 5, el = e & 31;
+            const int64_t w0 = __shfl_sync(0xffffffffu, eh ? mw0[1] : mw0[0], el);
+            const int64_t nent = __shfl_sync(0xffffffffu, eh ? mlen[1] : mlen[0], el);
+            const int64_t toff = __shfl_sync(0xffffffffu, eh ? mtoff[1] : mtoff[0], el);
+            // the next binade's window start (hint below)
+            const int e1 = e + 1 < ne ? e + 1 : e;
+            const int64_t nw0 = __shfl_sync(0xffffffffu, (e1 >> 5) ? mw0[1] : mw0[0], e1 & 31);
+            const int64_t nlen = __shfl_sync(0xffffffffu, (e1 >> 5) ? mlen[1] : mlen[0], e1 & 31);
             if (nent == 0 || a < w0 || a > w0 + nent - 2) { s = FB<F>::add(s, x[a++]); continue; }
-            const unsigned long long* Pr = P + ptoff[r];
-            const int32_t* Tr = T + ptoff[r];
+            const unsigned long long* Pr = P + toff;
+            const int32_t* Tr = T + toff;
             const unsigned long long pa = Pr[a - w0];
             if (pa >= kSat - (1ull << 55)) { s = FB<F>::add(s, x[a++]); continue; }
             const unsigned long long S =
@@ -607,7 +626,7 @@ __global__ void k_fs_walk(int64_t nseq, const F* __restrict__ terms,
             // answer is usually at or after the step before it (the last binade: the end).
             // One probe there, if it is good, leaves only the windows' overlap to search.
             int64_t hint = hi;
-            if (e + 1 < ne && plen[r + 1] > 0) hint = pw0[r + 1] - 1;
+            if (e + 1 < ne && nlen > 0) hint = nw0 - 1;
             if (hint > lo && hint <= hi && Pr[hint - w0] - pa <= lim && Tr[hint - w0] == ta)
                 lo = hint;
             while (hi > lo) {
