@@ -225,9 +225,13 @@ __device__ F tab_run(F s, int64_t a, int64_t b, const F* __restrict__ x,
         const unsigned long long S = (sb & ((1ull << FB<F>::kMant) - 1ull)) | (1ull << FB<F>::kMant);
         const unsigned long long lim = (1ull << (FB<F>::kMant + 1)) - S;
         int64_t lo = a, hi = b;  // largest k in [a, b] whose prefix stays on this grid
-        while (lo < hi) {
-            const int64_t mid = (lo + hi + 1) >> 1;
-            if (Pe[mid] - base <= lim) lo = mid; else hi = mid - 1;
+        if (Pe[b] - base <= lim) {
+            lo = b;  // the whole run stays on this grid: no search
+        } else {
+            while (lo < hi) {
+                const int64_t mid = (lo + hi + 1) >> 1;
+                if (Pe[mid] - base <= lim) lo = mid; else hi = mid - 1;
+            }
         }
         int64_t k = lo;
         const int32_t ta = Te[a];
@@ -268,6 +272,7 @@ __device__ F tab_run_warp(F s, int64_t a, int64_t b, const F* __restrict__ x,
         const int32_t ta = Te[a];
         // largest k in [a, b] with Pe[k] - base <= lim and no tie among [a, k)
         int64_t lo = a, hi = b;  // invariant: lo is good; answer in [lo, hi]
+        if (Pe[b] - base <= lim && Te[b] == ta) lo = b;  // the whole run: no search
         while (hi - lo > 0) {
             const int64_t span = hi - lo;
             const int64_t step = (span + 31) / 32;
