@@ -87,6 +87,7 @@ struct Work {
     Buf up_cnt, up_ptr, first_up, eu, ev, w_und, deg, p;       // S0-S2
     Buf long_rows, lr_base, lr_len, lr_idx, lr_eoff, heavy, seg_base, seg_len, seg_idx, seg_terms;
     Buf hub_leaf;                                               // per hub: its leaf edges' score
+    Buf hub_map, hub_slot;                                      // column maps of the largest hubs
     SeqTabBufs tab_w, tab_p, tab_s;                             // long sums: degrees, hubs, segments
     Buf parent, best_k[2], best_e[2], wl_e[2], wl_u[2], wl_v[2], msf;   // S5 MSF
     Buf counters, key_hist;                                     // small device ints

@@ -6,6 +6,7 @@
 // Every sum here runs sequentially in ascending column order with IEEE round-to-nearest adds
 // (__dadd_rn / __fadd_rn, no FMA), and p = w / d is one IEEE division per stored entry, so
 // the results are the same bits on every run and every schedule.
+#include <algorithm>
 #include <memory>
 
 #include "spc_seqsum.cuh"
@@ -549,6 +550,63 @@ k_score_warp_row(int64_t n, const int64_t* __restrict__ rowptr, const int32_t* _
 constexpr int kHeavySpecials = 32;  // edges whose other row is longer go to the warp kernel
 
 // light hub edges: one thread per entry (H, v) of a hub row, flat over all hubs
+// Column positions of the largest hub rows: for up to kMaxHubMaps hubs holding at least an
+// eighth of the nodes (and 2048 entries), map[slot * n + x] = the first position of the hub's
+// row whose column is >= x, so the hub kernels place a coordinate with one load instead of a
+// binary search over the hub's row.
+constexpr int kMaxHubMaps = 8;
+struct HubMaps {
+    const int32_t* map;   // nullptr: no maps on this level
+    const int32_t* slot;  // per long row: its map slot or -1
+    int64_t n;
+};
+
+__global__ void k_hub_slots(const int32_t* __restrict__ long_count,
+                            const int64_t* __restrict__ lr_len, int64_t n, int maps,
+                            int32_t* __restrict__ slot_of, int32_t* __restrict__ slot_hub,
+                            int32_t* __restrict__ nslots) {
+    spc::pdl_wait();
+    __shared__ int32_t cnt;
+    if (threadIdx.x == 0) cnt = 0;
+    __syncthreads();
+    const int32_t c = *long_count;
+    for (int32_t i = threadIdx.x; i < c; i += blockDim.x) {
+        int32_t sl = -1;
+        const int64_t d = lr_len[i];
+        if (d >= 2048 && d * 8 >= n) {
+            const int32_t s = atomicAdd(&cnt, 1);
+            if (s < maps) {
+                sl = s;
+                slot_hub[s] = i;
+            }
+        }
+        slot_of[i] = sl;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) *nslots = cnt < maps ? cnt : maps;
+}
+
+__global__ void __launch_bounds__(kThreads)
+k_hub_posmap(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+             const int32_t* __restrict__ long_rows, const int32_t* __restrict__ slot_hub,
+             const int32_t* __restrict__ nslots, int64_t n, int32_t* __restrict__ map) {
+    spc::pdl_wait();
+    const int64_t total = (int64_t)*nslots * n;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t s = (int32_t)(t / n);
+        const int64_t x = t - (int64_t)s * n;
+        const int64_t H = long_rows[slot_hub[s]];
+        const int64_t r0 = rowptr[H];
+        int64_t lo = 0, hi = rowptr[H + 1] - r0;
+        while (lo < hi) {
+            const int64_t mid = (lo + hi) >> 1;
+            if ((int64_t)col[r0 + mid] < x) lo = mid + 1; else hi = mid;
+        }
+        map[t] = (int32_t)lo;
+    }
+}
+
 // Hub edge (H, v) where v's only neighbour is H: the union of the two rows is H's row with the
 // single term |0 - p_v[H]| = 1 (p_v[H] = w / w) inserted at H's own column position, so every
 // such edge of H has the same score.  A warp evaluates it once per hub.
@@ -585,7 +643,7 @@ k_score_hub(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
             const PT* __restrict__ p, const int32_t* __restrict__ up_ptr,
             const int32_t* __restrict__ nlow, const int32_t* __restrict__ long_rows,
             const int32_t* __restrict__ long_count, const int64_t* __restrict__ lr_eoff,
-            SeqTabView tab, const PT* __restrict__ leaf, KT* __restrict__ score,
+            SeqTabView tab, HubMaps hm, const PT* __restrict__ leaf, KT* __restrict__ score,
             int32_t* __restrict__ heavy, int32_t* __restrict__ heavy_count,
             const uint32_t* status) {
     spc::pdl_wait();
@@ -621,6 +679,8 @@ k_score_hub(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
         const unsigned long long* P = tab.P + tab.tab_off[i];
         const int32_t* T = tab.T + tab.tab_off[i];
         const int eblo = tab.eblo[i], nE = tab.nE[i];
+        const int32_t* hmap = (hm.map && hm.slot[i] >= 0) ? hm.map + (int64_t)hm.slot[i] * hm.n
+                                                          : nullptr;
         PT s = PT(0);
         int64_t a = 0;
         int64_t jH = -1;  // position of H in v's row
@@ -628,9 +688,14 @@ k_score_hub(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
             const int32_t x = col[rv + j];
             if ((int64_t)x == H) jH = j;
             int64_t l2 = a, h2 = dH;  // first position >= a in H's row with column >= x
-            while (l2 < h2) {
-                const int64_t mid = (l2 + h2) >> 1;
-                if (cH[mid] < x) l2 = mid + 1; else h2 = mid;
+            if (hmap) {
+                l2 = hmap[x];
+                if (l2 < a) l2 = a;
+            } else {
+                while (l2 < h2) {
+                    const int64_t mid = (l2 + h2) >> 1;
+                    if (cH[mid] < x) l2 = mid + 1; else h2 = mid;
+                }
             }
             s = tab_run<PT>(s, a, l2, pH, P, T, eblo, nE, dH + 1);
             PT t;
@@ -661,7 +726,7 @@ k_score_hub_heavy(const int64_t* __restrict__ rowptr, const int32_t* __restrict_
                   const PT* __restrict__ p, const int32_t* __restrict__ up_ptr,
                   const int32_t* __restrict__ nlow, const int32_t* __restrict__ long_rows,
                   const int32_t* __restrict__ long_count, const int64_t* __restrict__ lr_eoff,
-                  SeqTabView tab, const int32_t* __restrict__ heavy,
+                  SeqTabView tab, HubMaps hm, const int32_t* __restrict__ heavy,
                   const int32_t* __restrict__ heavy_count, KT* __restrict__ score,
                   const uint32_t* status) {
     spc::pdl_wait();
@@ -689,6 +754,8 @@ k_score_hub_heavy(const int64_t* __restrict__ rowptr, const int32_t* __restrict_
         const unsigned long long* P = tab.P + tab.tab_off[i];
         const int32_t* T = tab.T + tab.tab_off[i];
         const int eblo = tab.eblo[i], nE = tab.nE[i];
+        const int32_t* hmap = (hm.map && hm.slot[i] >= 0) ? hm.map + (int64_t)hm.slot[i] * hm.n
+                                                          : nullptr;
         const int64_t d1 = dH + 1;
         PT s = PT(0);
         int64_t a = 0;      // next unread position of H's row
@@ -704,9 +771,14 @@ k_score_hub_heavy(const int64_t* __restrict__ rowptr, const int32_t* __restrict_
             if (act) {
                 x = col[rv + j];
                 int64_t l2 = a, h2 = dH;
-                while (l2 < h2) {
-                    const int64_t mid = (l2 + h2) >> 1;
-                    if (cH[mid] < x) l2 = mid + 1; else h2 = mid;
+                if (hmap) {
+                    l2 = hmap[x];
+                    if (l2 < a) l2 = a;
+                } else {
+                    while (l2 < h2) {
+                        const int64_t mid = (l2 + h2) >> 1;
+                        if (cH[mid] < x) l2 = mid + 1; else h2 = mid;
+                    }
                 }
                 pos = l2;
                 common = pos < dH && cH[pos] == x;
@@ -946,11 +1018,26 @@ static spc_status score_typed(spc_context* ctx, GraphView& g, bool validate, voi
     // stream, while the other edges are scored here), then one thread per hub entry (one warp
     // per entry whose other row is long)
     std::unique_ptr<SideBranch> side;
+    HubMaps hm{nullptr, nullptr, n};
     if (n_long > 0) {
         side.reset(new SideBranch(ctx));
         SPC_TRY(side->status());
         SPC_TRY(seqtab_build(ctx, W.p.p, std::is_same<P, float>::value, n_long,
                              W.lr_base.as<int64_t>(), W.lr_len.as<int64_t>(), W.tab_p));
+        // column maps of the largest hubs, within 64 M entries of memory
+        const int64_t maps = std::min<int64_t>(kMaxHubMaps, (int64_t(64) << 20) / (n + 1));
+        if (maps > 0) {
+            SPC_TRY(ensure(ctx, W.hub_map, (size_t)(maps * n + 1) * 4));
+            SPC_TRY(ensure(ctx, W.hub_slot, (size_t)(n_long + kMaxHubMaps) * 4));
+            int32_t* slot_of = W.hub_slot.as<int32_t>();
+            int32_t* slot_hub = slot_of + n_long;
+            int32_t* nslots = W.counters.as<int32_t>() + 13;
+            SPC_LAUNCH(ctx, k_hub_slots, 1, 1024, 0, long_count, W.lr_len.as<int64_t>(), n,
+                       (int)maps, slot_of, slot_hub, nslots);
+            SPC_LAUNCH(ctx, k_hub_posmap, grid_for(maps * n, kThreads, maxb), kThreads, 0,
+                       g.rowptr, g.col, long_rows, slot_hub, nslots, n, W.hub_map.as<int32_t>());
+            hm = HubMaps{W.hub_map.as<int32_t>(), slot_of, n};
+        }
         side->leave();
     }
     if (schedule == 2) {
@@ -972,11 +1059,11 @@ static spc_status score_typed(spc_context* ctx, GraphView& g, bool validate, voi
                g.rowptr, g.col, W.p.as<P>(), long_rows, long_count, tv, W.hub_leaf.as<P>());
     SPC_LAUNCH(ctx, (k_score_hub<P, Key>), maxb, kThreads, 0, g.rowptr, g.col, W.p.as<P>(),
                W.up_ptr.as<int32_t>(), W.first_up.as<int32_t>(), long_rows, long_count,
-               W.lr_eoff.as<int64_t>(), tv, W.hub_leaf.as<P>(), static_cast<Key*>(score),
+               W.lr_eoff.as<int64_t>(), tv, hm, W.hub_leaf.as<P>(), static_cast<Key*>(score),
                W.heavy.as<int32_t>(), heavy_count, status);
     SPC_LAUNCH(ctx, (k_score_hub_heavy<P, Key>), persist, kThreads, 0, g.rowptr, g.col,
                W.p.as<P>(), W.up_ptr.as<int32_t>(), W.first_up.as<int32_t>(), long_rows,
-               long_count, W.lr_eoff.as<int64_t>(), tv, W.heavy.as<int32_t>(), heavy_count,
+               long_count, W.lr_eoff.as<int64_t>(), tv, hm, W.heavy.as<int32_t>(), heavy_count,
                static_cast<Key*>(score), status);
     return validate ? check_status(ctx) : SPC_OK;  // every input check, symmetry included
 }
