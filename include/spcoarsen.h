@@ -290,6 +290,11 @@ SPC_API spc_status spc_kernel_profile(spc_context* ctx, char* buf, size_t len);
  * launches count their kernel nodes). */
 SPC_API int64_t spc_launch_count(const spc_context* ctx);
 
+/* 1 if the last spc_coarsen or spc_coarsen_batched call was served by replaying the captured
+ * graph of the previous identical call (same sizes, same input checksum, and every logged
+ * size confirmed on the device), 0 if it ran host-driven. */
+SPC_API int spc_last_call_replayed(const spc_context* ctx);
+
 #ifdef __cplusplus
 }
 #endif

@@ -324,6 +324,11 @@ class Context:
     def launch_count(self) -> int:
         return int(self.lib.spc_launch_count(self._handle))
 
+    @property
+    def last_call_replayed(self) -> bool:
+        """Whether the last coarsening call replayed the previous identical call's graph."""
+        return bool(self.lib.spc_last_call_replayed(self._handle))
+
 
 @dataclasses.dataclass
 class ContractionPlan:

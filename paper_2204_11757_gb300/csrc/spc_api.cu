@@ -753,6 +753,7 @@ static spc_status replay_graph(spc_context* ctx, bool* mismatch) {
 static spc_status drive(spc_context* ctx, const GraphView& v, const Schedule& S, bool use_graph,
                         int64_t* ncf, int32_t* warn) {
     Replay& R = ctx->replay;
+    ctx->replayed_last = 0;
     SPC_TRY(ensure(ctx, ctx->work.lift_final, ((size_t)v.n + 1) * 4));
     int32_t* lift_int = ctx->work.lift_final.as<int32_t>();
     const std::vector<int64_t> key = call_key(v, S);
@@ -770,6 +771,7 @@ static spc_status drive(spc_context* ctx, const GraphView& v, const Schedule& S,
             const spc_status st = replay_graph(ctx, &mismatch);
             if (st < 0) return st;
             if (!mismatch) {
+                ctx->replayed_last = 1;
                 const int L = (int)R.metas.size();
                 for (int l = 0; l < L; ++l) {
                     LevelBufs& lv = ctx->levels[l];
@@ -1227,5 +1229,7 @@ spc_status spc_kernel_profile(spc_context* ctx, char* buf, size_t len) {
 }
 
 int64_t spc_launch_count(const spc_context* ctx) { return ctx ? ctx->launches : 0; }
+
+int spc_last_call_replayed(const spc_context* ctx) { return ctx ? ctx->replayed_last : 0; }
 
 }  // extern "C"

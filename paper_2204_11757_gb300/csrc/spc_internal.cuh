@@ -178,6 +178,7 @@ struct spc_context {
     spc::Work work;
     std::vector<spc::LevelBufs> levels;
     int32_t n_levels = 0;
+    int32_t replayed_last = 0;       // the last coarsening call was a graph replay
     spc::Timer timer;
     int64_t launches = 0;
     spc::Replay replay;

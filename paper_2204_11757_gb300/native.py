@@ -88,6 +88,7 @@ SIGNATURES = {
     "spc_kernel_time": (ctypes.c_int, [P, PI64, ctypes.POINTER(ctypes.c_double)]),
     "spc_kernel_profile": (ctypes.c_int, [P, ctypes.c_char_p, ctypes.c_size_t]),
     "spc_launch_count": (ctypes.c_int64, [P]),
+    "spc_last_call_replayed": (ctypes.c_int, [P]),
 }
 
 _lib = None

@@ -248,6 +248,41 @@ def test_contract_bucket_and_radix_paths(ctx, dt, kb, bucket_path):
 
 
 @pytest.mark.parametrize("dt", [np.float64, np.int32])
+def test_contract_many_giant_buckets(ctx, dt):
+    """Nine disjoint K_{91,91} blocks, each a pair of super-nodes: nine buckets above 8192 items
+    (the radix path), chained: the oracle's coarse graph bit for bit."""
+    api = _api()
+    rng = np.random.default_rng(11)
+    kb, blocks = 91, 9
+    eu, ev, lift = [], [], []
+    for q in range(blocks):
+        A = 2 * kb * q + np.arange(kb)
+        B = A + kb
+        bu, bv = np.meshgrid(A, B, indexing="ij")
+        eu.append(bu.ravel())
+        ev.append(bv.ravel())
+        lift += [2 * q] * kb + [2 * q + 1] * kb
+    eu.append(np.arange(0, 2 * kb * (blocks - 1), 2 * kb))  # chain the blocks
+    ev.append(np.arange(2 * kb, 2 * kb * blocks, 2 * kb))
+    eu = np.concatenate(eu)
+    ev = np.concatenate(ev)
+    n = 2 * kb * blocks
+    w = (rng.uniform(0.5, 2.0, eu.size) if dt == np.float64
+         else rng.integers(1, 100, eu.size)).astype(dt)
+    g = I.csr_from_edges(n, eu, ev, w)
+    lift = np.array(lift, dtype=np.int32)
+    ref = O.contract(g, lift, 2 * blocks)
+    ctx.time_kernel("*")
+    try:
+        lv = ctx.contract(api.CSR.from_graph(g), torch.from_numpy(lift).cuda(), 2 * blocks)
+        prof = ctx.kernel_profile()
+    finally:
+        ctx.time_kernel(None)
+    assert any("k_classify" in k for k in prof), sorted(prof)
+    _check_level(lv, O.Level(n_c=2 * blocks, lift=lift, coarse=ref))
+
+
+@pytest.mark.parametrize("dt", [np.float64, np.int32])
 @pytest.mark.parametrize("center_last", [False, True])
 def test_contract_star_rows_paths(ctx, dt, center_last):
     """A star of 2000 leaves, each node its own super-node after a relabelling.  With the
@@ -284,6 +319,33 @@ def test_contract_star_rows_paths(ctx, dt, center_last):
     assert long_sorted == (not center_last), sorted(prof)
     assert any("k_bucket_rank_inter" in k for k in prof), sorted(prof)
     _check_level(lv, O.Level(n_c=n, lift=lift, coarse=ref))
+
+
+def test_repeated_coarsening_replays_with_giant_super_nodes(ctx):
+    """Three disjoint cliques K_150 (11,175 edges each) joined by two edges, coarsened to 3:
+    three giant super-nodes.  Every value the host reads while coarsening must be the same on
+    a repeated call (no order set by atomics), or the replay's check of its logged values
+    fails and every call runs host-driven; the third call must be a replay."""
+    api = _api()
+    k, cl = 150, 3
+    eu, ev = [], []
+    for q in range(cl):
+        iu, iv = np.triu_indices(k, 1)
+        eu.append(iu + q * k)
+        ev.append(iv + q * k)
+    eu.append(np.arange(cl - 1) * k)
+    ev.append(np.arange(1, cl) * k + 1)
+    eu = np.concatenate(eu)
+    ev = np.concatenate(ev)
+    w = np.random.default_rng(3).uniform(0.5, 2.0, eu.size)
+    g = I.csr_from_edges(k * cl, eu, ev, w)
+    ref = O.coarsen_level(g, cl)
+    csr = api.CSR.from_graph(g)
+    for _ in range(3):
+        lift, n_c, st = ctx.coarsen(csr, cl, levels=1)
+    assert ctx.last_call_replayed
+    assert n_c == ref.n_c
+    _check_level(ctx.level(0), ref)
 
 
 # ---- full method ------------------------------------------------------------------------------------
