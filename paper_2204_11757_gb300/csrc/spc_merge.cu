@@ -152,7 +152,7 @@ template <> struct MinKey<unsigned int> {
 // score prefix (key >> tau_shift <= *tau_top).  Each thread takes kMkItems edges per pass
 // (their loads overlap), and the survivors are appended with one global atomic per block
 // and pass.
-constexpr int kMkItems = 4;
+constexpr int kMkItems = 2;
 
 template <class KT>
 __global__ void __launch_bounds__(kThreads)
