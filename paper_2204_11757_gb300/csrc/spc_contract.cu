@@ -521,14 +521,13 @@ k_segsum_long(const int32_t* __restrict__ start, const uint32_t* __restrict__ id
     for (int32_t q = blockIdx.x; q < cnt; q += gridDim.x) {
         const int64_t r = long_list[q];
         const int32_t j0 = start[r], j1 = start[r + 1];
-        typename CT<WT>::Acc s;
-        if constexpr (std::is_same<WT, int32_t>::value) {
-            s = cta_sum_i64(j1 - j0, [&](int64_t k) { return (long long)w_und[idx[j0 + k]]; });
-        } else {
-            s = cta_seqsum<8>(WT(0), j1 - j0, [&](int64_t k) { return w_und[idx[j0 + k]]; });
-        }
+        // integer weights only (exact in any order); floating-point long segments go through
+        // the per-binade tables (long_segment_sums)
+        static_assert(std::is_same<WT, int32_t>::value, "integer weights only");
+        const long long s =
+            cta_sum_i64(j1 - j0, [&](int64_t k) { return (long long)w_und[idx[j0 + k]]; });
         if (threadIdx.x == 0) {
-            if constexpr (std::is_same<WT, int32_t>::value && sizeof(Out) == 4) {
+            if constexpr (sizeof(Out) == 4) {
                 if (s > 2147483647ll) atomicOr(status, DEV_OVERFLOW);
             }
             out[key ? (int64_t)key[j0] : r] = (Out)s;

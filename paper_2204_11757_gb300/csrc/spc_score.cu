@@ -103,7 +103,7 @@ k_rows_degree(int64_t n, int64_t nnz, const int64_t* __restrict__ rowptr,
             nlow_out[x] = 0;
             continue;
         }
-        if (r1 - r0 > kLongRow) {  // a whole CTA takes it (k_long_rows_degree)
+        if (r1 - r0 > kLongRow) {  // long rows: k_long_rows_meta and the per-binade tables
             long_rows[atomicAdd(long_count, 1)] = (int32_t)x;
             continue;
         }

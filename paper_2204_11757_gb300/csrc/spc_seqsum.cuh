@@ -17,9 +17,9 @@
 //   first step that crosses the binade or is a tie, one native addition there, repeat.  The
 //   running sum only grows (terms >= 0), so a sum crosses at most ~60 binades.
 //
-// Two evaluators are built on it: cta_seqsum (one long sum by a whole CTA, chunk by chunk) and
-// per-grid prefix tables over a hub row, which let every edge of the hub evaluate its runs of
-// that row with a few binary searches (spc_score.cu).
+// The evaluator built on it: per-binade prefix tables over a long sequence (spc_seqtab.cu),
+// which let every edge of a hub row evaluate its runs of that row with a few searches
+// (spc_score.cu) and a full sum jump from binade to binade.
 #pragma once
 
 #include "spc_internal.cuh"
@@ -81,91 +81,6 @@ __device__ __forceinline__ unsigned long long grid_units(F t, int eb, bool* tie)
 template <class F>
 __device__ __forceinline__ F from_units(unsigned long long S, int eb) {
     return FB<F>::from_bits(((unsigned long long)eb << FB<F>::kMant) + (S - (1ull << FB<F>::kMant)));
-}
-
-// One long sequential sum by a whole CTA (all threads call it with the same arguments and
-// get the same result).  term(i), i in [0, L), must be >= 0.  kItems consecutive terms per
-// thread and chunk.
-template <int kItems, class F, class Term>
-__device__ F cta_seqsum(F s, int64_t L, const Term& term) {
-    __shared__ unsigned long long sh_tot[32];
-    __shared__ int sh_first;
-    __shared__ unsigned long long sh_excl;
-    const int tid = threadIdx.x, nt = blockDim.x;
-    const int lane = tid & 31, warp = tid >> 5, nw = (nt + 31) >> 5;
-    int64_t k = 0;
-    while (k < L) {
-        const unsigned long long sb = FB<F>::bits(s);
-        const int eb = (int)(sb >> FB<F>::kMant);
-        if (s == F(0) || eb == 0) {  // zero or subnormal running sum: one native step
-            s = FB<F>::add(s, term(k));
-            ++k;
-            continue;
-        }
-        const unsigned long long S = (sb & ((1ull << FB<F>::kMant) - 1ull)) | (1ull << FB<F>::kMant);
-        const unsigned long long lim = (1ull << (FB<F>::kMant + 1)) - S;  // S + Q <= 2^(p) allowed
-        const int64_t chunk = (L - k) < (int64_t)nt * kItems ? (L - k) : (int64_t)nt * kItems;
-        unsigned long long r[kItems];
-        bool tie[kItems];
-        unsigned long long run = 0;
-#pragma unroll
-        for (int j = 0; j < kItems; ++j) {
-            const int64_t i = (int64_t)tid * kItems + j;
-            tie[j] = false;
-            r[j] = 0;
-            if (i < chunk) r[j] = grid_units<F>(term(k + i), eb, &tie[j]);
-            run = sat_add(run, r[j]);
-        }
-        // block exclusive scan of the per-thread totals (saturating)
-        unsigned long long v = run;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            unsigned long long t = __shfl_up_sync(0xffffffffu, v, o);
-            if (lane >= o) v = sat_add(v, t);
-        }
-        if (lane == 31) sh_tot[warp] = v;
-        if (tid == 0) sh_first = 0x7fffffff;
-        __syncthreads();
-        if (warp == 0) {
-            unsigned long long x = lane < nw ? sh_tot[lane] : 0ull;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                unsigned long long t = __shfl_up_sync(0xffffffffu, x, o);
-                if (lane >= o) x = sat_add(x, t);
-            }
-            sh_tot[lane] = x;
-        }
-        __syncthreads();
-        unsigned long long wex = __shfl_up_sync(0xffffffffu, v, 1);  // exclusive within warp
-        if (lane == 0) wex = 0ull;
-        unsigned long long excl = sat_add(warp > 0 ? sh_tot[warp - 1] : 0ull, wex);
-        const unsigned long long total = sh_tot[nw - 1];
-        // first step that leaves the binade or is a tie
-        int mine = 0x7fffffff;
-        unsigned long long pre = excl;
-#pragma unroll
-        for (int j = 0; j < kItems; ++j) {
-            const int64_t i = (int64_t)tid * kItems + j;
-            const unsigned long long q = sat_add(pre, r[j]);
-            if (i < chunk && mine == 0x7fffffff && (q > lim || tie[j])) mine = (int)i;
-            if (mine == 0x7fffffff) pre = q;
-        }
-        if (mine != 0x7fffffff) atomicMin(&sh_first, mine);
-        __syncthreads();
-        const int first = sh_first;
-        if (first != 0x7fffffff && first / kItems == tid && mine == first) sh_excl = pre;
-        __syncthreads();
-        if (first == 0x7fffffff) {
-            s = from_units<F>(S + total, eb);
-            k += chunk;
-        } else {
-            s = from_units<F>(S + sh_excl, eb);
-            s = FB<F>::add(s, term(k + first));
-            k += first + 1;
-        }
-        __syncthreads();
-    }
-    return s;
 }
 
 // Sum of int64 terms by a whole CTA (exact in any order).
