@@ -287,12 +287,12 @@ SPC_API spc_status spc_kernel_time(spc_context* ctx, int64_t* launches, double* 
 SPC_API spc_status spc_kernel_profile(spc_context* ctx, char* buf, size_t len);
 
 /* Number of kernel launches issued by the context since it was created (replayed graph
- * launches count their kernel nodes). */
+ * launches count their kernel nodes); 0 for a NULL context. */
 SPC_API int64_t spc_launch_count(const spc_context* ctx);
 
 /* 1 if the last spc_coarsen or spc_coarsen_batched call was served by replaying the captured
  * graph of the previous identical call (same sizes, same input checksum, and every logged
- * size confirmed on the device), 0 if it ran host-driven. */
+ * size confirmed on the device), 0 if it ran host-driven or ctx is NULL. */
 SPC_API int spc_last_call_replayed(const spc_context* ctx);
 
 #ifdef __cplusplus
