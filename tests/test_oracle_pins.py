@@ -18,12 +18,12 @@ from paper_2204_11757_gb300 import inputs as I
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
 
-# ---- hand-worked example (tests/golden/hand_example.txt) ---------------------------------
+# ---- hand-worked examples (tests/golden/hand_*.txt) -----------------------------------------
 
-def _parse_golden():
+def _parse_golden(name):
     rows = {}
     ncs = {}
-    with open(os.path.join(GOLDEN, "hand_example.txt")) as fh:
+    with open(os.path.join(GOLDEN, name)) as fh:
         for line in fh:
             line = line.strip()
             if not line or line.startswith("#"):
@@ -39,13 +39,17 @@ def _parse_golden():
     return rows, ncs
 
 
-def test_golden_hand_example():
-    """Scores, sort, merges and contraction of a 4-node example worked by hand."""
-    rows, ncs = _parse_golden()
+@pytest.mark.parametrize("name", ["hand_example.txt", "hand_cycle5_ties.txt"])
+def test_golden_hand_example(name):
+    """Scores, sort, merges and contraction of small examples worked by hand: a 4-node graph
+    with distinct scores, and a 5-cycle whose equal scores leave every merge to the edge id."""
+    rows, ncs = _parse_golden(name)
     trip = [t.split() for t in rows["edges"].split("|")]
     eu = np.array([int(t[0]) for t in trip]); ev = np.array([int(t[1]) for t in trip])
     w = np.array([int(t[2]) for t in trip], dtype=np.int32)
-    g = I.csr_from_edges(4, eu, ev, w)
+    n = int(max(eu.max(), ev.max())) + 1
+    g = I.csr_from_edges(n, eu, ev, w)
+    assert list(g.eu) == list(eu) and list(g.ev) == list(ev)   # listed in edge-id order
     assert list(O.degree(g)) == [int(x) for x in rows["degree"].split()]
     f = O.score(g)
     exact = [Fraction(s) for s in rows["score_num_den"].split()]
