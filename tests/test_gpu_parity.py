@@ -12,6 +12,8 @@ torch = pytest.importorskip("torch")
 from oracle import oracle as O
 from paper_2204_11757_gb300 import inputs as I
 
+import golden_io
+
 pytestmark = pytest.mark.gpu
 
 
@@ -190,6 +192,31 @@ def test_contract_small(ctx, gi):
         ref = O.coarsen_level(g, n_c)
         lv = ctx.contract(api.CSR.from_graph(g), torch.from_numpy(ref.lift).cuda(), ref.n_c)
         _check_level(lv, ref)
+
+
+@pytest.mark.parametrize("name", golden_io.FILES)
+def test_hand_examples_through_single_steps(ctx, name):
+    """The hand-worked examples (tests/golden) through the ABI's single steps, against the values
+    worked on paper rather than the oracle: score bits, each target's lift and contraction."""
+    rows, ncs = golden_io.parse(name)
+    n, eu, ev, w = golden_io.edges(rows)
+    api = _api()
+    csr = api.CSR.from_graph(I.csr_from_edges(n, eu, ev, w))
+    f = ctx.score(csr)
+    assert [int(x) for x in _bits(f.cpu().numpy())] == golden_io.ints(rows, "score_f64_bits")
+    for nc, (lift, emap, sm, rp, cc, wc) in ncs.items():
+        if nc >= n:
+            continue
+        got, _, nca, _ = ctx.select_merges(csr, f, nc)
+        assert nca == nc
+        assert got.cpu().numpy().tolist() == lift, nc
+        lv = ctx.contract(csr, got, nc)
+        assert lv.n_c == nc
+        assert lv.emap.cpu().numpy().tolist() == emap, nc
+        assert lv.self_mass.cpu().numpy().tolist() == sm, nc
+        assert lv.rowptr_c.cpu().numpy().tolist() == rp, nc
+        assert lv.col_c.cpu().numpy().tolist() == cc, nc
+        assert lv.w_c.cpu().numpy().tolist() == wc, nc
 
 
 def test_contract_int_overflow_reported(ctx):

@@ -4,7 +4,6 @@ Each test names what it pins.  The oracle is test infrastructure; these tests ar
 trustworthy before any GPU result is compared with it.
 """
 import itertools
-import os
 from fractions import Fraction
 
 import numpy as np
@@ -15,53 +14,30 @@ from scipy.sparse.csgraph import connected_components, minimum_spanning_tree
 from oracle import oracle as O
 from paper_2204_11757_gb300 import inputs as I
 
-GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+import golden_io
+
 
 
 # ---- hand-worked examples (tests/golden/hand_*.txt) -----------------------------------------
 
-def _parse_golden(name):
-    rows = {}
-    ncs = {}
-    with open(os.path.join(GOLDEN, name)) as fh:
-        for line in fh:
-            line = line.strip()
-            if not line or line.startswith("#"):
-                continue
-            if line.startswith("nc "):
-                head, rest = line.split(":", 1)
-                nc = int(head.split()[1])
-                parts = [p.split() for p in rest.split("|")]
-                ncs[nc] = parts
-            else:
-                key, rest = line.split(" ", 1)
-                rows[key] = rest
-    return rows, ncs
-
-
-@pytest.mark.parametrize("name", ["hand_example.txt", "hand_cycle5_ties.txt"])
+@pytest.mark.parametrize("name", golden_io.FILES)
 def test_golden_hand_example(name):
     """Scores, sort, merges and contraction of small examples worked by hand: a 4-node graph
     with distinct scores, and a 5-cycle whose equal scores leave every merge to the edge id."""
-    rows, ncs = _parse_golden(name)
-    trip = [t.split() for t in rows["edges"].split("|")]
-    eu = np.array([int(t[0]) for t in trip]); ev = np.array([int(t[1]) for t in trip])
-    w = np.array([int(t[2]) for t in trip], dtype=np.int32)
-    n = int(max(eu.max(), ev.max())) + 1
+    rows, ncs = golden_io.parse(name)
+    n, eu, ev, w = golden_io.edges(rows)
     g = I.csr_from_edges(n, eu, ev, w)
     assert list(g.eu) == list(eu) and list(g.ev) == list(ev)   # listed in edge-id order
-    assert list(O.degree(g)) == [int(x) for x in rows["degree"].split()]
+    assert list(O.degree(g)) == golden_io.ints(rows, "degree")
     f = O.score(g)
     exact = [Fraction(s) for s in rows["score_num_den"].split()]
-    bits = [int(b, 16) for b in rows["score_f64_bits"].split()]
-    assert [int(x) for x in f.view(np.uint64)] == bits
+    assert [int(x) for x in f.view(np.uint64)] == golden_io.ints(rows, "score_f64_bits")
     for fi, ex in zip(f, exact):
         assert abs(Fraction(float(fi)) - ex) <= Fraction(1, 2 ** 50)
     order = O.sort_fitness(f)
-    assert list(order) == [int(x) for x in rows["order"].split()]
-    for nc, parts in ncs.items():
+    assert list(order) == golden_io.ints(rows, "order")
+    for nc, (lift, emap, sm, rp, cc, wc) in ncs.items():
         lv = O.coarsen_level(g, nc)
-        lift, emap, sm, rp, cc, wc = ([int(x) for x in p] for p in parts)
         assert list(lv.lift) == lift, nc
         assert list(lv.coarse.emap) == emap, nc
         assert list(lv.coarse.self_mass) == sm, nc
