@@ -1,6 +1,6 @@
 """Spectral quality of a coarsening: the eigenvalue and eigenvector comparison of Section 3.2.
 
-The paper judges a coarsening by the smallest eigenvalues and the eigenvectors of the
+The paper assesses a coarsening by the smallest eigenvalues and the eigenvectors of the
 normalized Laplacian of G against those of the lift of G_c (Definition 2: a graph on the n
 original nodes whose weight between u and v is the total weight between their super-nodes
 divided by |u_c| |v_c|).  Theorem 1 bounds the eigenvalue change of one merge; Figure 2 shows
