@@ -17,6 +17,11 @@ graphs of a batch, and provides the dense spectral tools used to pin the oracle 
                        remark after Theorem 1);
 * ``greedy_literal``   Algorithm 1's merge loop written with explicit super-node sets, no
                        union-find, for brute-force cross-checks on tiny graphs.
+* ``with_self_mass``   the second reading of the multilevel driver: a coarse graph with its
+                       accumulated internal weight on the diagonal (the merged node
+                       (w_a + w_b) / (d_a + d_b) of the proof of Theorem 2), selected by
+                       ``coarsen(..., self_mass_degree=True)``; the GPU library implements the
+                       default reading only.
 """
 from __future__ import annotations
 
@@ -290,16 +295,62 @@ def level_targets(n: int, ratio: int, mode: str):
     return [max(1, n // (2 ** l)) for l in range(1, L + 1)]
 
 
-def coarsen(g, ratio: int, mode: str):
-    """The multilevel driver: repeat one level on the previous coarse graph (without its
-    self-mass) with the targets of ``level_targets``; returns (levels, composed lift)."""
+def with_self_mass(g, mass: np.ndarray):
+    """The graph g with twice each node's accumulated internal weight on its diagonal: entry
+    (x, x) = 2 mass[x], stored in its ascending-column place, for every x with mass[x] != 0.
+    The undirected edge list (eu, ev, w_und) and so the edge ids are unchanged.
+
+    This is the merged node of the proof of Theorem 2: merging a and b gives the normalized
+    adjacency vector (w_a + w_b) / (d_a + d_b), whose own coordinate holds w_ab + w_ba and whose
+    degree keeps the internal weight.  Degrees (ascending columns) and scores (the sorted union
+    of the two rows, which then contains the diagonal entries) follow with no other change."""
+    mass = np.asarray(mass)
+    diag = 2 * mass.astype(acc_dtype(g.w))
+    if g.w.dtype == np.int32:
+        if diag.size and int(diag.max()) > np.iinfo(np.int32).max:
+            raise OverflowError("2 x self-mass does not fit the int32 weights")
+    nodes = np.nonzero(diag)[0]
+    rows = np.repeat(np.arange(g.n, dtype=np.int64), np.diff(g.rowptr))
+    r = np.concatenate([rows, nodes.astype(np.int64)])
+    c = np.concatenate([g.col.astype(np.int64), nodes.astype(np.int64)])
+    w = np.concatenate([g.w, diag[nodes].astype(g.w.dtype)])
+    o = np.lexsort((c, r))
+    rowptr = np.zeros(g.n + 1, dtype=np.int64)
+    np.cumsum(np.bincount(r, minlength=g.n), out=rowptr[1:])
+    return _GraphLike(n=g.n, rowptr=rowptr, col=np.ascontiguousarray(c[o].astype(np.int32)),
+                      w=np.ascontiguousarray(w[o]), eu=g.eu, ev=g.ev, w_und=g.w_und)
+
+
+def carry_self_mass(mass: np.ndarray, lift: np.ndarray, n_c: int,
+                    new_mass: np.ndarray) -> np.ndarray:
+    """Accumulated internal weight of each super-node of the next level: its members' masses in
+    ascending member id, then the weight of this level's edges inside it (the contraction's
+    self-mass), summed left to right from 0."""
+    out = np.zeros(n_c, dtype=new_mass.dtype)
+    np.add.at(out, lift, mass.astype(new_mass.dtype))   # unbuffered, in ascending x
+    out += new_mass
+    return out
+
+
+def coarsen(g, ratio: int, mode: str, self_mass_degree: bool = False):
+    """The multilevel driver: repeat one level on the previous coarse graph with the targets of
+    ``level_targets``; returns (levels, composed lift).
+
+    By default each level scores the coarse graph without its self-mass (the reading the GPU
+    library implements).  With ``self_mass_degree`` each level scores the coarse graph with
+    its accumulated internal weight on the diagonal (``with_self_mass``): the merged node of
+    the proof of Theorem 2.  The first level is the same either way."""
     levels = []
     cur = g
     total = np.arange(g.n, dtype=np.int32)
+    mass = np.zeros(g.n, dtype=acc_dtype(g.w))
     for t in level_targets(g.n, ratio, mode):
-        lv = coarsen_level(cur, t)
+        lv = coarsen_level(with_self_mass(cur, mass) if self_mass_degree else cur, t)
         levels.append(lv)
         total = lv.lift[total]
+        if self_mass_degree:
+            mass = carry_self_mass(mass, lv.lift, lv.n_c, lv.coarse.self_mass)
+            lv.mass = mass
         cur = lv.coarse.graph
     return levels, total
 

@@ -575,3 +575,120 @@ def test_pool_features_three_tree_levels():
     xc = O.pool_features(lift, 2, x)
     assert xc[1, 0] == float(Fraction(10 ** 16 + 2, L))
     assert xc[0, 0] == 0.0
+
+
+# ---- the self-mass reading of the multilevel driver (the merged node of Theorem 2's proof) ----
+
+def _dense_rows(g):
+    """Dense weight matrix of a CSR that may hold diagonal entries."""
+    M = np.zeros((g.n, g.n))
+    rows = np.repeat(np.arange(g.n), np.diff(g.rowptr))
+    M[rows, g.col] = g.w
+    return M
+
+
+def test_self_mass_scores_are_the_merged_node_definition():
+    """With the self-mass on the diagonal, the next level's score of super-nodes (U, X) equals,
+    in exact rationals, || sum_{x in U} w_x / sum_{x in U} d_x - (the same for X) ||_1 with the
+    fine rows aggregated into super-node coordinates: the merged node (w_a + w_b) / (d_a + d_b)
+    of the proof of Theorem 2, repeated.  Without it (the default), some scores differ."""
+    differs = 0
+    for seed in range(12):
+        g = I.random_graph(10, 0.45, 1200 + seed, weight="int", dtype=np.int32, connected=True)
+        lv = O.coarsen_level(g, 5)
+        co = lv.coarse
+        g2 = O.with_self_mass(co.graph, co.self_mass)
+        f2 = O.score(g2)
+        f_r7 = O.score(co.graph)
+        W = O.dense_weights(g).astype(np.int64)
+        d = W.sum(axis=1)
+        agg = np.zeros((lv.n_c, lv.n_c), dtype=np.int64)      # C^T W C, diagonal included
+        for x in range(g.n):
+            for y in range(g.n):
+                agg[lv.lift[x], lv.lift[y]] += W[x, y]
+        D = np.zeros(lv.n_c, dtype=np.int64)
+        for x in range(g.n):
+            D[lv.lift[x]] += d[x]
+        for e in range(co.graph.m):
+            U, X = int(co.graph.eu[e]), int(co.graph.ev[e])
+            exact = sum(abs(Fraction(int(agg[U, y]), int(D[U])) - Fraction(int(agg[X, y]), int(D[X])))
+                        for y in range(lv.n_c))
+            assert abs(Fraction(float(f2[e])) - exact) <= Fraction(1, 2 ** 48)
+            differs += f_r7[e] != f2[e]
+    assert differs > 0
+
+
+def test_theorem2_proof_inequality_needs_the_self_mass():
+    """The proof of Theorem 2 bounds the merged node's distance from a member:
+    || w_a/d_a - (w_a + w_b)/(d_a + d_b) ||_1 <= f(a, b) / (d_a/d_b + 1).  Merging one edge and
+    reading the merged row from the next level's graph (in super-node coordinates, where the
+    distance can only shrink) satisfies it for every edge with the self-mass on the diagonal;
+    the graph without self-mass breaks it."""
+    broken = 0
+    checked = 0
+    for seed in range(25):
+        g = I.random_graph(9, 0.5, 1300 + seed, weight="float", dtype=np.float64,
+                           connected=True)
+        W = O.dense_weights(g)
+        d = W.sum(axis=1)
+        f = O.score(g)
+        for e in range(g.m):
+            a, b = int(g.eu[e]), int(g.ev[e])
+            rep = np.arange(g.n, dtype=np.int32)
+            rep[b] = a
+            lift, nc = O.relabel(rep)
+            co = O.contract(g, lift, nc)
+            C = O.membership(lift, nc)
+            member = (W[a] @ C) / d[a]                 # w_a / d_a in super-node coordinates
+            U = int(lift[a])
+            bound = float(f[e]) / (d[a] / d[b] + 1.0)
+            for gg, with_mass in ((O.with_self_mass(co.graph, co.self_mass), True),
+                                  (co.graph, False)):
+                M = _dense_rows(gg)
+                merged = M[U] / O.degree(gg)[U]
+                dist = float(np.abs(member - merged).sum())
+                if with_mass:
+                    assert dist <= bound + 1e-12, (seed, e)
+                else:
+                    broken += dist > bound + 1e-12
+            checked += 1
+    assert checked > 300 and broken > 0
+
+
+def test_self_mass_accumulates_internal_weight():
+    """For integer weights the carried mass of every super-node is exactly the total weight of
+    the original edges inside it, at every level; the first level does not depend on the
+    reading."""
+    g = I.random_graph(200, 0.04, 7, weight="int", dtype=np.int32, connected=True)
+    ref, _ = O.coarsen(g, 8, "halving")
+    levels, total = O.coarsen(g, 8, "halving", self_mass_degree=True)
+    assert np.array_equal(levels[0].lift, ref[0].lift)
+    comp = np.arange(g.n)
+    for lv in levels:
+        comp = lv.lift[comp]
+        inside = comp[g.eu] == comp[g.ev]
+        want = np.bincount(comp[g.eu][inside], weights=g.w_und[inside].astype(np.float64),
+                           minlength=lv.n_c).astype(np.int64)
+        assert np.array_equal(lv.mass, want)
+    assert np.array_equal(comp, total)
+
+
+def test_self_mass_reading_keeps_the_mesh_spectrum():
+    """A 128 x 128 mesh halved four times (n/16): without the self-mass one super-node takes
+    most of the graph and the lift loses the low spectrum; with it the super-nodes stay small
+    and the first 20 eigenvectors stay aligned (the Figure 2 comparison)."""
+    torch = pytest.importorskip("torch")
+    from paper_2204_11757_gb300 import spectral as S
+    g = I.tri_mesh_2d(128, 128, 7, jitter=0.3, weight="inv_len", dtype=np.float64)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a))
+    out = {}
+    for sm in (False, True):
+        levels, lift = O.coarsen(g, 16, "halving", self_mass_degree=sm)
+        n_c = levels[-1].n_c
+        rep = S.spectral_alignment_sparse(g.n, t(g.rowptr), t(g.col), t(g.w), t(lift), n_c,
+                                          k=20)
+        out[sm] = (np.bincount(lift).max() / g.n, float(rep.alignment.mean()),
+                   rep.max_eig_diff)
+    assert out[False][0] > 0.5 and out[False][1] < 0.5
+    assert out[True][0] < 0.05 and out[True][1] > 0.85
+    assert out[True][2] < out[False][2] / 5
