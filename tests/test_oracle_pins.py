@@ -692,3 +692,30 @@ def test_self_mass_reading_keeps_the_mesh_spectrum():
     assert out[False][0] > 0.5 and out[False][1] < 0.5
     assert out[True][0] < 0.05 and out[True][1] > 0.85
     assert out[True][2] < out[False][2] / 5
+
+
+def test_with_self_mass_edge_cases():
+    """Zero mass leaves the CSR as it was; a diagonal that does not fit int32 weights is an
+    error; diagonal entries sit in ascending-column order and leave the edge ids alone."""
+    g = I.random_graph(30, 0.2, 5, weight="int", dtype=np.int32, connected=True)
+    z = O.with_self_mass(g, np.zeros(g.n, dtype=np.int64))
+    assert np.array_equal(z.rowptr, g.rowptr) and np.array_equal(z.col, g.col)
+    assert np.array_equal(z.w, g.w)
+    mass = np.zeros(g.n, dtype=np.int64)
+    mass[[0, 7, g.n - 1]] = [3, 1, 5]
+    h = O.with_self_mass(g, mass)
+    assert h.rowptr[-1] == g.rowptr[-1] + 3
+    for x in range(g.n):
+        row = h.col[h.rowptr[x]:h.rowptr[x + 1]]
+        assert np.all(np.diff(row) > 0)
+        if mass[x]:
+            assert h.w[h.rowptr[x] + np.searchsorted(row, x)] == 2 * mass[x]
+    # a diagonal entry lies in its own row only: edges away from the massed nodes keep their bits
+    f, fh = O.score(g), O.score(h)
+    away = (mass[g.eu] == 0) & (mass[g.ev] == 0)
+    assert np.array_equal(f[away].view(np.uint64), fh[away].view(np.uint64))
+    assert np.all(f[~away] != fh[~away])
+    big = np.zeros(g.n, dtype=np.int64)
+    big[3] = 2 ** 30
+    with pytest.raises(OverflowError):
+        O.with_self_mass(g, big)
