@@ -355,9 +355,10 @@ def coarsen(g, ratio: int, mode: str, self_mass_degree: bool = False):
     return levels, total
 
 
-def coarsen_batch(batch, ratio: int, mode: str):
+def coarsen_batch(batch, ratio: int, mode: str, self_mass_degree: bool = False):
     """Each graph of the batch coarsened on its own (its targets from its own size), results
-    concatenated with global ids.  Returns per-graph level lists and the global outputs."""
+    concatenated with global ids.  Returns per-graph level lists and the global outputs.
+    ``self_mass_degree`` selects the multilevel reading as in ``coarsen``."""
     g = batch.graph
     gp = batch.graph_ptr
     eptr = np.searchsorted(g.eu, gp).astype(np.int64)
@@ -370,7 +371,7 @@ def coarsen_batch(batch, ratio: int, mode: str):
                          col=np.ascontiguousarray(g.col[p0:p1] - n0), w=g.w[p0:p1],
                          eu=np.ascontiguousarray(g.eu[e0:e1] - n0),
                          ev=np.ascontiguousarray(g.ev[e0:e1] - n0), w_und=g.w_und[e0:e1])
-        per_graph.append(coarsen(sub, ratio, mode))
+        per_graph.append(coarsen(sub, ratio, mode, self_mass_degree))
     return per_graph
 
 

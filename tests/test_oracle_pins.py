@@ -719,3 +719,16 @@ def test_with_self_mass_edge_cases():
     big[3] = 2 ** 30
     with pytest.raises(OverflowError):
         O.with_self_mass(g, big)
+
+
+def test_batch_oracle_self_mass_reading_is_per_graph():
+    """The batch oracle takes the self-mass reading graph by graph: each graph reaches its own
+    target and carries a non-negative finite mass."""
+    batch = I.mesh_batch(4, 3, nmin=200, nmax=600, dtype=np.float64)
+    per = O.coarsen_batch(batch, 8, "halving", self_mass_degree=True)
+    gp = batch.graph_ptr
+    for b, (levels, total) in enumerate(per):
+        n0, n1 = int(gp[b]), int(gp[b + 1])
+        assert total.shape[0] == n1 - n0
+        assert levels[-1].n_c == max(1, (n1 - n0) // 8)
+        assert np.all(np.isfinite(levels[-1].mass)) and levels[-1].mass.min() >= 0
