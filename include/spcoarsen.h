@@ -64,7 +64,9 @@ typedef enum {
     SPC_ERR_TIMEOUT = -7,            /* a bounded device-side wait gave up                     */
     SPC_ERR_OVERFLOW = -8,           /* an SPC_I32 coarse weight does not fit in int32         */
     SPC_ERR_BAD_WEIGHT = -9,         /* a weight <= 0, NaN or infinite                         */
-    SPC_ERR_TOO_LARGE = -10          /* m >= 2^31 or n >= 2^31                                 */
+    SPC_ERR_TOO_LARGE = -10          /* an input exceeds a fixed size limit of the entry point:
+                                        m >= 2^31 or n >= 2^31 everywhere, and the smaller
+                                        limit stated at an entry point's declaration          */
 } spc_status;
 
 typedef enum { SPC_I32 = 0, SPC_F32 = 1, SPC_F64 = 2 } spc_dtype;
@@ -98,6 +100,18 @@ typedef struct {
                            with the same shapes; 0: launch kernel by kernel                   */
     int32_t schedule;   /* score-kernel schedule: 0 auto (autotuned), 1 edge tiles
                            (one thread per edge), 2 warp per row                              */
+    int32_t self_mass;  /* multilevel reading (levels > 1 only; the first level is the same
+                           either way).  1 (default): a super-node keeps the weight inside it.
+                           Each level after the first scores its input graph with the diagonal
+                           entry (U, U) = 2 mass(U) of every super-node U with internal weight,
+                           stored in its ascending-column place, so it counts in U's degree and
+                           in the scores of U's edges.  mass(U) is U's accumulated internal
+                           weight: the masses of its members (ascending member id, summed left
+                           to right from 0) plus this level's self-mass of U.  This is the merged
+                           node (w_a + w_b) / (d_a + d_b) of the proof of Theorem 2, which keeps
+                           w_ab + w_ba in its own coordinate and the internal weight in its
+                           degree.  0: each level scores the coarse graph G_c as it is, without
+                           the internal weight.                                             */
 } spc_options;
 
 /* Per-level results retained by the context after spc_coarsen / spc_coarsen_batched /
@@ -126,6 +140,10 @@ typedef struct {
     const int32_t* seg;     /* [m_c+1] perm[seg[k] .. seg[k+1]) are coarse edge k's edges   */
     const int64_t* graph_ptr_c; /* [B+1] super-node offsets per graph (batched calls), else NULL */
     float ms;               /* device time of the level in milliseconds (CUDA events), or -1 */
+    const void* mass;       /* [n_c] accumulated internal weight of every super-node: the
+                               weight of the caller's edges inside it, as the self-mass reading
+                               carries it (int64 for SPC_I32); NULL when the call did not use
+                               that reading                                               */
 } spc_level;
 
 typedef struct spc_context spc_context;
@@ -146,7 +164,7 @@ SPC_API spc_status spc_context_set_stream(spc_context* ctx, void* stream);
 /* Human-readable name of a status code (static storage). */
 SPC_API const char* spc_status_string(spc_status status);
 
-/* Default options: levels 1, validate 1, use_graph 1, schedule 0. */
+/* Default options: levels 1, validate 1, use_graph 1, schedule 0, self_mass 1. */
 SPC_API spc_options spc_default_options(void);
 
 /* ---- the full method ---------------------------------------------------------------------- */
@@ -156,7 +174,9 @@ SPC_API spc_options spc_default_options(void);
  *                   member node id (device or host pointer, caller-allocated)
  *   n_c_actual      number of super-nodes at the last level (host pointer, may be NULL)
  * Per-level results (scores, maps, coarse graphs) are retained; see spc_get_level.  The last
- * level's coarse graph is the coarsened graph G_c.  n_c >= n returns the identity.
+ * level's coarse graph is the coarsened graph G_c (without diagonal entries: the weight inside
+ * each super-node is its self-mass, and with options->self_mass its accumulated mass).
+ * n_c >= n returns the identity.
  * Returns SPC_WARN_TARGET_NOT_REACHED if some level had more connected components than its
  * target. */
 SPC_API spc_status spc_coarsen(spc_context* ctx, const spc_csr* g, int64_t n_c, const spc_options* options,

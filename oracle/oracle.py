@@ -17,11 +17,11 @@ graphs of a batch, and provides the dense spectral tools used to pin the oracle 
                        remark after Theorem 1);
 * ``greedy_literal``   Algorithm 1's merge loop written with explicit super-node sets, no
                        union-find, for brute-force cross-checks on tiny graphs.
-* ``with_self_mass``   the second reading of the multilevel driver: a coarse graph with its
+* ``with_self_mass``   the multilevel driver's reading of a coarse graph: the graph with its
                        accumulated internal weight on the diagonal (the merged node
-                       (w_a + w_b) / (d_a + d_b) of the proof of Theorem 2), selected by
-                       ``coarsen(..., self_mass_degree=True)``; the GPU library implements the
-                       default reading only.
+                       (w_a + w_b) / (d_a + d_b) of the proof of Theorem 2), used by
+                       ``coarsen`` unless ``self_mass_degree=False`` asks for the coarse graph
+                       without it.
 """
 from __future__ import annotations
 
@@ -332,14 +332,16 @@ def carry_self_mass(mass: np.ndarray, lift: np.ndarray, n_c: int,
     return out
 
 
-def coarsen(g, ratio: int, mode: str, self_mass_degree: bool = False):
+def coarsen(g, ratio: int, mode: str, self_mass_degree: bool = True):
     """The multilevel driver: repeat one level on the previous coarse graph with the targets of
     ``level_targets``; returns (levels, composed lift).
 
-    By default each level scores the coarse graph without its self-mass (the reading the GPU
-    library implements).  With ``self_mass_degree`` each level scores the coarse graph with
-    its accumulated internal weight on the diagonal (``with_self_mass``): the merged node of
-    the proof of Theorem 2.  The first level is the same either way."""
+    With ``self_mass_degree`` (the default) each level scores the coarse graph with its
+    accumulated internal weight on the diagonal (``with_self_mass``): the merged node of the
+    proof of Theorem 2, which keeps w_ab + w_ba in its own coordinate and the internal weight in
+    its degree.  Each level then records ``mass``, the accumulated internal weight of its
+    super-nodes.  With ``self_mass_degree=False`` each level scores the coarse graph without
+    it.  The first level is the same either way."""
     levels = []
     cur = g
     total = np.arange(g.n, dtype=np.int32)
@@ -355,7 +357,7 @@ def coarsen(g, ratio: int, mode: str, self_mass_degree: bool = False):
     return levels, total
 
 
-def coarsen_batch(batch, ratio: int, mode: str, self_mass_degree: bool = False):
+def coarsen_batch(batch, ratio: int, mode: str, self_mass_degree: bool = True):
     """Each graph of the batch coarsened on its own (its targets from its own size), results
     concatenated with global ids.  Returns per-graph level lists and the global outputs.
     ``self_mass_degree`` selects the multilevel reading as in ``coarsen``."""

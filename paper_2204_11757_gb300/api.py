@@ -70,6 +70,8 @@ class Level:
     perm: torch.Tensor
     seg: torch.Tensor
     graph_ptr_c: Optional[torch.Tensor] = None
+    # accumulated internal weight of every super-node (the self-mass reading), else None
+    mass: Optional[torch.Tensor] = None
 
     def coarse_csr(self) -> CSR:
         return CSR(self.rowptr_c, self.col_c, self.w_c)
@@ -196,12 +198,16 @@ class Context:
     # ---- the method ----------------------------------------------------------------------
     def coarsen(self, g: CSR, n_c: int, levels: int = 1, validate: bool = True,
                 schedule: int = 0, lift_out: Optional[torch.Tensor] = None,
-                use_graph: bool = True):
+                use_graph: bool = True, self_mass: bool = True):
         """Coarsen to n_c super-nodes in `levels` levels; returns (lift, n_c_actual, status).
         With use_graph, a call that repeats the previous one on unchanged input replays the
-        recorded schedule as one CUDA graph."""
+        recorded schedule as one CUDA graph.  self_mass selects the multilevel reading: every
+        level after the first scores its input with each super-node's accumulated internal
+        weight on the diagonal (the merged node of the proof of Theorem 2); False scores the
+        coarse graph without it."""
         c = self._csr(g)
-        opts = N.spc_options(int(levels), int(bool(validate)), int(bool(use_graph)), int(schedule))
+        opts = N.spc_options(int(levels), int(bool(validate)), int(bool(use_graph)), int(schedule),
+                             int(bool(self_mass)))
         lift = lift_out if lift_out is not None else torch.empty(g.n, dtype=torch.int32,
                                                                  device=g.col.device)
         nca = ctypes.c_int64(0)
@@ -211,11 +217,14 @@ class Context:
         return lift, int(nca.value), st
 
     def coarsen_batched(self, g: CSR, graph_ptr: torch.Tensor, ratio: int, levels: int,
-                        validate: bool = True, schedule: int = 0, use_graph: bool = True):
-        """Coarsen every graph of a block-diagonal batch to floor(n_b / ratio) super-nodes."""
+                        validate: bool = True, schedule: int = 0, use_graph: bool = True,
+                        self_mass: bool = True):
+        """Coarsen every graph of a block-diagonal batch to floor(n_b / ratio) super-nodes
+        (self_mass as in coarsen)."""
         c = self._csr(g)
         B = int(graph_ptr.shape[0] - 1)
-        opts = N.spc_options(int(levels), int(bool(validate)), int(bool(use_graph)), int(schedule))
+        opts = N.spc_options(int(levels), int(bool(validate)), int(bool(use_graph)), int(schedule),
+                             int(bool(self_mass)))
         lift = torch.empty(g.n, dtype=torch.int32, device=g.col.device)
         gpc = torch.empty(B + 1, dtype=torch.int64, device=g.col.device)
         st = N.check(self.lib.spc_coarsen_batched(self._handle, ctypes.byref(c), _ptr(graph_ptr),
@@ -246,7 +255,8 @@ class Context:
             col_c=cp(i.col_c, 2 * i.m_c, torch.int32), w_c=cp(i.w_c, 2 * i.m_c, wt),
             perm=cp(i.perm, i.m_inter, torch.int32), seg=cp(i.seg, i.m_c + 1, torch.int32),
             graph_ptr_c=(cp(i.graph_ptr_c, batched_B + 1, torch.int64)
-                         if batched_B is not None else None))
+                         if batched_B is not None else None),
+            mass=cp(i.mass, i.n_c, acc) if i.mass else None)
 
     def levels(self, batched_B: Optional[int] = None) -> List[Level]:
         return [self.level(l, batched_B) for l in range(self.level_count())]

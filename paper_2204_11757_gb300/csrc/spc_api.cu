@@ -355,7 +355,9 @@ static spc_status reserve_work(spc_context* ctx, int64_t n, int64_t m, int64_t B
     SPC_TRY(ensure(ctx, W.ev, M * 4));
     SPC_TRY(ensure(ctx, W.w_und, M * 8));
     SPC_TRY(ensure(ctx, W.deg, N * 8));
-    SPC_TRY(ensure(ctx, W.p, 2 * M * 8));
+    // stored entries of a level's input: 2m, plus one diagonal entry per node under the
+    // self-mass reading
+    SPC_TRY(ensure(ctx, W.p, (2 * M + N) * 8));
     SPC_TRY(ensure(ctx, W.long_rows, N * 4));
     SPC_TRY(ensure(ctx, W.lr_base, N * 8));
     SPC_TRY(ensure(ctx, W.lr_len, N * 8));
@@ -417,8 +419,26 @@ static spc_status reserve_work(spc_context* ctx, int64_t n, int64_t m, int64_t B
     const size_t big = (N > M ? N : M) + 256 * ((M + 4095) / 4096) + 4096;
     // the scans keep their statuses zero between calls; a new block starts zeroed
     SPC_TRY(ensure_zeroed(ctx, W.scan_tmp, (big / 4096 + 4) * 8 + 256));
-    // one-sweep sort: 8 passes x (tiles x 256) look-back words + histograms
-    SPC_TRY(ensure(ctx, W.sort_hist, (8 * 256 * ((M + 4095) / 4096) + 8 * 512 + 64) * 4));
+    // one-sweep sort: 8 passes x (tiles x 256) look-back words + histograms (sorts of up to
+    // max(n, m) items: the super-node members of the self-mass reading sort n)
+    const size_t NM = N > M ? N : M;
+    SPC_TRY(ensure(ctx, W.sort_hist, (8 * 256 * ((NM + 4095) / 4096) + 8 * 512 + 64) * 4));
+    return SPC_OK;
+}
+
+// the self-mass reading: member sorts, and the next level's input with its diagonal entries
+static spc_status reserve_self_mass(spc_context* ctx, int64_t n, int64_t m, spc_dtype wt) {
+    Work& W = ctx->work;
+    const size_t N = (size_t)n + 1, M = (size_t)m + 1;
+    SPC_TRY(ensure(ctx, W.ms_key, N * 4));
+    SPC_TRY(ensure(ctx, W.ms_val, N * 4));
+    SPC_TRY(ensure(ctx, W.ms_key2, N * 4));
+    SPC_TRY(ensure(ctx, W.ms_val2, N * 4));
+    SPC_TRY(ensure(ctx, W.ms_start, (N + 1) * 4));
+    SPC_TRY(ensure(ctx, W.dg_rowptr, (N + 1) * 8));
+    SPC_TRY(ensure(ctx, W.dg_pos, (N + 1) * 4));
+    SPC_TRY(ensure(ctx, W.dg_col, (2 * M + N + 1) * 4));
+    SPC_TRY(ensure(ctx, W.dg_w, (2 * M + N + 1) * wsize(wt)));
     return SPC_OK;
 }
 
@@ -436,6 +456,7 @@ static spc_status reserve_level(spc_context* ctx, LevelBufs& lv, int64_t n, int6
     SPC_TRY(ensure(ctx, lv.seg, (M + 1) * 4));
     SPC_TRY(ensure(ctx, lv.score, M * 8));
     SPC_TRY(ensure(ctx, lv.graph_ptr_c, ((size_t)B + 2) * 8));
+    SPC_TRY(ensure(ctx, lv.mass, N * 8));
     if (!lv.ev0) {
         SPC_CUDA(cudaEventCreate(&lv.ev0));
         SPC_CUDA(cudaEventCreate(&lv.ev1));
@@ -511,6 +532,7 @@ static spc_status copy_out(spc_context* ctx, void* dst, const void* src, size_t 
 struct Schedule {
     int32_t levels = 1;
     bool validate = true;
+    bool self_mass = true;   // the self-mass reading of the multilevel driver
     int schedule = 0;
     // single graph
     int64_t n_c = 1;
@@ -530,6 +552,7 @@ static spc_status run_levels(spc_context* ctx, const GraphView& g0, const Schedu
     // reserve everything up front (level sizes are bounded by level 0)
     SPC_TRY(reserve_work(ctx, g0.n, g0.nnz / 2, S.B));
     for (int l = 0; l < L; ++l) SPC_TRY(reserve_level(ctx, ctx->levels[l], g0.n, g0.nnz / 2, S.B));
+    if (S.self_mass && L > 1) SPC_TRY(reserve_self_mass(ctx, g0.n, g0.nnz / 2, g0.wtype));
     if (batched) {
         SPC_TRY(ensure(ctx, ctx->work.stage_gptr, ((size_t)S.B + 1) * 8 * (L + 1)));
         d_targets = ctx->work.stage_gptr.as<int64_t>();
@@ -537,6 +560,7 @@ static spc_status run_levels(spc_context* ctx, const GraphView& g0, const Schedu
     const int maxb = ctx->num_sms * 8;
     GraphView cur = g0;
     const int64_t* cur_gptr = S.d_graph_ptr;
+    const void* mass = nullptr;  // accumulated internal weight of cur's nodes (null: all zero)
     *warn = 0;
     ctx->n_levels = 0;
     for (int l = 0; l < L; ++l) {
@@ -565,7 +589,14 @@ static spc_status run_levels(spc_context* ctx, const GraphView& g0, const Schedu
         SPC_TRY(run_select(ctx, cur, lv.score.p, sa, lv.lift.as<int32_t>(), nullptr, &n_c,
                            lv.graph_ptr_c.as<int64_t>(), &st));
         SPC_TRY(run_contract(ctx, cur, lv.lift.as<int32_t>(), n_c, lv));
-        SPC_CUDA(record_event(ctx, lv.ev1));
+        lv.mass_ptr = nullptr;
+        if (S.self_mass) {
+            // mass(U) = members' masses + this level's self-mass (the merged node of the proof
+            // of Theorem 2 keeps the weight inside it)
+            SPC_TRY(run_carry_mass(ctx, cur.n, lv.lift.as<int32_t>(), n_c, mass, lv.self_mass.p,
+                                   cur.wtype, lv.mass, &lv.mass_ptr));
+            mass = lv.mass_ptr;
+        }
         lv.status = st;
         lv.wtype = cur.wtype;
         if (st == SPC_WARN_TARGET_NOT_REACHED) *warn = 1;
@@ -578,6 +609,13 @@ static spc_status run_levels(spc_context* ctx, const GraphView& g0, const Schedu
         nx.col = lv.col_c.as<int32_t>();
         nx.w = lv.w_c.p;
         nx.wtype = cur.wtype;
+        // the next level scores G_c with each super-node's internal weight on its diagonal
+        if (S.self_mass && l + 1 < L) {
+            GraphView dg;
+            SPC_TRY(run_diag_graph(ctx, nx, mass, dg));
+            nx = dg;
+        }
+        SPC_CUDA(record_event(ctx, lv.ev1));
         cur = nx;
         cur_gptr = lv.graph_ptr_c.as<int64_t>();
     }
@@ -679,7 +717,7 @@ static void drop_graph(Replay& R) {
 static std::vector<int64_t> call_key(const GraphView& v, const Schedule& S) {
     return {(int64_t)(intptr_t)v.rowptr, (int64_t)(intptr_t)v.col, (int64_t)(intptr_t)v.w, v.n,
             v.nnz, (int64_t)v.wtype, S.levels, S.validate ? 1 : 0, S.schedule, S.n_c, S.B,
-            (int64_t)(intptr_t)S.d_graph_ptr, S.ratio};
+            (int64_t)(intptr_t)S.d_graph_ptr, S.ratio, S.self_mass ? 1 : 0};
 }
 
 static spc_status capture_graph(spc_context* ctx, const GraphView& v, const Schedule& S,
@@ -778,6 +816,7 @@ static spc_status drive(spc_context* ctx, const GraphView& v, const Schedule& S,
                     lv.n = R.metas[l].n; lv.m = R.metas[l].m; lv.n_c = R.metas[l].n_c;
                     lv.m_c = R.metas[l].m_c; lv.m_inter = R.metas[l].m_inter;
                     lv.status = R.metas[l].status; lv.wtype = R.metas[l].wtype;
+                    lv.mass_ptr = R.metas[l].mass_ptr;
                     float ms = -1.f;
                     if (cudaEventElapsedTime(&ms, lv.ev0, lv.ev1) != cudaSuccess) {
                         (void)cudaGetLastError();
@@ -810,6 +849,7 @@ static spc_status drive(spc_context* ctx, const GraphView& v, const Schedule& S,
             LevelMeta mt;
             mt.n = lv.n; mt.m = lv.m; mt.n_c = lv.n_c; mt.m_c = lv.m_c; mt.m_inter = lv.m_inter;
             mt.status = lv.status; mt.wtype = lv.wtype;
+            mt.mass_ptr = lv.mass_ptr;
             R.metas.push_back(mt);
         }
         R.n_c_final = *ncf;
@@ -849,6 +889,7 @@ spc_options spc_default_options(void) {
     o.validate = 1;
     o.use_graph = 1;
     o.schedule = 0;
+    o.self_mass = 1;
     return o;
 }
 
@@ -1016,6 +1057,7 @@ spc_status spc_contract(spc_context* ctx, const spc_csr* g, const int32_t* lift,
     lv.status = SPC_OK;
     lv.wtype = v.wtype;
     lv.ms = -1.f;
+    lv.mass_ptr = nullptr;
     ctx->n_levels = 1;
     if (m_c_out) *m_c_out = lv.m_c;
     return sync_status(ctx);
@@ -1033,6 +1075,7 @@ spc_status spc_coarsen(spc_context* ctx, const spc_csr* g, int64_t n_c, const sp
     S.levels = o.levels < 1 ? 1 : o.levels;
     S.validate = o.validate != 0;
     S.schedule = o.schedule;
+    S.self_mass = o.self_mass != 0;
     S.n_c = n_c;
     int64_t ncf = 0;
     int32_t warn = 0;
@@ -1065,6 +1108,7 @@ spc_status spc_coarsen_batched(spc_context* ctx, const spc_csr* g, const int64_t
     S.levels = L;
     S.validate = o.validate != 0;
     S.schedule = o.schedule;
+    S.self_mass = o.self_mass != 0;
     S.B = B;
     S.d_graph_ptr = gp_dev;
     S.ratio = ratio;
@@ -1104,6 +1148,7 @@ spc_status spc_get_level(const spc_context* ctx, int32_t level, spc_level* out) 
     out->seg = lv.seg.as<int32_t>();
     out->graph_ptr_c = lv.graph_ptr_c.as<int64_t>();
     out->ms = lv.ms;
+    out->mass = lv.mass_ptr;
     return SPC_OK;
 }
 

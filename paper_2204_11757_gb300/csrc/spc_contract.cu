@@ -982,6 +982,254 @@ spc_status forward_typed(spc_context* ctx, const int32_t* perm, const int32_t* s
                                      w_und, a_und);
 }
 
+// ---- the self-mass reading of the multilevel driver ----------------------------------------
+// Under this reading a super-node keeps the weight inside it.  The proof of Theorem 2 treats the
+// merged node as (w_a + w_b) / (d_a + d_b): its own coordinate holds w_ab + w_ba and its degree
+// keeps the internal weight.  The next level's input graph therefore holds, for every
+// super-node U with mass(U) != 0, the diagonal entry 2 mass(U) in its ascending-column place,
+// where mass(U) is U's accumulated internal weight: the masses of its members (ascending member
+// id, summed left to right from 0) plus the weight of this level's edges inside U (the
+// contraction's self-mass).  Degrees and scores of that graph follow with no other change.
+
+// members of every super-node in ascending id: a stable sort of (lift[x], x) by lift
+__global__ void __launch_bounds__(kThreads)
+k_member_keys(int64_t n, const int32_t* __restrict__ lift, uint32_t* __restrict__ key,
+              uint32_t* __restrict__ val) {
+    spc::pdl_wait();
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n;
+         x += (int64_t)gridDim.x * blockDim.x) {
+        key[x] = (uint32_t)lift[x];
+        val[x] = (uint32_t)x;
+    }
+}
+
+// start[U] = first sorted position of U's members; start[n_c] = n.  Every super-node of a
+// relabelled lift has at least one member.
+__global__ void __launch_bounds__(kThreads)
+k_member_starts(int64_t n, int64_t n_c, const uint32_t* __restrict__ key,
+                int32_t* __restrict__ start) {
+    spc::pdl_wait();
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t U = key[i];
+        if (i == 0 || key[i - 1] != U) start[U] = (int32_t)i;
+        if (i == n - 1) start[n_c] = (int32_t)n;
+    }
+}
+
+// mass[U] = (sum of the members' masses) + self_mass[U], one IEEE addition
+template <class WT>
+__global__ void __launch_bounds__(kThreads)
+k_mass_add_self(int64_t n_c, const WT* __restrict__ self, WT* __restrict__ mass) {
+    spc::pdl_wait();
+    for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n_c;
+         u += (int64_t)gridDim.x * blockDim.x)
+        mass[u] = CT<WT>::add(mass[u], self[u]);
+}
+
+// integer weights (int64 masses): exact in any order, so the members' masses are added by
+// atomics onto the self-mass
+__global__ void __launch_bounds__(kThreads)
+k_mass_int_init(int64_t n_c, const long long* __restrict__ self, long long* __restrict__ mass) {
+    spc::pdl_wait();
+    for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n_c;
+         u += (int64_t)gridDim.x * blockDim.x)
+        mass[u] = self[u];
+}
+
+__global__ void __launch_bounds__(kThreads)
+k_mass_int_add(int64_t n, const int32_t* __restrict__ lift, const long long* __restrict__ prev,
+               long long* mass) {
+    spc::pdl_wait();
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n;
+         x += (int64_t)gridDim.x * blockDim.x) {
+        const long long v = prev[x];
+        if (v) atomicAdd(reinterpret_cast<unsigned long long*>(mass + lift[x]),
+                         (unsigned long long)v);
+    }
+}
+
+// diagonal flags scanned in one pass: pos[x] = #{y < x : mass[y] != 0} (pos[n] = the count),
+// and the new row pointers rowptr[x] + pos[x]
+template <class AT>
+struct DiagLd {
+    const AT* mass;
+    __device__ unsigned long long operator()(int64_t g) const {
+        return mass[g] != AT(0) ? 1ull : 0ull;
+    }
+};
+
+struct DiagSt {
+    const int64_t* rowptr;
+    int64_t* rowptr_d;
+    int32_t* pos;
+    int64_t n;
+    struct Local {};
+    __device__ Local begin() const { return Local{}; }
+    __device__ void operator()(Local&, int64_t g, bool valid, unsigned long long excl,
+                               unsigned long long) const {
+        if (!valid) return;
+        pos[g] = (int32_t)excl;
+        rowptr_d[g] = rowptr[g] + (int64_t)excl;
+    }
+    __device__ void finish(Local&) const {}
+    __device__ void total(unsigned long long tot) const {
+        pos[n] = (int32_t)tot;
+        rowptr_d[n] = rowptr[n] + (int64_t)tot;
+    }
+};
+
+// the last row x with rowptr[x] <= j among rows [lo, hi] (the row holding entry j)
+__device__ __forceinline__ int64_t row_of_entry(const int64_t* __restrict__ rowptr, int64_t lo,
+                                                int64_t hi, int64_t j) {
+    while (lo < hi) {
+        const int64_t mid = (lo + hi + 1) >> 1;
+        if (rowptr[mid] <= j) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// every stored entry moves up by the diagonal entries before it: those of the rows above its
+// row, and its own row's when the entry's column is above the diagonal.  Each block takes
+// kDiagTile consecutive entries and first narrows their rows with two searches.
+constexpr int64_t kDiagTile = 2048;
+
+template <class WT>
+__global__ void __launch_bounds__(kThreads)
+k_diag_entries(int64_t n, int64_t nnz, const int64_t* __restrict__ rowptr,
+               const int32_t* __restrict__ col, const WT* __restrict__ w,
+               const int32_t* __restrict__ pos, int32_t* __restrict__ col_d,
+               WT* __restrict__ w_d) {
+    spc::pdl_wait();
+    __shared__ int64_t s_rows[2];
+    for (int64_t base = (int64_t)blockIdx.x * kDiagTile; base < nnz;
+         base += (int64_t)gridDim.x * kDiagTile) {
+        const int64_t last = (base + kDiagTile < nnz ? base + kDiagTile : nnz) - 1;
+        if (threadIdx.x < 2)
+            s_rows[threadIdx.x] = row_of_entry(rowptr, 0, n - 1, threadIdx.x ? last : base);
+        __syncthreads();
+        const int64_t r_lo = s_rows[0], r_hi = s_rows[1];
+        for (int64_t j = base + threadIdx.x; j <= last; j += blockDim.x) {
+            const int64_t x = row_of_entry(rowptr, r_lo, r_hi, j);
+            const int32_t y = col[j];
+            const int32_t p0 = pos[x];
+            const int64_t d = (int64_t)p0 + ((pos[x + 1] > p0 && (int64_t)y > x) ? 1 : 0);
+            col_d[j + d] = y;
+            w_d[j + d] = w[j];
+        }
+        __syncthreads();
+    }
+}
+
+__device__ __forceinline__ int32_t diag_weight(long long m, uint32_t* status) {
+    const long long v = 2 * m;
+    if (v > 2147483647ll) atomicOr(status, DEV_OVERFLOW);
+    return (int32_t)v;
+}
+__device__ __forceinline__ float diag_weight(float m, uint32_t*) { return __fmul_rn(m, 2.0f); }
+__device__ __forceinline__ double diag_weight(double m, uint32_t*) { return __dmul_rn(m, 2.0); }
+
+// the diagonal entry of every row with mass: after the row's entries below the diagonal
+template <class WT, class AT>
+__global__ void __launch_bounds__(kThreads)
+k_diag_place(int64_t n, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+             const int32_t* __restrict__ pos, const AT* __restrict__ mass,
+             int32_t* __restrict__ col_d, WT* __restrict__ w_d, uint32_t* status) {
+    spc::pdl_wait();
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n;
+         x += (int64_t)gridDim.x * blockDim.x) {
+        if (pos[x + 1] == pos[x]) continue;
+        int64_t lo = rowptr[x], hi = rowptr[x + 1];
+        while (lo < hi) {
+            const int64_t mid = (lo + hi) >> 1;
+            if ((int64_t)col[mid] < x) lo = mid + 1; else hi = mid;
+        }
+        const int64_t at = lo + pos[x];
+        col_d[at] = (int32_t)x;
+        w_d[at] = (WT)diag_weight(mass[x], status);
+    }
+}
+
+template <class WT>
+spc_status carry_mass_typed(spc_context* ctx, int64_t n, const int32_t* lift, int64_t n_c,
+                            const void* prev_mass, const void* self_mass, Buf& mass_out) {
+    using Acc = typename CT<WT>::Acc;
+    Work& W = ctx->work;
+    const int maxb = ctx->num_sms * 8;
+    SPC_TRY(ensure(ctx, mass_out, (size_t)(n_c + 1) * sizeof(Acc)));
+    Acc* out = mass_out.as<Acc>();
+    const Acc* self = static_cast<const Acc*>(self_mass);
+    const Acc* prev = static_cast<const Acc*>(prev_mass);
+    if (n_c <= 0) return SPC_OK;
+    if constexpr (std::is_same<WT, int32_t>::value) {
+        SPC_LAUNCH(ctx, k_mass_int_init, grid_for(n_c, kThreads, maxb), kThreads, 0, n_c, self,
+                   out);
+        SPC_LAUNCH(ctx, k_mass_int_add, grid_for(n, kThreads, maxb), kThreads, 0, n, lift, prev,
+                   out);
+        return SPC_OK;
+    } else {
+        int nb = 1;
+        while ((1ll << nb) < n_c) ++nb;
+        uint32_t* key = W.ms_key.as<uint32_t>();
+        uint32_t* val = W.ms_val.as<uint32_t>();
+        int32_t* start = W.ms_start.as<int32_t>();
+        const int gn = grid_for(n, kThreads, maxb);
+        SPC_LAUNCH(ctx, k_member_keys, gn, kThreads, 0, n, lift, key, val);
+        SPC_TRY(radix_sort_u32(ctx, key, val, W.ms_key2.as<uint32_t>(), W.ms_val2.as<uint32_t>(),
+                               n, nb));
+        SPC_LAUNCH(ctx, k_member_starts, gn, kThreads, 0, n, n_c, key, start);
+        int32_t* long_list = W.long_segs.as<int32_t>();
+        int32_t* long_cnt = W.counters.as<int32_t>() + 9;
+        SPC_LAUNCH(ctx, k_set_i32, 1, 32, 0, long_cnt, 0);
+        SPC_LAUNCH(ctx, (k_segsum_short<WT, WT>), grid_for(n_c, kThreads, maxb), kThreads, 0,
+                   n_c, start, val, nullptr, prev, out, long_list, long_cnt, ctx->d_status);
+        SPC_TRY((long_segment_sums<WT, WT>(ctx, start, val, nullptr, prev, out)));
+        SPC_LAUNCH(ctx, k_mass_add_self<WT>, grid_for(n_c, kThreads, maxb), kThreads, 0, n_c,
+                   self, out);
+        return SPC_OK;
+    }
+}
+
+template <class WT>
+spc_status diag_graph_typed(spc_context* ctx, const GraphView& g, const void* mass_v,
+                            GraphView& out) {
+    using Acc = typename CT<WT>::Acc;
+    Work& W = ctx->work;
+    const int64_t n = g.n;
+    const int maxb = ctx->num_sms * 8;
+    out = g;
+    if (n <= 0) return SPC_OK;
+    const Acc* mass = static_cast<const Acc*>(mass_v);
+    SPC_TRY(ensure(ctx, W.dg_rowptr, (size_t)(n + 1) * 8));
+    SPC_TRY(ensure(ctx, W.dg_pos, (size_t)(n + 1) * 4));
+    SPC_TRY(ensure(ctx, W.dg_col, (size_t)(g.nnz + n + 1) * 4));
+    SPC_TRY(ensure(ctx, W.dg_w, (size_t)(g.nnz + n + 1) * sizeof(WT)));
+    int64_t* rowptr_d = W.dg_rowptr.as<int64_t>();
+    int32_t* pos = W.dg_pos.as<int32_t>();
+    int32_t* col_d = W.dg_col.as<int32_t>();
+    WT* w_d = W.dg_w.as<WT>();
+    SPC_TRY(scan_fused<unsigned long long>(ctx, n, DiagLd<Acc>{mass},
+                                           DiagSt{g.rowptr, rowptr_d, pos, n},
+                                           (double)n * (sizeof(Acc) + 8.0 + 8.0 + 4.0)));
+    int64_t nd = 0;
+    SPC_TRY(read_i32(ctx, pos + n, &nd));
+    if (g.nnz > 0) {
+        note_bytes(ctx, (double)g.nnz * 2.0 * (4.0 + sizeof(WT)) + (double)(n + 1) * 12.0);
+        SPC_LAUNCH(ctx, k_diag_entries<WT>, grid_for(g.nnz, (int)kDiagTile, maxb), kThreads, 0,
+                   n, g.nnz, g.rowptr, g.col, static_cast<const WT*>(g.w), pos, col_d, w_d);
+    }
+    if (nd > 0) {
+        SPC_LAUNCH(ctx, (k_diag_place<WT, Acc>), grid_for(n, kThreads, maxb), kThreads, 0, n,
+                   g.rowptr, g.col, pos, mass, col_d, w_d, ctx->d_status);
+    }
+    out.rowptr = rowptr_d;
+    out.col = col_d;
+    out.w = w_d;
+    out.nnz = g.nnz + nd;
+    out.ndiag = nd;
+    return SPC_OK;
+}
+
 }  // namespace
 
 spc_status run_contract(spc_context* ctx, const GraphView& g, const int32_t* lift, int64_t n_c,
@@ -1019,6 +1267,37 @@ spc_status run_contract_backward(spc_context* ctx, const int32_t* emap, int64_t 
         return SPC_ERR_INVALID_ARG;
     }
     return SPC_OK;
+}
+
+}  // namespace spc
+
+namespace spc {
+
+spc_status run_carry_mass(spc_context* ctx, int64_t n, const int32_t* lift, int64_t n_c,
+                          const void* prev_mass, const void* self_mass, spc_dtype wt,
+                          Buf& mass_out, const void** mass_ptr) {
+    if (!prev_mass) {  // nothing carried in: (0 + 0 + ...) + self = self, bit for bit
+        *mass_ptr = self_mass;
+        return SPC_OK;
+    }
+    spc_status st = SPC_ERR_INVALID_ARG;
+    switch (wt) {
+        case SPC_I32: st = carry_mass_typed<int32_t>(ctx, n, lift, n_c, prev_mass, self_mass, mass_out); break;
+        case SPC_F32: st = carry_mass_typed<float>(ctx, n, lift, n_c, prev_mass, self_mass, mass_out); break;
+        case SPC_F64: st = carry_mass_typed<double>(ctx, n, lift, n_c, prev_mass, self_mass, mass_out); break;
+    }
+    *mass_ptr = st == SPC_OK ? mass_out.p : nullptr;
+    return st;
+}
+
+spc_status run_diag_graph(spc_context* ctx, const GraphView& g, const void* mass,
+                          GraphView& out) {
+    switch (g.wtype) {
+        case SPC_I32: return diag_graph_typed<int32_t>(ctx, g, mass, out);
+        case SPC_F32: return diag_graph_typed<float>(ctx, g, mass, out);
+        case SPC_F64: return diag_graph_typed<double>(ctx, g, mass, out);
+    }
+    return SPC_ERR_INVALID_ARG;
 }
 
 }  // namespace spc

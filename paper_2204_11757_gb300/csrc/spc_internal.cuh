@@ -66,6 +66,10 @@ struct Buf {
 // Device buffers of one level (inputs of the next level live in `out_*`).
 struct LevelBufs {
     Buf lift, emap, self_mass, a_und, rowptr_c, col_c, w_c, perm, seg, score, graph_ptr_c;
+    // self-mass reading: accumulated internal weight of every super-node of this level
+    // (`mass_ptr` is self_mass itself on the first level, else `mass`; null when not carried)
+    Buf mass;
+    const void* mass_ptr = nullptr;
     int64_t n = 0, m = 0, n_c = 0, m_c = 0, m_inter = 0;
     int32_t status = 0;
     spc_dtype wtype = SPC_F64;
@@ -108,6 +112,10 @@ struct Work {
     Buf seg_base_side, seg_len_side, seg_idx_side, seg_terms_side;
     SeqTabBufs tab_s_side;
     Buf lift_final;                                             // composed lift of a call
+    // self-mass reading: super-node members sorted by (super-node, id), and the next level's
+    // input graph with the accumulated internal weight on its diagonal
+    Buf ms_key, ms_val, ms_key2, ms_val2, ms_start;
+    Buf dg_rowptr, dg_col, dg_w, dg_pos;
 };
 
 struct Timer {
@@ -140,6 +148,7 @@ struct LevelMeta {
     int64_t n = 0, m = 0, n_c = 0, m_c = 0, m_inter = 0;
     int32_t status = 0;
     spc_dtype wtype = SPC_F64;
+    const void* mass_ptr = nullptr;
 };
 
 struct Replay {
@@ -329,6 +338,9 @@ spc_status seqtab_full(spc_context* ctx, const void* terms, bool f32, int64_t ns
 
 struct GraphView {
     int64_t n = 0, nnz = 0, m = 0;
+    // diagonal entries (x, x) stored in their rows (the self-mass reading's coarse graphs; 0 for
+    // a caller's graph, whose self-loops are rejected): nnz = 2 m + ndiag
+    int64_t ndiag = 0;
     const int64_t* rowptr = nullptr;
     const int32_t* col = nullptr;
     const void* w = nullptr;
@@ -363,6 +375,18 @@ spc_status run_sort_fitness(spc_context* ctx, int64_t m, const void* f, bool f32
 
 spc_status run_contract_forward(spc_context* ctx, const int32_t* perm, const int32_t* seg,
                                 int64_t m_c, const void* w_und, spc_dtype wt, void* a_und);
+
+// The self-mass reading of the multilevel driver (the merged node of the proof of Theorem 2).
+// mass_out[U] = (the members' masses prev_mass[x], ascending x, summed left to right from 0)
+// + self_mass[U]; prev_mass null means all zero (then mass_out is self_mass itself and nothing
+// runs: *mass_ptr = self_mass).  Types: int64 for SPC_I32, else the weight type.
+spc_status run_carry_mass(spc_context* ctx, int64_t n, const int32_t* lift, int64_t n_c,
+                          const void* prev_mass, const void* self_mass, spc_dtype wt,
+                          Buf& mass_out, const void** mass_ptr);
+// The graph g with entry (x, x) = 2 mass[x] in its ascending-column place for every x with
+// mass[x] != 0 (edge ids unchanged); written into the context's dg_* buffers, described by out.
+spc_status run_diag_graph(spc_context* ctx, const GraphView& g, const void* mass,
+                          GraphView& out);
 spc_status run_pool_forward(spc_context* ctx, int64_t n, const int32_t* lift, int64_t n_c,
                             int64_t F, spc_dtype dt, const void* x, void* xc);
 spc_status run_pool_backward(spc_context* ctx, int64_t n, const int32_t* lift, int64_t n_c,

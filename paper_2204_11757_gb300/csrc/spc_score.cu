@@ -2,7 +2,12 @@
 //
 // Score (Theorem 1; the fitness loop of Algorithm 1, one norm per edge, Section 2):
 //   f(a, b) = || w_a / d_a - w_b / d_b ||_1 = sum over x in N(a) u N(b) of |p_ax - p_bx|,
-// the union taken in ascending x and containing a and b themselves (p_aa = p_bb = 0).
+// the union taken in ascending x and containing a and b themselves.  A caller's graph has no
+// diagonal (p_aa = p_bb = 0).  Under the self-mass reading of the multilevel driver a coarse
+// graph holds the diagonal entry (x, x) = 2 mass(x) of every super-node with internal weight
+// (the merged node of the proof of Theorem 2); it is an ordinary stored entry of row x, so the
+// degree and the union walks include it with no special case.  `nlow` counts the entries of a
+// row at or below its diagonal: the upper (edge) entries start after them.
 // Every sum here runs sequentially in ascending column order with IEEE round-to-nearest adds
 // (__dadd_rn / __fadd_rn, no FMA), and p = w / d is one IEEE division per stored entry, so
 // the results are the same bits on every run and every schedule.
@@ -80,7 +85,7 @@ __device__ __forceinline__ unsigned long long key_bits(double s) {
 __device__ __forceinline__ unsigned int key_bits(float s) { return __float_as_uint(s); }
 
 // S0 + S1: one thread per row.  Checks the row (when `validate`), sums the weighted degree in
-// ascending column order, counts the entries below the diagonal and above it.
+// ascending column order, counts the entries at or below the diagonal and above it.
 template <class WT>
 __global__ void __launch_bounds__(kThreads)
 k_rows_degree(int64_t n, int64_t nnz, const int64_t* __restrict__ rowptr,
@@ -119,7 +124,7 @@ k_rows_degree(int64_t n, int64_t nnz, const int64_t* __restrict__ rowptr,
                 if (!Tr<WT>::ok(wj)) bits |= DEV_BAD_WEIGHT;
                 prev = y;
             }
-            nlow += ((int64_t)y < x) ? 1 : 0;
+            nlow += ((int64_t)y <= x) ? 1 : 0;
             acc = Tr<WT>::add(acc, wj);
         }
         deg[x] = acc;
@@ -131,8 +136,8 @@ k_rows_degree(int64_t n, int64_t nnz, const int64_t* __restrict__ rowptr,
 
 // S0 for rows longer than kLongRow, part 1: one warp per row records the row as a sequence
 // (base, length) for the exact degree sum (the per-binade tables of spc_seqtab.cu evaluate
-// it) and counts its lower neighbours by a 32-way search for x among the sorted columns.  On
-// an unsorted row the count is wrong but in range; part 2 reports the row.
+// it) and counts its entries at or below the diagonal by a 32-way search for x among the
+// sorted columns.  On an unsorted row the count is wrong but in range; part 2 reports the row.
 template <class WT>
 __global__ void __launch_bounds__(kThreads)
 k_long_rows_meta(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
@@ -150,14 +155,14 @@ k_long_rows_meta(const int64_t* __restrict__ rowptr, const int32_t* __restrict__
          i += warps) {
         const int64_t x = long_rows[i];
         const int64_t r0 = rowptr[x], r1 = rowptr[x + 1];
-        // first position in [r0, r1] whose column is >= x
+        // first position in [r0, r1] whose column is > x
         int64_t lo = r0, hi = r1;  // answer in [lo, hi]
         while (hi > lo) {
             const int64_t step = (hi - lo + 31) / 32;
             const int64_t probe = lo + (int64_t)lane * step;  // lane 0 probes lo itself
-            const bool below = probe < hi && (int64_t)col[probe] < x;
+            const bool below = probe < hi && (int64_t)col[probe] <= x;
             const int nb = __popc(__ballot_sync(0xffffffffu, below));
-            // columns below x form a prefix of the probes
+            // columns up to x form a prefix of the probes
             if (nb == 0) { hi = lo; break; }
             lo = lo + (int64_t)(nb - 1) * step + 1;
             const int64_t cap = lo - 1 + step;
@@ -607,8 +612,9 @@ k_hub_posmap(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col
     }
 }
 
-// Hub edge (H, v) where v's only neighbour is H: the union of the two rows is H's row with the
-// single term |0 - p_v[H]| = 1 (p_v[H] = w / w) inserted at H's own column position, so every
+// Hub edge (H, v) where v's only entry is H (v has no diagonal): the union of the two rows is
+// H's row with p_v[H] = w / w = 1 at H's own column position -- a term |0 - 1| = 1 inserted
+// there, or, when H's row holds its diagonal entry, that entry's term |p_HH - 1| -- so every
 // such edge of H has the same score.  A warp evaluates it once per hub.
 template <class PT>
 __global__ void __launch_bounds__(kThreads)
@@ -623,16 +629,18 @@ k_hub_leaf_score(const int64_t* __restrict__ rowptr, const int32_t* __restrict__
         const int64_t H = long_rows[i];
         const int64_t rH = rowptr[H], dH = rowptr[H + 1] - rH;
         const int32_t* cH = col + rH;
-        int64_t lo = 0, hi = dH;  // first position whose column is above H
+        int64_t lo = 0, hi = dH;  // first position whose column is H or above
         while (lo < hi) {
             const int64_t mid = (lo + hi) >> 1;
             if ((int64_t)cH[mid] < H) lo = mid + 1; else hi = mid;
         }
+        const bool diag = lo < dH && (int64_t)cH[lo] == H;
         const unsigned long long* P = tab.P + tab.tab_off[i];
         const int32_t* T = tab.T + tab.tab_off[i];
         PT s = tab_run_warp<PT>(PT(0), 0, lo, p + rH, P, T, tab.eblo[i], tab.nE[i], dH + 1);
-        s = p_add(s, PT(1));
-        s = tab_run_warp<PT>(s, lo, dH, p + rH, P, T, tab.eblo[i], tab.nE[i], dH + 1);
+        s = p_add(s, diag ? p_absdiff(p[rH + lo], PT(1)) : PT(1));
+        s = tab_run_warp<PT>(s, diag ? lo + 1 : lo, dH, p + rH, P, T, tab.eblo[i], tab.nE[i],
+                             dH + 1);
         if ((threadIdx.x & 31) == 0) leaf[i] = s;
     }
 }
@@ -662,6 +670,7 @@ k_score_hub(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
         const int64_t rH = rowptr[H], dH = rowptr[H + 1] - rH;
         const int64_t k = f - lr_eoff[i];
         const int64_t v = col[rH + k];
+        if (v == H) continue;  // H's diagonal entry is no edge
         const int64_t rv = rowptr[v], dv = rowptr[v + 1] - rv;
         if (dv > dH || (dv == dH && v < H)) continue;  // v's row is the hub of this edge
         if (dv == 1 && key_bits(p[rv]) == key_bits(PT(1))) {  // v a leaf of H: the hub's value
@@ -942,7 +951,7 @@ static spc_status score_typed(spc_context* ctx, GraphView& g, bool validate, voi
     }
     // every input check of every row so far
     SPC_TRY(check_status(ctx));
-    if (2 * m != nnz) return SPC_ERR_NOT_SYMMETRIC;
+    if (2 * m + g.ndiag != nnz) return SPC_ERR_NOT_SYMMETRIC;
     g.m = m;
     // rowptr, columns, weights, degrees and row counts read once; p and the undirected edge
     // list written once (no model on levels with long rows: another kernel takes their part)

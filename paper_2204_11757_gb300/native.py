@@ -43,7 +43,8 @@ class spc_allocator(ctypes.Structure):
 
 class spc_options(ctypes.Structure):
     _fields_ = [("levels", ctypes.c_int32), ("validate", ctypes.c_int32),
-                ("use_graph", ctypes.c_int32), ("schedule", ctypes.c_int32)]
+                ("use_graph", ctypes.c_int32), ("schedule", ctypes.c_int32),
+                ("self_mass", ctypes.c_int32)]
 
 
 class spc_level(ctypes.Structure):
@@ -54,7 +55,8 @@ class spc_level(ctypes.Structure):
                 ("self_mass", ctypes.c_void_p), ("a_und", ctypes.c_void_p),
                 ("rowptr_c", ctypes.c_void_p), ("col_c", ctypes.c_void_p),
                 ("w_c", ctypes.c_void_p), ("perm", ctypes.c_void_p), ("seg", ctypes.c_void_p),
-                ("graph_ptr_c", ctypes.c_void_p), ("ms", ctypes.c_float)]
+                ("graph_ptr_c", ctypes.c_void_p), ("ms", ctypes.c_float),
+                ("mass", ctypes.c_void_p)]
 
 
 # name -> (restype, argtypes); the full list of include/spcoarsen.h

@@ -174,6 +174,13 @@ def _check_level(lv, ref_level, exact_weights=True):
         assert got.dtype == want.dtype
         assert np.array_equal(_bits(got) if got.dtype.kind == "f" else got,
                               _bits(want) if want.dtype.kind == "f" else want)
+    # the accumulated internal weight of the self-mass reading
+    if getattr(ref_level, "mass", None) is not None:
+        assert lv.mass is not None
+        got, want = lv.mass.cpu().numpy(), ref_level.mass
+        assert got.dtype == want.dtype
+        assert np.array_equal(_bits(got) if got.dtype.kind == "f" else got,
+                              _bits(want) if want.dtype.kind == "f" else want)
     # perm/seg describe each coarse edge's fine edges in ascending eid order
     perm = lv.perm.cpu().numpy(); seg = lv.seg.cpu().numpy()
     assert seg[0] == 0 and seg[-1] == lv.m_inter
@@ -417,6 +424,52 @@ def test_powerlaw_multilevel_bitexact(ctx, name, weight, dt):
     for lv, ref in zip(ctx.levels(), levels_ref):
         assert np.array_equal(_bits(lv.score.cpu().numpy()), _bits(ref.f))
         _check_level(lv, ref)
+
+
+@pytest.mark.parametrize("name", ["s2_tri256_f64", "s4_rgg64k_f32", "powerlaw_int"])
+def test_coarsen_without_self_mass_matches_oracle(ctx, name):
+    """The other multilevel reading (each level scores the coarse graph without its internal
+    weight): every level bit-exact with the oracle's self_mass_degree=False, and no carried
+    mass reported."""
+    api = _api()
+    if name == "powerlaw_int":
+        g, ratio, mode = I.powerlaw_graph(4039, 22, 7, "int", np.int32), 8, "halving"
+    else:
+        g, cfg = I.config_graph(name)
+        ratio, mode = cfg["ratio"], cfg["mode"]
+    levels_ref, total_ref = O.coarsen(g, ratio, mode, self_mass_degree=False)
+    L = len(levels_ref)
+    lift, nca, st = ctx.coarsen(api.CSR.from_graph(g), levels_ref[-1].target, levels=L,
+                                self_mass=False)
+    assert nca == levels_ref[-1].n_c
+    assert np.array_equal(lift.cpu().numpy(), total_ref)
+    for lv, ref in zip(ctx.levels(), levels_ref):
+        assert lv.mass is None
+        assert np.array_equal(_bits(lv.score.cpu().numpy()), _bits(ref.f))
+        _check_level(lv, ref)
+
+
+def test_self_mass_reading_differs_and_carries_the_internal_weight(ctx):
+    """The two readings agree on the first level and part from the second on; under the
+    self-mass reading every level's carried mass of an integer-weight graph is exactly the
+    total weight of the original edges inside each super-node."""
+    api = _api()
+    g = I.random_graph(3000, 0.003, 21, weight="int", dtype=np.int32, connected=True)
+    csr = api.CSR.from_graph(g)
+    lift_a, _, _ = ctx.coarsen(csr, g.n // 16, levels=4)
+    lv_a = ctx.levels()
+    lift_b, _, _ = ctx.coarsen(csr, g.n // 16, levels=4, self_mass=False)
+    lv_b = ctx.levels()
+    assert torch.equal(lv_a[0].lift, lv_b[0].lift)
+    assert not all(torch.equal(x.lift, y.lift) for x, y in zip(lv_a, lv_b))
+    comp = np.arange(g.n)
+    for lv in lv_a:
+        comp = lv.lift.cpu().numpy()[comp]
+        inside = comp[g.eu] == comp[g.ev]
+        want = np.bincount(comp[g.eu][inside], weights=g.w_und[inside].astype(np.float64),
+                           minlength=lv.n_c).astype(np.int64)
+        assert np.array_equal(lv.mass.cpu().numpy(), want)
+    assert np.array_equal(comp, lift_a.cpu().numpy())
 
 
 def test_coarsen_host_buffers_match_device(ctx):

@@ -591,7 +591,7 @@ def test_self_mass_scores_are_the_merged_node_definition():
     """With the self-mass on the diagonal, the next level's score of super-nodes (U, X) equals,
     in exact rationals, || sum_{x in U} w_x / sum_{x in U} d_x - (the same for X) ||_1 with the
     fine rows aggregated into super-node coordinates: the merged node (w_a + w_b) / (d_a + d_b)
-    of the proof of Theorem 2, repeated.  Without it (the default), some scores differ."""
+    of the proof of Theorem 2, repeated.  Without it, some scores differ."""
     differs = 0
     for seed in range(12):
         g = I.random_graph(10, 0.45, 1200 + seed, weight="int", dtype=np.int32, connected=True)
@@ -660,8 +660,8 @@ def test_self_mass_accumulates_internal_weight():
     the original edges inside it, at every level; the first level does not depend on the
     reading."""
     g = I.random_graph(200, 0.04, 7, weight="int", dtype=np.int32, connected=True)
-    ref, _ = O.coarsen(g, 8, "halving")
-    levels, total = O.coarsen(g, 8, "halving", self_mass_degree=True)
+    ref, _ = O.coarsen(g, 8, "halving", self_mass_degree=False)
+    levels, total = O.coarsen(g, 8, "halving")
     assert np.array_equal(levels[0].lift, ref[0].lift)
     comp = np.arange(g.n)
     for lv in levels:
@@ -732,3 +732,23 @@ def test_batch_oracle_self_mass_reading_is_per_graph():
         assert total.shape[0] == n1 - n0
         assert levels[-1].n_c == max(1, (n1 - n0) // 8)
         assert np.all(np.isfinite(levels[-1].mass)) and levels[-1].mass.min() >= 0
+
+
+def test_carried_mass_order_is_ascending_members_then_self_mass():
+    """The carried mass of a super-node is its members' masses in ascending member id, summed
+    left to right from 0, then this level's self-mass.  In binary32 the order shows: 2^24 + 1 + 1
+    stays 2^24 left to right (each 1 is a tie to even), while 1 + 1 + 2^24 would give 2^24 + 2."""
+    big = np.float32(2 ** 24)
+    mass = np.array([big, 5, 1, 7, 1], dtype=np.float32)
+    lift = np.array([0, 1, 0, 1, 0], dtype=np.int32)
+    self_mass = np.array([1, 3], dtype=np.float32)
+    got = O.carry_self_mass(mass, lift, 2, self_mass)
+    want = np.zeros(2, dtype=np.float32)
+    for x in range(5):                      # ascending member id
+        want[lift[x]] = np.float32(want[lift[x]] + mass[x])
+    want = (want + self_mass).astype(np.float32)
+    assert got.dtype == np.float32
+    assert np.array_equal(got.view(np.uint32), want.view(np.uint32))
+    assert got[0] == big and got[1] == np.float32(15)
+    # the reverse member order would have kept the two ones
+    assert np.float32(np.float32(1 + 1) + big) + 1 != got[0]
