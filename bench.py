@@ -3,10 +3,15 @@
 
 One step = one full coarsening of the workload (every level: validation, degrees, normalised
 rows, scores, merge selection, relabel, contraction), inputs resident in HBM.  The default
-workload is the 2048x2048 jittered triangle mesh with FP64 1/length weights, coarsened by six
-halving levels to n/64.  value = (sum over levels of the fine edges that level processed) /
-(device time of a step).  Under torchrun each rank coarsens its own replica (the single-graph
-path does not shard), so value is the sum over ranks.
+workload (the headline) is the largest single graph: a random geometric graph of 2^23 points
+in the unit cube, mean degree 12, FP32 weights exp(-d^2/r^2), coarsened by eight halving
+levels to n/256.  value = (sum over levels of the fine edges that level processed) / (device
+time of a step).  The same line carries, under "configs", the other configurations: the
+2048x2048 FP64 triangle mesh (6 levels), the 129^3 FP64 tetrahedral mesh (7 levels), the
+random geometric graph coarsened in one level to n/256, and the 10,000-mesh batch (forward +
+backward graphs/s against a per-graph loop).  Under torchrun each rank coarsens its own
+replica (the single-graph path does not shard), so value is the sum over ranks; the batch
+shards by graphs.
 
 --impl reference times the CPU oracle instead (test infrastructure, the only other use of it
 here), on a bounded sample of the same workload.
@@ -266,38 +271,267 @@ class ClockSampler:
                 "samples": len(rows)}
 
 
-# GB300's nominal FP64 rate is 1.25 TFLOP/s counting a fused multiply-add as two operations:
-# 625 G plain FP64 additions or subtractions per second (152 SMs at up to 2.07 GHz)
-FP64_PEAK_GOPS = 625.0
+# The binary64 score is bound by the FP64 pipe: its peak is the measured FP64 add rate of a
+# GB300 (506.5 G additions/s, profiles/fp64_add_probe_gb300.md).
+FP64_PEAK_GOPS = 506.5
+FP64_PEAK_SOURCE = "measured FP64 add throughput (profiles/fp64_add_probe_gb300.md)"
 
-# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the dominant kernel,
-# from an ncu capture of the same kernel; None where no capture of the current kernel exists.
-# The 2048^2 mesh's score: the mean over the six level launches of one step (852.4, 257.4,
-# 104.6, 39.5, 8.6 and 2.1 MB; profiles/score_traffic_c2_tri2048_f64.md), the same launches
-# that `achieved` averages.
-TRAFFIC = {("c2_tri2048_f64", "(k_score_edges<P, Key, kScoreChains>)"): 210.80e6}
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of a workload's dominant
+# kernel, from an ncu capture of the same kernel; absent where no capture of the current kernel
+# exists (then `traffic` is null).
+TRAFFIC = {}
+
+HEADLINE = "c4_rgg8m_f32"
+# the other configurations reported in the same line (their own keys, fewer steps)
+EXTRAS = ["c4_rgg8m_f32_one", "c2_tri2048_f64", "c3_tet129_f64", "c5_batch10k_f32"]
 
 
-def run_batched(args):
+def _peaks():
+    try:
+        p = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        return float(p["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs)"
+    except (OSError, ValueError, KeyError):
+        return 6800.0, "fallback (6.8 TB/s)"
+
+
+def _roofline(workload, dominant, prof_entry, launches, ms, fp64):
+    """Roofline of the dominant kernel from its timed launches: algorithmic bytes (the library's
+    per-launch byte model: every input the operation needs read once, every output written
+    once) or, for the binary64 score, the additions and subtractions it needs, over the
+    launches' summed CUDA-event time."""
+    hbm, src = _peaks()
+    nbytes, ops = prof_entry[2], prof_entry[3]
+    ach = nbytes / (ms * 1e-3) / 1e9 if nbytes > 0 and ms > 0 else None
+    roof = {"kernel": dominant, "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
+            "frac": ach / hbm if ach else None,
+            "traffic": TRAFFIC.get((workload, dominant)), "peak_source": src,
+            "launches": launches, "avg_launch_ms": ms / max(1, launches),
+            "algorithmic_bytes_per_launch": nbytes / max(1, launches)}
+    if ops > 0 and fp64:
+        roof.update({"bound": "alu", "achieved": ops / (ms * 1e-3) / 1e9, "peak": FP64_PEAK_GOPS,
+                     "unit": "G FP64 adds/s", "peak_source": FP64_PEAK_SOURCE,
+                     "fp64_ops_per_launch": ops / max(1, launches),
+                     "hbm_achieved_gbs": ach, "hbm_frac": ach / hbm if ach else None})
+        roof["frac"] = roof["achieved"] / FP64_PEAK_GOPS
+    return roof
+
+
+def _dist_setup():
+    import torch
+    import torch.distributed as dist
+    ws, rank, local = _dist()
+    if ws > 1 and not dist.is_initialized():
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    return ws, rank, local
+
+
+def _max_over_ranks(t_ms, ws, dev):
+    if ws == 1:
+        return t_ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([t_ms], device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+_GRAPHS = {}
+
+
+def _config_graph(cfg_name):
+    """The workload's graph, generated once per process (the one-level and the multilevel
+    random geometric graph are the same graph)."""
+    from paper_2204_11757_gb300 import inputs as I
+    cfg = I.CONFIGS[cfg_name]
+    key = tuple(sorted((k, str(v)) for k, v in cfg.items() if k not in ("mode", "ratio")))
+    t0 = time.perf_counter()
+    if key not in _GRAPHS:
+        _GRAPHS.clear()
+        _GRAPHS[key] = I.config_graph(cfg_name)[0]
+    return _GRAPHS[key], cfg, time.perf_counter() - t0
+
+
+def bench_single(workload, steps, warmup, e2e_on=True, pool=0, want_profile=False):
+    """One step = one full coarsening of the workload (every level), inputs resident in HBM."""
+    import torch
+    import torch.distributed as dist
+    from paper_2204_11757_gb300 import api
+    ws, rank, local = _dist_setup()
+    cfg_name, L, desc = WORKLOADS[workload]
+    g, cfg, t_gen = _config_graph(cfg_name)
+    n_c = max(1, g.n // cfg["ratio"])
+    dev = torch.device("cuda", local)
+    csr = api.CSR.from_graph(g, dev)
+    ctx = api.Context(dev)
+    stream = ctx.stream
+    lift = torch.empty(g.n, dtype=torch.int32, device=dev)
+
+    def step():
+        ctx.coarsen(csr, n_c, levels=L, lift_out=lift)
+
+    for _ in range(warmup):
+        step()
+    levels = [ctx.level_info(l) for l in range(ctx.level_count())]
+    edges_per_step = sum(int(lv.m) for lv in levels)
+
+    # one profiled step: per-kernel device time, to find the dominant kernel
+    ctx.time_kernel("*")
+    step()
+    prof = ctx.kernel_profile()
+    step_prof_ms = sum(v[1] for v in prof.values())
+    dominant = max(prof.items(), key=lambda kv: kv[1][1])[0]
+
+    # ---- timed region: the dominant kernel's launches carry CUDA events on the library's
+    # stream (inside the captured graph) --------------------------------------------------------
+    ctx.time_kernel(dominant)
+    step()  # untimed: re-captures the schedule with the dominant kernel's events in it
+    ctx.kernel_time()
+    ctx.time_kernel(dominant)
+    sampler = ClockSampler(local)
+    if rank == 0:
+        sampler.start()
+        time.sleep(0.3)
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    launches0 = ctx.launch_count
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(steps):
+        step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    clocks = sampler.stop() if rank == 0 else None
+    launches = ctx.launch_count - launches0
+    t_ms = _max_over_ranks(ev0.elapsed_time(ev1) / steps, ws, dev)
+    dom_prof = ctx.kernel_profile()
+    dom_launches, dom_ms = ctx.kernel_time()
+    ctx.time_kernel(None)
+    level_ms = [float(ctx.level_info(l).ms) for l in range(len(levels))]
+    value = ws * edges_per_step / (t_ms * 1e-3) / 1e6
+    roof = _roofline(workload, dominant, dom_prof.get(dominant, (0, 0.0, 0.0, 0.0)),
+                     dom_launches, dom_ms, g.w.dtype != np.float32)
+
+    # ---- end to end through host buffers: the pinned host CSR in, the lift and the final
+    # coarse CSR out, every step ---------------------------------------------------------------
+    e2e = None
+    if e2e_on:
+        host = api.CSR.from_graph(g, device="cpu", pin=True)
+        lift_h = torch.empty(g.n, dtype=torch.int32).pin_memory()
+        bufs = None
+
+        def e2e_step():
+            nonlocal bufs
+            ctx.coarsen(host, n_c, levels=L, lift_out=lift_h)
+            info = ctx.level_info(ctx.level_count() - 1)
+            if bufs is None or bufs[1].shape[0] < 2 * info.m_c:
+                bufs = (torch.empty(info.n_c + 1, dtype=torch.int64).pin_memory(),
+                        torch.empty(2 * info.m_c, dtype=torch.int32).pin_memory(),
+                        torch.empty(2 * info.m_c, dtype=csr.w.dtype).pin_memory())
+            for dst, src in zip(bufs, (info.rowptr_c, info.col_c, info.w_c)):
+                ctx.lib.spc_copy(ctx._handle, api._ptr(dst), src, dst.numel() * dst.element_size())
+            return info
+
+        info = e2e_step()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        ksteps = max(1, min(steps, 5))
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(ksteps):
+            info = e2e_step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        e_ms = _max_over_ranks(e0.elapsed_time(e1) / ksteps, ws, dev)
+        h2d = host.rowptr.numel() * 8 + host.col.numel() * 4 + host.w.numel() * host.w.element_size()
+        d2h = g.n * 4 + (info.n_c + 1) * 8 + 2 * info.m_c * (4 + csr.w.element_size())
+        e2e = {"value": ws * edges_per_step / (e_ms * 1e-3) / 1e6, "unit": UNIT,
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+               "ms_per_step": e_ms}
+
+    # ---- node-feature pooling on the final lift (forward + backward), kernels timed live ------
+    pooling = None
+    if pool > 0:
+        hbm, _ = _peaks()
+        F = pool
+        n_c_f = int(ctx.level_info(ctx.level_count() - 1).n_c)
+        gen = torch.Generator(device=dev).manual_seed(0)
+        x = torch.randn(g.n, F, dtype=torch.float32, device=dev, generator=gen)
+        gxc = torch.randn(n_c_f, F, dtype=torch.float32, device=dev, generator=gen)
+        for _ in range(2):
+            ctx.pool_features(lift, n_c_f, x)
+            ctx.pool_features_backward(lift, n_c_f, gxc)
+        ctx.time_kernel("k_pool")
+        reps = 5
+        p0, p1, p2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        torch.cuda.synchronize()
+        p0.record(stream)
+        for _ in range(reps):
+            ctx.pool_features(lift, n_c_f, x)
+        p1.record(stream)
+        for _ in range(reps):
+            ctx.pool_features_backward(lift, n_c_f, gxc)
+        p2.record(stream)
+        torch.cuda.synchronize()
+        kp = ctx.kernel_profile()
+        ctx.time_kernel(None)
+        top = max(kp.items(), key=lambda kv: kv[1][1])
+        ach = top[1][2] / (top[1][1] * 1e-3) / 1e9 if top[1][2] > 0 else None
+        pooling = {"features": F, "dtype": "f32", "n": g.n, "n_c": n_c_f,
+                   "forward_ms": p0.elapsed_time(p1) / reps,
+                   "backward_ms": p1.elapsed_time(p2) / reps,
+                   "roofline": {"kernel": top[0], "bound": "hbm", "achieved": ach, "peak": hbm,
+                                "unit": "GB/s", "frac": ach / hbm if ach else None}}
+    res = {
+        "metric": METRIC, "value": value, "unit": UNIT, "ms_per_step": t_ms,
+        "dtype": {np.dtype("float64"): "f64", np.dtype("float32"): "f32",
+                  np.dtype("int32"): "i32"}[g.w.dtype],
+        "config": {
+            "workload": f"{workload}: {desc}", "n": g.n, "m": g.m, "n_c": n_c, "levels": L,
+            "multilevel_reading": "self-mass (the merged node of Theorem 2's proof)",
+            "parallelism": "replicas" if ws > 1 else "single GPU",
+            "l2": "inputs larger than L2 (%.0f MB resident CSR)" % (
+                (csr.rowptr.numel() * 8 + csr.col.numel() * 4
+                 + csr.w.numel() * csr.w.element_size()) / 1e6),
+            "generation_s": round(t_gen, 1),
+            "per_level": [{"n": int(lv.n), "m": int(lv.m), "n_c": int(lv.n_c),
+                           "m_c": int(lv.m_c), "ms": ms,
+                           "M_edges_s": (int(lv.m) / (ms * 1e-3) / 1e6) if ms > 0 else None}
+                          for lv, ms in zip(levels, level_ms)],
+        },
+        "roofline": roof, "e2e": e2e, "clocks": clocks, "gpu_launches": int(launches),
+        "steps": steps, "warmup": warmup,
+    }
+    if pooling is not None:
+        res["pooling"] = pooling
+    if want_profile:
+        res["kernel_profile"] = {k: [v[0], round(v[1], 4)] for k, v in
+                                 sorted(prof.items(), key=lambda kv: -kv[1][1])}
+        res["profiled_step_ms"] = step_prof_ms
+    ctx.close()
+    del csr, lift
+    torch.cuda.empty_cache()
+    return res
+
+
+def bench_batched(steps, warmup, want_profile=False, cpu=False):
     """Batched forward + backward: one coarsening of every graph of the batch (3 halving levels,
     one set of launches for all graphs), the coarse weights through the differentiable
     contraction, loss sum(a * g), backward to the fine weights.  graphs/s = B / step time,
     against a loop that coarsens the graphs one by one with the single-graph entry point."""
     import torch
     import torch.distributed as dist
-    import __graft_entry__ as ge
     from paper_2204_11757_gb300 import api, inputs as I, shard as S
 
-    ws, rank, local = _dist()
-    if ws > 1:
-        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
-        dist.init_process_group("nccl")
-    torch.cuda.set_device(local)
-    if rank == 0:
-        ge.build()
-    if ws > 1:
-        dist.barrier()
+    ws, rank, local = _dist_setup()
+    t_gen = time.perf_counter()
     full, cfg = I.config_graph("c5_batch10k_f32")
+    t_gen = time.perf_counter() - t_gen
     batch, (g0, g1) = S.local_batch(full, rank, ws) if ws > 1 else (full, (0, full.B))
     dev = torch.device("cuda", local)
     csr = api.CSR.from_graph(batch.graph, dev)
@@ -315,7 +549,7 @@ def run_batched(args):
         (a * gvec).sum().backward()
         return w.grad
 
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         step()
     # one profiled step finds the dominant kernel; the timed steps time its launches
     ctx.time_kernel("*")
@@ -324,38 +558,31 @@ def run_batched(args):
     dominant = max(prof.items(), key=lambda kv: kv[1][1])[0]
     ctx.time_kernel(dominant)
     step()  # untimed: re-captures with the dominant kernel's events
+    ctx.kernel_time()
     ctx.time_kernel(dominant)
+    sampler = ClockSampler(local)
+    if rank == 0:
+        sampler.start()
+        time.sleep(0.3)
     if ws > 1:
         dist.barrier()
     torch.cuda.synchronize()
     launches0 = ctx.launch_count
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
-    sampler = ClockSampler(local)
-    if rank == 0:
-        sampler.start()
-        time.sleep(0.3)
     ev0.record(ctx.stream)
-    for _ in range(args.steps):
+    for _ in range(steps):
         step()
     ev1.record(ctx.stream)
     torch.cuda.synchronize()
     clocks = sampler.stop() if rank == 0 else None
-    t_ms = ev0.elapsed_time(ev1) / args.steps
+    t_ms = _max_over_ranks(ev0.elapsed_time(ev1) / steps, ws, dev)
     launches = ctx.launch_count - launches0
-    dprof = ctx.kernel_profile().get(dominant, (0, 0.0, 0.0, 0.0))
+    dom_prof = ctx.kernel_profile()
+    dom_launches, dom_ms = ctx.kernel_time()
     ctx.time_kernel(None)
-    peaks = {}
-    try:
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-    except (OSError, ValueError):
-        pass
-    hbm = float(peaks.get("hbm_gbs", 6800.0))
-    ach = dprof[2] / (dprof[1] * 1e-3) / 1e9 if dprof[2] > 0 and dprof[1] > 0 else None
-    roof = {"kernel": dominant, "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
-            "frac": ach / hbm if ach else None, "traffic": None,
-            "peak_source": "measured" if peaks else "fallback", "launches": dprof[0],
-            "avg_launch_ms": dprof[1] / max(1, dprof[0])}
+    roof = _roofline("c5_batch10k_f32", dominant, dom_prof.get(dominant, (0, 0.0, 0.0, 0.0)),
+                     dom_launches, dom_ms, False)
 
     # end to end: the batch in pinned host memory, copied in by the library; the gradient
     # of the fine weights and the per-graph coarse offsets read back
@@ -376,21 +603,17 @@ def run_batched(args):
 
     e2e_step()
     torch.cuda.synchronize()
-    k = max(1, min(args.steps, 3))
+    k = max(1, min(steps, 3))
     t0 = time.perf_counter()
     for _ in range(k):
-        gpc = e2e_step()
+        e2e_step()
     torch.cuda.synchronize()
-    e_ms = (time.perf_counter() - t0) * 1e3 / k
+    e_ms = _max_over_ranks((time.perf_counter() - t0) * 1e3 / k, ws, dev)
     h2d = (host.rowptr.numel() * 8 + host.col.numel() * 4 + host.w.numel() * 4
            + gptr_h.numel() * 8 + batch.graph.m * 4)
     d2h = batch.graph.m * 4 + (batch.B + 1) * 8 + batch.graph.n * 4
     e2e = {"value": ws * batch.B / (e_ms * 1e-3), "unit": "graphs/s",
            "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "ms_per_step": e_ms}
-    if ws > 1:
-        t = torch.tensor([t_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_ms = float(t.item())
     value = full.B / (t_ms * 1e-3)
     # per-graph loop of the single-graph coarsener on a sample, same work per graph
     loop = None
@@ -416,29 +639,38 @@ def run_batched(args):
             one(gc, wu, n)
         torch.cuda.synchronize()
         loop_s = (time.perf_counter() - t0) / len(gs)
-        loop = {"graphs_s": 1.0 / loop_s, "sample_graphs": len(gs)}
-    if rank == 0:
-        line = {
-            "metric": "batched fwd+bwd graphs/s", "value": value, "unit": "graphs/s",
-            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_ms,
-            "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "f32",
-            "data": "synthetic",
-            "config": {"workload": "c5_batch10k_f32: 10,000 jittered 2D/3D meshes, node counts "
-                                   "log-uniform 200-20,000, FP32 1/edge-length, 3 halving "
-                                   "levels to n_b/8 each, forward + backward through the "
-                                   "contraction", "B": full.B, "n": full.graph.n,
-                       "m": full.graph.m, "parallelism": f"graphs sharded over {ws} rank(s)",
-                       "per_graph_loop": loop,
-                       "speedup_vs_per_graph_loop": (value / loop["graphs_s"]) if loop else None},
-            "roofline": roof, "e2e": e2e,
-            "cpu_baseline": _oracle_batched() if (ws == 1 and not args.no_cpu_baseline) else None,
-            "clocks": clocks, "gpu_launches": int(launches),
-        }
-        print(json.dumps(line), flush=True)
+        loop = {"graphs_s": 1.0 / loop_s, "sample_graphs": len(gs),
+                "what": "the same forward + backward, graph by graph, through spc_coarsen"}
+    res = {
+        "metric": "batched fwd+bwd graphs/s", "value": value, "unit": "graphs/s",
+        "ms_per_step": t_ms, "dtype": "f32", "steps": steps, "warmup": warmup,
+        "config": {"workload": "c5_batch10k_f32: 10,000 jittered 2D/3D meshes, node counts "
+                               "log-uniform 200-20,000, FP32 1/edge-length, 3 halving "
+                               "levels to n_b/8 each, forward + backward through the "
+                               "contraction", "B": full.B, "n": full.graph.n,
+                   "m": full.graph.m, "parallelism": f"graphs sharded over {ws} rank(s)",
+                   "generation_s": round(t_gen, 1), "per_graph_loop": loop,
+                   "speedup_vs_per_graph_loop": (value / loop["graphs_s"]) if loop else None},
+        "roofline": roof, "e2e": e2e, "clocks": clocks, "gpu_launches": int(launches),
+        "cpu_baseline": _oracle_batched() if (cpu and ws == 1 and rank == 0) else None,
+    }
+    if want_profile:
+        res["kernel_profile"] = {k: [v[0], round(v[1], 4)] for k, v in
+                                 sorted(prof.items(), key=lambda kv: -kv[1][1])}
     ctx.close()
-    if ws > 1:
-        dist.destroy_process_group()
-    return 0
+    del csr, gptr, w_und
+    torch.cuda.empty_cache()
+    return res
+
+
+def _summary(res):
+    """The keys of an extra configuration kept in the headline's line."""
+    keep = ("metric", "value", "unit", "ms_per_step", "dtype", "roofline", "e2e", "clocks",
+            "gpu_launches", "steps", "warmup", "kernel_profile")
+    out = {k: res[k] for k in keep if k in res}
+    cfg = dict(res["config"])
+    out["config"] = cfg
+    return out
 
 
 def main():
@@ -448,7 +680,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
     ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["c5_batch10k_f32"],
-                    default="c2_tri2048_f64")
+                    default=HEADLINE)
+    ap.add_argument("--no-extras", action="store_true",
+                    help="only the chosen workload (default: the headline adds the other "
+                         "configurations as keys of the same line)")
+    ap.add_argument("--extra-steps", type=int, default=5)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile", action="store_true", help="print the per-kernel breakdown")
@@ -460,224 +696,50 @@ def main():
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     if args.impl == "reference":
         return run_reference(args)
-    if args.workload == "c5_batch10k_f32":
-        return run_batched(args)
 
     import torch
     import torch.distributed as dist
-
-    ws, rank, local = _dist()
-    if ws > 1:
-        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
-        dist.init_process_group("nccl")
-    torch.cuda.set_device(local)
-
     import __graft_entry__ as ge
-    from paper_2204_11757_gb300 import api, inputs as I
+    ws, rank, local = _dist_setup()
     if rank == 0:
         ge.build()
     if ws > 1:
         dist.barrier()
-    cfg_name, L, desc = WORKLOADS[args.workload]
-    g, cfg = I.config_graph(cfg_name)
-    n_c = max(1, g.n // cfg["ratio"])
-    dev = torch.device("cuda", local)
-    csr = api.CSR.from_graph(g, dev)
-    ctx = api.Context(dev)
-    stream = ctx.stream
-    lift = torch.empty(g.n, dtype=torch.int32, device=dev)
 
-    def step():
-        ctx.coarsen(csr, n_c, levels=L, lift_out=lift)
-
-    for _ in range(args.warmup):
-        step()
-    levels = [ctx.level_info(l) for l in range(ctx.level_count())]
-    edges_per_step = sum(int(lv.m) for lv in levels)
-
-    # one profiled step: per-kernel device time, to find the dominant kernel
-    ctx.time_kernel("*")
-    step()
-    prof = ctx.kernel_profile()
-    step_prof_ms = sum(v[1] for v in prof.values())
-    dominant = max(prof.items(), key=lambda kv: kv[1][1])[0]
-
-    # ---- timed region ----------------------------------------------------------------------
-    sampler = ClockSampler(local)
-    if rank == 0:
-        sampler.start()
-        time.sleep(0.3)
-    ctx.time_kernel(dominant)
-    step()  # untimed: re-captures the schedule with the dominant kernel's events in it
-    ctx.kernel_time()
-    ctx.time_kernel(dominant)
-    if ws > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
-    launches0 = ctx.launch_count
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
-    ev0.record(stream)
-    for _ in range(args.steps):
-        step()
-    ev1.record(stream)
-    torch.cuda.synchronize()
-    if ws > 1:
-        dist.barrier()
-    launches = ctx.launch_count - launches0
-    t_ms = ev0.elapsed_time(ev1) / args.steps
-    dom_prof = ctx.kernel_profile()
-    dom_launches, dom_ms = ctx.kernel_time()
-    ctx.time_kernel(None)
-    clocks = sampler.stop() if rank == 0 else None
-    level_ms = [float(ctx.level_info(l).ms) for l in range(len(levels))]
-    if ws > 1:
-        t = torch.tensor([t_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_ms = float(t.item())
-    value = ws * edges_per_step / (t_ms * 1e-3) / 1e6
-
-    # ---- roofline of the dominant kernel --------------------------------------------------------
-    # algorithmic bytes per launch come from the library's per-launch byte models (every input
-    # the operation needs read once, every output written once); the time is the same launches'
-    # CUDA-event durations inside the timed region
-    peaks = {}
-    try:
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-    except (OSError, ValueError):
-        pass
-    hbm = float(peaks.get("hbm_gbs", 6800.0))
-    dom_bytes = dom_prof.get(dominant, (0, 0.0, 0.0, 0.0))[2]
-    dom_ops = dom_prof.get(dominant, (0, 0.0, 0.0, 0.0))[3]
-    achieved = dom_bytes / (dom_ms * 1e-3) / 1e9 if dom_bytes > 0 and dom_ms > 0 else None
-    roof = {"kernel": dominant, "bound": "hbm", "achieved": achieved, "peak": hbm,
-            "unit": "GB/s", "frac": achieved / hbm if achieved else None,
-            "traffic": TRAFFIC.get((args.workload, dominant)),
-            "peak_source": "measured" if peaks else "fallback",
-            "launches": dom_launches, "avg_launch_ms": dom_ms / max(1, dom_launches),
-            "algorithmic_bytes_per_launch": dom_bytes / max(1, dom_launches)}
-    if dom_ops > 0 and g.w.dtype != np.float32:
-        # binary64 score arithmetic: bound by the FP64 pipe, not by HBM
-        roof.update({"bound": "alu", "achieved": dom_ops / (dom_ms * 1e-3) / 1e9,
-                     "peak": FP64_PEAK_GOPS, "unit": "GFLOP/s",
-                     "peak_source": "nominal FP64 rate (1.25 TFLOP/s counting an FMA as 2)",
-                     "fp64_ops_per_launch": dom_ops / max(1, dom_launches),
-                     "hbm_achieved_gbs": achieved})
-        roof["frac"] = roof["achieved"] / FP64_PEAK_GOPS
-
-    # ---- end to end through host buffers -----------------------------------------------------------
-    e2e = None
-    if not args.no_e2e:
-        host = api.CSR.from_graph(g, device="cpu", pin=True)
-        lift_h = torch.empty(g.n, dtype=torch.int32).pin_memory()
-        last = levels[-1]
-        bufs = None
-
-        def e2e_step():
-            nonlocal bufs
-            ctx.coarsen(host, n_c, levels=L, lift_out=lift_h)
-            info = ctx.level_info(ctx.level_count() - 1)
-            if bufs is None or bufs[1].shape[0] < 2 * info.m_c:
-                bufs = (torch.empty(info.n_c + 1, dtype=torch.int64).pin_memory(),
-                        torch.empty(2 * info.m_c, dtype=torch.int32).pin_memory(),
-                        torch.empty(2 * info.m_c, dtype=csr.w.dtype).pin_memory())
-            for dst, src in zip(bufs, (info.rowptr_c, info.col_c, info.w_c)):
-                ctx.lib.spc_copy(ctx._handle, api._ptr(dst), src, dst.numel() * dst.element_size())
-            return info
-
-        info = e2e_step()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        ksteps = max(1, min(args.steps, 5))
-        torch.cuda.synchronize()
-        e0.record(stream)
-        for _ in range(ksteps):
-            info = e2e_step()
-        e1.record(stream)
-        torch.cuda.synchronize()
-        e_ms = e0.elapsed_time(e1) / ksteps
-        h2d = host.rowptr.numel() * 8 + host.col.numel() * 4 + host.w.numel() * host.w.element_size()
-        d2h = g.n * 4 + (info.n_c + 1) * 8 + 2 * info.m_c * (4 + csr.w.element_size())
-        e2e = {"value": ws * edges_per_step / (e_ms * 1e-3) / 1e6, "unit": UNIT,
-               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
-               "ms_per_step": e_ms}
-
-    # ---- node-feature pooling on the final lift (forward + backward), kernels timed live ----------
-    pooling = None
-    if args.pool > 0:
-        F = args.pool
-        n_c_f = int(ctx.level_info(ctx.level_count() - 1).n_c)
-        gen = torch.Generator(device=dev).manual_seed(0)
-        x = torch.randn(g.n, F, dtype=torch.float32, device=dev, generator=gen)
-        gxc = torch.randn(n_c_f, F, dtype=torch.float32, device=dev, generator=gen)
-        for _ in range(2):
-            ctx.pool_features(lift, n_c_f, x)
-            ctx.pool_features_backward(lift, n_c_f, gxc)
-        ctx.time_kernel("k_pool")
-        reps = 5
-        p0 = torch.cuda.Event(enable_timing=True)
-        p1 = torch.cuda.Event(enable_timing=True)
-        p2 = torch.cuda.Event(enable_timing=True)
-        torch.cuda.synchronize()
-        p0.record(stream)
-        for _ in range(reps):
-            ctx.pool_features(lift, n_c_f, x)
-        p1.record(stream)
-        for _ in range(reps):
-            ctx.pool_features_backward(lift, n_c_f, gxc)
-        p2.record(stream)
-        torch.cuda.synchronize()
-        kp = ctx.kernel_profile()
-        ctx.time_kernel(None)
-        kern = {k: {"launches": v[0], "ms": v[1] / max(1, v[0]),
-                    "GBps": (v[2] / (v[1] * 1e-3) / 1e9) if v[2] > 0 else None}
-                for k, v in kp.items()}
-        top = max(kp.items(), key=lambda kv: kv[1][1])
-        ach = top[1][2] / (top[1][1] * 1e-3) / 1e9 if top[1][2] > 0 else None
-        pooling = {"features": F, "dtype": "f32", "n": g.n, "n_c": n_c_f,
-                   "forward_ms": p0.elapsed_time(p1) / reps,
-                   "backward_ms": p1.elapsed_time(p2) / reps, "kernels": kern,
-                   "roofline": {"kernel": top[0], "bound": "hbm", "achieved": ach, "peak": hbm,
-                                "unit": "GB/s", "frac": ach / hbm if ach else None}}
-
-    cpu = None
-    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(args.workload)
-
+    if args.workload == "c5_batch10k_f32":
+        res = bench_batched(args.steps, args.warmup, args.profile, not args.no_cpu_baseline)
+    else:
+        res = bench_single(args.workload, args.steps, args.warmup, not args.no_e2e, args.pool,
+                           args.profile)
+        res["cpu_baseline"] = (cpu_baseline(args.workload) if rank == 0 and ws == 1
+                               and not args.no_cpu_baseline else None)
+    extras = {}
+    if args.workload == HEADLINE and not args.no_extras:
+        for name in EXTRAS:
+            st = max(1, args.extra_steps)
+            if name == "c5_batch10k_f32":
+                r = bench_batched(st, args.warmup, args.profile)
+            else:
+                r = bench_single(name, st, args.warmup, e2e_on=False, pool=0,
+                                 want_profile=args.profile)
+            extras[name] = _summary(r)
     if rank == 0:
         line = {
-            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": t_ms, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None,
-            "dtype": {np.dtype("float64"): "f64", np.dtype("float32"): "f32",
-                      np.dtype("int32"): "i32"}[g.w.dtype],
-            "data": "synthetic",
-            "config": {
-                "workload": f"{args.workload}: {desc}",
-                "n": g.n, "m": g.m, "n_c": n_c, "levels": L,
-                "parallelism": "replicas" if ws > 1 else "single GPU",
-                "l2": "inputs larger than L2 (%.0f MB resident CSR)" % (
-                    (csr.rowptr.numel() * 8 + csr.col.numel() * 4
-                     + csr.w.numel() * csr.w.element_size()) / 1e6),
-                "per_level": [{"n": int(lv.n), "m": int(lv.m), "n_c": int(lv.n_c),
-                               "m_c": int(lv.m_c), "ms": ms,
-                               "M_edges_s": (int(lv.m) / (ms * 1e-3) / 1e6) if ms > 0 else None}
-                              for lv, ms in zip(levels, level_ms)],
-            },
-            "roofline": roof,
-            "cpu_baseline": cpu,
-            "e2e": e2e,
-            "clocks": clocks,
-            "gpu_launches": int(launches),
+            "metric": res["metric"], "value": res["value"], "unit": res["unit"], "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": res["ms_per_step"],
+            "higher_is_better": True,
+            "scaling": "strong" if args.workload == "c5_batch10k_f32" else "weak",
+            "vs_baseline": None, "dtype": res["dtype"], "data": "synthetic",
+            "config": res["config"], "roofline": res["roofline"],
+            "cpu_baseline": res.get("cpu_baseline"), "e2e": res["e2e"], "clocks": res["clocks"],
+            "gpu_launches": res["gpu_launches"],
         }
-        if pooling is not None:
-            line["pooling"] = pooling
-        if args.profile:
-            line["kernel_profile"] = {k: [v[0], round(v[1], 4)] for k, v in
-                                      sorted(prof.items(), key=lambda kv: -kv[1][1])}
-            line["profiled_step_ms"] = step_prof_ms
+        for k in ("pooling", "kernel_profile", "profiled_step_ms"):
+            if k in res:
+                line[k] = res[k]
+        if extras:
+            line["configs"] = extras
         print(json.dumps(line), flush=True)
-    ctx.close()
     if ws > 1:
         dist.destroy_process_group()
     return 0
