@@ -158,6 +158,13 @@ SPC_API spc_status spc_context_create(spc_context** out, const spc_allocator* al
 /* Destroy a context and free everything it owns.  NULL is accepted. */
 SPC_API void spc_context_destroy(spc_context* ctx);
 
+/* Bound every device-side wait and retry loop of later calls on the context (the look-back
+ * of the scans and sorts, the union-find walks of the merge selection) to `iterations`;
+ * 0 restores the default of 2^22.  A wait that reaches the bound gives up and the call returns
+ * SPC_ERR_TIMEOUT; every index stays in range when a wait gives up, so the context stays
+ * usable.  Meant for exercising the timeout path: a small bound makes waits give up. */
+SPC_API spc_status spc_context_set_wait_limit(spc_context* ctx, uint32_t iterations);
+
 /* Change the stream later calls are issued on (captured graphs are re-captured). */
 SPC_API spc_status spc_context_set_stream(spc_context* ctx, void* stream);
 

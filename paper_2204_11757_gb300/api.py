@@ -89,7 +89,10 @@ class Context:
     """An spc_context bound to one CUDA device and stream."""
 
     def __init__(self, device=None, stream: Optional[torch.cuda.Stream] = None,
-                 torch_allocator: bool = True):
+                 torch_allocator: bool = True, alloc_hook=None):
+        """alloc_hook (optional, with torch_allocator): called with the byte count before every
+        workspace allocation; returning False makes that allocation fail (the library then
+        returns SPC_ERR_OOM), which lets a caller exercise the out-of-memory path."""
         if not torch.cuda.is_available():
             raise RuntimeError("the coarsener needs a CUDA device (there is no CPU path)")
         self.lib = N.lib()
@@ -104,6 +107,8 @@ class Context:
                 st = self.stream
 
                 def _alloc(_ctx, nbytes):
+                    if alloc_hook is not None and not alloc_hook(int(nbytes)):
+                        return None
                     try:
                         return torch.cuda.caching_allocator_alloc(int(nbytes), dev, st)
                     except Exception:  # out of memory -> NULL -> SPC_ERR_OOM
@@ -137,6 +142,12 @@ class Context:
 
     def __exit__(self, *exc):
         self.close()
+
+    def set_wait_limit(self, iterations: int):
+        """Bound every device-side wait of later calls (0: the default); a wait that reaches
+        the bound makes the call raise SpcError(SPC_ERR_TIMEOUT)."""
+        N.check(self.lib.spc_context_set_wait_limit(self._handle, int(iterations)),
+                "spc_context_set_wait_limit")
 
     # ---- helpers --------------------------------------------------------------------------
     def _csr(self, g: CSR) -> N.spc_csr:

@@ -953,6 +953,15 @@ void spc_context_destroy(spc_context* ctx) {
     delete ctx;
 }
 
+spc_status spc_context_set_wait_limit(spc_context* ctx, uint32_t iterations) {
+    if (!ctx) return SPC_ERR_INVALID_ARG;
+    SPC_CUDA(cudaSetDevice(ctx->device));
+    SPC_CUDA(cudaMemcpyAsync(ctx->d_status + 1, &iterations, sizeof(uint32_t),
+                             cudaMemcpyHostToDevice, ctx->stream));
+    SPC_CUDA(cudaStreamSynchronize(ctx->stream));
+    return SPC_OK;
+}
+
 spc_status spc_context_set_stream(spc_context* ctx, void* stream) {
     if (!ctx) return SPC_ERR_INVALID_ARG;
     SPC_CUDA(cudaStreamSynchronize(ctx->stream));

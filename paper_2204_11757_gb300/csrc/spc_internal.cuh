@@ -14,7 +14,7 @@
 namespace spc {
 
 constexpr int kThreads = 256;          // default block size
-constexpr uint32_t kSpinLimit = 1u << 22;  // bound for every device-side retry loop
+constexpr uint32_t kSpinLimit = 1u << 22;  // default bound of every device-side retry loop
 
 // bits of the device status word
 enum : uint32_t {
@@ -259,6 +259,14 @@ inline int grid_for(int64_t items, int threads, int max_blocks) {
 // and its writes are visible.  This hides the launch gap between dependent kernels (many of a
 // coarsening level's kernels are small).  Launched without the attribute, pdl_wait() returns
 // at once.
+// The device status block of a context: word 0 is the status word (DEV_* bits), word 1 the
+// bound of every device-side wait or retry loop (0: kSpinLimit), set by
+// spc_context_set_wait_limit.  A wait that reaches the bound gives up and sets DEV_TIMEOUT.
+__device__ __forceinline__ uint32_t spin_limit(const uint32_t* status) {
+    const uint32_t v = status[1];
+    return v ? v : kSpinLimit;
+}
+
 __device__ __forceinline__ void pdl_wait() {
 #if defined(__CUDA_ARCH__) && __CUDA_ARCH__ >= 900
     asm volatile("griddepcontrol.wait;" ::: "memory");

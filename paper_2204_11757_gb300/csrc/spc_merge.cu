@@ -21,7 +21,8 @@
 //      n_b - target_b of each graph are united.
 //   3. Relabel: root = smallest member; flag roots, exclusive scan, id = scan[root] (Definition
 //      1's super-nodes, numbered by smallest member).
-// Every retry loop is bounded (kSpinLimit); giving up sets DEV_TIMEOUT in the status word.
+// Every retry loop is bounded (spin_limit: kSpinLimit unless the context lowered it); giving up
+// sets DEV_TIMEOUT in the status word.
 #include <atomic>
 
 #include "spc_scan.cuh"
@@ -35,9 +36,11 @@ __device__ __forceinline__ int32_t ld_parent(const int32_t* parent, int32_t x) {
 }
 
 // find with path halving; parent pointers only ever move to an ancestor, so racing writes are
-// benign.  Bounded: the chain of a forest over n nodes is shorter than kSpinLimit.
+// benign.  Bounded: the chain of a forest over n nodes is shorter than kSpinLimit.  Giving up
+// returns a node of the set (an ancestor of x): every index stays in range.
 __device__ __forceinline__ int32_t uf_find(int32_t* parent, int32_t x, uint32_t* status) {
-    for (uint32_t it = 0; it < kSpinLimit; ++it) {
+    const uint32_t lim = spin_limit(status);
+    for (uint32_t it = 0; it < lim; ++it) {
         int32_t p = ld_parent(parent, x);
         if (p == x) return x;
         int32_t gp = ld_parent(parent, p);
@@ -87,7 +90,8 @@ __device__ __forceinline__ void warp_atomic_min_i32(int32_t* a, int32_t idx, int
 // root is always the smallest node id of its set.  Returns true if the sets were distinct.
 __device__ __forceinline__ bool uf_unite(int32_t* parent, int32_t a, int32_t b,
                                          uint32_t* status) {
-    for (uint32_t it = 0; it < kSpinLimit; ++it) {
+    const uint32_t lim = spin_limit(status);
+    for (uint32_t it = 0; it < lim; ++it) {
         a = uf_find(parent, a, status);
         b = uf_find(parent, b, status);
         if (a == b) return false;

@@ -120,7 +120,7 @@ __global__ void __launch_bounds__(ST) k_scan_fused(Ld ld, St st, int64_t n,
                 while (__any_sync(0xffffffffu, (w >> 62) == 0ull)) {
                     if ((w >> 62) == 0ull)
                         w = *reinterpret_cast<volatile unsigned long long*>(status + idx);
-                    if (++spins > kSpinLimit) {
+                    if (++spins > spin_limit(err)) {
                         if (lane == 0) atomicOr(err, DEV_TIMEOUT);
                         w = kScanInc;  // give up; the call reports the timeout
                     }

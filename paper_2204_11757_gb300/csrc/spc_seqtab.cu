@@ -380,8 +380,11 @@ k_fs_windows(int64_t nseq, const int64_t* __restrict__ len, const int64_t* __res
         const long long* C = cu + loff[q];
         const long long c0 = C[0];
         int64_t kmin = 0, kmax = L;  // steps k in [kmin, kmax]; empty when kmin > kmax
+        // Higham's gamma_L = L u / (1 - L u) bounds every prefix (|s_k - A_k| <= gamma A_k) while
+        // L u < 1; beyond that (binary32 sums of more than 2^24 / 5 terms) it bounds nothing and
+        // every window is the whole sequence
         const double g = (double)L * (sizeof(F) == 8 ? 0x1p-53 : 0x1p-24);
-        const double gam = g / (1.0 - g);
+        const double gam = g < 0.2 ? g / (1.0 - g) : 1.0;
         if (gam <= 0.25) {
             constexpr int kBias = FB<F>::kBiasM - FB<F>::kMant;
             const int E2 = eblo[q] + e - kBias - gexp[q];  // binade [2^E2, 2^(E2+1)) in units

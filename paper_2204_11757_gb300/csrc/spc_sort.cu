@@ -285,7 +285,7 @@ __global__ void __launch_bounds__(OT, 2) k_os_pass(const K* __restrict__ kin,
             uint32_t spins = 0;  // predecessor not published yet: wait, bounded
             while ((*reinterpret_cast<volatile uint32_t*>(status + t * RADIX + d) &
                     (kFlagAgg | kFlagInc)) == 0u) {
-                if (++spins > kSpinLimit) { atomicOr(err, DEV_TIMEOUT); t = -1; break; }
+                if (++spins > spin_limit(err)) { atomicOr(err, DEV_TIMEOUT); t = -1; break; }
             }
         }
         atomicExch(my, kFlagInc | (prefix + tcount));

@@ -67,6 +67,7 @@ SIGNATURES = {
     "spc_context_create": (ctypes.c_int, [ctypes.POINTER(P), ctypes.POINTER(spc_allocator), P]),
     "spc_context_destroy": (None, [P]),
     "spc_context_set_stream": (ctypes.c_int, [P, P]),
+    "spc_context_set_wait_limit": (ctypes.c_int, [P, ctypes.c_uint32]),
     "spc_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "spc_default_options": (spc_options, []),
     "spc_coarsen": (ctypes.c_int, [P, ctypes.POINTER(spc_csr), I64,
