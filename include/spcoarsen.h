@@ -99,7 +99,9 @@ typedef struct {
     int32_t use_graph;  /* 1: capture the schedule in a CUDA graph and replay it on later calls
                            with the same shapes; 0: launch kernel by kernel                   */
     int32_t schedule;   /* score-kernel schedule: 0 auto (autotuned), 1 edge tiles
-                           (one thread per edge), 2 warp per row                              */
+                           (one thread per edge), 2 warp per row, 3 staged rows (a warp
+                           moves the rows of 32 edges into shared memory, then one thread
+                           per edge); every schedule gives the same bits                    */
     int32_t self_mass;  /* multilevel reading (levels > 1 only; the first level is the same
                            either way).  1 (default): a super-node keeps the weight inside it.
                            Each level after the first scores its input graph with the diagonal
@@ -206,6 +208,33 @@ SPC_API spc_status spc_coarsen_batched(spc_context* ctx, const spc_csr* g, const
 SPC_API int32_t spc_level_count(const spc_context* ctx);
 SPC_API spc_status spc_get_level(const spc_context* ctx, int32_t level, spc_level* out);
 
+/* The result of the last spc_coarsen / spc_coarsen_batched call in buffers the caller owns:
+ * unlike the retained levels (spc_get_level), they outlive later calls on the context, so a
+ * caller can hold several coarsenings at once (a pooling layer keeps one per graph).  Every
+ * buffer is device memory allocated through the context's allocator (the spc_allocator given
+ * to spc_context_create, else cudaMalloc); release them with spc_result_free (or that
+ * allocator's free). */
+typedef struct {
+    int64_t n, m;        /* nodes and undirected edges of the caller's graph              */
+    int64_t n_c, m_c;    /* super-nodes and coarse undirected edges of the last level      */
+    spc_dtype wtype;     /* weight type                                                    */
+    int32_t* lift;       /* [n]       super-node of every node (as lift_out)                */
+    int32_t* emap;       /* [m]       coarse edge of every fine edge, -1 inside a super-node */
+    int64_t* rowptr_c;   /* [n_c + 1] the coarse graph G_c (symmetric CSR, no diagonal)     */
+    int32_t* col_c;      /* [2 m_c]                                                         */
+    void* w_c;           /* [2 m_c]   of type wtype                                         */
+    void* mass;          /* [n_c]     weight of the caller's edges inside every super-node as
+                            the self-mass reading carries it (int64 for SPC_I32); NULL when
+                            the call did not use that reading                             */
+} spc_result;
+
+/* Fill *out with the last coarsening's result (see spc_result).  SPC_ERR_INVALID_ARG when the
+ * context holds no coarsening result; SPC_ERR_OOM (nothing kept) when an allocation fails. */
+SPC_API spc_status spc_take_result(spc_context* ctx, spc_result* out);
+
+/* Release the buffers of a result taken from this context and zero *r.  NULL is accepted. */
+SPC_API void spc_result_free(spc_context* ctx, spc_result* r);
+
 /* Copy `bytes` from src to dst on the context's stream and wait for it.  Either side may be
  * host or device memory; used to read retained results into caller buffers. */
 SPC_API spc_status spc_copy(spc_context* ctx, void* dst, const void* src, size_t bytes);
@@ -264,7 +293,8 @@ SPC_API spc_status spc_compose_emap(spc_context* ctx, int32_t* emap_out);
  *               spc_sort_fitness
  *   stream      cudaStream_t the work is enqueued on (NULL: legacy default stream)
  * Returns once the work is enqueued; the result is ready when the stream reaches it.  Host
- * pointers are rejected with SPC_ERR_INVALID_ARG (staging them would need memory).  The first
+ * pointers, and device memory of a GPU other than the current one, are rejected with
+ * SPC_ERR_INVALID_ARG (staging them would need memory).  The first
  * call on a device looks up the array's device address (cudaGetSymbolAddress) for that device;
  * make it before any stream capture.  All calls share the array: calls that may execute
  * concurrently on the GPU race and must be ordered by the caller. */

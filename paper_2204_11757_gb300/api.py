@@ -243,6 +243,13 @@ class Context:
                                                   _ptr(gpc)), "spc_coarsen_batched")
         return lift, gpc, st
 
+    def take_result(self) -> "Result":
+        """The last coarsening's result in buffers the caller owns (they outlive later calls
+        on this context); see Result."""
+        r = N.spc_result()
+        N.check(self.lib.spc_take_result(self._handle, ctypes.byref(r)), "spc_take_result")
+        return Result(self, r)
+
     # ---- retained results ------------------------------------------------------------------
     def level_count(self) -> int:
         return int(self.lib.spc_level_count(self._handle))
@@ -349,6 +356,40 @@ class Context:
     def last_call_replayed(self) -> bool:
         """Whether the last coarsening call replayed the previous identical call's graph."""
         return bool(self.lib.spc_last_call_replayed(self._handle))
+
+
+class Result:
+    """A coarsening result owned by the caller (spc_take_result): the lift, the composed edge
+    map, the coarse graph and the carried mass, in device buffers that stay valid until free()
+    (or garbage collection) whatever the context computes meanwhile."""
+
+    def __init__(self, context: Context, r):
+        self.context, self._r = context, r
+        self.n, self.m, self.n_c, self.m_c = int(r.n), int(r.m), int(r.n_c), int(r.m_c)
+        self.wtype = _TD[r.wtype]
+
+    def tensors(self) -> dict:
+        """Copies of every buffer as tensors on the context's device."""
+        r, cp = self._r, self.context._copy_from
+        acc = torch.int64 if self.wtype == torch.int32 else self.wtype
+        out = {"lift": cp(r.lift, self.n, torch.int32), "emap": cp(r.emap, self.m, torch.int32),
+               "rowptr_c": cp(r.rowptr_c, self.n_c + 1, torch.int64),
+               "col_c": cp(r.col_c, 2 * self.m_c, torch.int32),
+               "w_c": cp(r.w_c, 2 * self.m_c, self.wtype)}
+        out["mass"] = cp(r.mass, self.n_c, acc) if r.mass else None
+        return out
+
+    def free(self):
+        if self._r is not None and getattr(self.context, "_handle", None) is not None \
+                and self.context._handle.value:
+            self.context.lib.spc_result_free(self.context._handle, ctypes.byref(self._r))
+        self._r = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
 
 
 @dataclasses.dataclass

@@ -514,6 +514,24 @@ static spc_status stage_graph(spc_context* ctx, const spc_csr* g, GraphView& v) 
     return SPC_OK;
 }
 
+// memory handed to the caller (spc_take_result): not recorded among the context's blocks
+static void* alloc_owned(spc_context* ctx, size_t bytes) {
+    if (bytes == 0) bytes = 256;
+    void* p = nullptr;
+    if (ctx->has_allocator) return ctx->allocator.alloc(ctx->allocator.ctx, bytes);
+    if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return nullptr;
+    }
+    return p;
+}
+
+static void free_owned(spc_context* ctx, void* p) {
+    if (!p) return;
+    if (ctx->has_allocator) ctx->allocator.free(ctx->allocator.ctx, p);
+    else cudaFree(p);
+}
+
 static spc_status begin_call(spc_context* ctx) {
     if (!ctx) return SPC_ERR_INVALID_ARG;
     SPC_CUDA(cudaSetDevice(ctx->device));
@@ -1060,6 +1078,7 @@ spc_status spc_contract(spc_context* ctx, const spc_csr* g, const int32_t* lift,
                    v.n, lv.lift.as<int32_t>(), n_c, ctx->d_status);
     }
     SPC_TRY(sync_status(ctx));  // an out-of-range id must not reach the contraction
+    ctx->has_result = false;
     SPC_TRY(run_contract(ctx, v, lv.lift.as<int32_t>(), n_c, lv));
     lv.n = v.n;
     lv.m = v.m;
@@ -1088,7 +1107,9 @@ spc_status spc_coarsen(spc_context* ctx, const spc_csr* g, int64_t n_c, const sp
     S.n_c = n_c;
     int64_t ncf = 0;
     int32_t warn = 0;
+    ctx->has_result = false;
     SPC_TRY(drive(ctx, v, S, o.use_graph != 0, &ncf, &warn));
+    ctx->has_result = true;
     SPC_TRY(copy_out(ctx, lift_out, ctx->work.lift_final.p, (size_t)v.n * 4));
     SPC_CUDA(cudaStreamSynchronize(ctx->stream));
     if (n_c_actual) *n_c_actual = ncf;
@@ -1123,13 +1144,76 @@ spc_status spc_coarsen_batched(spc_context* ctx, const spc_csr* g, const int64_t
     S.ratio = ratio;
     int64_t ncf = 0;
     int32_t warn = 0;
+    ctx->has_result = false;
     SPC_TRY(drive(ctx, v, S, o.use_graph != 0, &ncf, &warn));
+    ctx->has_result = true;
     SPC_TRY(copy_out(ctx, lift_out, ctx->work.lift_final.p, (size_t)v.n * 4));
     if (graph_ptr_c_out)
         SPC_TRY(copy_out(ctx, graph_ptr_c_out, ctx->levels[L - 1].graph_ptr_c.p,
                          ((size_t)B + 1) * 8));
     SPC_CUDA(cudaStreamSynchronize(ctx->stream));
     return warn ? SPC_WARN_TARGET_NOT_REACHED : SPC_OK;
+}
+
+void spc_result_free(spc_context* ctx, spc_result* r) {
+    if (!ctx || !r) return;
+    cudaStreamSynchronize(ctx->stream);
+    void* ps[6] = {r->lift, r->emap, r->rowptr_c, r->col_c, r->w_c, r->mass};
+    for (void* p : ps) free_owned(ctx, p);
+    *r = spc_result{};
+}
+
+spc_status spc_take_result(spc_context* ctx, spc_result* out) {
+    SPC_TRY(begin_call(ctx));
+    if (!out) return SPC_ERR_INVALID_ARG;
+    *out = spc_result{};
+    if (!ctx->has_result || ctx->n_levels < 1) return SPC_ERR_INVALID_ARG;
+    const LevelBufs& l0 = ctx->levels[0];
+    const LevelBufs& lz = ctx->levels[ctx->n_levels - 1];
+    spc_result r{};
+    r.n = l0.n;
+    r.m = l0.m;
+    r.n_c = lz.n_c;
+    r.m_c = lz.m_c;
+    r.wtype = lz.wtype;
+    const size_t ws = wsize(r.wtype), acc = accsize(r.wtype);
+    r.lift = static_cast<int32_t*>(alloc_owned(ctx, (size_t)r.n * 4));
+    r.emap = static_cast<int32_t*>(alloc_owned(ctx, (size_t)r.m * 4));
+    r.rowptr_c = static_cast<int64_t*>(alloc_owned(ctx, (size_t)(r.n_c + 1) * 8));
+    r.col_c = static_cast<int32_t*>(alloc_owned(ctx, (size_t)r.m_c * 2 * 4));
+    r.w_c = alloc_owned(ctx, (size_t)r.m_c * 2 * ws);
+    if (lz.mass_ptr) r.mass = alloc_owned(ctx, (size_t)r.n_c * acc);
+    if (!r.lift || !r.emap || !r.rowptr_c || !r.col_c || !r.w_c || (lz.mass_ptr && !r.mass)) {
+        spc_result_free(ctx, &r);
+        return SPC_ERR_OOM;
+    }
+    spc_status st = SPC_OK;
+    auto cp = [&](void* dst, const void* src, size_t bytes) {
+        if (st == SPC_OK && bytes &&
+            cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, ctx->stream) != cudaSuccess)
+            st = SPC_ERR_CUDA;
+    };
+    cp(r.lift, ctx->work.lift_final.p, (size_t)r.n * 4);
+    cp(r.emap, l0.emap.p, (size_t)r.m * 4);
+    cp(r.rowptr_c, lz.rowptr_c.p, (size_t)(r.n_c + 1) * 8);
+    cp(r.col_c, lz.col_c.p, (size_t)r.m_c * 2 * 4);
+    cp(r.w_c, lz.w_c.p, (size_t)r.m_c * 2 * ws);
+    if (r.mass) cp(r.mass, lz.mass_ptr, (size_t)r.n_c * acc);
+    for (int l = 1; l < ctx->n_levels && st == SPC_OK && r.m > 0; ++l) {
+        st = [&]() -> spc_status {
+            SPC_LAUNCH(ctx, k_compose_emap, grid_for(r.m, kThreads, ctx->num_sms * 8), kThreads, 0,
+                       r.m, ctx->levels[l].emap.as<int32_t>(), r.emap);
+            return SPC_OK;
+        }();
+    }
+    if (st == SPC_OK && cudaStreamSynchronize(ctx->stream) != cudaSuccess) st = SPC_ERR_CUDA;
+    if (st != SPC_OK) {
+        (void)cudaGetLastError();
+        spc_result_free(ctx, &r);
+        return st;
+    }
+    *out = r;
+    return SPC_OK;
 }
 
 int32_t spc_level_count(const spc_context* ctx) { return ctx ? ctx->n_levels : 0; }
@@ -1231,8 +1315,8 @@ spc_status spc_time_kernel(spc_context* ctx, const char* kernel_substr) {
     t.on = kernel_substr && kernel_substr[0];
     t.substr = t.on ? kernel_substr : "";
     if (t.on) {
-        if (!ctx->d_ops) SPC_CUDA(cudaMalloc(&ctx->d_ops, 4 * sizeof(unsigned long long)));
-        SPC_CUDA(cudaMemset(ctx->d_ops, 0, 4 * sizeof(unsigned long long)));
+        if (!ctx->d_ops) SPC_CUDA(cudaMalloc(&ctx->d_ops, 6 * sizeof(unsigned long long)));
+        SPC_CUDA(cudaMemset(ctx->d_ops, 0, 6 * sizeof(unsigned long long)));
     }
     return SPC_OK;
 }
@@ -1262,7 +1346,7 @@ spc_status spc_kernel_time(spc_context* ctx, int64_t* launches, double* total_ms
 spc_status spc_kernel_profile(spc_context* ctx, char* buf, size_t len) {
     if (!ctx || (!buf && len)) return SPC_ERR_INVALID_ARG;
     SPC_TRY(drain_timer(ctx));
-    unsigned long long ops[4] = {0, 0, 0, 0};
+    unsigned long long ops[6] = {0, 0, 0, 0, 0, 0};
     if (ctx->d_ops) SPC_CUDA(cudaMemcpy(ops, ctx->d_ops, sizeof(ops), cudaMemcpyDeviceToHost));
     std::string out;
     char line[512];
@@ -1270,6 +1354,7 @@ spc_status spc_kernel_profile(spc_context* ctx, char* buf, size_t len) {
         unsigned long long fp = 0;
         if (pk.name.find("k_score_edges") != std::string::npos) fp = ops[0] + ops[1];
         if (pk.name.find("k_score_warp_row") != std::string::npos) fp = ops[2] + ops[3];
+        if (pk.name.find("k_score_staged") != std::string::npos) fp = ops[4] + ops[5];
         snprintf(line, sizeof(line), "%s\t%lld\t%.6f\t%.0f\t%llu\n", pk.name.c_str(),
                  (long long)pk.launches, pk.ms, pk.bytes, fp);
         out += line;

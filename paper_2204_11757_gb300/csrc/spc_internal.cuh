@@ -188,14 +188,15 @@ struct spc_context {
     std::vector<spc::LevelBufs> levels;
     int32_t n_levels = 0;
     int32_t replayed_last = 0;       // the last coarsening call was a graph replay
+    bool has_result = false;         // lift_final and the levels hold a coarsening result
     spc::Timer timer;
     int64_t launches = 0;
     spc::Replay replay;
     // score-schedule autotuner: (dtype, log2 mean row length, log2 m) -> 1 edge tiles, 2 warp/row
     std::vector<std::pair<int64_t, int>> tuned;
-    cudaEvent_t tune_ev[3] = {nullptr, nullptr, nullptr};
+    cudaEvent_t tune_ev[4] = {nullptr, nullptr, nullptr, nullptr};
     // arithmetic counts of the timed score launches: [0..1] edge tiles (adds, subtractions),
-    // [2..3] warp per row
+    // [2..3] warp per row, [4..5] staged rows
     unsigned long long* d_ops = nullptr;
     // second stream for independent work inside a level (parallel branches of a captured graph)
     cudaStream_t side_stream = nullptr;

@@ -12,6 +12,7 @@
 // (__dadd_rn / __fadd_rn, no FMA), and p = w / d is one IEEE division per stored entry, so
 // the results are the same bits on every run and every schedule.
 #include <algorithm>
+#include <atomic>
 #include <memory>
 
 #include "spc_seqsum.cuh"
@@ -545,6 +546,130 @@ k_score_warp_row(int64_t n, const int64_t* __restrict__ rowptr, const int32_t* _
     count_ops(ops, n_add, n_sub);
 }
 
+
+// S3, staged schedule: a warp takes 32 consecutive edges (one lane each) and first moves their
+// rows into shared memory with coalesced bulk loads -- the rows a of the tile, which are one
+// contiguous slice of the CSR, and the 32 rows b, each read by the whole warp with its loads
+// for eight rows in flight together -- then every lane walks its edge's union from shared
+// memory with the same uniform step and order as k_score_edges (the same bits).  Walking rows
+// in place reads one element per step from wherever row b lives; on graphs whose rows b are
+// scattered (random node order) the lines are evicted between the steps and each step reads a
+// sector from DRAM again.  Rows b longer than kStageCap entries, or a tile whose rows a exceed
+// kStageA entries, are walked in place.
+constexpr int kStageCap = 32;
+constexpr int kStageStr = kStageCap + 1;  // padded: lanes of one step hit different banks
+constexpr int kStageA = 256;
+constexpr int kStageWarps = 4;
+constexpr int kStageRegion = kStageA + 32 * kStageStr;  // elements per warp
+
+template <class PT>
+constexpr size_t stage_smem_bytes() {
+    return (size_t)kStageWarps * kStageRegion * (sizeof(PT) + sizeof(int32_t));
+}
+
+template <class PT, class KT>
+__global__ void __launch_bounds__(kStageWarps * 32)
+k_score_staged(int64_t m, const int32_t* __restrict__ eu, const int32_t* __restrict__ ev,
+               const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+               const PT* __restrict__ p, KT* __restrict__ score, const void* __restrict__ w,
+               const void* __restrict__ w_und, int wsize, int validate, uint32_t* status,
+               unsigned long long* __restrict__ ops) {
+    spc::pdl_wait();
+    if (*status) return;
+    extern __shared__ __align__(16) unsigned char stage_raw[];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    PT* const sa_p = reinterpret_cast<PT*>(stage_raw) + (size_t)wib * kStageRegion;
+    PT* const sb_p = sa_p + kStageA;
+    int32_t* const sa_c = reinterpret_cast<int32_t*>(reinterpret_cast<PT*>(stage_raw) +
+                                                     (size_t)kStageWarps * kStageRegion) +
+                          (size_t)wib * kStageRegion;
+    int32_t* const sb_c = sa_c + kStageA;
+    constexpr int32_t kEnd = 0x7fffffff;
+    uint32_t n_add = 0, n_sub = 0;
+    bool asym = false;
+    const int64_t step_e = (int64_t)gridDim.x * kStageWarps * 32;
+    for (int64_t e0 = ((int64_t)blockIdx.x * kStageWarps + wib) * 32; e0 < m; e0 += step_e) {
+        const int64_t e = e0 + lane;
+        const bool act = e < m;
+        int32_t a = 0;
+        int64_t ra = 0, da = 0, rb = 0, db = 0;
+        if (act) {
+            a = eu[e];
+            const int32_t b = ev[e];
+            ra = rowptr[a];
+            da = rowptr[a + 1] - ra;
+            rb = rowptr[b];
+            db = rowptr[b + 1] - rb;
+        }
+        // the tile's rows a: entries [rowptr[a of lane 0], rowptr[a of the last lane + 1])
+        const int lastl = (int)((m - e0 < 32 ? m - e0 : 32) - 1);
+        const int64_t abase = __shfl_sync(0xffffffffu, ra, 0);
+        const int64_t alen = __shfl_sync(0xffffffffu, ra + da, lastl) - abase;
+        const bool a_staged = alen <= kStageA;
+        if (a_staged) {
+            for (int64_t i = lane; i < alen; i += 32) {
+                sa_c[i] = col[abase + i];
+                sa_p[i] = p[abase + i];
+            }
+        }
+        // the 32 rows b, eight at a time
+#pragma unroll
+        for (int k0 = 0; k0 < 32; k0 += 8) {
+            int32_t cv[8];
+            PT pv[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const int64_t rbk = __shfl_sync(0xffffffffu, rb, k0 + q);
+                const int64_t dbk = __shfl_sync(0xffffffffu, db, k0 + q);
+                const bool ld = dbk <= kStageCap && lane < dbk;
+                cv[q] = ld ? col[rbk + lane] : 0;
+                pv[q] = ld ? p[rbk + lane] : PT(0);
+            }
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                sb_c[(k0 + q) * kStageStr + lane] = cv[q];
+                sb_p[(k0 + q) * kStageStr + lane] = pv[q];
+            }
+        }
+        __syncwarp();
+        if (act) {
+            if (da > kLongRow || db > kLongRow) {  // hub edge: k_score_hub
+                if (validate && da <= kLongRow)
+                    asym = asym || !has_mirror(col, w, wsize, rb, rb + db, a,
+                                               weight_bits(w_und, wsize, e));
+            } else {
+                const int32_t* Ac = a_staged ? sa_c + (ra - abase) : col + ra;
+                const PT* Ap = a_staged ? sa_p + (ra - abase) : p + ra;
+                const int32_t* Bc = db <= kStageCap ? sb_c + lane * kStageStr : col + rb;
+                const PT* Bp = db <= kStageCap ? sb_p + lane * kStageStr : p + rb;
+                int64_t i = 0, j = 0;
+                int32_t ca = da > 0 ? Ac[0] : kEnd;
+                int32_t cb = db > 0 ? Bc[0] : kEnd;
+                PT s = PT(0);
+                bool mirror = false;
+                // the uniform step of k_score_edges: t = |pa - pb| with a missing side read as 0
+                while (ca != kEnd || cb != kEnd) {
+                    const bool ta = ca <= cb, tb = cb <= ca;
+                    if (validate && tb && cb == a)
+                        mirror = weight_bits(w, wsize, rb + j) == weight_bits(w_und, wsize, e);
+                    const PT pa = ta ? Ap[i] : PT(0);
+                    const PT pb = tb ? Bp[j] : PT(0);
+                    s = p_add(s, p_absdiff(pa, pb));
+                    ++n_add;
+                    n_sub += (ta && tb) ? 1u : 0u;
+                    if (ta) { ++i; ca = i < da ? Ac[i] : kEnd; }
+                    if (tb) { ++j; cb = j < db ? Bc[j] : kEnd; }
+                }
+                score[e] = key_bits(s);
+                asym = asym || (validate && !mirror);
+            }
+        }
+        __syncwarp();  // the next tile overwrites the stage
+    }
+    if (asym) atomicOr(status, DEV_NOT_SYMMETRIC);
+    count_ops(ops, n_add, n_sub);
+}
+
 // ---- hub edges ----------------------------------------------------------------------------------
 // An edge with an end point of more than kLongRow entries is scored from the larger row H (its
 // "hub"; ties go to the smaller id).  The score is the same left-to-right sum over the union of
@@ -901,8 +1026,29 @@ static spc_status launch_score_edges(spc_context* ctx, int64_t m, const GraphVie
     return SPC_OK;
 }
 
+template <class P, class Key>
+static spc_status launch_score_staged(spc_context* ctx, int64_t m, const GraphView& g, Work& W,
+                                      void* score, int wsize, int vflag, uint32_t* status,
+                                      bool count) {
+    constexpr size_t smem = stage_smem_bytes<P>();
+    static std::atomic<unsigned long long> attr_devs{0};  // devices already set up
+    const unsigned long long bit = 1ull << (ctx->device & 63);
+    if (!(attr_devs.load() & bit)) {
+        SPC_CUDA(cudaFuncSetAttribute(k_score_staged<P, Key>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        attr_devs.fetch_or(bit);
+    }
+    const int64_t tiles = (m + 31) / 32;
+    const int grid = grid_for(tiles, kStageWarps, ctx->num_sms * (sizeof(P) == 8 ? 3 : 5));
+    SPC_LAUNCH(ctx, (k_score_staged<P, Key>), grid, kStageWarps * 32, smem, m,
+               W.eu.as<int32_t>(), W.ev.as<int32_t>(), g.rowptr, g.col, W.p.as<P>(),
+               static_cast<Key*>(score), g.w, W.w_und.p, wsize, vflag, status,
+               count ? op_counter(ctx, "(k_score_staged<P, Key>)", 4) : nullptr);
+    return SPC_OK;
+}
+
 static int pick_default_schedule(int64_t n, int64_t nnz) {
-    return (n > 0 && nnz / n > 48) ? 2 : 1;  // long rows favour a warp per row
+    return (n > 0 && nnz / n > 48) ? 2 : 3;  // long rows favour a warp per row
 }
 
 template <class WT>
@@ -1011,11 +1157,16 @@ static spc_status score_typed(spc_context* ctx, GraphView& g, bool validate, voi
                        W.p.as<P>(), W.up_ptr.as<int32_t>(), W.first_up.as<int32_t>(),
                        static_cast<Key*>(score), g.w, W.w_und.p, wsize, vflag, status, nullptr);
             SPC_CUDA(cudaEventRecord(ctx->tune_ev[2], ctx->stream));
-            SPC_CUDA(cudaEventSynchronize(ctx->tune_ev[2]));
-            float t_edges = 0.f, t_rows = 0.f;
-            SPC_CUDA(cudaEventElapsedTime(&t_edges, ctx->tune_ev[0], ctx->tune_ev[1]));
-            SPC_CUDA(cudaEventElapsedTime(&t_rows, ctx->tune_ev[1], ctx->tune_ev[2]));
-            schedule = t_rows < t_edges ? 2 : 1;
+            SPC_TRY((launch_score_staged<P, Key>(ctx, m, g, W, score, wsize, vflag, status,
+                                                 false)));
+            SPC_CUDA(cudaEventRecord(ctx->tune_ev[3], ctx->stream));
+            SPC_CUDA(cudaEventSynchronize(ctx->tune_ev[3]));
+            float t[3] = {0.f, 0.f, 0.f};
+            for (int k = 0; k < 3; ++k)
+                SPC_CUDA(cudaEventElapsedTime(&t[k], ctx->tune_ev[k], ctx->tune_ev[k + 1]));
+            schedule = 1;
+            if (t[1] < t[schedule - 1]) schedule = 2;
+            if (t[2] < t[schedule - 1]) schedule = 3;
             ctx->tuned.push_back({tkey, schedule});
         }
         if (schedule == 0) schedule = pick_default_schedule(n, nnz);
@@ -1049,7 +1200,10 @@ static spc_status score_typed(spc_context* ctx, GraphView& g, bool validate, voi
         }
         side->leave();
     }
-    if (schedule == 2) {
+    if (schedule == 3) {
+        note_bytes(ctx, score_bytes);
+        SPC_TRY((launch_score_staged<P, Key>(ctx, m, g, W, score, wsize, vflag, status, true)));
+    } else if (schedule == 2) {
         const int warps_per_block = kThreads / 32;
         note_bytes(ctx, score_bytes);
         const int gw = grid_for(n, warps_per_block, maxb);

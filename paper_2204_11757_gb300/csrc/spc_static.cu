@@ -60,13 +60,17 @@ spc_status static_scratch(void** out) {
     return SPC_OK;
 }
 
+// device (or managed) memory that the current device's kernels can read: memory of another
+// GPU is refused, since the kernels would read it without peer access
 bool on_device(const void* p) {
     cudaPointerAttributes a;
-    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    int dev = -1;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess || cudaGetDevice(&dev) != cudaSuccess) {
         (void)cudaGetLastError();
         return false;
     }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+    if (a.type == cudaMemoryTypeManaged) return true;
+    return a.type == cudaMemoryTypeDevice && a.device == dev;
 }
 
 // keys = score bits (uint32 scores widened), values = edge ids

@@ -59,6 +59,13 @@ class spc_level(ctypes.Structure):
                 ("mass", ctypes.c_void_p)]
 
 
+class spc_result(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("m", ctypes.c_int64), ("n_c", ctypes.c_int64),
+                ("m_c", ctypes.c_int64), ("wtype", ctypes.c_int), ("lift", ctypes.c_void_p),
+                ("emap", ctypes.c_void_p), ("rowptr_c", ctypes.c_void_p),
+                ("col_c", ctypes.c_void_p), ("w_c", ctypes.c_void_p), ("mass", ctypes.c_void_p)]
+
+
 # name -> (restype, argtypes); the full list of include/spcoarsen.h
 P = ctypes.c_void_p
 I64 = ctypes.c_int64
@@ -77,6 +84,8 @@ SIGNATURES = {
     "spc_level_count": (ctypes.c_int32, [P]),
     "spc_get_level": (ctypes.c_int, [P, ctypes.c_int32, ctypes.POINTER(spc_level)]),
     "spc_copy": (ctypes.c_int, [P, P, P, ctypes.c_size_t]),
+    "spc_take_result": (ctypes.c_int, [P, ctypes.POINTER(spc_result)]),
+    "spc_result_free": (None, [P, ctypes.POINTER(spc_result)]),
     "spc_score": (ctypes.c_int, [P, ctypes.POINTER(spc_csr), P, PI64]),
     "spc_sort_fitness": (ctypes.c_int, [P, I64, P, ctypes.c_int, P]),
     "spc_select_merges": (ctypes.c_int, [P, ctypes.POINTER(spc_csr), P, I64, P, P, PI64]),

@@ -62,7 +62,7 @@ def _graph(name):
 # ---- S0-S3 -------------------------------------------------------------------------------------
 
 @pytest.mark.parametrize("gi", range(len(SMALL)))
-@pytest.mark.parametrize("schedule", [1, 2])
+@pytest.mark.parametrize("schedule", [1, 2, 3])
 def test_score_small_bitexact(ctx, gi, schedule):
     g = SMALL[gi]
     api = _api()
@@ -71,19 +71,46 @@ def test_score_small_bitexact(ctx, gi, schedule):
     if schedule == 1:
         f = ctx.score(csr).cpu().numpy()
     else:
-        ctx.coarsen(csr, g.n, levels=1, schedule=2)
+        ctx.coarsen(csr, g.n, levels=1, schedule=schedule)
         f = ctx.level(0).score.cpu().numpy()
     assert f.dtype == ref.dtype
     assert np.array_equal(_bits(f), _bits(ref))
 
 
 @pytest.mark.parametrize("name", MID)
-def test_score_mid_bitexact(ctx, name):
+@pytest.mark.parametrize("schedule", [1, 3])
+def test_score_mid_bitexact(ctx, name, schedule):
     g = _graph(name)
     api = _api()
     ref = O.score(g)
-    f = ctx.score(api.CSR.from_graph(g)).cpu().numpy()
+    csr = api.CSR.from_graph(g)
+    if schedule == 1:
+        f = ctx.score(csr).cpu().numpy()
+    else:
+        ctx.coarsen(csr, g.n, levels=1, schedule=schedule)
+        f = ctx.level(0).score.cpu().numpy()
     assert np.array_equal(_bits(f), _bits(ref))
+
+
+@pytest.mark.parametrize("weight,dt", [("float", np.float32), ("float", np.float64),
+                                       ("int", np.int32)])
+def test_staged_schedule_on_mixed_row_lengths(ctx, weight, dt):
+    """The staged schedule with every kind of row: rows b of up to 32 entries staged, longer
+    ones (up to 256) walked in place, tiles whose rows a exceed the stage walked in place, and
+    hub rows left to the hub kernels -- on a heavy-tailed graph, then on its multilevel
+    coarsening, every score bit-exact with the oracle."""
+    api = _api()
+    g = I.powerlaw_graph(4039, 22, 7, weight, dt)
+    deg = np.diff(g.rowptr)
+    assert deg.max() > 256 and np.any((deg > 32) & (deg <= 256)) and np.any(deg <= 32)
+    csr = api.CSR.from_graph(g)
+    ctx.coarsen(csr, g.n, levels=1, schedule=3)
+    assert np.array_equal(_bits(ctx.level(0).score.cpu().numpy()), _bits(O.score(g)))
+    levels_ref, total_ref = O.coarsen(g, 8, "halving")
+    lift, nca, st = ctx.coarsen(csr, levels_ref[-1].target, levels=len(levels_ref), schedule=3)
+    assert np.array_equal(lift.cpu().numpy(), total_ref)
+    for lv, ref in zip(ctx.levels(), levels_ref):
+        assert np.array_equal(_bits(lv.score.cpu().numpy()), _bits(ref.f))
 
 
 # ---- S4 ------------------------------------------------------------------------------------------
@@ -804,3 +831,36 @@ def test_graph_replay_batched(ctx):
     for bi, (levels_ref, total_ref) in enumerate(res):
         n0, n1 = b.graph_ptr[bi], b.graph_ptr[bi + 1]
         assert np.array_equal(lift[n0:n1] - gpc[bi], total_ref)
+
+
+def test_results_owned_by_the_caller_outlive_later_calls(ctx):
+    """spc_take_result hands over the coarse graph, the composed edge map, the lift and the
+    carried mass in buffers the caller owns: two coarsenings (and a third call in between) are
+    held at once and each still equals its oracle result."""
+    api = _api()
+    cases = [("s2_tri256_f64", 16), ("s4_rgg64k_f32", 8)]
+    held = []
+    for name, ratio in cases:
+        g, cfg = I.config_graph(name)
+        L = int(round(np.log2(ratio)))
+        ctx.coarsen(api.CSR.from_graph(g), g.n // ratio, levels=L)
+        held.append((g, ratio, ctx.take_result()))
+    ctx.coarsen(api.CSR.from_graph(I.cycle_graph(50)), 5, levels=2)  # overwrites the retained levels
+    for g, ratio, res in held:
+        levels_ref, total_ref = O.coarsen(g, ratio, "halving")
+        t = res.tensors()
+        last = levels_ref[-1]
+        assert (res.n, res.m, res.n_c, res.m_c) == (g.n, g.m, last.n_c, last.coarse.m_c)
+        assert np.array_equal(t["lift"].cpu().numpy(), total_ref)
+        assert np.array_equal(t["emap"].cpu().numpy(), O.compose_emaps(levels_ref))
+        assert np.array_equal(t["rowptr_c"].cpu().numpy(), last.coarse.graph.rowptr)
+        assert np.array_equal(t["col_c"].cpu().numpy(), last.coarse.graph.col)
+        assert np.array_equal(_bits(t["w_c"].cpu().numpy()), _bits(last.coarse.graph.w))
+        assert np.array_equal(_bits(t["mass"].cpu().numpy()), _bits(last.mass))
+        res.free()
+    from paper_2204_11757_gb300 import native as N
+    ctx.contract(api.CSR.from_graph(I.cycle_graph(8)),
+                 torch.zeros(8, dtype=torch.int32, device="cuda"), 1)
+    with pytest.raises(N.SpcError) as e:  # a single step leaves no coarsening result
+        ctx.take_result()
+    assert e.value.status == -1
