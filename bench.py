@@ -47,6 +47,10 @@ WORKLOADS = {
                      "FP32 exp(-d^2/r^2), 8 halving levels to n/256"),
     "c4_rgg8m_f32_one": ("c4_rgg8m_f32_one", 1, "random geometric graph, 2^23 points, mean "
                          "degree 12, FP32 exp(-d^2/r^2), one level to n/256"),
+    "c4_rgg8m_f32_reordered": ("c4_rgg8m_f32", 8, "random geometric graph, 2^23 points, mean "
+                               "degree 12, FP32 exp(-d^2/r^2), 8 halving levels to n/256, "
+                               "with the adjacency-reordering option: renumbered by "
+                               "breadth-first distance from node 0 inside the timed step"),
     # reduced case of the same construction, for profiler captures that must stay small
     "p2_tri512_f64": ("p2_tri512_f64", 6, "512x512 jittered triangle mesh (262,144 nodes, "
                       "784,385 edges), FP64 1/edge-length, 6 halving levels to n/64"),
@@ -62,6 +66,8 @@ SAMPLES = {
     "c4_rgg8m_f32": dict(kind="rgg", n=1 << 17, degree=12.0, dtype="float32", seed=4, ratio=256),
     "c4_rgg8m_f32_one": dict(kind="rgg", n=1 << 17, degree=12.0, dtype="float32", seed=4,
                              ratio=256, mode="one"),
+    "c4_rgg8m_f32_reordered": dict(kind="rgg", n=1 << 17, degree=12.0, dtype="float32", seed=4,
+                                   ratio=256, reorder=True),
     "p2_tri512_f64": dict(kind="tri", nx=256, ny=256, jitter=0.3, weight="inv_len",
                           dtype="float64", seed=12, ratio=64),
     "p4_rgg2m_f32": dict(kind="rgg", n=1 << 16, degree=12.0, dtype="float32", seed=4, ratio=256),
@@ -90,7 +96,10 @@ def _oracle_step(g, spec):
     """One oracle coarsening of the sample; returns (fine edges processed, seconds)."""
     from oracle import oracle as O
     t0 = time.perf_counter()
-    levels, _ = O.coarsen(g, spec["ratio"], spec.get("mode", "halving"))
+    if spec.get("reorder"):
+        levels, _, _ = O.coarsen_reordered(g, spec["ratio"], spec.get("mode", "halving"))
+    else:
+        levels, _ = O.coarsen(g, spec["ratio"], spec.get("mode", "halving"))
     dt = time.perf_counter() - t0
     return sum(lv.f.shape[0] for lv in levels), dt
 
@@ -283,7 +292,10 @@ TRAFFIC = {}
 
 HEADLINE = "c4_rgg8m_f32"
 # the other configurations reported in the same line (their own keys, fewer steps)
-EXTRAS = ["c4_rgg8m_f32_one", "c2_tri2048_f64", "c3_tet129_f64", "c5_batch10k_f32"]
+EXTRAS = ["c4_rgg8m_f32_one", "c4_rgg8m_f32_reordered", "c2_tri2048_f64", "c3_tet129_f64",
+          "c5_batch10k_f32"]
+# workloads run with the adjacency-reordering option
+REORDERED = {"c4_rgg8m_f32_reordered"}
 
 
 def _peaks():
@@ -368,8 +380,10 @@ def bench_single(workload, steps, warmup, e2e_on=True, pool=0, want_profile=Fals
     stream = ctx.stream
     lift = torch.empty(g.n, dtype=torch.int32, device=dev)
 
+    reorder = workload in REORDERED
+
     def step():
-        ctx.coarsen(csr, n_c, levels=L, lift_out=lift)
+        ctx.coarsen(csr, n_c, levels=L, lift_out=lift, reorder=reorder)
 
     for _ in range(warmup):
         step()
@@ -427,7 +441,7 @@ def bench_single(workload, steps, warmup, e2e_on=True, pool=0, want_profile=Fals
 
         def e2e_step():
             nonlocal bufs
-            ctx.coarsen(host, n_c, levels=L, lift_out=lift_h)
+            ctx.coarsen(host, n_c, levels=L, lift_out=lift_h, reorder=reorder)
             info = ctx.level_info(ctx.level_count() - 1)
             if bufs is None or bufs[1].shape[0] < 2 * info.m_c:
                 bufs = (torch.empty(info.n_c + 1, dtype=torch.int64).pin_memory(),
@@ -493,6 +507,7 @@ def bench_single(workload, steps, warmup, e2e_on=True, pool=0, want_profile=Fals
                   np.dtype("int32"): "i32"}[g.w.dtype],
         "config": {
             "workload": f"{workload}: {desc}", "n": g.n, "m": g.m, "n_c": n_c, "levels": L,
+            "reorder": reorder,
             "multilevel_reading": "self-mass (the merged node of Theorem 2's proof)",
             "parallelism": "replicas" if ws > 1 else "single GPU",
             "l2": "inputs larger than L2 (%.0f MB resident CSR)" % (

@@ -114,6 +114,14 @@ typedef struct {
                            w_ab + w_ba in its own coordinate and the internal weight in its
                            degree.  0: each level scores the coarse graph G_c as it is, without
                            the internal weight.                                             */
+    int32_t reorder;    /* adjacency reordering (spc_coarsen only; the paper's closing section
+                           suggests it).  1: the graph is first renumbered by (breadth-first hop
+                           distance from node 0, id), nodes that node 0 does not reach last,
+                           and coarsened in that numbering: node x is node perm[x] there
+                           (spc_get_reorder).  lift_out stays in the caller's numbering; the
+                           retained levels and spc_take_result's coarse graph and edge map
+                           refer to the renumbered graph, whose edge ids and whose order of
+                           equal scores differ from the caller's.  0 (default): no reordering. */
 } spc_options;
 
 /* Per-level results retained by the context after spc_coarsen / spc_coarsen_batched /
@@ -173,7 +181,7 @@ SPC_API spc_status spc_context_set_stream(spc_context* ctx, void* stream);
 /* Human-readable name of a status code (static storage). */
 SPC_API const char* spc_status_string(spc_status status);
 
-/* Default options: levels 1, validate 1, use_graph 1, schedule 0, self_mass 1. */
+/* Default options: levels 1, validate 1, use_graph 1, schedule 0, self_mass 1, reorder 0. */
 SPC_API spc_options spc_default_options(void);
 
 /* ---- the full method ---------------------------------------------------------------------- */
@@ -203,6 +211,11 @@ SPC_API spc_status spc_coarsen(spc_context* ctx, const spc_csr* g, int64_t n_c, 
 SPC_API spc_status spc_coarsen_batched(spc_context* ctx, const spc_csr* g, const int64_t* graph_ptr,
                                int64_t B, int64_t ratio, const spc_options* options,
                                int32_t* lift_out, int64_t* graph_ptr_c_out);
+
+/* The renumbering of the last spc_coarsen call made with options->reorder:
+ * perm_out[x] (int32, n entries, device or host) = the id of node x in the renumbered graph.
+ * SPC_ERR_INVALID_ARG when the last coarsening call did not reorder. */
+SPC_API spc_status spc_get_reorder(spc_context* ctx, int32_t* perm_out);
 
 /* Number of levels retained by the last coarsening call, and access to one of them. */
 SPC_API int32_t spc_level_count(const spc_context* ctx);

@@ -357,6 +357,57 @@ def coarsen(g, ratio: int, mode: str, self_mass_degree: bool = True):
     return levels, total
 
 
+def bfs_order(g) -> np.ndarray:
+    """The locality order of the adjacency-reordering option (the paper's closing section
+    suggests graph adjacency reordering; which order is this library's choice): every node's
+    hop distance from node 0 by breadth-first search, the nodes node 0 does not reach after all
+    the others, and the nodes renumbered by (distance, id).  Returns perm, perm[x] = the new id
+    of node x."""
+    from scipy.sparse import csr_matrix
+    from scipy.sparse.csgraph import breadth_first_order
+    n = g.n
+    dist = np.full(n, np.iinfo(np.int64).max, dtype=np.int64)
+    if n > 0:
+        A = csr_matrix((np.ones(g.nnz, dtype=np.int8), g.col, g.rowptr), shape=(n, n))
+        order, pred = breadth_first_order(A, 0, directed=True, return_predecessors=True)
+        # hop distances along the BFS tree, in discovery order (a parent precedes its child)
+        dist[0] = 0
+        for x in order[1:]:
+            dist[x] = dist[pred[x]] + 1
+        reached = dist != np.iinfo(np.int64).max
+        dist[~reached] = (dist[reached].max() + 1) if reached.any() else 0
+    key = np.lexsort((np.arange(n), dist))       # by distance, ties by id
+    perm = np.empty(n, dtype=np.int32)
+    perm[key] = np.arange(n, dtype=np.int32)
+    return perm
+
+
+def permute(g, perm: np.ndarray):
+    """The graph with node x renamed perm[x]: rows in new-id order, columns ascending, every
+    weight carried with its entry; edge ids follow the new upper triangle."""
+    rows = np.repeat(np.arange(g.n, dtype=np.int64), np.diff(g.rowptr))
+    r = perm[rows].astype(np.int64)
+    c = perm[g.col].astype(np.int64)
+    o = np.lexsort((c, r))
+    rowptr = np.zeros(g.n + 1, dtype=np.int64)
+    np.cumsum(np.bincount(r, minlength=g.n), out=rowptr[1:])
+    col = np.ascontiguousarray(c[o].astype(np.int32))
+    w = np.ascontiguousarray(g.w[o])
+    rr = r[o]
+    up = col > rr
+    return _GraphLike(n=g.n, rowptr=rowptr, col=col, w=w, eu=rr[up].astype(np.int32),
+                      ev=col[up], w_und=w[up])
+
+
+def coarsen_reordered(g, ratio: int, mode: str, self_mass_degree: bool = True):
+    """The adjacency-reordering option: the multilevel driver on permute(g, bfs_order(g)).
+    Returns (levels of the renumbered graph, composed lift of the original nodes, perm); the
+    lift of node x is the renumbered graph's lift of node perm[x]."""
+    perm = bfs_order(g)
+    levels, total = coarsen(permute(g, perm), ratio, mode, self_mass_degree)
+    return levels, total[perm], perm
+
+
 def coarsen_batch(batch, ratio: int, mode: str, self_mass_degree: bool = True):
     """Each graph of the batch coarsened on its own (its targets from its own size), results
     concatenated with global ids.  Returns per-graph level lists and the global outputs.

@@ -209,16 +209,17 @@ class Context:
     # ---- the method ----------------------------------------------------------------------
     def coarsen(self, g: CSR, n_c: int, levels: int = 1, validate: bool = True,
                 schedule: int = 0, lift_out: Optional[torch.Tensor] = None,
-                use_graph: bool = True, self_mass: bool = True):
+                use_graph: bool = True, self_mass: bool = True, reorder: bool = False):
         """Coarsen to n_c super-nodes in `levels` levels; returns (lift, n_c_actual, status).
         With use_graph, a call that repeats the previous one on unchanged input replays the
         recorded schedule as one CUDA graph.  self_mass selects the multilevel reading: every
         level after the first scores its input with each super-node's accumulated internal
         weight on the diagonal (the merged node of the proof of Theorem 2); False scores the
-        coarse graph without it."""
+        coarse graph without it.  reorder first renumbers the graph by breadth-first distance
+        from node 0 (see reorder_perm); the lift stays in the caller's numbering."""
         c = self._csr(g)
         opts = N.spc_options(int(levels), int(bool(validate)), int(bool(use_graph)), int(schedule),
-                             int(bool(self_mass)))
+                             int(bool(self_mass)), int(bool(reorder)))
         lift = lift_out if lift_out is not None else torch.empty(g.n, dtype=torch.int32,
                                                                  device=g.col.device)
         nca = ctypes.c_int64(0)
@@ -235,13 +236,20 @@ class Context:
         c = self._csr(g)
         B = int(graph_ptr.shape[0] - 1)
         opts = N.spc_options(int(levels), int(bool(validate)), int(bool(use_graph)), int(schedule),
-                             int(bool(self_mass)))
+                             int(bool(self_mass)), 0)
         lift = torch.empty(g.n, dtype=torch.int32, device=g.col.device)
         gpc = torch.empty(B + 1, dtype=torch.int64, device=g.col.device)
         st = N.check(self.lib.spc_coarsen_batched(self._handle, ctypes.byref(c), _ptr(graph_ptr),
                                                   B, int(ratio), ctypes.byref(opts), _ptr(lift),
                                                   _ptr(gpc)), "spc_coarsen_batched")
         return lift, gpc, st
+
+    def reorder_perm(self, n: int) -> torch.Tensor:
+        """perm[x] = the id of node x in the renumbered graph of the last coarsening made with
+        reorder=True."""
+        out = torch.empty(n, dtype=torch.int32, device=self.device)
+        N.check(self.lib.spc_get_reorder(self._handle, _ptr(out)), "spc_get_reorder")
+        return out
 
     def take_result(self) -> "Result":
         """The last coarsening's result in buffers the caller owns (they outlive later calls

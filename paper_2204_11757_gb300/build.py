@@ -18,7 +18,7 @@ ROOT = os.path.dirname(HERE)
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libspcoarsen.so")
 SOURCES = ["spc_scan.cu", "spc_sort.cu", "spc_score.cu", "spc_merge.cu", "spc_contract.cu",
-           "spc_api.cu", "spc_static.cu", "spc_seqtab.cu", "spc_pool.cu"]
+           "spc_api.cu", "spc_static.cu", "spc_seqtab.cu", "spc_pool.cu", "spc_reorder.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "--fmad=false", "-Xcompiler", "-fPIC",
          "-Xcompiler", "-fvisibility=hidden", "-I" + os.path.join(ROOT, "include")]

@@ -551,6 +551,7 @@ struct Schedule {
     int32_t levels = 1;
     bool validate = true;
     bool self_mass = true;   // the self-mass reading of the multilevel driver
+    bool reorder = false;    // coarsen the graph renumbered by breadth-first distance
     int schedule = 0;
     // single graph
     int64_t n_c = 1;
@@ -578,6 +579,15 @@ static spc_status run_levels(spc_context* ctx, const GraphView& g0, const Schedu
     const int maxb = ctx->num_sms * 8;
     GraphView cur = g0;
     const int64_t* cur_gptr = S.d_graph_ptr;
+    if (S.reorder) {
+        // the caller's graph is checked before anything indexes with it, then renumbered
+        if (S.validate) SPC_TRY(run_score(ctx, cur, true, nullptr, 1));
+        GraphView rg;
+        SPC_TRY(run_reorder(ctx, cur, rg));
+        cur = rg;
+        SPC_TRY(ensure(ctx, ctx->work.ro_lift, ((size_t)g0.n + 1) * 4));
+    }
+    int32_t* lift_comp = S.reorder ? ctx->work.ro_lift.as<int32_t>() : lift_total_dev;
     const void* mass = nullptr;  // accumulated internal weight of cur's nodes (null: all zero)
     *warn = 0;
     ctx->n_levels = 0;
@@ -599,7 +609,8 @@ static spc_status run_levels(spc_context* ctx, const GraphView& g0, const Schedu
             if (t < 1) t = 1;
             sa.target = t;
         }
-        SPC_TRY(run_score(ctx, cur, S.validate && l == 0, lv.score.p, S.schedule));
+        SPC_TRY(run_score(ctx, cur, S.validate && l == 0 && !S.reorder, lv.score.p,
+                          S.schedule));
         lv.n = cur.n;
         lv.m = cur.m;
         int64_t n_c = 0;
@@ -641,12 +652,13 @@ static spc_status run_levels(spc_context* ctx, const GraphView& g0, const Schedu
     for (int l = 0; l < L;) {  // chains of up to kComposeMax lifts, continuing in place
         LiftChain ch{};
         ch.levels = 0;
-        if (l > 0) ch.lift[ch.levels++] = lift_total_dev;
+        if (l > 0) ch.lift[ch.levels++] = lift_comp;
         while (l < L && ch.levels < kComposeMax)
             ch.lift[ch.levels++] = ctx->levels[l++].lift.as<int32_t>();
         SPC_LAUNCH(ctx, k_compose_all, grid_for(g0.n, kThreads, maxb), kThreads, 0, g0.n, ch,
-                   lift_total_dev);
+                   lift_comp);
     }
+    if (S.reorder) SPC_TRY(run_unpermute(ctx, g0.n, lift_comp, lift_total_dev));
     *n_c_final = cur.n;
     if (capturing(ctx)) return SPC_OK;
     SPC_TRY(sync_status(ctx));
@@ -735,7 +747,8 @@ static void drop_graph(Replay& R) {
 static std::vector<int64_t> call_key(const GraphView& v, const Schedule& S) {
     return {(int64_t)(intptr_t)v.rowptr, (int64_t)(intptr_t)v.col, (int64_t)(intptr_t)v.w, v.n,
             v.nnz, (int64_t)v.wtype, S.levels, S.validate ? 1 : 0, S.schedule, S.n_c, S.B,
-            (int64_t)(intptr_t)S.d_graph_ptr, S.ratio, S.self_mass ? 1 : 0};
+            (int64_t)(intptr_t)S.d_graph_ptr, S.ratio, S.self_mass ? 1 : 0,
+            S.reorder ? 1 : 0};
 }
 
 static spc_status capture_graph(spc_context* ctx, const GraphView& v, const Schedule& S,
@@ -908,6 +921,7 @@ spc_options spc_default_options(void) {
     o.use_graph = 1;
     o.schedule = 0;
     o.self_mass = 1;
+    o.reorder = 0;
     return o;
 }
 
@@ -1079,6 +1093,7 @@ spc_status spc_contract(spc_context* ctx, const spc_csr* g, const int32_t* lift,
     }
     SPC_TRY(sync_status(ctx));  // an out-of-range id must not reach the contraction
     ctx->has_result = false;
+    ctx->reorder_n = 0;
     SPC_TRY(run_contract(ctx, v, lv.lift.as<int32_t>(), n_c, lv));
     lv.n = v.n;
     lv.m = v.m;
@@ -1104,12 +1119,15 @@ spc_status spc_coarsen(spc_context* ctx, const spc_csr* g, int64_t n_c, const sp
     S.validate = o.validate != 0;
     S.schedule = o.schedule;
     S.self_mass = o.self_mass != 0;
+    S.reorder = o.reorder != 0;
     S.n_c = n_c;
     int64_t ncf = 0;
     int32_t warn = 0;
     ctx->has_result = false;
+    ctx->reorder_n = 0;
     SPC_TRY(drive(ctx, v, S, o.use_graph != 0, &ncf, &warn));
     ctx->has_result = true;
+    ctx->reorder_n = S.reorder ? v.n : 0;
     SPC_TRY(copy_out(ctx, lift_out, ctx->work.lift_final.p, (size_t)v.n * 4));
     SPC_CUDA(cudaStreamSynchronize(ctx->stream));
     if (n_c_actual) *n_c_actual = ncf;
@@ -1145,6 +1163,7 @@ spc_status spc_coarsen_batched(spc_context* ctx, const spc_csr* g, const int64_t
     int64_t ncf = 0;
     int32_t warn = 0;
     ctx->has_result = false;
+    ctx->reorder_n = 0;
     SPC_TRY(drive(ctx, v, S, o.use_graph != 0, &ncf, &warn));
     ctx->has_result = true;
     SPC_TRY(copy_out(ctx, lift_out, ctx->work.lift_final.p, (size_t)v.n * 4));
@@ -1213,6 +1232,14 @@ spc_status spc_take_result(spc_context* ctx, spc_result* out) {
         return st;
     }
     *out = r;
+    return SPC_OK;
+}
+
+spc_status spc_get_reorder(spc_context* ctx, int32_t* perm_out) {
+    SPC_TRY(begin_call(ctx));
+    if (!perm_out || ctx->reorder_n <= 0) return SPC_ERR_INVALID_ARG;
+    SPC_TRY(copy_out(ctx, perm_out, ctx->work.ro_perm.p, (size_t)ctx->reorder_n * 4));
+    SPC_CUDA(cudaStreamSynchronize(ctx->stream));
     return SPC_OK;
 }
 

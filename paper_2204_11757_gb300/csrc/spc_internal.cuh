@@ -116,6 +116,9 @@ struct Work {
     // input graph with the accumulated internal weight on its diagonal
     Buf ms_key, ms_val, ms_key2, ms_val2, ms_start;
     Buf dg_rowptr, dg_col, dg_w, dg_pos;
+    // adjacency reordering: distances, frontiers, the renumbering and the renumbered CSR
+    Buf ro_dist, ro_front[2], ro_key, ro_val, ro_key2, ro_val2, ro_perm, ro_deg;
+    Buf ro_rowptr, ro_col, ro_w, ro_lkey, ro_lkey2, ro_lval, ro_lval2, ro_head, ro_lift;
 };
 
 struct Timer {
@@ -189,6 +192,7 @@ struct spc_context {
     int32_t n_levels = 0;
     int32_t replayed_last = 0;       // the last coarsening call was a graph replay
     bool has_result = false;         // lift_final and the levels hold a coarsening result
+    int64_t reorder_n = 0;           // the last coarsening renumbered its n nodes (0: it did not)
     spc::Timer timer;
     int64_t launches = 0;
     spc::Replay replay;
@@ -396,6 +400,12 @@ spc_status run_carry_mass(spc_context* ctx, int64_t n, const int32_t* lift, int6
 // mass[x] != 0 (edge ids unchanged); written into the context's dg_* buffers, described by out.
 spc_status run_diag_graph(spc_context* ctx, const GraphView& g, const void* mass,
                           GraphView& out);
+
+// Adjacency reordering (spc_reorder.cu): the graph renumbered by (breadth-first distance from
+// node 0, id), into the context's ro_* buffers (work.ro_perm[x] = the new id of node x), and
+// out[x] = in[ro_perm[x]] for a lift computed on the renumbered graph.  g must be valid.
+spc_status run_reorder(spc_context* ctx, const GraphView& g, GraphView& out);
+spc_status run_unpermute(spc_context* ctx, int64_t n, const int32_t* in, int32_t* out);
 spc_status run_pool_forward(spc_context* ctx, int64_t n, const int32_t* lift, int64_t n_c,
                             int64_t F, spc_dtype dt, const void* x, void* xc);
 spc_status run_pool_backward(spc_context* ctx, int64_t n, const int32_t* lift, int64_t n_c,

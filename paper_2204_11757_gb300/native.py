@@ -44,7 +44,7 @@ class spc_allocator(ctypes.Structure):
 class spc_options(ctypes.Structure):
     _fields_ = [("levels", ctypes.c_int32), ("validate", ctypes.c_int32),
                 ("use_graph", ctypes.c_int32), ("schedule", ctypes.c_int32),
-                ("self_mass", ctypes.c_int32)]
+                ("self_mass", ctypes.c_int32), ("reorder", ctypes.c_int32)]
 
 
 class spc_level(ctypes.Structure):
@@ -81,6 +81,7 @@ SIGNATURES = {
                                    ctypes.POINTER(spc_options), P, PI64]),
     "spc_coarsen_batched": (ctypes.c_int, [P, ctypes.POINTER(spc_csr), P, I64, I64,
                                            ctypes.POINTER(spc_options), P, P]),
+    "spc_get_reorder": (ctypes.c_int, [P, P]),
     "spc_level_count": (ctypes.c_int32, [P]),
     "spc_get_level": (ctypes.c_int, [P, ctypes.c_int32, ctypes.POINTER(spc_level)]),
     "spc_copy": (ctypes.c_int, [P, P, P, ctypes.c_size_t]),

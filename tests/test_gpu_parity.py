@@ -864,3 +864,40 @@ def test_results_owned_by_the_caller_outlive_later_calls(ctx):
     with pytest.raises(N.SpcError) as e:  # a single step leaves no coarsening result
         ctx.take_result()
     assert e.value.status == -1
+
+
+def _reorder_case(name):
+    if name == "powerlaw":
+        return I.powerlaw_graph(4039, 22, 7, "float", np.float32), 8
+    if name == "disconnected":
+        g = I.random_graph(3000, 0.0012, 17, weight="int", dtype=np.int32, connected=False)
+        return g, 4
+    g, cfg = I.config_graph(name)
+    return g, cfg["ratio"]
+
+
+@pytest.mark.parametrize("name", ["s4_rgg64k_f32", "s2_tri256_f64", "powerlaw", "disconnected"])
+def test_reordered_coarsening_matches_oracle(ctx, name):
+    """The adjacency-reordering option: the renumbering equals the oracle's (breadth-first
+    distance from node 0, then id; unreached nodes last), the lift equals the oracle's
+    coarsening of the renumbered graph read back in the caller's numbering, and every retained
+    level equals the oracle's level of the renumbered graph, bit for bit.  A second call replays
+    the captured graph with the same result."""
+    api = _api()
+    g, ratio = _reorder_case(name)
+    L = int(round(np.log2(ratio)))
+    levels_ref, total_ref, perm_ref = O.coarsen_reordered(g, ratio, "halving")
+    csr = api.CSR.from_graph(g)
+    for call in range(2):
+        lift, nca, st = ctx.coarsen(csr, levels_ref[-1].target, levels=L, reorder=True)
+        assert np.array_equal(ctx.reorder_perm(g.n).cpu().numpy(), perm_ref)
+        assert nca == levels_ref[-1].n_c
+        assert np.array_equal(lift.cpu().numpy(), total_ref)
+        for lv, ref in zip(ctx.levels(), levels_ref):
+            assert np.array_equal(_bits(lv.score.cpu().numpy()), _bits(ref.f))
+            _check_level(lv, ref)
+    assert ctx.last_call_replayed
+    ctx.coarsen(csr, levels_ref[-1].target, levels=L)
+    from paper_2204_11757_gb300 import native as N
+    with pytest.raises(N.SpcError):
+        ctx.reorder_perm(g.n)  # the last call did not reorder

@@ -752,3 +752,71 @@ def test_carried_mass_order_is_ascending_members_then_self_mass():
     assert got[0] == big and got[1] == np.float32(15)
     # the reverse member order would have kept the two ones
     assert np.float32(np.float32(1 + 1) + big) + 1 != got[0]
+
+
+def _bfs_dist_bruteforce(g):
+    """Hop distances from node 0 by the textbook queue, in plain Python (tiny graphs)."""
+    from collections import deque
+    dist = [None] * g.n
+    if g.n:
+        dist[0] = 0
+        q = deque([0])
+        while q:
+            u = q.popleft()
+            for v in g.col[g.rowptr[u]:g.rowptr[u + 1]]:
+                if dist[v] is None:
+                    dist[v] = dist[u] + 1
+                    q.append(int(v))
+    far = max([d for d in dist if d is not None], default=-1) + 1
+    return [far if d is None else d for d in dist]
+
+
+def test_bfs_order_is_distance_then_id():
+    """The reordering's order against a textbook breadth-first search: new ids ascend with
+    (hop distance from node 0, id), unreached nodes last."""
+    graphs = [I.path_graph(9), I.cycle_graph(12), I.complete_graph(5)]
+    for seed in range(6):
+        graphs.append(I.random_graph(60, 0.05, 40 + seed, weight="float", dtype=np.float64,
+                                     connected=seed % 2 == 0))
+    for g in graphs:
+        perm = O.bfs_order(g)
+        assert sorted(perm.tolist()) == list(range(g.n))
+        d = _bfs_dist_bruteforce(g)
+        want = sorted(range(g.n), key=lambda x: (d[x], x))
+        assert [int(np.nonzero(perm == i)[0][0]) for i in range(g.n)] == want
+
+
+def test_permuted_graph_is_the_same_graph():
+    """permute() renames nodes only: the renamed weighted adjacency matrix equals the
+    original's, rows stay sorted, and the undirected edge list follows the new upper triangle."""
+    g = I.random_graph(80, 0.06, 9, weight="float", dtype=np.float64, connected=True)
+    perm = O.bfs_order(g)
+    h = O.permute(g, perm)
+    W, H = O.dense_weights(g), O.dense_weights(h)
+    assert np.array_equal(H[np.ix_(perm, perm)], W)
+    for x in range(h.n):
+        assert np.all(np.diff(h.col[h.rowptr[x]:h.rowptr[x + 1]]) > 0)
+    assert h.m == g.m and np.all(h.eu < h.ev)
+    assert np.all(np.diff(h.eu.astype(np.int64) * h.n + h.ev) > 0)
+
+
+def test_reordered_coarsening_is_a_coarsening_of_the_input():
+    """The reordering option coarsens an isomorphic copy: its lift, read on the input graph, is
+    a partition of the target size whose super-nodes are connected, and its coarse graph's total
+    weight plus the carried mass equals the input's total weight."""
+    g = I.tri_mesh_2d(30, 20, 4, jitter=0.3, weight="inv_len", dtype=np.float64)
+    levels, lift, perm = O.coarsen_reordered(g, 8, "halving")
+    assert lift.max() + 1 == levels[-1].n_c == g.n // 8
+    for U in range(levels[-1].n_c):
+        members = set(np.nonzero(lift == U)[0].tolist())
+        seen, stack = set(), [next(iter(members))]
+        while stack:
+            x = stack.pop()
+            if x in seen:
+                continue
+            seen.add(x)
+            stack.extend(int(y) for y in g.col[g.rowptr[x]:g.rowptr[x + 1]] if y in members)
+        assert seen == members
+    last = levels[-1]
+    np.testing.assert_allclose(last.coarse.a_und.sum() + last.mass.sum(), g.w_und.sum(),
+                               rtol=1e-12)
