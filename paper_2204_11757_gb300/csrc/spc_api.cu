@@ -580,8 +580,9 @@ static spc_status run_levels(spc_context* ctx, const GraphView& g0, const Schedu
     GraphView cur = g0;
     const int64_t* cur_gptr = S.d_graph_ptr;
     if (S.reorder) {
-        // the caller's graph is checked before anything indexes with it, then renumbered
-        if (S.validate) SPC_TRY(run_score(ctx, cur, true, nullptr, 1));
+        // the caller's rows are checked before the renumbering indexes with them; their
+        // symmetry is checked by the renumbered graph's first score walk
+        if (S.validate) SPC_TRY(run_check_rows(ctx, cur));
         GraphView rg;
         SPC_TRY(run_reorder(ctx, cur, rg));
         cur = rg;
@@ -609,8 +610,7 @@ static spc_status run_levels(spc_context* ctx, const GraphView& g0, const Schedu
             if (t < 1) t = 1;
             sa.target = t;
         }
-        SPC_TRY(run_score(ctx, cur, S.validate && l == 0 && !S.reorder, lv.score.p,
-                          S.schedule));
+        SPC_TRY(run_score(ctx, cur, S.validate && l == 0, lv.score.p, S.schedule));
         lv.n = cur.n;
         lv.m = cur.m;
         int64_t n_c = 0;

@@ -117,7 +117,7 @@ struct Work {
     Buf ms_key, ms_val, ms_key2, ms_val2, ms_start;
     Buf dg_rowptr, dg_col, dg_w, dg_pos;
     // adjacency reordering: distances, frontiers, the renumbering and the renumbered CSR
-    Buf ro_dist, ro_front[2], ro_key, ro_val, ro_key2, ro_val2, ro_perm, ro_deg;
+    Buf ro_dist, ro_key, ro_val, ro_key2, ro_val2, ro_perm, ro_deg;
     Buf ro_rowptr, ro_col, ro_w, ro_lkey, ro_lkey2, ro_lval, ro_lval2, ro_head, ro_lift;
 };
 
@@ -406,6 +406,9 @@ spc_status run_diag_graph(spc_context* ctx, const GraphView& g, const void* mass
 // out[x] = in[ro_perm[x]] for a lift computed on the renumbered graph.  g must be valid.
 spc_status run_reorder(spc_context* ctx, const GraphView& g, GraphView& out);
 spc_status run_unpermute(spc_context* ctx, int64_t n, const int32_t* in, int32_t* out);
+// S0 row checks only (monotone row pointers, sorted in-range columns, no self-loop, valid
+// weights), synchronising to report them: what the renumbering indexes with.
+spc_status run_check_rows(spc_context* ctx, const GraphView& g);
 spc_status run_pool_forward(spc_context* ctx, int64_t n, const int32_t* lift, int64_t n_c,
                             int64_t F, spc_dtype dt, const void* x, void* xc);
 spc_status run_pool_backward(spc_context* ctx, int64_t n, const int32_t* lift, int64_t n_c,

@@ -157,20 +157,48 @@ template <> struct MinKey<unsigned int> {
 // (their loads overlap), and the survivors are appended with one global atomic per block
 // and pass.
 constexpr int kMkItems = 2;
+constexpr uint32_t kNoSlab = 0xffffffffu;  // no lower bound on the score slab
+
+// The start of a further slab: the forest found so far (parent, forest flags) stays; the
+// best-edge slots of both parities and the work-list counts are reset.
+__global__ void k_bv_reinit(int64_t n, unsigned long long* __restrict__ bk0,
+                            unsigned long long* __restrict__ bk1, int32_t* __restrict__ be0,
+                            int32_t* __restrict__ be1, int32_t* __restrict__ counts) {
+    spc::pdl_wait();
+    const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    for (int64_t i = t0; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        bk0[i] = ~0ull;
+        bk1[i] = ~0ull;
+        if (be0) {
+            be0[i] = INT32_MAX;
+            be1[i] = INT32_MAX;
+        }
+    }
+    if (t0 < 2) counts[t0] = 0;
+}
+
+// the slab just done becomes the lower bound of the next
+__global__ void k_bump_slab(const uint32_t* __restrict__ tau_top, uint32_t* __restrict__ tau_lo) {
+    spc::pdl_wait();
+    if (blockIdx.x == 0 && threadIdx.x == 0) *tau_lo = *tau_top;
+}
 
 template <class KT>
 __global__ void __launch_bounds__(kThreads)
-k_bv_minkey(int round0, int64_t m, const int32_t* __restrict__ in_count,
+k_bv_minkey(int round0, int resume, int64_t m, const int32_t* __restrict__ in_count,
             const int32_t* __restrict__ wi_e, const int32_t* __restrict__ wi_u,
             const int32_t* __restrict__ wi_v, const int32_t* __restrict__ eu,
             const int32_t* __restrict__ ev, const KT* __restrict__ key, int tau_shift,
-            const uint32_t* __restrict__ tau_top, int32_t* parent, unsigned long long* best_k,
-            int32_t* wo_e, int32_t* wo_u, int32_t* wo_v, int32_t* out_count, uint32_t* status) {
+            const uint32_t* __restrict__ tau_top, const uint32_t* __restrict__ tau_lo,
+            int32_t* parent, unsigned long long* best_k, int32_t* wo_e, int32_t* wo_u,
+            int32_t* wo_v, int32_t* out_count, uint32_t* status) {
     spc::pdl_wait();
     __shared__ int32_t sh_wsum[kThreads / 32];
     __shared__ int32_t sh_base;
     const int64_t cnt = round0 ? m : (int64_t)*in_count;
     const uint32_t top = tau_top ? *tau_top : 0xffffffffu;
+    // a resumed first round (the next slab of scores) skips the slabs already done
+    const uint32_t lo = tau_lo ? *tau_lo : kNoSlab;
     const int64_t per = (int64_t)blockDim.x * kMkItems;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int64_t base = (int64_t)blockIdx.x * per; base < cnt; base += (int64_t)gridDim.x * per) {
@@ -190,14 +218,18 @@ k_bv_minkey(int round0, int64_t m, const int32_t* __restrict__ in_count,
 #pragma unroll
         for (int it = 0; it < kMkItems; ++it) {
             k[it] = in[it] ? key[e[it]] : KT(0);
-            if (round0 && in[it] && (uint32_t)(k[it] >> tau_shift) > top) in[it] = false;
+            if (round0 && in[it]) {
+                const uint32_t bin = (uint32_t)(k[it] >> tau_shift);
+                if (bin > top || (lo != kNoSlab && bin <= lo)) in[it] = false;
+            }
         }
         int32_t ru[kMkItems], rv[kMkItems];
         int32_t nkeep = 0;
 #pragma unroll
         for (int it = 0; it < kMkItems; ++it) {
-            ru[it] = in[it] ? (round0 ? u[it] : uf_find(parent, u[it], status)) : 0;
-            rv[it] = in[it] ? (round0 ? v[it] : uf_find(parent, v[it], status)) : 0;
+            const bool direct = round0 && !resume;  // every node its own component
+            ru[it] = in[it] ? (direct ? u[it] : uf_find(parent, u[it], status)) : 0;
+            rv[it] = in[it] ? (direct ? v[it] : uf_find(parent, v[it], status)) : 0;
             in[it] = in[it] && ru[it] != rv[it];
             const unsigned long long pk = MinKey<KT>::pack(k[it], e[it]);
             warp_atomic_min_u64(best_k, ru[it], pk, in[it]);
@@ -234,6 +266,105 @@ k_bv_minkey(int round0, int64_t m, const int32_t* __restrict__ in_count,
             }
         }
         __syncthreads();
+    }
+}
+
+
+// The last Boruvka rounds in one CTA.  Once the work list holds at most kFinishMax items (the
+// last rounds of a large level; every round of a small one) a round is a few microseconds of
+// work and three launches; here one CTA of kFinishThreads runs every remaining round, its
+// phases separated by block barriers: the lowering of the component minima (as k_bv_minkey,
+// the survivors compacted into the other list through a shared-memory counter), the tie-break
+// by edge id for 64-bit scores (as k_bv_tiebreak), the hook (as k_bv_hook).  Each component's
+// lightest edge is unique, so the forest does not depend on the order of the lists.
+// round0: the first round reads the edges directly (e = i, u = eu[i], v = ev[i]) with the
+// score-prefix filter, like k_bv_minkey's first round.
+constexpr int kFinishMax = 16384;
+constexpr int kFinishThreads = 1024;
+
+template <class KT>
+__global__ void __launch_bounds__(kFinishThreads, 1)
+k_bv_finish(int round0, int par0, int64_t m, int32_t* count_in, int32_t* li_e, int32_t* li_u,
+            int32_t* li_v, int32_t* lo_e, int32_t* lo_u, int32_t* lo_v,
+            const int32_t* __restrict__ eu, const int32_t* __restrict__ ev,
+            const KT* __restrict__ key, int tau_shift, const uint32_t* __restrict__ tau_top,
+            const uint32_t* __restrict__ tau_lo, int32_t* parent, unsigned long long* bk0,
+            unsigned long long* bk1, int32_t* be0, int32_t* be1, uint8_t* msf,
+            uint32_t* status) {
+    spc::pdl_wait();
+    __shared__ int32_t sh_cnt[2];
+    const uint32_t top = tau_top ? *tau_top : 0xffffffffu;
+    const uint32_t slab_lo = tau_lo ? *tau_lo : kNoSlab;
+    int64_t cnt = round0 ? m : (int64_t)*count_in;
+    int par = par0;
+    int32_t *ie = li_e, *iu = li_u, *iv = li_v, *oe = lo_e, *ou = lo_u, *ov = lo_v;
+    for (int r = 0; cnt > 0; ++r) {
+        if (r >= 64) {  // every round at least halves the components that still have edges
+            if (threadIdx.x == 0) atomicOr(status, DEV_TIMEOUT);
+            break;
+        }
+        unsigned long long* bk = par ? bk1 : bk0;
+        unsigned long long* bk_next = par ? bk0 : bk1;
+        int32_t* be = par ? be1 : be0;
+        int32_t* be_next = par ? be0 : be1;
+        if (threadIdx.x == 0) sh_cnt[0] = 0;
+        __syncthreads();
+        // lower the component minima; keep the edges between two components
+        for (int64_t i = threadIdx.x; i < cnt; i += kFinishThreads) {
+            int32_t e, u, v;
+            if (round0 && r == 0) { e = (int32_t)i; u = eu[i]; v = ev[i]; }
+            else { e = ie[i]; u = iu[i]; v = iv[i]; }
+            const KT k = key[e];
+            if (round0 && r == 0) {
+                const uint32_t bin = (uint32_t)(k >> tau_shift);
+                if (bin > top || (slab_lo != kNoSlab && bin <= slab_lo)) continue;
+            }
+            const int32_t ru = uf_find(parent, u, status), rv = uf_find(parent, v, status);
+            if (ru == rv) continue;
+            const unsigned long long pk = MinKey<KT>::pack(k, e);
+            atomicMin(bk + ru, pk);
+            atomicMin(bk + rv, pk);
+            const int32_t slot = atomicAdd(&sh_cnt[0], 1);
+            oe[slot] = e;
+            ou[slot] = ru;
+            ov[slot] = rv;
+        }
+        __syncthreads();
+        const int32_t kept = sh_cnt[0];
+        if (MinKey<KT>::two_phase) {  // among equal scores, the smallest edge id
+            for (int32_t i = threadIdx.x; i < kept; i += kFinishThreads) {
+                const int32_t e = oe[i], ru = ou[i], rv = ov[i];
+                const unsigned long long k = (unsigned long long)key[e];
+                if (k == bk[ru]) atomicMin(be + ru, e);
+                if (k == bk[rv]) atomicMin(be + rv, e);
+            }
+            __syncthreads();
+        }
+        // hook the picked edges; clear the next round's slots of these components
+        for (int32_t i = threadIdx.x; i < kept; i += kFinishThreads) {
+            const int32_t e = oe[i], ru = ou[i], rv = ov[i];
+            bool picked;
+            if (MinKey<KT>::two_phase) {
+                picked = be[ru] == e || be[rv] == e;
+                be_next[ru] = INT32_MAX;
+                be_next[rv] = INT32_MAX;
+            } else {
+                picked = (int32_t)(uint32_t)bk[ru] == e || (int32_t)(uint32_t)bk[rv] == e;
+            }
+            bk_next[ru] = ~0ull;
+            bk_next[rv] = ~0ull;
+            if (picked) {
+                msf[e] = 1;
+                uf_unite(parent, ru, rv, status);
+            }
+        }
+        __syncthreads();
+        cnt = kept;
+        par ^= 1;
+        int32_t* t;
+        t = ie; ie = oe; oe = t;
+        t = iu; iu = ou; ou = t;
+        t = iv; iv = ov; ov = t;
     }
 }
 
@@ -830,50 +961,96 @@ spc_status select_typed(spc_context* ctx, const GraphView& g, const KT* key,
     const int64_t k_need = batched ? 0 : (n - sa.target > 0 ? n - sa.target : 0);
     const int tau_shift = sizeof(KT) == 8 ? 48 : 16;
     uint32_t* tau_top = reinterpret_cast<uint32_t*>(counters + 12);
-    bool use_prefix = !batched && m > 65536 && k_need > 0 && (k_need + k_need / 2) < m;
-    if (use_prefix) {
-        SPC_TRY(ensure_key_hist(ctx));
-        static std::atomic<unsigned long long> attr_devs{0};  // devices already set up
-        const unsigned long long bit = 1ull << (ctx->device & 63);
-        if (!(attr_devs.load() & bit)) {
-            SPC_CUDA(cudaFuncSetAttribute(k_key_hist<KT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          32768 * 4));
-            attr_devs.fetch_or(bit);
-        }
-        SPC_LAUNCH(ctx, k_key_hist<KT>, ctx->num_sms, 1024, 32768 * 4, m, key, tau_shift,
-                   W.key_hist.as<uint32_t>());
-        SPC_LAUNCH(ctx, k_pick_tau, 1, 1024, 0, W.key_hist.as<uint32_t>(),
-                   k_need + k_need / 2, tau_top);
-    }
+    // Kruskal's first n - n_c merges are the lightest n - n_c edges of the minimum spanning
+    // forest of any score prefix whose forest has that many edges; the forest of a longer
+    // prefix is the shorter prefix's forest plus Boruvka over the next slab of scores between
+    // its components.  So the selection starts with about 1.5 (n - n_c) edges and, when their
+    // forest falls short, extends it slab by slab (twice the edges each time) instead of
+    // starting over.
+    int64_t need = k_need + k_need / 2;
+    bool use_prefix = !batched && m > 65536 && k_need > 0 && need < m;
+    uint32_t* tau_lo = reinterpret_cast<uint32_t*>(counters + 14);
     int32_t* pos = W.c_pos.as<int32_t>();
     int64_t n_msf = 0;
-    for (int attempt = 0; attempt < 2; ++attempt) {
+    for (int attempt = 0;; ++attempt) {
         const bool two = MinKey<KT>::two_phase;
-        SPC_LAUNCH(ctx, k_bv_init, grid_for(n > m ? n : m + 1, kThreads, maxb), kThreads, 0, n,
-                   m, parent, W.best_k[0].as<unsigned long long>(),
-                   W.best_k[1].as<unsigned long long>(), two ? W.best_e[0].as<int32_t>() : nullptr,
-                   two ? W.best_e[1].as<int32_t>() : nullptr, W.msf.as<uint8_t>(), merged,
-                   counters);
+        if (use_prefix) {
+            SPC_TRY(ensure_key_hist(ctx));
+            static std::atomic<unsigned long long> attr_devs{0};  // devices already set up
+            const unsigned long long bit = 1ull << (ctx->device & 63);
+            if (!(attr_devs.load() & bit)) {
+                SPC_CUDA(cudaFuncSetAttribute(k_key_hist<KT>,
+                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              32768 * 4));
+                attr_devs.fetch_or(bit);
+            }
+            if (attempt > 0) SPC_LAUNCH(ctx, k_bump_slab, 1, 32, 0, tau_top, tau_lo);
+            SPC_LAUNCH(ctx, k_key_hist<KT>, ctx->num_sms, 1024, 32768 * 4, m, key, tau_shift,
+                       W.key_hist.as<uint32_t>());
+            SPC_LAUNCH(ctx, k_pick_tau, 1, 1024, 0, W.key_hist.as<uint32_t>(), need, tau_top);
+        } else if (attempt > 0) {
+            SPC_LAUNCH(ctx, k_bump_slab, 1, 32, 0, tau_top, tau_lo);
+        }
+        const uint32_t* slab_lo = attempt > 0 ? tau_lo : nullptr;
+        if (attempt == 0) {
+            SPC_LAUNCH(ctx, k_bv_init, grid_for(n > m ? n : m + 1, kThreads, maxb), kThreads, 0,
+                       n, m, parent, W.best_k[0].as<unsigned long long>(),
+                       W.best_k[1].as<unsigned long long>(),
+                       two ? W.best_e[0].as<int32_t>() : nullptr,
+                       two ? W.best_e[1].as<int32_t>() : nullptr, W.msf.as<uint8_t>(), merged,
+                       counters);
+        } else {
+            SPC_LAUNCH(ctx, k_bv_reinit, grid_for(n, kThreads, maxb), kThreads, 0, n,
+                       W.best_k[0].as<unsigned long long>(),
+                       W.best_k[1].as<unsigned long long>(),
+                       two ? W.best_e[0].as<int32_t>() : nullptr,
+                       two ? W.best_e[1].as<int32_t>() : nullptr, counters);
+        }
         // ---- 1. Boruvka minimum spanning forest (of the prefix) ---------------------------
         int64_t cur = m;
         for (int round = 0; cur > 0; ++round) {
             const int in = round & 1, out = in ^ 1;
             const int par = round & 1;
+            if (cur <= kFinishMax) {  // the remaining rounds in one CTA
+                note_bytes(ctx, round == 0 ? (double)m * (8 + sizeof(KT))
+                                           : (double)cur * (12 + sizeof(KT) + 8 + 32 + 12));
+                SPC_LAUNCH(ctx, k_bv_finish<KT>, 1, kFinishThreads, 0, round == 0 ? 1 : 0, par,
+                           m, counters + in, W.wl_e[in].as<int32_t>(), W.wl_u[in].as<int32_t>(),
+                           W.wl_v[in].as<int32_t>(), W.wl_e[out].as<int32_t>(),
+                           W.wl_u[out].as<int32_t>(), W.wl_v[out].as<int32_t>(),
+                           W.eu.as<int32_t>(), W.ev.as<int32_t>(), key, tau_shift,
+                           use_prefix ? tau_top : nullptr, slab_lo, parent,
+                           W.best_k[0].as<unsigned long long>(),
+                           W.best_k[1].as<unsigned long long>(),
+                           MinKey<KT>::two_phase ? W.best_e[0].as<int32_t>() : nullptr,
+                           MinKey<KT>::two_phase ? W.best_e[1].as<int32_t>() : nullptr,
+                           W.msf.as<uint8_t>(), status);
+                break;
+            }
+            // algorithmic bytes: the first round reads every edge's ends and key; a later one
+            // reads each work-list item (e, u, v) and key, walks two parents, lowers two best
+            // slots (read and write) and writes the item back
+            note_bytes(ctx, round == 0 ? (double)m * (8 + sizeof(KT))
+                                       : (double)cur * (12 + sizeof(KT) + 8 + 32 + 12));
             SPC_LAUNCH(ctx, k_bv_minkey<KT>,
                        grid_for(cur, kThreads * kMkItems, maxb), kThreads, 0,
-                       round == 0 ? 1 : 0, m, counters + in, W.wl_e[in].as<int32_t>(),
-                       W.wl_u[in].as<int32_t>(), W.wl_v[in].as<int32_t>(), W.eu.as<int32_t>(),
-                       W.ev.as<int32_t>(), key, tau_shift, use_prefix ? tau_top : nullptr, parent,
+                       round == 0 ? 1 : 0, attempt > 0 ? 1 : 0, m, counters + in,
+                       W.wl_e[in].as<int32_t>(), W.wl_u[in].as<int32_t>(),
+                       W.wl_v[in].as<int32_t>(), W.eu.as<int32_t>(), W.ev.as<int32_t>(), key,
+                       tau_shift, use_prefix ? tau_top : nullptr, slab_lo, parent,
                        W.best_k[par].as<unsigned long long>(), W.wl_e[out].as<int32_t>(),
                        W.wl_u[out].as<int32_t>(), W.wl_v[out].as<int32_t>(), counters + out,
                        status);
             if (MinKey<KT>::two_phase) {
+                note_bytes(ctx, (double)cur * (12 + 8 + 16 + 8));
                 SPC_LAUNCH(ctx, k_bv_tiebreak, grid_for(cur, kThreads, maxb), kThreads, 0,
                            counters + out, W.wl_e[out].as<int32_t>(), W.wl_u[out].as<int32_t>(),
                            W.wl_v[out].as<int32_t>(),
                            reinterpret_cast<const unsigned long long*>(key),
                            W.best_k[par].as<unsigned long long>(), W.best_e[par].as<int32_t>());
             }
+            // each item and the two best slots read, the forest flag written, one parent swap
+            note_bytes(ctx, (double)cur * (12 + 24 + 1 + 8));
             SPC_LAUNCH(ctx, k_bv_hook<KT>, grid_for(cur, kThreads, maxb), kThreads, 0,
                        counters + out, W.wl_e[out].as<int32_t>(), W.wl_u[out].as<int32_t>(),
                        W.wl_v[out].as<int32_t>(), W.best_k[par].as<unsigned long long>(),
@@ -890,7 +1067,8 @@ spc_status select_typed(spc_context* ctx, const GraphView& g, const KT* key,
         SPC_TRY(read_i32(ctx, pos + m, &n_msf));
         // the prefix's forest holds Kruskal's first n_msf merges; enough when >= n - n_c
         if (!use_prefix || n_msf >= k_need) break;
-        use_prefix = false;
+        need *= 2;
+        if (need >= m) use_prefix = false;  // the last slab: every remaining score
     }
     // ---- 2. lightest forest edges per graph ---------------------------------------------
     KT* sk = W.sel_key.as<KT>();

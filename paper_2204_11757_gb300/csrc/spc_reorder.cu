@@ -7,6 +7,8 @@
 // renumbered CSR.  The coarsening then runs on the renumbered graph: node x of the caller's
 // graph is node perm[x] there, and every result refers to the renumbered graph except the
 // composed lift, which is read back in the caller's numbering.
+#include <atomic>
+
 #include "spc_scan.cuh"
 
 namespace spc {
@@ -17,52 +19,146 @@ constexpr int32_t kUnreached = 0x7fffffff;
 constexpr int kShortRow = 32;  // rows ranked in registers; longer rows by a radix sort
 
 __global__ void __launch_bounds__(kThreads)
-k_bfs_init(int64_t n, int32_t* __restrict__ dist, int32_t* __restrict__ frontier,
-           int32_t* __restrict__ counts) {
+k_bfs_init(int64_t n, int32_t* __restrict__ dist, int32_t* __restrict__ flags,
+           unsigned* __restrict__ bar) {
     spc::pdl_wait();
     const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     for (int64_t x = t0; x < n; x += (int64_t)gridDim.x * blockDim.x)
         dist[x] = x == 0 ? 0 : kUnreached;
     if (t0 == 0) {
-        frontier[0] = 0;
-        counts[0] = 1;
-        counts[1] = 0;
-        counts[2] = 0;
+        flags[0] = 0;
+        flags[1] = 0;
+        flags[2] = 0;
+        bar[0] = 0u;
+        bar[1] = 0u;
     }
 }
 
-// One breadth-first level: the unreached neighbours of the frontier get distance d1 and form
-// the next frontier, appended by one atomic per warp and step.  Counts rotate over three
-// words: this level reads counts[in], fills counts[out] and zeroes the third, which the level
-// before read and the level after fills.
-__global__ void __launch_bounds__(kThreads)
-k_bfs_expand(const int32_t* __restrict__ frontier_in, const int32_t* in_count,
-             const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
-             int32_t* dist, int32_t d1, int32_t* __restrict__ frontier_out, int32_t* out_count,
-             int32_t* spare_count) {
-    spc::pdl_wait();
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t0 == 0) *spare_count = 0;
-    const int64_t cnt = *in_count;
-    const int lane = threadIdx.x & 31;
-    for (int64_t i = t0; i < cnt; i += stride) {
-        const int32_t u = frontier_in[i];
-        const int64_t r1 = rowptr[u + 1];
-        for (int64_t j = rowptr[u]; j < r1; ++j) {
-            const int32_t v = col[j];
-            const bool found = dist[v] == kUnreached && atomicCAS(dist + v, kUnreached, d1) ==
-                                                            kUnreached;
-            const unsigned mask = __activemask();
-            const unsigned b = __ballot_sync(mask, found);
-            if (b) {
-                const int leader = __ffs(b) - 1;
-                int32_t base = 0;
-                if (lane == leader) base = atomicAdd(out_count, __popc(b));
-                base = __shfl_sync(mask, base, leader);
-                if (found) frontier_out[base + __popc(b & ((1u << lane) - 1u))] = v;
+// Grid-wide barrier of a cooperative launch (every block resident, so every wait ends); the
+// waits are bounded by the context's wait limit all the same.  bar[0] counts the blocks that
+// arrived, bar[1] is the generation.  Returns false (and sets DEV_TIMEOUT) when a wait gave up.
+__device__ bool grid_barrier(unsigned* bar, uint32_t* status) {
+    __shared__ int sh_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned* gen = bar + 1;
+        const unsigned g = *gen;
+        __threadfence();
+        int ok = 1;
+        if (atomicAdd(bar, 1u) + 1u == gridDim.x) {
+            bar[0] = 0u;
+            __threadfence();
+            atomicAdd(bar + 1, 1u);
+        } else {
+            const uint32_t lim = spin_limit(status);
+            uint32_t spins = 0;
+            while (*gen == g) {
+                if (++spins > lim) {
+                    atomicOr(status, DEV_TIMEOUT);
+                    ok = 0;
+                    break;
+                }
             }
         }
+        __threadfence();
+        sh_ok = ok;
+    }
+    __syncthreads();
+    return sh_ok != 0;
+}
+
+// Every breadth-first level in one cooperative launch.  At level d every node at distance d
+// gives its unreached neighbours distance d + 1 (one compare-and-swap each).  The nodes of a
+// level are found by scanning the distance array (4 bytes a node, resident in L2) rather than
+// through a frontier queue, so no counter is shared by the whole grid; the reads bypass L1,
+// where a line of an earlier level could be stale.  A block that reached a node sets the
+// level's flag (three words rotate: level d sets flags[d % 3] and clears flags[(d + 1) % 3],
+// last read two levels earlier); after the grid barrier every block reads the flag, and the
+// first level that reached nothing ends the loop.  *levels_out = that level + 1, one past the
+// largest distance.
+__global__ void __launch_bounds__(kThreads)
+k_bfs_all(int64_t n, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+          int32_t* dist, int32_t* flags, unsigned* bar, int32_t* levels_out, uint32_t* status) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t n4 = n >> 2;
+    const int4* dist4 = reinterpret_cast<const int4*>(dist);
+    constexpr int kScanUnroll = 8;  // groups of four distances in flight per thread
+    int32_t d = 0;
+    for (;; ++d) {
+        if (t0 == 0) flags[(d + 1) % 3] = 0;
+        bool any = false;
+        auto expand = [&](int64_t x) {
+            const int64_t r1 = rowptr[x + 1];
+            for (int64_t j = rowptr[x]; j < r1; ++j) {
+                const int32_t v = col[j];
+                if (__ldcg(dist + v) == kUnreached &&
+                    atomicCAS(dist + v, kUnreached, d + 1) == kUnreached)
+                    any = true;
+            }
+        };
+        for (int64_t g0 = t0; g0 < n4; g0 += (int64_t)kScanUnroll * stride) {
+            int4 q[kScanUnroll];
+#pragma unroll
+            for (int u = 0; u < kScanUnroll; ++u) {
+                const int64_t g = g0 + (int64_t)u * stride;
+                q[u] = g < n4 ? __ldcg(dist4 + g) : make_int4(-1, -1, -1, -1);
+            }
+#pragma unroll
+            for (int u = 0; u < kScanUnroll; ++u) {
+                const int64_t x0 = (g0 + (int64_t)u * stride) << 2;
+                if (q[u].x == d) expand(x0);
+                if (q[u].y == d) expand(x0 + 1);
+                if (q[u].z == d) expand(x0 + 2);
+                if (q[u].w == d) expand(x0 + 3);
+            }
+        }
+        // the last n mod 4 nodes
+        if (t0 < (n & 3) && __ldcg(dist + (n4 << 2) + t0) == d) expand((n4 << 2) + t0);
+        if (__syncthreads_or(any) && threadIdx.x == 0) flags[d % 3] = 1;
+        if (!grid_barrier(bar, status)) break;
+        if (*reinterpret_cast<volatile int32_t*>(flags + d % 3) == 0) break;
+    }
+    if (t0 == 0) *levels_out = d + 1;
+}
+
+// S0 row checks of the caller's graph before the renumbering indexes with it: row pointers
+// monotone, columns strictly ascending inside [0, n), no self-loop, weights finite and > 0.
+// (Symmetry is checked on the renumbered graph, whose first score walk checks every mirror.)
+template <class WT> __device__ __forceinline__ bool weight_ok(WT w);
+template <> __device__ __forceinline__ bool weight_ok<int32_t>(int32_t w) { return w > 0; }
+template <> __device__ __forceinline__ bool weight_ok<float>(float w) {
+    const int b = __float_as_int(w);
+    return b > 0 && b < 0x7f800000;
+}
+template <> __device__ __forceinline__ bool weight_ok<double>(double w) {
+    const long long b = __double_as_longlong(w);
+    return b > 0 && b < 0x7ff0000000000000ll;
+}
+
+template <class WT>
+__global__ void __launch_bounds__(kThreads)
+k_check_rows(int64_t n, int64_t nnz, const int64_t* __restrict__ rowptr,
+             const int32_t* __restrict__ col, const WT* __restrict__ w, uint32_t* status) {
+    spc::pdl_wait();
+    const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t0 == 0 && (rowptr[0] != 0 || rowptr[n] != nnz)) atomicOr(status, DEV_UNSORTED);
+    for (int64_t x = t0; x < n; x += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r0 = rowptr[x], r1 = rowptr[x + 1];
+        if (r0 < 0 || r1 < r0 || r1 > nnz) {
+            atomicOr(status, DEV_UNSORTED);
+            continue;
+        }
+        uint32_t bits = 0;
+        int64_t prev = -1;
+        for (int64_t j = r0; j < r1; ++j) {
+            const int32_t y = col[j];
+            if (y < 0 || (int64_t)y >= n || (int64_t)y <= prev) bits |= DEV_UNSORTED;
+            if ((int64_t)y == x) bits |= DEV_SELF_LOOP;
+            if (!weight_ok<WT>(w[j])) bits |= DEV_BAD_WEIGHT;
+            prev = y;
+        }
+        if (bits) atomicOr(status, bits);
     }
 }
 
@@ -210,6 +306,52 @@ k_unpermute(int64_t n, const int32_t* __restrict__ perm, const int32_t* __restri
         out[x] = in[perm[x]];
 }
 
+// the cooperative launch: as many blocks as fit on the device at once (all resident)
+spc_status launch_bfs_all(spc_context* ctx, const GraphView& g, int32_t* dist, int32_t* flags,
+                          unsigned* bar, int32_t* levels) {
+    static std::atomic<unsigned long long> occ_devs{0};
+    static int occ_blocks[64];
+    const unsigned long long bit = 1ull << (ctx->device & 63);
+    if (!(occ_devs.load() & bit)) {
+        int b = 0;
+        SPC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_bfs_all, kThreads, 0));
+        occ_blocks[ctx->device & 63] = b;
+        occ_devs.fetch_or(bit);
+    }
+    int per_sm = occ_blocks[ctx->device & 63];
+    if (per_sm > 4) per_sm = 4;
+    if (per_sm < 1) return SPC_ERR_CUDA;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(ctx->num_sms * per_sm));
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = ctx->stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    // the CSR's row pointers and columns read once, every distance written once
+    note_bytes(ctx, 8.0 * (g.n + 1) + 4.0 * g.nnz + 4.0 * g.n);
+    before_launch(ctx, "k_bfs_all");
+    cudaError_t e = cudaLaunchKernelEx(&cfg, k_bfs_all, g.n, g.rowptr, g.col, dist, flags, bar,
+                                       levels, ctx->d_status);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    after_launch(ctx, "k_bfs_all");
+    if (e != cudaSuccess) {
+        set_last_cuda_error(e, "k_bfs_all", __FILE__, __LINE__);
+        return SPC_ERR_CUDA;
+    }
+    return SPC_OK;
+}
+
+template <class WT>
+spc_status check_rows_typed(spc_context* ctx, const GraphView& g) {
+    SPC_LAUNCH(ctx, k_check_rows<WT>, grid_for(g.n, kThreads, ctx->num_sms * 8), kThreads, 0,
+               g.n, g.nnz, g.rowptr, g.col, static_cast<const WT*>(g.w), ctx->d_status);
+    return check_status(ctx);
+}
+
 template <class WT>
 spc_status reorder_typed(spc_context* ctx, const GraphView& g, GraphView& out) {
     Work& W = ctx->work;
@@ -218,8 +360,6 @@ spc_status reorder_typed(spc_context* ctx, const GraphView& g, GraphView& out) {
     const int gn = grid_for(n, kThreads, maxb);
     const size_t N = (size_t)n + 1;
     SPC_TRY(ensure(ctx, W.ro_dist, N * 4));
-    SPC_TRY(ensure(ctx, W.ro_front[0], N * 4));
-    SPC_TRY(ensure(ctx, W.ro_front[1], N * 4));
     SPC_TRY(ensure(ctx, W.ro_key, N * 4));
     SPC_TRY(ensure(ctx, W.ro_val, N * 4));
     SPC_TRY(ensure(ctx, W.ro_key2, N * 4));
@@ -230,23 +370,18 @@ spc_status reorder_typed(spc_context* ctx, const GraphView& g, GraphView& out) {
     SPC_TRY(ensure(ctx, W.ro_col, (size_t)(nnz + 1) * 4));
     SPC_TRY(ensure(ctx, W.ro_w, (size_t)(nnz + 1) * sizeof(WT)));
     int32_t* dist = W.ro_dist.as<int32_t>();
-    int32_t* counts = W.counters.as<int32_t>() + 56;  // three rotating frontier counts
+    int32_t* flags = W.counters.as<int32_t>() + 56;  // three rotating level flags
     out = g;
     if (n == 0) return SPC_OK;
-    // ---- breadth-first levels from node 0 --------------------------------------------------
-    SPC_LAUNCH(ctx, k_bfs_init, gn, kThreads, 0, n, dist, W.ro_front[0].as<int32_t>(), counts);
-    int64_t cur = 1;
-    int32_t d = 0;
-    for (; cur > 0; ++d) {
-        if (d >= n) return SPC_ERR_TIMEOUT;  // a BFS has at most n levels
-        const int in = d % 3, o = (d + 1) % 3, spare = (d + 2) % 3;
-        SPC_LAUNCH(ctx, k_bfs_expand, grid_for(cur, kThreads, maxb), kThreads, 0,
-                   W.ro_front[d & 1].as<int32_t>(), counts + in, g.rowptr, g.col, dist,
-                   (int32_t)(d + 1), W.ro_front[(d + 1) & 1].as<int32_t>(), counts + o,
-                   counts + spare);
-        SPC_TRY(read_loop_count(ctx, counts + o, &cur));
-    }
-    // d levels were expanded; the last one found nothing, so distances are at most d - 1
+    // ---- breadth-first levels from node 0, all in one cooperative launch ----------------------
+    unsigned* bar = reinterpret_cast<unsigned*>(W.counters.as<int32_t>() + 60);  // [60], [61]
+    int32_t* levels = W.counters.as<int32_t>() + 62;
+    SPC_LAUNCH(ctx, k_bfs_init, gn, kThreads, 0, n, dist, flags, bar);
+    SPC_TRY(launch_bfs_all(ctx, g, dist, flags, bar, levels));
+    int64_t d = 0;
+    SPC_TRY(read_i32(ctx, levels, &d));
+    SPC_TRY(check_status(ctx));  // a barrier that gave up
+    // one past the largest distance: the key of the unreached nodes
     const uint32_t far = (uint32_t)d;
     int bits = 1;
     while ((1ll << bits) <= (int64_t)far) ++bits;
@@ -313,6 +448,15 @@ spc_status run_reorder(spc_context* ctx, const GraphView& g, GraphView& out) {
         case SPC_I32: return reorder_typed<int32_t>(ctx, g, out);
         case SPC_F32: return reorder_typed<float>(ctx, g, out);
         case SPC_F64: return reorder_typed<double>(ctx, g, out);
+    }
+    return SPC_ERR_INVALID_ARG;
+}
+
+spc_status run_check_rows(spc_context* ctx, const GraphView& g) {
+    switch (g.wtype) {
+        case SPC_I32: return check_rows_typed<int32_t>(ctx, g);
+        case SPC_F32: return check_rows_typed<float>(ctx, g);
+        case SPC_F64: return check_rows_typed<double>(ctx, g);
     }
     return SPC_ERR_INVALID_ARG;
 }

@@ -556,15 +556,38 @@ k_score_warp_row(int64_t n, const int64_t* __restrict__ rowptr, const int32_t* _
 // scattered (random node order) the lines are evicted between the steps and each step reads a
 // sector from DRAM again.  Rows b longer than kStageCap entries, or a tile whose rows a exceed
 // kStageA entries, are walked in place.
+// cp.async copies of one 4- or 8-byte element from global into shared memory (sm_80 and
+// later), completed by cp_async_wait_all
+__device__ __forceinline__ void cp_async_4(void* smem, const void* gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_8(void* smem, const void* gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(sa), "l"(gmem) : "memory");
+}
+template <class T>
+__device__ __forceinline__ void cp_async_elem(T* smem, const T* gmem) {
+    if constexpr (sizeof(T) == 8) cp_async_8(smem, gmem);
+    else cp_async_4(smem, gmem);
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+}
+
 constexpr int kStageCap = 32;
 constexpr int kStageStr = kStageCap + 1;  // padded: lanes of one step hit different banks
 constexpr int kStageA = 256;
 constexpr int kStageWarps = 4;
 constexpr int kStageRegion = kStageA + 32 * kStageStr;  // elements per warp
 
+// binary64: the positions of each lane's common coordinates in rows a and b (split walk)
+constexpr int kSplitBytes = 2 * 32 * kStageCap;  // per warp: i and j, one byte each
+
 template <class PT>
 constexpr size_t stage_smem_bytes() {
-    return (size_t)kStageWarps * kStageRegion * (sizeof(PT) + sizeof(int32_t));
+    return (size_t)kStageWarps * kStageRegion * (sizeof(PT) + sizeof(int32_t)) +
+           (sizeof(PT) == 8 ? (size_t)kStageWarps * kSplitBytes : 0);
 }
 
 template <class PT, class KT>
@@ -584,6 +607,12 @@ k_score_staged(int64_t m, const int32_t* __restrict__ eu, const int32_t* __restr
                                                      (size_t)kStageWarps * kStageRegion) +
                           (size_t)wib * kStageRegion;
     int32_t* const sb_c = sa_c + kStageA;
+    // binary64 split walk: lane l's common positions at sp_i/sp_j[l * kStageCap + c]
+    uint8_t* const sp_i = reinterpret_cast<uint8_t*>(reinterpret_cast<int32_t*>(
+                              reinterpret_cast<PT*>(stage_raw) + (size_t)kStageWarps * kStageRegion) +
+                          (size_t)kStageWarps * kStageRegion) + (size_t)wib * kSplitBytes;
+    uint8_t* const sp_j = sp_i + 32 * kStageCap;
+    constexpr bool kSplit = sizeof(PT) == 8;
     constexpr int32_t kEnd = 0x7fffffff;
     uint32_t n_add = 0, n_sub = 0;
     bool asym = false;
@@ -606,34 +635,84 @@ k_score_staged(int64_t m, const int32_t* __restrict__ eu, const int32_t* __restr
         const int64_t abase = __shfl_sync(0xffffffffu, ra, 0);
         const int64_t alen = __shfl_sync(0xffffffffu, ra + da, lastl) - abase;
         const bool a_staged = alen <= kStageA;
+        // asynchronous copies straight into shared memory: the row-a slice and all 32 rows b
+        // of the tile are in flight together
         if (a_staged) {
             for (int64_t i = lane; i < alen; i += 32) {
-                sa_c[i] = col[abase + i];
-                sa_p[i] = p[abase + i];
+                cp_async_4(sa_c + i, col + abase + i);
+                cp_async_elem(sa_p + i, p + abase + i);
             }
         }
-        // the 32 rows b, eight at a time
-#pragma unroll
-        for (int k0 = 0; k0 < 32; k0 += 8) {
-            int32_t cv[8];
-            PT pv[8];
-#pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                const int64_t rbk = __shfl_sync(0xffffffffu, rb, k0 + q);
-                const int64_t dbk = __shfl_sync(0xffffffffu, db, k0 + q);
-                const bool ld = dbk <= kStageCap && lane < dbk;
-                cv[q] = ld ? col[rbk + lane] : 0;
-                pv[q] = ld ? p[rbk + lane] : PT(0);
-            }
-#pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                sb_c[(k0 + q) * kStageStr + lane] = cv[q];
-                sb_p[(k0 + q) * kStageStr + lane] = pv[q];
+#pragma unroll 8
+        for (int k = 0; k < 32; ++k) {
+            const int64_t rbk = __shfl_sync(0xffffffffu, rb, k);
+            const int64_t dbk = __shfl_sync(0xffffffffu, db, k);
+            if (dbk <= kStageCap && lane < dbk) {
+                cp_async_4(sb_c + k * kStageStr + lane, col + rbk + lane);
+                cp_async_elem(sb_p + k * kStageStr + lane, p + rbk + lane);
             }
         }
+        cp_async_wait_all();
         __syncwarp();
-        if (act) {
-            if (da > kLongRow || db > kLongRow) {  // hub edge: k_score_hub
+        const bool hub = act && (da > kLongRow || db > kLongRow);
+        // binary64 rows that are both staged take the split walk: the subtractions, which only
+        // coordinates in both rows need, in a loop of their own, then the additions
+        const bool split = kSplit && act && !hub && a_staged && db <= kStageCap;
+        if constexpr (kSplit) {
+            int nc = 0;
+            const int32_t* Ac = sa_c + (ra - abase);
+            PT* const Bp = sb_p + lane * kStageStr;
+            if (split) {  // integers only: where the two rows share a coordinate
+                const int32_t* Bc = sb_c + lane * kStageStr;
+                int i = 0, j = 0;
+                while (i < da && j < db) {
+                    const int32_t ca = Ac[i], cb = Bc[j];
+                    if (ca == cb) {
+                        sp_i[lane * kStageCap + nc] = (uint8_t)i;
+                        sp_j[lane * kStageCap + nc] = (uint8_t)j;
+                        ++nc;
+                    }
+                    i += ca <= cb ? 1 : 0;
+                    j += cb <= ca ? 1 : 0;
+                }
+            }
+            // one subtraction per common coordinate, |p_a - p_b| written over p_b
+            const int maxc = __reduce_max_sync(0xffffffffu, nc);
+            const PT* Ap = sa_p + (ra - abase);
+            for (int c = 0; c < maxc; ++c) {
+                if (c < nc) {
+                    const int i = sp_i[lane * kStageCap + c], j = sp_j[lane * kStageCap + c];
+                    Bp[j] = p_absdiff(Ap[i], Bp[j]);
+                }
+            }
+            n_sub += (uint32_t)nc;
+            __syncwarp();
+        }
+        if (split) {
+            // one addition per coordinate of the union: the term is p_a, p_b or the difference
+            // already in p_b's place (|x - 0| = x, so the bits equal the uniform step's)
+            const int32_t* Ac = sa_c + (ra - abase);
+            const PT* Ap = sa_p + (ra - abase);
+            const int32_t* Bc = sb_c + lane * kStageStr;
+            const PT* Bp = sb_p + lane * kStageStr;
+            int i = 0, j = 0;
+            int32_t ca = da > 0 ? Ac[0] : kEnd;
+            int32_t cb = db > 0 ? Bc[0] : kEnd;
+            PT s = PT(0);
+            bool mirror = false;
+            while (ca != kEnd || cb != kEnd) {
+                const bool ta = ca <= cb, tb = cb <= ca;
+                if (validate && tb && cb == a)
+                    mirror = weight_bits(w, wsize, rb + j) == weight_bits(w_und, wsize, e);
+                s = p_add(s, tb ? Bp[j] : Ap[i]);
+                ++n_add;
+                if (ta) { ++i; ca = i < da ? Ac[i] : kEnd; }
+                if (tb) { ++j; cb = j < db ? Bc[j] : kEnd; }
+            }
+            score[e] = key_bits(s);
+            asym = asym || (validate && !mirror);
+        } else if (act) {
+            if (hub) {  // hub edge: k_score_hub
                 if (validate && da <= kLongRow)
                     asym = asym || !has_mirror(col, w, wsize, rb, rb + db, a,
                                                weight_bits(w_und, wsize, e));
@@ -1137,8 +1216,8 @@ static spc_status score_typed(spc_context* ctx, GraphView& g, bool validate, voi
         if (validate) SPC_TRY(check_status(ctx));
         return SPC_OK;
     }
-    if (schedule != 1 && schedule != 2) {
-        // autotuned: both schedules compute the same bits; time each once per shape bucket
+    if (schedule != 1 && schedule != 2 && schedule != 3) {
+        // autotuned: every schedule computes the same bits; time each once per shape bucket
         int lg_deg = 0, lg_m = 0;
         while ((1ll << (lg_deg + 1)) <= (n > 0 ? nnz / n : 0)) ++lg_deg;
         while ((1ll << (lg_m + 1)) <= m) ++lg_m;

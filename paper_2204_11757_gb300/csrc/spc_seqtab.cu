@@ -24,47 +24,79 @@ namespace {
 constexpr int kChunk = 4096;
 constexpr int kCT = 256;  // threads of the chunk kernels (kChunk / kCT = 16 terms each)
 
-// min and max term bits of every sequence: flat over all terms (loff = exclusive prefix of the
-// lengths), reduced per warp when the warp's lanes share a sequence
+// min and max term bits of every sequence, flat over all terms (loff = exclusive prefix of the
+// lengths).  Each block takes one contiguous range of terms and each thread a strided part of
+// it, keeping a running min/max while its terms stay in one sequence; the threads' results are
+// combined per warp and per block, so a sequence of millions of terms costs one pair of
+// atomics per block instead of one per warp (the atomics of one address serialise).
 template <class F>
 __global__ void __launch_bounds__(kCT)
 k_seq_minmax(int64_t nseq, const F* __restrict__ terms, const int64_t* __restrict__ base,
              const int64_t* __restrict__ loff, unsigned long long* __restrict__ mn,
              unsigned long long* __restrict__ mx) {
     spc::pdl_wait();
+    __shared__ int64_t sh_q[kCT / 32];
+    __shared__ unsigned long long sh_mn[kCT / 32], sh_mx[kCT / 32];
     const int64_t total = loff[nseq];
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    const int64_t wbase = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) & ~(int64_t)31;
-    const int lane = threadIdx.x & 31;
-    for (int64_t b0 = wbase; b0 < total; b0 += stride) {
-        const int64_t f = b0 + lane;
-        int64_t q = -1;
-        unsigned long long v = 0;
-        if (f < total) {
-            int64_t lo = 0, hi = nseq - 1;
+    const int64_t per = ((total + gridDim.x - 1) / gridDim.x + kCT - 1) / kCT * kCT;
+    const int64_t r0 = (int64_t)blockIdx.x * per;
+    const int64_t r1 = r0 + per < total ? r0 + per : total;
+    int64_t q = -1;
+    unsigned long long a = ~0ull, b = 0ull;
+    for (int64_t f = r0 + threadIdx.x; f < r1; f += kCT) {
+        if (q < 0 || f >= loff[q + 1]) {  // entering another sequence
+            if (q >= 0) { atomicMin(mn + q, a); atomicMax(mx + q, b); }
+            int64_t lo = q < 0 ? 0 : q + 1, hi = nseq - 1;
             while (lo < hi) {
                 const int64_t mid = (lo + hi + 1) >> 1;
                 if (loff[mid] <= f) lo = mid; else hi = mid - 1;
             }
             q = lo;
-            v = FB<F>::bits(terms[base[q] + (f - loff[q])]);
+            a = ~0ull;
+            b = 0ull;
         }
-        const int64_t q0 = __shfl_sync(0xffffffffu, q, 0);
-        const bool same = __all_sync(0xffffffffu, q == q0);
-        if (same) {
-            unsigned long long a = v, b = v;
+        const unsigned long long v = FB<F>::bits(terms[base[q] + (f - loff[q])]);
+        a = v < a ? v : a;
+        b = v > b ? v : b;
+    }
+    // combine the warp when its lanes end in one sequence, then the block
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t q0 = __shfl_sync(0xffffffffu, q, 0);
+    const bool same = __all_sync(0xffffffffu, q == q0 || q < 0);
+    if (same) {
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                const unsigned long long x = __shfl_xor_sync(0xffffffffu, a, o);
-                const unsigned long long y = __shfl_xor_sync(0xffffffffu, b, o);
-                a = x < a ? x : a;
-                b = y > b ? y : b;
-            }
-            if (lane == 0) { atomicMin(mn + q0, a); atomicMax(mx + q0, b); }
-        } else if (q >= 0) {
-            atomicMin(mn + q, v);
-            atomicMax(mx + q, v);
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long x = __shfl_xor_sync(0xffffffffu, a, o);
+            const unsigned long long y = __shfl_xor_sync(0xffffffffu, b, o);
+            a = x < a ? x : a;
+            b = y > b ? y : b;
         }
+    } else if (q >= 0) {
+        atomicMin(mn + q, a);
+        atomicMax(mx + q, b);
+    }
+    if (lane == 0) {
+        sh_q[warp] = same ? q0 : -1;
+        sh_mn[warp] = a;
+        sh_mx[warp] = b;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int64_t cq = -1;
+        unsigned long long ca = ~0ull, cb = 0ull;
+        for (int w = 0; w < kCT / 32; ++w) {
+            const int64_t wq = sh_q[w];
+            if (wq < 0) continue;
+            if (wq != cq) {
+                if (cq >= 0) { atomicMin(mn + cq, ca); atomicMax(mx + cq, cb); }
+                cq = wq;
+                ca = ~0ull;
+                cb = 0ull;
+            }
+            ca = sh_mn[w] < ca ? sh_mn[w] : ca;
+            cb = sh_mx[w] > cb ? sh_mx[w] : cb;
+        }
+        if (cq >= 0) { atomicMin(mn + cq, ca); atomicMax(mx + cq, cb); }
     }
 }
 
@@ -380,17 +412,20 @@ k_fs_windows(int64_t nseq, const int64_t* __restrict__ len, const int64_t* __res
         const long long* C = cu + loff[q];
         const long long c0 = C[0];
         int64_t kmin = 0, kmax = L;  // steps k in [kmin, kmax]; empty when kmin > kmax
-        // Higham's gamma_L = L u / (1 - L u) bounds every prefix (|s_k - A_k| <= gamma A_k) while
-        // L u < 1; beyond that (binary32 sums of more than 2^24 / 5 terms) it bounds nothing and
-        // every window is the whole sequence
-        const double g = (double)L * (sizeof(F) == 8 ? 0x1p-53 : 0x1p-24);
-        const double gam = g < 0.2 ? g / (1.0 - g) : 1.0;
-        if (gam <= 0.25) {
+        // Every prefix of a left-to-right sum of non-negative terms with round-to-nearest
+        // satisfies (1 - u)^k A_k <= s_k <= (1 + u)^k A_k (each step multiplies by 1 + delta,
+        // |delta| <= u; by induction on k).  With the uniform factors of k = L the windows stay
+        // finite for any length (a binary32 sum of tens of millions of terms still gets narrow
+        // windows in its low binades).
+        const double lu = (double)L * log1p(sizeof(F) == 8 ? 0x1p-53 : 0x1p-24);
+        const double f_hi = exp(lu) * (1.0 + 0x1p-40);           // >= (1 + u)^L
+        const double f_lo = exp(-lu * (1.0 + 0x1p-20)) * (1.0 - 0x1p-40);  // <= (1 - u)^L
+        {
             constexpr int kBias = FB<F>::kBiasM - FB<F>::kMant;
             const int E2 = eblo[q] + e - kBias - gexp[q];  // binade [2^E2, 2^(E2+1)) in units
             constexpr double kCap = 0x1p62;
-            double lo_t = ldexp(1.0, E2) * (1.0 - gam) * (1.0 - 0x1p-40);
-            double hi_t = ldexp(1.0, E2 + 1) * (1.0 + 2.0 * gam) * (1.0 + 0x1p-40);
+            double lo_t = ldexp(1.0, E2) / f_hi * (1.0 - 0x1p-40);
+            double hi_t = ldexp(1.0, E2 + 1) / f_lo * (1.0 + 0x1p-40);
             lo_t = lo_t > kCap ? kCap : floor(lo_t);
             hi_t = hi_t > kCap ? kCap : ceil(hi_t);
             const long long thr_lo = (long long)lo_t, thr_hi = (long long)hi_t;
@@ -721,6 +756,8 @@ spc_status full_windowed(spc_context* ctx, const F* terms, int64_t nseq, const i
         SPC_TRY(ensure(ctx, tb.csum, (size_t)ntrip * 8 + 256));
         SPC_TRY(ensure(ctx, tb.ctie, (size_t)ntrip * 4 + 256));
         if (ntrip > 0) {
+            // every window position's term read once
+            note_bytes(ctx, (double)elems * sizeof(F));
             SPC_LAUNCH(ctx, k_fs_chunk_sums<F>, grid_for(ntrip, 1, maxb), kCT, 0, ntrip, npair,
                        tb.pcoff.as<int64_t>(), tb.pq.as<int32_t>(), tb.pe.as<int32_t>(),
                        tb.pw0.as<int64_t>(), tb.plen.as<int64_t>(), terms, base,
@@ -729,6 +766,9 @@ spc_status full_windowed(spc_context* ctx, const F* terms, int64_t nseq, const i
             SPC_LAUNCH(ctx, k_fs_chunk_scan, grid_for(npair, 64, maxb), 64, 0, npair,
                        tb.pcoff.as<int64_t>(), tb.csum.as<unsigned long long>(),
                        tb.ctie.as<int32_t>());
+            // every window position's term read once, its prefix (8 B) and tie count (4 B)
+            // written once
+            note_bytes(ctx, (double)elems * (sizeof(F) + 12));
             SPC_LAUNCH(ctx, k_fs_chunk_write<F>, grid_for(ntrip, 1, maxb), kCT, 0, ntrip, npair,
                        tb.pcoff.as<int64_t>(), tb.pq.as<int32_t>(), tb.pe.as<int32_t>(),
                        tb.pw0.as<int64_t>(), tb.plen.as<int64_t>(), tb.ptoff.as<int64_t>(), terms,
