@@ -118,7 +118,7 @@ struct Work {
     Buf dg_rowptr, dg_col, dg_w, dg_pos;
     // adjacency reordering: distances, frontiers, the renumbering and the renumbered CSR
     Buf ro_dist, ro_key, ro_val, ro_key2, ro_val2, ro_perm, ro_deg;
-    Buf ro_rowptr, ro_col, ro_w, ro_lkey, ro_lkey2, ro_lval, ro_lval2, ro_head, ro_lift;
+    Buf ro_rowptr, ro_col, ro_w, ro_lkey, ro_lkey2, ro_lval, ro_lval2, ro_head, ro_lift, ro_bar;
 };
 
 struct Timer {

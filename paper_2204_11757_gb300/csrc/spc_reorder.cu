@@ -17,6 +17,7 @@ namespace {
 
 constexpr int32_t kUnreached = 0x7fffffff;
 constexpr int kShortRow = 32;  // rows ranked in registers; longer rows by a radix sort
+constexpr int kBarGen = 32;    // the grid barrier's generation word, 128 bytes past its counter
 
 __global__ void __launch_bounds__(kThreads)
 k_bfs_init(int64_t n, int32_t* __restrict__ dist, int32_t* __restrict__ flags,
@@ -30,29 +31,32 @@ k_bfs_init(int64_t n, int32_t* __restrict__ dist, int32_t* __restrict__ flags,
         flags[1] = 0;
         flags[2] = 0;
         bar[0] = 0u;
-        bar[1] = 0u;
+        bar[kBarGen] = 0u;
     }
 }
 
 // Grid-wide barrier of a cooperative launch (every block resident, so every wait ends); the
 // waits are bounded by the context's wait limit all the same.  bar[0] counts the blocks that
-// arrived, bar[1] is the generation.  Returns false (and sets DEV_TIMEOUT) when a wait gave up.
+// arrived, bar[kBarGen] (another 128-byte line, so the pollers do not contend with the
+// arrivals) is the generation; the pollers back off between reads.  Returns false (and sets
+// DEV_TIMEOUT) when a wait gave up.
 __device__ bool grid_barrier(unsigned* bar, uint32_t* status) {
     __shared__ int sh_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
-        volatile unsigned* gen = bar + 1;
+        volatile unsigned* gen = bar + kBarGen;
         const unsigned g = *gen;
         __threadfence();
         int ok = 1;
         if (atomicAdd(bar, 1u) + 1u == gridDim.x) {
             bar[0] = 0u;
             __threadfence();
-            atomicAdd(bar + 1, 1u);
+            atomicAdd(bar + kBarGen, 1u);
         } else {
             const uint32_t lim = spin_limit(status);
             uint32_t spins = 0;
             while (*gen == g) {
+                __nanosleep(32);
                 if (++spins > lim) {
                     atomicOr(status, DEV_TIMEOUT);
                     ok = 0;
@@ -374,7 +378,8 @@ spc_status reorder_typed(spc_context* ctx, const GraphView& g, GraphView& out) {
     out = g;
     if (n == 0) return SPC_OK;
     // ---- breadth-first levels from node 0, all in one cooperative launch ----------------------
-    unsigned* bar = reinterpret_cast<unsigned*>(W.counters.as<int32_t>() + 60);  // [60], [61]
+    SPC_TRY(ensure(ctx, W.ro_bar, 256));
+    unsigned* bar = W.ro_bar.as<unsigned>();
     int32_t* levels = W.counters.as<int32_t>() + 62;
     SPC_LAUNCH(ctx, k_bfs_init, gn, kThreads, 0, n, dist, flags, bar);
     SPC_TRY(launch_bfs_all(ctx, g, dist, flags, bar, levels));

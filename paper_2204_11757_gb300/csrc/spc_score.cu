@@ -335,6 +335,56 @@ k_rows_edges(int64_t n, const int64_t* __restrict__ rowptr, const int32_t* __res
     }
 }
 
+// S2 (+ the edge list) for binary32 weights, flat over the stored entries: each block takes
+// kFlatTile consecutive entries and narrows their rows with two searches, so the columns,
+// weights and p values of a warp are consecutive (the row-per-thread kernel reads 32 rows at
+// once).  p = w / d is one IEEE division per entry, exactly as k_rows_edges computes it.
+// Rows longer than kLongRow are left to k_long_rows_edges.
+constexpr int64_t kFlatTile = 2048;
+
+__device__ __forceinline__ int64_t row_of(const int64_t* __restrict__ rowptr, int64_t lo,
+                                          int64_t hi, int64_t j) {
+    while (lo < hi) {  // the last row x in [lo, hi] with rowptr[x] <= j
+        const int64_t mid = (lo + hi + 1) >> 1;
+        if (rowptr[mid] <= j) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__global__ void __launch_bounds__(kThreads)
+k_rows_edges_flat(int64_t n, int64_t nnz, const int64_t* __restrict__ rowptr,
+                  const int32_t* __restrict__ col, const float* __restrict__ w,
+                  const float* __restrict__ deg, const int32_t* __restrict__ nlow,
+                  const int32_t* __restrict__ up_ptr, float* __restrict__ p,
+                  int32_t* __restrict__ eu, int32_t* __restrict__ ev, float* __restrict__ w_und,
+                  const uint32_t* status) {
+    spc::pdl_wait();
+    if (*status) return;  // invalid input: nothing below may index with it
+    __shared__ int64_t s_rows[2];
+    for (int64_t base = (int64_t)blockIdx.x * kFlatTile; base < nnz;
+         base += (int64_t)gridDim.x * kFlatTile) {
+        const int64_t last = (base + kFlatTile < nnz ? base + kFlatTile : nnz) - 1;
+        if (threadIdx.x < 2) s_rows[threadIdx.x] = row_of(rowptr, 0, n - 1, threadIdx.x ? last : base);
+        __syncthreads();
+        const int64_t r_lo = s_rows[0], r_hi = s_rows[1];
+        for (int64_t j = base + threadIdx.x; j <= last; j += blockDim.x) {
+            const int64_t x = row_of(rowptr, r_lo, r_hi, j);
+            const int64_t r0 = rowptr[x];
+            if (rowptr[x + 1] - r0 > kLongRow) continue;  // k_long_rows_edges
+            const int32_t y = col[j];
+            const float wj = w[j];
+            p[j] = __fdiv_rn(wj, deg[x]);
+            if ((int64_t)y > x) {
+                const int64_t e = (int64_t)up_ptr[x] + (j - (r0 + nlow[x]));
+                eu[e] = (int32_t)x;
+                ev[e] = y;
+                w_und[e] = wj;
+            }
+        }
+        __syncthreads();
+    }
+}
+
 // Arithmetic count of a score launch, for the roofline: ops[0] += additions into the running
 // sums (one per union coordinate), ops[1] += subtractions (one per coordinate present in both
 // rows).  One atomic per warp; every lane of the block reaches it.
@@ -1207,10 +1257,25 @@ static spc_status score_typed(spc_context* ctx, GraphView& g, bool validate, voi
                        W.ev.as<int32_t>(), W.w_und.as<WT>(), status);
             side->leave();
         }
-        SPC_LAUNCH(ctx, k_rows_edges<WT>, gb, kThreads, 0, n, g.rowptr, g.col,
-                   static_cast<const WT*>(g.w), mirror_here ? 1 : 0, W.deg.as<Acc>(),
-                   W.first_up.as<int32_t>(), W.up_ptr.as<int32_t>(), W.p.as<P>(),
-                   W.eu.as<int32_t>(), W.ev.as<int32_t>(), W.w_und.as<WT>(), status);
+        if constexpr (std::is_same<WT, float>::value) {
+            if (!mirror_here && n > 0) {
+                SPC_LAUNCH(ctx, k_rows_edges_flat, grid_for(nnz, (int)kFlatTile, maxb), kThreads,
+                           0, n, nnz, g.rowptr, g.col, static_cast<const float*>(g.w),
+                           W.deg.as<float>(), W.first_up.as<int32_t>(), W.up_ptr.as<int32_t>(),
+                           W.p.as<float>(), W.eu.as<int32_t>(), W.ev.as<int32_t>(),
+                           W.w_und.as<float>(), status);
+            } else {
+                SPC_LAUNCH(ctx, k_rows_edges<WT>, gb, kThreads, 0, n, g.rowptr, g.col,
+                           static_cast<const WT*>(g.w), mirror_here ? 1 : 0, W.deg.as<Acc>(),
+                           W.first_up.as<int32_t>(), W.up_ptr.as<int32_t>(), W.p.as<P>(),
+                           W.eu.as<int32_t>(), W.ev.as<int32_t>(), W.w_und.as<WT>(), status);
+            }
+        } else {
+            SPC_LAUNCH(ctx, k_rows_edges<WT>, gb, kThreads, 0, n, g.rowptr, g.col,
+                       static_cast<const WT*>(g.w), mirror_here ? 1 : 0, W.deg.as<Acc>(),
+                       W.first_up.as<int32_t>(), W.up_ptr.as<int32_t>(), W.p.as<P>(),
+                       W.eu.as<int32_t>(), W.ev.as<int32_t>(), W.w_und.as<WT>(), status);
+        }
     }  // the main stream waits for the long rows here
     if (score == nullptr || m == 0) {
         if (validate) SPC_TRY(check_status(ctx));

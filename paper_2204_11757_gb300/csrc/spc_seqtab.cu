@@ -512,21 +512,58 @@ k_fs_chunk_sums(int64_t ntrip, int64_t npair, const int64_t* __restrict__ pcoff,
 }
 
 // exclusive scan of every window's chunk sums, in place (one thread per pair)
-__global__ void k_fs_chunk_scan(int64_t npair, const int64_t* __restrict__ pcoff,
-                                unsigned long long* __restrict__ csum, int32_t* __restrict__ ctie) {
+// one block per pair: each thread takes a contiguous run of the pair's chunks, sums it, a
+// block scan (saturating for the unit sums) gives every run its start, and each thread writes
+// its chunks' exclusive prefixes.  (One thread per pair walked a 50M-term sum's 12,000 chunks
+// per binade one dependent step at a time.)
+constexpr int kChunkScanThreads = 256;
+
+__global__ void __launch_bounds__(kChunkScanThreads)
+k_fs_chunk_scan(int64_t npair, const int64_t* __restrict__ pcoff,
+                unsigned long long* __restrict__ csum, int32_t* __restrict__ ctie) {
     spc::pdl_wait();
-    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < npair;
-         r += (int64_t)gridDim.x * blockDim.x) {
-        unsigned long long run = 0;
-        int32_t tr = 0;
-        for (int64_t c = pcoff[r]; c < pcoff[r + 1]; ++c) {
-            const unsigned long long v = csum[c];
-            const int32_t tv = ctie[c];
+    __shared__ unsigned long long sh_v[kChunkScanThreads / 32];
+    __shared__ int32_t sh_t[kChunkScanThreads / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int64_t r = blockIdx.x; r < npair; r += gridDim.x) {
+        const int64_t c0 = pcoff[r], len = pcoff[r + 1] - c0;
+        const int64_t K = (len + kChunkScanThreads - 1) / kChunkScanThreads;
+        const int64_t a = c0 + (int64_t)threadIdx.x * K;
+        const int64_t b = a + K < c0 + len ? a + K : c0 + len;
+        unsigned long long v = 0;
+        int32_t tv = 0;
+        for (int64_t c = a; c < b; ++c) {
+            v = sat_add(v, csum[c]);
+            tv += ctie[c];
+        }
+        // inclusive warp scan, then the warp totals
+        unsigned long long iv = v;
+        int32_t it = tv;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long u = __shfl_up_sync(0xffffffffu, iv, o);
+            const int32_t t = __shfl_up_sync(0xffffffffu, it, o);
+            if (lane >= o) { iv = sat_add(iv, u); it += t; }
+        }
+        if (lane == 31) { sh_v[warp] = iv; sh_t[warp] = it; }
+        __syncthreads();
+        unsigned long long wv = 0;
+        int32_t wt = 0;
+        for (int w = 0; w < warp; ++w) { wv = sat_add(wv, sh_v[w]); wt += sh_t[w]; }
+        unsigned long long ev = __shfl_up_sync(0xffffffffu, iv, 1);
+        int32_t et = __shfl_up_sync(0xffffffffu, it, 1);
+        if (lane == 0) { ev = 0ull; et = 0; }
+        unsigned long long run = sat_add(wv, ev);
+        int32_t tr = wt + et;
+        for (int64_t c = a; c < b; ++c) {
+            const unsigned long long x = csum[c];
+            const int32_t tx = ctie[c];
             csum[c] = run;
             ctie[c] = tr;
-            run = sat_add(run, v);
-            tr += tv;
+            run = sat_add(run, x);
+            tr += tx;
         }
+        __syncthreads();  // sh_v / sh_t are rewritten for the next pair
     }
 }
 
@@ -763,7 +800,7 @@ spc_status full_windowed(spc_context* ctx, const F* terms, int64_t nseq, const i
                        tb.pw0.as<int64_t>(), tb.plen.as<int64_t>(), terms, base,
                        tb.eblo.as<int32_t>(), tb.csum.as<unsigned long long>(),
                        tb.ctie.as<int32_t>());
-            SPC_LAUNCH(ctx, k_fs_chunk_scan, grid_for(npair, 64, maxb), 64, 0, npair,
+            SPC_LAUNCH(ctx, k_fs_chunk_scan, grid_for(npair, 1, maxb), kChunkScanThreads, 0, npair,
                        tb.pcoff.as<int64_t>(), tb.csum.as<unsigned long long>(),
                        tb.ctie.as<int32_t>());
             // every window position's term read once, its prefix (8 B) and tie count (4 B)
