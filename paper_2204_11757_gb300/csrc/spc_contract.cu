@@ -96,12 +96,15 @@ __device__ __forceinline__ void warp_count(int32_t* cnt, int32_t key, bool act) 
 }
 
 // Buckets of at most kSmallBucket items: each item is ranked by one thread (at most
-// kSmallBucket comparisons per item).  Longer ones, up to kBlockBucket items: one CTA sorts the
-// bucket in shared memory (bitonic network); they are listed by the scan of
-// the bucket sizes.
+// kSmallBucket comparisons per item).  Longer ones are listed by the scan of the bucket sizes:
+// up to kWarpBucket items, one warp ranks the bucket's items by comparison in shared memory;
+// up to kBlockBucket items, one CTA sorts the bucket in shared memory (bitonic network).
 constexpr int kSmallBucket = 64;
+constexpr int kWarpBucket = 256;
 constexpr int kBlockBucket = 8192;
 constexpr int kBlockSortThreads = 512;
+static_assert((kBlockSortThreads / 32) * kWarpBucket <= kBlockBucket,
+              "the warps' stages share the CTA's");
 
 // scan storer of the two packed bucket sizes (spc_scan.cuh PairLd: inter, intra): both
 // exclusive prefixes and totals, and per side the ranking statistics -- sum of squared sizes in
@@ -295,13 +298,54 @@ k_bucket_scatter(int64_t m, int nb, const int32_t* __restrict__ eu,
     }
 }
 
-// Step 3, long buckets (listed by the scan of the sizes): one CTA per bucket sorts the bucket's
-// items in shared memory by one 64-bit key -- (b << 32) | eid for inter edges (a is the
-// bucket), the eid for intra edges -- with a bitonic network over the next power of two
-// (padding keys all ones), then writes them back in order: inter edges as (key, eid) with
-// their head flags, intra edges as eids.
+// warp sort of the items of one bucket (at most kWarpBucket, in sk[0, s)) by ranking: every
+// item's rank is the number of smaller keys of the bucket (all distinct: they hold the eid).
+// Each lane keeps its items (lane, lane + 32, ...) in registers and every key is read once per
+// warp (a broadcast) and compared with all of them; the items then move to their ranks in the
+// stage and leave it in order, with the head flag of every coarse edge's first item.
+template <bool kInter, int kPer>
+__device__ __forceinline__ void warp_sort_bucket(unsigned long long* sk, int s, int lane,
+                                                 int32_t bkt, int32_t lo, int nb,
+                                                 uint64_t* __restrict__ key2,
+                                                 uint32_t* __restrict__ val2,
+                                                 uint8_t* __restrict__ head) {
+    unsigned long long k[kPer];
+    int r[kPer];
+#pragma unroll
+    for (int t = 0; t < kPer; ++t) {
+        const int i = lane + 32 * t;
+        k[t] = i < s ? sk[i] : ~0ull;
+        r[t] = 0;
+    }
+    for (int j = 0; j < s; ++j) {
+        const unsigned long long x = sk[j];
+#pragma unroll
+        for (int t = 0; t < kPer; ++t) r[t] += x < k[t] ? 1 : 0;
+    }
+    __syncwarp();  // every key is read: the stage takes the sorted order
+#pragma unroll
+    for (int t = 0; t < kPer; ++t)
+        if (lane + 32 * t < s) sk[r[t]] = k[t];
+    __syncwarp();
+    for (int i = lane; i < s; i += 32) {
+        const unsigned long long x = sk[i];
+        if constexpr (kInter) {
+            key2[lo + i] = ((uint64_t)bkt << nb) | (x >> 32);
+            val2[lo + i] = (uint32_t)x;
+            head[lo + i] = (i == 0 || (sk[i - 1] >> 32) != (x >> 32)) ? 1 : 0;
+        } else {
+            val2[lo + i] = (uint32_t)x;
+        }
+    }
+}
+
+// Step 3, long buckets (listed by the scan of the sizes), sorted by one 64-bit key -- (b << 32)
+// | eid for inter edges (a is the bucket), the eid for intra edges -- and written back in
+// order: inter edges as (key, eid) with their head flags, intra edges as eids.  Buckets of more
+// than kWarpBucket items: one CTA each, a bitonic network over the next power of two (padding
+// keys all ones) in shared memory.  The others: one warp each (warp_sort_bucket).
 template <bool kInter>
-__global__ void __launch_bounds__(kBlockSortThreads)
+__global__ void __launch_bounds__(kBlockSortThreads, 3)
 k_bucket_sort_long(const int32_t* __restrict__ list, const unsigned long long* __restrict__ list_cnt,
                    const int32_t* __restrict__ off, int nb, const uint64_t* __restrict__ key,
                    const uint32_t* __restrict__ val, uint64_t* __restrict__ key2,
@@ -314,6 +358,7 @@ k_bucket_sort_long(const int32_t* __restrict__ list, const unsigned long long* _
         const int32_t bkt = list[q];
         const int32_t lo = off[bkt];
         const int s = off[bkt + 1] - lo;  // kSmallBucket < s <= kBlockBucket (host checked)
+        if (s <= kWarpBucket) continue;   // a warp's bucket (below)
         int P = 1;
         while (P < s) P <<= 1;
         for (int i = threadIdx.x; i < P; i += blockDim.x) {
@@ -351,6 +396,26 @@ k_bucket_sort_long(const int32_t* __restrict__ list, const unsigned long long* _
             }
         }
         __syncthreads();
+    }
+    // buckets of at most kWarpBucket items, one warp each, in the warp's part of the stage
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    unsigned long long* wk = sk + (size_t)wib * kWarpBucket;
+    for (int64_t q = (int64_t)blockIdx.x * (blockDim.x >> 5) + wib; q < cnt; q += nwarps) {
+        const int32_t bkt = list[q];
+        const int32_t lo = off[bkt];
+        const int s = off[bkt + 1] - lo;
+        if (s > kWarpBucket) continue;  // a CTA's bucket (above)
+        for (int i = lane; i < s; i += 32) {
+            if constexpr (kInter) wk[i] = ((key[lo + i] & bmask) << 32) | val[lo + i];
+            else wk[i] = val[lo + i];
+        }
+        __syncwarp();
+        if (s <= 128)
+            warp_sort_bucket<kInter, 4>(wk, s, lane, bkt, lo, nb, key2, val2, head);
+        else
+            warp_sort_bucket<kInter, 8>(wk, s, lane, bkt, lo, nb, key2, val2, head);
+        __syncwarp();  // the next bucket overwrites the stage
     }
 }
 
@@ -1079,19 +1144,9 @@ struct DiagSt {
     }
 };
 
-// the last row x with rowptr[x] <= j among rows [lo, hi] (the row holding entry j)
-__device__ __forceinline__ int64_t row_of_entry(const int64_t* __restrict__ rowptr, int64_t lo,
-                                                int64_t hi, int64_t j) {
-    while (lo < hi) {
-        const int64_t mid = (lo + hi + 1) >> 1;
-        if (rowptr[mid] <= j) lo = mid; else hi = mid - 1;
-    }
-    return lo;
-}
-
 // every stored entry moves up by the diagonal entries before it: those of the rows above its
 // row, and its own row's when the entry's column is above the diagonal.  Each block takes
-// kDiagTile consecutive entries and first narrows their rows with two searches.
+// kDiagTile consecutive entries and marks their rows in shared memory (tile_rows).
 constexpr int64_t kDiagTile = 2048;
 
 template <class WT>
@@ -1102,15 +1157,13 @@ k_diag_entries(int64_t n, int64_t nnz, const int64_t* __restrict__ rowptr,
                WT* __restrict__ w_d) {
     spc::pdl_wait();
     __shared__ int64_t s_rows[2];
+    __shared__ int32_t s_row[kDiagTile];
     for (int64_t base = (int64_t)blockIdx.x * kDiagTile; base < nnz;
          base += (int64_t)gridDim.x * kDiagTile) {
-        const int64_t last = (base + kDiagTile < nnz ? base + kDiagTile : nnz) - 1;
-        if (threadIdx.x < 2)
-            s_rows[threadIdx.x] = row_of_entry(rowptr, 0, n - 1, threadIdx.x ? last : base);
-        __syncthreads();
-        const int64_t r_lo = s_rows[0], r_hi = s_rows[1];
-        for (int64_t j = base + threadIdx.x; j <= last; j += blockDim.x) {
-            const int64_t x = row_of_entry(rowptr, r_lo, r_hi, j);
+        const int64_t end = base + kDiagTile < nnz ? base + kDiagTile : nnz;
+        const int64_t r_lo = tile_rows(rowptr, n, base, end, -1, s_row, s_rows);
+        for (int64_t j = base + threadIdx.x; j < end; j += blockDim.x) {
+            const int64_t x = r_lo + s_row[j - base];
             const int32_t y = col[j];
             const int32_t p0 = pos[x];
             const int64_t d = (int64_t)p0 + ((pos[x + 1] > p0 && (int64_t)y > x) ? 1 : 0);

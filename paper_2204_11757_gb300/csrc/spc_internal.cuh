@@ -89,6 +89,7 @@ struct SeqTabBufs {
 // Work buffers shared by all levels (sized for level 0).
 struct Work {
     Buf up_cnt, up_ptr, first_up, eu, ev, w_und, deg, p;       // S0-S2
+    Buf pk;                                                     // binary32 (column, p) pairs
     Buf long_rows, lr_base, lr_len, lr_idx, lr_eoff, heavy, seg_base, seg_len, seg_idx, seg_terms;
     Buf hub_leaf;                                               // per hub: its leaf edges' score
     Buf hub_map, hub_slot;                                      // column maps of the largest hubs
@@ -276,6 +277,39 @@ __device__ __forceinline__ void pdl_wait() {
 #if defined(__CUDA_ARCH__) && __CUDA_ARCH__ >= 900
     asm volatile("griddepcontrol.wait;" ::: "memory");
 #endif
+}
+
+// The rows of a tile of consecutive CSR entries [base, end), for kernels that run flat over the
+// stored entries: every thread of the block calls it (it synchronises the block).  Two searches
+// find the first row r_lo and the last row of the tile; one thread per row then marks the row
+// of each of its entries, s_row[j - base] = row - r_lo, or -1 for a row of more than
+// `long_row` entries (long_row < 0: no limit).  Returns r_lo.  Rows spanned by a tile are
+// visited by that tile alone (neighbouring tiles share at most one row), so the marking is
+// O(rows + entries) over the whole array.
+__device__ __forceinline__ int64_t csr_last_row_at(const int64_t* __restrict__ rowptr, int64_t lo,
+                                                   int64_t hi, int64_t j) {
+    while (lo < hi) {  // the last row x in [lo, hi] with rowptr[x] <= j
+        const int64_t mid = (lo + hi + 1) >> 1;
+        if (rowptr[mid] <= j) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ int64_t tile_rows(const int64_t* __restrict__ rowptr, int64_t n,
+                                             int64_t base, int64_t end, int64_t long_row,
+                                             int32_t* s_row, int64_t* s_rows) {
+    if (threadIdx.x < 2)
+        s_rows[threadIdx.x] = csr_last_row_at(rowptr, 0, n - 1, threadIdx.x ? end - 1 : base);
+    __syncthreads();
+    const int64_t r_lo = s_rows[0], r_hi = s_rows[1];
+    for (int64_t x = r_lo + threadIdx.x; x <= r_hi; x += blockDim.x) {
+        const int64_t r0 = rowptr[x], r1 = rowptr[x + 1];
+        const int32_t mark = (long_row >= 0 && r1 - r0 > long_row) ? -1 : (int32_t)(x - r_lo);
+        for (int64_t j = r0 > base ? r0 : base; j < (r1 < end ? r1 : end); ++j)
+            s_row[j - base] = mark;
+    }
+    __syncthreads();
+    return r_lo;
 }
 
 template <typename... Params, typename... Args>

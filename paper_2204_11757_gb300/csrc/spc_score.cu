@@ -336,46 +336,39 @@ k_rows_edges(int64_t n, const int64_t* __restrict__ rowptr, const int32_t* __res
 }
 
 // S2 (+ the edge list) for binary32 weights, flat over the stored entries: each block takes
-// kFlatTile consecutive entries and narrows their rows with two searches, so the columns,
-// weights and p values of a warp are consecutive (the row-per-thread kernel reads 32 rows at
-// once).  p = w / d is one IEEE division per entry, exactly as k_rows_edges computes it.
-// Rows longer than kLongRow are left to k_long_rows_edges.
+// kFlatTile consecutive entries and marks the row of each in shared memory (tile_rows), so the
+// columns, weights and p values of a warp are consecutive (the row-per-thread kernel reads 32
+// rows at once).  p = w / d is one IEEE division per entry, exactly as k_rows_edges computes
+// it.  `p` (may be null) receives p alone, `pk` the (column, p) pair of every entry.  Rows
+// longer than kLongRow are left to k_long_rows_edges.
 constexpr int64_t kFlatTile = 2048;
-
-__device__ __forceinline__ int64_t row_of(const int64_t* __restrict__ rowptr, int64_t lo,
-                                          int64_t hi, int64_t j) {
-    while (lo < hi) {  // the last row x in [lo, hi] with rowptr[x] <= j
-        const int64_t mid = (lo + hi + 1) >> 1;
-        if (rowptr[mid] <= j) lo = mid; else hi = mid - 1;
-    }
-    return lo;
-}
 
 __global__ void __launch_bounds__(kThreads)
 k_rows_edges_flat(int64_t n, int64_t nnz, const int64_t* __restrict__ rowptr,
                   const int32_t* __restrict__ col, const float* __restrict__ w,
                   const float* __restrict__ deg, const int32_t* __restrict__ nlow,
                   const int32_t* __restrict__ up_ptr, float* __restrict__ p,
-                  int32_t* __restrict__ eu, int32_t* __restrict__ ev, float* __restrict__ w_und,
-                  const uint32_t* status) {
+                  uint2* __restrict__ pk, int32_t* __restrict__ eu, int32_t* __restrict__ ev,
+                  float* __restrict__ w_und, const uint32_t* status) {
     spc::pdl_wait();
     if (*status) return;  // invalid input: nothing below may index with it
     __shared__ int64_t s_rows[2];
+    __shared__ int32_t s_row[kFlatTile];  // row of each entry of the tile minus the first row
     for (int64_t base = (int64_t)blockIdx.x * kFlatTile; base < nnz;
          base += (int64_t)gridDim.x * kFlatTile) {
-        const int64_t last = (base + kFlatTile < nnz ? base + kFlatTile : nnz) - 1;
-        if (threadIdx.x < 2) s_rows[threadIdx.x] = row_of(rowptr, 0, n - 1, threadIdx.x ? last : base);
-        __syncthreads();
-        const int64_t r_lo = s_rows[0], r_hi = s_rows[1];
-        for (int64_t j = base + threadIdx.x; j <= last; j += blockDim.x) {
-            const int64_t x = row_of(rowptr, r_lo, r_hi, j);
-            const int64_t r0 = rowptr[x];
-            if (rowptr[x + 1] - r0 > kLongRow) continue;  // k_long_rows_edges
+        const int64_t end = base + kFlatTile < nnz ? base + kFlatTile : nnz;
+        const int64_t r_lo = tile_rows(rowptr, n, base, end, kLongRow, s_row, s_rows);
+        for (int64_t j = base + threadIdx.x; j < end; j += blockDim.x) {
+            const int32_t rel = s_row[j - base];
+            if (rel < 0) continue;  // k_long_rows_edges
+            const int64_t x = r_lo + rel;
             const int32_t y = col[j];
             const float wj = w[j];
-            p[j] = __fdiv_rn(wj, deg[x]);
+            const float pj = __fdiv_rn(wj, deg[x]);
+            if (p) p[j] = pj;
+            pk[j] = make_uint2((uint32_t)y, __float_as_uint(pj));
             if ((int64_t)y > x) {
-                const int64_t e = (int64_t)up_ptr[x] + (j - (r0 + nlow[x]));
+                const int64_t e = (int64_t)up_ptr[x] + (j - (rowptr[x] + nlow[x]));
                 eu[e] = (int32_t)x;
                 ev[e] = y;
                 w_und[e] = wj;
@@ -799,6 +792,132 @@ k_score_staged(int64_t m, const int32_t* __restrict__ eu, const int32_t* __restr
     count_ops(ops, n_add, n_sub);
 }
 
+// S3, packed schedule for binary32 rows: the normalise kernel stores every entry as one 8-byte
+// (column, p) pair, so a row is one contiguous run of bytes.  A warp takes 32 consecutive
+// edges (one lane each): the tile's rows a, one contiguous slice, are copied by the whole warp,
+// and every lane copies its own row b into the warp's area, the rows packed one after the other
+// (a prefix sum of their lengths places them), all with 16-byte asynchronous copies.  A copy
+// keeps each entry's position modulo two entries, so both of its ends are 16-byte aligned; a
+// row that starts or ends inside a 16-byte chunk brings its neighbour along, never read.  Then
+// every lane walks its edge's union from shared memory, one 8-byte load per step, with the
+// uniform step of k_score_edges (the same bits).  Rows that do not fit are walked in place.
+constexpr int kPkWarps = 8;
+constexpr int kPkA = 192;  // entries of the tile's row-a slice staged per warp
+constexpr int kPkB = 576;  // entries of the tile's 32 rows b staged per warp
+constexpr int kPkRegion = kPkA + kPkB;
+constexpr size_t kPkSmem = (size_t)kPkWarps * kPkRegion * sizeof(uint2);
+
+// L2 eviction priority (createpolicy, sm_80 and later): the row pointers, read at random once
+// per edge endpoint, are kept in L2 ahead of the rows, which are far larger than L2 on big graphs.
+__device__ __forceinline__ uint64_t l2_policy_evict_last() {
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+__device__ __forceinline__ int64_t ld_l2hint(const int64_t* ptr, uint64_t pol) {
+    int64_t v;
+    asm volatile("ld.global.nc.L2::cache_hint.s64 %0, [%1], %2;" : "=l"(v) : "l"(ptr), "l"(pol));
+    return v;
+}
+__device__ __forceinline__ void cp_async_16(void* smem, const void* gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem) : "memory");
+}
+
+template <class KT>
+__global__ void __launch_bounds__(kPkWarps * 32)
+k_score_packed(int64_t m, const int32_t* __restrict__ eu, const int32_t* __restrict__ ev,
+               const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+               const uint2* __restrict__ pk, KT* __restrict__ score, const void* __restrict__ w,
+               const void* __restrict__ w_und, int wsize, int validate, uint32_t* status,
+               unsigned long long* __restrict__ ops) {
+    spc::pdl_wait();
+    if (*status) return;
+    extern __shared__ __align__(16) uint2 pk_stage[];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    uint2* const sa = pk_stage + (size_t)wib * kPkRegion;
+    uint2* const sb = sa + kPkA;
+    const uint4* const pk16 = reinterpret_cast<const uint4*>(pk);
+    constexpr int32_t kEnd = 0x7fffffff;
+    const uint2 kEndPair = make_uint2((uint32_t)kEnd, 0u);
+    uint32_t n_add = 0, n_sub = 0;
+    bool asym = false;
+    const uint64_t keep = l2_policy_evict_last();
+    const int64_t step_e = (int64_t)gridDim.x * kPkWarps * 32;
+    for (int64_t e0 = ((int64_t)blockIdx.x * kPkWarps + wib) * 32; e0 < m; e0 += step_e) {
+        const int64_t e = e0 + lane;
+        const bool act = e < m;
+        int32_t a = 0;
+        int64_t ra = 0, da = 0, rb = 0, db = 0;
+        if (act) {
+            a = eu[e];
+            const int32_t b = ev[e];
+            ra = ld_l2hint(rowptr + a, keep);
+            da = ld_l2hint(rowptr + a + 1, keep) - ra;
+            rb = ld_l2hint(rowptr + b, keep);
+            db = ld_l2hint(rowptr + b + 1, keep) - rb;
+        }
+        const bool hub = act && (da > kLongRow || db > kLongRow);
+        // the rows a of the tile: entries [rowptr[a of lane 0], rowptr[a of the last lane + 1]),
+        // as 16-byte chunks [ac0, ac1)
+        const int lastl = (int)((m - e0 < 32 ? m - e0 : 32) - 1);
+        const int64_t ac0 = __shfl_sync(0xffffffffu, ra, 0) >> 1;
+        const int64_t ac1 = (__shfl_sync(0xffffffffu, ra + da, lastl) + 1) >> 1;
+        const bool a_staged = 2 * (ac1 - ac0) <= kPkA;
+        if (a_staged)
+            for (int64_t q = ac0 + lane; q < ac1; q += 32)
+                cp_async_16(sa + 2 * (q - ac0), pk16 + q);
+        // this lane's row b: chunks [rb / 2, (rb + db + 1) / 2), placed after the other lanes'
+        const int64_t bc0 = rb >> 1;
+        const int nch = (act && !hub && db > 0) ? (int)(((rb + db + 1) >> 1) - bc0) : 0;
+        int choff = nch;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, choff, d);
+            if (lane >= d) choff += t;
+        }
+        choff -= nch;
+        const bool b_staged = 2 * (choff + nch) <= kPkB;
+        const int maxch = __reduce_max_sync(0xffffffffu, b_staged ? nch : 0);
+        for (int k = 0; k < maxch; ++k)
+            if (b_staged && k < nch) cp_async_16(sb + 2 * (choff + k), pk16 + bc0 + k);
+        cp_async_wait_all();
+        __syncwarp();
+        if (act && !hub) {
+            const uint2* A = a_staged ? sa + (ra - 2 * ac0) : pk + ra;
+            const uint2* B = b_staged ? sb + 2 * choff + (rb & 1) : pk + rb;
+            const int na = (int)da, nb = (int)db;
+            int i = 0, j = 0, jm = -1;
+            uint2 xa = na > 0 ? A[0] : kEndPair;
+            uint2 xb = nb > 0 ? B[0] : kEndPair;
+            float s = 0.f;
+            for (;;) {
+                const int32_t ca = (int32_t)xa.x, cb = (int32_t)xb.x;
+                if (ca == kEnd && cb == kEnd) break;
+                const bool ta = ca <= cb, tb = cb <= ca;
+                jm = (tb && cb == a) ? j : jm;  // the mirror entry (b, a)
+                const float pa = ta ? __uint_as_float(xa.y) : 0.f;
+                const float pb = tb ? __uint_as_float(xb.y) : 0.f;
+                s = p_add(s, p_absdiff(pa, pb));
+                ++n_add;
+                n_sub += (ta && tb) ? 1u : 0u;
+                if (ta) { ++i; xa = i < na ? A[i] : kEndPair; }
+                if (tb) { ++j; xb = j < nb ? B[j] : kEndPair; }
+            }
+            score[e] = key_bits(s);
+            if (validate)
+                asym = asym || jm < 0 ||
+                       weight_bits(w, wsize, rb + jm) != weight_bits(w_und, wsize, e);
+        } else if (hub && validate && da <= kLongRow) {
+            // hub edge (k_score_hub): a long row b only holds the mirror of this entry
+            asym = asym || !has_mirror(col, w, wsize, rb, rb + db, a, weight_bits(w_und, wsize, e));
+        }
+        __syncwarp();  // the next tile overwrites the stage
+    }
+    if (asym) atomicOr(status, DEV_NOT_SYMMETRIC);
+    count_ops(ops, n_add, n_sub);
+}
+
 // ---- hub edges ----------------------------------------------------------------------------------
 // An edge with an end point of more than kLongRow entries is scored from the larger row H (its
 // "hub"; ties go to the smaller id).  The score is the same left-to-right sum over the union of
@@ -1176,6 +1295,37 @@ static spc_status launch_score_staged(spc_context* ctx, int64_t m, const GraphVi
     return SPC_OK;
 }
 
+template <class Key>
+static spc_status launch_score_packed(spc_context* ctx, int64_t m, const GraphView& g, Work& W,
+                                      void* score, int wsize, int vflag, uint32_t* status,
+                                      bool count) {
+    static std::atomic<unsigned long long> attr_devs{0};  // devices already set up
+    const unsigned long long bit = 1ull << (ctx->device & 63);
+    if (!(attr_devs.load() & bit)) {
+        SPC_CUDA(cudaFuncSetAttribute(k_score_packed<Key>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPkSmem));
+        attr_devs.fetch_or(bit);
+    }
+    const int64_t tiles = (m + 31) / 32;
+    const int grid = grid_for(tiles, kPkWarps, ctx->num_sms * 4);
+    SPC_LAUNCH(ctx, k_score_packed<Key>, grid, kPkWarps * 32, kPkSmem, m, W.eu.as<int32_t>(),
+               W.ev.as<int32_t>(), g.rowptr, g.col, W.pk.as<uint2>(), static_cast<Key*>(score),
+               g.w, W.w_und.p, wsize, vflag, status,
+               count ? op_counter(ctx, "k_score_packed<Key>", 4) : nullptr);
+    return SPC_OK;
+}
+
+// schedule 3: rows staged in shared memory (binary32 rows as packed (column, p) pairs)
+template <class P, class Key>
+static spc_status launch_score_stage(spc_context* ctx, int64_t m, const GraphView& g, Work& W,
+                                     void* score, int wsize, int vflag, uint32_t* status,
+                                     bool count) {
+    if constexpr (std::is_same<P, float>::value)
+        return launch_score_packed<Key>(ctx, m, g, W, score, wsize, vflag, status, count);
+    else
+        return launch_score_staged<P, Key>(ctx, m, g, W, score, wsize, vflag, status, count);
+}
+
 static int pick_default_schedule(int64_t n, int64_t nnz) {
     return (n > 0 && nnz / n > 48) ? 2 : 3;  // long rows favour a warp per row
 }
@@ -1238,6 +1388,21 @@ static spc_status score_typed(spc_context* ctx, GraphView& g, bool validate, voi
     const int vflag = validate ? 1 : 0;
     const int wsize = (int)sizeof(WT);
     const bool mirror_here = validate && (score == nullptr || m == 0);
+    // the score schedule: forced, or autotuned once per shape bucket (every schedule computes
+    // the same bits)
+    int lg_deg = 0, lg_m = 0;
+    while ((1ll << (lg_deg + 1)) <= (n > 0 ? nnz / n : 0)) ++lg_deg;
+    while ((1ll << (lg_m + 1)) <= m) ++lg_m;
+    const int64_t tkey = ((int64_t)g.wtype << 16) | (lg_deg << 8) | lg_m;
+    if (schedule != 1 && schedule != 2 && schedule != 3) {
+        schedule = 0;
+        for (const auto& tk : ctx->tuned)
+            if (tk.first == tkey) schedule = tk.second;
+        if (schedule == 0 && capturing(ctx)) schedule = pick_default_schedule(n, nnz);
+    }
+    // binary32 rows: the packed schedule reads only the (column, p) pairs; p alone serves the
+    // other schedules (and the autotuner, which times them) and the hub kernels
+    const bool need_p = score == nullptr || n_long > 0 || schedule != 3;
     {
         // long rows (exact degrees from per-binade tables, then p and their edges) on the
         // second stream while the short rows run here
@@ -1262,8 +1427,8 @@ static spc_status score_typed(spc_context* ctx, GraphView& g, bool validate, voi
                 SPC_LAUNCH(ctx, k_rows_edges_flat, grid_for(nnz, (int)kFlatTile, maxb), kThreads,
                            0, n, nnz, g.rowptr, g.col, static_cast<const float*>(g.w),
                            W.deg.as<float>(), W.first_up.as<int32_t>(), W.up_ptr.as<int32_t>(),
-                           W.p.as<float>(), W.eu.as<int32_t>(), W.ev.as<int32_t>(),
-                           W.w_und.as<float>(), status);
+                           need_p ? W.p.as<float>() : nullptr, W.pk.as<uint2>(),
+                           W.eu.as<int32_t>(), W.ev.as<int32_t>(), W.w_und.as<float>(), status);
             } else {
                 SPC_LAUNCH(ctx, k_rows_edges<WT>, gb, kThreads, 0, n, g.rowptr, g.col,
                            static_cast<const WT*>(g.w), mirror_here ? 1 : 0, W.deg.as<Acc>(),
@@ -1281,39 +1446,28 @@ static spc_status score_typed(spc_context* ctx, GraphView& g, bool validate, voi
         if (validate) SPC_TRY(check_status(ctx));
         return SPC_OK;
     }
-    if (schedule != 1 && schedule != 2 && schedule != 3) {
-        // autotuned: every schedule computes the same bits; time each once per shape bucket
-        int lg_deg = 0, lg_m = 0;
-        while ((1ll << (lg_deg + 1)) <= (n > 0 ? nnz / n : 0)) ++lg_deg;
-        while ((1ll << (lg_m + 1)) <= m) ++lg_m;
-        const int64_t tkey = ((int64_t)g.wtype << 16) | (lg_deg << 8) | lg_m;
-        schedule = 0;
-        for (const auto& tk : ctx->tuned)
-            if (tk.first == tkey) schedule = tk.second;
-        if (schedule == 0 && !capturing(ctx)) {
-            if (!ctx->tune_ev[0])
-                for (auto& ev : ctx->tune_ev) SPC_CUDA(cudaEventCreate(&ev));
-            const int gw = grid_for(n, kThreads / 32, maxb);
-            SPC_CUDA(cudaEventRecord(ctx->tune_ev[0], ctx->stream));
-            SPC_TRY((launch_score_edges<P, Key>(ctx, m, g, W, score, wsize, vflag, status, false)));
-            SPC_CUDA(cudaEventRecord(ctx->tune_ev[1], ctx->stream));
-            SPC_LAUNCH(ctx, (k_score_warp_row<P, Key>), gw, kThreads, 0, n, g.rowptr, g.col,
-                       W.p.as<P>(), W.up_ptr.as<int32_t>(), W.first_up.as<int32_t>(),
-                       static_cast<Key*>(score), g.w, W.w_und.p, wsize, vflag, status, nullptr);
-            SPC_CUDA(cudaEventRecord(ctx->tune_ev[2], ctx->stream));
-            SPC_TRY((launch_score_staged<P, Key>(ctx, m, g, W, score, wsize, vflag, status,
-                                                 false)));
-            SPC_CUDA(cudaEventRecord(ctx->tune_ev[3], ctx->stream));
-            SPC_CUDA(cudaEventSynchronize(ctx->tune_ev[3]));
-            float t[3] = {0.f, 0.f, 0.f};
-            for (int k = 0; k < 3; ++k)
-                SPC_CUDA(cudaEventElapsedTime(&t[k], ctx->tune_ev[k], ctx->tune_ev[k + 1]));
-            schedule = 1;
-            if (t[1] < t[schedule - 1]) schedule = 2;
-            if (t[2] < t[schedule - 1]) schedule = 3;
-            ctx->tuned.push_back({tkey, schedule});
-        }
-        if (schedule == 0) schedule = pick_default_schedule(n, nnz);
+    if (schedule == 0) {  // not tuned yet for this shape: time each schedule once
+        if (!ctx->tune_ev[0])
+            for (auto& ev : ctx->tune_ev) SPC_CUDA(cudaEventCreate(&ev));
+        const int gw = grid_for(n, kThreads / 32, maxb);
+        SPC_CUDA(cudaEventRecord(ctx->tune_ev[0], ctx->stream));
+        SPC_TRY((launch_score_edges<P, Key>(ctx, m, g, W, score, wsize, vflag, status, false)));
+        SPC_CUDA(cudaEventRecord(ctx->tune_ev[1], ctx->stream));
+        SPC_LAUNCH(ctx, (k_score_warp_row<P, Key>), gw, kThreads, 0, n, g.rowptr, g.col,
+                   W.p.as<P>(), W.up_ptr.as<int32_t>(), W.first_up.as<int32_t>(),
+                   static_cast<Key*>(score), g.w, W.w_und.p, wsize, vflag, status, nullptr);
+        SPC_CUDA(cudaEventRecord(ctx->tune_ev[2], ctx->stream));
+        SPC_TRY((launch_score_stage<P, Key>(ctx, m, g, W, score, wsize, vflag, status,
+                                            false)));
+        SPC_CUDA(cudaEventRecord(ctx->tune_ev[3], ctx->stream));
+        SPC_CUDA(cudaEventSynchronize(ctx->tune_ev[3]));
+        float t[3] = {0.f, 0.f, 0.f};
+        for (int k = 0; k < 3; ++k)
+            SPC_CUDA(cudaEventElapsedTime(&t[k], ctx->tune_ev[k], ctx->tune_ev[k + 1]));
+        schedule = 1;
+        if (t[1] < t[schedule - 1]) schedule = 2;
+        if (t[2] < t[schedule - 1]) schedule = 3;
+        ctx->tuned.push_back({tkey, schedule});
     }
     // rowptr, every stored column and p read once, every score written once (no model on
     // levels with long rows: the hub kernels take their edges)
@@ -1346,7 +1500,7 @@ static spc_status score_typed(spc_context* ctx, GraphView& g, bool validate, voi
     }
     if (schedule == 3) {
         note_bytes(ctx, score_bytes);
-        SPC_TRY((launch_score_staged<P, Key>(ctx, m, g, W, score, wsize, vflag, status, true)));
+        SPC_TRY((launch_score_stage<P, Key>(ctx, m, g, W, score, wsize, vflag, status, true)));
     } else if (schedule == 2) {
         const int warps_per_block = kThreads / 32;
         note_bytes(ctx, score_bytes);

@@ -95,10 +95,12 @@ def test_score_mid_bitexact(ctx, name, schedule):
 @pytest.mark.parametrize("weight,dt", [("float", np.float32), ("float", np.float64),
                                        ("int", np.int32)])
 def test_staged_schedule_on_mixed_row_lengths(ctx, weight, dt):
-    """The staged schedule with every kind of row: rows b of up to 32 entries staged, longer
-    ones (up to 256) walked in place, tiles whose rows a exceed the stage walked in place, and
-    hub rows left to the hub kernels -- on a heavy-tailed graph, then on its multilevel
-    coarsening, every score bit-exact with the oracle."""
+    """The staged schedule with every kind of row -- binary64 and int: rows b of up to 32
+    entries staged, longer ones (up to 256) walked in place; binary32 (packed (column, p)
+    pairs): rows b staged while the warp's area has room, the rest walked in place -- tiles
+    whose rows a exceed the stage walked in place, and hub rows left to the hub kernels, on a
+    heavy-tailed graph, then on its multilevel coarsening, every score bit-exact with the
+    oracle."""
     api = _api()
     g = I.powerlaw_graph(4039, 22, 7, weight, dt)
     deg = np.diff(g.rowptr)
