@@ -95,7 +95,11 @@ typedef struct {
                            level l (1-based) targets max(n_c, floor(n / 2^l)) super-nodes and
                            the last level targets n_c (Section 4: recompute the norms after
                            partial coarsening; Section 3 coarsens by halves).                 */
-    int32_t validate;   /* 1: check the input graph (S0) before the first level; 0: trust it */
+    int32_t validate;   /* 1: check the input graph (S0) before the first level; 0: trust it.
+                           Rows (order, range, self-loops, weights) are checked exactly, and so
+                           is symmetry for int32 and binary64 weights; for binary32 weights
+                           symmetry is checked by a keyed 64-bit fingerprint of all entries
+                           (an asymmetric graph passes with probability about 2^-64) */
     int32_t use_graph;  /* 1: capture the schedule in a CUDA graph and replay it on later calls
                            with the same shapes; 0: launch kernel by kernel                   */
     int32_t schedule;   /* score-kernel schedule: 0 auto (autotuned), 1 edge tiles

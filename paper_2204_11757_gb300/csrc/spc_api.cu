@@ -3,6 +3,7 @@
 #include <cstdio>
 #include <cstring>
 #include <mutex>
+#include <random>
 
 #include "spc_internal.cuh"
 
@@ -361,6 +362,7 @@ static spc_status reserve_work(spc_context* ctx, int64_t n, int64_t m, int64_t B
     // binary32 levels also keep every stored entry as one 8-byte (column, p) pair, with room
     // for the 16-byte copies that start or end on the neighbouring entry
     SPC_TRY(ensure(ctx, W.pk, (2 * M + N + 2) * 8));
+    SPC_TRY(ensure(ctx, W.sym, 16));
     SPC_TRY(ensure(ctx, W.long_rows, N * 4));
     SPC_TRY(ensure(ctx, W.lr_base, N * 8));
     SPC_TRY(ensure(ctx, W.lr_len, N * 8));
@@ -952,6 +954,10 @@ spc_status spc_context_create(spc_context** out, const spc_allocator* allocator,
         return SPC_ERR_CUDA;
     }
     cudaMemset(ctx->d_status, 0, 256);
+    {
+        std::random_device rd;  // the symmetry fingerprint's key, unknown to whoever built the input
+        for (auto& k : ctx->sym_key) k = ((uint64_t)rd() << 32) ^ (uint64_t)rd();
+    }
     *out = ctx;
     return SPC_OK;
 }

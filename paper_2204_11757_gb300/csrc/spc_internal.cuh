@@ -90,6 +90,7 @@ struct SeqTabBufs {
 struct Work {
     Buf up_cnt, up_ptr, first_up, eu, ev, w_und, deg, p;       // S0-S2
     Buf pk;                                                     // binary32 (column, p) pairs
+    Buf sym;                                                    // symmetry fingerprint (u64)
     Buf long_rows, lr_base, lr_len, lr_idx, lr_eoff, heavy, seg_base, seg_len, seg_idx, seg_terms;
     Buf hub_leaf;                                               // per hub: its leaf edges' score
     Buf hub_map, hub_slot;                                      // column maps of the largest hubs
@@ -200,6 +201,7 @@ struct spc_context {
     // score-schedule autotuner: (dtype, log2 mean row length, log2 m) -> 1 edge tiles, 2 warp/row
     std::vector<std::pair<int64_t, int>> tuned;
     cudaEvent_t tune_ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    uint64_t sym_key[2] = {0, 0};    // key of the symmetry fingerprint, drawn at creation
     // arithmetic counts of the timed score launches: [0..1] edge tiles (adds, subtractions),
     // [2..3] warp per row, [4..5] staged rows
     unsigned long long* d_ops = nullptr;
@@ -282,8 +284,8 @@ __device__ __forceinline__ void pdl_wait() {
 // The rows of a tile of consecutive CSR entries [base, end), for kernels that run flat over the
 // stored entries: every thread of the block calls it (it synchronises the block).  Two searches
 // find the first row r_lo and the last row of the tile; one thread per row then marks the row
-// of each of its entries, s_row[j - base] = row - r_lo, or -1 for a row of more than
-// `long_row` entries (long_row < 0: no limit).  Returns r_lo.  Rows spanned by a tile are
+// of each of its entries, s_row[j - base] = row - r_lo, or -2 - (row - r_lo) for a row of
+// more than `long_row` entries (long_row < 0: no limit).  Returns r_lo.  Rows spanned by a tile are
 // visited by that tile alone (neighbouring tiles share at most one row), so the marking is
 // O(rows + entries) over the whole array.
 __device__ __forceinline__ int64_t csr_last_row_at(const int64_t* __restrict__ rowptr, int64_t lo,
@@ -304,7 +306,8 @@ __device__ __forceinline__ int64_t tile_rows(const int64_t* __restrict__ rowptr,
     const int64_t r_lo = s_rows[0], r_hi = s_rows[1];
     for (int64_t x = r_lo + threadIdx.x; x <= r_hi; x += blockDim.x) {
         const int64_t r0 = rowptr[x], r1 = rowptr[x + 1];
-        const int32_t mark = (long_row >= 0 && r1 - r0 > long_row) ? -1 : (int32_t)(x - r_lo);
+        const int32_t rel = (int32_t)(x - r_lo);
+        const int32_t mark = (long_row >= 0 && r1 - r0 > long_row) ? -2 - rel : rel;
         for (int64_t j = r0 > base ? r0 : base; j < (r1 < end ? r1 : end); ++j)
             s_row[j - base] = mark;
     }

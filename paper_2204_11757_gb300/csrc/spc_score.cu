@@ -335,12 +335,33 @@ k_rows_edges(int64_t n, const int64_t* __restrict__ rowptr, const int32_t* __res
     }
 }
 
+// Symmetry fingerprint (S0) of a binary32 graph: every stored entry (x, y, w) off the diagonal
+// adds +H(min, max, bits of w) when x < y and -H(...) when x > y, modulo 2^64.  A symmetric
+// graph pairs every upper entry with a lower one of the same (min, max, w), so the sum is 0
+// whatever the order of the additions.  An asymmetric graph leaves a nonempty set of
+// unpaired terms, whose signed sum is 0 only by a coincidence of the 64-bit keyed hash (about
+// 2^-64 per input; the key is drawn at context creation).  H chains two rounds of the
+// SplitMix64 output function (Steele, Lea and Flood, "Fast splittable pseudorandom number
+// generators", OOPSLA 2014), keyed by k0 and k1.
+__device__ __forceinline__ uint64_t mix64(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+    return z ^ (z >> 31);
+}
+__device__ __forceinline__ uint64_t sym_term(int64_t x, int32_t y, uint32_t wbits, uint64_t k0,
+                                             uint64_t k1) {
+    const uint64_t lo = (uint64_t)((int64_t)y < x ? y : x), hi = (uint64_t)((int64_t)y < x ? x : y);
+    const uint64_t h = mix64(mix64(k0 ^ ((lo << 32) | hi)) ^ (wbits + k1));
+    return (int64_t)y > x ? h : (uint64_t)0 - h;
+}
+
 // S2 (+ the edge list) for binary32 weights, flat over the stored entries: each block takes
 // kFlatTile consecutive entries and marks the row of each in shared memory (tile_rows), so the
 // columns, weights and p values of a warp are consecutive (the row-per-thread kernel reads 32
 // rows at once).  p = w / d is one IEEE division per entry, exactly as k_rows_edges computes
 // it.  `p` (may be null) receives p alone, `pk` the (column, p) pair of every entry.  Rows
-// longer than kLongRow are left to k_long_rows_edges.
+// longer than kLongRow are left to k_long_rows_edges.  With `sym` (input validation), every
+// entry of every row, long ones included, also adds its symmetry fingerprint term into *sym.
 constexpr int64_t kFlatTile = 2048;
 
 __global__ void __launch_bounds__(kThreads)
@@ -349,21 +370,24 @@ k_rows_edges_flat(int64_t n, int64_t nnz, const int64_t* __restrict__ rowptr,
                   const float* __restrict__ deg, const int32_t* __restrict__ nlow,
                   const int32_t* __restrict__ up_ptr, float* __restrict__ p,
                   uint2* __restrict__ pk, int32_t* __restrict__ eu, int32_t* __restrict__ ev,
-                  float* __restrict__ w_und, const uint32_t* status) {
+                  float* __restrict__ w_und, unsigned long long* sym, uint64_t k0, uint64_t k1,
+                  const uint32_t* status) {
     spc::pdl_wait();
     if (*status) return;  // invalid input: nothing below may index with it
     __shared__ int64_t s_rows[2];
     __shared__ int32_t s_row[kFlatTile];  // row of each entry of the tile minus the first row
+    uint64_t fp = 0;                      // this thread's fingerprint terms
     for (int64_t base = (int64_t)blockIdx.x * kFlatTile; base < nnz;
          base += (int64_t)gridDim.x * kFlatTile) {
         const int64_t end = base + kFlatTile < nnz ? base + kFlatTile : nnz;
         const int64_t r_lo = tile_rows(rowptr, n, base, end, kLongRow, s_row, s_rows);
         for (int64_t j = base + threadIdx.x; j < end; j += blockDim.x) {
             const int32_t rel = s_row[j - base];
-            if (rel < 0) continue;  // k_long_rows_edges
-            const int64_t x = r_lo + rel;
+            const int64_t x = r_lo + (rel >= 0 ? rel : -2 - rel);
             const int32_t y = col[j];
             const float wj = w[j];
+            if (sym && (int64_t)y != x) fp += sym_term(x, y, __float_as_uint(wj), k0, k1);
+            if (rel < 0) continue;  // long row: k_long_rows_edges
             const float pj = __fdiv_rn(wj, deg[x]);
             if (p) p[j] = pj;
             pk[j] = make_uint2((uint32_t)y, __float_as_uint(pj));
@@ -376,6 +400,17 @@ k_rows_edges_flat(int64_t n, int64_t nnz, const int64_t* __restrict__ rowptr,
         }
         __syncthreads();
     }
+    if (sym) {
+        for (int o = 16; o > 0; o >>= 1) fp += __shfl_xor_sync(0xffffffffu, fp, o);
+        if ((threadIdx.x & 31) == 0 && fp) atomicAdd(sym, (unsigned long long)fp);
+    }
+}
+
+// the verdict of the symmetry fingerprint: a nonzero sum is an asymmetric input (unless a row
+// check already failed, in which case the flat kernel did not run and that error stands)
+__global__ void k_sym_check(const unsigned long long* __restrict__ sym, uint32_t* status) {
+    spc::pdl_wait();
+    if (threadIdx.x == 0 && *status == 0u && *sym != 0ull) atomicOr(status, DEV_NOT_SYMMETRIC);
 }
 
 // Arithmetic count of a score launch, for the roofline: ops[0] += additions into the running
@@ -1385,9 +1420,12 @@ static spc_status score_typed(spc_context* ctx, GraphView& g, bool validate, voi
                             m * (8 + s_w));
     // the symmetry of rows up to kLongRow is checked by the score kernels' walks when scores
     // are computed; without scores, here
-    const int vflag = validate ? 1 : 0;
     const int wsize = (int)sizeof(WT);
     const bool mirror_here = validate && (score == nullptr || m == 0);
+    // binary32 levels that are scored check symmetry by the fingerprint of the flat normalise
+    // kernel; the others by the score walks (or, without scores, by k_rows_edges' searches)
+    const bool fingerprint = std::is_same<WT, float>::value && validate && !mirror_here && n > 0;
+    const int vflag = validate && !fingerprint ? 1 : 0;
     // the score schedule: forced, or autotuned once per shape bucket (every schedule computes
     // the same bits)
     int lg_deg = 0, lg_m = 0;
@@ -1424,11 +1462,18 @@ static spc_status score_typed(spc_context* ctx, GraphView& g, bool validate, voi
         }
         if constexpr (std::is_same<WT, float>::value) {
             if (!mirror_here && n > 0) {
+                unsigned long long* sym = nullptr;
+                if (fingerprint) {
+                    sym = W.sym.as<unsigned long long>();
+                    SPC_CUDA(cudaMemsetAsync(sym, 0, 8, ctx->stream));
+                }
                 SPC_LAUNCH(ctx, k_rows_edges_flat, grid_for(nnz, (int)kFlatTile, maxb), kThreads,
                            0, n, nnz, g.rowptr, g.col, static_cast<const float*>(g.w),
                            W.deg.as<float>(), W.first_up.as<int32_t>(), W.up_ptr.as<int32_t>(),
                            need_p ? W.p.as<float>() : nullptr, W.pk.as<uint2>(),
-                           W.eu.as<int32_t>(), W.ev.as<int32_t>(), W.w_und.as<float>(), status);
+                           W.eu.as<int32_t>(), W.ev.as<int32_t>(), W.w_und.as<float>(), sym,
+                           ctx->sym_key[0], ctx->sym_key[1], status);
+                if (fingerprint) SPC_LAUNCH(ctx, k_sym_check, 1, 32, 0, sym, status);
             } else {
                 SPC_LAUNCH(ctx, k_rows_edges<WT>, gb, kThreads, 0, n, g.rowptr, g.col,
                            static_cast<const WT*>(g.w), mirror_here ? 1 : 0, W.deg.as<Acc>(),

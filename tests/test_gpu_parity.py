@@ -605,8 +605,8 @@ def test_autograd_gradcheck_and_fd_float64(ctx):
 
 # ---- error paths -----------------------------------------------------------------------------------
 
-def _bad(kind):
-    g = I.random_graph(30, 0.2, 1, weight="float", dtype=np.float64, connected=True)
+def _bad(kind, dtype=np.float64):
+    g = I.random_graph(30, 0.2, 1, weight="float", dtype=dtype, connected=True)
     rowptr, col, w = g.rowptr.copy(), g.col.copy(), g.w.copy()
     if kind == "unsorted":
         r = np.argmax(np.diff(rowptr) >= 3)
@@ -614,6 +614,8 @@ def _bad(kind):
         col[a], col[a + 1] = col[a + 1], col[a]
     elif kind == "asym":
         w[5] = w[5] * 1.5
+    elif kind == "asym_ulp":  # one unit in the last place, one entry
+        w[5] = np.nextafter(w[5], w.dtype.type(np.inf))
     elif kind == "weight":
         w[3] = -1.0
         # keep it symmetric so only the weight check can fire
@@ -626,12 +628,15 @@ def _bad(kind):
     return rowptr, col, w
 
 
-@pytest.mark.parametrize("kind,code", [("unsorted", -4), ("asym", -2), ("weight", -9),
-                                       ("range", -4)])
-def test_invalid_input_reported(ctx, kind, code):
+@pytest.mark.parametrize("dt", [np.float64, np.float32])
+@pytest.mark.parametrize("kind,code", [("unsorted", -4), ("asym", -2), ("asym_ulp", -2),
+                                       ("weight", -9), ("range", -4)])
+def test_invalid_input_reported(ctx, kind, code, dt):
+    """Every input check, on binary64 (symmetry by the score walks) and binary32 (symmetry by
+    the fingerprint of the flat normalise kernel) graphs."""
     api = _api()
     from paper_2204_11757_gb300 import native as N
-    rowptr, col, w = _bad(kind)
+    rowptr, col, w = _bad(kind, dt)
     csr = api.CSR.from_numpy(rowptr, col, w)
     with pytest.raises(N.SpcError) as ei:
         ctx.coarsen(csr, 5, levels=1)
@@ -642,7 +647,7 @@ def test_invalid_input_reported(ctx, kind, code):
     assert nc == 2
 
 
-def _balanced_asymmetric():
+def _balanced_asymmetric(dtype=np.float64):
     """Symmetric graph with a long row (node 599, 400 neighbours), then two defects that keep
     the entry count even and every row sorted: an upper entry (450, 599) whose mirror the long
     row lacks, and an upper entry (x, y) between short rows removed while its mirror (y, x)
@@ -666,18 +671,20 @@ def _balanced_asymmetric():
     rowptr = np.zeros(n + 1, dtype=np.int64)
     rowptr[1:] = np.cumsum([len(r) for r in rows])
     col = np.array([c for r in rows for c, _ in r], dtype=np.int32)
-    w = np.array([wv for r in rows for _, wv in r], dtype=np.float64)
+    w = np.array([wv for r in rows for _, wv in r], dtype=dtype)
     assert rowptr[-1] == g.nnz
     return rowptr, col, w
 
 
-def test_asymmetry_hidden_by_balanced_counts_is_reported(ctx):
+@pytest.mark.parametrize("dt", [np.float64, np.float32])
+def test_asymmetry_hidden_by_balanced_counts_is_reported(ctx, dt):
     """Equal numbers of entries above and below the diagonal, yet not symmetric: the missing
-    mirror of an entry pointing into a long row must be found (by the score kernels' lookup in
-    the long row), with and without graph replay."""
+    mirror of an entry pointing into a long row must be found (binary64: by the score kernels'
+    lookup in the long row; binary32: by the symmetry fingerprint), with and without graph
+    replay."""
     api = _api()
     from paper_2204_11757_gb300 import native as N
-    rowptr, col, w = _balanced_asymmetric()
+    rowptr, col, w = _balanced_asymmetric(dt)
     csr = api.CSR.from_numpy(rowptr, col, w)
     for _ in range(3):
         with pytest.raises(N.SpcError) as ei:
@@ -686,6 +693,26 @@ def test_asymmetry_hidden_by_balanced_counts_is_reported(ctx):
     with pytest.raises(N.SpcError) as ei:
         ctx.score(csr)
     assert ei.value.status == -2
+
+
+def test_long_row_weight_asymmetry_reported_binary32(ctx):
+    """A binary32 hub whose row holds one weight a unit in the last place off its mirror: the
+    fingerprint covers the entries of long rows too."""
+    api = _api()
+    from paper_2204_11757_gb300 import native as N
+    g = I.powerlaw_graph(4039, 22, 7, "float", np.float32)
+    deg = np.diff(g.rowptr)
+    h = int(np.argmax(deg))
+    assert deg[h] > 256
+    w = g.w.copy()
+    j = int(g.rowptr[h]) + 3
+    w[j] = np.nextafter(w[j], np.float32(np.inf))
+    csr = api.CSR.from_numpy(g.rowptr, g.col, w)
+    with pytest.raises(N.SpcError) as ei:
+        ctx.coarsen(csr, g.n // 2, levels=1)
+    assert ei.value.status == -2
+    # unchanged weights pass
+    ctx.coarsen(api.CSR.from_graph(g), g.n // 2, levels=1)
 
 
 def test_invalid_arguments(ctx):
