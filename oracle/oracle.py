@@ -357,26 +357,38 @@ def coarsen(g, ratio: int, mode: str, self_mass_degree: bool = True):
     return levels, total
 
 
-def bfs_order(g) -> np.ndarray:
-    """The locality order of the adjacency-reordering option (the paper's closing section
-    suggests graph adjacency reordering; which order is this library's choice): every node's
-    hop distance from node 0 by breadth-first search, the nodes node 0 does not reach after all
-    the others, and the nodes renumbered by (distance, id).  Returns perm, perm[x] = the new id
-    of node x."""
-    from scipy.sparse import csr_matrix
-    from scipy.sparse.csgraph import breadth_first_order
+# The adjacency-reordering option's order (the paper's closing section suggests graph adjacency
+# reordering for memory locality; which order is this library's choice).
+REORDER_HOPS = 8  # the cluster label: the smallest node id within this many hops
+REORDER_SUB = 2   # the sub-cluster label, the same within fewer hops
+
+
+def hop_min_labels(g, k: int):
+    """L_0 .. L_k, where L_i(x) is the smallest node id within i hops of x (x included):
+    L_0(x) = x and L_{i+1}(x) = min(L_i(x), min over the neighbours y of x of L_i(y)), one
+    synchronous round per hop (a node with no neighbour keeps its own id)."""
     n = g.n
-    dist = np.full(n, np.iinfo(np.int64).max, dtype=np.int64)
-    if n > 0:
-        A = csr_matrix((np.ones(g.nnz, dtype=np.int8), g.col, g.rowptr), shape=(n, n))
-        order, pred = breadth_first_order(A, 0, directed=True, return_predecessors=True)
-        # hop distances along the BFS tree, in discovery order (a parent precedes its child)
-        dist[0] = 0
-        for x in order[1:]:
-            dist[x] = dist[pred[x]] + 1
-        reached = dist != np.iinfo(np.int64).max
-        dist[~reached] = (dist[reached].max() + 1) if reached.any() else 0
-    key = np.lexsort((np.arange(n), dist))       # by distance, ties by id
+    L = np.arange(n, dtype=np.int64)
+    out = [L]
+    deg = np.diff(g.rowptr)
+    for _ in range(k):
+        nb = np.full(n, n, dtype=np.int64)
+        has = deg > 0
+        if g.nnz > 0:
+            nb[has] = np.minimum.reduceat(L[g.col], g.rowptr[:-1][has])
+        L = np.minimum(L, nb)
+        out.append(L)
+    return out
+
+
+def cluster_order(g, hops: int = REORDER_HOPS, sub: int = REORDER_SUB) -> np.ndarray:
+    """The locality order of the adjacency-reordering option: nodes renumbered by
+    (L_hops(x), L_sub(x), x) with the labels of hop_min_labels.  Nodes sharing the smallest id
+    within `hops` hops form clusters of nearby nodes; inside a cluster the `sub`-hop label
+    groups nearer ones.  Returns perm, perm[x] = the new id of node x."""
+    n = g.n
+    labels = hop_min_labels(g, hops)
+    key = np.lexsort((np.arange(n), labels[sub], labels[hops]))
     perm = np.empty(n, dtype=np.int32)
     perm[key] = np.arange(n, dtype=np.int32)
     return perm
@@ -400,10 +412,10 @@ def permute(g, perm: np.ndarray):
 
 
 def coarsen_reordered(g, ratio: int, mode: str, self_mass_degree: bool = True):
-    """The adjacency-reordering option: the multilevel driver on permute(g, bfs_order(g)).
+    """The adjacency-reordering option: the multilevel driver on permute(g, cluster_order(g)).
     Returns (levels of the renumbered graph, composed lift of the original nodes, perm); the
     lift of node x is the renumbered graph's lift of node perm[x]."""
-    perm = bfs_order(g)
+    perm = cluster_order(g)
     levels, total = coarsen(permute(g, perm), ratio, mode, self_mass_degree)
     return levels, total[perm], perm
 

@@ -754,43 +754,55 @@ def test_carried_mass_order_is_ascending_members_then_self_mass():
     assert np.float32(np.float32(1 + 1) + big) + 1 != got[0]
 
 
-def _bfs_dist_bruteforce(g):
-    """Hop distances from node 0 by the textbook queue, in plain Python (tiny graphs)."""
+def _hop_dists_bruteforce(g):
+    """All-pairs hop distances by a textbook queue BFS from every node (None: unreachable)."""
     from collections import deque
-    dist = [None] * g.n
-    if g.n:
-        dist[0] = 0
-        q = deque([0])
+    adj = [g.col[g.rowptr[x]:g.rowptr[x + 1]].tolist() for x in range(g.n)]
+    out = []
+    for s in range(g.n):
+        dist = [None] * g.n
+        dist[s] = 0
+        q = deque([s])
         while q:
-            u = q.popleft()
-            for v in g.col[g.rowptr[u]:g.rowptr[u + 1]]:
-                if dist[v] is None:
-                    dist[v] = dist[u] + 1
-                    q.append(int(v))
-    far = max([d for d in dist if d is not None], default=-1) + 1
-    return [far if d is None else d for d in dist]
+            x = q.popleft()
+            for y in adj[x]:
+                if dist[y] is None:
+                    dist[y] = dist[x] + 1
+                    q.append(y)
+        out.append(dist)
+    return out
 
 
-def test_bfs_order_is_distance_then_id():
-    """The reordering's order against a textbook breadth-first search: new ids ascend with
-    (hop distance from node 0, id), unreached nodes last."""
-    graphs = [I.path_graph(9), I.cycle_graph(12), I.complete_graph(5)]
+def test_cluster_order_is_hop_min_label_then_id():
+    """The reordering's order against its definition by brute force: L_k(x) is the smallest id
+    among the nodes within k hops of x (all-pairs BFS), and new ids ascend with
+    (L_8(x), L_2(x), x); every round of the oracle's label propagation equals L_k."""
+    graphs = [I.path_graph(19), I.cycle_graph(24), I.complete_graph(5)]
     for seed in range(6):
         graphs.append(I.random_graph(60, 0.05, 40 + seed, weight="float", dtype=np.float64,
                                      connected=seed % 2 == 0))
+    graphs.append(I.tri_mesh_2d(9, 7, 3, jitter=0.3, weight="inv_len", dtype=np.float64))
     for g in graphs:
-        perm = O.bfs_order(g)
+        d = _hop_dists_bruteforce(g)
+        lab = lambda x, k: min(y for y in range(g.n) if d[x][y] is not None and d[x][y] <= k)
+        labels = O.hop_min_labels(g, O.REORDER_HOPS)
+        for k in range(O.REORDER_HOPS + 1):
+            assert labels[k].tolist() == [lab(x, k) for x in range(g.n)]
+        perm = O.cluster_order(g)
         assert sorted(perm.tolist()) == list(range(g.n))
-        d = _bfs_dist_bruteforce(g)
-        want = sorted(range(g.n), key=lambda x: (d[x], x))
+        want = sorted(range(g.n), key=lambda x: (lab(x, O.REORDER_HOPS), lab(x, O.REORDER_SUB), x))
         assert [int(np.nonzero(perm == i)[0][0]) for i in range(g.n)] == want
+    # a path 0 - 1 - ... - 18 renumbered: node x's 8-hop label is max(0, x - 8), so the nodes
+    # within 8 hops of 0 come first, then one node per label
+    g = I.path_graph(19)
+    assert O.hop_min_labels(g, 8)[8].tolist() == [max(0, x - 8) for x in range(19)]
 
 
 def test_permuted_graph_is_the_same_graph():
     """permute() renames nodes only: the renamed weighted adjacency matrix equals the
     original's, rows stay sorted, and the undirected edge list follows the new upper triangle."""
     g = I.random_graph(80, 0.06, 9, weight="float", dtype=np.float64, connected=True)
-    perm = O.bfs_order(g)
+    perm = O.cluster_order(g)
     h = O.permute(g, perm)
     W, H = O.dense_weights(g), O.dense_weights(h)
     assert np.array_equal(H[np.ix_(perm, perm)], W)
