@@ -50,7 +50,7 @@ WORKLOADS = {
     "c4_rgg8m_f32_reordered": ("c4_rgg8m_f32", 8, "random geometric graph, 2^23 points, mean "
                                "degree 12, FP32 exp(-d^2/r^2), 8 halving levels to n/256, "
                                "with the adjacency-reordering option: renumbered by "
-                               "breadth-first distance from node 0 inside the timed step"),
+                               "(8-hop min label, 2-hop min label, id) inside the timed step"),
     # reduced case of the same construction, for profiler captures that must stay small
     "p2_tri512_f64": ("p2_tri512_f64", 6, "512x512 jittered triangle mesh (262,144 nodes, "
                       "784,385 edges), FP64 1/edge-length, 6 halving levels to n/64"),
@@ -286,9 +286,17 @@ FP64_PEAK_GOPS = 506.5
 FP64_PEAK_SOURCE = "measured FP64 add throughput (profiles/fp64_add_probe_gb300.md)"
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of a workload's dominant
-# kernel, from an ncu capture of the same kernel; absent where no capture of the current kernel
-# exists (then `traffic` is null).
-TRAFFIC = {}
+# kernel, from single-pass ncu captures of the full-size workload (one step's launches summed
+# and divided by the launches of a step, as `achieved` averages them; the commands and every
+# launch are in profiles/traffic_dominant_kernels.md); absent where no capture of the current
+# kernel exists (then `traffic` is null).
+TRAFFIC = {
+    ("c4_rgg8m_f32", "k_score_packed<Key>"): 2.180100e9,
+    ("c4_rgg8m_f32_one", "k_score_packed<Key>"): 1.376518e10,
+    ("c2_tri2048_f64", "(k_score_edges<P, Key, kScoreChains>)"): 2.226063e8,
+    ("c3_tet129_f64", "(k_score_edges<P, Key, kScoreChains>)"): 3.163520e8,
+    ("c5_batch10k_f32", "k_bv_minkey<KT>"): 1.647388e9,
+}
 
 HEADLINE = "c4_rgg8m_f32"
 # the other configurations reported in the same line (their own keys, fewer steps)

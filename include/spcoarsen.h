@@ -119,9 +119,9 @@ typedef struct {
                            degree.  0: each level scores the coarse graph G_c as it is, without
                            the internal weight.                                             */
     int32_t reorder;    /* adjacency reordering (spc_coarsen only; the paper's closing section
-                           suggests it).  1: the graph is first renumbered by (breadth-first hop
-                           distance from node 0, id), nodes that node 0 does not reach last,
-                           and coarsened in that numbering: node x is node perm[x] there
+                           suggests it).  1: the graph is first renumbered by (L_8(x), L_2(x),
+                           x), where L_k(x) is the smallest node id within k hops of x, and
+                           coarsened in that numbering: node x is node perm[x] there
                            (spc_get_reorder).  lift_out stays in the caller's numbering; the
                            retained levels and spc_take_result's coarse graph and edge map
                            refer to the renumbered graph, whose edge ids and whose order of

@@ -215,8 +215,8 @@ class Context:
         recorded schedule as one CUDA graph.  self_mass selects the multilevel reading: every
         level after the first scores its input with each super-node's accumulated internal
         weight on the diagonal (the merged node of the proof of Theorem 2); False scores the
-        coarse graph without it.  reorder first renumbers the graph by breadth-first distance
-        from node 0 (see reorder_perm); the lift stays in the caller's numbering."""
+        coarse graph without it.  reorder first renumbers the graph by (8-hop min label,
+        2-hop min label, id) (see reorder_perm); the lift stays in the caller's numbering."""
         c = self._csr(g)
         opts = N.spc_options(int(levels), int(bool(validate)), int(bool(use_graph)), int(schedule),
                              int(bool(self_mass)), int(bool(reorder)))

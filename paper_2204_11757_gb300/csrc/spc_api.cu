@@ -556,7 +556,7 @@ struct Schedule {
     int32_t levels = 1;
     bool validate = true;
     bool self_mass = true;   // the self-mass reading of the multilevel driver
-    bool reorder = false;    // coarsen the graph renumbered by breadth-first distance
+    bool reorder = false;    // coarsen the graph renumbered by its hop-min labels
     int schedule = 0;
     // single graph
     int64_t n_c = 1;

@@ -118,9 +118,9 @@ struct Work {
     // input graph with the accumulated internal weight on its diagonal
     Buf ms_key, ms_val, ms_key2, ms_val2, ms_start;
     Buf dg_rowptr, dg_col, dg_w, dg_pos;
-    // adjacency reordering: distances, frontiers, the renumbering and the renumbered CSR
+    // adjacency reordering: labels, sort keys, the renumbering and the renumbered CSR
     Buf ro_dist, ro_key, ro_val, ro_key2, ro_val2, ro_perm, ro_deg;
-    Buf ro_rowptr, ro_col, ro_w, ro_lkey, ro_lkey2, ro_lval, ro_lval2, ro_head, ro_lift, ro_bar;
+    Buf ro_rowptr, ro_col, ro_w, ro_lkey, ro_lkey2, ro_lval, ro_lval2, ro_head, ro_lift;
 };
 
 struct Timer {
@@ -438,8 +438,8 @@ spc_status run_carry_mass(spc_context* ctx, int64_t n, const int32_t* lift, int6
 spc_status run_diag_graph(spc_context* ctx, const GraphView& g, const void* mass,
                           GraphView& out);
 
-// Adjacency reordering (spc_reorder.cu): the graph renumbered by (breadth-first distance from
-// node 0, id), into the context's ro_* buffers (work.ro_perm[x] = the new id of node x), and
+// Adjacency reordering (spc_reorder.cu): the graph renumbered by (L_8(x), L_2(x), x), L_k(x) the
+// smallest node id within k hops of x, into the context's ro_* buffers (work.ro_perm[x] = the new id of node x), and
 // out[x] = in[ro_perm[x]] for a lift computed on the renumbered graph.  g must be valid.
 spc_status run_reorder(spc_context* ctx, const GraphView& g, GraphView& out);
 spc_status run_unpermute(spc_context* ctx, int64_t n, const int32_t* in, int32_t* out);

@@ -907,8 +907,8 @@ def _reorder_case(name):
 
 @pytest.mark.parametrize("name", ["s4_rgg64k_f32", "s2_tri256_f64", "powerlaw", "disconnected"])
 def test_reordered_coarsening_matches_oracle(ctx, name):
-    """The adjacency-reordering option: the renumbering equals the oracle's (breadth-first
-    distance from node 0, then id; unreached nodes last), the lift equals the oracle's
+    """The adjacency-reordering option: the renumbering equals the oracle's (8-hop min label,
+    2-hop min label, id), the lift equals the oracle's
     coarsening of the renumbered graph read back in the caller's numbering, and every retained
     level equals the oracle's level of the renumbered graph, bit for bit.  A second call replays
     the captured graph with the same result."""
