@@ -253,16 +253,15 @@ k_bucket_count(int64_t m, const int32_t* __restrict__ eu, const int32_t* __restr
 
 // Step 2 (after the exclusive scans off_c, off_i of the sizes): every edge takes a slot of
 // its bucket by counting the bucket's size down, which leaves the counts zero for the next
-// call; the statistics (already read by the host) are zeroed too.  Inter edges store the key
-// (a << nb) | b and their eid, intra edges the super-node and their eid (emap -1).
+// call; the statistics (already read by the host) are zeroed too.  An inter edge stores one
+// 16-byte item (a, b, eid, 0), an intra edge one 8-byte item (super-node, eid) and emap -1:
+// one store per item.
 __global__ void __launch_bounds__(kThreads)
-k_bucket_scatter(int64_t m, int nb, const int32_t* __restrict__ eu,
-                 const int32_t* __restrict__ ev, const int32_t* __restrict__ lift,
-                 const int32_t* __restrict__ off_c, const int32_t* __restrict__ off_i,
-                 int32_t* cnt_c, int32_t* cnt_i, unsigned long long* __restrict__ stats,
-                 uint64_t* __restrict__ ckey, uint32_t* __restrict__ cval,
-                 uint32_t* __restrict__ ikey, uint32_t* __restrict__ ival,
-                 int32_t* __restrict__ emap) {
+k_bucket_scatter(int64_t m, const int32_t* __restrict__ eu, const int32_t* __restrict__ ev,
+                 const int32_t* __restrict__ lift, const int32_t* __restrict__ off_c,
+                 const int32_t* __restrict__ off_i, int32_t* cnt_c, int32_t* cnt_i,
+                 unsigned long long* __restrict__ stats, uint4* __restrict__ citem,
+                 uint2* __restrict__ iitem, int32_t* __restrict__ emap) {
     spc::pdl_wait();
     if (blockIdx.x == 0 && threadIdx.x < 4) stats[threadIdx.x] = 0ull;
     const int lane = threadIdx.x & 31;
@@ -287,12 +286,9 @@ k_bucket_scatter(int64_t m, int nb, const int32_t* __restrict__ eu,
         const int below = __popc(peers & ((1u << lane) - 1u));
         const int32_t q = (inter ? off_c : off_i)[b] + old - 1 - below;
         if (inter) {
-            const uint64_t hi = (uint64_t)(U < V ? V : U);
-            ckey[q] = ((uint64_t)b << nb) | hi;
-            cval[q] = (uint32_t)e;
+            citem[q] = make_uint4((uint32_t)b, (uint32_t)(U < V ? V : U), (uint32_t)e, 0u);
         } else {
-            ikey[q] = (uint32_t)U;
-            ival[q] = (uint32_t)e;
+            iitem[q] = make_uint2((uint32_t)U, (uint32_t)e);
             emap[e] = -1;
         }
     }
@@ -347,13 +343,12 @@ __device__ __forceinline__ void warp_sort_bucket(unsigned long long* sk, int s, 
 template <bool kInter>
 __global__ void __launch_bounds__(kBlockSortThreads, 3)
 k_bucket_sort_long(const int32_t* __restrict__ list, const unsigned long long* __restrict__ list_cnt,
-                   const int32_t* __restrict__ off, int nb, const uint64_t* __restrict__ key,
-                   const uint32_t* __restrict__ val, uint64_t* __restrict__ key2,
+                   const int32_t* __restrict__ off, int nb, const uint4* __restrict__ citem,
+                   const uint2* __restrict__ iitem, uint64_t* __restrict__ key2,
                    uint32_t* __restrict__ val2, uint8_t* __restrict__ head) {
     spc::pdl_wait();
     extern __shared__ unsigned long long sk[];  // kBlockBucket keys
     const int64_t cnt = (int64_t)*list_cnt;
-    const uint64_t bmask = (1ull << nb) - 1ull;
     for (int64_t q = blockIdx.x; q < cnt; q += gridDim.x) {
         const int32_t bkt = list[q];
         const int32_t lo = off[bkt];
@@ -364,8 +359,12 @@ k_bucket_sort_long(const int32_t* __restrict__ list, const unsigned long long* _
         for (int i = threadIdx.x; i < P; i += blockDim.x) {
             unsigned long long k = ~0ull;
             if (i < s) {
-                if constexpr (kInter) k = ((key[lo + i] & bmask) << 32) | val[lo + i];
-                else k = val[lo + i];
+                if constexpr (kInter) {
+                    const uint4 it = citem[lo + i];
+                    k = ((uint64_t)it.y << 32) | it.z;
+                } else {
+                    k = iitem[lo + i].y;
+                }
             }
             sk[i] = k;
         }
@@ -407,8 +406,12 @@ k_bucket_sort_long(const int32_t* __restrict__ list, const unsigned long long* _
         const int s = off[bkt + 1] - lo;
         if (s > kWarpBucket) continue;  // a CTA's bucket (above)
         for (int i = lane; i < s; i += 32) {
-            if constexpr (kInter) wk[i] = ((key[lo + i] & bmask) << 32) | val[lo + i];
-            else wk[i] = val[lo + i];
+            if constexpr (kInter) {
+                const uint4 it = citem[lo + i];
+                wk[i] = ((uint64_t)it.y << 32) | it.z;
+            } else {
+                wk[i] = iitem[lo + i].y;
+            }
         }
         __syncwarp();
         if (s <= 128)
@@ -424,29 +427,27 @@ k_bucket_sort_long(const int32_t* __restrict__ list, const unsigned long long* _
 // coarse edge.  Runs after k_bucket_sort_long, whose list it then empties.
 __global__ void __launch_bounds__(kThreads)
 k_bucket_rank_inter(int64_t cnt, int nb, const int32_t* __restrict__ off_c,
-                    const uint64_t* __restrict__ key, const uint32_t* __restrict__ val,
-                    uint64_t* __restrict__ key2, uint32_t* __restrict__ val2,
-                    uint8_t* __restrict__ head, unsigned long long* __restrict__ list_cnt) {
+                    const uint4* __restrict__ citem, uint64_t* __restrict__ key2,
+                    uint32_t* __restrict__ val2, uint8_t* __restrict__ head,
+                    unsigned long long* __restrict__ list_cnt) {
     spc::pdl_wait();
     if (blockIdx.x == 0 && threadIdx.x == 0) *list_cnt = 0ull;  // long buckets are sorted
     for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < cnt;
          p += (int64_t)gridDim.x * blockDim.x) {
-        const uint64_t k = key[p];
-        const uint32_t v = val[p];
-        const int64_t a = (int64_t)(k >> nb);
-        const int32_t lo = off_c[a], hi = off_c[a + 1];
+        const uint4 it = citem[p];
+        const uint32_t b = it.y, v = it.z;
+        const int32_t lo = off_c[it.x], hi = off_c[it.x + 1];
         if (hi - lo > kSmallBucket) continue;
         int32_t r = 0;
         bool first = true;
 #pragma unroll 4
         for (int32_t j = lo; j < hi; ++j) {
-            const uint64_t kj = key[j];
-            const uint32_t vj = val[j];
-            const bool same_before = kj == k && vj < v;
-            r += (kj < k || same_before) ? 1 : 0;
+            const uint4 jt = citem[j];
+            const bool same_before = jt.y == b && jt.z < v;
+            r += (jt.y < b || same_before) ? 1 : 0;
             first = first && !same_before;
         }
-        key2[lo + r] = k;
+        key2[lo + r] = ((uint64_t)it.x << nb) | b;
         val2[lo + r] = v;
         head[lo + r] = first ? 1 : 0;
     }
@@ -456,18 +457,19 @@ k_bucket_rank_inter(int64_t cnt, int nb, const int32_t* __restrict__ off_c,
 // bucket.  Runs after k_bucket_sort_long, whose list it then empties.
 __global__ void __launch_bounds__(kThreads)
 k_bucket_rank_intra(int64_t cnt, const int32_t* __restrict__ off_i,
-                    const uint32_t* __restrict__ ikey, const uint32_t* __restrict__ ival,
-                    uint32_t* __restrict__ ival2, unsigned long long* __restrict__ list_cnt) {
+                    const uint2* __restrict__ iitem, uint32_t* __restrict__ ival2,
+                    unsigned long long* __restrict__ list_cnt) {
     spc::pdl_wait();
     if (blockIdx.x == 0 && threadIdx.x == 0) *list_cnt = 0ull;  // long buckets are sorted
     for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < cnt;
          p += (int64_t)gridDim.x * blockDim.x) {
-        const uint32_t U = ikey[p], v = ival[p];
-        const int32_t lo = off_i[U], hi = off_i[U + 1];
+        const uint2 it = iitem[p];
+        const uint32_t v = it.y;
+        const int32_t lo = off_i[it.x], hi = off_i[it.x + 1];
         if (hi - lo > kSmallBucket) continue;
         int32_t r = 0;
 #pragma unroll 4
-        for (int32_t j = lo; j < hi; ++j) r += ival[j] < v ? 1 : 0;
+        for (int32_t j = lo; j < hi; ++j) r += iitem[j].y < v ? 1 : 0;
         ival2[lo + r] = v;
     }
 }
@@ -788,7 +790,7 @@ constexpr int64_t kRankWork = 48;
 // one CTA per long bucket, each with kBlockBucket keys of shared memory
 static spc_status sort_long_buckets(spc_context* ctx, bool inter, const int32_t* list,
                                     const unsigned long long* list_cnt, const int32_t* off,
-                                    int nb, const uint64_t* key, const uint32_t* val,
+                                    int nb, const uint4* citem, const uint2* iitem,
                                     uint64_t* key2, uint32_t* val2, uint8_t* head) {
     constexpr int smem = kBlockBucket * 8;
     static std::atomic<unsigned long long> attr_devs{0};  // devices already set up
@@ -803,10 +805,10 @@ static spc_status sort_long_buckets(spc_context* ctx, bool inter, const int32_t*
     const int grid = ctx->num_sms * 3;
     if (inter) {
         SPC_LAUNCH(ctx, k_bucket_sort_long<true>, grid, kBlockSortThreads, smem, list, list_cnt,
-                   off, nb, key, val, key2, val2, head);
+                   off, nb, citem, iitem, key2, val2, head);
     } else {
         SPC_LAUNCH(ctx, k_bucket_sort_long<false>, grid, kBlockSortThreads, smem, list, list_cnt,
-                   off, nb, key, val, key2, val2, head);
+                   off, nb, citem, iitem, key2, val2, head);
     }
     return SPC_OK;
 }
@@ -830,6 +832,11 @@ spc_status contract_typed(spc_context* ctx, const GraphView& g, const int32_t* l
     uint32_t* ikey = W.i_key.as<uint32_t>();
     uint32_t* ival = W.i_val.as<uint32_t>();
     int32_t* emap = lv.emap.as<int32_t>();
+    // the bucket path's scattered items, one store each
+    SPC_TRY(ensure(ctx, W.c_item, (size_t)(m + 1) * 16));
+    SPC_TRY(ensure(ctx, W.i_item, (size_t)(m + 1) * 8));
+    uint4* citem = W.c_item.as<uint4>();
+    uint2* iitem = W.i_item.as<uint2>();
     // ---- bucket sizes, offsets and ranking work ------------------------------------------
     // the counts are zero between calls (the scatter counts them down); a call that stopped
     // in between leaves them dirty
@@ -865,9 +872,9 @@ spc_status contract_typed(spc_context* ctx, const GraphView& g, const int32_t* l
     const bool buckets = bv[3] <= kBlockBucket && bv[5] <= kBlockBucket;
     if (buckets) {
         if (m > 0) {
-            SPC_LAUNCH(ctx, k_bucket_scatter, gm, kThreads, 0, m, nb, W.eu.as<int32_t>(),
-                       W.ev.as<int32_t>(), lift, off_c, off_i, cnt_c, cnt_i, bstats, ckey, cval,
-                       ikey, ival, emap);
+            SPC_LAUNCH(ctx, k_bucket_scatter, gm, kThreads, 0, m, W.eu.as<int32_t>(),
+                       W.ev.as<int32_t>(), lift, off_c, off_i, cnt_c, cnt_i, bstats, citem,
+                       iitem, emap);
         }
     } else {
         SPC_CUDA(cudaMemsetAsync(cnt_c, 0, (size_t)(n_c + 1) * 8, ctx->stream));
@@ -905,9 +912,9 @@ spc_status contract_typed(spc_context* ctx, const GraphView& g, const int32_t* l
         if (m_intra > 0) {
             if (long_i > 0)
                 SPC_TRY(sort_long_buckets(ctx, false, list_i, bstats + 7, off_i, nb, nullptr,
-                                          ival, nullptr, ival2, nullptr));
+                                          iitem, nullptr, ival2, nullptr));
             SPC_LAUNCH(ctx, k_bucket_rank_intra, grid_for(m_intra, kThreads, maxb), kThreads, 0,
-                       m_intra, off_i, ikey, ival, ival2, bstats + 7);
+                       m_intra, off_i, iitem, ival2, bstats + 7);
         }
         SPC_LAUNCH(ctx, (k_segsum_short<WT, Acc>), grid_for(n_c, kThreads, maxb), kThreads, 0,
                    n_c, off_i, ival2, nullptr, W.w_und.as<WT>(), self_mass,
@@ -948,11 +955,11 @@ spc_status contract_typed(spc_context* ctx, const GraphView& g, const int32_t* l
     if (buckets) {
         if (m_inter > 0) {
             if (long_c > 0)
-                SPC_TRY(sort_long_buckets(ctx, true, list_c, bstats + 6, off_c, nb, ckey, cval,
-                                          W.c_key2.as<uint64_t>(), W.c_val2.as<uint32_t>(),
-                                          head));
+                SPC_TRY(sort_long_buckets(ctx, true, list_c, bstats + 6, off_c, nb, citem,
+                                          nullptr, W.c_key2.as<uint64_t>(),
+                                          W.c_val2.as<uint32_t>(), head));
             SPC_LAUNCH(ctx, k_bucket_rank_inter, grid_for(m_inter, kThreads, maxb), kThreads, 0,
-                       m_inter, nb, off_c, ckey, cval, W.c_key2.as<uint64_t>(),
+                       m_inter, nb, off_c, citem, W.c_key2.as<uint64_t>(),
                        W.c_val2.as<uint32_t>(), head, bstats + 6);
         }
         skey = W.c_key2.as<uint64_t>();

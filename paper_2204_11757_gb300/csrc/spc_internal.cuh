@@ -102,6 +102,7 @@ struct Work {
     Buf c_key, c_val, c_key2, c_val2, c_flag, c_pos, c_head, cU, cV;    // S7
     Buf t_key, t_val, t_key2, t_val2, up_deg, low_deg, deg_c, ufirst, lstart;
     Buf i_key, i_val, i_key2, i_val2, long_segs;                // intra edges (self-mass)
+    Buf c_item, i_item;                                         // bucket items (16 / 8 bytes)
     // contraction buckets: sizes (zero between calls), offsets, ranking statistics
     Buf b_cnt, b_off, b_stats, b_list;
     bool b_dirty = true;
@@ -279,6 +280,25 @@ __device__ __forceinline__ void pdl_wait() {
 #if defined(__CUDA_ARCH__) && __CUDA_ARCH__ >= 900
     asm volatile("griddepcontrol.wait;" ::: "memory");
 #endif
+}
+
+// cp.async copies of one 4- or 8-byte element from global into shared memory (sm_80 and
+// later), completed by cp_async_wait_all
+__device__ __forceinline__ void cp_async_4(void* smem, const void* gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_8(void* smem, const void* gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(sa), "l"(gmem) : "memory");
+}
+template <class T>
+__device__ __forceinline__ void cp_async_elem(T* smem, const T* gmem) {
+    if constexpr (sizeof(T) == 8) cp_async_8(smem, gmem);
+    else cp_async_4(smem, gmem);
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
 }
 
 // The rows of a tile of consecutive CSR entries [base, end), for kernels that run flat over the

@@ -415,8 +415,8 @@ __device__ __forceinline__ unsigned long long block_incl_scan(unsigned long long
     return r;
 }
 
-// smallest bin whose cumulative count reaches `need` (all bins when need >= m); leaves the
-// histogram zero for the next level.  Each thread holds 32 consecutive bins in registers; the
+// smallest bin whose cumulative count reaches `need` (all bins when need >= m); the histogram
+// stays for a later attempt of the same selection.  Each thread holds 32 consecutive bins in registers; the
 // block scan of the thread totals is two rounds of warp shuffles.
 __global__ void __launch_bounds__(1024)
 k_pick_tau(uint32_t* __restrict__ hist, int64_t need, uint32_t* __restrict__ tau_top) {
@@ -436,8 +436,6 @@ k_pick_tau(uint32_t* __restrict__ hist, int64_t need, uint32_t* __restrict__ tau
         v[4 * j + 3] = q.w;
         loc += (unsigned long long)q.x + q.y + q.z + q.w;
     }
-#pragma unroll
-    for (int j = 0; j < kPer / 4; ++j) h4[j] = make_uint4(0u, 0u, 0u, 0u);
     unsigned long long x = loc;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -937,8 +935,9 @@ spc_status finish_select(spc_context* ctx, const GraphView& g, const SelectArgs&
     return SPC_OK;
 }
 
-// key_hist: the score-prefix histogram (kTauBins words, left zero by k_pick_tau), then the
-// radix-select histograms of every round (zeroed by k_rsel_init); zeroed once on allocation
+// key_hist: the score-prefix histogram (kTauBins words, zeroed before each selection's first
+// attempt and kept for its later ones), then the radix-select histograms of every round
+// (zeroed by k_rsel_init); zeroed once on allocation
 constexpr int kTauBins = 32768;
 constexpr size_t kKeyHistBytes = (size_t)(kTauBins + SelBits<uint64_t>::kRounds * kSelBins) * 4;
 static spc_status ensure_key_hist(spc_context* ctx) {
@@ -984,9 +983,14 @@ spc_status select_typed(spc_context* ctx, const GraphView& g, const KT* key,
                                               32768 * 4));
                 attr_devs.fetch_or(bit);
             }
-            if (attempt > 0) SPC_LAUNCH(ctx, k_bump_slab, 1, 32, 0, tau_top, tau_lo);
-            SPC_LAUNCH(ctx, k_key_hist<KT>, ctx->num_sms, 1024, 32768 * 4, m, key, tau_shift,
-                       W.key_hist.as<uint32_t>());
+            if (attempt > 0) {
+                // the histogram of every key is still there: only the threshold moves up
+                SPC_LAUNCH(ctx, k_bump_slab, 1, 32, 0, tau_top, tau_lo);
+            } else {
+                SPC_CUDA(cudaMemsetAsync(W.key_hist.p, 0, (size_t)kTauBins * 4, ctx->stream));
+                SPC_LAUNCH(ctx, k_key_hist<KT>, ctx->num_sms, 1024, 32768 * 4, m, key,
+                           tau_shift, W.key_hist.as<uint32_t>());
+            }
             SPC_LAUNCH(ctx, k_pick_tau, 1, 1024, 0, W.key_hist.as<uint32_t>(), need, tau_top);
         } else if (attempt > 0) {
             SPC_LAUNCH(ctx, k_bump_slab, 1, 32, 0, tau_top, tau_lo);

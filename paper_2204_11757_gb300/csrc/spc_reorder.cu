@@ -20,7 +20,10 @@ constexpr int kReorderHops = 8;  // the cluster label's hops
 constexpr int kReorderSub = 2;   // the sub-cluster label's hops
 
 // one synchronous round of the labels: out[x] = min(in[x], min over the row of x of in[y]);
-// the round that makes the sub-cluster label also copies it to `sub` (may be null)
+// the round that makes the sub-cluster label also copies it to `sub` (may be null).  A row is
+// read in batches of kLabelBatch columns whose label gathers are all in flight together.
+constexpr int kLabelBatch = 8;
+
 __global__ void __launch_bounds__(kThreads)
 k_label_round(int64_t n, const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
               const int32_t* __restrict__ in, int32_t* __restrict__ out,
@@ -30,10 +33,16 @@ k_label_round(int64_t n, const int64_t* __restrict__ rowptr, const int32_t* __re
          x += (int64_t)gridDim.x * blockDim.x) {
         int32_t m = in ? in[x] : (int32_t)x;  // round 1 starts from the ids
         const int64_t r1 = rowptr[x + 1];
-        for (int64_t j = rowptr[x]; j < r1; ++j) {
-            const int32_t y = col[j];
-            const int32_t l = in ? in[y] : y;
-            m = l < m ? l : m;
+        for (int64_t j0 = rowptr[x]; j0 < r1; j0 += kLabelBatch) {
+            int32_t y[kLabelBatch];
+#pragma unroll
+            for (int t = 0; t < kLabelBatch; ++t) y[t] = j0 + t < r1 ? col[j0 + t] : -1;
+#pragma unroll
+            for (int t = 0; t < kLabelBatch; ++t) {
+                if (y[t] < 0) continue;
+                const int32_t l = in ? in[y[t]] : y[t];
+                m = l < m ? l : m;
+            }
         }
         out[x] = m;
         if (sub) sub[x] = m;
@@ -124,39 +133,114 @@ k_perm_rows(int64_t n, const uint32_t* __restrict__ order, const int64_t* __rest
     }
 }
 
-// Renumbered row r (old row order[r]) of at most kShortRow entries: the new columns perm[y]
-// staged in shared memory (one column of a [kShortRow][kThreads] array per thread, so the
-// threads of a warp hit distinct banks), each ranked among the row's d entries (d^2
-// comparisons), and written in ascending order with their weights.  Longer rows are listed for
-// the radix path.
+// Renumbered rows of at most kShortRow entries, one warp per 32 consecutive new rows (whose
+// entries form one contiguous run of the new CSR).  The warp copies each of its rows into
+// shared memory (lanes along the row: the old row's columns mapped through perm, its weights,
+// and the row's index within the tile), then every entry is ranked among its row's entries
+// (at most kShortRow comparisons) and written at its place: the stores of a warp instruction
+// land in the few rows that 32 consecutive entries span.  Rows longer than kShortRow are listed
+// for the radix path; a tile whose rows exceed kPermStage entries is ranked the same way from
+// global memory.
+constexpr int kPermStage = 512;  // entries staged per warp
+// warps per block: the stage of 8 warps of binary64 weights would pass 48 KB
 template <class WT>
-__global__ void __launch_bounds__(kThreads)
+__host__ __device__ constexpr int perm_warps() { return sizeof(WT) == 8 ? 4 : 8; }
+
+template <class WT>
+__global__ void __launch_bounds__(perm_warps<WT>() * 32)
 k_perm_short(int64_t n, const uint32_t* __restrict__ order, const int32_t* __restrict__ perm,
              const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
              const WT* __restrict__ w, const int64_t* __restrict__ rowptr_new,
              int32_t* __restrict__ col_new, WT* __restrict__ w_new,
              int32_t* __restrict__ long_rows, int32_t* long_count) {
     spc::pdl_wait();
-    __shared__ int32_t s_c[kShortRow][kThreads];
-    int32_t* const c = &s_c[0][threadIdx.x];  // entry k at c[k * kThreads]
-    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n;
-         r += (int64_t)gridDim.x * blockDim.x) {
-        const uint32_t x = order[r];
-        const int64_t r0 = rowptr[x];
-        const int d = (int)(rowptr[x + 1] - r0);
-        if (d > kShortRow) {
-            long_rows[atomicAdd(long_count, 1)] = (int32_t)r;
-            continue;
+    constexpr int kPermWarps = perm_warps<WT>();
+    __shared__ int32_t s_col[kPermWarps][kPermStage];
+    __shared__ WT s_w[kPermWarps][kPermStage];
+    __shared__ uint8_t s_row[kPermWarps][kPermStage];
+    __shared__ int32_t s_off[kPermWarps][33];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    int32_t* const sc = s_col[wib];
+    WT* const sw = s_w[wib];
+    uint8_t* const sr = s_row[wib];
+    int32_t* const so = s_off[wib];
+    const int64_t nwarps = (int64_t)gridDim.x * kPermWarps;
+    for (int64_t r0 = ((int64_t)blockIdx.x * kPermWarps + wib) * 32; r0 < n; r0 += nwarps * 32) {
+        const int64_t r = r0 + lane;
+        int64_t rs = 0;
+        int d = 0;
+        if (r < n) {
+            const uint32_t x = order[r];
+            rs = rowptr[x];
+            d = (int)(rowptr[x + 1] - rs);
+            if (d > kShortRow) {
+                long_rows[atomicAdd(long_count, 1)] = (int32_t)r;
+                d = 0;
+            }
         }
-        for (int k = 0; k < d; ++k) c[k * kThreads] = perm[col[r0 + k]];
-        const int64_t base = rowptr_new[r];
-        for (int k = 0; k < d; ++k) {
-            const int32_t ck = c[k * kThreads];
-            int rank = 0;
-            for (int k2 = 0; k2 < d; ++k2) rank += c[k2 * kThreads] < ck ? 1 : 0;
-            col_new[base + rank] = ck;
-            w_new[base + rank] = w[r0 + k];
+        // offsets of the short rows within the tile's run of the new CSR (a long row's entries
+        // are placed by the radix path; its slot here is empty)
+        int o = d;
+#pragma unroll
+        for (int k = 1; k < 32; k <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, o, k);
+            if (lane >= k) o += t;
         }
+        const int total = __shfl_sync(0xffffffffu, o, 31);
+        o -= d;
+        if (total <= kPermStage) {
+            so[lane] = o;
+            if (lane == 31) so[32] = total;
+            // the rows' old columns and weights, every copy in flight together
+#pragma unroll 8
+            for (int k = 0; k < 32; ++k) {  // row k of the tile, lanes along it
+                const int dk = __shfl_sync(0xffffffffu, d, k);
+                const int ok = __shfl_sync(0xffffffffu, o, k);
+                const int64_t rk = __shfl_sync(0xffffffffu, rs, k);
+                if (lane < dk) {
+                    cp_async_4(sc + ok + lane, col + rk + lane);
+                    cp_async_elem(sw + ok + lane, w + rk + lane);
+                    sr[ok + lane] = (uint8_t)k;
+                }
+            }
+            cp_async_wait_all();
+            __syncwarp();
+            // the new columns: the gathers of perm, four per lane in flight
+            for (int i0 = 0; i0 < total; i0 += 128) {
+                int32_t y[4];
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    const int i = i0 + 32 * t + lane;
+                    y[t] = i < total ? perm[sc[i]] : 0;
+                }
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    const int i = i0 + 32 * t + lane;
+                    if (i < total) sc[i] = y[t];
+                }
+            }
+            __syncwarp();
+            for (int i = lane; i < total; i += 32) {
+                const int k = sr[i];
+                const int lo = so[k], hi = so[k + 1];
+                const int32_t ci = sc[i];
+                int rank = 0;
+                for (int j = lo; j < hi; ++j) rank += sc[j] < ci ? 1 : 0;
+                const int64_t dest = rowptr_new[r0 + k] + rank;
+                col_new[dest] = ci;
+                w_new[dest] = sw[i];
+            }
+        } else if (d > 0) {  // a tile too large for the stage: each lane ranks its own row
+            const int64_t base = rowptr_new[r];
+            for (int k = 0; k < d; ++k) {
+                const int32_t ck = perm[col[rs + k]];
+                int rank = 0;
+                for (int j = 0; j < d; ++j) rank += perm[col[rs + j]] < ck ? 1 : 0;
+                col_new[base + rank] = ck;
+                w_new[base + rank] = w[rs + k];
+            }
+        }
+        __syncwarp();  // the next tile overwrites the stage
     }
 }
 
@@ -278,7 +362,8 @@ spc_status reorder_typed(spc_context* ctx, const GraphView& g, GraphView& out) {
     int32_t* long_rows = W.long_rows.as<int32_t>();
     int32_t* long_count = W.counters.as<int32_t>() + 59;
     SPC_LAUNCH(ctx, k_set_count, 1, 32, 0, long_count);
-    SPC_LAUNCH(ctx, k_perm_short<WT>, gn, kThreads, 0, n, order, perm, g.rowptr, g.col,
+    SPC_LAUNCH(ctx, k_perm_short<WT>, grid_for((n + 31) / 32, perm_warps<WT>(), maxb),
+               perm_warps<WT>() * 32, 0, n, order, perm, g.rowptr, g.col,
                static_cast<const WT*>(g.w), rowptr_new, col_new, w_new, long_rows,
                long_count);
     int64_t n_long = 0;

@@ -634,25 +634,6 @@ k_score_warp_row(int64_t n, const int64_t* __restrict__ rowptr, const int32_t* _
 // scattered (random node order) the lines are evicted between the steps and each step reads a
 // sector from DRAM again.  Rows b longer than kStageCap entries, or a tile whose rows a exceed
 // kStageA entries, are walked in place.
-// cp.async copies of one 4- or 8-byte element from global into shared memory (sm_80 and
-// later), completed by cp_async_wait_all
-__device__ __forceinline__ void cp_async_4(void* smem, const void* gmem) {
-    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(sa), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_8(void* smem, const void* gmem) {
-    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(sa), "l"(gmem) : "memory");
-}
-template <class T>
-__device__ __forceinline__ void cp_async_elem(T* smem, const T* gmem) {
-    if constexpr (sizeof(T) == 8) cp_async_8(smem, gmem);
-    else cp_async_4(smem, gmem);
-}
-__device__ __forceinline__ void cp_async_wait_all() {
-    asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
-}
-
 constexpr int kStageCap = 32;
 constexpr int kStageStr = kStageCap + 1;  // padded: lanes of one step hit different banks
 constexpr int kStageA = 256;
