@@ -817,6 +817,8 @@ k_score_staged(int64_t m, const int32_t* __restrict__ eu, const int32_t* __restr
 // row that starts or ends inside a 16-byte chunk brings its neighbour along, never read.  Then
 // every lane walks its edge's union from shared memory, one 8-byte load per step, with the
 // uniform step of k_score_edges (the same bits).  Rows that do not fit are walked in place.
+// Binary32 inputs have their symmetry checked by the fingerprint of the normalise kernel, so
+// the walk carries no mirror check (and no arithmetic count, which serves binary64 only).
 constexpr int kPkWarps = 8;
 constexpr int kPkA = 192;  // entries of the tile's row-a slice staged per warp
 constexpr int kPkB = 576;  // entries of the tile's 32 rows b staged per warp
@@ -843,10 +845,8 @@ __device__ __forceinline__ void cp_async_16(void* smem, const void* gmem) {
 template <class KT>
 __global__ void __launch_bounds__(kPkWarps * 32)
 k_score_packed(int64_t m, const int32_t* __restrict__ eu, const int32_t* __restrict__ ev,
-               const int64_t* __restrict__ rowptr, const int32_t* __restrict__ col,
-               const uint2* __restrict__ pk, KT* __restrict__ score, const void* __restrict__ w,
-               const void* __restrict__ w_und, int wsize, int validate, uint32_t* status,
-               unsigned long long* __restrict__ ops) {
+               const int64_t* __restrict__ rowptr, const uint2* __restrict__ pk,
+               KT* __restrict__ score, const uint32_t* status) {
     spc::pdl_wait();
     if (*status) return;
     extern __shared__ __align__(16) uint2 pk_stage[];
@@ -856,8 +856,6 @@ k_score_packed(int64_t m, const int32_t* __restrict__ eu, const int32_t* __restr
     const uint4* const pk16 = reinterpret_cast<const uint4*>(pk);
     constexpr int32_t kEnd = 0x7fffffff;
     const uint2 kEndPair = make_uint2((uint32_t)kEnd, 0u);
-    uint32_t n_add = 0, n_sub = 0;
-    bool asym = false;
     const uint64_t keep = l2_policy_evict_last();
     const int64_t step_e = (int64_t)gridDim.x * kPkWarps * 32;
     for (int64_t e0 = ((int64_t)blockIdx.x * kPkWarps + wib) * 32; e0 < m; e0 += step_e) {
@@ -903,7 +901,7 @@ k_score_packed(int64_t m, const int32_t* __restrict__ eu, const int32_t* __restr
             const uint2* A = a_staged ? sa + (ra - 2 * ac0) : pk + ra;
             const uint2* B = b_staged ? sb + 2 * choff + (rb & 1) : pk + rb;
             const int na = (int)da, nb = (int)db;
-            int i = 0, j = 0, jm = -1;
+            int i = 0, j = 0;
             uint2 xa = na > 0 ? A[0] : kEndPair;
             uint2 xb = nb > 0 ? B[0] : kEndPair;
             float s = 0.f;
@@ -911,27 +909,16 @@ k_score_packed(int64_t m, const int32_t* __restrict__ eu, const int32_t* __restr
                 const int32_t ca = (int32_t)xa.x, cb = (int32_t)xb.x;
                 if (ca == kEnd && cb == kEnd) break;
                 const bool ta = ca <= cb, tb = cb <= ca;
-                jm = (tb && cb == a) ? j : jm;  // the mirror entry (b, a)
                 const float pa = ta ? __uint_as_float(xa.y) : 0.f;
                 const float pb = tb ? __uint_as_float(xb.y) : 0.f;
                 s = p_add(s, p_absdiff(pa, pb));
-                ++n_add;
-                n_sub += (ta && tb) ? 1u : 0u;
                 if (ta) { ++i; xa = i < na ? A[i] : kEndPair; }
                 if (tb) { ++j; xb = j < nb ? B[j] : kEndPair; }
             }
             score[e] = key_bits(s);
-            if (validate)
-                asym = asym || jm < 0 ||
-                       weight_bits(w, wsize, rb + jm) != weight_bits(w_und, wsize, e);
-        } else if (hub && validate && da <= kLongRow) {
-            // hub edge (k_score_hub): a long row b only holds the mirror of this entry
-            asym = asym || !has_mirror(col, w, wsize, rb, rb + db, a, weight_bits(w_und, wsize, e));
         }
         __syncwarp();  // the next tile overwrites the stage
     }
-    if (asym) atomicOr(status, DEV_NOT_SYMMETRIC);
-    count_ops(ops, n_add, n_sub);
 }
 
 // ---- hub edges ----------------------------------------------------------------------------------
@@ -1324,10 +1311,13 @@ static spc_status launch_score_packed(spc_context* ctx, int64_t m, const GraphVi
     }
     const int64_t tiles = (m + 31) / 32;
     const int grid = grid_for(tiles, kPkWarps, ctx->num_sms * 4);
+    // binary32 rows only: symmetry is checked by the fingerprint of the normalise kernel, and
+    // the arithmetic count serves the binary64 roofline alone
+    (void)wsize;
+    (void)vflag;
+    (void)count;
     SPC_LAUNCH(ctx, k_score_packed<Key>, grid, kPkWarps * 32, kPkSmem, m, W.eu.as<int32_t>(),
-               W.ev.as<int32_t>(), g.rowptr, g.col, W.pk.as<uint2>(), static_cast<Key*>(score),
-               g.w, W.w_und.p, wsize, vflag, status,
-               count ? op_counter(ctx, "k_score_packed<Key>", 4) : nullptr);
+               W.ev.as<int32_t>(), g.rowptr, W.pk.as<uint2>(), static_cast<Key*>(score), status);
     return SPC_OK;
 }
 

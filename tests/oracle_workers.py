@@ -45,3 +45,12 @@ def coarsen_config(name: str, one_level: bool = False):
         lv = O.coarsen_level(g, max(1, g.n // cfg["ratio"]))
         return [lv], lv.lift
     return O.coarsen(g, cfg["ratio"], cfg["mode"])
+
+
+def coarsen_config_reordered(name: str):
+    """The oracle's coarsening of a named workload under the adjacency-reordering option: the
+    levels of the renumbered graph, the composed lift in the caller's numbering, and perm."""
+    from oracle import oracle as O
+    from paper_2204_11757_gb300 import inputs as I
+    g, cfg = I.config_graph(name)
+    return O.coarsen_reordered(g, cfg["ratio"], cfg["mode"])

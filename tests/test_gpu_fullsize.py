@@ -2,7 +2,8 @@
 
 Every configuration is compared with the oracle bit for bit, at every level:
 * the 2048x2048 FP64 mesh (6 halving levels) and the 129^3 tetrahedral mesh (7 levels);
-* the 2^23-point random geometric graph, 8 halving levels and one level straight to n/256;
+* the 2^23-point random geometric graph, 8 halving levels, one level straight to n/256, and 8
+  levels under the adjacency-reordering option;
 * the 10,000-mesh batch (3 levels): every graph of the batch against the oracle run on that
   graph alone (graphs of a batch are independent).
 Scores, lifts, edge maps, coarse CSRs, coarse weights, self-mass and the carried mass of the
@@ -32,6 +33,7 @@ def oracle_runs():
     O.build()  # compiled once here, not by every worker at the same time
     pool = W.pool()
     fut = {"c4_rgg8m_f32": pool.submit(W.coarsen_config, "c4_rgg8m_f32"),
+           "c4_reordered": pool.submit(W.coarsen_config_reordered, "c4_rgg8m_f32"),
            "c4_one": pool.submit(W.coarsen_config, "c4_rgg8m_f32", True),
            "c3_tet129_f64": pool.submit(W.coarsen_config, "c3_tet129_f64"),
            "c2_tri2048_f64": pool.submit(W.coarsen_config, "c2_tri2048_f64")}
@@ -109,6 +111,26 @@ def test_rgg_one_level_bitexact(ctx, oracle_runs):
     assert nc == levels[0].n_c
     _same(lift, total)
     _same_level(got[0], levels[0])
+
+
+def test_rgg_reordered_bitexact(ctx, oracle_runs):
+    """The adjacency-reordering option on the 2^23-point RGG, 8 levels: the renumbering, the
+    composed lift in the caller's numbering and every level of the renumbered graph."""
+    from paper_2204_11757_gb300 import api
+    g, cfg = I.config_graph("c4_rgg8m_f32")
+    L = int(round(np.log2(cfg["ratio"])))
+    lift, nc, st = ctx.coarsen(api.CSR.from_graph(g), g.n // cfg["ratio"], levels=L,
+                               reorder=True)
+    perm = ctx.reorder_perm(g.n)
+    got = ctx.levels()
+    del g
+    levels, total, perm_ref = oracle_runs[0]["c4_reordered"].result()
+    _same(perm, perm_ref)
+    assert len(got) == len(levels) == L
+    assert nc == levels[-1].n_c
+    _same(lift, total)
+    for lv, ref in zip(got, levels):
+        _same_level(lv, ref)
 
 
 def test_batch10k_every_graph(ctx, oracle_runs):
