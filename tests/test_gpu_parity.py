@@ -384,6 +384,46 @@ def test_contract_star_rows_paths(ctx, dt, center_last):
     _check_level(lv, O.Level(n_c=n, lift=lift, coarse=ref))
 
 
+@pytest.mark.parametrize("dt", [np.float64, np.float32])
+def test_contract_long_lower_row_on_bucket_path(ctx, dt):
+    """A star of 100 leaves beside a 100 x 100 grid, every node its own super-node with the
+    star's centre numbered last: its coarse row has 100 lower entries, past one thread's share
+    (32), while the grid's many short rows keep the lower rows on the bucket path; the long row
+    is filled by a warp.  The coarse graph equals the oracle's."""
+    api = _api()
+    rng = np.random.default_rng(11)
+    side, leaves = 100, 100
+    ng = side * side
+    n = ng + leaves + 1
+    gu, gv = [], []
+    for r in range(side):
+        for c in range(side):
+            x = r * side + c
+            if c + 1 < side:
+                gu.append(x); gv.append(x + 1)
+            if r + 1 < side:
+                gu.append(x); gv.append(x + side)
+    center = n - 1
+    su = np.full(leaves, center)
+    sv = np.arange(ng, ng + leaves)
+    eu = np.concatenate([np.array(gu), su]); ev = np.concatenate([np.array(gv), sv])
+    w = rng.uniform(0.5, 2.0, eu.size).astype(dt)
+    g = I.csr_from_edges(n, eu, ev, w)
+    lift = np.empty(n, dtype=np.int32)
+    lift[:n - 1] = rng.permutation(n - 1)
+    lift[center] = n - 1
+    ref = O.contract(g, lift, n)
+    ctx.time_kernel("*")
+    try:
+        lv = ctx.contract(api.CSR.from_graph(g), torch.from_numpy(lift).cuda(), n)
+        prof = ctx.kernel_profile()
+    finally:
+        ctx.time_kernel(None)
+    assert any("k_fill_lower_rows" in k for k in prof), sorted(prof)
+    assert any("k_fill_lower_long" in k for k in prof), sorted(prof)
+    _check_level(lv, O.Level(n_c=n, lift=lift, coarse=ref))
+
+
 def test_repeated_coarsening_replays_with_giant_super_nodes(ctx):
     """Three disjoint cliques K_150 (11,175 edges each) joined by two edges, coarsened to 3:
     three giant super-nodes.  Every value the host reads while coarsening must be the same on
