@@ -397,7 +397,6 @@ static spc_status reserve_work(spc_context* ctx, int64_t n, int64_t m, int64_t B
     SPC_TRY(ensure(ctx, W.c_key, M * 8));
     SPC_TRY(ensure(ctx, W.c_item, M * 16));
     SPC_TRY(ensure(ctx, W.lower_long, 16));
-    SPC_TRY(ensure(ctx, W.w_sort, M * 4));
     SPC_TRY(ensure(ctx, W.i_item, M * 8));
     SPC_TRY(ensure(ctx, W.c_val, M * 4));
     SPC_TRY(ensure(ctx, W.c_key2, M * 8));

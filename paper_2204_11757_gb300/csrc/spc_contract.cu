@@ -254,16 +254,14 @@ k_bucket_count(int64_t m, const int32_t* __restrict__ eu, const int32_t* __restr
 // Step 2 (after the exclusive scans off_c, off_i of the sizes): every edge takes a slot of
 // its bucket by counting the bucket's size down, which leaves the counts zero for the next
 // call; the statistics (already read by the host) are zeroed too.  An inter edge stores one
-// 16-byte item (a, b, eid, w) -- w the bits of its 4-byte weight (`w32`; 0 for binary64
-// weights, which do not fit) -- an intra edge one 8-byte item (super-node, eid) and emap -1:
+// 16-byte item (a, b, eid, 0), an intra edge one 8-byte item (super-node, eid) and emap -1:
 // one store per item.
 __global__ void __launch_bounds__(kThreads)
 k_bucket_scatter(int64_t m, const int32_t* __restrict__ eu, const int32_t* __restrict__ ev,
                  const int32_t* __restrict__ lift, const int32_t* __restrict__ off_c,
                  const int32_t* __restrict__ off_i, int32_t* cnt_c, int32_t* cnt_i,
-                 unsigned long long* __restrict__ stats, const uint32_t* __restrict__ w32,
-                 uint4* __restrict__ citem, uint2* __restrict__ iitem,
-                 int32_t* __restrict__ emap) {
+                 unsigned long long* __restrict__ stats, uint4* __restrict__ citem,
+                 uint2* __restrict__ iitem, int32_t* __restrict__ emap) {
     spc::pdl_wait();
     if (blockIdx.x == 0 && threadIdx.x < 4) stats[threadIdx.x] = 0ull;
     const int lane = threadIdx.x & 31;
@@ -288,8 +286,7 @@ k_bucket_scatter(int64_t m, const int32_t* __restrict__ eu, const int32_t* __res
         const int below = __popc(peers & ((1u << lane) - 1u));
         const int32_t q = (inter ? off_c : off_i)[b] + old - 1 - below;
         if (inter) {
-            citem[q] = make_uint4((uint32_t)b, (uint32_t)(U < V ? V : U), (uint32_t)e,
-                                  w32 ? w32[e] : 0u);
+            citem[q] = make_uint4((uint32_t)b, (uint32_t)(U < V ? V : U), (uint32_t)e, 0u);
         } else {
             iitem[q] = make_uint2((uint32_t)U, (uint32_t)e);
             emap[e] = -1;
@@ -305,10 +302,8 @@ k_bucket_scatter(int64_t m, const int32_t* __restrict__ eu, const int32_t* __res
 template <bool kInter, int kPer>
 __device__ __forceinline__ void warp_sort_bucket(unsigned long long* sk, int s, int lane,
                                                  int32_t bkt, int32_t lo, int nb,
-                                                 const uint32_t* __restrict__ w32,
                                                  uint64_t* __restrict__ key2,
                                                  uint32_t* __restrict__ val2,
-                                                 uint32_t* __restrict__ wsort,
                                                  uint8_t* __restrict__ head) {
     unsigned long long k[kPer];
     int r[kPer];
@@ -333,7 +328,6 @@ __device__ __forceinline__ void warp_sort_bucket(unsigned long long* sk, int s, 
         if constexpr (kInter) {
             key2[lo + i] = ((uint64_t)bkt << nb) | (x >> 32);
             val2[lo + i] = (uint32_t)x;
-            if (wsort) wsort[lo + i] = w32[(uint32_t)x];
             head[lo + i] = (i == 0 || (sk[i - 1] >> 32) != (x >> 32)) ? 1 : 0;
         } else {
             val2[lo + i] = (uint32_t)x;
@@ -350,9 +344,8 @@ template <bool kInter>
 __global__ void __launch_bounds__(kBlockSortThreads, 3)
 k_bucket_sort_long(const int32_t* __restrict__ list, const unsigned long long* __restrict__ list_cnt,
                    const int32_t* __restrict__ off, int nb, const uint4* __restrict__ citem,
-                   const uint2* __restrict__ iitem, const uint32_t* __restrict__ w32,
-                   uint64_t* __restrict__ key2, uint32_t* __restrict__ val2,
-                   uint32_t* __restrict__ wsort, uint8_t* __restrict__ head) {
+                   const uint2* __restrict__ iitem, uint64_t* __restrict__ key2,
+                   uint32_t* __restrict__ val2, uint8_t* __restrict__ head) {
     spc::pdl_wait();
     extern __shared__ unsigned long long sk[];  // kBlockBucket keys
     const int64_t cnt = (int64_t)*list_cnt;
@@ -396,7 +389,6 @@ k_bucket_sort_long(const int32_t* __restrict__ list, const unsigned long long* _
                 const uint64_t b = k >> 32;
                 key2[lo + i] = ((uint64_t)bkt << nb) | b;
                 val2[lo + i] = (uint32_t)k;
-                if (wsort) wsort[lo + i] = w32[(uint32_t)k];
                 head[lo + i] = (i == 0 || (sk[i - 1] >> 32) != b) ? 1 : 0;
             } else {
                 val2[lo + i] = (uint32_t)k;
@@ -423,22 +415,21 @@ k_bucket_sort_long(const int32_t* __restrict__ list, const unsigned long long* _
         }
         __syncwarp();
         if (s <= 128)
-            warp_sort_bucket<kInter, 4>(wk, s, lane, bkt, lo, nb, w32, key2, val2, wsort, head);
+            warp_sort_bucket<kInter, 4>(wk, s, lane, bkt, lo, nb, key2, val2, head);
         else
-            warp_sort_bucket<kInter, 8>(wk, s, lane, bkt, lo, nb, w32, key2, val2, wsort, head);
+            warp_sort_bucket<kInter, 8>(wk, s, lane, bkt, lo, nb, key2, val2, head);
         __syncwarp();  // the next bucket overwrites the stage
     }
 }
 
 // Step 3, inter edges in short buckets: the item at p goes to its rank by (key, eid) within
-// its bucket [off_c[a], off_c[a + 1]), with its weight bits when `wsort` is given; head marks
-// the first item (smallest eid) of every coarse edge.  Runs after k_bucket_sort_long, whose
-// list it then empties.
+// its bucket [off_c[a], off_c[a + 1]); head marks the first item (smallest eid) of every
+// coarse edge.  Runs after k_bucket_sort_long, whose list it then empties.
 __global__ void __launch_bounds__(kThreads)
 k_bucket_rank_inter(int64_t cnt, int nb, const int32_t* __restrict__ off_c,
                     const uint4* __restrict__ citem, uint64_t* __restrict__ key2,
-                    uint32_t* __restrict__ val2, uint32_t* __restrict__ wsort,
-                    uint8_t* __restrict__ head, unsigned long long* __restrict__ list_cnt) {
+                    uint32_t* __restrict__ val2, uint8_t* __restrict__ head,
+                    unsigned long long* __restrict__ list_cnt) {
     spc::pdl_wait();
     if (blockIdx.x == 0 && threadIdx.x == 0) *list_cnt = 0ull;  // long buckets are sorted
     for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < cnt;
@@ -458,7 +449,6 @@ k_bucket_rank_inter(int64_t cnt, int nb, const int32_t* __restrict__ off_c,
         }
         key2[lo + r] = ((uint64_t)it.x << nb) | b;
         val2[lo + r] = v;
-        if (wsort) wsort[lo + r] = it.w;
         head[lo + r] = first ? 1 : 0;
     }
 }
@@ -546,10 +536,9 @@ k_run_starts(int64_t cnt, const uint8_t* __restrict__ head, const int32_t* __res
     }
 }
 
-// Segment sums: out[slot(r)] = sum of w_und[idx[j]] (w_und[j] when idx is null: terms already
-// in segment order) for j in [start[r], start[r+1]), left to right.  slot(r) = r, or
-// key[start[r]] when `key` is given (self-mass by super-node).  Short segments: one thread
-// each; segments longer than kLongRow go to a list for k_segsum_long.
+// Segment sums: out[slot(r)] = sum of w_und[idx[j]] for j in [start[r], start[r+1]), left to
+// right.  slot(r) = r, or key[start[r]] when `key` is given (self-mass by super-node).  Short
+// segments: one thread each; segments longer than kLongRow go to a list for k_segsum_long.
 template <class WT, class Out>
 __global__ void __launch_bounds__(kThreads)
 k_segsum_short(int64_t nseg, const int32_t* __restrict__ start, const uint32_t* __restrict__ idx,
@@ -571,7 +560,7 @@ k_segsum_short(int64_t nseg, const int32_t* __restrict__ start, const uint32_t* 
             WT t[4];
 #pragma unroll
             for (int q = 0; q < 4; ++q)
-                if (j0 + q < j1) ix[q] = idx ? idx[j0 + q] : (uint32_t)(j0 + q);
+                if (j0 + q < j1) ix[q] = idx[j0 + q];
 #pragma unroll
             for (int q = 0; q < 4; ++q)
                 if (j0 + q < j1) t[q] = w_und[ix[q]];
@@ -579,7 +568,7 @@ k_segsum_short(int64_t nseg, const int32_t* __restrict__ start, const uint32_t* 
             for (int q = 0; q < 4; ++q)
                 if (j0 + q < j1) s = CT<WT>::add(s, t[q]);
         } else {
-            for (int32_t j = j0; j < j1; ++j) s = CT<WT>::add(s, w_und[idx ? idx[j] : j]);
+            for (int32_t j = j0; j < j1; ++j) s = CT<WT>::add(s, w_und[idx[j]]);
         }
         if constexpr (std::is_same<WT, int32_t>::value && sizeof(Out) == 4) {
             if (s > 2147483647ll) atomicOr(status, DEV_OVERFLOW);
@@ -603,9 +592,7 @@ k_segsum_long(const int32_t* __restrict__ start, const uint32_t* __restrict__ id
         // the per-binade tables (long_segment_sums)
         static_assert(std::is_same<WT, int32_t>::value, "integer weights only");
         const long long s =
-            cta_sum_i64(j1 - j0, [&](int64_t k) {
-                return (long long)w_und[idx ? (int64_t)idx[j0 + k] : j0 + k];
-            });
+            cta_sum_i64(j1 - j0, [&](int64_t k) { return (long long)w_und[idx[j0 + k]]; });
         if (threadIdx.x == 0) {
             if constexpr (sizeof(Out) == 4) {
                 if (s > 2147483647ll) atomicOr(status, DEV_OVERFLOW);
@@ -648,8 +635,7 @@ k_gather_long_terms(const int32_t* __restrict__ long_list, const int32_t* __rest
             if (base[mid] <= f) lo = mid; else hi = mid - 1;
         }
         const int32_t r = long_list[lo];
-        const int64_t j = start[r] + (f - base[lo]);
-        terms[f] = w_und[idx ? (int64_t)idx[j] : j];
+        terms[f] = w_und[idx[start[r] + (f - base[lo])]];
     }
 }
 
@@ -840,8 +826,7 @@ constexpr int64_t kRankWork = 48;
 static spc_status sort_long_buckets(spc_context* ctx, bool inter, const int32_t* list,
                                     const unsigned long long* list_cnt, const int32_t* off,
                                     int nb, const uint4* citem, const uint2* iitem,
-                                    const uint32_t* w32, uint64_t* key2, uint32_t* val2,
-                                    uint32_t* wsort, uint8_t* head) {
+                                    uint64_t* key2, uint32_t* val2, uint8_t* head) {
     constexpr int smem = kBlockBucket * 8;
     static std::atomic<unsigned long long> attr_devs{0};  // devices already set up
     const unsigned long long bit = 1ull << (ctx->device & 63);
@@ -855,10 +840,10 @@ static spc_status sort_long_buckets(spc_context* ctx, bool inter, const int32_t*
     const int grid = ctx->num_sms * 3;
     if (inter) {
         SPC_LAUNCH(ctx, k_bucket_sort_long<true>, grid, kBlockSortThreads, smem, list, list_cnt,
-                   off, nb, citem, iitem, w32, key2, val2, wsort, head);
+                   off, nb, citem, iitem, key2, val2, head);
     } else {
         SPC_LAUNCH(ctx, k_bucket_sort_long<false>, grid, kBlockSortThreads, smem, list, list_cnt,
-                   off, nb, citem, iitem, w32, key2, val2, wsort, head);
+                   off, nb, citem, iitem, key2, val2, head);
     }
     return SPC_OK;
 }
@@ -920,15 +905,11 @@ spc_status contract_typed(spc_context* ctx, const GraphView& g, const int32_t* l
     const int64_t m_inter = bv[0];
     const int64_t m_intra = bv[1];
     const bool buckets = bv[3] <= kBlockBucket && bv[5] <= kBlockBucket;
-    // 4-byte weights travel in the inter items, so the coarse sums read their terms in order
-    const uint32_t* w32 =
-        sizeof(WT) == 4 ? reinterpret_cast<const uint32_t*>(W.w_und.as<WT>()) : nullptr;
-    uint32_t* wsort = (buckets && w32) ? W.w_sort.as<uint32_t>() : nullptr;
     if (buckets) {
         if (m > 0) {
             SPC_LAUNCH(ctx, k_bucket_scatter, gm, kThreads, 0, m, W.eu.as<int32_t>(),
-                       W.ev.as<int32_t>(), lift, off_c, off_i, cnt_c, cnt_i, bstats, w32,
-                       citem, iitem, emap);
+                       W.ev.as<int32_t>(), lift, off_c, off_i, cnt_c, cnt_i, bstats, citem,
+                       iitem, emap);
         }
     } else {
         SPC_CUDA(cudaMemsetAsync(cnt_c, 0, (size_t)(n_c + 1) * 8, ctx->stream));
@@ -966,7 +947,7 @@ spc_status contract_typed(spc_context* ctx, const GraphView& g, const int32_t* l
         if (m_intra > 0) {
             if (long_i > 0)
                 SPC_TRY(sort_long_buckets(ctx, false, list_i, bstats + 7, off_i, nb, nullptr,
-                                          iitem, nullptr, nullptr, ival2, nullptr, nullptr));
+                                          iitem, nullptr, ival2, nullptr));
             SPC_LAUNCH(ctx, k_bucket_rank_intra, grid_for(m_intra, kThreads, maxb), kThreads, 0,
                        m_intra, off_i, iitem, ival2, bstats + 7);
         }
@@ -1010,11 +991,11 @@ spc_status contract_typed(spc_context* ctx, const GraphView& g, const int32_t* l
         if (m_inter > 0) {
             if (long_c > 0)
                 SPC_TRY(sort_long_buckets(ctx, true, list_c, bstats + 6, off_c, nb, citem,
-                                          nullptr, w32, W.c_key2.as<uint64_t>(),
-                                          W.c_val2.as<uint32_t>(), wsort, head));
+                                          nullptr, W.c_key2.as<uint64_t>(),
+                                          W.c_val2.as<uint32_t>(), head));
             SPC_LAUNCH(ctx, k_bucket_rank_inter, grid_for(m_inter, kThreads, maxb), kThreads, 0,
                        m_inter, nb, off_c, citem, W.c_key2.as<uint64_t>(),
-                       W.c_val2.as<uint32_t>(), wsort, head, bstats + 6);
+                       W.c_val2.as<uint32_t>(), head, bstats + 6);
         }
         skey = W.c_key2.as<uint64_t>();
         sval = W.c_val2.as<uint32_t>();
@@ -1057,13 +1038,11 @@ spc_status contract_typed(spc_context* ctx, const GraphView& g, const int32_t* l
     SPC_LAUNCH(ctx, k_set_i32, 1, 32, 0, seg + m_c, (int32_t)m_inter);
     WT* a_und = lv.a_und.as<WT>();
     if (m_c > 0) {
-        // terms in coarse-edge order: the sorted weights when they travelled with the items,
-        // else the fine weights gathered through perm
-        const uint32_t* idx = wsort ? nullptr : reinterpret_cast<const uint32_t*>(perm);
-        const WT* terms = wsort ? reinterpret_cast<const WT*>(wsort) : W.w_und.as<WT>();
         SPC_LAUNCH(ctx, (k_segsum_short<WT, WT>), grid_for(m_c, kThreads, maxb), kThreads, 0,
-                   m_c, seg, idx, nullptr, terms, a_und, long_list, long_cnt, status);
-        SPC_TRY((long_segment_sums<WT, WT>(ctx, seg, idx, nullptr, terms, a_und)));
+                   m_c, seg, reinterpret_cast<const uint32_t*>(perm), nullptr, W.w_und.as<WT>(),
+                   a_und, long_list, long_cnt, status);
+        SPC_TRY((long_segment_sums<WT, WT>(ctx, seg, reinterpret_cast<const uint32_t*>(perm),
+                                            nullptr, W.w_und.as<WT>(), a_und)));
     }
     if (m_c > 0) {
         const int gc = grid_for(m_c, kThreads, maxb);

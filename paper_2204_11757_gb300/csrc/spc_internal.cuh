@@ -104,7 +104,6 @@ struct Work {
     Buf i_key, i_val, i_key2, i_val2, long_segs;                // intra edges (self-mass)
     Buf c_item, i_item;                                         // bucket items (16 / 8 bytes)
     Buf lower_long;                                             // count of long lower rows
-    Buf w_sort;                                                 // 4-byte weights in coarse order
     // contraction buckets: sizes (zero between calls), offsets, ranking statistics
     Buf b_cnt, b_off, b_stats, b_list;
     bool b_dirty = true;
