@@ -98,6 +98,7 @@ struct Work {
     Buf parent, best_k[2], best_e[2], wl_e[2], wl_u[2], wl_v[2], msf;   // S5 MSF
     Buf counters, key_hist;                                     // small device ints
     Buf sel_key, sel_val, sel_key2, sel_val2, node_graph, seg_start, k_graph;  // selection
+    Buf g_need, g_tau, g_lo, g_short;                           // per-graph prefixes (batch)
     Buf parent2, flag, ids;                                     // S6
     Buf c_key, c_val, c_key2, c_val2, c_flag, c_pos, c_head, cU, cV;    // S7
     Buf t_key, t_val, t_key2, t_val2, up_deg, low_deg, deg_c, ufirst, lstart;

@@ -159,6 +159,20 @@ template <> struct MinKey<unsigned int> {
 constexpr int kMkItems = 2;
 constexpr uint32_t kNoSlab = 0xffffffffu;  // no lower bound on the score slab
 
+// Per-graph score slabs of a batch: the first Boruvka pass keeps an edge of graph g when its
+// key lies in (lo[g], tau[g]] (lo[g] all ones: no lower bound).  node_graph null: no slabs.
+template <class KT>
+struct GraphSlab {
+    const int32_t* node_graph;
+    const KT* tau;
+    const KT* lo;
+    __device__ __forceinline__ bool outside(int32_t u, KT k) const {
+        const int32_t g = node_graph[u];
+        const KT l = lo[g];
+        return k > tau[g] || (l != ~KT(0) && k <= l);
+    }
+};
+
 // The start of a further slab: the forest found so far (parent, forest flags) stays; the
 // best-edge slots of both parities and the work-list counts are reset.
 __global__ void k_bv_reinit(int64_t n, unsigned long long* __restrict__ bk0,
@@ -190,8 +204,8 @@ k_bv_minkey(int round0, int resume, int64_t m, const int32_t* __restrict__ in_co
             const int32_t* __restrict__ wi_v, const int32_t* __restrict__ eu,
             const int32_t* __restrict__ ev, const KT* __restrict__ key, int tau_shift,
             const uint32_t* __restrict__ tau_top, const uint32_t* __restrict__ tau_lo,
-            int32_t* parent, unsigned long long* best_k, int32_t* wo_e, int32_t* wo_u,
-            int32_t* wo_v, int32_t* out_count, uint32_t* status) {
+            GraphSlab<KT> gs, int32_t* parent, unsigned long long* best_k, int32_t* wo_e,
+            int32_t* wo_u, int32_t* wo_v, int32_t* out_count, uint32_t* status) {
     spc::pdl_wait();
     __shared__ int32_t sh_wsum[kThreads / 32];
     __shared__ int32_t sh_base;
@@ -221,6 +235,7 @@ k_bv_minkey(int round0, int resume, int64_t m, const int32_t* __restrict__ in_co
             if (round0 && in[it]) {
                 const uint32_t bin = (uint32_t)(k[it] >> tau_shift);
                 if (bin > top || (lo != kNoSlab && bin <= lo)) in[it] = false;
+                if (gs.node_graph && gs.outside(u[it], k[it])) in[it] = false;
             }
         }
         int32_t ru[kMkItems], rv[kMkItems];
@@ -288,9 +303,9 @@ k_bv_finish(int round0, int par0, int64_t m, int32_t* count_in, int32_t* li_e, i
             int32_t* li_v, int32_t* lo_e, int32_t* lo_u, int32_t* lo_v,
             const int32_t* __restrict__ eu, const int32_t* __restrict__ ev,
             const KT* __restrict__ key, int tau_shift, const uint32_t* __restrict__ tau_top,
-            const uint32_t* __restrict__ tau_lo, int32_t* parent, unsigned long long* bk0,
-            unsigned long long* bk1, int32_t* be0, int32_t* be1, uint8_t* msf,
-            uint32_t* status) {
+            const uint32_t* __restrict__ tau_lo, GraphSlab<KT> gs, int32_t* parent,
+            unsigned long long* bk0, unsigned long long* bk1, int32_t* be0, int32_t* be1,
+            uint8_t* msf, uint32_t* status) {
     spc::pdl_wait();
     __shared__ int32_t sh_cnt[2];
     const uint32_t top = tau_top ? *tau_top : 0xffffffffu;
@@ -318,6 +333,7 @@ k_bv_finish(int round0, int par0, int64_t m, int32_t* count_in, int32_t* li_e, i
             if (round0 && r == 0) {
                 const uint32_t bin = (uint32_t)(k >> tau_shift);
                 if (bin > top || (slab_lo != kNoSlab && bin <= slab_lo)) continue;
+                if (gs.node_graph && gs.outside(u, k)) continue;
             }
             const int32_t ru = uf_find(parent, u, status), rv = uf_find(parent, v, status);
             if (ru == rv) continue;
@@ -578,6 +594,141 @@ __global__ void k_graph_keys(const int32_t* __restrict__ count, const uint32_t* 
          i += (int64_t)gridDim.x * blockDim.x)
         gkey[i] = (uint32_t)node_graph[eu[eids[i]]];
 }
+
+// ---- per-graph score prefixes of a batch ------------------------------------------------
+// Graphs of a batch are disjoint, so each one's Kruskal merges are the lightest forest edges
+// of any prefix of its own scores whose forest holds them (the argument of the single-graph
+// prefix, graph by graph).  Each graph's first slab is its lightest 1.5 (n_b - n_c,b) keys;
+// a graph whose forest falls short takes the next slab of twice as many keys.  One CTA per
+// graph finds the threshold with two histogram passes over its keys (2048 bins each: the 11
+// highest value bits, then the next 11 among the keys of the chosen bin), so the slab's top
+// is exact up to its low bits (they are all included).
+constexpr int kGpThreads = 256;
+constexpr int kGpBins = 2048;
+template <class KT> struct GpShift;
+template <> struct GpShift<unsigned int> { static constexpr int s1 = 20, s2 = 9; };
+template <> struct GpShift<unsigned long long> { static constexpr int s1 = 52, s2 = 41; };
+
+// the first bin whose running count over hist reaches `need` (1 <= need <= total); also the
+// count before it.  Every thread of the block calls it.
+__device__ void cta_find_bin(const uint32_t* hist, int64_t need, int* bin_out,
+                             int64_t* before_out) {
+    __shared__ unsigned long long s_part[kGpThreads / 32];
+    __shared__ int s_bin;
+    __shared__ long long s_before;
+    constexpr int kPer = kGpBins / kGpThreads;
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    unsigned long long loc = 0;
+    for (int j = 0; j < kPer; ++j) loc += hist[t * kPer + j];
+    unsigned long long incl = loc;
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) s_part[w] = incl;
+    if (t == 0) s_bin = kGpBins - 1;
+    __syncthreads();
+    unsigned long long base = 0;
+    for (int i = 0; i < w; ++i) base += s_part[i];
+    unsigned long long run = base + incl - loc;  // count before this thread's bins
+    if (run < (unsigned long long)need && run + loc >= (unsigned long long)need) {
+        for (int j = 0; j < kPer; ++j) {
+            const uint32_t c = hist[t * kPer + j];
+            if (run + c >= (unsigned long long)need) {
+                s_bin = t * kPer + j;
+                s_before = (long long)run;
+                break;
+            }
+            run += c;
+        }
+    }
+    __syncthreads();
+    *bin_out = s_bin;
+    *before_out = s_before;
+    __syncthreads();
+}
+
+// the smallest threshold t (its low s2 bits all set) with at least `need` keys of key[e0, e1)
+// at or below it; 1 <= need <= e1 - e0.  Every thread of the block calls it.
+template <class KT>
+__device__ KT cta_select_key(const KT* __restrict__ key, int64_t e0, int64_t e1, int64_t need,
+                             uint32_t* hist) {
+    constexpr int S1 = GpShift<KT>::s1, S2 = GpShift<KT>::s2;
+    for (int i = threadIdx.x; i < kGpBins; i += blockDim.x) hist[i] = 0u;
+    __syncthreads();
+    for (int64_t e = e0 + threadIdx.x; e < e1; e += blockDim.x)
+        atomicAdd(&hist[(uint32_t)(key[e] >> S1) & (kGpBins - 1)], 1u);
+    __syncthreads();
+    int c1;
+    int64_t before;
+    cta_find_bin(hist, need, &c1, &before);
+    for (int i = threadIdx.x; i < kGpBins; i += blockDim.x) hist[i] = 0u;
+    __syncthreads();
+    for (int64_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+        const KT k = key[e];
+        if ((int)(k >> S1) == c1) atomicAdd(&hist[(uint32_t)(k >> S2) & (kGpBins - 1)], 1u);
+    }
+    __syncthreads();
+    int c2;
+    int64_t before2;
+    cta_find_bin(hist, need - before, &c2, &before2);
+    return ((KT)c1 << S1) | ((KT)c2 << S2) | (((KT)1 << S2) - 1);
+}
+
+// attempt 0: every graph's first slab [0, tau]; later attempts: a graph whose forest (the
+// forest flags of its edge range) holds fewer than its n_b - n_c,b merges, and whose slab does
+// not yet reach its last key, takes the next slab (old tau, new tau] of twice the keys (and
+// counts into *n_short); every other graph an empty slab.
+template <class KT>
+__global__ void __launch_bounds__(kGpThreads)
+k_graph_prefix(int64_t B, int attempt, const int64_t* __restrict__ graph_ptr,
+               const int32_t* __restrict__ up_ptr, const int64_t* __restrict__ targets,
+               const KT* __restrict__ key, const uint8_t* __restrict__ msf,
+               int64_t* __restrict__ need, KT* __restrict__ tau, KT* __restrict__ lo,
+               int32_t* n_short) {
+    spc::pdl_wait();
+    __shared__ uint32_t hist[kGpBins];
+    __shared__ int s_short;
+    __shared__ unsigned long long s_sum[kGpThreads / 32];
+    constexpr KT kAll = ~KT(0);
+    for (int64_t b = blockIdx.x; b < B; b += gridDim.x) {
+        const int64_t n0 = graph_ptr[b], n1 = graph_ptr[b + 1];
+        const int64_t e0 = up_ptr[n0], e1 = up_ptr[n1], mb = e1 - e0;
+        const int64_t k_b = (n1 - n0) - targets[b] > 0 ? (n1 - n0) - targets[b] : 0;
+        int64_t nd;
+        if (attempt == 0) {
+            nd = k_b + k_b / 2;
+            if (threadIdx.x == 0) lo[b] = k_b == 0 ? KT(0) : kAll;
+        } else {
+            // the forest edges of this graph so far
+            unsigned long long f = 0;
+            for (int64_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) f += msf[e] ? 1 : 0;
+            for (int o = 16; o > 0; o >>= 1) f += __shfl_xor_sync(0xffffffffu, f, o);
+            if ((threadIdx.x & 31) == 0) s_sum[threadIdx.x >> 5] = f;
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                unsigned long long tot = 0;
+                for (int i = 0; i < kGpThreads / 32; ++i) tot += s_sum[i];
+                s_short = ((int64_t)tot < k_b && need[b] < mb) ? 1 : 0;
+                lo[b] = tau[b];  // done up to the old top: the next slab starts above it
+            }
+            __syncthreads();
+            if (!s_short) continue;  // empty slab (tau, tau]
+            nd = 2 * need[b];
+            if (threadIdx.x == 0) atomicAdd(n_short, 1);
+        }
+        if (k_b == 0) {
+            if (threadIdx.x == 0) { tau[b] = KT(0); need[b] = 0; }  // empty slab (0, 0]
+        } else if (nd >= mb) {
+            if (threadIdx.x == 0) { tau[b] = kAll; need[b] = mb; }   // every key
+        } else {
+            const KT t = cta_select_key<KT>(key, e0, e1, nd, hist);
+            if (threadIdx.x == 0) { tau[b] = t; need[b] = nd; }
+        }
+        __syncthreads();
+    }
+}
+
 
 // per graph: first forest edge position and the number of merges k_b = n_b - target_b
 __global__ void k_graph_segments(int64_t B, const int64_t* __restrict__ graph_ptr,
@@ -971,9 +1122,38 @@ spc_status select_typed(spc_context* ctx, const GraphView& g, const KT* key,
     uint32_t* tau_lo = reinterpret_cast<uint32_t*>(counters + 14);
     int32_t* pos = W.c_pos.as<int32_t>();
     int64_t n_msf = 0;
+    // a batch: every graph its own prefix (k_graph_prefix), which needs the graph of every node
+    int32_t* node_graph = W.node_graph.as<int32_t>();
+    if (batched) {
+        SPC_LAUNCH(ctx, k_node_graph, grid_for(n, kThreads, maxb), kThreads, 0, n, sa.B,
+                   sa.d_graph_ptr, node_graph);
+    }
+    const bool use_gprefix = batched && m > 65536 && sa.d_graph_ptr && sa.d_targets;
+    GraphSlab<KT> gs{nullptr, nullptr, nullptr};
+    int64_t* g_need = nullptr;
+    KT* g_tau = nullptr;
+    KT* g_lo = nullptr;
+    int32_t* g_short = nullptr;
+    const int g_grid = (int)std::min<int64_t>(sa.B, (int64_t)ctx->num_sms * 8);
+    if (use_gprefix) {
+        SPC_TRY(ensure(ctx, W.g_need, (size_t)(sa.B + 1) * 8));
+        SPC_TRY(ensure(ctx, W.g_tau, (size_t)(sa.B + 1) * sizeof(KT)));
+        SPC_TRY(ensure(ctx, W.g_lo, (size_t)(sa.B + 1) * sizeof(KT)));
+        SPC_TRY(ensure(ctx, W.g_short, 16));
+        g_need = W.g_need.as<int64_t>();
+        g_tau = W.g_tau.as<KT>();
+        g_lo = W.g_lo.as<KT>();
+        g_short = W.g_short.as<int32_t>();
+        gs = GraphSlab<KT>{node_graph, g_tau, g_lo};
+    }
     for (int attempt = 0;; ++attempt) {
         const bool two = MinKey<KT>::two_phase;
-        if (use_prefix) {
+        if (use_gprefix) {
+            if (attempt == 0)
+                SPC_LAUNCH(ctx, k_graph_prefix<KT>, g_grid, kGpThreads, 0, sa.B, 0,
+                           sa.d_graph_ptr, W.up_ptr.as<int32_t>(), sa.d_targets, key,
+                           W.msf.as<uint8_t>(), g_need, g_tau, g_lo, g_short);
+        } else if (use_prefix) {
             SPC_TRY(ensure_key_hist(ctx));
             static std::atomic<unsigned long long> attr_devs{0};  // devices already set up
             const unsigned long long bit = 1ull << (ctx->device & 63);
@@ -995,7 +1175,7 @@ spc_status select_typed(spc_context* ctx, const GraphView& g, const KT* key,
         } else if (attempt > 0) {
             SPC_LAUNCH(ctx, k_bump_slab, 1, 32, 0, tau_top, tau_lo);
         }
-        const uint32_t* slab_lo = attempt > 0 ? tau_lo : nullptr;
+        const uint32_t* slab_lo = (attempt > 0 && !use_gprefix) ? tau_lo : nullptr;
         if (attempt == 0) {
             SPC_LAUNCH(ctx, k_bv_init, grid_for(n > m ? n : m + 1, kThreads, maxb), kThreads, 0,
                        n, m, parent, W.best_k[0].as<unsigned long long>(),
@@ -1023,7 +1203,7 @@ spc_status select_typed(spc_context* ctx, const GraphView& g, const KT* key,
                            W.wl_v[in].as<int32_t>(), W.wl_e[out].as<int32_t>(),
                            W.wl_u[out].as<int32_t>(), W.wl_v[out].as<int32_t>(),
                            W.eu.as<int32_t>(), W.ev.as<int32_t>(), key, tau_shift,
-                           use_prefix ? tau_top : nullptr, slab_lo, parent,
+                           use_prefix ? tau_top : nullptr, slab_lo, gs, parent,
                            W.best_k[0].as<unsigned long long>(),
                            W.best_k[1].as<unsigned long long>(),
                            MinKey<KT>::two_phase ? W.best_e[0].as<int32_t>() : nullptr,
@@ -1041,7 +1221,7 @@ spc_status select_typed(spc_context* ctx, const GraphView& g, const KT* key,
                        round == 0 ? 1 : 0, attempt > 0 ? 1 : 0, m, counters + in,
                        W.wl_e[in].as<int32_t>(), W.wl_u[in].as<int32_t>(),
                        W.wl_v[in].as<int32_t>(), W.eu.as<int32_t>(), W.ev.as<int32_t>(), key,
-                       tau_shift, use_prefix ? tau_top : nullptr, slab_lo, parent,
+                       tau_shift, use_prefix ? tau_top : nullptr, slab_lo, gs, parent,
                        W.best_k[par].as<unsigned long long>(), W.wl_e[out].as<int32_t>(),
                        W.wl_u[out].as<int32_t>(), W.wl_v[out].as<int32_t>(), counters + out,
                        status);
@@ -1069,6 +1249,18 @@ spc_status select_typed(spc_context* ctx, const GraphView& g, const KT* key,
         }
         SPC_TRY(scan_flags_u8(ctx, W.msf.as<uint8_t>(), pos, m));
         SPC_TRY(read_i32(ctx, pos + m, &n_msf));
+        if (use_gprefix) {
+            // graphs whose forest falls short take their next slab; done when none does
+            SPC_CUDA(cudaMemsetAsync(g_short, 0, sizeof(int32_t), ctx->stream));
+            SPC_LAUNCH(ctx, k_graph_prefix<KT>, g_grid, kGpThreads, 0, sa.B, attempt + 1,
+                       sa.d_graph_ptr, W.up_ptr.as<int32_t>(), sa.d_targets, key,
+                       W.msf.as<uint8_t>(), g_need, g_tau, g_lo, g_short);
+            int64_t n_short = 0;
+            SPC_TRY(read_i32(ctx, g_short, &n_short));
+            if (n_short == 0) break;
+            if (attempt > 64) return SPC_ERR_TIMEOUT;  // each slab doubles: never reached
+            continue;
+        }
         // the prefix's forest holds Kruskal's first n_msf merges; enough when >= n - n_c
         if (!use_prefix || n_msf >= k_need) break;
         need *= 2;
@@ -1134,9 +1326,6 @@ spc_status select_typed(spc_context* ctx, const GraphView& g, const KT* key,
     SPC_CUDA(cudaMemcpyAsync(cnt_dev, pos + m, sizeof(int32_t), cudaMemcpyDeviceToDevice,
                              ctx->stream));
     if (batched) {
-        int32_t* node_graph = W.node_graph.as<int32_t>();
-        SPC_LAUNCH(ctx, k_node_graph, grid_for(n, kThreads, maxb), kThreads, 0, n, sa.B,
-                   sa.d_graph_ptr, node_graph);
         gkey = W.sel_key2.as<uint32_t>();  // reuse: free after the score sort
         uint32_t* gval = sv;
         SPC_LAUNCH(ctx, k_graph_keys, grid_for(n_msf, kThreads, maxb), kThreads, 0, cnt_dev,

@@ -33,7 +33,7 @@ import numpy as np
 __all__ = [
     "Graph", "Batch", "csr_from_edges", "upper_edges", "tri_mesh_2d", "tet_mesh_3d", "rgg_3d",
     "mesh_batch", "config_graph", "CONFIGS", "path_graph", "cycle_graph", "complete_graph",
-    "random_graph", "subsample_batch", "powerlaw_graph",
+    "random_graph", "subsample_batch", "powerlaw_graph", "batch_of",
 ]
 
 
@@ -292,6 +292,31 @@ def mesh_batch(B: int, seed: int, nmin: int = 200, nmax: int = 20000, dtype=np.f
     graph_ptr = np.zeros(B + 1, dtype=np.int64)
     np.cumsum(np.array(ns, dtype=np.int64), out=graph_ptr[1:])
     return Batch(graph=graph, graph_ptr=graph_ptr, kinds=np.array(kinds, dtype=np.int8))
+
+
+def batch_of(graphs, kinds=None, name: str = "") -> Batch:
+    """Graphs laid out as one block-diagonal CSR (graph g's node x becomes node x + the nodes of
+    the graphs before it); ``kinds`` labels each graph (0 when not given)."""
+    rowptrs, cols, ws, eus, evs, wus, ns = [], [], [], [], [], [], []
+    noff = 0
+    eoff = 0
+    for gr in graphs:
+        rowptrs.append(gr.rowptr[:-1] + eoff)
+        cols.append(gr.col + noff)
+        ws.append(gr.w)
+        eus.append(gr.eu + noff); evs.append(gr.ev + noff); wus.append(gr.w_und)
+        ns.append(gr.n)
+        noff += gr.n
+        eoff += gr.nnz
+    rowptr = np.concatenate(rowptrs + [np.array([eoff], dtype=np.int64)])
+    graph = Graph(n=noff, rowptr=rowptr, col=np.concatenate(cols).astype(np.int32),
+                  w=np.concatenate(ws), eu=np.concatenate(eus).astype(np.int32),
+                  ev=np.concatenate(evs).astype(np.int32), w_und=np.concatenate(wus),
+                  name=name or f"batch{len(ns)}")
+    graph_ptr = np.zeros(len(ns) + 1, dtype=np.int64)
+    np.cumsum(np.array(ns, dtype=np.int64), out=graph_ptr[1:])
+    k = np.zeros(len(ns), dtype=np.int8) if kinds is None else np.asarray(kinds, dtype=np.int8)
+    return Batch(graph=graph, graph_ptr=graph_ptr, kinds=k)
 
 
 def subsample_batch(batch: Batch, idx) -> Batch:

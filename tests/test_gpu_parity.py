@@ -576,6 +576,47 @@ def test_coarsen_batched_matches_per_graph_oracle(ctx):
         assert np.array_equal(_bits(wc[rp[s0]:rp[s1]]), _bits(cg.w))
 
 
+def test_batched_per_graph_prefixes(ctx):
+    """A batch of random geometric graphs (their first level needs about 1.7 times n - n_c of
+    the lightest scores, so their first per-graph slab of 1.5 times falls short and is
+    extended), meshes, a disconnected graph and graphs too small to keep a super-node of eight:
+    every graph's lift and final coarse graph equal the oracle's coarsening of that graph."""
+    api = _api()
+    graphs = [I.rgg_3d(4096, 12.0, 31), I.tri_mesh_2d(40, 30, 5, jitter=0.3, weight="inv_len",
+                                                        dtype=np.float32),
+              I.rgg_3d(20000, 12.0, 32), I.path_graph(5, np.float32),
+              I.random_graph(3000, 0.0012, 17, weight="float", dtype=np.float32,
+                             connected=False),
+              I.rgg_3d(1500, 8.0, 33), I.tet_mesh_3d(12, 6, jitter=0.25, weight="inv_len",
+                                                     dtype=np.float32)]
+    b = I.batch_of(graphs)
+    assert b.graph.m > 65536  # large enough for the per-graph prefixes
+    res = O.coarsen_batch(b, 8, "halving")
+    csr = api.CSR.from_graph(b.graph)
+    gp = torch.from_numpy(b.graph_ptr).cuda()
+    ctx.time_kernel("*")
+    try:
+        lift, gpc, st = ctx.coarsen_batched(csr, gp, 8, levels=3)
+        prof = ctx.kernel_profile()
+    finally:
+        ctx.time_kernel(None)
+    # level 0 (the levels below 65,536 edges take no prefix): the first slabs, the extension
+    # of the graphs that fell short, the final check
+    assert prof.get("k_graph_prefix<KT>", (0,))[0] >= 3, sorted(prof)
+    lift = lift.cpu().numpy(); gpc = gpc.cpu().numpy()
+    last = ctx.level(2, batched_B=b.B)
+    rp = last.rowptr_c.cpu().numpy(); cc = last.col_c.cpu().numpy(); wc = last.w_c.cpu().numpy()
+    for bi, (levels_ref, total_ref) in enumerate(res):
+        n0, n1 = b.graph_ptr[bi], b.graph_ptr[bi + 1]
+        assert gpc[bi + 1] - gpc[bi] == levels_ref[-1].n_c
+        assert np.array_equal(lift[n0:n1] - gpc[bi], total_ref)
+        cg = levels_ref[-1].coarse.graph
+        s0, s1 = gpc[bi], gpc[bi + 1]
+        assert np.array_equal(rp[s0:s1 + 1] - rp[s0], cg.rowptr)
+        assert np.array_equal(cc[rp[s0]:rp[s1]] - s0, cg.col)
+        assert np.array_equal(_bits(wc[rp[s0]:rp[s1]]), _bits(cg.w))
+
+
 # ---- S9 and the autograd Function ---------------------------------------------------------------------
 
 def test_backward_and_autograd(ctx):
