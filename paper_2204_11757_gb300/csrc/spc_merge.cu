@@ -654,19 +654,39 @@ template <class KT>
 __device__ KT cta_select_key(const KT* __restrict__ key, int64_t e0, int64_t e1, int64_t need,
                              uint32_t* hist) {
     constexpr int S1 = GpShift<KT>::s1, S2 = GpShift<KT>::s2;
+    constexpr int kB = 8;  // keys per thread in flight (one CTA may walk a large graph)
+    const int64_t step = (int64_t)blockDim.x * kB;
     for (int i = threadIdx.x; i < kGpBins; i += blockDim.x) hist[i] = 0u;
     __syncthreads();
-    for (int64_t e = e0 + threadIdx.x; e < e1; e += blockDim.x)
-        atomicAdd(&hist[(uint32_t)(key[e] >> S1) & (kGpBins - 1)], 1u);
+    for (int64_t b0 = e0 + threadIdx.x; b0 < e1; b0 += step) {
+        KT k[kB];
+#pragma unroll
+        for (int q = 0; q < kB; ++q) {
+            const int64_t e = b0 + (int64_t)q * blockDim.x;
+            k[q] = e < e1 ? key[e] : KT(0);
+        }
+#pragma unroll
+        for (int q = 0; q < kB; ++q)
+            if (b0 + (int64_t)q * blockDim.x < e1)
+                atomicAdd(&hist[(uint32_t)(k[q] >> S1) & (kGpBins - 1)], 1u);
+    }
     __syncthreads();
     int c1;
     int64_t before;
     cta_find_bin(hist, need, &c1, &before);
     for (int i = threadIdx.x; i < kGpBins; i += blockDim.x) hist[i] = 0u;
     __syncthreads();
-    for (int64_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
-        const KT k = key[e];
-        if ((int)(k >> S1) == c1) atomicAdd(&hist[(uint32_t)(k >> S2) & (kGpBins - 1)], 1u);
+    for (int64_t b0 = e0 + threadIdx.x; b0 < e1; b0 += step) {
+        KT k[kB];
+#pragma unroll
+        for (int q = 0; q < kB; ++q) {
+            const int64_t e = b0 + (int64_t)q * blockDim.x;
+            k[q] = e < e1 ? key[e] : KT(0);
+        }
+#pragma unroll
+        for (int q = 0; q < kB; ++q)
+            if (b0 + (int64_t)q * blockDim.x < e1 && (int)(k[q] >> S1) == c1)
+                atomicAdd(&hist[(uint32_t)(k[q] >> S2) & (kGpBins - 1)], 1u);
     }
     __syncthreads();
     int c2;
@@ -702,7 +722,16 @@ k_graph_prefix(int64_t B, int attempt, const int64_t* __restrict__ graph_ptr,
         } else {
             // the forest edges of this graph so far
             unsigned long long f = 0;
-            for (int64_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) f += msf[e] ? 1 : 0;
+            for (int64_t b0 = e0 + threadIdx.x; b0 < e1; b0 += (int64_t)blockDim.x * 8) {
+                uint8_t fl[8];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    const int64_t e = b0 + (int64_t)q * blockDim.x;
+                    fl[q] = e < e1 ? msf[e] : 0;
+                }
+#pragma unroll
+                for (int q = 0; q < 8; ++q) f += fl[q] ? 1 : 0;
+            }
             for (int o = 16; o > 0; o >>= 1) f += __shfl_xor_sync(0xffffffffu, f, o);
             if ((threadIdx.x & 31) == 0) s_sum[threadIdx.x >> 5] = f;
             __syncthreads();

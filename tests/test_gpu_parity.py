@@ -576,19 +576,20 @@ def test_coarsen_batched_matches_per_graph_oracle(ctx):
         assert np.array_equal(_bits(wc[rp[s0]:rp[s1]]), _bits(cg.w))
 
 
-def test_batched_per_graph_prefixes(ctx):
+@pytest.mark.parametrize("dt", [np.float32, np.float64])
+def test_batched_per_graph_prefixes(ctx, dt):
     """A batch of random geometric graphs (their first level needs about 1.7 times n - n_c of
     the lightest scores, so their first per-graph slab of 1.5 times falls short and is
     extended), meshes, a disconnected graph and graphs too small to keep a super-node of eight:
-    every graph's lift and final coarse graph equal the oracle's coarsening of that graph."""
+    every graph's lift and final coarse graph equal the oracle's coarsening of that graph
+    (binary32 and binary64 weights: 32- and 64-bit score keys)."""
     api = _api()
-    graphs = [I.rgg_3d(4096, 12.0, 31), I.tri_mesh_2d(40, 30, 5, jitter=0.3, weight="inv_len",
-                                                        dtype=np.float32),
-              I.rgg_3d(20000, 12.0, 32), I.path_graph(5, np.float32),
-              I.random_graph(3000, 0.0012, 17, weight="float", dtype=np.float32,
-                             connected=False),
-              I.rgg_3d(1500, 8.0, 33), I.tet_mesh_3d(12, 6, jitter=0.25, weight="inv_len",
-                                                     dtype=np.float32)]
+    graphs = [I.rgg_3d(4096, 12.0, 31, dtype=dt),
+              I.tri_mesh_2d(40, 30, 5, jitter=0.3, weight="inv_len", dtype=dt),
+              I.rgg_3d(20000, 12.0, 32, dtype=dt), I.path_graph(5, dt),
+              I.random_graph(3000, 0.0012, 17, weight="float", dtype=dt, connected=False),
+              I.rgg_3d(1500, 8.0, 33, dtype=dt),
+              I.tet_mesh_3d(12, 6, jitter=0.25, weight="inv_len", dtype=dt)]
     b = I.batch_of(graphs)
     assert b.graph.m > 65536  # large enough for the per-graph prefixes
     res = O.coarsen_batch(b, 8, "halving")
