@@ -615,6 +615,15 @@ def bench_batched(steps, warmup, want_profile=False, cpu=False):
     grad_h = torch.empty(batch.graph.m, dtype=torch.float32).pin_memory()
     w_h = torch.from_numpy(batch.graph.w_und).pin_memory()
 
+    ranges = S.shard_ranges(S.batch_edge_counts(full), ws) if ws > 1 else None
+
+    def gather_counts(parts, t):
+        # NCCL gathers device tensors; global_offsets hands host ones
+        dparts = [torch.empty_like(t, device=dev) for _ in parts]
+        dist.all_gather(dparts, t.to(dev))
+        for p, d in zip(parts, dparts):
+            p.copy_(d.cpu())
+
     def e2e_step():
         _, gpc, _ = ctx.coarsen_batched(host, gptr_h, cfg["ratio"], L)
         plan = api.ContractionPlan.from_levels(ctx, ctx.levels())
@@ -623,6 +632,11 @@ def bench_batched(steps, warmup, want_profile=False, cpu=False):
         a = api.contract_weights(w, plan)
         (a * torch.ones_like(a)).sum().backward()
         grad_h.copy_(w.grad, non_blocking=True)
+        if ranges is not None:
+            # the one collective of a sharded batch: every rank's per-graph super-node
+            # counts, for the global offsets of the coarse graphs
+            counts = torch.diff(gpc.cpu()).numpy()
+            return S.global_offsets(counts, ranges, ws, all_gather=gather_counts)
         return gpc
 
     e2e_step()
