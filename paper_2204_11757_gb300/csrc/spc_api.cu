@@ -359,9 +359,9 @@ static spc_status reserve_work(spc_context* ctx, int64_t n, int64_t m, int64_t B
     // stored entries of a level's input: 2m, plus one diagonal entry per node under the
     // self-mass reading
     SPC_TRY(ensure(ctx, W.p, (2 * M + N) * 8));
-    // binary32 levels also keep every stored entry as one 8-byte (column, p) pair, with room
-    // for the 16-byte copies that start or end on the neighbouring entry
-    SPC_TRY(ensure(ctx, W.pk, (2 * M + N + 2) * 8));
+    // binary32 levels also keep every stored entry as one 8-byte (column, p) pair plus one end
+    // marker per row, with room for the 16-byte copies that start or end on a neighbour
+    SPC_TRY(ensure(ctx, W.pk, (2 * M + 2 * N + 4) * 8));
     SPC_TRY(ensure(ctx, W.sym, 16));
     SPC_TRY(ensure(ctx, W.long_rows, N * 4));
     SPC_TRY(ensure(ctx, W.lr_base, N * 8));

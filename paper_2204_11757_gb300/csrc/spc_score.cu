@@ -390,7 +390,9 @@ k_rows_edges_flat(int64_t n, int64_t nnz, const int64_t* __restrict__ rowptr,
             if (rel < 0) continue;  // long row: k_long_rows_edges
             const float pj = __fdiv_rn(wj, deg[x]);
             if (p) p[j] = pj;
-            pk[j] = make_uint2((uint32_t)y, __float_as_uint(pj));
+            // row x's pairs at pk[rowptr[x] + x ..], then its end marker
+            pk[j + x] = make_uint2((uint32_t)y, __float_as_uint(pj));
+            if (j + 1 == rowptr[x + 1]) pk[j + x + 1] = make_uint2(0x7fffffffu, 0u);
             if ((int64_t)y > x) {
                 const int64_t e = (int64_t)up_ptr[x] + (j - (rowptr[x] + nlow[x]));
                 eu[e] = (int32_t)x;
@@ -854,56 +856,60 @@ k_score_packed(int64_t m, const int32_t* __restrict__ eu, const int32_t* __restr
     uint2* const sa = pk_stage + (size_t)wib * kPkRegion;
     uint2* const sb = sa + kPkA;
     const uint4* const pk16 = reinterpret_cast<const uint4*>(pk);
-    constexpr int32_t kEnd = 0x7fffffff;
-    const uint2 kEndPair = make_uint2((uint32_t)kEnd, 0u);
+    constexpr int32_t kEnd = 0x7fffffff;  // the end marker's column
     const uint64_t keep = l2_policy_evict_last();
     const int64_t step_e = (int64_t)gridDim.x * kPkWarps * 32;
     for (int64_t e0 = ((int64_t)blockIdx.x * kPkWarps + wib) * 32; e0 < m; e0 += step_e) {
         const int64_t e = e0 + lane;
         const bool act = e < m;
-        int32_t a = 0;
+        int32_t a = 0, b = 0;
         int64_t ra = 0, da = 0, rb = 0, db = 0;
         if (act) {
             a = eu[e];
-            const int32_t b = ev[e];
+            b = ev[e];
             ra = ld_l2hint(rowptr + a, keep);
             da = ld_l2hint(rowptr + a + 1, keep) - ra;
             rb = ld_l2hint(rowptr + b, keep);
             db = ld_l2hint(rowptr + b + 1, keep) - rb;
         }
         const bool hub = act && (da > kLongRow || db > kLongRow);
-        // the rows a of the tile: entries [rowptr[a of lane 0], rowptr[a of the last lane + 1]),
-        // as 16-byte chunks [ac0, ac1)
+        // packed positions: row x's pairs start at rowptr[x] + x, its end marker follows them
+        const int64_t pa0 = ra + a, pb0 = rb + b;
+        // the rows a of the tile, end markers included: pairs [pa0 of lane 0, pa0 + da + 1
+        // of the last lane), as 16-byte chunks [ac0, ac1)
         const int lastl = (int)((m - e0 < 32 ? m - e0 : 32) - 1);
-        const int64_t ac0 = __shfl_sync(0xffffffffu, ra, 0) >> 1;
-        const int64_t ac1 = (__shfl_sync(0xffffffffu, ra + da, lastl) + 1) >> 1;
+        const int64_t ac0 = __shfl_sync(0xffffffffu, pa0, 0) >> 1;
+        const int64_t ac1 = (__shfl_sync(0xffffffffu, pa0 + da + 1, lastl) + 1) >> 1;
         const bool a_staged = 2 * (ac1 - ac0) <= kPkA;
         if (a_staged)
             for (int64_t q = ac0 + lane; q < ac1; q += 32)
                 cp_async_16(sa + 2 * (q - ac0), pk16 + q);
-        // this lane's row b: chunks [rb / 2, (rb + db + 1) / 2), placed after the other lanes'
-        const int64_t bc0 = rb >> 1;
-        const int nch = (act && !hub && db > 0) ? (int)(((rb + db + 1) >> 1) - bc0) : 0;
-        int choff = nch;
+        // this lane's row b: its pairs, chunks [pb0 / 2, (pb0 + db + 1) / 2), placed after the
+        // other lanes'; its end marker is written in shared memory (a random row fetches no
+        // more than its pairs), in one more chunk of room when the pairs fill their last one
+        const int64_t bc0 = pb0 >> 1;
+        const int nch = (act && !hub) ? (int)(((pb0 + db + 1) >> 1) - bc0) : 0;
+        const int nroom = nch + ((act && !hub && (pb0 & 1) + db == 2 * nch) ? 1 : 0);
+        int choff = nroom;
 #pragma unroll
         for (int d = 1; d < 32; d <<= 1) {
             const int t = __shfl_up_sync(0xffffffffu, choff, d);
             if (lane >= d) choff += t;
         }
-        choff -= nch;
-        const bool b_staged = 2 * (choff + nch) <= kPkB;
+        choff -= nroom;
+        const bool b_staged = 2 * (choff + nroom) <= kPkB;
         const int maxch = __reduce_max_sync(0xffffffffu, b_staged ? nch : 0);
         for (int k = 0; k < maxch; ++k)
             if (b_staged && k < nch) cp_async_16(sb + 2 * (choff + k), pk16 + bc0 + k);
         cp_async_wait_all();
+        if (b_staged && act && !hub)
+            sb[2 * choff + (pb0 & 1) + db] = make_uint2((uint32_t)kEnd, 0u);
         __syncwarp();
         if (act && !hub) {
-            const uint2* A = a_staged ? sa + (ra - 2 * ac0) : pk + ra;
-            const uint2* B = b_staged ? sb + 2 * choff + (rb & 1) : pk + rb;
-            const int na = (int)da, nb = (int)db;
-            int i = 0, j = 0;
-            uint2 xa = na > 0 ? A[0] : kEndPair;
-            uint2 xb = nb > 0 ? B[0] : kEndPair;
+            // both rows end in their marker: the walk advances without bounds
+            const uint2* A = a_staged ? sa + (pa0 - 2 * ac0) : pk + pa0;
+            const uint2* B = b_staged ? sb + 2 * choff + (pb0 & 1) : pk + pb0;
+            uint2 xa = A[0], xb = B[0];
             float s = 0.f;
             for (;;) {
                 const int32_t ca = (int32_t)xa.x, cb = (int32_t)xb.x;
@@ -912,8 +918,8 @@ k_score_packed(int64_t m, const int32_t* __restrict__ eu, const int32_t* __restr
                 const float pa = ta ? __uint_as_float(xa.y) : 0.f;
                 const float pb = tb ? __uint_as_float(xb.y) : 0.f;
                 s = p_add(s, p_absdiff(pa, pb));
-                if (ta) { ++i; xa = i < na ? A[i] : kEndPair; }
-                if (tb) { ++j; xb = j < nb ? B[j] : kEndPair; }
+                if (ta) xa = *++A;
+                if (tb) xb = *++B;
             }
             score[e] = key_bits(s);
         }
