@@ -291,12 +291,12 @@ FP64_PEAK_SOURCE = "measured FP64 add throughput (profiles/fp64_add_probe_gb300.
 # launch are in profiles/traffic_dominant_kernels.md); absent where no capture of the current
 # kernel exists (then `traffic` is null).
 TRAFFIC = {
-    ("c4_rgg8m_f32", "k_score_packed<Key>"): 2.170865e+09,
-    ("c4_rgg8m_f32_one", "k_score_packed<Key>"): 1.374394e+10,
-    ("c4_rgg8m_f32_reordered", "k_score_packed<Key>"): 3.832510e+08,
+    ("c4_rgg8m_f32", "k_score_packed<Key>"): 2.236592e+09,
+    ("c4_rgg8m_f32_one", "k_score_packed<Key>"): 1.393540e+10,
+    ("c4_rgg8m_f32_reordered", "k_score_packed<Key>"): 4.090090e+08,
     ("c2_tri2048_f64", "(k_score_edges<P, Key, kScoreChains>)"): 2.226063e8,
     ("c3_tet129_f64", "(k_score_edges<P, Key, kScoreChains>)"): 3.163520e8,
-    ("c5_batch10k_f32", "k_score_packed<Key>"): 3.605553e+09,
+    ("c5_batch10k_f32", "k_score_packed<Key>"): 3.834753e+09,
 }
 
 HEADLINE = "c4_rgg8m_f32"
