@@ -12,8 +12,9 @@
 //      node id of their set; edges inside one component drop out of the work list.  Only a
 //      prefix of the score order takes part: Kruskal's first n - n_c merges all lie among the
 //      lightest edges, so the rounds run on the edges up to a threshold chosen from a score
-//      histogram to hold about 1.5 (n - n_c) edges; if that prefix's forest has fewer than
-//      n - n_c edges, the rounds are run again on every edge.
+//      histogram to hold about 1.5 (n - n_c) edges (on very large graphs the slab's edges are
+//      first compacted into the work list); if that prefix's forest has fewer than n - n_c
+//      edges, the rounds resume on the next slab, the forest found so far kept.
 //   2. The forest edges are compacted in eid order.  For one graph an exact radix select on
 //      11-bit digits of (score, eid) finds the (n - n_c)-th lightest and every forest edge up to
 //      it is united in a second union-find; for batches the forest edges are radix-sorted by
@@ -197,9 +198,79 @@ __global__ void k_bump_slab(const uint32_t* __restrict__ tau_top, uint32_t* __re
     if (blockIdx.x == 0 && threadIdx.x == 0) *tau_lo = *tau_top;
 }
 
+// The edges of the current score slab as the first Boruvka work list: every edge whose key
+// lies in the slab is written as (e, eu[e], ev[e]).
+// A streaming pass: kSlItems keys a thread in flight, the ends read only for the slab's edges,
+// one global atomic per kThreads * kSlItems edges.  The list's order is the threads' order,
+// which the forest does not depend on (every component's lightest edge is unique).
+constexpr int kSlItems = 16;
+constexpr int64_t kSlabListMin = int64_t{1} << 25;
+
 template <class KT>
 __global__ void __launch_bounds__(kThreads)
-k_bv_minkey(int round0, int resume, int64_t m, const int32_t* __restrict__ in_count,
+k_slab_list(int64_t m, const int32_t* __restrict__ eu, const int32_t* __restrict__ ev,
+            const KT* __restrict__ key, int tau_shift, const uint32_t* __restrict__ tau_top,
+            const uint32_t* __restrict__ tau_lo, int32_t* __restrict__ wo_e,
+            int32_t* __restrict__ wo_u, int32_t* __restrict__ wo_v,
+            int32_t* __restrict__ out_count) {
+    spc::pdl_wait();
+    __shared__ int32_t sh_wsum[kThreads / 32];
+    __shared__ int32_t sh_base;
+    const uint32_t top = tau_top ? *tau_top : 0xffffffffu;
+    const uint32_t lo = tau_lo ? *tau_lo : kNoSlab;
+    const int64_t per = (int64_t)kThreads * kSlItems;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int64_t base = (int64_t)blockIdx.x * per; base < m; base += (int64_t)gridDim.x * per) {
+        KT k[kSlItems];
+#pragma unroll
+        for (int it = 0; it < kSlItems; ++it) {
+            const int64_t i = base + (int64_t)it * kThreads + threadIdx.x;
+            k[it] = i < m ? key[i] : KT(0);
+        }
+        unsigned keep = 0;  // bit it: item it lies in the slab
+#pragma unroll
+        for (int it = 0; it < kSlItems; ++it) {
+            const int64_t i = base + (int64_t)it * kThreads + threadIdx.x;
+            const uint32_t bin = (uint32_t)(k[it] >> tau_shift);
+            const bool in = i < m && bin <= top && (lo == kNoSlab || bin > lo);
+            keep |= in ? 1u << it : 0u;
+        }
+        const int32_t nkeep = __popc(keep);
+        int32_t incl = nkeep;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += t;
+        }
+        if (lane == 31) sh_wsum[warp] = incl;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int32_t tot = 0;
+            for (int w = 0; w < kThreads / 32; ++w) {
+                const int32_t t = sh_wsum[w];
+                sh_wsum[w] = tot;
+                tot += t;
+            }
+            sh_base = tot ? atomicAdd(out_count, tot) : 0;
+        }
+        __syncthreads();
+        int32_t slot = sh_base + sh_wsum[warp] + incl - nkeep;
+        while (keep) {
+            const int it = __ffs(keep) - 1;
+            keep &= keep - 1;
+            const int64_t i = base + (int64_t)it * kThreads + threadIdx.x;
+            wo_e[slot] = (int32_t)i;
+            wo_u[slot] = eu[i];
+            wo_v[slot] = ev[i];
+            ++slot;
+        }
+        __syncthreads();
+    }
+}
+
+template <class KT>
+__global__ void __launch_bounds__(kThreads)
+k_bv_minkey(int round0, int direct, int64_t m, const int32_t* __restrict__ in_count,
             const int32_t* __restrict__ wi_e, const int32_t* __restrict__ wi_u,
             const int32_t* __restrict__ wi_v, const int32_t* __restrict__ eu,
             const int32_t* __restrict__ ev, const KT* __restrict__ key, int tau_shift,
@@ -211,7 +282,7 @@ k_bv_minkey(int round0, int resume, int64_t m, const int32_t* __restrict__ in_co
     __shared__ int32_t sh_base;
     const int64_t cnt = round0 ? m : (int64_t)*in_count;
     const uint32_t top = tau_top ? *tau_top : 0xffffffffu;
-    // a resumed first round (the next slab of scores) skips the slabs already done
+    // a first round over the next slab of scores skips the slabs already done
     const uint32_t lo = tau_lo ? *tau_lo : kNoSlab;
     const int64_t per = (int64_t)blockDim.x * kMkItems;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -242,7 +313,7 @@ k_bv_minkey(int round0, int resume, int64_t m, const int32_t* __restrict__ in_co
         int32_t nkeep = 0;
 #pragma unroll
         for (int it = 0; it < kMkItems; ++it) {
-            const bool direct = round0 && !resume;  // every node its own component
+            // direct: the selection's first round, every node still its own component
             ru[it] = in[it] ? (direct ? u[it] : uf_find(parent, u[it], status)) : 0;
             rv[it] = in[it] ? (direct ? v[it] : uf_find(parent, v[it], status)) : 0;
             in[it] = in[it] && ru[it] != rv[it];
@@ -384,16 +455,23 @@ k_bv_finish(int round0, int par0, int64_t m, int32_t* count_in, int32_t* li_e, i
     }
 }
 
-// histogram of the top 15 bits of the scores (bits below the sign), per block in shared memory
+// histogram of the top 15 bits of the scores (bits below the sign), per block in shared memory,
+// over a sample of the keys: one chunk of kHistChunk consecutive keys in every 2^samp (samp 0:
+// every key).  The threshold it gives only sizes the score prefix, never changes a result.
+constexpr int kHistChunk = 256;
+
 template <class KT>
 __global__ void __launch_bounds__(1024)
-k_key_hist(int64_t m, const KT* __restrict__ key, int shift, uint32_t* __restrict__ hist) {
+k_key_hist(int64_t m, const KT* __restrict__ key, int shift, int samp,
+           uint32_t* __restrict__ hist) {
     spc::pdl_wait();
     extern __shared__ uint32_t sh_hist[];
     for (int b = threadIdx.x; b < 32768; b += blockDim.x) sh_hist[b] = 0;
     __syncthreads();
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m;
-         i += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;;
+         v += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = ((v / kHistChunk) << samp) * kHistChunk + v % kHistChunk;
+        if (i >= m) break;  // i grows with v
         const uint32_t b = (uint32_t)(key[i] >> shift) & 32767u;
         const unsigned peers = __match_any_sync(__activemask(), b);
         if ((int)(threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&sh_hist[b], __popc(peers));
@@ -1148,6 +1226,8 @@ spc_status select_typed(spc_context* ctx, const GraphView& g, const KT* key,
     // starting over.
     int64_t need = k_need + k_need / 2;
     bool use_prefix = !batched && m > 65536 && k_need > 0 && need < m;
+    // the threshold's histogram samples one key chunk in eight on large selections
+    const int hist_samp = m >= (int64_t{1} << 22) ? 3 : 0;
     uint32_t* tau_lo = reinterpret_cast<uint32_t*>(counters + 14);
     int32_t* pos = W.c_pos.as<int32_t>();
     int64_t n_msf = 0;
@@ -1193,18 +1273,25 @@ spc_status select_typed(spc_context* ctx, const GraphView& g, const KT* key,
                 attr_devs.fetch_or(bit);
             }
             if (attempt > 0) {
-                // the histogram of every key is still there: only the threshold moves up
+                // the histogram is still there: only the threshold moves up
                 SPC_LAUNCH(ctx, k_bump_slab, 1, 32, 0, tau_top, tau_lo);
             } else {
                 SPC_CUDA(cudaMemsetAsync(W.key_hist.p, 0, (size_t)kTauBins * 4, ctx->stream));
+                note_bytes(ctx, (double)m * sizeof(KT) / (double)(1 << hist_samp));
                 SPC_LAUNCH(ctx, k_key_hist<KT>, ctx->num_sms, 1024, 32768 * 4, m, key,
-                           tau_shift, W.key_hist.as<uint32_t>());
+                           tau_shift, hist_samp, W.key_hist.as<uint32_t>());
             }
-            SPC_LAUNCH(ctx, k_pick_tau, 1, 1024, 0, W.key_hist.as<uint32_t>(), need, tau_top);
+            // the histogram counts one key in 2^hist_samp
+            const int64_t need_s = (need + (int64_t{1} << hist_samp) - 1) >> hist_samp;
+            SPC_LAUNCH(ctx, k_pick_tau, 1, 1024, 0, W.key_hist.as<uint32_t>(), need_s, tau_top);
         } else if (attempt > 0) {
             SPC_LAUNCH(ctx, k_bump_slab, 1, 32, 0, tau_top, tau_lo);
         }
         const uint32_t* slab_lo = (attempt > 0 && !use_gprefix) ? tau_lo : nullptr;
+        // the slab of a very large single-graph selection: its edges become the first work
+        // list, so the first round does not sweep every edge.  Below kSlabListMin edges, and
+        // for a batch's per-graph slabs, the extra pass costs more than the sweep it replaces.
+        const bool slab_list = !batched && m >= kSlabListMin && (use_prefix || slab_lo);
         if (attempt == 0) {
             SPC_LAUNCH(ctx, k_bv_init, grid_for(n > m ? n : m + 1, kThreads, maxb), kThreads, 0,
                        n, m, parent, W.best_k[0].as<unsigned long long>(),
@@ -1219,15 +1306,27 @@ spc_status select_typed(spc_context* ctx, const GraphView& g, const KT* key,
                        two ? W.best_e[0].as<int32_t>() : nullptr,
                        two ? W.best_e[1].as<int32_t>() : nullptr, counters);
         }
+        if (slab_list) {
+            note_bytes(ctx, (double)m * sizeof(KT) + (double)std::min<int64_t>(need, m) * 20);
+            SPC_LAUNCH(ctx, k_slab_list<KT>, grid_for(m, kThreads * kSlItems, maxb), kThreads,
+                       0, m, W.eu.as<int32_t>(), W.ev.as<int32_t>(), key, tau_shift,
+                       use_prefix ? tau_top : nullptr, slab_lo, W.wl_e[0].as<int32_t>(),
+                       W.wl_u[0].as<int32_t>(), W.wl_v[0].as<int32_t>(), counters);
+        }
         // ---- 1. Boruvka minimum spanning forest (of the prefix) ---------------------------
+        // the first round reads the edges themselves (filtered by the slab) unless the slab
+        // list holds them; its count is then known on the device only
+        const bool scan0 = !slab_list;
         int64_t cur = m;
         for (int round = 0; cur > 0; ++round) {
             const int in = round & 1, out = in ^ 1;
             const int par = round & 1;
-            if (cur <= kFinishMax) {  // the remaining rounds in one CTA
-                note_bytes(ctx, round == 0 ? (double)m * (8 + sizeof(KT))
-                                           : (double)cur * (12 + sizeof(KT) + 8 + 32 + 12));
-                SPC_LAUNCH(ctx, k_bv_finish<KT>, 1, kFinishThreads, 0, round == 0 ? 1 : 0, par,
+            const int first = (round == 0 && scan0) ? 1 : 0;
+            const int direct = (round == 0 && attempt == 0) ? 1 : 0;
+            if (cur <= kFinishMax && (round > 0 || scan0)) {  // the remaining rounds in one CTA
+                note_bytes(ctx, first ? (double)m * (8 + sizeof(KT))
+                                      : (double)cur * (12 + sizeof(KT) + 8 + 32 + 12));
+                SPC_LAUNCH(ctx, k_bv_finish<KT>, 1, kFinishThreads, 0, first, par,
                            m, counters + in, W.wl_e[in].as<int32_t>(), W.wl_u[in].as<int32_t>(),
                            W.wl_v[in].as<int32_t>(), W.wl_e[out].as<int32_t>(),
                            W.wl_u[out].as<int32_t>(), W.wl_v[out].as<int32_t>(),
@@ -1243,11 +1342,13 @@ spc_status select_typed(spc_context* ctx, const GraphView& g, const KT* key,
             // algorithmic bytes: the first round reads every edge's ends and key; a later one
             // reads each work-list item (e, u, v) and key, walks two parents, lowers two best
             // slots (read and write) and writes the item back
-            note_bytes(ctx, round == 0 ? (double)m * (8 + sizeof(KT))
-                                       : (double)cur * (12 + sizeof(KT) + 8 + 32 + 12));
+            // (a first round over the slab list: about `need` items)
+            const double items = round > 0 ? (double)cur : (double)std::min<int64_t>(need, m);
+            note_bytes(ctx, first ? (double)m * (8 + sizeof(KT))
+                                  : items * (12 + sizeof(KT) + 8 + 32 + 12));
             SPC_LAUNCH(ctx, k_bv_minkey<KT>,
                        grid_for(cur, kThreads * kMkItems, maxb), kThreads, 0,
-                       round == 0 ? 1 : 0, attempt > 0 ? 1 : 0, m, counters + in,
+                       first, direct, m, counters + in,
                        W.wl_e[in].as<int32_t>(), W.wl_u[in].as<int32_t>(),
                        W.wl_v[in].as<int32_t>(), W.eu.as<int32_t>(), W.ev.as<int32_t>(), key,
                        tau_shift, use_prefix ? tau_top : nullptr, slab_lo, gs, parent,
@@ -1292,7 +1393,14 @@ spc_status select_typed(spc_context* ctx, const GraphView& g, const KT* key,
         }
         // the prefix's forest holds Kruskal's first n_msf merges; enough when >= n - n_c
         if (!use_prefix || n_msf >= k_need) break;
-        need *= 2;
+        // the next slab: twice the edges, or, when the forest came within 15 % of n - n_c,
+        // the prefix its yield so far extrapolates to, and a quarter more
+        int64_t next = need * 2;
+        if (n_msf * 20 >= k_need * 17) {
+            const int64_t est = (int64_t)((double)need * (double)k_need / (double)n_msf * 1.25);
+            next = std::min(next, std::max(est, need + need / 8));
+        }
+        need = next;
         if (need >= m) use_prefix = false;  // the last slab: every remaining score
     }
     // ---- 2. lightest forest edges per graph ---------------------------------------------
