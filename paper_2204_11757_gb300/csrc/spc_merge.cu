@@ -199,10 +199,12 @@ __global__ void k_bump_slab(const uint32_t* __restrict__ tau_top, uint32_t* __re
 }
 
 // The edges of the current score slab as the first Boruvka work list: every edge whose key
-// lies in the slab is written as (e, eu[e], ev[e]).
-// A streaming pass: kSlItems keys a thread in flight, the ends read only for the slab's edges,
-// one global atomic per kThreads * kSlItems edges.  The list's order is the threads' order,
-// which the forest does not depend on (every component's lightest edge is unique).
+// lies in the slab is written as (e, eu[e], ev[e]).  A streaming pass: each thread takes
+// kSlItems consecutive edges (their keys in 16-byte loads; key 16-byte aligned), the ends are
+// read only for the slab's edges, and one global atomic per kThreads * kSlItems edges places
+// a block's survivors, so the list is in edge order within each block's chunk (the next
+// rounds' parent and flag accesses stay close together); the forest does not depend on the
+// order (every component's lightest edge is unique).
 constexpr int kSlItems = 16;
 constexpr int64_t kSlabListMin = int64_t{1} << 25;
 
@@ -213,6 +215,8 @@ k_slab_list(int64_t m, const int32_t* __restrict__ eu, const int32_t* __restrict
             const uint32_t* __restrict__ tau_lo, int32_t* __restrict__ wo_e,
             int32_t* __restrict__ wo_u, int32_t* __restrict__ wo_v,
             int32_t* __restrict__ out_count) {
+    static_assert(kSlItems * sizeof(KT) % 16 == 0, "whole 16-byte loads");
+    constexpr int kVec = (int)(kSlItems * sizeof(KT) / 16);
     spc::pdl_wait();
     __shared__ int32_t sh_wsum[kThreads / 32];
     __shared__ int32_t sh_base;
@@ -221,18 +225,23 @@ k_slab_list(int64_t m, const int32_t* __restrict__ eu, const int32_t* __restrict
     const int64_t per = (int64_t)kThreads * kSlItems;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int64_t base = (int64_t)blockIdx.x * per; base < m; base += (int64_t)gridDim.x * per) {
+        const int64_t i0 = base + (int64_t)threadIdx.x * kSlItems;
         KT k[kSlItems];
+        if (i0 + kSlItems <= m) {
+            const uint4* p = reinterpret_cast<const uint4*>(key + i0);
+            uint4 q[kVec];
 #pragma unroll
-        for (int it = 0; it < kSlItems; ++it) {
-            const int64_t i = base + (int64_t)it * kThreads + threadIdx.x;
-            k[it] = i < m ? key[i] : KT(0);
+            for (int j = 0; j < kVec; ++j) q[j] = p[j];
+            memcpy(k, q, sizeof(k));
+        } else {
+#pragma unroll
+            for (int it = 0; it < kSlItems; ++it) k[it] = i0 + it < m ? key[i0 + it] : KT(0);
         }
-        unsigned keep = 0;  // bit it: item it lies in the slab
+        unsigned keep = 0;  // bit it: edge i0 + it lies in the slab
 #pragma unroll
         for (int it = 0; it < kSlItems; ++it) {
-            const int64_t i = base + (int64_t)it * kThreads + threadIdx.x;
             const uint32_t bin = (uint32_t)(k[it] >> tau_shift);
-            const bool in = i < m && bin <= top && (lo == kNoSlab || bin > lo);
+            const bool in = i0 + it < m && bin <= top && (lo == kNoSlab || bin > lo);
             keep |= in ? 1u << it : 0u;
         }
         const int32_t nkeep = __popc(keep);
@@ -258,7 +267,7 @@ k_slab_list(int64_t m, const int32_t* __restrict__ eu, const int32_t* __restrict
         while (keep) {
             const int it = __ffs(keep) - 1;
             keep &= keep - 1;
-            const int64_t i = base + (int64_t)it * kThreads + threadIdx.x;
+            const int64_t i = i0 + it;
             wo_e[slot] = (int32_t)i;
             wo_u[slot] = eu[i];
             wo_v[slot] = ev[i];
@@ -1291,7 +1300,8 @@ spc_status select_typed(spc_context* ctx, const GraphView& g, const KT* key,
         // the slab of a very large single-graph selection: its edges become the first work
         // list, so the first round does not sweep every edge.  Below kSlabListMin edges, and
         // for a batch's per-graph slabs, the extra pass costs more than the sweep it replaces.
-        const bool slab_list = !batched && m >= kSlabListMin && (use_prefix || slab_lo);
+        const bool slab_list = !batched && m >= kSlabListMin && (use_prefix || slab_lo) &&
+                               (reinterpret_cast<uintptr_t>(key) & 15) == 0;
         if (attempt == 0) {
             SPC_LAUNCH(ctx, k_bv_init, grid_for(n > m ? n : m + 1, kThreads, maxb), kThreads, 0,
                        n, m, parent, W.best_k[0].as<unsigned long long>(),
