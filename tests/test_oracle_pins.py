@@ -233,6 +233,65 @@ def test_greedy_bruteforce_small_graphs():
     assert checked > 300
 
 
+def _prefix_forest(n, eu, ev, order, ids):
+    """Edge ids of the minimum spanning forest of the edges `ids` (rank in `order` as weight),
+    by plain Kruskal: ascending rank, union-find with no other structure."""
+    rank = np.empty(len(order), dtype=np.int64)
+    rank[np.asarray(order)] = np.arange(len(order))
+    parent = list(range(n))
+
+    def find(x):
+        while parent[x] != x:
+            x = parent[x]
+        return x
+
+    out = []
+    for e in sorted(ids, key=lambda e: rank[e]):
+        a, b = find(int(eu[e])), find(int(ev[e]))
+        if a != b:
+            parent[max(a, b)] = min(a, b)
+            out.append(int(e))
+    return out
+
+
+def test_prefix_forest_gives_the_merges_and_extends_by_slabs():
+    """Kruskal's view of Algorithm 1's merge loop, on prefixes of the sorted (f, eid) list:
+    (1) for every prefix whose spanning forest holds at least k = n - n_c edges, the k
+    lightest of them give the loop's partition; (2) the forest of a longer prefix is the
+    forest of the shorter one plus the next slab of edges, so a selection can resume slab by
+    slab instead of starting over.  Checked against the oracle's loop, not against itself."""
+    cases = [I.random_graph(24 + s, 0.25, 70 + s, weight="float", dtype=np.float64,
+                            connected=(s % 2 == 0)) for s in range(6)]
+    cases.append(I.clique_ring(12, 4, 3, np.float64))
+    cases.append(I.rgg_3d(256, 8.0, 5, np.float32))
+    checked = resumed = 0
+    for g in cases:
+        f = O.score(g)
+        order = O.sort_fitness(f)
+        m = len(order)
+        for n_c in (1, g.n // 8, g.n // 4, g.n // 2, g.n - 1):
+            k = g.n - max(1, n_c)
+            if k <= 0:
+                continue
+            _, merged, _, _ = O.greedy_merge(g, order, max(1, n_c))
+            want = sorted(np.nonzero(merged)[0].tolist())
+            rank = np.empty(m, dtype=np.int64)
+            rank[order] = np.arange(m)
+            for P in sorted({k, (3 * k) // 2, 2 * k, (5 * m) // 8, m}):
+                P = min(P, m)
+                forest = _prefix_forest(g.n, g.eu, g.ev, order, order[:P])
+                if len(forest) >= k:
+                    lightest = sorted(forest, key=lambda e: rank[e])[:k]
+                    assert sorted(lightest) == want
+                    checked += 1
+                for P2 in (min(m, P + max(1, P // 2)), m):
+                    whole = _prefix_forest(g.n, g.eu, g.ev, order, order[:P2])
+                    slab = forest + [int(e) for e in order[P:P2]]
+                    assert sorted(_prefix_forest(g.n, g.eu, g.ev, order, slab)) == sorted(whole)
+                    resumed += 1
+    assert checked > 60 and resumed > 100
+
+
 def test_relabel_is_first_occurrence_order():
     g = I.random_graph(50, 0.1, 9, weight="float", dtype=np.float64, connected=True)
     lv = O.coarsen_level(g, 17)
