@@ -116,6 +116,30 @@ def _score_rate(g, fn, budget_s):
     return done / t / 1e6, out
 
 
+def _host():
+    """The host the CPU numbers were taken on: its hardware threads and processor model."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name:"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if model is None:
+        try:
+            with open("/proc/cpuinfo") as fh:
+                for line in fh:
+                    if line.lower().startswith("model name"):
+                        model = line.split(":", 1)[1].strip()
+                        break
+        except OSError:
+            pass
+    import platform
+    return {"nproc": os.cpu_count(), "machine": platform.machine(), "model": model}
+
+
 def cpu_baseline(workload, budget_s=10.0):
     from oracle import oracle as O
     spec = SAMPLES[workload]
@@ -136,7 +160,8 @@ def cpu_baseline(workload, budget_s=10.0):
                       f"{dt:.1f} s single-threaded C",
             "score_step": {"unit": "M edges/s", "sequential": seq, "parallel": par,
                            "parallel_threads": threads,
-                           "sample": f"level-0 scores (S1-S3) of the same sample, ~2 s each"}}
+                           "sample": f"level-0 scores (S1-S3) of the same sample, ~2 s each"},
+            "host": _host()}
 
 
 def _oracle_batch_sample():
@@ -165,7 +190,7 @@ def _oracle_batched(budget_s=10.0):
         runs += 1
     return {"value": sub.B * runs / t, "unit": "graphs/s", "cores": 1, "kind": "oracle",
             "sample": f"{sub.B} sampled graphs of the batch, {runs} runs, {t:.1f} s "
-                      f"single-threaded C"}
+                      f"single-threaded C", "host": _host()}
 
 
 def run_reference_batched(args):
@@ -184,7 +209,8 @@ def run_reference_batched(args):
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": "c5_batch10k_f32", "sample_graphs": sub.B},
         "cpu_baseline": {"value": value, "unit": "graphs/s", "cores": 1, "kind": "oracle",
-                         "sample": f"{sub.B} sampled graphs of the batch per step"},
+                         "sample": f"{sub.B} sampled graphs of the batch per step",
+                         "host": _host()},
         "e2e": {"value": value, "unit": "graphs/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
@@ -217,7 +243,8 @@ def run_reference(args):
         "config": {"workload": args.workload, "sample_n": g.n, "sample_m": g.m},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                          "sample": f"{spec.get('mode', 'halving')} coarsening of the reduced "
-                                   f"construction (n={g.n}, m={g.m}) per step"},
+                                   f"construction (n={g.n}, m={g.m}) per step",
+                         "host": _host()},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
