@@ -31,7 +31,7 @@ k_label_round(int64_t n, const int64_t* __restrict__ rowptr, const int32_t* __re
     spc::pdl_wait();
     for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n;
          x += (int64_t)gridDim.x * blockDim.x) {
-        int32_t m = in ? in[x] : (int32_t)x;  // round 1 starts from the ids
+        int32_t m = in ? in[x] : (int32_t)x;  // the first label round starts from the ids
         const int64_t r1 = rowptr[x + 1];
         for (int64_t j0 = rowptr[x]; j0 < r1; j0 += kLabelBatch) {
             int32_t y[kLabelBatch];
