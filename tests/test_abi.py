@@ -69,3 +69,48 @@ def test_product_path_does_not_import_oracle():
             if f.endswith((".py", ".cu", ".cuh", ".h", ".c")):
                 txt = open(os.path.join(dirpath, f)).read()
                 assert "oracle" not in txt.lower() or f == "inputs.py", f
+
+
+def _close(s, i):
+    """Index just past the parenthesis that closes the one at s[i]."""
+    depth = 0
+    while True:
+        depth += {"(": 1, ")": -1}.get(s[i], 0)
+        i += 1
+        if depth == 0:
+            return i
+
+
+def _kernels():
+    """(file, name, body) of every __global__ function defined in the library's sources."""
+    csrc = os.path.join(ROOT, "paper_2204_11757_gb300", "csrc")
+    out = []
+    for f in sorted(os.listdir(csrc)):
+        if not f.endswith((".cu", ".cuh")):
+            continue
+        s = open(os.path.join(csrc, f)).read()
+        for mm in re.finditer(r"__global__\s+void\b", s):
+            rest = s[mm.end():].lstrip()
+            if rest.startswith("__launch_bounds__"):  # skip the attribute and its arguments
+                rest = rest[_close(rest, rest.index("(")):].lstrip()
+            name = re.match(r"(\w+)\s*\(", rest).group(1)
+            i = _close(rest, rest.index("("))  # past the parameter list
+            body_start = rest.index("{", i)
+            assert ";" not in rest[i:body_start], (f, name)  # a definition, not a declaration
+            out.append((f, name, rest[body_start + 1:]))
+    return out
+
+
+def test_every_kernel_waits_for_its_predecessor_first():
+    """Kernels are launched with programmatic stream serialization: each may start while the
+    kernel before it on the stream is still running, so before its first memory access each
+    must wait for it (spc::pdl_wait()).  Only compile-time statements may precede the wait."""
+    ks = _kernels()
+    assert len(ks) > 100
+    for f, name, body in ks:
+        for stmt in body.split(";"):
+            st = stmt.strip()
+            if st.startswith(("static_assert", "constexpr")):
+                continue
+            assert re.fullmatch(r"(spc::)?pdl_wait\(\)", st), (f, name, st[:80])
+            break
